@@ -1,0 +1,137 @@
+"""One iteration of Algorithm 1 ("Level set algorithm", Sec. 4) in the oracle.
+
+Order within iteration i (0-based): coefficients from phi^i; state solve;
+adjoint (closed form for the compliance costs: p = -u for heat, Sec. 6.3, and
+p = -2u for elasticity, Sec. 6.2, already folded into the S tensors); cost and
+constraint; one PPL update giving lambda (Sec. 5.4); S-assembly; velocity solve
+and B(theta, theta); adaptive time; transport to phi^{i+1}; reinitialisation
+when reinit_step > 0, i > 0 and i mod reinit_step == 0 (Sec. 5.7).
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import fem, levelset, ppl as ppl_mod, shape, solvers, velocity
+from .mesh import BoxMesh
+
+HEAT, ELASTIC, HELMHOLTZ = 0, 1, 2
+
+
+@dataclass
+class Problem:
+    mesh: BoxMesh
+    kind: int = HEAT
+    a_in: float = 1.0
+    a_out: float = 1e-3
+    E: float = 1.0
+    nu: float = 0.3
+    dirichlet_faces: list = field(default_factory=list)     # [(axis, side)]
+    f_nodal: np.ndarray = None                               # heat / Helmholtz body source
+    point_loads: list = field(default_factory=list)          # [(node, vector)]
+    tractions: list = field(default_factory=list)            # [(axis, side, vector)]
+    volume_target: float = 0.0                               # V; 0 = unconstrained
+    k: float = 1.0                                           # Helmholtz conductivity factor
+    omega: float = 0.0                                       # Helmholtz zero-order coefficient
+    vform: velocity.VelocityForm = field(default_factory=velocity.VelocityForm)
+
+    @property
+    def ncomp(self):
+        return self.mesh.dim if self.kind == ELASTIC else 1
+
+    def dirichlet(self):
+        return self.mesh.dirichlet_mask(self.dirichlet_faces, self.ncomp)
+
+    def load(self):
+        m = self.mesh
+        n = m.num_nodes * self.ncomp
+        F = np.zeros(n)
+        if self.kind in (HEAT, HELMHOLTZ) and self.f_nodal is not None:
+            F += fem.body_load(m.coords, m.cells, self.f_nodal)
+        for node, vec in self.point_loads:
+            for c in range(self.ncomp):
+                F[node * self.ncomp + c] += vec[c]
+        for axis, side, vec in self.tractions:
+            F += fem.facet_load(m.coords, m.boundary_facets(axis, side), vec, self.ncomp)
+        F[self.dirichlet() == 1] = 0.0
+        return F
+
+    def stiffness(self, A):
+        m = self.mesh
+        vol, g = fem.geometry(m.coords, m.cells)
+        if self.kind == ELASTIC:
+            lam, mu = fem.lame(self.E, self.nu)
+            Ke = fem.elastic_stiffness(vol, g, A, lam, mu)
+        else:
+            Ke = fem.scalar_stiffness(vol, g, A * self.k)
+            if self.kind == HELMHOLTZ and self.omega != 0.0:
+                Ke = Ke + self.omega**2 * fem.mass(vol, m.dim)
+        return fem.assemble(Ke, fem.element_dofs(m.cells, self.ncomp), m.num_nodes * self.ncomp)
+
+    def state(self, phi):
+        A, chi = shape.coefficient(phi, self.mesh.cells, self.a_in, self.a_out)
+        K = self.stiffness(A)
+        u = solvers.solve_free(K, self.load(), self.dirichlet() == 0)
+        return u, A, chi
+
+    def cost(self, u, A):
+        m = self.mesh
+        vol, g = fem.geometry(m.coords, m.cells)
+        if self.kind == ELASTIC:
+            lam, mu = fem.lame(self.E, self.nu)
+            return shape.elastic_cost(vol, g, A, u, m.cells, lam, mu)
+        if self.kind == HEAT:
+            return shape.heat_cost(vol, g, A, u, m.cells)
+        return float(self.load() @ u)                      # J = int f u
+
+    def constraint(self, chi):
+        vol, _ = fem.geometry(self.mesh.coords, self.mesh.cells)
+        return shape.volume(vol, chi) / self.volume_target
+
+    def rhs(self, u, A, chi, lam):
+        m = self.mesh
+        V = self.volume_target if self.volume_target > 0 else 1.0
+        if self.kind == ELASTIC:
+            le, me = fem.lame(self.E, self.nu)
+            return shape.elastic_rhs(m.coords, m.cells, A, u, le, me, lam, chi, V)
+        if self.kind == HEAT:
+            f = self.f_nodal if self.f_nodal is not None else np.zeros(m.num_nodes)
+            return shape.heat_rhs(m.coords, m.cells, A, u, f, lam, chi, V)
+        b = shape.helmholtz_rhs(m.coords, m.cells, A, self.k, self.omega, u, self.f_nodal)
+        if lam != 0.0:
+            b = b + lam * shape.volume_rhs(m.coords, m.cells, chi, V)
+        return b
+
+
+@dataclass
+class RunOptions:
+    """Run parameters of runDP / runTP / runMP (Sec. 5.1) used by one iteration."""
+    dfactor: float = 1e-2
+    lv_time: tuple = (1e-3, 1e-1)
+    lv_iter: tuple = (8, 16)
+    smooth: bool = False
+    reinit_step: int = 0
+    reinit_pars: tuple = (8, 1e-1)
+    h: float = None
+
+
+def opt_step(prob, phi, i, ppl_state, opts):
+    """One iteration of Algorithm 1; returns (phi^{i+1}, log dict)."""
+    h = opts.h if opts.h is not None else prob.mesh.diameter()
+    u, A, chi = prob.state(phi)
+    J = prob.cost(u, A)
+    lam, L, C = 0.0, J, None
+    if prob.volume_target > 0:
+        C = prob.constraint(chi)
+        lam_v, L = ppl_state.update([C], J)
+        lam = float(lam_v[0])
+    b = prob.rhs(u, A, chi, lam)
+    theta, Btt = velocity.solve(prob.mesh, prob.vform, b)
+    t_end, ns = ppl_mod.adaptime(Btt, opts.dfactor, opts.lv_time, opts.lv_iter)
+    phi_new = levelset.transport(prob.mesh, phi, theta, t_end, ns, h, opts.smooth)
+    reinit_done = False
+    if opts.reinit_step and i > 0 and i % opts.reinit_step == 0:
+        phi_new = levelset.reinit(prob.mesh, phi_new, opts.reinit_pars[0], opts.reinit_pars[1], h)
+        reinit_done = True
+    log = dict(J=J, C=C, L=L, lam=lam, Btt=Btt, t_end=t_end, nsteps=ns, reinit=reinit_done,
+               u=u, theta=theta, rhs=b)
+    return phi_new, log
