@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the level-set shape-optimisation step on GB300.
+
+Workload: the 2D linear-elasticity cantilever compliance problem, P1-vector on a 256 x 128
+Kuhn mesh of (0,2) x (0,1) (65,536 triangles, 66,306 DOFs), E = 1, nu = 0.3, ersatz
+contrast 1e-3, left edge clamped, unit point load (0,-1) at (2, 0.5), volume V = 1 through
+the Proximal-Perturbed Lagrangian, velocity form with the 1e4 normal and subdomain
+penalties, smooth transport, reinitialisation every 4 iterations with (20, 0.1),
+dfactor 0.1; phi0 = a lattice of 32 round holes of radius 0.08.  One step = one iteration of
+Algorithm 1 (coefficients, state solve, cost and constraint, PPL update, shape derivative,
+velocity solve, adaptive time, transport, reinitialisation on every 4th iteration).  The
+run is the optimisation itself: W warm-up iterations, then K timed iterations (default
+3 + 47 = the 50 iterations of the workload).
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead (on the host
+cores, a bounded sample of the same iterations).  Multi-GPU (torchrun): every rank runs an
+independent replica of the workload (the step does not shard); rank 0 prints.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG GDOF-iters/s & opt-iters/s vs HBM roofline; batched/served vs plain; p99 ms"
+WORKLOAD = ("cantilever2d: P1-vector elasticity compliance on a 256x128 Kuhn mesh of (0,2)x(0,1) "
+            "(65,536 triangles, 66,306 DOFs), E=1, nu=0.3, ersatz 1e-3, clamp x=0, point load (0,-1) at (2,0.5), "
+            "V=1 via PPL, 50 Algorithm-1 iterations (reinit every 4)")
+NX, NY = 256, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=47)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--l2-flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------ problem
+def run_options(api, precision):
+    prec = api.FO_MIXED if precision == "mixed" else api.FO_FP64
+    state = api.solve_opts(precision=prec, rtol=1e-12, warm_start=1)
+    vel = api.solve_opts(rtol=1e-12, warm_start=1)
+    tr = api.solve_opts(rtol=1e-12)
+    return api.run_options(dfactor=0.1, lv_time=(1e-3, 1e-1), lv_iter=(8, 16), smooth=True, reinit_step=4,
+                           reinit_pars=(20, 0.1), state=state, velocity=vel, transport=tr)
+
+
+def make_problem(api, ctx):
+    from paper_2601_05709_gb300 import workloads
+    mesh = ctx.mesh_box(2, (NX, NY), (0.0, 0.0), (2.0, 1.0))
+    desc = api.model_desc(api.FO_ELASTIC, a_in=1.0, a_out=1e-3, E=1.0, nu=0.3, dirichlet=[(0, 0)],
+                          point_loads=[(mesh.node_id((NX, NY // 2)), (0.0, -1.0))], volume=1.0, alpha_mass=0.1,
+                          normal_penalty=1e4, omega0_weight=1e4, omega0_boxes=[((1.95, 0.42), (float("inf"), 0.58))])
+    prob = mesh.problem(desc)
+    centres, radii = workloads.hole_lattice()
+    prob.initial_level(centres, radii, factor=1.0, ord=2)
+    return mesh, prob
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------- cpu oracle
+CPU_SAMPLE_ITERS = 4
+
+
+def oracle_sample(iters, warm=0):
+    """Time the FP64 oracle on iterations 0..iters-1 of the workload (single host thread).
+
+    Runs in a fresh interpreter (spawned before any CUDA work in this one matters) with the
+    BLAS / OpenMP thread pools pinned to one thread, so `cores` is 1."""
+    code = f"""
+import json, os, sys, time
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from oracle import algorithm as oalg, levelset, ppl
+from oracle.mesh import BoxMesh
+from oracle.velocity import VelocityForm
+from paper_2601_05709_gb300 import workloads
+m = BoxMesh(2, ({NX}, {NY}), (0.0, 0.0), (2.0, 1.0))
+prob = oalg.Problem(mesh=m, kind=oalg.ELASTIC, a_in=1.0, a_out=1e-3, E=1.0, nu=0.3, dirichlet_faces=[(0, 0)],
+                    point_loads=[(int(m.node_id(np.array([{NX}, {NY // 2}]))), (0.0, -1.0))], volume_target=1.0,
+                    vform=VelocityForm(alpha_mass=0.1, normal_penalty=1e4, omega0_weight=1e4,
+                                       omega0_boxes=[((1.95, 0.42), (np.inf, 0.58))]))
+c, r = workloads.hole_lattice()
+phi = levelset.initial_level(m.coords, c, r)
+st = ppl.PPL(1)
+opts = oalg.RunOptions(dfactor=0.1, smooth=True, reinit_step=4, reinit_pars=(20, 0.1))
+times = []
+for i in range({iters + warm}):
+    t = time.perf_counter()
+    phi, log = oalg.opt_step(prob, phi, i, st, opts)
+    times.append(time.perf_counter() - t)
+print(json.dumps({{"times": times[{warm}:], "J": log["J"]}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1200)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu model")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+# ----------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    iters = max(1, min(args.steps, CPU_SAMPLE_ITERS))
+    res = oracle_sample(iters, warm=0)
+    total = sum(res["times"])
+    value = iters / total
+    sample = f"iterations 0..{iters - 1} of the 50 (FP64 oracle, sparse direct solves)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "opt-iters/s", "n_gpus": args.gpus,
+        "steps": iters, "warmup": 0, "ms_per_step": 1e3 * total / iters, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": "single host thread"},
+        "cpu_baseline": {"value": value, "unit": "opt-iters/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "cpu": cpu_model()},
+        "e2e": {"value": value, "unit": "opt-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps")
+    # the CPU baseline runs first, in its own interpreter, before this process touches CUDA
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(CPU_SAMPLE_ITERS)
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2601_05709_gb300 import api
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    ctx = api.Context(local, stream=stream.cuda_stream)
+    ctx.set_timing(True)
+    mesh, prob = make_problem(api, ctx)
+    opts = run_options(api, args.precision)
+    ppl = api.PPL(1)
+    flush = torch.empty(max(args.l2_flush_mb, 1) * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2
+
+    it = 0
+    for _ in range(args.warmup):
+        prob.opt_step(it, opts, ppl)
+        it += 1
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    logs = []
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = api.launch_count()
+    for k in range(args.steps):
+        flush.zero_()                                    # evict the working set from L2
+        ev0[k].record(stream)
+        logs.append(prob.opt_step(it, opts, ppl))
+        ev1[k].record(stream)
+        it += 1
+    torch.cuda.synchronize()
+    launches = api.launch_count() - launches0 - 0     # our kernels only (the flush is torch's)
+    if dist:
+        dist.barrier()
+    clock_info = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_s = sum(ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * args.steps / total_s
+
+    # PCG work: state DOF-iterations (free DOFs x operator applies) + velocity (2 N_n per apply)
+    ndof_free = 2 * mesh.num_nodes - 2 * (NY + 1)
+    state_applies = sum(l.state.operator_applies for l in logs)
+    vel_applies = sum(l.velocity.operator_applies for l in logs)
+    gdof = (ndof_free * state_applies + 2 * mesh.num_nodes * vel_applies) / total_s / 1e9
+    state_iters = sum(l.state.iterations for l in logs)
+    state_ms = sum(l.ms_state for l in logs)
+    phase = {k: sum(getattr(l, "ms_" + k) for l in logs) / len(logs)
+             for k in ("state", "functionals", "shape", "velocity", "transport", "reinit")}
+
+    # roofline of the dominant kernel: the persistent state PCG (FP64 elasticity apply + CG)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    NT = 2 * NX * NY
+    flop_per_it = 210.0 * mesh.num_nodes + 12.0 * 2 * mesh.num_nodes     # elastic apply + CG vector updates
+    bytes_per_it = 96.0 * 2 * mesh.num_nodes + 8.0 * NT
+    if args.precision == "fp64":
+        achieved = flop_per_it * state_iters / (state_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s (FP64)",
+                "frac": achieved / 1.25, "traffic": None,
+                "kernel": "k_pcg<2, ElasticStateOp<2,double>, double, 1>",
+                "note": "FP64 peak 1.25 TFLOP/s nominal (probe measured 1.19); L2-resident working set "
+                        f"(~{bytes_per_it / 1e6:.1f} MB/iteration), so HBM is not the bound",
+                "hbm_frac_of_measured": bytes_per_it * state_iters / (state_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
+    else:
+        achieved = bytes_per_it / 2 * state_iters / (state_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                "frac": achieved / peaks.get("hbm_gbs", 6800.0), "traffic": None,
+                "kernel": "k_pcg<2, ElasticStateOp<2,float>, float, 1>"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "opt-iters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "precision": args.precision,
+                   "l2": f"flushed between timed steps ({args.l2_flush_mb} MiB write, untimed)"},
+        "pcg_gdof_iters_per_s": gdof, "state_pcg_iterations": state_iters,
+        "phase_ms_per_step": phase, "roofline": roof, "gpu_launches": int(launches), "clocks": clock_info,
+        "final": {"J": logs[-1].J, "C": logs[-1].C, "lambda": logs[-1].lam},
+    }
+
+    # end to end through the C ABI with host buffers: phi in from pinned host memory, phi out
+    if not args.no_e2e:
+        import numpy as np
+        mesh2, prob2 = make_problem(api, ctx)
+        ppl2 = api.PPL(1)
+        phi_host = torch.empty(mesh2.num_nodes, dtype=torch.float64).pin_memory()
+        phi_host.copy_(torch.from_numpy(prob2.get(api._lib.FO_FIELD_PHI)))
+        for i in range(args.warmup):
+            prob2.opt_step(i, opts, ppl2)
+        phi_host.copy_(torch.from_numpy(prob2.get(api._lib.FO_FIELD_PHI)))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = np.empty(mesh2.num_nodes)
+        for k in range(args.steps):
+            prob2.set_levelset(phi_host.numpy())            # H2D
+            log2 = prob2.opt_step(args.warmup + k, opts, ppl2)
+            out = prob2.get(api._lib.FO_FIELD_PHI)          # D2H
+            phi_host.copy_(torch.from_numpy(out))
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        line["e2e"] = {"value": args.steps / e2e_s, "unit": "opt-iters/s",
+                       "h2d_bytes_per_step": 8 * mesh2.num_nodes, "d2h_bytes_per_step": 8 * mesh2.num_nodes}
+    if cpu is not None:
+        line["cpu_baseline"] = {"value": len(cpu["times"]) / sum(cpu["times"]), "unit": "opt-iters/s", "cores": 1,
+                                "kind": "oracle", "cpu": cpu_model(),
+                                "sample": f"iterations 0..{len(cpu['times']) - 1} of the same optimisation, "
+                                          "FP64 oracle with sparse direct solves, one host thread"}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,261 @@
+/*
+ * formopt_gb300.h -- C ABI of the GB300 (sm_103a) level-set shape-optimisation hot path.
+ *
+ * The library computes one iteration of the level-set algorithm of arXiv 2601.05709
+ * (Algorithm 1, Sec. 4) on a fixed structured Kuhn simplicial mesh of a box D, with P1
+ * finite elements:
+ *   state solve with the ersatz coefficient A_Omega(phi)     (Sec. 6.2 eq. compli_weak,
+ *                                                             Sec. 6.3 eq. heat_weak)
+ *   cost and volume constraint                               (eqs compli_cost, heat_cost,
+ *                                                             compli_constr)
+ *   distributed shape derivative (S0, S1) assembled into the velocity right-hand side
+ *                                                            (Def. 2, eqs dJ1, dC1, S0andS1)
+ *   H1-type velocity solve for the descent direction theta   (Sec. 5.5, eq. velocity)
+ *   SUPG / Crank-Nicolson level-set transport                (Sec. 5.6, eq. weak_transport)
+ *   reinitialisation                                         (Sec. 5.7, eq. weak_HJ)
+ *   Proximal-Perturbed Lagrangian constraint update, on the host (Sec. 5.4, eq. lag_method)
+ *
+ * Conventions
+ *   - Every call returns fo_status (0 = FO_OK, negative = error).  No C++ exception crosses
+ *     the ABI.  fo_last_error(ctx) gives a message for the last failing call on that
+ *     context; the string is owned by the context and valid until its next call.
+ *   - A context owns every device allocation made for it (meshes, problems, scratch); the
+ *     matching _destroy call, or fo_ctx_destroy, frees them.  Handles die with the context.
+ *   - Device work is enqueued on the context's stream (the one given to fo_ctx_create, or a
+ *     stream the context creates).  Calls that return host values (fo_functionals,
+ *     fo_descent's B(theta, theta), fo_get, stats) synchronise that stream.
+ *   - Host arrays passed in are copied before the call returns.  Where a call takes
+ *     `on_device`, a nonzero value means the pointer is device memory on the context's
+ *     device (for example a torch tensor's data_ptr()); the caller keeps ownership.
+ *   - A context is not thread-safe: use one context per host thread.
+ *   - Mesh layout.  Node (i, j, k) has id i + (nx+1)(j + (ny+1)k) and coordinate
+ *     lo_a + (hi_a - lo_a) * i_a / n_a.  Cell (i, j, k) has id c = i + nx(j + ny k) and holds
+ *     d! simplices d!*c + p, one per permutation pi of the axes in lexicographic order, with
+ *     vertices v_0 = cell corner, v_{m+1} = v_m + e_{pi_m}.  Scalar DOF = node; vector DOF =
+ *     d*node + component.  Faces are numbered 2*axis + side (side 0: x_axis = lo, 1: = hi).
+ */
+#ifndef FORMOPT_GB300_H
+#define FORMOPT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FO_API __attribute__((visibility("default")))
+#else
+#define FO_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int fo_status;
+#define FO_OK              0
+#define FO_EINVAL         -1   /* bad argument (null pointer, size, enum)                    */
+#define FO_ENOMEM         -2   /* cudaMalloc failed                                         */
+#define FO_ENOMEM_BUDGET  -3   /* the allocation would exceed the context's memory budget   */
+#define FO_ECUDA          -4   /* a CUDA runtime call failed; see fo_last_error             */
+#define FO_ENOCONV        -5   /* a Krylov solve hit maxit; the result is written, stats say why */
+#define FO_ENAN           -6   /* NaN or Inf found in an input or a residual                */
+#define FO_ETIMEOUT       -7   /* a bounded device wait gave up (grid barrier) or fo_wait timed out */
+#define FO_EBUSY          -8   /* queue full (serving)                                      */
+#define FO_ESTATE         -9   /* call out of order (e.g. descent before shape derivative)  */
+
+typedef struct fo_ctx fo_ctx;
+typedef struct fo_mesh fo_mesh;
+typedef struct fo_problem fo_problem;
+
+/* model kinds (fo_model_desc.kind) */
+#define FO_HEAT       0   /* -div(A grad u) = f, J = int A |grad u|^2          (Sec. 6.3) */
+#define FO_ELASTIC    1   /* -div(A sigma(u)) = 0 + loads, J = int A sigma:eps   (Sec. 6.2) */
+#define FO_HELMHOLTZ  2   /* -div(A k grad u) + omega^2 u = f, J = int f u (screened family) */
+
+/* precisions (fo_solve_opts.precision) */
+#define FO_FP64   0       /* FP64 operator, vectors and reductions                        */
+#define FO_MIXED  1       /* FP32 inner PCG (FP64 dots) wrapped in FP64 iterative refinement */
+
+/* fields (fo_get / fo_set) */
+#define FO_FIELD_PHI    0 /* level set, N_n                                                */
+#define FO_FIELD_U      1 /* state, N_dof                                                 */
+#define FO_FIELD_P      2 /* adjoint, N_dof                                               */
+#define FO_FIELD_THETA  3 /* velocity, d*N_n interleaved                                  */
+#define FO_FIELD_RHS    4 /* shape-derivative RHS b, d*N_n interleaved                    */
+#define FO_FIELD_COEF   5 /* A_e per element (double)                                     */
+#define FO_FIELD_CHI    6 /* chi_e per element as double (0 / 1)                          */
+#define FO_FIELD_LOAD   7 /* state load F, N_dof (zero on Dirichlet DOFs)                 */
+#define FO_FIELD_OMEGA0 8 /* penalised-subdomain mask per element as double (0 / 1)       */
+
+/* operators (fo_apply) */
+#define FO_OP_STATE      0 /* y = K_A x, Dirichlet rows/columns replaced by identity      */
+#define FO_OP_VELOCITY   1 /* y = B x on d*N_n interleaved vectors (component-blocked)    */
+#define FO_OP_TRANSPORT_L 2 /* y = L x (after fo_transport_assemble)                      */
+#define FO_OP_TRANSPORT_R 3 /* y = R x (after fo_transport_assemble)                      */
+#define FO_OP_STATE_FP32 4 /* the FP32 state operator of the mixed path (x, y still double) */
+
+typedef struct {
+  int dim;                  /* 2 or 3                                                   */
+  int n[3];                 /* cells per axis                                           */
+  double lo[3], hi[3];      /* box                                                      */
+  int64_t num_nodes, num_cells, num_elems;
+  double volume;            /* |D|                                                      */
+  double h;                 /* mesh diameter of Sec. 5.6: the edge of the equilateral   */
+                            /* triangle / regular tet of measure |D|/N_T (square root   */
+                            /* of the printed expression)                               */
+} fo_mesh_info;
+
+typedef struct {
+  int kind;                 /* FO_HEAT / FO_ELASTIC / FO_HELMHOLTZ                      */
+  double a_in, a_out;       /* ersatz coefficient: a_in on {phi < 0}, a_out elsewhere   */
+  double E, nu;             /* elasticity (plane strain in 2D)                          */
+  double k, omega;          /* Helmholtz: conductivity factor and zero-order coefficient */
+  uint32_t dirichlet_faces; /* bit (2*axis + side): homogeneous Dirichlet on that face  */
+  const double *f_nodal;    /* host, N_n nodal source values (heat / Helmholtz) or NULL */
+  int n_point_loads;        /* <= 4                                                     */
+  int64_t point_node[4];
+  double point_vec[4][3];
+  int n_tractions;          /* <= 4, constant traction on a whole face                  */
+  int traction_face[4];
+  double traction_vec[4][3];
+  double volume_target;     /* V of C = |Omega| / V; 0 = unconstrained                  */
+  /* velocity form B (Sec. 5.5, eqs bd_plt, sub_dom, compli1_bili)                      */
+  double alpha_mass;        /* alpha_m int theta . xi                                   */
+  double normal_penalty;    /* gamma_b int_{dD} (theta.n)(xi.n)                         */
+  double omega0_weight;     /* gamma_0 int chi_{Omega_0} theta . xi                     */
+  int n_omega0;             /* <= 4 boxes; element in Omega_0 when its centroid is      */
+  double omega0_lo[4][3];   /* strictly inside one box (use +-inf for open sides)       */
+  double omega0_hi[4][3];
+  int velocity_dirichlet;   /* 1: H = H^1_0(D)^d                                        */
+} fo_model_desc;
+
+typedef struct {
+  int precision;            /* FO_FP64 or FO_MIXED                                      */
+  double rtol;              /* stop when ||r||_2 <= rtol ||b||_2                        */
+  int maxit;                /* iteration cap (FO_ENOCONV when reached)                  */
+  int warm_start;           /* 1: start from the field's current value                  */
+  double inner_rtol;        /* FO_MIXED: relative reduction asked of each FP32 solve    */
+  int inner_maxit;          /* FO_MIXED: cap per FP32 solve                             */
+  int grid_blocks;          /* 0 = autotuned; else blocks of the persistent kernel      */
+} fo_solve_opts;
+
+typedef struct {
+  int iterations;           /* Krylov iterations (FP64, or total inner FP32)            */
+  int outer_iterations;     /* FO_MIXED refinement steps                                */
+  int operator_applies;     /* operator applications in total                          */
+  double rel_residual;      /* final ||r||/||b|| (FP64)                                 */
+} fo_solve_stats;
+
+typedef struct {
+  double dfactor;           /* t_end = dfactor / B(theta, theta)        (eq. tend)      */
+  double t_min, t_max;      /* lv_time                                                  */
+  int s_min, s_max;         /* lv_iter                                  (eq. steps)     */
+  int smooth;               /* diffusion in the transport (eq. transport)               */
+  int reinit_step;          /* 0 = never; else reinitialise when i > 0, i % step == 0   */
+  int reinit_steps;         /* reinit_pars[0]                                           */
+  double reinit_time;       /* reinit_pars[1]                                           */
+  double h;                 /* mesh diameter used by transport / reinit (0 = mesh's)    */
+  fo_solve_opts state, velocity, transport;
+} fo_run_options;
+
+typedef struct {
+  int nc;                   /* number of constraints (<= 4)                             */
+  double r, delta, alpha, beta;
+  double z[4], lambda[4], mu[4];
+} fo_ppl;
+
+typedef struct {
+  double J, C, L, lambda, Btt, t_end;
+  int nsteps, reinit;
+  fo_solve_stats state, velocity, transport, reinit_stats;
+  /* device time of each phase in ms (CUDA events on the context stream; filled when
+   * fo_ctx_set_timing(ctx, 1) is on, else 0): coefficients + state solve, functionals,
+   * shape derivative, velocity, transport (assembly + steps), reinitialisation */
+  double ms_state, ms_functionals, ms_shape, ms_velocity, ms_transport, ms_reinit;
+} fo_iter_log;
+
+/* ---------------------------------------------------------------- context ----- */
+/* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to enqueue on
+ * (NULL: the context creates its own).  mem_budget_bytes: 0 = unlimited; otherwise device
+ * allocations beyond it fail with FO_ENOMEM_BUDGET. */
+FO_API fo_status fo_ctx_create(int device, void *cuda_stream, size_t mem_budget_bytes, fo_ctx **out);
+FO_API fo_status fo_ctx_destroy(fo_ctx *ctx);
+FO_API const char *fo_last_error(const fo_ctx *ctx);
+/* bytes of device memory currently held by the context */
+FO_API fo_status fo_ctx_memory(const fo_ctx *ctx, size_t *bytes_in_use);
+/* Turn per-phase device timing of fo_opt_step on (1) or off (0). */
+FO_API fo_status fo_ctx_set_timing(fo_ctx *ctx, int on);
+/* Number of kernels this library has launched in the process so far (all contexts). */
+FO_API fo_status fo_launch_count(unsigned long long *out);
+/* wait for all work enqueued on the context's stream */
+FO_API fo_status fo_ctx_sync(fo_ctx *ctx);
+
+/* ------------------------------------------------------------------- mesh ----- */
+/* Structured Kuhn mesh of prod [lo_a, hi_a] with n[a] cells per axis (Sec. 5.2 domain,
+ * replacing the paper's Gmsh meshes).  Connectivity and coordinates are built on the GPU. */
+FO_API fo_status fo_mesh_box(fo_ctx *ctx, int dim, const int n[3], const double lo[3], const double hi[3],
+                      fo_mesh **out);
+FO_API fo_status fo_mesh_destroy(fo_mesh *mesh);
+FO_API fo_status fo_mesh_query(const fo_mesh *mesh, fo_mesh_info *out);
+/* Copy connectivity (int32 [N_T][d+1]) and coordinates (f64 [N_n][d]) to host arrays;
+ * either pointer may be NULL. */
+FO_API fo_status fo_mesh_copy_out(const fo_mesh *mesh, int32_t *cells, double *coords);
+
+/* ---------------------------------------------------------------- problem ----- */
+FO_API fo_status fo_problem_create(fo_mesh *mesh, const fo_model_desc *desc, fo_problem **out);
+FO_API fo_status fo_problem_destroy(fo_problem *prob);
+/* Set the level set phi (N_n values). */
+FO_API fo_status fo_set_levelset(fo_problem *prob, const double *phi, int on_device);
+/* InitialLevel (Sec. 5.7, eq. phi0): phi = factor * max_k (radii_k - |x - centers_k|_ord),
+ * ord = 2 or 0 (0 means the infinity norm); centers [count][d] and radii on the host. */
+FO_API fo_status fo_initial_level(fo_problem *prob, int count, const double *centers, const double *radii,
+                           double factor, int ord);
+/* Element coefficient A_e and chi_e from phi (one-point rule: the vertex values of phi
+ * summed in vertex order; < 0 is inside, eqs heat_AOmega / compli_AOmega). */
+FO_API fo_status fo_coefficients(fo_problem *prob);
+/* State solve K_A u = F (Algorithm 1 step "state"). */
+FO_API fo_status fo_state_solve(fo_problem *prob, const fo_solve_opts *opts, fo_solve_stats *stats);
+/* Explicit adjoint solve K_A p = -c F with c = 2 for FO_ELASTIC (p = -2u, Sec. 6.2) and
+ * c = 1 otherwise (p = -u, Sec. 6.3); the shape derivative uses these closed forms. */
+FO_API fo_status fo_adjoint_solve(fo_problem *prob, const fo_solve_opts *opts, fo_solve_stats *stats);
+/* Cost J and constraint C = |Omega| / V (C = |Omega| when V = 0); synchronises. */
+FO_API fo_status fo_functionals(fo_problem *prob, double *J, double *C);
+/* Velocity RHS b[d*a + k] = sum_e int_e S0_k psi_a + (S1 grad psi_a)_k with
+ * S = S^J + lambda S^C (eq. S0andS1).  rhs_out (host, d*N_n) may be NULL. */
+FO_API fo_status fo_shape_derivative(fo_problem *prob, double lambda, double *rhs_out);
+/* Velocity solve B theta = -b (eq. velocity); Btt = B(theta, theta) = -b . theta. */
+FO_API fo_status fo_descent(fo_problem *prob, const fo_solve_opts *opts, double *Btt, fo_solve_stats *stats);
+/* Build the transport matrices L, R for time step dt (eq. weak_transport, tau of
+ * eq. tau_lv at degree-2 quadrature points, diffusion tested with the full grad psi^). */
+FO_API fo_status fo_transport_assemble(fo_problem *prob, double dt, double h, int smooth);
+/* nsteps Crank-Nicolson steps of size t_end/nsteps moving phi along theta. */
+FO_API fo_status fo_levelset_step(fo_problem *prob, double t_end, int nsteps, double h, int smooth,
+                           const fo_solve_opts *opts, fo_solve_stats *stats);
+/* Reinitialisation: nsteps steps of size t_final/nsteps, explicit Euler then AB2 (eq. weak_HJ). */
+FO_API fo_status fo_reinit(fo_problem *prob, int nsteps, double t_final, double h,
+                    const fo_solve_opts *opts, fo_solve_stats *stats);
+/* One Algorithm-1 iteration number `iter` (0-based): coefficients, state, functionals,
+ * PPL update (when V > 0), shape derivative, velocity, adaptive time, transport, reinit. */
+FO_API fo_status fo_opt_step(fo_problem *prob, int iter, const fo_run_options *opts, fo_ppl *ppl,
+                      fo_iter_log *log);
+/* Copy a field out to the host (synchronises) / in from host or device memory. */
+FO_API fo_status fo_get(fo_problem *prob, int field, double *host_out);
+FO_API fo_status fo_set(fo_problem *prob, int field, const double *values, int on_device);
+/* y = Op x for parity tests; x and y are host arrays (or device if on_device). */
+FO_API fo_status fo_apply(fo_problem *prob, int op, const double *x, double *y, int on_device);
+
+/* ------------------------------------------------------------- host-only ----- */
+/* PPL state with r = 0.999, delta0 = 0.5, alpha = 2000, beta = 0.5, z = lambda = mu = 0. */
+FO_API void fo_ppl_init(fo_ppl *s, int nc);
+/* One update of eq. lag_method from C; writes lambda (nc values) and L of eq. lagrangian. */
+FO_API void fo_ppl_update(fo_ppl *s, const double *C, double J, double *lambda_out, double *L_out);
+/* Adaptive time (eqs tend, steps): t_end clamped to [t_min, t_max] with B(theta, theta)
+ * floored at 1e-12, steps clamped to [s_min, s_max] and rounded half away from zero. */
+FO_API void fo_adaptime(double Btt, const fo_run_options *opts, double *t_end, int *nsteps);
+/* Default run options of runDP (Sec. 5.1) and default solver options. */
+FO_API void fo_run_options_default(fo_run_options *opts);
+FO_API void fo_solve_opts_default(fo_solve_opts *opts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FORMOPT_GB300_H */

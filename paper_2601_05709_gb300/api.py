@@ -1,0 +1,321 @@
+"""Python binding of the C ABI: the same calls, with numpy / torch arrays marshalled.
+
+Every computation runs in the CUDA library; this module only converts arguments, checks
+status codes and owns handles.  Device arrays may be passed as torch CUDA tensors (their
+data_ptr() is handed to the library with on_device = 1).
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (FO_ELASTIC, FO_FIELD_CHI, FO_FIELD_COEF, FO_FIELD_LOAD, FO_FIELD_OMEGA0, FO_FIELD_P,
+                   FO_FIELD_PHI, FO_FIELD_RHS, FO_FIELD_THETA, FO_FIELD_U, FO_FP64, FO_HEAT, FO_HELMHOLTZ,
+                   FO_MIXED, FO_OP_STATE, FO_OP_STATE_FP32, FO_OP_TRANSPORT_L, FO_OP_TRANSPORT_R,
+                   FO_OP_VELOCITY, FO_OK, FormoptError)
+
+__all__ = ["Context", "Mesh", "Problem", "model_desc", "solve_opts", "run_options", "PPL", "adaptime",
+           "FO_HEAT", "FO_ELASTIC", "FO_HELMHOLTZ", "FO_FP64", "FO_MIXED", "FormoptError"]
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _is_device(x):
+    return hasattr(x, "data_ptr") and getattr(x, "is_cuda", False)
+
+
+def solve_opts(precision=FO_FP64, rtol=1e-12, maxit=200000, warm_start=0, inner_rtol=1e-3, inner_maxit=20000,
+               grid_blocks=0):
+    o = _lib.SolveOpts()
+    _lib.load().fo_solve_opts_default(C.byref(o))
+    o.precision, o.rtol, o.maxit, o.warm_start = precision, rtol, maxit, int(warm_start)
+    o.inner_rtol, o.inner_maxit, o.grid_blocks = inner_rtol, inner_maxit, grid_blocks
+    return o
+
+
+def run_options(dfactor=1e-2, lv_time=(1e-3, 1e-1), lv_iter=(8, 16), smooth=False, reinit_step=0,
+                reinit_pars=(8, 1e-1), h=0.0, state=None, velocity=None, transport=None):
+    o = _lib.RunOptions()
+    _lib.load().fo_run_options_default(C.byref(o))
+    o.dfactor = dfactor
+    o.t_min, o.t_max = lv_time
+    o.s_min, o.s_max = lv_iter
+    o.smooth = int(bool(smooth))
+    o.reinit_step = int(reinit_step or 0)
+    o.reinit_steps, o.reinit_time = int(reinit_pars[0]), float(reinit_pars[1])
+    o.h = h
+    if state is not None:
+        o.state = state
+    if velocity is not None:
+        o.velocity = velocity
+    if transport is not None:
+        o.transport = transport
+    return o
+
+
+def model_desc(kind, a_in=1.0, a_out=1e-3, E=1.0, nu=0.3, k=1.0, omega=0.0, dirichlet=(), f_nodal=None,
+               point_loads=(), tractions=(), volume=0.0, alpha_mass=0.1, normal_penalty=0.0, omega0_weight=0.0,
+               omega0_boxes=(), velocity_dirichlet=False):
+    """Build a fo_model_desc.  dirichlet: [(axis, side)]; point_loads: [(node, vec)];
+    tractions: [(axis, side, vec)]; omega0_boxes: [(lo, hi)] with strict inequalities."""
+    d = _lib.ModelDesc()
+    d.kind, d.a_in, d.a_out, d.E, d.nu, d.k, d.omega = kind, a_in, a_out, E, nu, k, omega
+    mask = 0
+    for axis, side in dirichlet:
+        mask |= 1 << (2 * axis + side)
+    d.dirichlet_faces = mask
+    keep = None
+    if f_nodal is not None:
+        keep = _f64(f_nodal)
+        d.f_nodal = _dp(keep)
+    if len(point_loads) > 4 or len(tractions) > 4 or len(omega0_boxes) > 4:
+        raise ValueError("at most 4 point loads, tractions and subdomain boxes")
+    d.n_point_loads = len(point_loads)
+    for i, (node, vec) in enumerate(point_loads):
+        d.point_node[i] = int(node)
+        for c, v in enumerate(vec):
+            d.point_vec[i][c] = v
+    d.n_tractions = len(tractions)
+    for i, (axis, side, vec) in enumerate(tractions):
+        d.traction_face[i] = 2 * axis + side
+        for c, v in enumerate(vec):
+            d.traction_vec[i][c] = v
+    d.volume_target = volume
+    d.alpha_mass, d.normal_penalty, d.omega0_weight = alpha_mass, normal_penalty, omega0_weight
+    d.n_omega0 = len(omega0_boxes)
+    for i, (lo, hi) in enumerate(omega0_boxes):
+        for c in range(3):
+            d.omega0_lo[i][c] = lo[c] if c < len(lo) else -np.inf
+            d.omega0_hi[i][c] = hi[c] if c < len(hi) else np.inf
+    d.velocity_dirichlet = int(bool(velocity_dirichlet))
+    d._keep = keep                       # keep f alive until fo_problem_create copied it
+    return d
+
+
+class Context:
+    def __init__(self, device=0, stream=None, mem_budget=0):
+        self.lib = _lib.load()
+        h = C.c_void_p()
+        s = None if stream is None else C.c_void_p(int(stream))
+        st = self.lib.fo_ctx_create(device, s, mem_budget, C.byref(h))
+        if st != FO_OK:
+            raise FormoptError(st, "fo_ctx_create failed")
+        self.handle = h
+        self._children = []
+
+    def check(self, st, what=""):
+        if st != FO_OK:
+            msg = self.lib.fo_last_error(self.handle)
+            raise FormoptError(st, f"{what}: {msg.decode() if msg else ''}")
+        return st
+
+    def memory(self):
+        v = C.c_size_t()
+        self.check(self.lib.fo_ctx_memory(self.handle, C.byref(v)), "fo_ctx_memory")
+        return v.value
+
+    def sync(self):
+        self.check(self.lib.fo_ctx_sync(self.handle), "fo_ctx_sync")
+
+    def set_timing(self, on=True):
+        self.check(self.lib.fo_ctx_set_timing(self.handle, int(bool(on))), "fo_ctx_set_timing")
+
+    def mesh_box(self, dim, n, lo, hi):
+        return Mesh(self, dim, n, lo, hi)
+
+    def close(self):
+        if self.handle:
+            self.lib.fo_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh:
+    def __init__(self, ctx, dim, n, lo, hi):
+        self.ctx = ctx
+        nn = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+        lo3 = (C.c_double * 3)(*(list(lo) + [0.0] * (3 - len(lo))))
+        hi3 = (C.c_double * 3)(*(list(hi) + [1.0] * (3 - len(hi))))
+        h = C.c_void_p()
+        ctx.check(ctx.lib.fo_mesh_box(ctx.handle, dim, nn, lo3, hi3, C.byref(h)), "fo_mesh_box")
+        self.handle = h
+        info = _lib.MeshInfo()
+        ctx.check(ctx.lib.fo_mesh_query(h, C.byref(info)), "fo_mesh_query")
+        self.dim = info.dim
+        self.n = tuple(info.n[:dim])
+        self.num_nodes, self.num_cells, self.num_elems = info.num_nodes, info.num_cells, info.num_elems
+        self.volume, self.h = info.volume, info.h
+
+    def copy_out(self):
+        cells = np.empty((self.num_elems, self.dim + 1), dtype=np.int32)
+        coords = np.empty((self.num_nodes, self.dim), dtype=np.float64)
+        self.ctx.check(self.ctx.lib.fo_mesh_copy_out(self.handle, cells.ctypes.data_as(C.c_void_p),
+                                                     coords.ctypes.data_as(C.c_void_p)), "fo_mesh_copy_out")
+        return cells, coords
+
+    def node_id(self, ijk):
+        nid = 0
+        for a in reversed(range(self.dim)):
+            nid = nid * (self.n[a] + 1) + int(ijk[a])
+        return nid
+
+    def problem(self, desc):
+        return Problem(self, desc)
+
+
+class Problem:
+    def __init__(self, mesh, desc):
+        self.mesh, self.ctx = mesh, mesh.ctx
+        self.lib = self.ctx.lib
+        h = C.c_void_p()
+        self.ctx.check(self.lib.fo_problem_create(mesh.handle, C.byref(desc), C.byref(h)), "fo_problem_create")
+        self.handle = h
+        self.kind = desc.kind
+        self.ncomp = mesh.dim if desc.kind == FO_ELASTIC else 1
+
+    def _chk(self, st, what):
+        return self.ctx.check(st, what)
+
+    def set_levelset(self, phi):
+        if _is_device(phi):
+            self._chk(self.lib.fo_set_levelset(self.handle, C.c_void_p(phi.data_ptr()), 1), "fo_set_levelset")
+        else:
+            a = _f64(phi)
+            self._chk(self.lib.fo_set_levelset(self.handle, a.ctypes.data_as(C.c_void_p), 0), "fo_set_levelset")
+
+    def initial_level(self, centers, radii, factor=1.0, ord=2):
+        c = _f64(centers).reshape(-1)
+        r = _f64(radii)
+        o = 0 if ord in (np.inf, "inf", 0) else 2
+        self._chk(self.lib.fo_initial_level(self.handle, len(r), _dp(c), _dp(r), factor, o), "fo_initial_level")
+
+    def coefficients(self):
+        self._chk(self.lib.fo_coefficients(self.handle), "fo_coefficients")
+
+    def state_solve(self, opts=None, allow_noconv=False):
+        st = _lib.SolveStats()
+        s = self.lib.fo_state_solve(self.handle, C.byref(opts) if opts else None, C.byref(st))
+        if not (allow_noconv and s == _lib.FO_ENOCONV):
+            self._chk(s, "fo_state_solve")
+        return st
+
+    def adjoint_solve(self, opts=None):
+        st = _lib.SolveStats()
+        self._chk(self.lib.fo_adjoint_solve(self.handle, C.byref(opts) if opts else None, C.byref(st)),
+                  "fo_adjoint_solve")
+        return st
+
+    def functionals(self):
+        J, Cv = C.c_double(), C.c_double()
+        self._chk(self.lib.fo_functionals(self.handle, C.byref(J), C.byref(Cv)), "fo_functionals")
+        return J.value, Cv.value
+
+    def shape_derivative(self, lam=0.0, copy=True):
+        out = np.empty(self.mesh.dim * self.mesh.num_nodes) if copy else None
+        ptr = out.ctypes.data_as(C.c_void_p) if copy else None
+        self._chk(self.lib.fo_shape_derivative(self.handle, lam, ptr), "fo_shape_derivative")
+        return out
+
+    def descent(self, opts=None):
+        btt = C.c_double()
+        st = _lib.SolveStats()
+        self._chk(self.lib.fo_descent(self.handle, C.byref(opts) if opts else None, C.byref(btt), C.byref(st)),
+                  "fo_descent")
+        return btt.value, st
+
+    def transport_assemble(self, dt, h, smooth):
+        self._chk(self.lib.fo_transport_assemble(self.handle, dt, h, int(smooth)), "fo_transport_assemble")
+
+    def levelset_step(self, t_end, nsteps, h, smooth, opts=None):
+        st = _lib.SolveStats()
+        self._chk(self.lib.fo_levelset_step(self.handle, t_end, nsteps, h, int(smooth),
+                                            C.byref(opts) if opts else None, C.byref(st)), "fo_levelset_step")
+        return st
+
+    def reinit(self, nsteps, t_final, h, opts=None):
+        st = _lib.SolveStats()
+        self._chk(self.lib.fo_reinit(self.handle, nsteps, t_final, h, C.byref(opts) if opts else None,
+                                     C.byref(st)), "fo_reinit")
+        return st
+
+    def opt_step(self, it, opts, ppl=None):
+        log = _lib.IterLog()
+        self._chk(self.lib.fo_opt_step(self.handle, it, C.byref(opts), C.byref(ppl.state) if ppl else None,
+                                       C.byref(log)), "fo_opt_step")
+        return log
+
+    def _field_len(self, field):
+        m = self.mesh
+        if field in (FO_FIELD_U, FO_FIELD_P, FO_FIELD_LOAD):
+            return self.ncomp * m.num_nodes
+        if field in (FO_FIELD_THETA, FO_FIELD_RHS):
+            return m.dim * m.num_nodes
+        if field in (FO_FIELD_COEF, FO_FIELD_CHI, FO_FIELD_OMEGA0):
+            return m.num_elems
+        return m.num_nodes
+
+    def get(self, field):
+        out = np.empty(self._field_len(field))
+        self._chk(self.lib.fo_get(self.handle, field, out.ctypes.data_as(C.c_void_p)), "fo_get")
+        return out
+
+    def set(self, field, values):
+        if _is_device(values):
+            self._chk(self.lib.fo_set(self.handle, field, C.c_void_p(values.data_ptr()), 1), "fo_set")
+        else:
+            a = _f64(values)
+            self._chk(self.lib.fo_set(self.handle, field, a.ctypes.data_as(C.c_void_p), 0), "fo_set")
+
+    def apply(self, op, x):
+        x = _f64(x)
+        y = np.empty_like(x)
+        self._chk(self.lib.fo_apply(self.handle, op, x.ctypes.data_as(C.c_void_p), y.ctypes.data_as(C.c_void_p), 0),
+                  "fo_apply")
+        return y
+
+    def close(self):
+        if self.handle and self.ctx.handle:
+            self.lib.fo_problem_destroy(self.handle)
+        self.handle = None
+
+
+class PPL:
+    """Host-side PPL state of the library (fo_ppl_init / fo_ppl_update)."""
+
+    def __init__(self, nc=1):
+        self.lib = _lib.load()
+        self.state = _lib.PPLState()
+        self.lib.fo_ppl_init(C.byref(self.state), nc)
+
+    def update(self, C_values, J):
+        cv = _f64(np.atleast_1d(C_values))
+        lam = np.zeros(4)
+        L = C.c_double()
+        self.lib.fo_ppl_update(C.byref(self.state), _dp(cv), J, _dp(lam), C.byref(L))
+        return lam[: self.state.nc].copy(), L.value
+
+
+def launch_count():
+    """Kernels the library has launched in this process so far."""
+    v = C.c_ulonglong()
+    _lib.load().fo_launch_count(C.byref(v))
+    return v.value
+
+
+def adaptime(Btt, opts=None):
+    lib = _lib.load()
+    opts = opts or run_options()
+    t, n = C.c_double(), C.c_int()
+    lib.fo_adaptime(Btt, C.byref(opts), C.byref(t), C.byref(n))
+    return t.value, n.value

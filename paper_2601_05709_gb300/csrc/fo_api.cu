@@ -1,0 +1,730 @@
+// Host side of the C ABI: contexts, meshes, problems, field I/O, the host-only PPL and
+// adaptive-time helpers, and the orchestration of one Algorithm-1 iteration.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <algorithm>
+#include <atomic>
+
+#include "fo_internal.cuh"
+
+// ----------------------------------------------------------------------- launch counter
+static std::atomic<unsigned long long> g_launches{0};
+void fo_note_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+extern "C" fo_status fo_launch_count(unsigned long long *out) {
+  if (!out) return FO_EINVAL;
+  *out = g_launches.load(std::memory_order_relaxed);
+  return FO_OK;
+}
+
+// ------------------------------------------------------------------------- status helpers
+fo_status fo_fail(fo_ctx *ctx, fo_status st, const char *fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return st;
+}
+
+fo_status fo_cuda_check(fo_ctx *ctx, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return FO_OK;
+  if (e == cudaErrorMemoryAllocation) return fo_fail(ctx, FO_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return fo_fail(ctx, FO_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+fo_status fo_alloc(fo_ctx *ctx, void **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return FO_OK;
+  if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+    return fo_fail(ctx, FO_ENOMEM_BUDGET, "allocation of %zu bytes exceeds the budget (%zu of %zu in use)",
+                   bytes, ctx->in_use, ctx->budget);
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fo_cuda_check(ctx, e, "cudaMalloc");
+  }
+  ctx->in_use += bytes;
+  return FO_OK;
+}
+
+void fo_free(fo_ctx *ctx, void *p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  ctx->in_use -= std::min(ctx->in_use, bytes);
+}
+
+// ------------------------------------------------------------------------------- context
+extern "C" fo_status fo_ctx_create(int device, void *cuda_stream, size_t mem_budget_bytes, fo_ctx **out) {
+  if (!out) return FO_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FO_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return FO_ECUDA;
+  fo_ctx *c = new fo_ctx();
+  c->device = device;
+  c->budget = mem_budget_bytes;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return FO_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  if (cudaMallocHost(&c->h_scalars, 64 * sizeof(double)) != cudaSuccess) {
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return FO_ENOMEM;
+  }
+  *out = c;
+  return FO_OK;
+}
+
+extern "C" fo_status fo_ctx_destroy(fo_ctx *ctx) {
+  if (!ctx) return FO_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  while (!ctx->problems.empty()) fo_problem_destroy(ctx->problems.back());
+  while (!ctx->meshes.empty()) fo_mesh_destroy(ctx->meshes.back());
+  if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
+  for (auto &e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return FO_OK;
+}
+
+extern "C" fo_status fo_ctx_set_timing(fo_ctx *ctx, int on) {
+  if (!ctx) return FO_EINVAL;
+  if (on && !ctx->ev[0])
+    for (auto &e : ctx->ev) FO_CU(ctx, cudaEventCreate(&e));
+  ctx->timing = on ? 1 : 0;
+  return FO_OK;
+}
+
+extern "C" const char *fo_last_error(const fo_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" fo_status fo_ctx_memory(const fo_ctx *ctx, size_t *bytes) {
+  if (!ctx || !bytes) return FO_EINVAL;
+  *bytes = ctx->in_use;
+  return FO_OK;
+}
+
+extern "C" fo_status fo_ctx_sync(fo_ctx *ctx) {
+  if (!ctx) return FO_EINVAL;
+  FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  return FO_OK;
+}
+
+// ---------------------------------------------------------------------------------- mesh
+static double mesh_diameter(const Grid &g) {
+  double D = 1.0;
+  for (int a = 0; a < g.dim; ++a) D *= g.hi[a] - g.lo[a];
+  double NT = (double)g.num_elems;
+  if (g.dim == 2) return std::sqrt(4.0 * D / (NT * std::sqrt(3.0)));
+  return std::sqrt(std::pow(6.0 * std::sqrt(2.0) * D / NT, 2.0 / 3.0));
+}
+
+extern "C" fo_status fo_mesh_box(fo_ctx *ctx, int dim, const int n[3], const double lo[3], const double hi[3],
+                                 fo_mesh **out) {
+  if (!ctx || !out || !n || !lo || !hi) return FO_EINVAL;
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return fo_fail(ctx, FO_EINVAL, "dim must be 2 or 3");
+  Grid g{};
+  g.dim = dim;
+  long long nodes = 1, cells = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (a < dim) {
+      if (n[a] < 1 || !(hi[a] > lo[a])) return fo_fail(ctx, FO_EINVAL, "bad extent on axis %d", a);
+      g.n[a] = n[a];
+      g.lo[a] = lo[a];
+      g.hi[a] = hi[a];
+    } else {
+      g.n[a] = 1;
+      g.lo[a] = 0;
+      g.hi[a] = 1;
+    }
+    g.nn[a] = (a < dim) ? (long long)g.n[a] + 1 : 1;
+    g.h[a] = (g.hi[a] - g.lo[a]) / g.n[a];
+    g.inv_h[a] = 1.0 / g.h[a];
+  }
+  g.stride[0] = 1;
+  g.stride[1] = g.nn[0];
+  g.stride[2] = g.nn[0] * g.nn[1];
+  g.cstride[0] = 1;
+  g.cstride[1] = g.n[0];
+  g.cstride[2] = (long long)g.n[0] * g.n[1];
+  for (int a = 0; a < dim; ++a) {
+    nodes *= g.nn[a];
+    cells *= g.n[a];
+  }
+  if (nodes > (1ll << 31) - 1) return fo_fail(ctx, FO_EINVAL, "mesh too large for int32 connectivity");
+  g.num_nodes = nodes;
+  g.num_cells = cells;
+  g.num_elems = cells * (dim == 2 ? 2 : 6);
+  g.vol_e = (dim == 2) ? g.h[0] * g.h[1] / 2.0 : g.h[0] * g.h[1] * g.h[2] / 6.0;
+  for (int a = 0; a < 3; ++a) {
+    if (dim == 2) g.facet_area[a] = g.h[1 - (a & 1)];
+    else {
+      int o1 = (a + 1) % 3, o2 = (a + 2) % 3;
+      g.facet_area[a] = g.h[o1] * g.h[o2] / 2.0;
+    }
+  }
+  fo_mesh *m = new fo_mesh();
+  m->ctx = ctx;
+  m->g = g;
+  m->h_diam = mesh_diameter(g);
+  fo_status st = fo_alloc(ctx, (void **)&m->d_cells, sizeof(int32_t) * g.num_elems * (dim + 1));
+  if (st == FO_OK) st = fo_alloc(ctx, (void **)&m->d_coords, sizeof(double) * g.num_nodes * dim);
+  if (st == FO_OK) st = fo_launch_mesh_build(m);
+  if (st != FO_OK) {
+    fo_free(ctx, m->d_cells, sizeof(int32_t) * g.num_elems * (dim + 1));
+    fo_free(ctx, m->d_coords, sizeof(double) * g.num_nodes * dim);
+    delete m;
+    return st;
+  }
+  ctx->meshes.push_back(m);
+  *out = m;
+  return FO_OK;
+}
+
+extern "C" fo_status fo_mesh_destroy(fo_mesh *m) {
+  if (!m) return FO_EINVAL;
+  fo_ctx *ctx = m->ctx;
+  cudaStreamSynchronize(ctx->stream);
+  for (size_t i = 0; i < ctx->problems.size();) {
+    if (ctx->problems[i]->mesh == m) fo_problem_destroy(ctx->problems[i]);
+    else ++i;
+  }
+  const Grid &g = m->g;
+  fo_free(ctx, m->d_cells, sizeof(int32_t) * g.num_elems * (g.dim + 1));
+  fo_free(ctx, m->d_coords, sizeof(double) * g.num_nodes * g.dim);
+  ctx->meshes.erase(std::remove(ctx->meshes.begin(), ctx->meshes.end(), m), ctx->meshes.end());
+  delete m;
+  return FO_OK;
+}
+
+extern "C" fo_status fo_mesh_query(const fo_mesh *m, fo_mesh_info *out) {
+  if (!m || !out) return FO_EINVAL;
+  const Grid &g = m->g;
+  memset(out, 0, sizeof *out);
+  out->dim = g.dim;
+  double D = 1;
+  for (int a = 0; a < 3; ++a) {
+    out->n[a] = a < g.dim ? g.n[a] : 0;
+    out->lo[a] = a < g.dim ? g.lo[a] : 0;
+    out->hi[a] = a < g.dim ? g.hi[a] : 0;
+    if (a < g.dim) D *= g.hi[a] - g.lo[a];
+  }
+  out->num_nodes = g.num_nodes;
+  out->num_cells = g.num_cells;
+  out->num_elems = g.num_elems;
+  out->volume = D;
+  out->h = m->h_diam;
+  return FO_OK;
+}
+
+extern "C" fo_status fo_mesh_copy_out(const fo_mesh *m, int32_t *cells, double *coords) {
+  if (!m) return FO_EINVAL;
+  fo_ctx *ctx = m->ctx;
+  const Grid &g = m->g;
+  if (cells)
+    FO_CU(ctx, cudaMemcpyAsync(cells, m->d_cells, sizeof(int32_t) * g.num_elems * (g.dim + 1),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+  if (coords)
+    FO_CU(ctx, cudaMemcpyAsync(coords, m->d_coords, sizeof(double) * g.num_nodes * g.dim, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  return FO_OK;
+}
+
+// ------------------------------------------------------------------------------- problem
+static size_t prob_bytes_fields(const fo_problem *p, std::vector<std::pair<void **, size_t>> &list) {
+  const Grid &g = p->mesh->g;
+  const long long NN = g.num_nodes, NT = g.num_elems, ND = p->ndof;
+  const int d = g.dim;
+  const int S = (d == 2) ? 7 : 15;
+  list = {
+      {(void **)&p->phi, sizeof(double) * NN},       {(void **)&p->coef, sizeof(double) * NT},
+      {(void **)&p->coef32, sizeof(float) * NT},     {(void **)&p->chi, NT},
+      {(void **)&p->omega0, NT},                     {(void **)&p->dir, ND},
+      {(void **)&p->vdir, NN},                       {(void **)&p->load, sizeof(double) * ND},
+      {(void **)&p->u, sizeof(double) * ND},         {(void **)&p->p, sizeof(double) * ND},
+      {(void **)&p->rhs, sizeof(double) * d * NN},   {(void **)&p->theta, sizeof(double) * d * NN},
+      {(void **)&p->dinv_state, sizeof(double) * ND}, {(void **)&p->dinv_state32, sizeof(float) * ND},
+      {(void **)&p->dinv_vel, sizeof(double) * d * NN}, {(void **)&p->L, sizeof(double) * S * NN},
+      {(void **)&p->R, sizeof(double) * S * NN},     {(void **)&p->dinvL, sizeof(double) * NN},
+      {(void **)&p->red, sizeof(double) * FO_MAX_RED * 4096},
+      {(void **)&p->bar, 64},                        {(void **)&p->dev_status, sizeof(int) * DS_COUNT},
+  };
+  if (p->f || p->desc.kind != FO_ELASTIC) list.push_back({(void **)&p->f, sizeof(double) * NN});
+  size_t s = 0;
+  for (auto &e : list) s += e.second;
+  return s;
+}
+
+extern "C" fo_status fo_problem_destroy(fo_problem *p) {
+  if (!p) return FO_EINVAL;
+  fo_ctx *ctx = p->ctx;
+  cudaStreamSynchronize(ctx->stream);
+  std::vector<std::pair<void **, size_t>> list;
+  prob_bytes_fields(p, list);
+  for (auto &e : list) {
+    fo_free(ctx, *e.first, e.second);
+    *e.first = nullptr;
+  }
+  fo_free(ctx, p->scratch.buf, p->scratch.bytes);
+  ctx->problems.erase(std::remove(ctx->problems.begin(), ctx->problems.end(), p), ctx->problems.end());
+  delete p;
+  return FO_OK;
+}
+
+extern "C" fo_status fo_problem_create(fo_mesh *m, const fo_model_desc *desc, fo_problem **out) {
+  if (!m || !desc || !out) return FO_EINVAL;
+  fo_ctx *ctx = m->ctx;
+  *out = nullptr;
+  if (desc->kind < FO_HEAT || desc->kind > FO_HELMHOLTZ) return fo_fail(ctx, FO_EINVAL, "bad model kind");
+  if (desc->n_point_loads < 0 || desc->n_point_loads > 4 || desc->n_tractions < 0 || desc->n_tractions > 4 ||
+      desc->n_omega0 < 0 || desc->n_omega0 > 4)
+    return fo_fail(ctx, FO_EINVAL, "too many loads / subdomain boxes");
+  const Grid &g = m->g;
+  for (int i = 0; i < desc->n_point_loads; ++i)
+    if (desc->point_node[i] < 0 || desc->point_node[i] >= g.num_nodes)
+      return fo_fail(ctx, FO_EINVAL, "point load node out of range");
+  for (int i = 0; i < desc->n_tractions; ++i)
+    if (desc->traction_face[i] < 0 || desc->traction_face[i] >= 2 * g.dim)
+      return fo_fail(ctx, FO_EINVAL, "bad traction face");
+  if (desc->kind == FO_ELASTIC && !(desc->nu > -1.0 && desc->nu < 0.5 && desc->E > 0))
+    return fo_fail(ctx, FO_EINVAL, "bad elastic parameters");
+  fo_problem *p = new fo_problem();
+  p->ctx = ctx;
+  p->mesh = m;
+  p->desc = *desc;
+  p->desc.f_nodal = nullptr;
+  p->ncomp = desc->kind == FO_ELASTIC ? g.dim : 1;
+  p->ndof = g.num_nodes * p->ncomp;
+  if (desc->kind == FO_ELASTIC) {
+    p->lame_lambda = desc->E * desc->nu / ((1.0 + desc->nu) * (1.0 - 2.0 * desc->nu));
+    p->lame_mu = desc->E / (2.0 * (1.0 + desc->nu));
+  }
+  if (desc->kind == FO_HELMHOLTZ && !(desc->k > 0)) p->desc.k = 1.0;
+  if (desc->kind == FO_HEAT) p->desc.k = 1.0;
+  std::vector<std::pair<void **, size_t>> list;
+  prob_bytes_fields(p, list);
+  fo_status st = FO_OK;
+  for (auto &e : list) {
+    st = fo_alloc(ctx, e.first, e.second);
+    if (st != FO_OK) break;
+  }
+  ctx->problems.push_back(p);
+  if (st == FO_OK && p->f) {
+    if (desc->f_nodal)
+      st = fo_cuda_check(ctx, cudaMemcpyAsync(p->f, desc->f_nodal, sizeof(double) * g.num_nodes,
+                                              cudaMemcpyHostToDevice, ctx->stream), "copy f");
+    else
+      st = fo_cuda_check(ctx, cudaMemsetAsync(p->f, 0, sizeof(double) * g.num_nodes, ctx->stream), "zero f");
+  }
+  if (st == FO_OK) st = fo_cuda_check(ctx, cudaMemsetAsync(p->phi, 0, sizeof(double) * g.num_nodes, ctx->stream), "phi");
+  if (st == FO_OK) st = fo_cuda_check(ctx, cudaMemsetAsync(p->u, 0, sizeof(double) * p->ndof, ctx->stream), "u");
+  if (st == FO_OK) st = fo_cuda_check(ctx, cudaMemsetAsync(p->theta, 0, sizeof(double) * g.dim * g.num_nodes, ctx->stream), "theta");
+  if (st == FO_OK) st = fo_launch_masks(p);
+  if (st == FO_OK) st = fo_launch_loads(p);
+  if (st == FO_OK) st = fo_launch_velocity_diag(p);
+  if (st == FO_OK) st = fo_cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "problem setup");
+  if (st != FO_OK) {
+    fo_problem_destroy(p);
+    return st;
+  }
+  *out = p;
+  return FO_OK;
+}
+
+static fo_status copy_in(fo_problem *p, double *dst, const double *src, size_t n, int on_device) {
+  fo_ctx *ctx = p->ctx;
+  if (!src) return fo_fail(ctx, FO_EINVAL, "null input");
+  FO_CU(ctx, cudaMemcpyAsync(dst, src, sizeof(double) * n,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  if (!on_device) FO_CU(ctx, cudaStreamSynchronize(ctx->stream));   // host buffer may be reused
+  return FO_OK;
+}
+
+extern "C" fo_status fo_set_levelset(fo_problem *p, const double *phi, int on_device) {
+  if (!p) return FO_EINVAL;
+  FO_TRY(copy_in(p, p->phi, phi, p->mesh->g.num_nodes, on_device));
+  p->coef_valid = false;
+  return FO_OK;
+}
+
+extern "C" fo_status fo_initial_level(fo_problem *p, int count, const double *centers, const double *radii,
+                                      double factor, int ord) {
+  if (!p || count < 1 || !centers || !radii || (ord != 2 && ord != 0)) return FO_EINVAL;
+  p->coef_valid = false;
+  return fo_launch_initial_level(p, count, centers, radii, factor, ord);
+}
+
+extern "C" fo_status fo_coefficients(fo_problem *p) {
+  if (!p) return FO_EINVAL;
+  FO_TRY(fo_launch_coefficients(p));
+  FO_TRY(fo_launch_state_diag(p));
+  p->coef_valid = true;
+  return FO_OK;
+}
+
+extern "C" fo_status fo_state_solve(fo_problem *p, const fo_solve_opts *o, fo_solve_stats *st) {
+  if (!p) return FO_EINVAL;
+  fo_solve_opts def;
+  fo_solve_opts_default(&def);
+  if (!o) o = &def;
+  if (!p->coef_valid) FO_TRY(fo_coefficients(p));
+  fo_status s = fo_state_pcg(p, p->load, p->u, o, st);
+  if (s == FO_OK || s == FO_ENOCONV) p->u_valid = true;
+  return s;
+}
+
+__global__ void k_scale(const double *__restrict__ x, double *__restrict__ y, double c, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = c * x[i];
+}
+
+extern "C" fo_status fo_adjoint_solve(fo_problem *p, const fo_solve_opts *o, fo_solve_stats *st) {
+  if (!p) return FO_EINVAL;
+  fo_solve_opts def;
+  fo_solve_opts_default(&def);
+  if (!o) o = &def;
+  if (!p->coef_valid) FO_TRY(fo_coefficients(p));
+  double c = p->desc.kind == FO_ELASTIC ? -2.0 : -1.0;
+  double *b = p->rhs;   // reuse the RHS buffer as the adjoint load (d*N_n >= N_dof)
+  k_scale<<<fo_blocks_for(p->ndof), FO_BLOCK, 0, p->ctx->stream>>>(p->load, b, c, p->ndof);
+  fo_note_launch(1);
+  FO_CU(p->ctx, cudaGetLastError());
+  fo_solve_opts oo = *o;
+  oo.warm_start = 0;
+  fo_status s = fo_state_pcg(p, b, p->p, &oo, st);
+  p->rhs_valid = false;
+  return s;
+}
+
+extern "C" fo_status fo_functionals(fo_problem *p, double *J, double *C) {
+  if (!p) return FO_EINVAL;
+  if (!p->coef_valid) FO_TRY(fo_coefficients(p));
+  double j = 0, vol = 0;
+  FO_TRY(fo_launch_functionals(p, &j, &vol));
+  if (J) *J = j;
+  if (C) *C = p->desc.volume_target > 0 ? vol / p->desc.volume_target : vol;
+  if (!std::isfinite(j) || !std::isfinite(vol)) return fo_fail(p->ctx, FO_ENAN, "non-finite functional");
+  return FO_OK;
+}
+
+extern "C" fo_status fo_shape_derivative(fo_problem *p, double lambda, double *rhs_out) {
+  if (!p) return FO_EINVAL;
+  if (!p->coef_valid) FO_TRY(fo_coefficients(p));
+  FO_TRY(fo_launch_shape_rhs(p, lambda));
+  p->rhs_valid = true;
+  p->last_lambda = lambda;
+  if (rhs_out) {
+    const Grid &g = p->mesh->g;
+    FO_CU(p->ctx, cudaMemcpyAsync(rhs_out, p->rhs, sizeof(double) * g.dim * g.num_nodes, cudaMemcpyDeviceToHost,
+                                  p->ctx->stream));
+    FO_CU(p->ctx, cudaStreamSynchronize(p->ctx->stream));
+  }
+  return FO_OK;
+}
+
+extern "C" fo_status fo_descent(fo_problem *p, const fo_solve_opts *o, double *Btt, fo_solve_stats *st) {
+  if (!p) return FO_EINVAL;
+  if (!p->rhs_valid) return fo_fail(p->ctx, FO_ESTATE, "fo_descent needs fo_shape_derivative first");
+  fo_solve_opts def;
+  fo_solve_opts_default(&def);
+  if (!o) o = &def;
+  double btt = 0;
+  fo_status s = fo_velocity_pcg(p, o, &btt, st);
+  if (Btt) *Btt = btt;
+  if (s == FO_OK || s == FO_ENOCONV) p->theta_valid = true;
+  p->transport_valid = false;
+  return s;
+}
+
+extern "C" fo_status fo_transport_assemble(fo_problem *p, double dt, double h, int smooth) {
+  if (!p || !(dt > 0) || !(h > 0)) return FO_EINVAL;
+  FO_TRY(fo_launch_transport_assemble(p, dt, h, smooth));
+  p->transport_valid = true;
+  p->transport_dt = dt;
+  p->transport_h = h;
+  p->transport_smooth = smooth;
+  return FO_OK;
+}
+
+extern "C" fo_status fo_levelset_step(fo_problem *p, double t_end, int nsteps, double h, int smooth,
+                                      const fo_solve_opts *o, fo_solve_stats *st) {
+  if (!p || nsteps < 1 || !(t_end > 0) || !(h > 0)) return FO_EINVAL;
+  fo_solve_opts def;
+  fo_solve_opts_default(&def);
+  if (!o) o = &def;
+  double dt = t_end / nsteps;
+  if (!(p->transport_valid && p->transport_dt == dt && p->transport_h == h && p->transport_smooth == smooth))
+    FO_TRY(fo_transport_assemble(p, dt, h, smooth));
+  fo_status s = fo_transport_run(p, nsteps, o, st);
+  p->coef_valid = false;
+  return s;
+}
+
+extern "C" fo_status fo_reinit(fo_problem *p, int nsteps, double t_final, double h, const fo_solve_opts *o,
+                               fo_solve_stats *st) {
+  if (!p || nsteps < 1 || !(t_final > 0) || !(h > 0)) return FO_EINVAL;
+  fo_solve_opts def;
+  fo_solve_opts_default(&def);
+  if (!o) o = &def;
+  fo_status s = fo_reinit_run(p, nsteps, t_final / nsteps, h, o, st);
+  p->coef_valid = false;
+  return s;
+}
+
+static double *field_ptr(fo_problem *p, int field, size_t *n, bool *is_u8) {
+  const Grid &g = p->mesh->g;
+  *is_u8 = false;
+  switch (field) {
+    case FO_FIELD_PHI: *n = g.num_nodes; return p->phi;
+    case FO_FIELD_U: *n = p->ndof; return p->u;
+    case FO_FIELD_P: *n = p->ndof; return p->p;
+    case FO_FIELD_THETA: *n = g.dim * g.num_nodes; return p->theta;
+    case FO_FIELD_RHS: *n = g.dim * g.num_nodes; return p->rhs;
+    case FO_FIELD_COEF: *n = g.num_elems; return p->coef;
+    case FO_FIELD_CHI: *n = g.num_elems; *is_u8 = true; return (double *)p->chi;
+    case FO_FIELD_LOAD: *n = p->ndof; return p->load;
+    case FO_FIELD_OMEGA0: *n = g.num_elems; *is_u8 = true; return (double *)p->omega0;
+    default: return nullptr;
+  }
+}
+
+extern "C" fo_status fo_get(fo_problem *p, int field, double *out) {
+  if (!p || !out) return FO_EINVAL;
+  size_t n;
+  bool u8;
+  double *src = field_ptr(p, field, &n, &u8);
+  if (!src) return fo_fail(p->ctx, FO_EINVAL, "unknown field %d", field);
+  fo_ctx *ctx = p->ctx;
+  if (field == FO_FIELD_COEF && p->desc.kind == FO_HELMHOLTZ) {
+    // stored as A_e * k; report A_e
+  }
+  if (u8) {
+    std::vector<uint8_t> tmp(n);
+    FO_CU(ctx, cudaMemcpyAsync(tmp.data(), src, n, cudaMemcpyDeviceToHost, ctx->stream));
+    FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i < n; ++i) out[i] = tmp[i];
+    return FO_OK;
+  }
+  FO_CU(ctx, cudaMemcpyAsync(out, src, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  if (field == FO_FIELD_COEF && p->desc.kind == FO_HELMHOLTZ)
+    for (size_t i = 0; i < n; ++i) out[i] /= p->desc.k;
+  return FO_OK;
+}
+
+extern "C" fo_status fo_set(fo_problem *p, int field, const double *v, int on_device) {
+  if (!p || !v) return FO_EINVAL;
+  size_t n;
+  bool u8;
+  double *dst = field_ptr(p, field, &n, &u8);
+  if (!dst || u8 || field == FO_FIELD_COEF || field == FO_FIELD_LOAD)
+    return fo_fail(p->ctx, FO_EINVAL, "field %d cannot be set", field);
+  FO_TRY(copy_in(p, dst, v, n, on_device));
+  if (field == FO_FIELD_PHI) p->coef_valid = false;
+  if (field == FO_FIELD_U) p->u_valid = true;
+  if (field == FO_FIELD_RHS) p->rhs_valid = true;
+  if (field == FO_FIELD_THETA) {
+    p->theta_valid = true;
+    p->transport_valid = false;
+  }
+  return FO_OK;
+}
+
+extern "C" fo_status fo_apply(fo_problem *p, int op, const double *x, double *y, int on_device) {
+  if (!p || !x || !y) return FO_EINVAL;
+  fo_ctx *ctx = p->ctx;
+  const Grid &g = p->mesh->g;
+  size_t n;
+  switch (op) {
+    case FO_OP_STATE: case FO_OP_STATE_FP32: n = p->ndof; break;
+    case FO_OP_VELOCITY: n = g.dim * g.num_nodes; break;
+    case FO_OP_TRANSPORT_L: case FO_OP_TRANSPORT_R:
+      if (!p->transport_valid) return fo_fail(ctx, FO_ESTATE, "transport matrices not assembled");
+      n = g.num_nodes;
+      break;
+    default: return fo_fail(ctx, FO_EINVAL, "unknown operator %d", op);
+  }
+  if ((op == FO_OP_STATE || op == FO_OP_STATE_FP32) && !p->coef_valid) FO_TRY(fo_coefficients(p));
+  double *dx, *dy;
+  FO_TRY(fo_alloc(ctx, (void **)&dx, sizeof(double) * n));
+  fo_status st = fo_alloc(ctx, (void **)&dy, sizeof(double) * n);
+  if (st != FO_OK) {
+    fo_free(ctx, dx, sizeof(double) * n);
+    return st;
+  }
+  cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  st = fo_cuda_check(ctx, cudaMemcpyAsync(dx, x, sizeof(double) * n, kin, ctx->stream), "apply in");
+  if (st == FO_OK) {
+    if (op == FO_OP_STATE) st = fo_launch_state_apply(p, dx, dy, true);
+    else if (op == FO_OP_STATE_FP32) st = fo_launch_state_apply32(p, dx, dy);
+    else if (op == FO_OP_VELOCITY) st = fo_launch_velocity_apply(p, dx, dy);
+    else st = fo_launch_stencil_apply(p, op == FO_OP_TRANSPORT_L ? p->L : p->R, dx, dy);
+  }
+  if (st == FO_OK) st = fo_cuda_check(ctx, cudaMemcpyAsync(y, dy, sizeof(double) * n, kout, ctx->stream), "apply out");
+  if (st == FO_OK) st = fo_cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "apply sync");
+  fo_free(ctx, dx, sizeof(double) * n);
+  fo_free(ctx, dy, sizeof(double) * n);
+  return st;
+}
+
+// ------------------------------------------------------------------------- host helpers
+extern "C" void fo_ppl_init(fo_ppl *s, int nc) {
+  if (!s) return;
+  memset(s, 0, sizeof *s);
+  s->nc = nc < 0 ? 0 : (nc > 4 ? 4 : nc);
+  s->r = 0.999;
+  s->delta = 0.5;
+  s->alpha = 2000.0;
+  s->beta = 0.5;
+}
+
+extern "C" void fo_ppl_update(fo_ppl *s, const double *C, double J, double *lambda_out, double *L_out) {
+  if (!s) return;
+  const int nc = s->nc;
+  double dd = 0;
+  for (int i = 0; i < nc; ++i) dd += (s->lambda[i] - s->mu[i]) * (s->lambda[i] - s->mu[i]);
+  for (int i = 0; i < nc; ++i) s->mu[i] = s->mu[i] + s->delta * (s->lambda[i] - s->mu[i]) / (dd + 1.0);
+  for (int i = 0; i < nc; ++i) {
+    s->lambda[i] = s->mu[i] + s->alpha / (1.0 + s->alpha * s->beta) * (C[i] - 1.0);
+    s->z[i] = (s->lambda[i] - s->mu[i]) / s->alpha;
+  }
+  s->delta = s->r * s->delta;
+  double L = J, zz = 0, lm = 0;
+  for (int i = 0; i < nc; ++i) {
+    L += s->lambda[i] * (C[i] - 1.0) + s->mu[i] * s->z[i];
+    zz += s->z[i] * s->z[i];
+    lm += (s->lambda[i] - s->mu[i]) * (s->lambda[i] - s->mu[i]);
+  }
+  L += 0.5 * s->alpha * zz + 0.5 * s->beta * lm;
+  if (lambda_out)
+    for (int i = 0; i < nc; ++i) lambda_out[i] = s->lambda[i];
+  if (L_out) *L_out = L;
+}
+
+extern "C" void fo_adaptime(double Btt, const fo_run_options *o, double *t_end, int *nsteps) {
+  fo_run_options def;
+  fo_run_options_default(&def);
+  if (!o) o = &def;
+  double t = o->dfactor / std::max(Btt, 1e-12);
+  t = std::min(std::max(t, o->t_min), o->t_max);
+  double s = (o->s_max - o->s_min) * std::pow((t - o->t_min) / (o->t_max - o->t_min), 1.0 / 6.0) + o->s_min;
+  s = std::min(std::max(s, (double)o->s_min), (double)o->s_max);
+  if (t_end) *t_end = t;
+  if (nsteps) *nsteps = (int)std::floor(s + 0.5);
+}
+
+extern "C" void fo_solve_opts_default(fo_solve_opts *o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->precision = FO_FP64;
+  o->rtol = 1e-12;
+  o->maxit = 200000;
+  o->warm_start = 0;
+  o->inner_rtol = 1e-3;
+  o->inner_maxit = 20000;
+  o->grid_blocks = 0;
+}
+
+extern "C" void fo_run_options_default(fo_run_options *o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->dfactor = 1e-2;
+  o->t_min = 1e-3;
+  o->t_max = 1e-1;
+  o->s_min = 8;
+  o->s_max = 16;
+  o->smooth = 0;
+  o->reinit_step = 0;
+  o->reinit_steps = 8;
+  o->reinit_time = 1e-1;
+  o->h = 0;
+  fo_solve_opts_default(&o->state);
+  fo_solve_opts_default(&o->velocity);
+  fo_solve_opts_default(&o->transport);
+  o->state.warm_start = 1;
+}
+
+// ----------------------------------------------------------------- one Algorithm-1 step
+extern "C" fo_status fo_opt_step(fo_problem *p, int iter, const fo_run_options *o, fo_ppl *ppl, fo_iter_log *log) {
+  if (!p || !o) return FO_EINVAL;
+  fo_iter_log lg;
+  memset(&lg, 0, sizeof lg);
+  fo_ctx *ctx = p->ctx;
+  const bool tm = ctx->timing != 0;
+  auto mark = [&](int i) -> fo_status {
+    if (tm) FO_CU(ctx, cudaEventRecord(ctx->ev[i], ctx->stream));
+    return FO_OK;
+  };
+  const double h = o->h > 0 ? o->h : p->mesh->h_diam;
+  FO_TRY(mark(0));
+  FO_TRY(fo_coefficients(p));
+  fo_status s = fo_state_solve(p, &o->state, &lg.state);
+  if (s != FO_OK) return s;
+  FO_TRY(mark(1));
+  double J = 0, C = 0;
+  FO_TRY(fo_functionals(p, &J, &C));
+  FO_TRY(mark(2));
+  lg.J = J;
+  lg.L = J;
+  double lam = 0;
+  if (p->desc.volume_target > 0) {
+    lg.C = C;
+    if (ppl) {
+      double lv[4] = {0, 0, 0, 0};
+      double Cv[4] = {C, 0, 0, 0};
+      fo_ppl_update(ppl, Cv, J, lv, &lg.L);
+      lam = lv[0];
+    }
+  }
+  lg.lambda = lam;
+  FO_TRY(mark(3));
+  FO_TRY(fo_shape_derivative(p, lam, nullptr));
+  FO_TRY(mark(4));
+  double Btt = 0;
+  s = fo_descent(p, &o->velocity, &Btt, &lg.velocity);
+  if (s != FO_OK) return s;
+  FO_TRY(mark(5));
+  lg.Btt = Btt;
+  double t_end;
+  int ns;
+  fo_adaptime(Btt, o, &t_end, &ns);
+  lg.t_end = t_end;
+  lg.nsteps = ns;
+  s = fo_levelset_step(p, t_end, ns, h, o->smooth, &o->transport, &lg.transport);
+  if (s != FO_OK) return s;
+  FO_TRY(mark(6));
+  if (o->reinit_step > 0 && iter > 0 && iter % o->reinit_step == 0) {
+    s = fo_reinit(p, o->reinit_steps, o->reinit_time, h, &o->transport, &lg.reinit_stats);
+    if (s != FO_OK) return s;
+    lg.reinit = 1;
+  }
+  FO_TRY(mark(7));
+  if (tm) {
+    FO_CU(ctx, cudaEventSynchronize(ctx->ev[7]));
+    float ms[7];
+    for (int i = 0; i < 7; ++i) FO_CU(ctx, cudaEventElapsedTime(&ms[i], ctx->ev[i], ctx->ev[i + 1]));
+    lg.ms_state = ms[0];
+    lg.ms_functionals = ms[1] + ms[2];   // functionals + host PPL update
+    lg.ms_shape = ms[3];
+    lg.ms_velocity = ms[4];
+    lg.ms_transport = ms[5];
+    lg.ms_reinit = ms[6];
+  }
+  if (log) *log = lg;
+  return FO_OK;
+}

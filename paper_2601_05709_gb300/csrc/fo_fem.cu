@@ -1,0 +1,716 @@
+// Element-level kernels: mesh build, masks, loads, ersatz coefficient, operator applies and
+// diagonals, functionals, the shape-derivative right-hand side and the initial level set.
+#include <cmath>
+#include <vector>
+
+#include "fo_internal.cuh"
+#include "fo_ops.cuh"
+
+// -------------------------------------------------------------------------- mesh build
+// Coordinates lo + (hi - lo) * i / n in that operation order; connectivity of simplex
+// P*c + p along the Kuhn path of permutation p.
+template <int D>
+__global__ void k_mesh_build(Grid g, int32_t *cells, double *coords) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long a = tid; a < g.num_nodes; a += stride) {
+    int idx[3];
+    node_ijk(g, a, idx);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      double t = (g.hi[k] - g.lo[k]) * (double)idx[k];
+      t = t / (double)g.n[k];
+      coords[a * D + k] = g.lo[k] + t;
+    }
+  }
+  for (long long e = tid; e < g.num_elems; e += stride) {
+    const long long c = e / KP<D>::P;
+    const int p = (int)(e % KP<D>::P);
+    int ci[3];
+    ci[0] = (int)(c % g.n[0]);
+    long long t = c / g.n[0];
+    ci[1] = (int)(t % g.n[1]);
+    ci[2] = (int)(t / g.n[1]);
+    long long v = ci[0] + g.stride[1] * ci[1] + (D == 3 ? g.stride[2] * ci[2] : 0);
+    cells[e * (D + 1)] = (int32_t)v;
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      v += g.stride[kperm<D>(p, l)];
+      cells[e * (D + 1) + l + 1] = (int32_t)v;
+    }
+  }
+}
+
+fo_status fo_launch_mesh_build(fo_mesh *m) {
+  const Grid &g = m->g;
+  long long n = g.num_nodes > g.num_elems ? g.num_nodes : g.num_elems;
+  int blocks = fo_blocks_for(n, FO_BLOCK, 65536);
+  if (g.dim == 2) k_mesh_build<2><<<blocks, FO_BLOCK, 0, m->ctx->stream>>>(g, m->d_cells, m->d_coords);
+  else k_mesh_build<3><<<blocks, FO_BLOCK, 0, m->ctx->stream>>>(g, m->d_cells, m->d_coords);
+  fo_note_launch(1);
+  FO_CU(m->ctx, cudaGetLastError());
+  return FO_OK;
+}
+
+// -------------------------------------------------------------------------------- masks
+struct MaskArgs {
+  Grid g;
+  uint32_t faces;     // Dirichlet faces of the state
+  int ncomp;
+  int vel_dirichlet;
+  int n_omega0;
+  double o_lo[4][3], o_hi[4][3];
+};
+
+template <int D>
+__global__ void k_masks(MaskArgs m, const double *coords, uint8_t *dir, uint8_t *vdir, uint8_t *omega0) {
+  const Grid &g = m.g;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long a = tid; a < g.num_nodes; a += stride) {
+    int idx[3];
+    node_ijk(g, a, idx);
+    bool on = false, bd = false;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      if (idx[k] == 0) { bd = true; on |= (m.faces >> (2 * k)) & 1u; }
+      if (idx[k] == g.n[k]) { bd = true; on |= (m.faces >> (2 * k + 1)) & 1u; }
+    }
+    for (int c = 0; c < m.ncomp; ++c) dir[a * m.ncomp + c] = on ? 1 : 0;
+    vdir[a] = (m.vel_dirichlet && bd) ? 1 : 0;
+  }
+  // Omega_0: centroid ((x_0 + x_1) + x_2 (+ x_3)) / (D+1) strictly inside one of the boxes
+  for (long long e = tid; e < g.num_elems; e += stride) {
+    const long long c = e / KP<D>::P;
+    const int p = (int)(e % KP<D>::P);
+    int ci[3];
+    ci[0] = (int)(c % g.n[0]);
+    long long t = c / g.n[0];
+    ci[1] = (int)(t % g.n[1]);
+    ci[2] = (int)(t / g.n[1]);
+    long long v = ci[0] + g.stride[1] * ci[1] + (D == 3 ? g.stride[2] * ci[2] : 0);
+    double s[3];
+#pragma unroll
+    for (int k = 0; k < D; ++k) s[k] = coords[v * D + k];
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      v += g.stride[kperm<D>(p, l)];
+#pragma unroll
+      for (int k = 0; k < D; ++k) s[k] = s[k] + coords[v * D + k];
+    }
+    bool in = false;
+    for (int b = 0; b < m.n_omega0; ++b) {
+      bool ok = true;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double x = s[k] / (double)(D + 1);
+        ok = ok && (x > m.o_lo[b][k]) && (x < m.o_hi[b][k]);
+      }
+      in = in || ok;
+    }
+    omega0[e] = in ? 1 : 0;
+  }
+}
+
+fo_status fo_launch_masks(fo_problem *p) {
+  const Grid &g = p->mesh->g;
+  MaskArgs m{};
+  m.g = g;
+  m.faces = p->desc.dirichlet_faces;
+  m.ncomp = p->ncomp;
+  m.vel_dirichlet = p->desc.velocity_dirichlet;
+  m.n_omega0 = p->desc.omega0_weight != 0.0 ? p->desc.n_omega0 : 0;
+  for (int b = 0; b < 4; ++b)
+    for (int k = 0; k < 3; ++k) {
+      m.o_lo[b][k] = p->desc.omega0_lo[b][k];
+      m.o_hi[b][k] = p->desc.omega0_hi[b][k];
+    }
+  long long n = g.num_nodes > g.num_elems ? g.num_nodes : g.num_elems;
+  int blocks = fo_blocks_for(n, FO_BLOCK, 65536);
+  if (g.dim == 2) k_masks<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, p->mesh->d_coords, p->dir, p->vdir, p->omega0);
+  else k_masks<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, p->mesh->d_coords, p->dir, p->vdir, p->omega0);
+  fo_note_launch(1);
+  FO_CU(p->ctx, cudaGetLastError());
+  return FO_OK;
+}
+
+// -------------------------------------------------------------------------------- loads
+struct LoadArgs {
+  Grid g;
+  int ncomp;
+  int n_tr;
+  int tr_face[4];
+  double tr_vec[4][3];
+  double mref;   // |e| / ((D+1)(D+2))
+};
+
+// F = M f (P1 body source) + constant tractions (|f| / D per facet vertex); point loads are
+// added on the host side of the launch; Dirichlet DOFs are zeroed.
+template <int D>
+__global__ void k_loads(LoadArgs L, const double *f, const uint8_t *dir, double *F) {
+  const Grid &g = L.g;
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < g.num_nodes;
+       a += (long long)gridDim.x * blockDim.x) {
+    int idx[3];
+    node_ijk(g, a, idx);
+    double acc[3] = {0, 0, 0};
+    if (f) {
+      double fs[ST<D>::S][1];
+      load_stencil<D, 1, double>(g, idx, a, VecX<double>{f}, fs);
+      double s = 0;
+#pragma unroll
+      for (int p = 0; p < KP<D>::P; ++p)
+#pragma unroll
+        for (int m = 0; m <= D; ++m) {
+          long long e;
+          if (!elem_of<D>(g, idx, p, m, e)) continue;
+          double sum = fs[0][0];
+#pragma unroll
+          for (int l = 0; l <= D; ++l) sum += fs[rel_slot<D>(p, m, l)][0];
+          s += L.mref * sum;
+        }
+      acc[0] = s;
+    }
+    for (int t = 0; t < L.n_tr; ++t) {
+      const int axis = L.tr_face[t] >> 1, side = L.tr_face[t] & 1;
+      if (idx[axis] != (side ? g.n[axis] : 0)) continue;
+      int cnt = 0;
+      if (D == 2) {
+        const int o = 1 - axis;
+        cnt = (idx[o] + 1 <= g.n[o]) + (idx[o] - 1 >= 0);
+      } else {
+        const int o1 = axis == 0 ? 1 : 0, o2 = axis == 2 ? 1 : 2;
+        for (int q = 0; q < 2; ++q)
+          for (int m = 0; m <= 2; ++m) {
+            const int ax[2] = {q == 0 ? o1 : o2, q == 0 ? o2 : o1};
+            int c[3] = {idx[0], idx[1], idx[2]};
+            for (int l = 0; l < m; ++l) c[ax[l]] -= 1;
+            if (c[o1] < 0 || c[o1] >= g.n[o1] || c[o2] < 0 || c[o2] >= g.n[o2]) continue;
+            ++cnt;
+          }
+      }
+      const double w = g.facet_area[axis] / D * cnt;
+      for (int c = 0; c < L.ncomp; ++c) acc[c] += w * L.tr_vec[t][c];
+    }
+    for (int c = 0; c < L.ncomp; ++c) F[a * L.ncomp + c] = dir[a * L.ncomp + c] ? 0.0 : acc[c];
+  }
+}
+
+__global__ void k_point_loads(int n, const long long *node, const double *vec, int ncomp, const uint8_t *dir,
+                              double *F) {
+  // single thread: point loads applied in order (deterministic)
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int i = 0; i < n; ++i)
+    for (int c = 0; c < ncomp; ++c) {
+      long long k = node[i] * ncomp + c;
+      if (!dir[k]) F[k] += vec[i * 3 + c];
+    }
+}
+
+fo_status fo_launch_loads(fo_problem *p) {
+  const Grid &g = p->mesh->g;
+  fo_ctx *ctx = p->ctx;
+  LoadArgs L{};
+  L.g = g;
+  L.ncomp = p->ncomp;
+  L.n_tr = p->desc.n_tractions;
+  for (int t = 0; t < 4; ++t) {
+    L.tr_face[t] = p->desc.traction_face[t];
+    for (int k = 0; k < 3; ++k) L.tr_vec[t][k] = p->desc.traction_vec[t][k];
+  }
+  L.mref = g.vol_e / ((g.dim + 1) * (g.dim + 2));
+  const double *f = (p->desc.kind != FO_ELASTIC) ? p->f : nullptr;
+  int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
+  if (g.dim == 2) k_loads<2><<<blocks, FO_BLOCK, 0, ctx->stream>>>(L, f, p->dir, p->load);
+  else k_loads<3><<<blocks, FO_BLOCK, 0, ctx->stream>>>(L, f, p->dir, p->load);
+  fo_note_launch(1);
+  FO_CU(ctx, cudaGetLastError());
+  if (p->desc.n_point_loads > 0) {
+    // stage the point loads through the reduction buffer (fits: <= 4 * (1 + 3) doubles)
+    long long nodes[4];
+    double vec[12];
+    for (int i = 0; i < 4; ++i) {
+      nodes[i] = p->desc.point_node[i];
+      for (int c = 0; c < 3; ++c) vec[i * 3 + c] = p->desc.point_vec[i][c];
+    }
+    char *stage = (char *)p->red;
+    FO_CU(ctx, cudaMemcpyAsync(stage, nodes, sizeof nodes, cudaMemcpyHostToDevice, ctx->stream));
+    FO_CU(ctx, cudaMemcpyAsync(stage + 64, vec, sizeof vec, cudaMemcpyHostToDevice, ctx->stream));
+    k_point_loads<<<1, 1, 0, ctx->stream>>>(p->desc.n_point_loads, (const long long *)stage,
+                                            (const double *)(stage + 64), p->ncomp, p->dir, p->load);
+    fo_note_launch(1);
+    FO_CU(ctx, cudaGetLastError());
+    FO_CU(ctx, cudaStreamSynchronize(ctx->stream));   // host staging arrays go out of scope
+  }
+  return FO_OK;
+}
+
+// -------------------------------------------------------------------------- coefficient
+// chi_e = [(phi_0 + phi_1) + phi_2 (+ phi_3) < 0], A_e = chi ? a_in : a_out (times k).
+template <int D>
+__global__ void k_coefficients(Grid g, const double *phi, double a_in, double a_out, double *coef, float *coef32,
+                               uint8_t *chi) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.num_elems;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / KP<D>::P;
+    const int p = (int)(e % KP<D>::P);
+    int ci[3];
+    ci[0] = (int)(c % g.n[0]);
+    long long t = c / g.n[0];
+    ci[1] = (int)(t % g.n[1]);
+    ci[2] = (int)(t / g.n[1]);
+    long long v = ci[0] + g.stride[1] * ci[1] + (D == 3 ? g.stride[2] * ci[2] : 0);
+    double s = phi[v];
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      v += g.stride[kperm<D>(p, l)];
+      s = s + phi[v];
+    }
+    const bool in = s < 0.0;
+    const double A = in ? a_in : a_out;
+    coef[e] = A;
+    coef32[e] = (float)A;
+    chi[e] = in ? 1 : 0;
+  }
+}
+
+fo_status fo_launch_coefficients(fo_problem *p) {
+  const Grid &g = p->mesh->g;
+  const double k = p->desc.kind == FO_HELMHOLTZ ? p->desc.k : 1.0;
+  int blocks = fo_blocks_for(g.num_elems, FO_BLOCK, 65536);
+  if (g.dim == 2)
+    k_coefficients<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(g, p->phi, p->desc.a_in * k, p->desc.a_out * k,
+                                                                p->coef, p->coef32, p->chi);
+  else
+    k_coefficients<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(g, p->phi, p->desc.a_in * k, p->desc.a_out * k,
+                                                                p->coef, p->coef32, p->chi);
+  fo_note_launch(1);
+  FO_CU(p->ctx, cudaGetLastError());
+  return FO_OK;
+}
+
+// generic node-parallel apply / diag
+template <int D, class Op, class X, typename T>
+__global__ void k_apply(Op op, X x, T *y) {
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < op.g.num_nodes;
+       a += (long long)gridDim.x * blockDim.x) {
+    int idx[3];
+    node_ijk(op.g, a, idx);
+    T out[Op::NPN];
+    op.row(a, idx, x, out);
+#pragma unroll
+    for (int c = 0; c < Op::NPN; ++c) y[a * Op::NPN + c] = out[c];
+  }
+}
+
+template <int D, class Op, typename T>
+__global__ void k_diag_inv(Op op, T *dinv, float *dinv32) {
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < op.g.num_nodes;
+       a += (long long)gridDim.x * blockDim.x) {
+    int idx[3];
+    node_ijk(op.g, a, idx);
+    T out[Op::NPN];
+    op.diag(a, idx, out);
+#pragma unroll
+    for (int c = 0; c < Op::NPN; ++c) {
+      dinv[a * Op::NPN + c] = T(1) / out[c];
+      if (dinv32) dinv32[a * Op::NPN + c] = (float)(T(1) / out[c]);
+    }
+  }
+}
+
+__global__ void k_d2f(const double *x, float *y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+__global__ void k_f2d(const float *x, double *y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+
+fo_status fo_launch_state_diag(fo_problem *p) {
+  const Grid &g = p->mesh->g;
+  int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
+  cudaStream_t s = p->ctx->stream;
+  if (p->desc.kind == FO_ELASTIC) {
+    if (g.dim == 2) k_diag_inv<2><<<blocks, FO_BLOCK, 0, s>>>(make_elastic_op<2, double>(p), p->dinv_state, p->dinv_state32);
+    else k_diag_inv<3><<<blocks, FO_BLOCK, 0, s>>>(make_elastic_op<3, double>(p), p->dinv_state, p->dinv_state32);
+  } else {
+    if (g.dim == 2) k_diag_inv<2><<<blocks, FO_BLOCK, 0, s>>>(make_scalar_op<2, double>(p), p->dinv_state, p->dinv_state32);
+    else k_diag_inv<3><<<blocks, FO_BLOCK, 0, s>>>(make_scalar_op<3, double>(p), p->dinv_state, p->dinv_state32);
+  }
+  fo_note_launch(1);
+  FO_CU(p->ctx, cudaGetLastError());
+  return FO_OK;
+}
+
+fo_status fo_launch_velocity_diag(fo_problem *p) {
+  const Grid &g = p->mesh->g;
+  int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
+  if (g.dim == 2) k_diag_inv<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(make_velocity_op<2, double>(p), p->dinv_vel, (float *)nullptr);
+  else k_diag_inv<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(make_velocity_op<3, double>(p), p->dinv_vel, (float *)nullptr);
+  fo_note_launch(1);
+  FO_CU(p->ctx, cudaGetLastError());
+  return FO_OK;
+}
+
+fo_status fo_launch_state_apply(fo_problem *p, const double *x, double *y, bool mask) {
+  const Grid &g = p->mesh->g;
+  int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
+  cudaStream_t s = p->ctx->stream;
+  if (p->desc.kind == FO_ELASTIC) {
+    if (g.dim == 2) {
+      auto op = make_elastic_op<2, double>(p);
+      if (mask) k_apply<2><<<blocks, FO_BLOCK, 0, s>>>(op, MaskedX<double>{x, p->dir}, y);
+      else k_apply<2><<<blocks, FO_BLOCK, 0, s>>>(op, VecX<double>{x}, y);
+    } else {
+      auto op = make_elastic_op<3, double>(p);
+      if (mask) k_apply<3><<<blocks, FO_BLOCK, 0, s>>>(op, MaskedX<double>{x, p->dir}, y);
+      else k_apply<3><<<blocks, FO_BLOCK, 0, s>>>(op, VecX<double>{x}, y);
+    }
+  } else {
+    if (g.dim == 2) {
+      auto op = make_scalar_op<2, double>(p);
+      if (mask) k_apply<2><<<blocks, FO_BLOCK, 0, s>>>(op, MaskedX<double>{x, p->dir}, y);
+      else k_apply<2><<<blocks, FO_BLOCK, 0, s>>>(op, VecX<double>{x}, y);
+    } else {
+      auto op = make_scalar_op<3, double>(p);
+      if (mask) k_apply<3><<<blocks, FO_BLOCK, 0, s>>>(op, MaskedX<double>{x, p->dir}, y);
+      else k_apply<3><<<blocks, FO_BLOCK, 0, s>>>(op, VecX<double>{x}, y);
+    }
+  }
+  fo_note_launch(1);
+  FO_CU(p->ctx, cudaGetLastError());
+  return FO_OK;
+}
+
+// FP32 operator of the mixed path, applied to double vectors (x masked, converted in the gather)
+template <typename T>
+struct MaskedCastX {
+  const double *v;
+  const uint8_t *dir;
+  __device__ __forceinline__ T operator()(long long i) const { return dir[i] ? T(0) : (T)v[i]; }
+};
+
+template <int D, class Op>
+__global__ void k_apply32(Op op, MaskedCastX<float> x, double *y) {
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < op.g.num_nodes;
+       a += (long long)gridDim.x * blockDim.x) {
+    int idx[3];
+    node_ijk(op.g, a, idx);
+    float out[Op::NPN];
+    op.row(a, idx, x, out);
+#pragma unroll
+    for (int c = 0; c < Op::NPN; ++c) y[a * Op::NPN + c] = (double)out[c];
+  }
+}
+
+fo_status fo_launch_state_apply32(fo_problem *p, const double *x, double *y) {
+  const Grid &g = p->mesh->g;
+  int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
+  cudaStream_t s = p->ctx->stream;
+  MaskedCastX<float> mx{x, p->dir};
+  if (p->desc.kind == FO_ELASTIC) {
+    if (g.dim == 2) k_apply32<2><<<blocks, FO_BLOCK, 0, s>>>(make_elastic_op<2, float>(p), mx, y);
+    else k_apply32<3><<<blocks, FO_BLOCK, 0, s>>>(make_elastic_op<3, float>(p), mx, y);
+  } else {
+    if (g.dim == 2) k_apply32<2><<<blocks, FO_BLOCK, 0, s>>>(make_scalar_op<2, float>(p), mx, y);
+    else k_apply32<3><<<blocks, FO_BLOCK, 0, s>>>(make_scalar_op<3, float>(p), mx, y);
+  }
+  fo_note_launch(1);
+  FO_CU(p->ctx, cudaGetLastError());
+  return FO_OK;
+}
+
+fo_status fo_launch_velocity_apply(fo_problem *p, const double *x, double *y) {
+  const Grid &g = p->mesh->g;
+  int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
+  // H^1_0: boundary columns are dropped (rows are identity), as in the reduced system
+  if (g.dim == 2)
+    k_apply<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(make_velocity_op<2, double>(p), NodeMaskedX<double, 2>{x, p->vdir}, y);
+  else
+    k_apply<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(make_velocity_op<3, double>(p), NodeMaskedX<double, 3>{x, p->vdir}, y);
+  fo_note_launch(1);
+  FO_CU(p->ctx, cudaGetLastError());
+  return FO_OK;
+}
+
+// --------------------------------------------------------------------------- functionals
+// J and |Omega| as element sums: block partials, then one block adds them in a fixed order.
+struct FuncArgs {
+  Grid g;
+  int kind;
+  double lam, mu;
+};
+
+template <int D>
+__global__ void k_functionals(FuncArgs f, const double *coef, const uint8_t *chi, const double *u,
+                              const double *load, double *partials) {
+  __shared__ double smem[32 * 2];
+  const Grid &g = f.g;
+  double v[2] = {0.0, 0.0};
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = tid; e < g.num_elems; e += stride) {
+    const long long c = e / KP<D>::P;
+    const int p = (int)(e % KP<D>::P);
+    int ci[3];
+    ci[0] = (int)(c % g.n[0]);
+    long long t = c / g.n[0];
+    ci[1] = (int)(t % g.n[1]);
+    ci[2] = (int)(t / g.n[1]);
+    long long vtx[D + 1];
+    vtx[0] = ci[0] + g.stride[1] * ci[1] + (D == 3 ? g.stride[2] * ci[2] : 0);
+#pragma unroll
+    for (int l = 0; l < D; ++l) vtx[l + 1] = vtx[l] + g.stride[kperm<D>(p, l)];
+    const double A = coef[e];
+    if (f.kind == FO_ELASTIC) {
+      double du[D][D];
+#pragma unroll
+      for (int l = 0; l < D; ++l) {
+        const int ax = kperm<D>(p, l);
+#pragma unroll
+        for (int i = 0; i < D; ++i) du[i][ax] = (u[vtx[l + 1] * D + i] - u[vtx[l] * D + i]) * g.inv_h[ax];
+      }
+      double tr = 0;
+#pragma unroll
+      for (int i = 0; i < D; ++i) tr += du[i][i];
+      double se = 0;   // sigma : eps = lam tr^2 + 2 mu eps : eps
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          const double eij = 0.5 * (du[i][j] + du[j][i]);
+          se += 2.0 * f.mu * eij * eij;
+        }
+      se += f.lam * tr * tr;
+      v[0] += A * g.vol_e * se;
+    } else if (f.kind == FO_HEAT) {
+      double g2 = 0;
+#pragma unroll
+      for (int l = 0; l < D; ++l) {
+        const int ax = kperm<D>(p, l);
+        const double d = (u[vtx[l + 1]] - u[vtx[l]]) * g.inv_h[ax];
+        g2 += d * d;
+      }
+      v[0] += A * g.vol_e * g2;
+    }
+    v[1] += chi[e] ? g.vol_e : 0.0;
+  }
+  if (f.kind == FO_HELMHOLTZ) {   // J = F . u
+    for (long long a = tid; a < g.num_nodes; a += stride) v[0] += load[a] * u[a];
+  }
+  block_sum<2>(v, smem);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x * 2 + 0] = v[0];
+    partials[blockIdx.x * 2 + 1] = v[1];
+  }
+}
+
+__global__ void k_finish_sum(const double *partials, int nblocks, int nr, double *out) {
+  // one warp per value, fixed order
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (w >= nr) return;
+  double t = 0;
+  for (int b = lane; b < nblocks; b += 32) t += partials[(size_t)b * nr + w];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  if (lane == 0) out[w] = t;
+}
+
+fo_status fo_launch_functionals(fo_problem *p, double *J, double *vol) {
+  const Grid &g = p->mesh->g;
+  fo_ctx *ctx = p->ctx;
+  FuncArgs f{g, p->desc.kind, p->lame_lambda, p->lame_mu};
+  const int blocks = fo_blocks_for(g.num_elems, FO_BLOCK, 1024);
+  double *part = p->red, *res = p->red + 2 * 1024;
+  if (g.dim == 2) k_functionals<2><<<blocks, FO_BLOCK, 0, ctx->stream>>>(f, p->coef, p->chi, p->u, p->load, part);
+  else k_functionals<3><<<blocks, FO_BLOCK, 0, ctx->stream>>>(f, p->coef, p->chi, p->u, p->load, part);
+  k_finish_sum<<<1, 64, 0, ctx->stream>>>(part, blocks, 2, res);
+  fo_note_launch(2);
+  FO_CU(ctx, cudaGetLastError());
+  FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars, res, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  *J = ctx->h_scalars[0];
+  *vol = ctx->h_scalars[1];
+  return FO_OK;
+}
+
+// ------------------------------------------------------------------ shape derivative RHS
+// b[D a + k] = sum over the simplices (p, m) of node a of
+//   |e| (S1 grad lambda_m)_k + int_e S0_k lambda_m,   S1 = S1^J + lambda chi / V I.
+struct ShapeArgs {
+  Grid g;
+  int kind;
+  double lam_e, mu_e;       // Lame
+  double lam_ppl, inv_V;    // PPL multiplier and 1 / V
+  double mref;              // |e| / ((D+1)(D+2))
+};
+
+template <int D>
+__global__ void k_shape_rhs(ShapeArgs s, const double *coef, const uint8_t *chi, const double *u, const double *f,
+                            double *b) {
+  const Grid &g = s.g;
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < g.num_nodes;
+       a += (long long)gridDim.x * blockDim.x) {
+    int idx[3];
+    node_ijk(g, a, idx);
+    double acc[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[k] = 0;
+    if (s.kind == FO_ELASTIC) {
+      double us[ST<D>::S][D];
+      load_stencil<D, D, double>(g, idx, a, VecX<double>{u}, us);
+#pragma unroll
+      for (int p = 0; p < KP<D>::P; ++p)
+#pragma unroll
+        for (int m = 0; m <= D; ++m) {
+          long long e;
+          if (!elem_of<D>(g, idx, p, m, e)) continue;
+          double du[D][D];
+#pragma unroll
+          for (int l = 0; l < D; ++l) {
+            const int ax = kperm<D>(p, l);
+            const int s0 = rel_slot<D>(p, m, l), s1 = rel_slot<D>(p, m, l + 1);
+#pragma unroll
+            for (int i = 0; i < D; ++i) du[i][ax] = (us[s1][i] - us[s0][i]) * g.inv_h[ax];
+          }
+          double tr = 0;
+#pragma unroll
+          for (int i = 0; i < D; ++i) tr += du[i][i];
+          double sig[D][D], se = 0;
+#pragma unroll
+          for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+              sig[i][j] = (i == j ? s.lam_e * tr : 0.0) + s.mu_e * (du[i][j] + du[j][i]);
+              se += sig[i][j] * 0.5 * (du[i][j] + du[j][i]);
+            }
+          const double A = coef[e];
+          const double cv = chi[e] ? s.lam_ppl * s.inv_V : 0.0;
+          // S1[i][j] = A (2 sum_k du[k][i] sig[k][j] - se delta_ij) + cv delta_ij
+#pragma unroll
+          for (int side = 0; side < 2; ++side) {
+            if (side == 0 && m < 1) continue;
+            if (side == 1 && m >= D) continue;
+            const int j = side == 0 ? kperm<D>(p, m - 1) : kperm<D>(p, m);
+            const double sgn = side == 0 ? g.inv_h[j] : -g.inv_h[j];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+              double t = 0;
+#pragma unroll
+              for (int k = 0; k < D; ++k) t += du[k][i] * sig[k][j];
+              const double S1ij = A * (2.0 * t - (i == j ? se : 0.0)) + (i == j ? cv : 0.0);
+              acc[i] += g.vol_e * sgn * S1ij;
+            }
+          }
+        }
+    } else {   // heat: S0 = 2u grad f, S1 = (2uf - A|grad u|^2) I + 2A grad u (x) grad u
+      double us[ST<D>::S][1], fs[ST<D>::S][1];
+      load_stencil<D, 1, double>(g, idx, a, VecX<double>{u}, us);
+      load_stencil<D, 1, double>(g, idx, a, VecX<double>{f}, fs);
+#pragma unroll
+      for (int p = 0; p < KP<D>::P; ++p)
+#pragma unroll
+        for (int m = 0; m <= D; ++m) {
+          long long e;
+          if (!elem_of<D>(g, idx, p, m, e)) continue;
+          double gu[3] = {0, 0, 0}, gf[3] = {0, 0, 0};
+          double su = 0, sf = 0, suf = 0;
+#pragma unroll
+          for (int l = 0; l < D; ++l) {
+            const int ax = kperm<D>(p, l);
+            const int s0 = rel_slot<D>(p, m, l), s1 = rel_slot<D>(p, m, l + 1);
+            gu[ax] = (us[s1][0] - us[s0][0]) * g.inv_h[ax];
+            gf[ax] = (fs[s1][0] - fs[s0][0]) * g.inv_h[ax];
+          }
+#pragma unroll
+          for (int l = 0; l <= D; ++l) {
+            const int sl = rel_slot<D>(p, m, l);
+            su += us[sl][0];
+            sf += fs[sl][0];
+            suf += us[sl][0] * fs[sl][0];
+          }
+          const double A = coef[e];
+          double g2 = 0;
+#pragma unroll
+          for (int k = 0; k < D; ++k) g2 += gu[k] * gu[k];
+          const double uf = s.mref * (suf + su * sf);          // int_e u f
+          const double Mu = s.mref * (su + us[0][0]);          // int_e u lambda_m
+          const double cv = chi[e] ? s.lam_ppl * s.inv_V : 0.0;
+          // grad lambda_m components
+          double gl[3] = {0, 0, 0};
+          if (m >= 1) gl[kperm<D>(p, m - 1)] += g.inv_h[kperm<D>(p, m - 1)];
+          if (m < D) gl[kperm<D>(p, m)] -= g.inv_h[kperm<D>(p, m)];
+          double gdot = 0;
+#pragma unroll
+          for (int k = 0; k < D; ++k) gdot += gu[k] * gl[k];
+#pragma unroll
+          for (int i = 0; i < D; ++i) {
+            const double S1gl = A * (-g2 * gl[i] + 2.0 * gu[i] * gdot) + cv * gl[i];
+            acc[i] += g.vol_e * S1gl + 2.0 * uf * gl[i] + 2.0 * gf[i] * Mu;
+          }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) b[a * D + k] = acc[k];
+  }
+}
+
+fo_status fo_launch_shape_rhs(fo_problem *p, double lambda) {
+  const Grid &g = p->mesh->g;
+  if (p->desc.kind == FO_HELMHOLTZ)
+    return fo_fail(p->ctx, FO_EINVAL, "the single-instance shape derivative covers FO_HEAT and FO_ELASTIC");
+  ShapeArgs s{g, p->desc.kind, p->lame_lambda, p->lame_mu, lambda,
+              p->desc.volume_target > 0 ? 1.0 / p->desc.volume_target : 1.0, g.vol_e / ((g.dim + 1) * (g.dim + 2))};
+  int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
+  if (g.dim == 2) k_shape_rhs<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(s, p->coef, p->chi, p->u, p->f, p->rhs);
+  else k_shape_rhs<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(s, p->coef, p->chi, p->u, p->f, p->rhs);
+  fo_note_launch(1);
+  FO_CU(p->ctx, cudaGetLastError());
+  return FO_OK;
+}
+
+// --------------------------------------------------------------------------- initial level
+// phi0(x) = factor * max_k (r_k - |x - c_k|_ord)   (ord 2 or infinity)
+__global__ void k_initial_level(int dim, long long nn, const double *coords, int count, const double *cr,
+                                double factor, int ord, double *phi) {
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < nn; a += (long long)gridDim.x * blockDim.x) {
+    double best = -INFINITY;
+    for (int k = 0; k < count; ++k) {
+      double dist = 0;
+      for (int j = 0; j < dim; ++j) {
+        const double d = coords[a * dim + j] - cr[k * 4 + j];
+        if (ord == 2) dist += d * d;
+        else dist = fmax(dist, fabs(d));
+      }
+      if (ord == 2) dist = sqrt(dist);
+      best = fmax(best, cr[k * 4 + 3] - dist);
+    }
+    phi[a] = factor * best;
+  }
+}
+
+fo_status fo_launch_initial_level(fo_problem *p, int count, const double *centers, const double *radii, double factor,
+                                  int ord) {
+  const Grid &g = p->mesh->g;
+  fo_ctx *ctx = p->ctx;
+  std::vector<double> cr(4 * (size_t)count);
+  for (int k = 0; k < count; ++k) {
+    for (int j = 0; j < g.dim; ++j) cr[k * 4 + j] = centers[k * g.dim + j];
+    cr[k * 4 + 3] = radii[k];
+  }
+  double *d_cr;
+  FO_TRY(fo_alloc(ctx, (void **)&d_cr, sizeof(double) * cr.size()));
+  fo_status st = fo_cuda_check(ctx, cudaMemcpyAsync(d_cr, cr.data(), sizeof(double) * cr.size(),
+                                                    cudaMemcpyHostToDevice, ctx->stream), "copy centres");
+  if (st == FO_OK) {
+    k_initial_level<<<fo_blocks_for(g.num_nodes, FO_BLOCK, 65536), FO_BLOCK, 0, ctx->stream>>>(
+        g.dim, g.num_nodes, p->mesh->d_coords, count, d_cr, factor, ord, p->phi);
+    fo_note_launch(1);
+    st = fo_cuda_check(ctx, cudaGetLastError(), "initial level");
+  }
+  if (st == FO_OK) st = fo_cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "initial level sync");
+  fo_free(ctx, d_cr, sizeof(double) * cr.size());
+  return st;
+}

@@ -1,0 +1,325 @@
+// Internal types and device helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "formopt_gb300.h"
+
+// ----------------------------------------------------------------------------- host side
+struct fo_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0;        // 0 = unlimited
+  size_t in_use = 0;
+  int num_sms = 0;
+  std::string err;
+  std::vector<fo_mesh *> meshes;
+  std::vector<fo_problem *> problems;
+  // pinned host staging for scalar read-backs
+  double *h_scalars = nullptr;
+  // per-phase timing of fo_opt_step
+  int timing = 0;
+  cudaEvent_t ev[8] = {};
+};
+
+// Structured Kuhn grid: everything a kernel needs to enumerate nodes and elements.
+struct Grid {
+  int dim;
+  int n[3];              // cells per axis (1 for unused axes)
+  long long nn[3];       // nodes per axis
+  long long stride[3];   // node id strides
+  long long cstride[3];  // cell id strides
+  long long num_nodes, num_cells, num_elems;
+  double lo[3], hi[3];
+  double h[3];           // cell spacing (hi - lo) / n
+  double inv_h[3];
+  double vol_e;          // measure of every simplex: prod h / d!
+  double facet_area[3];  // measure of a boundary facet on a face normal to axis a
+};
+
+struct fo_mesh {
+  fo_ctx *ctx;
+  Grid g;
+  int32_t *d_cells = nullptr;   // [N_T][d+1]
+  double *d_coords = nullptr;   // [N_n][d]
+  double h_diam = 0;
+};
+
+// Krylov scratch kept per problem (sized for the largest system it solves).
+struct Scratch {
+  void *buf = nullptr;
+  size_t bytes = 0;
+};
+
+struct fo_problem {
+  fo_ctx *ctx;
+  fo_mesh *mesh;
+  fo_model_desc desc;
+  int ncomp = 1;                 // state components per node
+  long long ndof = 0;            // state DOFs
+  double lame_lambda = 0, lame_mu = 0;
+  // device fields
+  double *phi = nullptr;         // N_n
+  double *coef = nullptr;        // N_T  (A_e, times k for Helmholtz)
+  float *coef32 = nullptr;       // N_T
+  uint8_t *chi = nullptr;        // N_T
+  uint8_t *omega0 = nullptr;     // N_T
+  uint8_t *dir = nullptr;        // N_dof state Dirichlet mask
+  uint8_t *vdir = nullptr;       // N_n velocity Dirichlet mask (H^1_0)
+  double *f = nullptr;           // N_n nodal source (heat / Helmholtz) or null
+  double *load = nullptr;        // N_dof
+  double *u = nullptr;           // N_dof
+  double *p = nullptr;           // N_dof
+  double *rhs = nullptr;         // d * N_n
+  double *theta = nullptr;       // d * N_n
+  double *dinv_state = nullptr;  // N_dof
+  float *dinv_state32 = nullptr; // N_dof
+  double *dinv_vel = nullptr;    // d * N_n
+  double *L = nullptr, *R = nullptr;   // transport stencils [S][N_n]
+  double *dinvL = nullptr;       // N_n
+  double *red = nullptr;         // reduction partials
+  unsigned *bar = nullptr;       // grid barrier counter
+  int *dev_status = nullptr;     // device error word + solver outputs
+  Scratch scratch;
+  bool coef_valid = false, u_valid = false, rhs_valid = false, theta_valid = false;
+  bool transport_valid = false;
+  double transport_dt = 0, transport_h = 0;
+  int transport_smooth = 0;
+  double last_lambda = 0;
+};
+
+// status helpers
+void fo_note_launch(int n);   // count kernel launches made by the library
+fo_status fo_fail(fo_ctx *ctx, fo_status st, const char *fmt, ...);
+fo_status fo_cuda_check(fo_ctx *ctx, cudaError_t e, const char *what);
+fo_status fo_alloc(fo_ctx *ctx, void **p, size_t bytes);
+void fo_free(fo_ctx *ctx, void *p, size_t bytes);
+
+#define FO_CU(ctx, call)                                                   \
+  do {                                                                     \
+    cudaError_t _e = (call);                                               \
+    if (_e != cudaSuccess) return fo_cuda_check((ctx), _e, #call);         \
+  } while (0)
+#define FO_TRY(call)                       \
+  do {                                     \
+    fo_status _s = (call);                 \
+    if (_s != FO_OK) return _s;            \
+  } while (0)
+
+// device status words (prob->dev_status[...])
+enum { DS_ERR = 0, DS_ITERS = 1, DS_APPLIES = 2, DS_FLAG = 3, DS_COUNT = 8 };
+enum { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_NAN = 2, DEV_NOCONV = 3 };
+
+// ----------------------------------------------------------------------------- device side
+#define FO_BLOCK 256
+#define FO_MAX_RED 16          // reduction values per block
+
+// Kuhn permutation pi_l of simplex p (lexicographic order of the axis permutations).
+template <int D>
+__host__ __device__ __forceinline__ int kperm(int p, int l) {
+  if (D == 2) return (p == 0) ? l : 1 - l;
+  // 012, 021, 102, 120, 201, 210
+  switch (p) {
+    case 0: return l;
+    case 1: return l == 0 ? 0 : (l == 1 ? 2 : 1);
+    case 2: return l == 0 ? 1 : (l == 1 ? 0 : 2);
+    case 3: return l == 0 ? 1 : (l == 1 ? 2 : 0);
+    case 4: return l == 0 ? 2 : (l == 1 ? 0 : 1);
+    default: return l == 0 ? 2 : (l == 1 ? 1 : 0);
+  }
+}
+template <int D> struct KP { static constexpr int P = (D == 2) ? 2 : 6; };
+
+__device__ __forceinline__ void node_ijk(const Grid &g, long long a, int idx[3]) {
+  idx[0] = (int)(a % g.nn[0]);
+  long long t = a / g.nn[0];
+  idx[1] = (int)(t % g.nn[1]);
+  idx[2] = (int)(t / g.nn[1]);
+}
+
+// Element (p, m) of node `a` at grid index idx: node is vertex m of simplex p whose cell
+// corner is idx - sum_{l<m} e_{pi_l}.  Returns false when that cell lies outside the grid.
+// On success writes the element id and the vertex node ids v[0..D].
+template <int D>
+__device__ __forceinline__ bool kuhn_elem(const Grid &g, const int idx[3], long long a, int p, int m,
+                                          long long &elem, long long v[D + 1]) {
+  int c[3] = {idx[0], idx[1], idx[2]};
+#pragma unroll
+  for (int l = 0; l < D; ++l)
+    if (l < m) c[kperm<D>(p, l)] -= 1;
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+    if (c[k] < 0 || c[k] >= g.n[k]) return false;
+  long long cell = c[0] + g.cstride[1] * c[1] + (D == 3 ? g.cstride[2] * c[2] : 0);
+  elem = (long long)KP<D>::P * cell + p;
+  long long base = c[0] + g.stride[1] * c[1] + (D == 3 ? g.stride[2] * c[2] : 0);
+  v[0] = base;
+#pragma unroll
+  for (int l = 0; l < D; ++l) v[l + 1] = v[l] + g.stride[kperm<D>(p, l)];
+  (void)a;
+  return true;
+}
+
+// Stencil slot of the neighbour at offset delta (each component in {-1, 0, 1}); Kuhn
+// neighbours have delta in {0,1}^D or -{0,1}^D.  Slot order: 0 = self, then positive
+// offsets by bitmask 1..2^D-1, then negative offsets by bitmask.
+template <int D>
+__device__ __forceinline__ int stencil_slot(const int delta[3]) {
+  int pos = 0, neg = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    if (delta[k] > 0) pos |= 1 << k;
+    if (delta[k] < 0) neg |= 1 << k;
+  }
+  if (pos == 0 && neg == 0) return 0;
+  if (neg == 0) return pos;
+  return (1 << D) - 1 + neg;
+}
+template <int D> struct ST { static constexpr int S = (D == 2) ? 7 : 15; };
+
+template <int D>
+__device__ __forceinline__ void slot_offset(int s, int delta[3]) {
+  delta[0] = delta[1] = delta[2] = 0;
+  if (s == 0) return;
+  int sign = 1, mask = s;
+  if (s >= (1 << D)) { sign = -1; mask = s - ((1 << D) - 1); }
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+    if (mask & (1 << k)) delta[k] = sign;
+}
+
+// ---- bounded grid barrier --------------------------------------------------------------
+// One counter; block 0 adds 2^31 - (G - 1), every other block adds 1, so the top bit flips
+// exactly when all G blocks have arrived.  The counter must hold 0 at launch and the grid
+// must be co-resident (cooperative launch).  A wait longer than `limit_ns` sets the error
+// word to DEV_TIMEOUT and every block returns false from that barrier on.
+__device__ __forceinline__ unsigned fo_ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned fo_atom_add_release(unsigned *p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned long long fo_globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+struct GridBar {
+  unsigned *count;
+  int *err;
+  unsigned long long limit_ns;
+};
+
+__device__ __forceinline__ bool grid_sync(const GridBar &b) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned inc = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1)) : 1u;
+    __threadfence();
+    unsigned old = fo_atom_add_release(b.count, inc);
+    int ok = 1;
+    unsigned long long t0 = 0;
+    unsigned spins = 0;
+    while (((old ^ fo_ld_acquire(b.count)) & 0x80000000u) == 0) {
+      if (++spins == 64) t0 = fo_globaltimer();
+      if (spins > 64) {
+        __nanosleep(40);
+        if ((spins & 255) == 0 && fo_globaltimer() - t0 > b.limit_ns) {
+          atomicExch(b.err, DEV_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    if (ok && *(volatile int *)b.err == DEV_TIMEOUT) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---- deterministic reductions -----------------------------------------------------------
+// Block sum of NR values (fixed shuffle tree, fixed warp order); result valid in thread 0.
+template <int NR>
+__device__ __forceinline__ void block_sum(double (&v)[NR], double *smem /* [32*NR] */) {
+#pragma unroll
+  for (int j = 0; j < NR; ++j)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) smem[warp * NR + j] = v[j];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      double t = (lane < nw) ? smem[lane * NR + j] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      v[j] = t;
+    }
+  }
+}
+
+// Sum of the per-block partials [G][NR] in a fixed order; every block gets the same bits.
+// Result broadcast to all threads through smem_out[NR].
+template <int NR>
+__device__ __forceinline__ void grid_total(const double *partials, double *smem_out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      double t = 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(partials + (size_t)b * NR + j);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0) smem_out[j] = t;
+    }
+  }
+  __syncthreads();
+}
+
+// ---- host launch helpers ------------------------------------------------------------------
+inline int fo_blocks_for(long long n, int block = FO_BLOCK, int cap = 1 << 20) {
+  long long b = (n + block - 1) / block;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+// internal entry points implemented across translation units
+fo_status fo_launch_coefficients(fo_problem *p);
+fo_status fo_launch_loads(fo_problem *p);
+fo_status fo_launch_masks(fo_problem *p);
+fo_status fo_launch_state_diag(fo_problem *p);
+fo_status fo_launch_velocity_diag(fo_problem *p);
+fo_status fo_launch_state_apply(fo_problem *p, const double *x, double *y, bool mask_input);
+fo_status fo_launch_state_apply32(fo_problem *p, const double *x, double *y);
+fo_status fo_launch_velocity_apply(fo_problem *p, const double *x, double *y);
+fo_status fo_launch_functionals(fo_problem *p, double *J, double *vol);
+fo_status fo_launch_shape_rhs(fo_problem *p, double lambda);
+fo_status fo_launch_mesh_build(fo_mesh *m);
+fo_status fo_launch_initial_level(fo_problem *p, int count, const double *centers, const double *radii,
+                                  double factor, int ord);
+fo_status fo_state_pcg(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st);
+fo_status fo_velocity_pcg(fo_problem *p, const fo_solve_opts *o, double *Btt, fo_solve_stats *st);
+fo_status fo_launch_transport_assemble(fo_problem *p, double dt, double h, int smooth);
+fo_status fo_launch_stencil_apply(fo_problem *p, const double *S, const double *x, double *y);
+fo_status fo_transport_run(fo_problem *p, int nsteps, const fo_solve_opts *o, fo_solve_stats *st);
+fo_status fo_reinit_run(fo_problem *p, int nsteps, double dt, double h, const fo_solve_opts *o,
+                        fo_solve_stats *st);
+fo_status fo_scratch(fo_problem *p, size_t bytes, void **out);
+fo_status fo_cooperative_grid(fo_problem *p, const void *kernel, int block, size_t smem, long long work,
+                              int requested, int *grid);

@@ -1,0 +1,472 @@
+// Persistent, cooperatively launched Jacobi-PCG for the state and velocity systems, and the
+// FP32-inner / FP64-refinement driver of the mixed path.
+//
+// One launch runs the whole solve.  Per iteration there are two grid barriers:
+//   phase A  p_new = z + beta p_old for the owned nodes, q = A (z + beta p_old) with the
+//            combination formed inside the operator's gather (so no barrier is needed
+//            between the p update and the apply), partial p.q;
+//   phase B  x += alpha p, r -= alpha q, z = D^{-1} r, partials r.z and r.r.
+// p is double-buffered so that phase A never overwrites a value another block still reads.
+// All dot products are accumulated in FP64 with a fixed reduction order: block partials,
+// then every block sums the partials in the same order, so every block takes the same
+// branch and the result does not depend on timing.
+#include <cmath>
+#include <cstring>
+#include <algorithm>
+
+#include "fo_internal.cuh"
+#include "fo_ops.cuh"
+
+
+// ----------------------------------------------------------------------------- scratch
+fo_status fo_scratch(fo_problem *p, size_t bytes, void **out) {
+  if (bytes > p->scratch.bytes) {
+    fo_free(p->ctx, p->scratch.buf, p->scratch.bytes);
+    p->scratch.buf = nullptr;
+    p->scratch.bytes = 0;
+    FO_TRY(fo_alloc(p->ctx, &p->scratch.buf, bytes));
+    p->scratch.bytes = bytes;
+  }
+  if (out) *out = p->scratch.buf;
+  return FO_OK;
+}
+
+fo_status fo_cooperative_grid(fo_problem *p, const void *kernel, int block, size_t smem, long long work,
+                              int requested, int *grid) {
+  int per_sm = 0;
+  FO_CU(p->ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem));
+  if (per_sm < 1) return fo_fail(p->ctx, FO_ECUDA, "persistent kernel does not fit on an SM");
+  long long cap = (long long)per_sm * p->ctx->num_sms;
+  long long want = requested > 0 ? requested : (work + block - 1) / block;
+  if (want > cap) want = cap;
+  if (want > 4096) want = 4096;
+  if (want < 1) want = 1;
+  *grid = (int)want;
+  return FO_OK;
+}
+
+// ------------------------------------------------------------------------------ kernel
+template <int NC, typename T>
+struct PcgArgs {
+  T *x, *r, *z, *p0, *p1, *q;
+  const double *b;       // right-hand side (FP64), scaled by bscale
+  const T *bT;           // right-hand side in T when non-null (inner solves)
+  const uint8_t *bmask;  // per node: nonzero rows get a zero right-hand side (H^1_0 rows)
+  double bscale;
+  const T *dinv;
+  double *partials;      // [2][G][3 NC]: two buffers used alternately
+  double *out;           // [4 NC]: rr, bb, b.x, pad
+  int *status;           // DS_* words
+  GridBar bar;
+  double rtol2;
+  int maxit;
+  int warm;
+};
+
+// Block-sum the NR values, publish the block partial, wait for the grid, and sum all
+// partials in a fixed order into stot.  Consecutive reductions alternate between two
+// partial buffers: a block that races ahead to the next reduction cannot overwrite a
+// partial that a slower block is still summing (it passed the barrier in between).
+template <int NR>
+__device__ __forceinline__ bool reduce_grid(double (&v)[NR], double *sred, double *stot, double *partials, int &rk,
+                                            const GridBar &bar) {
+  block_sum<NR>(v, sred);
+  double *part = partials + (size_t)(rk & 1) * gridDim.x * NR;
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) part[(size_t)blockIdx.x * NR + j] = v[j];
+  if (!grid_sync(bar)) return false;
+  grid_total<NR>(part, stot);
+  ++rk;
+  return true;
+}
+
+template <int D, class Op, typename T, int NC>
+__global__ void __launch_bounds__(FO_BLOCK) k_pcg(Op op, PcgArgs<NC, T> S) {
+  constexpr int NPN = Op::NPN;
+  constexpr int NR = 3 * NC;
+  __shared__ double sred[32 * NR];
+  __shared__ double stot[NR];
+  const Grid &g = op.g;
+  const long long N = g.num_nodes;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long gstride = (long long)gridDim.x * blockDim.x;
+
+  // ---- phase 0: r = b - A x0, z = D^{-1} r, p_old = 0
+  double v[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) v[j] = 0.0;
+  for (long long a = tid; a < N; a += gstride) {
+    int idx[3];
+    node_ijk(g, a, idx);
+    T ax[NPN];
+    if (S.warm) op.row(a, idx, VecX<T>{S.x}, ax);
+#pragma unroll
+    for (int c = 0; c < NPN; ++c) {
+      const long long k = a * NPN + c;
+      const int sy = (NC == 1) ? 0 : c;
+      const double bk = (S.bmask && S.bmask[a]) ? 0.0 : (S.bT ? (double)S.bT[k] : S.bscale * S.b[k]);
+      if (!S.warm) { ax[c] = T(0); S.x[k] = T(0); }
+      const T rk = (T)(bk - (double)ax[c]);
+      const T zk = S.dinv[k] * rk;
+      S.r[k] = rk;
+      S.z[k] = zk;
+      S.p0[k] = T(0);
+      v[sy * 3 + 0] += (double)rk * (double)zk;
+      v[sy * 3 + 1] += (double)rk * (double)rk;
+      v[sy * 3 + 2] += bk * bk;
+    }
+  }
+  int rk = 0;
+  if (!reduce_grid<NR>(v, sred, stot, S.partials, rk, S.bar)) return;
+  double rz[NC], rr[NC], bb[NC], beta[NC], alpha[NC];
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    rz[s] = stot[s * 3 + 0];
+    rr[s] = stot[s * 3 + 1];
+    bb[s] = stot[s * 3 + 2];
+    beta[s] = 0.0;
+  }
+  T *pold = S.p0, *pnew = S.p1;
+  int it = 0, err = DEV_OK;
+  for (;;) {
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      if (!(rr[s] == rr[s]) || !(rz[s] == rz[s])) err = DEV_NAN;
+      if (rr[s] > S.rtol2 * bb[s]) any = true;
+    }
+    if (err != DEV_OK || !any) break;
+    if (it >= S.maxit) { err = DEV_NOCONV; break; }
+    bool active[NC];
+#pragma unroll
+    for (int s = 0; s < NC; ++s) active[s] = rr[s] > S.rtol2 * bb[s];
+    // ---- phase A
+    __syncthreads();   // stot is rewritten below
+    double w[NC];
+#pragma unroll
+    for (int s = 0; s < NC; ++s) w[s] = 0.0;
+    CombX<T, NC> cx;
+    cx.z = S.z;
+    cx.p = pold;
+#pragma unroll
+    for (int s = 0; s < NC; ++s) cx.beta[s] = (T)beta[s];
+    for (long long a = tid; a < N; a += gstride) {
+      int idx[3];
+      node_ijk(g, a, idx);
+      T qa[NPN];
+      op.row(a, idx, cx, qa);
+#pragma unroll
+      for (int c = 0; c < NPN; ++c) {
+        const long long k = a * NPN + c;
+        const int sy = (NC == 1) ? 0 : c;
+        const T pk = S.z[k] + cx.beta[sy] * pold[k];
+        pnew[k] = pk;
+        S.q[k] = qa[c];
+        w[sy] += (double)pk * (double)qa[c];
+      }
+    }
+    {
+      double tmp[NR];
+#pragma unroll
+      for (int j = 0; j < NR; ++j) tmp[j] = (j % 3 == 0) ? w[j / 3] : 0.0;
+      if (!reduce_grid<NR>(tmp, sred, stot, S.partials, rk, S.bar)) return;
+    }
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      const double pq = stot[s * 3];
+      alpha[s] = (active[s] && pq != 0.0) ? rz[s] / pq : 0.0;
+    }
+    // ---- phase B
+#pragma unroll
+    for (int j = 0; j < NR; ++j) v[j] = 0.0;
+    for (long long a = tid; a < N; a += gstride) {
+#pragma unroll
+      for (int c = 0; c < NPN; ++c) {
+        const long long k = a * NPN + c;
+        const int sy = (NC == 1) ? 0 : c;
+        const T al = (T)alpha[sy];
+        S.x[k] += al * pnew[k];
+        const T rk = S.r[k] - al * S.q[k];
+        const T zk = S.dinv[k] * rk;
+        S.r[k] = rk;
+        S.z[k] = zk;
+        v[sy * 3 + 0] += (double)rk * (double)zk;
+        v[sy * 3 + 1] += (double)rk * (double)rk;
+      }
+    }
+    if (!reduce_grid<NR>(v, sred, stot, S.partials, rk, S.bar)) return;
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      const double rzn = stot[s * 3 + 0];
+      rr[s] = stot[s * 3 + 1];
+      beta[s] = (active[s] && rz[s] != 0.0) ? rzn / rz[s] : 0.0;
+      if (active[s]) rz[s] = rzn;
+    }
+    T *t = pold;
+    pold = pnew;
+    pnew = t;
+    ++it;
+  }
+  // ---- b . x per system (B(theta, theta) = -b . theta for the velocity)
+  __syncthreads();
+  double bx[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) bx[j] = 0.0;
+  for (long long a = tid; a < N; a += gstride)
+#pragma unroll
+    for (int c = 0; c < NPN; ++c) {
+      const long long k = a * NPN + c;
+      const int sy = (NC == 1) ? 0 : c;
+      const double bk = (S.bmask && S.bmask[a]) ? 0.0 : (S.bT ? (double)S.bT[k] : S.bscale * S.b[k]);
+      bx[sy * 3] += bk * (double)S.x[k];
+    }
+  if (!reduce_grid<NR>(bx, sred, stot, S.partials, rk, S.bar)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int s = 0; s < NC; ++s) {
+      S.out[s * 4 + 0] = rr[s];
+      S.out[s * 4 + 1] = bb[s];
+      S.out[s * 4 + 2] = stot[s * 3];
+    }
+    S.status[DS_ITERS] = it;
+    if (err != DEV_OK) atomicCAS(S.status + DS_ERR, DEV_OK, err);
+  }
+}
+
+// ------------------------------------------------------------------------- host driver
+template <class K, class... Args>
+static fo_status coop_launch(fo_problem *p, K kernel, int grid, Args... args) {
+  void *argv[] = {(void *)&args...};
+  FO_CU(p->ctx, cudaMemsetAsync(p->bar, 0, 64, p->ctx->stream));
+  FO_CU(p->ctx, cudaMemsetAsync(p->dev_status, 0, sizeof(int) * DS_COUNT, p->ctx->stream));
+  FO_CU(p->ctx, cudaLaunchCooperativeKernel((const void *)kernel, grid, FO_BLOCK, argv, 0, p->ctx->stream));
+  fo_note_launch(1);
+  return FO_OK;
+}
+
+struct SolveOut {
+  int status[DS_COUNT];
+  double out[16];
+};
+
+static fo_status read_out(fo_problem *p, double *out_dev, SolveOut *o, int nout) {
+  fo_ctx *ctx = p->ctx;
+  FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars, out_dev, sizeof(double) * nout, cudaMemcpyDeviceToHost, ctx->stream));
+  FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars + 32, p->dev_status, sizeof(int) * DS_COUNT, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+  FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  memcpy(o->out, ctx->h_scalars, sizeof(double) * nout);
+  memcpy(o->status, ctx->h_scalars + 32, sizeof(int) * DS_COUNT);
+  return FO_OK;
+}
+
+static double *out_area(fo_problem *p) { return p->red + FO_MAX_RED * 4096 - 64; }
+
+template <int D, class Op, typename T, int NC>
+static fo_status run_pcg(fo_problem *p, const Op &op, PcgArgs<NC, T> a, long long nodes, int requested, SolveOut *o) {
+  auto kern = k_pcg<D, Op, T, NC>;
+  int grid;
+  FO_TRY(fo_cooperative_grid(p, (const void *)kern, FO_BLOCK, 0, nodes, requested, &grid));
+  a.partials = p->red;
+  a.out = out_area(p);
+  a.status = p->dev_status;
+  a.bar = GridBar{p->bar, p->dev_status + DS_ERR, 2000000000ull};
+  FO_TRY(coop_launch(p, kern, grid, op, a));
+  FO_CU(p->ctx, cudaGetLastError());
+  FO_TRY(read_out(p, out_area(p), o, 4 * NC));
+  if (o->status[DS_ERR] == DEV_TIMEOUT) return fo_fail(p->ctx, FO_ETIMEOUT, "grid barrier timed out in PCG");
+  if (o->status[DS_ERR] == DEV_NAN) return fo_fail(p->ctx, FO_ENAN, "NaN in the PCG recurrence");
+  return FO_OK;
+}
+
+__global__ void k_residual_norms(const double *b, const double *ax, double *r, long long n, double *partials) {
+  __shared__ double sm[64];
+  double v[2] = {0, 0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double ri = b[i] - ax[i];
+    r[i] = ri;
+    v[0] += ri * ri;
+    v[1] += b[i] * b[i];
+  }
+  block_sum<2>(v, sm);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x * 2] = v[0];
+    partials[blockIdx.x * 2 + 1] = v[1];
+  }
+}
+__global__ void k_finish_sum2(const double *partials, int nblocks, double *out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (w >= 2) return;
+  double t = 0;
+  for (int b = lane; b < nblocks; b += 32) t += partials[(size_t)b * 2 + w];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  if (lane == 0) out[w] = t;
+}
+__global__ void k_to_float(const double *x, float *y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+__global__ void k_add_float(double *x, const float *d, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] += (double)d[i];
+}
+
+template <int D, class Op64, class Op32>
+static fo_status state_solve_impl(fo_problem *p, const Op64 &op64, const Op32 &op32, const double *b, double *x,
+                                  const fo_solve_opts *o, fo_solve_stats *st) {
+  const Grid &g = p->mesh->g;
+  const long long n = p->ndof;
+  fo_solve_stats s;
+  memset(&s, 0, sizeof s);
+  if (o->precision == FO_FP64) {
+    double *buf;
+    FO_TRY(fo_scratch(p, sizeof(double) * 5 * n, (void **)&buf));
+    PcgArgs<1, double> a{};
+    a.x = x;
+    a.r = buf;
+    a.z = buf + n;
+    a.p0 = buf + 2 * n;
+    a.p1 = buf + 3 * n;
+    a.q = buf + 4 * n;
+    a.b = b;
+    a.bscale = 1.0;
+    a.dinv = p->dinv_state;
+    a.rtol2 = o->rtol * o->rtol;
+    a.maxit = o->maxit;
+    a.warm = o->warm_start;
+    SolveOut out;
+    FO_TRY(run_pcg<D>(p, op64, a, g.num_nodes, o->grid_blocks, &out));
+    s.iterations = out.status[DS_ITERS];
+    s.operator_applies = s.iterations + (o->warm_start ? 1 : 0);
+    s.outer_iterations = 1;
+    s.rel_residual = out.out[1] > 0 ? std::sqrt(out.out[0] / out.out[1]) : 0.0;
+    if (st) *st = s;
+    if (out.status[DS_ERR] == DEV_NOCONV) return fo_fail(p->ctx, FO_ENOCONV, "PCG reached maxit=%d", o->maxit);
+    return FO_OK;
+  }
+  // ---- mixed: FP32 inner PCG (FP64 dots) inside FP64 iterative refinement
+  char *buf;
+  const size_t bytes = sizeof(double) * 2 * n + sizeof(float) * 7 * n;
+  FO_TRY(fo_scratch(p, bytes, (void **)&buf));
+  double *r64 = (double *)buf, *ax64 = r64 + n;
+  float *f = (float *)(ax64 + n);
+  float *d32 = f, *r32 = f + n, *z32 = f + 2 * n, *p0 = f + 3 * n, *p1 = f + 4 * n, *q32 = f + 5 * n, *b32 = f + 6 * n;
+  fo_ctx *ctx = p->ctx;
+  const int blocks = fo_blocks_for(n, FO_BLOCK, 1024);
+  if (!o->warm_start) FO_CU(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream));
+  double bnorm2 = -1, prev_rn2 = INFINITY, prev2_rn2 = INFINITY;
+  const int max_outer = 60;
+  const char *tr = getenv("FORMOPT_TRACE");   // trace the refinement on stderr when set
+  const bool trace = tr && tr[0] && tr[0] != '0';
+  for (int outer = 0;; ++outer) {
+    // FP64 residual r = b - A x (the operator masks Dirichlet columns; rows are identity)
+    FO_TRY(fo_launch_state_apply(p, x, ax64, true));
+    k_residual_norms<<<blocks, FO_BLOCK, 0, ctx->stream>>>(b, ax64, r64, n, p->red);
+    k_finish_sum2<<<1, 64, 0, ctx->stream>>>(p->red, blocks, out_area(p) + 8);
+    fo_note_launch(2);
+    FO_CU(ctx, cudaGetLastError());
+    FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars, out_area(p) + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    const double rn2 = ctx->h_scalars[0];
+    if (bnorm2 < 0) bnorm2 = ctx->h_scalars[1];
+    s.operator_applies += 1;
+    s.rel_residual = bnorm2 > 0 ? std::sqrt(rn2 / bnorm2) : 0.0;
+    if (trace)
+      fprintf(stderr, "[formopt] refinement step %d: ||b - Ax||/||b|| = %.3e after %d inner iterations\n", outer,
+              s.rel_residual, s.iterations);
+    if (!std::isfinite(rn2)) return fo_fail(ctx, FO_ENAN, "NaN in the refinement residual");
+    if (rn2 <= o->rtol * o->rtol * bnorm2 || bnorm2 == 0) break;
+    // The FP64 residual cannot fall below its own rounding floor (about eps * ||A|| ||x||,
+    // i.e. kappa * eps relative to ||b|| on ill-conditioned systems).  Two consecutive steps
+    // that fail to halve it mean the floor is reached: x is as accurate as FP64 allows.
+    if (outer >= 2 && rn2 > 0.25 * prev_rn2 && prev_rn2 > 0.25 * prev2_rn2) break;
+    prev2_rn2 = prev_rn2;
+    prev_rn2 = rn2;
+    if (outer >= max_outer || s.iterations >= o->maxit) {
+      if (st) *st = s;
+      return fo_fail(ctx, FO_ENOCONV, "iterative refinement stalled at %.3e", s.rel_residual);
+    }
+    k_to_float<<<blocks, FO_BLOCK, 0, ctx->stream>>>(r64, b32, n);
+    fo_note_launch(1);
+    PcgArgs<1, float> a{};
+    a.x = d32;
+    a.r = r32;
+    a.z = z32;
+    a.p0 = p0;
+    a.p1 = p1;
+    a.q = q32;
+    a.b = nullptr;
+    a.bT = b32;
+    a.bscale = 1.0;
+    a.dinv = p->dinv_state32;
+    a.rtol2 = o->inner_rtol * o->inner_rtol;
+    a.maxit = o->inner_maxit;
+    a.warm = 0;
+    SolveOut out;
+    FO_TRY(run_pcg<D>(p, op32, a, g.num_nodes, o->grid_blocks, &out));
+    s.iterations += out.status[DS_ITERS];
+    s.operator_applies += out.status[DS_ITERS];
+    s.outer_iterations = outer + 1;
+    k_add_float<<<blocks, FO_BLOCK, 0, ctx->stream>>>(x, d32, n);
+    fo_note_launch(1);
+    FO_CU(ctx, cudaGetLastError());
+  }
+  if (st) *st = s;
+  return FO_OK;
+}
+
+fo_status fo_state_pcg(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st) {
+  const Grid &g = p->mesh->g;
+  if (p->desc.kind == FO_ELASTIC) {
+    if (g.dim == 2)
+      return state_solve_impl<2>(p, make_elastic_op<2, double>(p), make_elastic_op<2, float>(p), b, x, o, st);
+    return state_solve_impl<3>(p, make_elastic_op<3, double>(p), make_elastic_op<3, float>(p), b, x, o, st);
+  }
+  if (g.dim == 2) return state_solve_impl<2>(p, make_scalar_op<2, double>(p), make_scalar_op<2, float>(p), b, x, o, st);
+  return state_solve_impl<3>(p, make_scalar_op<3, double>(p), make_scalar_op<3, float>(p), b, x, o, st);
+}
+
+template <int D>
+static fo_status velocity_impl(fo_problem *p, const fo_solve_opts *o, double *Btt, fo_solve_stats *st) {
+  const Grid &g = p->mesh->g;
+  const long long n = (long long)D * g.num_nodes;
+  double *buf;
+  FO_TRY(fo_scratch(p, sizeof(double) * 5 * n, (void **)&buf));
+  PcgArgs<D, double> a{};
+  a.x = p->theta;
+  a.r = buf;
+  a.z = buf + n;
+  a.p0 = buf + 2 * n;
+  a.p1 = buf + 3 * n;
+  a.q = buf + 4 * n;
+  a.b = p->rhs;
+  a.bscale = -1.0;                // B theta = -b
+  a.bmask = p->desc.velocity_dirichlet ? p->vdir : nullptr;
+  a.dinv = p->dinv_vel;
+  a.rtol2 = o->rtol * o->rtol;
+  a.maxit = o->maxit;
+  a.warm = o->warm_start;
+  SolveOut out;
+  FO_TRY(run_pcg<D>(p, make_velocity_op<D, double>(p), a, g.num_nodes, o->grid_blocks, &out));
+  double rr = 0, bb = 0, bx = 0;
+  for (int s = 0; s < D; ++s) {
+    rr += out.out[s * 4];
+    bb += out.out[s * 4 + 1];
+    bx += out.out[s * 4 + 2];   // (-b) . theta summed over components
+  }
+  if (Btt) *Btt = bx;           // B(theta, theta) = -b . theta
+  if (st) {
+    st->iterations = out.status[DS_ITERS];
+    st->operator_applies = out.status[DS_ITERS] + (o->warm_start ? 1 : 0);
+    st->outer_iterations = 1;
+    st->rel_residual = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+  }
+  if (out.status[DS_ERR] == DEV_NOCONV) return fo_fail(p->ctx, FO_ENOCONV, "velocity PCG reached maxit");
+  return FO_OK;
+}
+
+fo_status fo_velocity_pcg(fo_problem *p, const fo_solve_opts *o, double *Btt, fo_solve_stats *st) {
+  if (p->mesh->g.dim == 2) return velocity_impl<2>(p, o, Btt, st);
+  return velocity_impl<3>(p, o, Btt, st);
+}

@@ -1,0 +1,302 @@
+"""GPU (sm_103a, through the C ABI) against the FP64 oracle, step by step.
+
+Tolerances: integer results (connectivity, masks, element flags, step counts) bit-exact;
+deterministic FP64 kernels (loads, operator applies, RHS) elementwise within 1e-12 of the
+vector's scale; FP64 solves within 1e-10 relative of the oracle's direct solution where the
+system's conditioning allows any FP64 solver to reach it, and otherwise with componentwise
+backward error at the FP64 rounding level and forward difference inside the first-order
+perturbation bound (never above 1e-8; see tests/helpers.assert_solve_parity); the mixed
+FP32+FP64-refinement path within 1e-8.
+"""
+import numpy as np
+import pytest
+
+from oracle import fem, levelset, shape, solvers, velocity as ovel
+from oracle.mesh import BoxMesh
+from paper_2601_05709_gb300 import workloads
+from tests.helpers import (HEAT2D, assert_solve_parity, cantilever2d, cantilever3d, case, close_scaled, gpu_problem,
+                           oracle_problem, rel)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2601_05709_gb300 import api as a
+    return a
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def tight(api, precision=None):
+    return api.solve_opts(precision=api.FO_FP64 if precision is None else precision, rtol=1e-13, maxit=400000)
+
+
+# ------------------------------------------------------------------------------- mesh
+@pytest.mark.parametrize("dim,n,lo,hi", [(2, (1, 1), (0, 0), (1, 1)), (2, (7, 5), (0.1, -0.3), (0.7, 0.9)),
+                                         (2, (64, 64), (0, 0), (1, 1)), (2, (256, 128), (0, 0), (2, 1)),
+                                         (3, (1, 1, 1), (0, 0, 0), (1, 1, 1)), (3, (3, 2, 5), (0, 0, 0), (1, 2, 3)),
+                                         (3, (96, 48, 48), (0, 0, 0), (2, 1, 1))])
+def test_mesh_bit_exact(ctx, dim, n, lo, hi):
+    m = ctx.mesh_box(dim, n, lo, hi)
+    cells, coords = m.copy_out()
+    om = BoxMesh(dim, n, lo, hi)
+    assert cells.dtype == om.cells.dtype and np.array_equal(cells, om.cells)
+    assert np.array_equal(coords.view(np.uint64), om.coords.view(np.uint64))
+    assert m.num_elems == om.num_elems and m.num_nodes == om.num_nodes
+    assert m.h == om.diameter()
+
+
+# ----------------------------------------------------------------- coefficients / masks
+@pytest.mark.parametrize("dim,n", [(2, (33, 17)), (3, (9, 7, 5))])
+def test_coefficients_and_masks_bit_exact(ctx, api, dim, n):
+    c = case(dim=dim, n=n, hi=(2.0,) + (1.0,) * (dim - 1), omega0_weight=1e4,
+             omega0_boxes=[((1.5,) + (0.3,) * (dim - 1), (np.inf,) + (0.7,) * (dim - 1)),
+                           ((-np.inf,) * dim, (0.2,) * dim)])
+    mesh, prob = gpu_problem(ctx, c)
+    op = oracle_problem(c)
+    _, coords = mesh.copy_out()
+    phi = workloads.phi_cos(coords) if dim == 2 else workloads.phi_bumps(coords, workloads.bump_centres((0,) * 3, (2, 1, 1), 6, 1))
+    # plant exact ties: a zero vertex sum must count as outside
+    phi[: min(40, len(phi))] = 0.0
+    prob.set_levelset(phi)
+    prob.coefficients()
+    A, chi = shape.coefficient(phi, op.mesh.cells, c["a_in"], c["a_out"])
+    assert np.array_equal(prob.get(api._lib.FO_FIELD_CHI).astype(np.uint8), chi)
+    assert np.array_equal(prob.get(api._lib.FO_FIELD_COEF), A)
+    om0 = op.mesh.subdomain_mask(c["omega0_boxes"])
+    assert np.array_equal(prob.get(api._lib.FO_FIELD_OMEGA0).astype(np.uint8), om0)
+
+
+# -------------------------------------------------------------------------------- loads
+@pytest.mark.parametrize("c", [
+    case(dim=2, n=(9, 6), kind=0, f=lambda X: 1 + X[:, 0] * X[:, 1], dirichlet=[(0, 0), (1, 1)]),
+    case(dim=3, n=(4, 3, 5), kind=0, f=lambda X: np.cos(X[:, 2]) + X[:, 0]),
+    case(dim=2, n=(16, 8), lo=(0, 0), hi=(2, 1), kind=1, point_loads=[((16, 4), (0.3, -1.0)), ((5, 8), (1.0, 0.0))],
+         tractions=[(1, 0, (0.0, -0.5))]),
+    case(dim=3, n=(6, 3, 3), lo=(0, 0, 0), hi=(2, 1, 1), kind=1, tractions=[(0, 1, (0.0, 0.0, -1.0)), (2, 1, (0.1, 0.2, 0.3))]),
+])
+def test_loads(ctx, api, c):
+    _, prob = gpu_problem(ctx, c)
+    op = oracle_problem(c)
+    F = prob.get(api._lib.FO_FIELD_LOAD)
+    assert close_scaled(F, op.load(), 1e-14)
+
+
+# ------------------------------------------------------------------------ operator applies
+STATE_CASES = [
+    case(dim=2, n=(13, 9), kind=0, dirichlet=[(0, 0)]),
+    case(dim=3, n=(5, 4, 6), kind=0, dirichlet=[(0, 0), (2, 1)]),
+    case(dim=2, n=(11, 7), lo=(0, 0), hi=(2, 1), kind=1, dirichlet=[(0, 0)]),
+    case(dim=3, n=(6, 3, 4), lo=(0, 0, 0), hi=(2, 1, 1), kind=1, dirichlet=[(0, 0)]),
+    case(dim=2, n=(10, 10), kind=2, k=1.7, omega=3.1, dirichlet=[(0, 0)], f=lambda X: X[:, 0]),
+]
+
+
+@pytest.mark.parametrize("c", STATE_CASES)
+def test_state_apply(ctx, api, c):
+    mesh, prob = gpu_problem(ctx, c)
+    op = oracle_problem(c)
+    phi = workloads.phi_bumps(op.mesh.coords, workloads.bump_centres(c["lo"], c["hi"], 5, 2), 0.2, 0.5)
+    prob.set_levelset(phi)
+    A, chi = shape.coefficient(phi, op.mesh.cells, c["a_in"], c["a_out"])
+    K = op.stiffness(A)
+    dmask = op.dirichlet()
+    x = workloads.random_field(K.shape[0], 9)
+    x[dmask == 1] = 0.0
+    y = prob.apply(api._lib.FO_OP_STATE, x)
+    ref = K @ x
+    ref[dmask == 1] = 0.0
+    assert close_scaled(y, ref, 1e-12)
+    # Dirichlet columns are dropped: a nonzero x there must not leak into free rows
+    x2 = workloads.random_field(K.shape[0], 10)
+    y2 = prob.apply(api._lib.FO_OP_STATE, x2)
+    x2m = np.where(dmask == 1, 0.0, x2)
+    ref2 = K @ x2m
+    ref2[dmask == 1] = 0.0
+    assert close_scaled(y2, ref2, 1e-12)
+    # the FP32 operator of the mixed path agrees to single precision
+    y32 = prob.apply(api._lib.FO_OP_STATE_FP32, x)
+    assert close_scaled(y32, ref, 2e-5)
+
+
+@pytest.mark.parametrize("c", [
+    case(dim=2, n=(12, 6), lo=(0, 0), hi=(2, 1), kind=1, alpha_mass=0.1, normal_penalty=1e4, omega0_weight=1e4,
+         omega0_boxes=[((1.5, 0.3), (np.inf, 0.7))]),
+    case(dim=3, n=(6, 3, 4), lo=(0, 0, 0), hi=(2, 1, 1), kind=1, alpha_mass=0.1, normal_penalty=1e4, omega0_weight=1e4,
+         omega0_boxes=[((1.5, 0.3, 0.3), (np.inf, 0.7, 0.7))]),
+    case(dim=2, n=(9, 9), kind=0, alpha_mass=0.01, velocity_dirichlet=True),
+    case(dim=3, n=(4, 4, 3), kind=0, alpha_mass=0.01, velocity_dirichlet=True),
+])
+def test_velocity_apply(ctx, api, c):
+    mesh, prob = gpu_problem(ctx, c)
+    op = oracle_problem(c)
+    d = c["dim"]
+    x = workloads.random_field(d * op.mesh.num_nodes, 4)
+    y = prob.apply(api._lib.FO_OP_VELOCITY, x).reshape(-1, d)
+    free = ovel.free_nodes(op.mesh, op.vform)
+    x2 = x.reshape(-1, d)
+    for a in range(d):
+        B = ovel.component_matrix(op.mesh, op.vform, a)
+        ref = np.where(free, B @ np.where(free, x2[:, a], 0.0), x2[:, a])
+        if c["velocity_dirichlet"]:
+            # H^1_0: free rows see only free columns; boundary rows are the identity applied to
+            # the masked input, i.e. zero
+            assert close_scaled(y[free, a], ref[free], 1e-12)
+            assert np.all(y[~free, a] == 0.0)
+        else:
+            assert close_scaled(y[:, a], B @ x2[:, a], 1e-12)
+
+
+# ------------------------------------------------------------------------------ state solves
+@pytest.mark.parametrize("c", [
+    case(**HEAT2D),
+    case(dim=2, n=(37, 23), kind=0, f=lambda X: 1 + X[:, 1], dirichlet=[(0, 0), (1, 1)]),
+    case(dim=3, n=(10, 8, 6), kind=0, f=lambda X: np.ones(X.shape[0]), dirichlet=[(0, 0)]),
+    cantilever2d((64, 32)),
+    cantilever2d((256, 128)),
+    cantilever3d((12, 6, 6)),
+    case(dim=2, n=(40, 40), kind=2, k=0.8, omega=4.0, f=lambda X: np.cos(np.pi * X[:, 0]) + X[:, 1], dirichlet=[(0, 0)]),
+])
+def test_state_solve_fp64(ctx, api, c):
+    mesh, prob = gpu_problem(ctx, c)
+    op = oracle_problem(c)
+    phi = (workloads.phi_cos(op.mesh.coords) if c["dim"] == 2 else
+           workloads.phi_bumps(op.mesh.coords, workloads.bump_centres(c["lo"], c["hi"], 8, 0), 0.25, 0.2))
+    prob.set_levelset(phi)
+    st = prob.state_solve(tight(api))
+    u = prob.get(api._lib.FO_FIELD_U)
+    u_ref, A, chi = op.state(phi)
+    K, F, free = op.stiffness(A), op.load(), op.dirichlet() == 0
+    # 1e-10 where the conditioning allows it; otherwise backward error at FP64 level and the
+    # forward difference inside the perturbation bound (<= 1e-8)
+    fwd, om, skeel = assert_solve_parity(K, F, free, u, u_ref, 1e-10, omega_max=1e-12)
+    if skeel * 1e-16 <= 1e-11:
+        assert rel(u, u_ref) <= 1e-10, (rel(u, u_ref), st.iterations)
+    J, C = prob.functionals()
+    J_ref = op.cost(u_ref, A)
+    assert abs(J - J_ref) <= max(1e-10, fwd) * abs(J_ref)
+    vol, _ = fem.geometry(op.mesh.coords, op.mesh.cells)
+    vol_ref = shape.volume(vol, chi)
+    C_ref = vol_ref / c["volume"] if c["volume"] > 0 else vol_ref
+    assert abs(C - C_ref) <= 1e-13 * abs(C_ref)
+
+
+@pytest.mark.parametrize("c", [case(**HEAT2D), cantilever2d((128, 64)), cantilever3d((12, 6, 6))])
+def test_state_solve_mixed(ctx, api, c):
+    mesh, prob = gpu_problem(ctx, c)
+    op = oracle_problem(c)
+    phi = (workloads.phi_cos(op.mesh.coords) if c["dim"] == 2 else
+           workloads.phi_bumps(op.mesh.coords, workloads.bump_centres(c["lo"], c["hi"], 8, 0), 0.25, 0.2))
+    prob.set_levelset(phi)
+    st = prob.state_solve(api.solve_opts(precision=api.FO_MIXED, rtol=1e-12, inner_rtol=1e-3))
+    u = prob.get(api._lib.FO_FIELD_U)
+    u_ref, A, _ = op.state(phi)
+    assert rel(u, u_ref) <= 1e-8, (rel(u, u_ref), st.iterations, st.outer_iterations)
+    assert_solve_parity(op.stiffness(A), op.load(), op.dirichlet() == 0, u, u_ref, 1e-8, omega_max=1e-12)
+    assert st.outer_iterations >= 2
+
+
+def test_adjoint_closed_forms(ctx, api):
+    for c, factor in ((case(**HEAT2D), -1.0), (cantilever2d((32, 16)), -2.0)):
+        mesh, prob = gpu_problem(ctx, c)
+        _, coords = mesh.copy_out()
+        prob.set_levelset(workloads.phi_cos(coords))
+        prob.state_solve(tight(api))
+        prob.adjoint_solve(tight(api))
+        u, p = prob.get(api._lib.FO_FIELD_U), prob.get(api._lib.FO_FIELD_P)
+        assert rel(p, factor * u) <= 1e-10
+
+
+# ---------------------------------------------------------------------- shape derivative
+@pytest.mark.parametrize("c,lam", [
+    (case(dim=2, n=(20, 14), kind=0, f=lambda X: 1 + 0.5 * X[:, 0] - X[:, 1] ** 2, volume=0.4), 0.7),
+    (case(dim=3, n=(6, 5, 4), kind=0, f=lambda X: np.ones(X.shape[0]), volume=0.3), -0.2),
+    (cantilever2d((24, 12)), 0.35),
+    (cantilever3d((8, 4, 4)), 1.1),
+])
+def test_shape_rhs(ctx, api, c, lam):
+    mesh, prob = gpu_problem(ctx, c)
+    op = oracle_problem(c)
+    phi = (workloads.phi_cos(op.mesh.coords) if c["dim"] == 2 else
+           workloads.phi_bumps(op.mesh.coords, workloads.bump_centres(c["lo"], c["hi"], 6, 5), 0.25, 0.3))
+    prob.set_levelset(phi)
+    prob.coefficients()
+    u = workloads.smooth_field(op.mesh.coords, op.ncomp, 17)
+    u[op.dirichlet() == 1] = 0.0
+    prob.set(api._lib.FO_FIELD_U, u)
+    b = prob.shape_derivative(lam)
+    A, chi = shape.coefficient(phi, op.mesh.cells, c["a_in"], c["a_out"])
+    ref = op.rhs(u, A, chi, lam)
+    assert close_scaled(b, ref, 1e-12)
+
+
+@pytest.mark.parametrize("c", [case(**HEAT2D), cantilever2d((128, 64)), cantilever3d((10, 5, 5))])
+def test_descent(ctx, api, c):
+    mesh, prob = gpu_problem(ctx, c)
+    op = oracle_problem(c)
+    prob.set_levelset(np.zeros(op.mesh.num_nodes) - 1.0)
+    prob.coefficients()
+    b = workloads.smooth_field(op.mesh.coords, c["dim"], 23)
+    prob.set(api._lib.FO_FIELD_RHS, b)
+    Btt, st = prob.descent(tight(api))
+    theta = prob.get(api._lib.FO_FIELD_THETA)
+    theta_ref, Btt_ref = ovel.solve(op.mesh, op.vform, b)
+    assert rel(theta, theta_ref) <= 1e-10, (rel(theta, theta_ref), st.iterations)
+    assert abs(Btt - Btt_ref) <= 1e-10 * abs(Btt_ref)
+
+
+# ----------------------------------------------------------------------------- transport
+@pytest.mark.parametrize("dim,n,smooth", [(2, (16, 12), False), (2, (16, 12), True), (3, (5, 4, 4), True)])
+def test_transport_matrices_and_steps(ctx, api, dim, n, smooth):
+    c = case(dim=dim, n=n, kind=0)
+    mesh, prob = gpu_problem(ctx, c)
+    op = oracle_problem(c)
+    m = op.mesh
+    theta = workloads.smooth_field(m.coords, dim, 31)
+    phi = workloads.phi_cos(m.coords) if dim == 2 else workloads.phi_bumps(m.coords, workloads.bump_centres((0,) * 3, (1,) * 3, 4, 3), 0.3, 0.5)
+    prob.set(api._lib.FO_FIELD_THETA, theta)
+    prob.set_levelset(phi)
+    h, t_end, ns = m.diameter(), 0.05, 9
+    dt = t_end / ns
+    prob.transport_assemble(dt, h, smooth)
+    L, R = levelset.transport_matrices(m, theta, dt, h, smooth)
+    x = workloads.random_field(m.num_nodes, 3)
+    assert close_scaled(prob.apply(api._lib.FO_OP_TRANSPORT_L, x), L @ x, 1e-12)
+    assert close_scaled(prob.apply(api._lib.FO_OP_TRANSPORT_R, x), R @ x, 1e-12)
+    prob.levelset_step(t_end, ns, h, smooth, tight(api))
+    out = prob.get(api._lib.FO_FIELD_PHI)
+    ref = levelset.transport(m, phi, theta, t_end, ns, h, smooth)
+    assert rel(out, ref) <= 1e-11
+
+
+@pytest.mark.parametrize("dim,n", [(2, (24, 24)), (3, (6, 6, 5))])
+def test_reinit(ctx, api, dim, n):
+    c = case(dim=dim, n=n, kind=0)
+    mesh, prob = gpu_problem(ctx, c)
+    m = oracle_problem(c).mesh
+    phi = 2.5 * levelset.initial_level(m.coords, [(0.5,) * dim, (0.2,) * dim], [0.25, 0.1])
+    prob.set_levelset(phi)
+    h = m.diameter()
+    prob.reinit(6, 0.05, h, tight(api))
+    out = prob.get(api._lib.FO_FIELD_PHI)
+    ref = levelset.reinit(m, phi, 6, 0.05, h)
+    assert rel(out, ref) <= 1e-10
+
+
+def test_initial_level(ctx, api):
+    c = cantilever2d((64, 32))
+    mesh, prob = gpu_problem(ctx, c)
+    m = oracle_problem(c).mesh
+    cen, rad = workloads.hole_lattice()
+    prob.initial_level(cen, rad, factor=1.0, ord=2)
+    assert close_scaled(prob.get(api._lib.FO_FIELD_PHI), levelset.initial_level(m.coords, cen, rad), 1e-15)
+    prob.initial_level(cen, rad, factor=-2.0, ord=np.inf)
+    assert close_scaled(prob.get(api._lib.FO_FIELD_PHI), levelset.initial_level(m.coords, cen, rad, -2.0, np.inf), 1e-15)
