@@ -260,7 +260,7 @@ static size_t prob_bytes_fields(const fo_problem *p, std::vector<std::pair<void 
       {(void **)&p->dinv_state, sizeof(double) * ND}, {(void **)&p->dinv_state32, sizeof(float) * ND},
       {(void **)&p->dinv_vel, sizeof(double) * d * NN}, {(void **)&p->L, sizeof(double) * S * NN},
       {(void **)&p->R, sizeof(double) * S * NN},     {(void **)&p->dinvL, sizeof(double) * NN},
-      {(void **)&p->red, sizeof(double) * FO_MAX_RED * 4096},
+      {(void **)&p->red, sizeof(double) * FO_RED_DOUBLES},
       {(void **)&p->bar, 64},                        {(void **)&p->dev_status, sizeof(int) * DS_COUNT},
   };
   if (p->f || p->desc.kind != FO_ELASTIC) list.push_back({(void **)&p->f, sizeof(double) * NN});

@@ -117,7 +117,7 @@ enum { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_NAN = 2, DEV_NOCONV = 3 };
 
 // ----------------------------------------------------------------------------- device side
 #define FO_BLOCK 256
-#define FO_MAX_RED 16          // reduction values per block
+#define FO_RED_DOUBLES (1 << 17)   // per-problem reduction buffer (partials + solver outputs)
 
 // Kuhn permutation pi_l of simplex p (lexicographic order of the axis permutations).
 template <int D>
@@ -225,22 +225,24 @@ __device__ __forceinline__ bool grid_sync(const GridBar &b) {
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned inc = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1)) : 1u;
-    __threadfence();
-    unsigned old = fo_atom_add_release(b.count, inc);
+    __threadfence();                               // this block's writes before the arrival
+    unsigned old = atomicAdd(b.count, inc);
+    volatile unsigned *cnt = b.count;
     int ok = 1;
     unsigned long long t0 = 0;
     unsigned spins = 0;
-    while (((old ^ fo_ld_acquire(b.count)) & 0x80000000u) == 0) {
-      if (++spins == 64) t0 = fo_globaltimer();
-      if (spins > 64) {
-        __nanosleep(40);
-        if ((spins & 255) == 0 && fo_globaltimer() - t0 > b.limit_ns) {
+    while (((old ^ *cnt) & 0x80000000u) == 0) {
+      if (++spins == 1024) t0 = fo_globaltimer();
+      if (spins > 1024 && (spins & 255) == 0) {
+        __nanosleep(64);
+        if (fo_globaltimer() - t0 > b.limit_ns) {
           atomicExch(b.err, DEV_TIMEOUT);
           ok = 0;
           break;
         }
       }
     }
+    __threadfence();                               // other blocks' writes after the release
     if (ok && *(volatile int *)b.err == DEV_TIMEOUT) ok = 0;
     s_ok = ok;
   }
@@ -321,5 +323,6 @@ fo_status fo_transport_run(fo_problem *p, int nsteps, const fo_solve_opts *o, fo
 fo_status fo_reinit_run(fo_problem *p, int nsteps, double dt, double h, const fo_solve_opts *o,
                         fo_solve_stats *st);
 fo_status fo_scratch(fo_problem *p, size_t bytes, void **out);
+int fo_persistent_block(const fo_problem *p, long long n);
 fo_status fo_cooperative_grid(fo_problem *p, const void *kernel, int block, size_t smem, long long work,
                               int requested, int *grid);

@@ -1,22 +1,27 @@
-// Persistent, cooperatively launched Jacobi-PCG for the state and velocity systems, and the
-// FP32-inner / FP64-refinement driver of the mixed path.
+// Persistent, cooperatively launched Jacobi-preconditioned conjugate gradients for the
+// state and velocity systems, and the FP32-inner / FP64-refinement driver of the mixed path.
 //
-// One launch runs the whole solve.  Per iteration there are two grid barriers:
-//   phase A  p_new = z + beta p_old for the owned nodes, q = A (z + beta p_old) with the
-//            combination formed inside the operator's gather (so no barrier is needed
-//            between the p update and the apply), partial p.q;
-//   phase B  x += alpha p, r -= alpha q, z = D^{-1} r, partials r.z and r.r.
-// p is double-buffered so that phase A never overwrites a value another block still reads.
-// All dot products are accumulated in FP64 with a fixed reduction order: block partials,
-// then every block sums the partials in the same order, so every block takes the same
-// branch and the result does not depend on timing.
+// The recurrence is the single-reduction form of PCG due to Chronopoulos and Gear:
+//   p_i = u_i + b_i p_{i-1},  s_i = w_i + b_i s_{i-1}          (s_i = A p_i)
+//   x_{i+1} = x_i + a_i p_i,  r_{i+1} = r_i - a_i s_i,  u_{i+1} = D^{-1} r_{i+1},  w_{i+1} = A u_{i+1}
+//   g_{i+1} = (r_{i+1}, u_{i+1}),  d_{i+1} = (w_{i+1}, u_{i+1}),
+//   b_{i+1} = g_{i+1} / g_i,  a_{i+1} = g_{i+1} / (d_{i+1} - b_{i+1} g_{i+1} / a_i).
+// Its three dot products are reduced together, so an iteration needs one grid barrier:
+// the apply w_{i+1} = A u_{i+1} gathers u_{i+1} at the stencil neighbours and forms it
+// there from the previous iteration's r_i, w_i and s_{i-1},
+//   u_{i+1}[nb] = D^{-1}[nb] (r_i[nb] - a_i (w_i[nb] + b_i s_{i-1}[nb])),
+// which are final once the previous barrier has passed.  r, w and s are double-buffered
+// so that a phase never overwrites a value another block may still gather.
+// All dot products are accumulated in FP64 with a fixed reduction order (block partials,
+// then every block sums all partials in the same order): every block takes the same
+// branch, and the result does not depend on timing.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 
 #include "fo_internal.cuh"
 #include "fo_ops.cuh"
-
 
 // ----------------------------------------------------------------------------- scratch
 fo_status fo_scratch(fo_problem *p, size_t bytes, void **out) {
@@ -31,6 +36,8 @@ fo_status fo_scratch(fo_problem *p, size_t bytes, void **out) {
   return FO_OK;
 }
 
+// Grid of a persistent kernel: enough blocks to cover `work` items (one per thread), at
+// most what fits co-resident on the device.
 fo_status fo_cooperative_grid(fo_problem *p, const void *kernel, int block, size_t smem, long long work,
                               int requested, int *grid) {
   int per_sm = 0;
@@ -45,17 +52,28 @@ fo_status fo_cooperative_grid(fo_problem *p, const void *kernel, int block, size
   return FO_OK;
 }
 
+// Threads per block for a persistent kernel over n nodes: 256, or fewer (>= 64) so that a
+// small problem still spreads over every SM (the FP64 work is ALU-bound per SM).
+int fo_persistent_block(const fo_problem *p, long long n) {
+  const long long sms = p->ctx->num_sms > 0 ? p->ctx->num_sms : 1;
+  long long per = (n + sms - 1) / sms;
+  int b = 64;
+  while (b < 256 && b < per) b *= 2;
+  return b;
+}
+
 // ------------------------------------------------------------------------------ kernel
 template <int NC, typename T>
 struct PcgArgs {
-  T *x, *r, *z, *p0, *p1, *q;
+  T *x, *u, *p;          // single buffers (own nodes only)
+  T *r[2], *s[2], *w[2]; // double buffers (gathered at neighbours)
   const double *b;       // right-hand side (FP64), scaled by bscale
   const T *bT;           // right-hand side in T when non-null (inner solves)
   const uint8_t *bmask;  // per node: nonzero rows get a zero right-hand side (H^1_0 rows)
   double bscale;
   const T *dinv;
   double *partials;      // [2][G][3 NC]: two buffers used alternately
-  double *out;           // [4 NC]: rr, bb, b.x, pad
+  double *out;           // [4 NC]: rr, bb, b.x
   int *status;           // DS_* words
   GridBar bar;
   double rtol2;
@@ -81,6 +99,17 @@ __device__ __forceinline__ bool reduce_grid(double (&v)[NR], double *sred, doubl
   return true;
 }
 
+// u_{i+1} at any DOF, formed from the previous iteration's r, w, s (see the file comment)
+template <typename T, int NC>
+struct NextU {
+  const T *r, *w, *s, *dinv;
+  T a[NC], b[NC];
+  __device__ __forceinline__ T operator()(long long k) const {
+    const int c = (NC == 1) ? 0 : (int)(k % NC);
+    return dinv[k] * (r[k] - a[c] * (w[k] + b[c] * s[k]));
+  }
+};
+
 template <int D, class Op, typename T, int NC>
 __global__ void __launch_bounds__(FO_BLOCK) k_pcg(Op op, PcgArgs<NC, T> S) {
   constexpr int NPN = Op::NPN;
@@ -91,8 +120,9 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg(Op op, PcgArgs<NC, T> S) {
   const long long N = g.num_nodes;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long gstride = (long long)gridDim.x * blockDim.x;
+  int rk = 0;
 
-  // ---- phase 0: r = b - A x0, z = D^{-1} r, p_old = 0
+  // ---- start 1: r_0 = b - A x_0, u_0 = D^{-1} r_0, s_{-1} = 0; ||b||^2
   double v[NR];
 #pragma unroll
   for (int j = 0; j < NR; ++j) v[j] = 0.0;
@@ -107,105 +137,117 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg(Op op, PcgArgs<NC, T> S) {
       const int sy = (NC == 1) ? 0 : c;
       const double bk = (S.bmask && S.bmask[a]) ? 0.0 : (S.bT ? (double)S.bT[k] : S.bscale * S.b[k]);
       if (!S.warm) { ax[c] = T(0); S.x[k] = T(0); }
-      const T rk = (T)(bk - (double)ax[c]);
-      const T zk = S.dinv[k] * rk;
-      S.r[k] = rk;
-      S.z[k] = zk;
-      S.p0[k] = T(0);
-      v[sy * 3 + 0] += (double)rk * (double)zk;
-      v[sy * 3 + 1] += (double)rk * (double)rk;
-      v[sy * 3 + 2] += bk * bk;
+      const T rk0 = (T)(bk - (double)ax[c]);
+      S.r[0][k] = rk0;
+      S.u[k] = S.dinv[k] * rk0;
+      S.s[1][k] = T(0);
+      S.p[k] = T(0);
+      v[sy * 3 + 0] += (double)rk0 * (double)rk0;
+      v[sy * 3 + 1] += bk * bk;
     }
   }
-  int rk = 0;
   if (!reduce_grid<NR>(v, sred, stot, S.partials, rk, S.bar)) return;
-  double rz[NC], rr[NC], bb[NC], beta[NC], alpha[NC];
+  double rr[NC], bb[NC], gam[NC], alpha[NC], beta[NC];
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
-    rz[s] = stot[s * 3 + 0];
-    rr[s] = stot[s * 3 + 1];
-    bb[s] = stot[s * 3 + 2];
+    rr[s] = stot[s * 3 + 0];
+    bb[s] = stot[s * 3 + 1];
+  }
+  // ---- start 2: w_0 = A u_0, g_0 = (r_0, u_0), d_0 = (w_0, u_0)
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NR; ++j) v[j] = 0.0;
+  for (long long a = tid; a < N; a += gstride) {
+    int idx[3];
+    node_ijk(g, a, idx);
+    T wa[NPN];
+    op.row(a, idx, VecX<T>{S.u}, wa);
+#pragma unroll
+    for (int c = 0; c < NPN; ++c) {
+      const long long k = a * NPN + c;
+      const int sy = (NC == 1) ? 0 : c;
+      S.w[0][k] = wa[c];
+      const double uk = (double)S.u[k];
+      v[sy * 3 + 0] += (double)S.r[0][k] * uk;
+      v[sy * 3 + 1] += (double)wa[c] * uk;
+    }
+  }
+  if (!reduce_grid<NR>(v, sred, stot, S.partials, rk, S.bar)) return;
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    gam[s] = stot[s * 3 + 0];
+    const double del = stot[s * 3 + 1];
+    alpha[s] = (del != 0.0) ? gam[s] / del : 0.0;
     beta[s] = 0.0;
   }
-  T *pold = S.p0, *pnew = S.p1;
+
   int it = 0, err = DEV_OK;
   for (;;) {
     bool any = false;
 #pragma unroll
     for (int s = 0; s < NC; ++s) {
-      if (!(rr[s] == rr[s]) || !(rz[s] == rz[s])) err = DEV_NAN;
+      if (!(rr[s] == rr[s]) || !(alpha[s] == alpha[s])) err = DEV_NAN;
       if (rr[s] > S.rtol2 * bb[s]) any = true;
     }
     if (err != DEV_OK || !any) break;
     if (it >= S.maxit) { err = DEV_NOCONV; break; }
-    bool active[NC];
+    // converged systems keep x: their step length is zero from here on
 #pragma unroll
-    for (int s = 0; s < NC; ++s) active[s] = rr[s] > S.rtol2 * bb[s];
-    // ---- phase A
-    __syncthreads();   // stot is rewritten below
-    double w[NC];
-#pragma unroll
-    for (int s = 0; s < NC; ++s) w[s] = 0.0;
-    CombX<T, NC> cx;
-    cx.z = S.z;
-    cx.p = pold;
-#pragma unroll
-    for (int s = 0; s < NC; ++s) cx.beta[s] = (T)beta[s];
-    for (long long a = tid; a < N; a += gstride) {
-      int idx[3];
-      node_ijk(g, a, idx);
-      T qa[NPN];
-      op.row(a, idx, cx, qa);
-#pragma unroll
-      for (int c = 0; c < NPN; ++c) {
-        const long long k = a * NPN + c;
-        const int sy = (NC == 1) ? 0 : c;
-        const T pk = S.z[k] + cx.beta[sy] * pold[k];
-        pnew[k] = pk;
-        S.q[k] = qa[c];
-        w[sy] += (double)pk * (double)qa[c];
-      }
-    }
-    {
-      double tmp[NR];
-#pragma unroll
-      for (int j = 0; j < NR; ++j) tmp[j] = (j % 3 == 0) ? w[j / 3] : 0.0;
-      if (!reduce_grid<NR>(tmp, sred, stot, S.partials, rk, S.bar)) return;
-    }
+    for (int s = 0; s < NC; ++s)
+      if (!(rr[s] > S.rtol2 * bb[s])) alpha[s] = 0.0, beta[s] = 0.0;
+    const int cur = it & 1, nxt = cur ^ 1;
+    T *rc = S.r[cur], *rn = S.r[nxt], *wc = S.w[cur], *wn = S.w[nxt], *sp = S.s[nxt], *sc = S.s[cur];
+    NextU<T, NC> nu;
+    nu.r = rc;
+    nu.w = wc;
+    nu.s = sp;
+    nu.dinv = S.dinv;
 #pragma unroll
     for (int s = 0; s < NC; ++s) {
-      const double pq = stot[s * 3];
-      alpha[s] = (active[s] && pq != 0.0) ? rz[s] / pq : 0.0;
+      nu.a[s] = (T)alpha[s];
+      nu.b[s] = (T)beta[s];
     }
-    // ---- phase B
+    __syncthreads();   // stot is rewritten by the reduction below
 #pragma unroll
     for (int j = 0; j < NR; ++j) v[j] = 0.0;
     for (long long a = tid; a < N; a += gstride) {
+      int idx[3];
+      node_ijk(g, a, idx);
+      T wa[NPN];
+      op.row(a, idx, nu, wa);   // w_{i+1} = A u_{i+1}
 #pragma unroll
       for (int c = 0; c < NPN; ++c) {
         const long long k = a * NPN + c;
         const int sy = (NC == 1) ? 0 : c;
-        const T al = (T)alpha[sy];
-        S.x[k] += al * pnew[k];
-        const T rk = S.r[k] - al * S.q[k];
-        const T zk = S.dinv[k] * rk;
-        S.r[k] = rk;
-        S.z[k] = zk;
-        v[sy * 3 + 0] += (double)rk * (double)zk;
-        v[sy * 3 + 1] += (double)rk * (double)rk;
+        const T al = nu.a[sy], be = nu.b[sy];
+        const T pk = S.u[k] + be * S.p[k];
+        const T sk = wc[k] + be * sp[k];
+        S.p[k] = pk;
+        sc[k] = sk;
+        S.x[k] += al * pk;
+        const T rk1 = rc[k] - al * sk;
+        const T uk1 = S.dinv[k] * rk1;
+        rn[k] = rk1;
+        S.u[k] = uk1;
+        wn[k] = wa[c];
+        v[sy * 3 + 0] += (double)rk1 * (double)uk1;
+        v[sy * 3 + 1] += (double)wa[c] * (double)uk1;
+        v[sy * 3 + 2] += (double)rk1 * (double)rk1;
       }
     }
     if (!reduce_grid<NR>(v, sred, stot, S.partials, rk, S.bar)) return;
 #pragma unroll
     for (int s = 0; s < NC; ++s) {
-      const double rzn = stot[s * 3 + 0];
-      rr[s] = stot[s * 3 + 1];
-      beta[s] = (active[s] && rz[s] != 0.0) ? rzn / rz[s] : 0.0;
-      if (active[s]) rz[s] = rzn;
+      const double gn = stot[s * 3 + 0], del = stot[s * 3 + 1];
+      rr[s] = stot[s * 3 + 2];
+      if (alpha[s] != 0.0) {
+        const double bn = (gam[s] != 0.0) ? gn / gam[s] : 0.0;
+        const double den = del - bn * gn / alpha[s];
+        beta[s] = bn;
+        alpha[s] = (den != 0.0) ? gn / den : 0.0;
+        gam[s] = gn;
+      }
     }
-    T *t = pold;
-    pold = pnew;
-    pnew = t;
     ++it;
   }
   // ---- b . x per system (B(theta, theta) = -b . theta for the velocity)
@@ -235,11 +277,11 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg(Op op, PcgArgs<NC, T> S) {
 
 // ------------------------------------------------------------------------- host driver
 template <class K, class... Args>
-static fo_status coop_launch(fo_problem *p, K kernel, int grid, Args... args) {
+static fo_status coop_launch(fo_problem *p, K kernel, int grid, int block, Args... args) {
   void *argv[] = {(void *)&args...};
   FO_CU(p->ctx, cudaMemsetAsync(p->bar, 0, 64, p->ctx->stream));
   FO_CU(p->ctx, cudaMemsetAsync(p->dev_status, 0, sizeof(int) * DS_COUNT, p->ctx->stream));
-  FO_CU(p->ctx, cudaLaunchCooperativeKernel((const void *)kernel, grid, FO_BLOCK, argv, 0, p->ctx->stream));
+  FO_CU(p->ctx, cudaLaunchCooperativeKernel((const void *)kernel, grid, block, argv, 0, p->ctx->stream));
   fo_note_launch(1);
   return FO_OK;
 }
@@ -248,6 +290,8 @@ struct SolveOut {
   int status[DS_COUNT];
   double out[16];
 };
+
+static double *out_area(fo_problem *p) { return p->red + FO_RED_DOUBLES - 64; }
 
 static fo_status read_out(fo_problem *p, double *out_dev, SolveOut *o, int nout) {
   fo_ctx *ctx = p->ctx;
@@ -260,18 +304,31 @@ static fo_status read_out(fo_problem *p, double *out_dev, SolveOut *o, int nout)
   return FO_OK;
 }
 
-static double *out_area(fo_problem *p) { return p->red + FO_MAX_RED * 4096 - 64; }
+// 9 vectors of n entries of T: x is external; u, p, r[2], s[2], w[2] come from `buf`
+template <int NC, typename T>
+static void bind_vectors(PcgArgs<NC, T> &a, T *x, T *buf, long long n) {
+  a.x = x;
+  a.u = buf;
+  a.p = buf + n;
+  a.r[0] = buf + 2 * n;
+  a.r[1] = buf + 3 * n;
+  a.s[0] = buf + 4 * n;
+  a.s[1] = buf + 5 * n;
+  a.w[0] = buf + 6 * n;
+  a.w[1] = buf + 7 * n;
+}
 
 template <int D, class Op, typename T, int NC>
 static fo_status run_pcg(fo_problem *p, const Op &op, PcgArgs<NC, T> a, long long nodes, int requested, SolveOut *o) {
   auto kern = k_pcg<D, Op, T, NC>;
+  const int block = fo_persistent_block(p, nodes);
   int grid;
-  FO_TRY(fo_cooperative_grid(p, (const void *)kern, FO_BLOCK, 0, nodes, requested, &grid));
+  FO_TRY(fo_cooperative_grid(p, (const void *)kern, block, 0, nodes, requested, &grid));
   a.partials = p->red;
   a.out = out_area(p);
   a.status = p->dev_status;
   a.bar = GridBar{p->bar, p->dev_status + DS_ERR, 2000000000ull};
-  FO_TRY(coop_launch(p, kern, grid, op, a));
+  FO_TRY(coop_launch(p, kern, grid, block, op, a));
   FO_CU(p->ctx, cudaGetLastError());
   FO_TRY(read_out(p, out_area(p), o, 4 * NC));
   if (o->status[DS_ERR] == DEV_TIMEOUT) return fo_fail(p->ctx, FO_ETIMEOUT, "grid barrier timed out in PCG");
@@ -303,13 +360,9 @@ __global__ void k_finish_sum2(const double *partials, int nblocks, double *out) 
   for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
   if (lane == 0) out[w] = t;
 }
-__global__ void k_to_float(const double *x, float *y, long long n) {
+__global__ void k_axpy(double *x, const double *d, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = (float)x[i];
-}
-__global__ void k_add_float(double *x, const float *d, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    x[i] += (double)d[i];
+    x[i] += d[i];
 }
 
 template <int D, class Op64, class Op32>
@@ -321,14 +374,9 @@ static fo_status state_solve_impl(fo_problem *p, const Op64 &op64, const Op32 &o
   memset(&s, 0, sizeof s);
   if (o->precision == FO_FP64) {
     double *buf;
-    FO_TRY(fo_scratch(p, sizeof(double) * 5 * n, (void **)&buf));
+    FO_TRY(fo_scratch(p, sizeof(double) * 8 * n, (void **)&buf));
     PcgArgs<1, double> a{};
-    a.x = x;
-    a.r = buf;
-    a.z = buf + n;
-    a.p0 = buf + 2 * n;
-    a.p1 = buf + 3 * n;
-    a.q = buf + 4 * n;
+    bind_vectors(a, x, buf, n);
     a.b = b;
     a.bscale = 1.0;
     a.dinv = p->dinv_state;
@@ -338,20 +386,20 @@ static fo_status state_solve_impl(fo_problem *p, const Op64 &op64, const Op32 &o
     SolveOut out;
     FO_TRY(run_pcg<D>(p, op64, a, g.num_nodes, o->grid_blocks, &out));
     s.iterations = out.status[DS_ITERS];
-    s.operator_applies = s.iterations + (o->warm_start ? 1 : 0);
+    s.operator_applies = s.iterations + 1 + (o->warm_start ? 1 : 0);
     s.outer_iterations = 1;
     s.rel_residual = out.out[1] > 0 ? std::sqrt(out.out[0] / out.out[1]) : 0.0;
     if (st) *st = s;
     if (out.status[DS_ERR] == DEV_NOCONV) return fo_fail(p->ctx, FO_ENOCONV, "PCG reached maxit=%d", o->maxit);
     return FO_OK;
   }
-  // ---- mixed: FP32 inner PCG (FP64 dots) inside FP64 iterative refinement
-  char *buf;
-  const size_t bytes = sizeof(double) * 2 * n + sizeof(float) * 7 * n;
-  FO_TRY(fo_scratch(p, bytes, (void **)&buf));
-  double *r64 = (double *)buf, *ax64 = r64 + n;
-  float *f = (float *)(ax64 + n);
-  float *d32 = f, *r32 = f + n, *z32 = f + 2 * n, *p0 = f + 3 * n, *p1 = f + 4 * n, *q32 = f + 5 * n, *b32 = f + 6 * n;
+  // ---- mixed: FP64 iterative refinement around an inner PCG whose operator applies run in
+  // FP32 (FP32 element data and accumulation); the inner recurrence, its dot products and
+  // the refinement residual stay in FP64.
+  double *buf;
+  FO_TRY(fo_scratch(p, sizeof(double) * 11 * n, (void **)&buf));
+  double *r64 = buf, *ax64 = buf + n, *d64 = buf + 2 * n, *vec64 = buf + 3 * n;
+  const Fp32ApplyOp<Op32> op_mixed{op32, op32.g};
   fo_ctx *ctx = p->ctx;
   const int blocks = fo_blocks_for(n, FO_BLOCK, 1024);
   if (!o->warm_start) FO_CU(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream));
@@ -387,28 +435,20 @@ static fo_status state_solve_impl(fo_problem *p, const Op64 &op64, const Op32 &o
       if (st) *st = s;
       return fo_fail(ctx, FO_ENOCONV, "iterative refinement stalled at %.3e", s.rel_residual);
     }
-    k_to_float<<<blocks, FO_BLOCK, 0, ctx->stream>>>(r64, b32, n);
-    fo_note_launch(1);
-    PcgArgs<1, float> a{};
-    a.x = d32;
-    a.r = r32;
-    a.z = z32;
-    a.p0 = p0;
-    a.p1 = p1;
-    a.q = q32;
-    a.b = nullptr;
-    a.bT = b32;
+    PcgArgs<1, double> a{};
+    bind_vectors(a, d64, vec64, n);
+    a.b = r64;
     a.bscale = 1.0;
-    a.dinv = p->dinv_state32;
+    a.dinv = p->dinv_state;
     a.rtol2 = o->inner_rtol * o->inner_rtol;
     a.maxit = o->inner_maxit;
     a.warm = 0;
     SolveOut out;
-    FO_TRY(run_pcg<D>(p, op32, a, g.num_nodes, o->grid_blocks, &out));
+    FO_TRY(run_pcg<D>(p, op_mixed, a, g.num_nodes, o->grid_blocks, &out));
     s.iterations += out.status[DS_ITERS];
-    s.operator_applies += out.status[DS_ITERS];
+    s.operator_applies += out.status[DS_ITERS] + 1;
     s.outer_iterations = outer + 1;
-    k_add_float<<<blocks, FO_BLOCK, 0, ctx->stream>>>(x, d32, n);
+    k_axpy<<<blocks, FO_BLOCK, 0, ctx->stream>>>(x, d64, n);
     fo_note_launch(1);
     FO_CU(ctx, cudaGetLastError());
   }
@@ -432,14 +472,9 @@ static fo_status velocity_impl(fo_problem *p, const fo_solve_opts *o, double *Bt
   const Grid &g = p->mesh->g;
   const long long n = (long long)D * g.num_nodes;
   double *buf;
-  FO_TRY(fo_scratch(p, sizeof(double) * 5 * n, (void **)&buf));
+  FO_TRY(fo_scratch(p, sizeof(double) * 8 * n, (void **)&buf));
   PcgArgs<D, double> a{};
-  a.x = p->theta;
-  a.r = buf;
-  a.z = buf + n;
-  a.p0 = buf + 2 * n;
-  a.p1 = buf + 3 * n;
-  a.q = buf + 4 * n;
+  bind_vectors(a, p->theta, buf, n);
   a.b = p->rhs;
   a.bscale = -1.0;                // B theta = -b
   a.bmask = p->desc.velocity_dirichlet ? p->vdir : nullptr;
@@ -458,7 +493,7 @@ static fo_status velocity_impl(fo_problem *p, const fo_solve_opts *o, double *Bt
   if (Btt) *Btt = bx;           // B(theta, theta) = -b . theta
   if (st) {
     st->iterations = out.status[DS_ITERS];
-    st->operator_applies = out.status[DS_ITERS] + (o->warm_start ? 1 : 0);
+    st->operator_applies = out.status[DS_ITERS] + 1 + (o->warm_start ? 1 : 0);
     st->outer_iterations = 1;
     st->rel_residual = bb > 0 ? std::sqrt(rr / bb) : 0.0;
   }

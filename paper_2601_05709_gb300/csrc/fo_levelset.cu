@@ -4,7 +4,7 @@
 // they are assembled (node-centrically, deterministic) into stencil form: for every node the
 // 7 (2D) / 15 (3D) couplings to its Kuhn neighbours, stored slot-major [S][N_n] so that a
 // warp reads consecutive nodes of one slot.  The nonsymmetric systems are solved by a
-// persistent, cooperatively launched Jacobi-BiCGStab; one launch runs every substep.
+// persistent, cooperatively launched restarted GMRES; one launch runs every substep.
 //
 // Quadrature: degree-2 rule (2D: barycentrics (2/3, 1/6, 1/6) and permutations, weights
 // |e|/3; 3D: (a, b, b, b), a = (5 + 3 sqrt 5)/20, b = (5 - sqrt 5)/20, weights |e|/4).
@@ -188,128 +188,216 @@ fo_status fo_launch_stencil_apply(fo_problem *p, const double *S, const double *
   return FO_OK;
 }
 
-// ------------------------------------------------------------------- persistent BiCGStab
-struct BcgBufs {
-  double *x, *rhs, *r, *rhat, *p0, *p1, *v0, *v1, *s, *t;
-  const double *M;       // stencil matrix [S][N]
-  const double *dinv;    // [N]
+// --------------------------------------------------------------------- persistent GMRES
+// Restarted GMRES(GM_M) with right Jacobi preconditioning on a stencil matrix.  The
+// Petrov-Galerkin matrices of the transport and, above all, of the reinitialisation are far
+// from normal (the streamline term is about half the size of the mass term), where
+// BiCGStab breaks down; GMRES minimises the residual and cannot.  Arnoldi uses classical
+// Gram-Schmidt with one reorthogonalisation pass (CGS2), each pass one fused grid
+// reduction; the Hessenberg matrix, Givens rotations and the small triangular solve live in
+// shared memory and are computed identically by every block from the same reduction totals.
+#define GM_M 24
+#define GM_NR (GM_M + 2)
+
+struct KrylovBufs {
+  double *V;             // (GM_M + 1) basis vectors [GM_M + 1][N]
+  double *w;             // [N]
+  double *rhs;           // [N]
 };
 
 template <int NR>
-__device__ __forceinline__ bool bcg_reduce(double (&v)[NR], double *sred, double *stot, double *partials, int &rk,
-                                           const GridBar &bar) {
+__device__ __forceinline__ bool ls_reduce(double (&v)[NR], double *sred, double *stot, double *partials, int &rk,
+                                          const GridBar &bar) {
   block_sum<NR>(v, sred);
-  double *part = partials + (size_t)(rk & 1) * gridDim.x * 4;
+  double *part = partials + (size_t)(rk & 1) * gridDim.x * NR;
   if (threadIdx.x == 0)
 #pragma unroll
-    for (int j = 0; j < NR; ++j) part[(size_t)blockIdx.x * 4 + j] = v[j];
+    for (int j = 0; j < NR; ++j) part[(size_t)blockIdx.x * NR + j] = v[j];
   if (!grid_sync(bar)) return false;
-  // fixed-order total of the first NR of the 4 slots
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (warp == 0) {
-#pragma unroll
-    for (int j = 0; j < NR; ++j) {
-      double t = 0.0;
-      for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(part + (size_t)b * 4 + j);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-      if (lane == 0) stot[j] = t;
-    }
-  }
-  __syncthreads();
+  grid_total<NR>(part, stot);
   ++rk;
   return true;
 }
 
-// BiCGStab (right Jacobi preconditioning) on M x = rhs, x holding the start value and r,
-// rhat holding rhs - M x (set by the caller's phase, followed by a reduction giving
-// rr = r.r, bb = rhs.rhs, rho = rhat.r).  Three grid reductions per iteration; the search
-// direction and s = r - alpha v are formed inside the gathers of the two applies.
+struct GmresShared {
+  double sred[32 * GM_NR];
+  double stot[GM_NR];
+  double H[(GM_M + 1) * GM_M];   // column-major: H[j * (GM_M + 1) + i]
+  double cs[GM_M], sn[GM_M], g[GM_M + 1], y[GM_M];
+};
+
+// Solve M x = rhs (x holds the start value).  When Rm is given, the first residual pass
+// also forms rhs = Rm x (the transport's right-hand side R phi^n, gathered from the same
+// x before it changes).  Returns the number of Arnoldi steps; err / ok report failures.
 template <int D>
-__device__ int bicgstab_loop(const Grid &g, BcgBufs B, double rr, double bb, double rho_new, double rtol2, int maxit,
-                             double *sred, double *stot, double *partials, int &rk, const GridBar &bar, int *err,
-                             bool *ok) {
+__device__ int gmres_solve(const Grid &g, const double *M, const double *dinv, const double *Rm, double *x,
+                           KrylovBufs K, double rtol2, int maxit, GmresShared &sh, double *partials, int &rk,
+                           const GridBar &bar, int *err, bool *ok) {
   const long long N = g.num_nodes;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long gs = (long long)gridDim.x * blockDim.x;
-  double rho = 1.0, alpha = 1.0, omega = 1.0;
-  double *pold = B.p0, *pnew = B.p1, *vold = B.v0, *vnew = B.v1;
-  // v_old = p_old = 0 is ensured by the caller
-  int it = 0;
+  int total = 0;
+  double bb = -1.0;
   *ok = true;
-  while (rr > rtol2 * bb) {
-    if (it >= maxit) { *err = DEV_NOCONV; break; }
-    if (!(rr == rr)) { *err = DEV_NAN; break; }
-    const double beta = (rho_new / rho) * (alpha / omega);
-    // phase 1: p = r + beta (p_old - omega v_old); v = M D^{-1} p
-    double w1[1] = {0.0};
+  for (int cycle = 0;; ++cycle) {
+    // ---- true residual r = rhs - M x into V_0 (and rhs = Rm x on the first cycle)
+    double v2[2] = {0.0, 0.0};
     for (long long a = tid; a < N; a += gs) {
       int idx[3];
       node_ijk(g, a, idx);
-      double acc = 0;
+      double ra;
+      if (cycle == 0 && Rm) {
+        ra = 0.0;
+        double la = 0.0;
 #pragma unroll
-      for (int s = 0; s < ST<D>::S; ++s) {
-        const long long nb = slot_node<D>(g, idx, a, s);
-        if (nb >= 0) {
-          const double pn = B.r[nb] + beta * (pold[nb] - omega * vold[nb]);
-          acc += B.M[s * N + a] * (B.dinv[nb] * pn);
+        for (int s = 0; s < ST<D>::S; ++s) {
+          const long long nb = slot_node<D>(g, idx, a, s);
+          if (nb >= 0) {
+            const double xv = x[nb];
+            ra += Rm[s * N + a] * xv;
+            la += M[s * N + a] * xv;
+          }
         }
+        K.rhs[a] = ra;
+        ra = ra - la;
+      } else {
+        double la = 0.0;
+#pragma unroll
+        for (int s = 0; s < ST<D>::S; ++s) {
+          const long long nb = slot_node<D>(g, idx, a, s);
+          if (nb >= 0) la += M[s * N + a] * x[nb];
+        }
+        ra = K.rhs[a] - la;
       }
-      pnew[a] = B.r[a] + beta * (pold[a] - omega * vold[a]);
-      vnew[a] = acc;
-      w1[0] += B.rhat[a] * acc;
+      K.V[a] = ra;
+      v2[0] += ra * ra;
+      if (cycle == 0) v2[1] += K.rhs[a] * K.rhs[a];
+    }
+    if (!ls_reduce<2>(v2, sh.sred, sh.stot, partials, rk, bar)) { *ok = false; return total; }
+    const double rr = sh.stot[0];
+    if (cycle == 0) bb = sh.stot[1];
+    if (!(rr == rr)) { *err = DEV_NAN; return total; }
+    if (rr <= rtol2 * bb) return total;
+    if (total >= maxit) { *err = DEV_NOCONV; return total; }
+    const double beta = sqrt(rr);
+    for (long long a = tid; a < N; a += gs) K.V[a] /= beta;
+    if (threadIdx.x == 0) {
+      sh.g[0] = beta;
+      for (int i = 1; i <= GM_M; ++i) sh.g[i] = 0.0;
+    }
+    if (!grid_sync(bar)) { *ok = false; return total; }
+    int j = 0;
+    bool done = false;
+    for (; j < GM_M; ++j) {
+      const double *Vj = K.V + (size_t)j * N;
+      // ---- w = M D^{-1} v_j and h_i = v_i . w (first Gram-Schmidt pass)
+      double h1[GM_NR];
+#pragma unroll
+      for (int i = 0; i < GM_NR; ++i) h1[i] = 0.0;
+      for (long long a = tid; a < N; a += gs) {
+        int idx[3];
+        node_ijk(g, a, idx);
+        double wa = 0.0;
+#pragma unroll
+        for (int s = 0; s < ST<D>::S; ++s) {
+          const long long nb = slot_node<D>(g, idx, a, s);
+          if (nb >= 0) wa += M[s * N + a] * (dinv[nb] * Vj[nb]);
+        }
+        K.w[a] = wa;
+#pragma unroll
+        for (int i = 0; i < GM_M; ++i)
+          if (i <= j) h1[i] += K.V[(size_t)i * N + a] * wa;
+      }
+      if (!ls_reduce<GM_NR>(h1, sh.sred, sh.stot, partials, rk, bar)) { *ok = false; return total; }
+      double hc[GM_M];
+#pragma unroll
+      for (int i = 0; i < GM_M; ++i) hc[i] = (i <= j) ? sh.stot[i] : 0.0;
+      // ---- w -= V h; second pass h2 = V^T w and |w|^2
+      double h2[GM_NR];
+#pragma unroll
+      for (int i = 0; i < GM_NR; ++i) h2[i] = 0.0;
+      for (long long a = tid; a < N; a += gs) {
+        double wa = K.w[a];
+#pragma unroll
+        for (int i = 0; i < GM_M; ++i)
+          if (i <= j) wa -= hc[i] * K.V[(size_t)i * N + a];
+        K.w[a] = wa;
+#pragma unroll
+        for (int i = 0; i < GM_M; ++i)
+          if (i <= j) h2[i] += K.V[(size_t)i * N + a] * wa;
+        h2[GM_M] += wa * wa;
+      }
+      if (!ls_reduce<GM_NR>(h2, sh.sred, sh.stot, partials, rk, bar)) { *ok = false; return total; }
+      double hn2 = sh.stot[GM_M];
+      double h2c[GM_M];
+#pragma unroll
+      for (int i = 0; i < GM_M; ++i) {
+        h2c[i] = (i <= j) ? sh.stot[i] : 0.0;
+        hc[i] += h2c[i];
+        hn2 -= h2c[i] * h2c[i];
+      }
+      const double hnext = sqrt(fmax(hn2, 0.0));
+      // ---- v_{j+1} = (w - V h2) / hnext
+      double *Vn = K.V + (size_t)(j + 1) * N;
+      const double inv = hnext > 0.0 ? 1.0 / hnext : 0.0;
+      for (long long a = tid; a < N; a += gs) {
+        double wa = K.w[a];
+#pragma unroll
+        for (int i = 0; i < GM_M; ++i)
+          if (i <= j) wa -= h2c[i] * K.V[(size_t)i * N + a];
+        Vn[a] = wa * inv;
+      }
+      // ---- Hessenberg column, Givens rotations, residual estimate (same in every block)
+      if (threadIdx.x == 0) {
+        double col[GM_M + 1];
+        for (int i = 0; i <= j; ++i) col[i] = hc[i];
+        col[j + 1] = hnext;
+        for (int i = 0; i < j; ++i) {
+          const double t = sh.cs[i] * col[i] + sh.sn[i] * col[i + 1];
+          col[i + 1] = -sh.sn[i] * col[i] + sh.cs[i] * col[i + 1];
+          col[i] = t;
+        }
+        const double rnorm = hypot(col[j], col[j + 1]);
+        const double c = rnorm > 0.0 ? col[j] / rnorm : 1.0, s = rnorm > 0.0 ? col[j + 1] / rnorm : 0.0;
+        sh.cs[j] = c;
+        sh.sn[j] = s;
+        col[j] = rnorm;
+        col[j + 1] = 0.0;
+        sh.g[j + 1] = -s * sh.g[j];
+        sh.g[j] = c * sh.g[j];
+        for (int i = 0; i <= j; ++i) sh.H[j * (GM_M + 1) + i] = col[i];
+      }
+      __syncthreads();
+      ++total;
+      const double est = sh.g[j + 1] * sh.g[j + 1];
+      done = !(est > rtol2 * bb) || hnext == 0.0 || total >= maxit;
+      if (done) { ++j; break; }
+      if (!grid_sync(bar)) { *ok = false; return total; }   // v_{j+1} complete before the next apply
+    }
+    if (j > GM_M) j = GM_M;
+    // ---- y = H^{-1} g (upper triangular, j x j), x += D^{-1} V y
+    if (threadIdx.x == 0) {
+      for (int i = j - 1; i >= 0; --i) {
+        double t = sh.g[i];
+        for (int k = i + 1; k < j; ++k) t -= sh.H[k * (GM_M + 1) + i] * sh.y[k];
+        const double d = sh.H[i * (GM_M + 1) + i];
+        sh.y[i] = d != 0.0 ? t / d : 0.0;
+      }
     }
     __syncthreads();
-    if (!bcg_reduce<1>(w1, sred, stot, partials, rk, bar)) { *ok = false; return it; }
-    const double rv = stot[0];
-    alpha = (rv != 0.0) ? rho_new / rv : 0.0;
-    // phase 2: s = r - alpha v; t = M D^{-1} s
-    double w2[2] = {0.0, 0.0};
     for (long long a = tid; a < N; a += gs) {
-      int idx[3];
-      node_ijk(g, a, idx);
-      double acc = 0;
-#pragma unroll
-      for (int s = 0; s < ST<D>::S; ++s) {
-        const long long nb = slot_node<D>(g, idx, a, s);
-        if (nb >= 0) acc += B.M[s * N + a] * (B.dinv[nb] * (B.r[nb] - alpha * vnew[nb]));
-      }
-      const double sa = B.r[a] - alpha * vnew[a];
-      B.s[a] = sa;
-      B.t[a] = acc;
-      w2[0] += acc * sa;
-      w2[1] += acc * acc;
+      double s = 0.0;
+      for (int i = 0; i < j; ++i) s += sh.y[i] * K.V[(size_t)i * N + a];
+      x[a] += dinv[a] * s;
     }
-    if (!bcg_reduce<2>(w2, sred, stot, partials, rk, bar)) { *ok = false; return it; }
-    omega = (stot[1] > 0.0) ? stot[0] / stot[1] : 0.0;
-    // phase 3: x += alpha D^{-1} p + omega D^{-1} s; r = s - omega t
-    double w3[2] = {0.0, 0.0};
-    for (long long a = tid; a < N; a += gs) {
-      const double di = B.dinv[a];
-      B.x[a] += alpha * di * pnew[a] + omega * di * B.s[a];
-      const double ra = B.s[a] - omega * B.t[a];
-      B.r[a] = ra;
-      w3[0] += ra * ra;
-      w3[1] += B.rhat[a] * ra;
-    }
-    if (!bcg_reduce<2>(w3, sred, stot, partials, rk, bar)) { *ok = false; return it; }
-    rr = stot[0];
-    rho = rho_new;
-    rho_new = stot[1];
-    double *t = pold; pold = pnew; pnew = t;
-    t = vold; vold = vnew; vnew = t;
-    ++it;
-    if (omega == 0.0 || rho_new == 0.0) {   // breakdown: stop here, caller sees the residual
-      if (rr > rtol2 * bb) *err = DEV_NOCONV;
-      break;
-    }
+    if (!grid_sync(bar)) { *ok = false; return total; }   // x complete before the residual pass
   }
-  return it;
 }
 
 struct TransportArgs {
-  BcgBufs B;
-  const double *Rm;      // R stencil
+  KrylovBufs K;
+  const double *L, *R, *dinv;
+  double *phi;
   double rtol2;
   int maxit, nsteps;
   double *partials;
@@ -319,34 +407,12 @@ struct TransportArgs {
 
 template <int D>
 __global__ void __launch_bounds__(FO_BLOCK) k_transport_run(Grid g, TransportArgs A) {
-  __shared__ double sred[32 * 3];
-  __shared__ double stot[4];
-  const long long N = g.num_nodes;
-  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long gs = (long long)gridDim.x * blockDim.x;
+  __shared__ GmresShared sh;
   int rk = 0, err = DEV_OK, total = 0;
   bool ok = true;
   for (int step = 0; step < A.nsteps && err == DEV_OK; ++step) {
-    // rhs = R phi^n, r = rhs - L phi^n (x starts at phi^n), zero the directions
-    double v[3] = {0, 0, 0};
-    for (long long a = tid; a < N; a += gs) {
-      int idx[3];
-      node_ijk(g, a, idx);
-      const double ra = stencil_row<D>(g, A.Rm, a, idx, VecX<double>{A.B.x});
-      const double la = stencil_row<D>(g, A.B.M, a, idx, VecX<double>{A.B.x});
-      A.B.rhs[a] = ra;
-      const double r = ra - la;
-      A.B.r[a] = r;
-      A.B.rhat[a] = r;
-      A.B.p0[a] = A.B.p1[a] = A.B.v0[a] = A.B.v1[a] = 0.0;
-      v[0] += r * r;
-      v[1] += ra * ra;
-      v[2] += r * r;
-    }
-    if (!bcg_reduce<3>(v, sred, stot, A.partials, rk, A.bar)) return;
-    const double rr = stot[0], bb = stot[1], rho = stot[2];
-    // the first-step x update writes phi in place; every block has finished gathering phi^n
-    total += bicgstab_loop<D>(g, A.B, rr, bb, rho, A.rtol2, A.maxit, sred, stot, A.partials, rk, A.bar, &err, &ok);
+    // L phi^{n+1} = R phi^n, started from phi^n; rhs is formed in the first residual pass
+    total += gmres_solve<D>(g, A.L, A.dinv, A.R, A.phi, A.K, A.rtol2, A.maxit, sh, A.partials, rk, A.bar, &err, &ok);
     if (!ok) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -374,34 +440,35 @@ static fo_status finish_status(fo_problem *p, fo_solve_stats *st, const char *wh
   if (st) {
     memset(st, 0, sizeof *st);
     st->iterations = hs[DS_ITERS];
-    st->operator_applies = 2 * hs[DS_ITERS];
+    st->operator_applies = hs[DS_ITERS];
     st->outer_iterations = 1;
   }
   if (hs[DS_ERR] == DEV_TIMEOUT) return fo_fail(ctx, FO_ETIMEOUT, "grid barrier timed out in %s", what);
   if (hs[DS_ERR] == DEV_NAN) return fo_fail(ctx, FO_ENAN, "NaN in %s", what);
-  if (hs[DS_ERR] == DEV_NOCONV) return fo_fail(ctx, FO_ENOCONV, "%s BiCGStab did not converge", what);
+  if (hs[DS_ERR] == DEV_NOCONV) return fo_fail(ctx, FO_ENOCONV, "%s GMRES did not converge", what);
+  return FO_OK;
+}
+
+static fo_status krylov_bufs(fo_problem *p, long long extra, KrylovBufs *K, double **extra_out) {
+  const long long N = p->mesh->g.num_nodes;
+  double *buf;
+  FO_TRY(fo_scratch(p, sizeof(double) * (size_t)((GM_M + 3) * N + extra * N), (void **)&buf));
+  K->V = buf;
+  K->w = buf + (size_t)(GM_M + 1) * N;
+  K->rhs = buf + (size_t)(GM_M + 2) * N;
+  if (extra_out) *extra_out = buf + (size_t)(GM_M + 3) * N;
   return FO_OK;
 }
 
 fo_status fo_transport_run(fo_problem *p, int nsteps, const fo_solve_opts *o, fo_solve_stats *st) {
   const Grid &g = p->mesh->g;
   const long long N = g.num_nodes;
-  double *buf;
-  FO_TRY(fo_scratch(p, sizeof(double) * 9 * N, (void **)&buf));
   TransportArgs A{};
-  A.B.x = p->phi;
-  A.B.rhs = buf;
-  A.B.r = buf + N;
-  A.B.rhat = buf + 2 * N;
-  A.B.p0 = buf + 3 * N;
-  A.B.p1 = buf + 4 * N;
-  A.B.v0 = buf + 5 * N;
-  A.B.v1 = buf + 6 * N;
-  A.B.s = buf + 7 * N;
-  A.B.t = buf + 8 * N;
-  A.B.M = p->L;
-  A.B.dinv = p->dinvL;
-  A.Rm = p->R;
+  FO_TRY(krylov_bufs(p, 0, &A.K, nullptr));
+  A.L = p->L;
+  A.R = p->R;
+  A.dinv = p->dinvL;
+  A.phi = p->phi;
   A.rtol2 = o->rtol * o->rtol;
   A.maxit = o->maxit;
   A.nsteps = nsteps;
@@ -515,8 +582,8 @@ __device__ __forceinline__ void reinit_row(const Grid &g, long long a, const int
 }
 
 struct ReinitArgs {
-  BcgBufs B;             // B.M = P stencil (rewritten each step), B.dinv = its inverse diagonal
-  double *Pm, *dinvP;
+  KrylovBufs K;
+  double *Pm, *dinvP;    // P stencil (rewritten every step) and its inverse diagonal
   const double *phi0;    // level set at the start (copy)
   double *bufA, *bufB;   // rotating storage for prev / next
   double *phi;           // in/out
@@ -531,8 +598,7 @@ struct ReinitArgs {
 template <int D>
 __global__ void __launch_bounds__(FO_BLOCK) k_reinit_run(Grid g, ReinitArgs A) {
   constexpr int S = ST<D>::S;
-  __shared__ double sred[32 * 3];
-  __shared__ double stot[4];
+  __shared__ GmresShared sh;
   const long long N = g.num_nodes;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long gs = (long long)gridDim.x * blockDim.x;
@@ -541,43 +607,26 @@ __global__ void __launch_bounds__(FO_BLOCK) k_reinit_run(Grid g, ReinitArgs A) {
   // storage: cur, prev, next rotate through {phi, bufA, bufB}; the result ends in phi
   double *cur = A.phi, *prev = nullptr, *next = A.bufA, *spare = A.bufB;
   for (int step = 0; step < A.nsteps && err == DEV_OK; ++step) {
-    double v[3] = {0, 0, 0};
     for (long long a = tid; a < N; a += gs) {
       int idx[3];
       node_ijk(g, a, idx);
       double Ps[S], rhs;
       reinit_row<D>(g, a, idx, A.phi0, cur, prev, A.dt, A.h, Ps, rhs);
-      double px = 0;
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        A.Pm[s * N + a] = Ps[s];
-        const long long nb = slot_node<D>(g, idx, a, s);
-        if (nb >= 0) px += Ps[s] * cur[nb];
-      }
+      for (int s = 0; s < S; ++s) A.Pm[s * N + a] = Ps[s];
       A.dinvP[a] = 1.0 / Ps[0];
+      A.K.rhs[a] = rhs;
       next[a] = cur[a];
-      A.B.rhs[a] = rhs;
-      const double r = rhs - px;
-      A.B.r[a] = r;
-      A.B.rhat[a] = r;
-      A.B.p0[a] = A.B.p1[a] = A.B.v0[a] = A.B.v1[a] = 0.0;
-      v[0] += r * r;
-      v[1] += rhs * rhs;
-      v[2] += r * r;
     }
-    if (!bcg_reduce<3>(v, sred, stot, A.partials, rk, A.bar)) return;
-    BcgBufs B = A.B;
-    B.x = next;
-    total += bicgstab_loop<D>(g, B, stot[0], stot[1], stot[2], A.rtol2, A.maxit, sred, stot, A.partials, rk, A.bar,
-                              &err, &ok);
+    if (!grid_sync(A.bar)) return;   // P rows, D^{-1} and the start value complete
+    total += gmres_solve<D>(g, A.Pm, A.dinvP, nullptr, next, A.K, A.rtol2, A.maxit, sh, A.partials, rk, A.bar, &err,
+                            &ok);
     if (!ok) return;
-    // rotate: prev <- cur, cur <- next
     double *old_prev = prev;
     prev = cur;
     cur = next;
     next = old_prev ? old_prev : spare;
   }
-  // copy the result into phi when it ended elsewhere
   if (cur != A.phi) {
     for (long long a = tid; a < N; a += gs) A.phi[a] = cur[a];
   }
@@ -590,25 +639,14 @@ __global__ void __launch_bounds__(FO_BLOCK) k_reinit_run(Grid g, ReinitArgs A) {
 fo_status fo_reinit_run(fo_problem *p, int nsteps, double dt, double h, const fo_solve_opts *o, fo_solve_stats *st) {
   const Grid &g = p->mesh->g;
   const long long N = g.num_nodes;
-  double *buf;
-  FO_TRY(fo_scratch(p, sizeof(double) * 12 * N, (void **)&buf));
   ReinitArgs A{};
-  A.B.rhs = buf;
-  A.B.r = buf + N;
-  A.B.rhat = buf + 2 * N;
-  A.B.p0 = buf + 3 * N;
-  A.B.p1 = buf + 4 * N;
-  A.B.v0 = buf + 5 * N;
-  A.B.v1 = buf + 6 * N;
-  A.B.s = buf + 7 * N;
-  A.B.t = buf + 8 * N;
-  double *phi0 = buf + 9 * N;
-  A.bufA = buf + 10 * N;
-  A.bufB = buf + 11 * N;
+  double *extra;
+  FO_TRY(krylov_bufs(p, 3, &A.K, &extra));
+  double *phi0 = extra;
+  A.bufA = extra + N;
+  A.bufB = extra + 2 * N;
   A.Pm = p->L;           // the transport matrices are rebuilt before the next transport
   A.dinvP = p->dinvL;
-  A.B.M = p->L;
-  A.B.dinv = p->dinvL;
   A.phi0 = phi0;
   A.phi = p->phi;
   A.dt = dt;

@@ -42,6 +42,31 @@ struct CombX {
   }
 };
 
+// A field view read in single precision (the gathered FP64 value rounded once to FP32).
+template <class X>
+struct CastX {
+  X x;
+  __device__ __forceinline__ float operator()(long long i) const { return (float)x(i); }
+};
+
+// Operator adapter of the mixed path: the element arithmetic of the wrapped FP32 operator
+// (FP32 element data, FP32 accumulation) on FP64 vectors, so that the Krylov recurrence
+// around it stays in FP64.  On GB300 the FP64 pipe is about 1/58 of the FP32 one, and the
+// element arithmetic is most of the FP64 work of an iteration.
+template <class Op32>
+struct Fp32ApplyOp {
+  static constexpr int NPN = Op32::NPN;
+  Op32 op;
+  Grid g;
+  template <class X>
+  __device__ __forceinline__ void row(long long a, const int idx[3], const X &x, double out[NPN]) const {
+    float o[NPN];
+    op.row(a, idx, CastX<X>{x}, o);
+#pragma unroll
+    for (int c = 0; c < NPN; ++c) out[c] = (double)o[c];
+  }
+};
+
 // Slot (stencil index) of vertex l of simplex p as seen from its vertex m.
 template <int D>
 __device__ __forceinline__ int rel_slot(int p, int m, int l) {
