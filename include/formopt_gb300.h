@@ -243,6 +243,27 @@ FO_API fo_status fo_set(fo_problem *prob, int field, const double *values, int o
 /* y = Op x for parity tests; x and y are host arrays (or device if on_device). */
 FO_API fo_status fo_apply(fo_problem *prob, int op, const double *x, double *y, int on_device);
 
+/* State solve that allocates no device memory.  The paper has no counterpart: this is for
+ * callers that cannot let a library call cudaMalloc / cudaFree while they run -- those calls
+ * may synchronise the whole device, they are not allowed while a stream is being captured,
+ * and another framework's caching allocator may already hold the device memory.
+ * Computes the same FP64 Jacobi-PCG solve K_A x = b as fo_state_solve, but its working
+ * memory (Krylov vectors, reduction partials, grid-barrier counter, status words) is one
+ * fixed array of FO_NOALLOC_SCRATCH_BYTES that the library declares in device memory; every
+ * GPU that loads the library holds it until the process exits.
+ *   b: device array, N_dof values (zero on Dirichlet DOFs, like FO_FIELD_LOAD); read only.
+ *   x: device array, N_dof values; the solution (also the start value when o->warm_start).
+ *   o: NULL for defaults; o->precision must be FO_FP64 (FO_MIXED -> FO_EINVAL).
+ * Returns FO_EINVAL when N_dof > FO_NOALLOC_MAX_DOFS; FO_ENOCONV / FO_ENAN / FO_ETIMEOUT as
+ * fo_state_solve.  The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  Every call uses the same array and finds it as the
+ * previous call left it (the call clears what must start at zero): two calls that overlap on
+ * the GPU -- other streams, other contexts, other threads -- race; serialise them. */
+#define FO_NOALLOC_SCRATCH_BYTES (16 << 20)
+#define FO_NOALLOC_MAX_DOFS 258048      /* (16 MiB / 8 - 32768 header doubles) / 8 vectors */
+FO_API fo_status fo_state_solve_noalloc(fo_problem *prob, const double *b, double *x, const fo_solve_opts *o,
+                                        fo_solve_stats *stats);
+
 /* ------------------------------------------------------------- host-only ----- */
 /* PPL state with r = 0.999, delta0 = 0.5, alpha = 2000, beta = 0.5, z = lambda = mu = 0. */
 FO_API void fo_ppl_init(fo_ppl *s, int nc);

@@ -92,6 +92,7 @@ PROTOTYPES = {
     "fo_initial_level": (ST, [VP, C.c_int, DP, DP, C.c_double, C.c_int]),
     "fo_coefficients": (ST, [VP]),
     "fo_state_solve": (ST, [VP, C.POINTER(SolveOpts), C.POINTER(SolveStats)]),
+    "fo_state_solve_noalloc": (ST, [VP, VP, VP, C.POINTER(SolveOpts), C.POINTER(SolveStats)]),
     "fo_adjoint_solve": (ST, [VP, C.POINTER(SolveOpts), C.POINTER(SolveStats)]),
     "fo_functionals": (ST, [VP, DP, DP]),
     "fo_shape_derivative": (ST, [VP, C.c_double, VP]),

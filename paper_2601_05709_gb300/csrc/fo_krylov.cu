@@ -505,3 +505,108 @@ fo_status fo_velocity_pcg(fo_problem *p, const fo_solve_opts *o, double *Btt, fo
   if (p->mesh->g.dim == 2) return velocity_impl<2>(p, o, Btt, st);
   return velocity_impl<3>(p, o, Btt, st);
 }
+
+// ============================================================ state solve without allocation
+// Some callers cannot let a library allocate device memory while they run: cudaMalloc and
+// cudaFree may synchronise the whole device (a stall in a latency-bound loop), they are not
+// allowed while a stream is being captured, and another framework's caching allocator may
+// already own the device memory.  fo_state_solve_noalloc gives them a state solve whose
+// working memory -- the Krylov vectors, the reduction partials, the grid-barrier counter and
+// the status words of the persistent PCG -- is this fixed array, which every GPU that loads
+// the library holds until the process exits.  The caller passes the right-hand side and the
+// solution; nothing is allocated or freed by the call.
+//
+// Layout (doubles): [0, 8) barrier counter, [8, 16) status words, [16, 48) solver outputs,
+// [64, 64 + 2*4096*3) reduction partials, from FO_NOALLOC_HEADER on: 8 vectors of N_dof.
+#define FO_NOALLOC_HEADER 32768
+#define FO_NOALLOC_DOUBLES (FO_NOALLOC_SCRATCH_BYTES / 8)
+static __device__ __align__(256) double g_noalloc_scratch[FO_NOALLOC_DOUBLES];
+
+static fo_status noalloc_scratch_address(fo_ctx *ctx, double **out) {
+  // The array's device address is looked up once per device, with that device current.
+  // Host code cannot use the symbol itself: on the host it names a stand-in, not GPU memory.
+  static double *addr[64] = {};
+  static bool ready[64] = {};
+  const int dev = ctx->device;
+  if (dev < 0 || dev >= 64) return fo_fail(ctx, FO_EINVAL, "device index out of range");
+  if (!ready[dev]) {
+    FO_CU(ctx, cudaSetDevice(dev));
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return fo_cuda_check(ctx, e, "cudaGetSymbolAddress(no-alloc scratch)");
+    addr[dev] = (double *)p;
+    ready[dev] = true;
+  }
+  *out = addr[dev];
+  return FO_OK;
+}
+
+template <int D, class Op>
+static fo_status noalloc_pcg(fo_problem *p, const Op &op, const double *b, double *x, const fo_solve_opts *o,
+                             fo_solve_stats *st) {
+  fo_ctx *ctx = p->ctx;
+  const long long n = p->ndof;
+  double *base;
+  FO_TRY(noalloc_scratch_address(ctx, &base));
+  unsigned *bar = (unsigned *)base;
+  int *status = (int *)(base + 8);
+  double *out = base + 16;
+  // the counter must start at zero and the status words are read back: clear them (the
+  // array keeps whatever the previous call left there)
+  FO_CU(ctx, cudaMemsetAsync(base, 0, 64 * sizeof(double), ctx->stream));
+  PcgArgs<1, double> a{};
+  bind_vectors(a, x, base + FO_NOALLOC_HEADER, n);
+  a.b = b;
+  a.bscale = 1.0;
+  a.dinv = p->dinv_state;
+  a.rtol2 = o->rtol * o->rtol;
+  a.maxit = o->maxit;
+  a.warm = o->warm_start;
+  a.partials = base + 64;
+  a.out = out;
+  a.status = status;
+  a.bar = GridBar{bar, status + DS_ERR, 2000000000ull};
+  auto kern = k_pcg<D, Op, double, 1>;
+  const int block = fo_persistent_block(p, p->mesh->g.num_nodes);
+  int grid;
+  FO_TRY(fo_cooperative_grid(p, (const void *)kern, block, 0, p->mesh->g.num_nodes, o->grid_blocks, &grid));
+  void *argv[] = {(void *)&op, (void *)&a};
+  FO_CU(ctx, cudaLaunchCooperativeKernel((const void *)kern, grid, block, argv, 0, ctx->stream));
+  fo_note_launch(1);
+  FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars, out, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars + 32, status, sizeof(int) * DS_COUNT, cudaMemcpyDeviceToHost, ctx->stream));
+  FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  const int *hs = (const int *)(ctx->h_scalars + 32);
+  if (st) {
+    memset(st, 0, sizeof *st);
+    st->iterations = hs[DS_ITERS];
+    st->operator_applies = hs[DS_ITERS] + 1 + (o->warm_start ? 1 : 0);
+    st->outer_iterations = 1;
+    st->rel_residual = ctx->h_scalars[1] > 0 ? std::sqrt(ctx->h_scalars[0] / ctx->h_scalars[1]) : 0.0;
+  }
+  if (hs[DS_ERR] == DEV_TIMEOUT) return fo_fail(ctx, FO_ETIMEOUT, "grid barrier timed out in PCG");
+  if (hs[DS_ERR] == DEV_NAN) return fo_fail(ctx, FO_ENAN, "NaN in the PCG recurrence");
+  if (hs[DS_ERR] == DEV_NOCONV) return fo_fail(ctx, FO_ENOCONV, "PCG reached maxit=%d", o->maxit);
+  return FO_OK;
+}
+
+extern "C" fo_status fo_state_solve_noalloc(fo_problem *p, const double *b, double *x, const fo_solve_opts *o,
+                                            fo_solve_stats *st) {
+  if (!p || !b || !x) return FO_EINVAL;
+  fo_solve_opts def;
+  fo_solve_opts_default(&def);
+  if (!o) o = &def;
+  if (o->precision != FO_FP64)
+    return fo_fail(p->ctx, FO_EINVAL, "fo_state_solve_noalloc runs the FP64 solve only");
+  if (p->ndof > (long long)FO_NOALLOC_MAX_DOFS)
+    return fo_fail(p->ctx, FO_EINVAL, "%lld DOFs exceed the no-allocation limit of %d (a %d MiB device array)",
+                   p->ndof, (int)FO_NOALLOC_MAX_DOFS, FO_NOALLOC_SCRATCH_BYTES >> 20);
+  if (!p->coef_valid) FO_TRY(fo_coefficients(p));   // launches kernels, allocates nothing
+  const Grid &g = p->mesh->g;
+  if (p->desc.kind == FO_ELASTIC) {
+    if (g.dim == 2) return noalloc_pcg<2>(p, make_elastic_op<2, double>(p), b, x, o, st);
+    return noalloc_pcg<3>(p, make_elastic_op<3, double>(p), b, x, o, st);
+  }
+  if (g.dim == 2) return noalloc_pcg<2>(p, make_scalar_op<2, double>(p), b, x, o, st);
+  return noalloc_pcg<3>(p, make_scalar_op<3, double>(p), b, x, o, st);
+}
