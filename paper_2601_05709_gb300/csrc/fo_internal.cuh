@@ -264,31 +264,45 @@ __device__ __forceinline__ void block_sum(double (&v)[NR], double *smem /* [32*N
 #pragma unroll
     for (int j = 0; j < NR; ++j) smem[warp * NR + j] = v[j];
   __syncthreads();
-  if (warp == 0) {
+  // value j is finished by warp j mod nw (the values proceed in parallel); its result goes
+  // to smem[j], a slot only that warp reads
+  for (int j = warp; j < NR; j += nw) {
+    double t = (lane < nw) ? smem[lane * NR + j] : 0.0;
 #pragma unroll
-    for (int j = 0; j < NR; ++j) {
-      double t = (lane < nw) ? smem[lane * NR + j] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-      v[j] = t;
-    }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) smem[j] = t;
   }
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) v[j] = smem[j];
 }
 
 // Sum of the per-block partials [G][NR] in a fixed order; every block gets the same bits.
-// Result broadcast to all threads through smem_out[NR].
+// Values are spread over the warps; each lane issues its partial loads in independent
+// batches of four before adding them (a fixed order), so a reduction costs about one L2
+// round trip instead of one per partial.  Result broadcast through smem_out[NR].
 template <int NR>
 __device__ __forceinline__ void grid_total(const double *partials, double *smem_out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (warp == 0) {
-#pragma unroll
-    for (int j = 0; j < NR; ++j) {
-      double t = 0.0;
-      for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(partials + (size_t)b * NR + j);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-      if (lane == 0) smem_out[j] = t;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int G = (int)gridDim.x;
+  for (int j = warp; j < NR; j += nw) {
+    double t = 0.0;
+    int b = lane;
+    for (; b + 96 < G; b += 128) {
+      const double x0 = __ldcg(partials + (size_t)b * NR + j);
+      const double x1 = __ldcg(partials + (size_t)(b + 32) * NR + j);
+      const double x2 = __ldcg(partials + (size_t)(b + 64) * NR + j);
+      const double x3 = __ldcg(partials + (size_t)(b + 96) * NR + j);
+      t += x0;
+      t += x1;
+      t += x2;
+      t += x3;
     }
+    for (; b < G; b += 32) t += __ldcg(partials + (size_t)b * NR + j);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) smem_out[j] = t;
   }
   __syncthreads();
 }

@@ -126,18 +126,16 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg(Op op, PcgArgs<NC, T> S) {
   double v[NR];
 #pragma unroll
   for (int j = 0; j < NR; ++j) v[j] = 0.0;
-  for (long long a = tid; a < N; a += gstride) {
-    int idx[3];
-    node_ijk(g, a, idx);
-    T ax[NPN];
-    if (S.warm) op.row(a, idx, VecX<T>{S.x}, ax);
+  auto start1 = [&](long long a, const auto *ax) {
 #pragma unroll
     for (int c = 0; c < NPN; ++c) {
       const long long k = a * NPN + c;
       const int sy = (NC == 1) ? 0 : c;
       const double bk = (S.bmask && S.bmask[a]) ? 0.0 : (S.bT ? (double)S.bT[k] : S.bscale * S.b[k]);
-      if (!S.warm) { ax[c] = T(0); S.x[k] = T(0); }
-      const T rk0 = (T)(bk - (double)ax[c]);
+      double axc = 0.0;
+      if (ax) axc = (double)ax[c];
+      else S.x[k] = T(0);
+      const T rk0 = (T)(bk - axc);
       S.r[0][k] = rk0;
       S.u[k] = S.dinv[k] * rk0;
       S.s[1][k] = T(0);
@@ -145,7 +143,9 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg(Op op, PcgArgs<NC, T> S) {
       v[sy * 3 + 0] += (double)rk0 * (double)rk0;
       v[sy * 3 + 1] += bk * bk;
     }
-  }
+  };
+  if (S.warm) op.sweep(VecX<T>{S.x}, start1);
+  else op.each([&](long long a) { start1(a, (const double *)nullptr); });
   if (!reduce_grid<NR>(v, sred, stot, S.partials, rk, S.bar)) return;
   double rr[NC], bb[NC], gam[NC], alpha[NC], beta[NC];
 #pragma unroll
@@ -157,21 +157,18 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg(Op op, PcgArgs<NC, T> S) {
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < NR; ++j) v[j] = 0.0;
-  for (long long a = tid; a < N; a += gstride) {
-    int idx[3];
-    node_ijk(g, a, idx);
-    T wa[NPN];
-    op.row(a, idx, VecX<T>{S.u}, wa);
+  op.sweep(VecX<T>{S.u}, [&](long long a, const auto *wa) {
 #pragma unroll
     for (int c = 0; c < NPN; ++c) {
       const long long k = a * NPN + c;
       const int sy = (NC == 1) ? 0 : c;
-      S.w[0][k] = wa[c];
+      const T wk = (T)wa[c];
+      S.w[0][k] = wk;
       const double uk = (double)S.u[k];
       v[sy * 3 + 0] += (double)S.r[0][k] * uk;
-      v[sy * 3 + 1] += (double)wa[c] * uk;
+      v[sy * 3 + 1] += (double)wk * uk;
     }
-  }
+  });
   if (!reduce_grid<NR>(v, sred, stot, S.partials, rk, S.bar)) return;
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
@@ -210,11 +207,7 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg(Op op, PcgArgs<NC, T> S) {
     __syncthreads();   // stot is rewritten by the reduction below
 #pragma unroll
     for (int j = 0; j < NR; ++j) v[j] = 0.0;
-    for (long long a = tid; a < N; a += gstride) {
-      int idx[3];
-      node_ijk(g, a, idx);
-      T wa[NPN];
-      op.row(a, idx, nu, wa);   // w_{i+1} = A u_{i+1}
+    op.sweep(nu, [&](long long a, const auto *wa) {   // wa = w_{i+1} = A u_{i+1}
 #pragma unroll
       for (int c = 0; c < NPN; ++c) {
         const long long k = a * NPN + c;
@@ -227,14 +220,15 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg(Op op, PcgArgs<NC, T> S) {
         S.x[k] += al * pk;
         const T rk1 = rc[k] - al * sk;
         const T uk1 = S.dinv[k] * rk1;
+        const T wk1 = (T)wa[c];
         rn[k] = rk1;
         S.u[k] = uk1;
-        wn[k] = wa[c];
+        wn[k] = wk1;
         v[sy * 3 + 0] += (double)rk1 * (double)uk1;
-        v[sy * 3 + 1] += (double)wa[c] * (double)uk1;
+        v[sy * 3 + 1] += (double)wk1 * (double)uk1;
         v[sy * 3 + 2] += (double)rk1 * (double)rk1;
       }
-    }
+    });
     if (!reduce_grid<NR>(v, sred, stot, S.partials, rk, S.bar)) return;
 #pragma unroll
     for (int s = 0; s < NC; ++s) {
@@ -255,7 +249,7 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg(Op op, PcgArgs<NC, T> S) {
   double bx[NR];
 #pragma unroll
   for (int j = 0; j < NR; ++j) bx[j] = 0.0;
-  for (long long a = tid; a < N; a += gstride)
+  op.each([&](long long a) {
 #pragma unroll
     for (int c = 0; c < NPN; ++c) {
       const long long k = a * NPN + c;
@@ -263,6 +257,7 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg(Op op, PcgArgs<NC, T> S) {
       const double bk = (S.bmask && S.bmask[a]) ? 0.0 : (S.bT ? (double)S.bT[k] : S.bscale * S.b[k]);
       bx[sy * 3] += bk * (double)S.x[k];
     }
+  });
   if (!reduce_grid<NR>(bx, sred, stot, S.partials, rk, S.bar)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int s = 0; s < NC; ++s) {
@@ -277,13 +272,28 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg(Op op, PcgArgs<NC, T> S) {
 
 // ------------------------------------------------------------------------- host driver
 template <class K, class... Args>
-static fo_status coop_launch(fo_problem *p, K kernel, int grid, int block, Args... args) {
+static fo_status coop_launch(fo_problem *p, K kernel, int grid, int block, size_t smem, Args... args) {
   void *argv[] = {(void *)&args...};
   FO_CU(p->ctx, cudaMemsetAsync(p->bar, 0, 64, p->ctx->stream));
   FO_CU(p->ctx, cudaMemsetAsync(p->dev_status, 0, sizeof(int) * DS_COUNT, p->ctx->stream));
-  FO_CU(p->ctx, cudaLaunchCooperativeKernel((const void *)kernel, grid, block, argv, 0, p->ctx->stream));
+  FO_CU(p->ctx, cudaLaunchCooperativeKernel((const void *)kernel, grid, block, argv, smem, p->ctx->stream));
   fo_note_launch(1);
   return FO_OK;
+}
+
+// Block size, work items and dynamic shared memory of a persistent sweep with operator Op:
+// node-centric operators take one node per thread; tiled operators one tile per block.
+template <class Op>
+static void sweep_shape(const fo_problem *p, const Op &op, long long nodes, int *block, long long *work, size_t *smem) {
+  if constexpr (Op::smem_bytes > 0) {
+    *block = Op::THREADS;
+    *work = op.ntiles * Op::THREADS;
+    *smem = Op::smem_bytes;
+  } else {
+    *block = fo_persistent_block(p, nodes);
+    *work = nodes;
+    *smem = 0;
+  }
 }
 
 struct SolveOut {
@@ -321,14 +331,18 @@ static void bind_vectors(PcgArgs<NC, T> &a, T *x, T *buf, long long n) {
 template <int D, class Op, typename T, int NC>
 static fo_status run_pcg(fo_problem *p, const Op &op, PcgArgs<NC, T> a, long long nodes, int requested, SolveOut *o) {
   auto kern = k_pcg<D, Op, T, NC>;
-  const int block = fo_persistent_block(p, nodes);
-  int grid;
-  FO_TRY(fo_cooperative_grid(p, (const void *)kern, block, 0, nodes, requested, &grid));
+  int block, grid;
+  long long work;
+  size_t smem;
+  sweep_shape(p, op, nodes, &block, &work, &smem);
+  if (smem > 48 * 1024)
+    FO_CU(p->ctx, cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FO_TRY(fo_cooperative_grid(p, (const void *)kern, block, smem, work, requested, &grid));
   a.partials = p->red;
   a.out = out_area(p);
   a.status = p->dev_status;
   a.bar = GridBar{p->bar, p->dev_status + DS_ERR, 2000000000ull};
-  FO_TRY(coop_launch(p, kern, grid, block, op, a));
+  FO_TRY(coop_launch(p, kern, grid, block, smem, op, a));
   FO_CU(p->ctx, cudaGetLastError());
   FO_TRY(read_out(p, out_area(p), o, 4 * NC));
   if (o->status[DS_ERR] == DEV_TIMEOUT) return fo_fail(p->ctx, FO_ETIMEOUT, "grid barrier timed out in PCG");
@@ -365,9 +379,11 @@ __global__ void k_axpy(double *x, const double *d, long long n) {
     x[i] += d[i];
 }
 
-template <int D, class Op64, class Op32>
-static fo_status state_solve_impl(fo_problem *p, const Op64 &op64, const Op32 &op32, const double *b, double *x,
-                                  const fo_solve_opts *o, fo_solve_stats *st) {
+// op64: the FP64 operator; op_mixed: the operator of the inner solve of the mixed path
+// (FP32 element arithmetic, FP64 vectors)
+template <int D, class Op64, class OpMixed>
+static fo_status state_solve_impl(fo_problem *p, const Op64 &op64, const OpMixed &op_mixed, const double *b,
+                                  double *x, const fo_solve_opts *o, fo_solve_stats *st) {
   const Grid &g = p->mesh->g;
   const long long n = p->ndof;
   fo_solve_stats s;
@@ -399,7 +415,6 @@ static fo_status state_solve_impl(fo_problem *p, const Op64 &op64, const Op32 &o
   double *buf;
   FO_TRY(fo_scratch(p, sizeof(double) * 11 * n, (void **)&buf));
   double *r64 = buf, *ax64 = buf + n, *d64 = buf + 2 * n, *vec64 = buf + 3 * n;
-  const Fp32ApplyOp<Op32> op_mixed{op32, op32.g};
   fo_ctx *ctx = p->ctx;
   const int blocks = fo_blocks_for(n, FO_BLOCK, 1024);
   if (!o->warm_start) FO_CU(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream));
@@ -460,11 +475,17 @@ fo_status fo_state_pcg(fo_problem *p, const double *b, double *x, const fo_solve
   const Grid &g = p->mesh->g;
   if (p->desc.kind == FO_ELASTIC) {
     if (g.dim == 2)
-      return state_solve_impl<2>(p, make_elastic_op<2, double>(p), make_elastic_op<2, float>(p), b, x, o, st);
-    return state_solve_impl<3>(p, make_elastic_op<3, double>(p), make_elastic_op<3, float>(p), b, x, o, st);
+      return state_solve_impl<2>(p, make_tiled_elastic_op<2, double>(p), make_tiled_elastic_op<2, float>(p), b, x,
+                                 o, st);
+    return state_solve_impl<3>(p, make_tiled_elastic_op<3, double>(p), make_tiled_elastic_op<3, float>(p), b, x, o,
+                               st);
   }
-  if (g.dim == 2) return state_solve_impl<2>(p, make_scalar_op<2, double>(p), make_scalar_op<2, float>(p), b, x, o, st);
-  return state_solve_impl<3>(p, make_scalar_op<3, double>(p), make_scalar_op<3, float>(p), b, x, o, st);
+  if (g.dim == 2) {
+    const auto s32 = make_scalar_op<2, float>(p);
+    return state_solve_impl<2>(p, make_scalar_op<2, double>(p), Fp32ApplyOp<decltype(s32)>{s32, s32.g}, b, x, o, st);
+  }
+  const auto s32 = make_scalar_op<3, float>(p);
+  return state_solve_impl<3>(p, make_scalar_op<3, double>(p), Fp32ApplyOp<decltype(s32)>{s32, s32.g}, b, x, o, st);
 }
 
 template <int D>

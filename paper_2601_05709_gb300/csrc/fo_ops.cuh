@@ -42,6 +42,34 @@ struct CombX {
   }
 };
 
+// ---- node ownership ---------------------------------------------------------------------
+// A persistent kernel walks "its" nodes through the operator: `sweep(x, f)` applies the
+// operator to the field view x and calls f(a, row[NPN]) for every node a the calling
+// thread owns; `each(f)` calls f(a) for the same nodes without applying anything.  The
+// node-centric operators own nodes grid-stride, one per thread.
+template <int NPN, typename OUT, class Op, class X, class F>
+__device__ __forceinline__ void node_sweep(const Op &op, const Grid &g, const X &x, F &&f) {
+  const long long gs = (long long)gridDim.x * blockDim.x;
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < g.num_nodes; a += gs) {
+    int idx[3];
+    node_ijk(g, a, idx);
+    OUT out[NPN];
+    op.row(a, idx, x, out);
+    f(a, out);
+  }
+}
+template <class F>
+__device__ __forceinline__ void node_each(const Grid &g, F &&f) {
+  const long long gs = (long long)gridDim.x * blockDim.x;
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < g.num_nodes; a += gs) f(a);
+}
+#define FO_NODE_OWNERSHIP(OUT)                                                                           \
+  static constexpr size_t smem_bytes = 0;                                                                \
+  template <class X, class F>                                                                            \
+  __device__ __forceinline__ void sweep(const X &x, F &&f) const { node_sweep<NPN, OUT>(*this, g, x, f); } \
+  template <class F>                                                                                     \
+  __device__ __forceinline__ void each(F &&f) const { node_each(g, f); }
+
 // A field view read in single precision (the gathered FP64 value rounded once to FP32).
 template <class X>
 struct CastX {
@@ -58,6 +86,7 @@ struct Fp32ApplyOp {
   static constexpr int NPN = Op32::NPN;
   Op32 op;
   Grid g;
+  FO_NODE_OWNERSHIP(double)
   template <class X>
   __device__ __forceinline__ void row(long long a, const int idx[3], const X &x, double out[NPN]) const {
     float o[NPN];
@@ -126,6 +155,7 @@ template <int D, typename T>
 struct ScalarStateOp {
   static constexpr int NPN = 1;
   Grid g;
+  FO_NODE_OWNERSHIP(T)
   const T *coef;       // A_e * k per element
   const uint8_t *dir;  // per node
   T sk[3];             // |e| / h_a^2
@@ -181,6 +211,7 @@ template <int D, typename T>
 struct ElasticStateOp {
   static constexpr int NPN = D;
   Grid g;
+  FO_NODE_OWNERSHIP(T)
   const T *coef;
   const uint8_t *dir;   // per DOF
   T lam, mu, vol;
@@ -264,6 +295,7 @@ template <int D, typename T>
 struct VelocityOp {
   static constexpr int NPN = D;
   Grid g;
+  FO_NODE_OWNERSHIP(T)
   const uint8_t *omega0;   // per element
   const uint8_t *vdir;     // per node (H^1_0)
   T sk[3];                 // |e| / h_a^2
@@ -390,6 +422,156 @@ struct VelocityOp {
   }
 };
 
+// ---- tiled linear elasticity: element data computed once per simplex -----------------------
+// A block owns a tile of TX x TY (x TZ) nodes.  Stage 1 stages the field on the tile and a
+// one-node halo in shared memory (the view x is evaluated once per node); stage 2 computes,
+// for every simplex of the cells touching the tile, the scaled stress A_e |e| sigma(u_e)
+// once (the node-centric operator recomputes it for each of the simplex's vertices);
+// stage 3 forms each tile node's row from the stresses of its simplices:
+//   row_m = sum_{(p,m)} S_e[:, pi_{m-1}] / h_{pi_{m-1}} - S_e[:, pi_m] / h_{pi_m}.
+// T is the element arithmetic (double, or float for the mixed path); rows are returned in
+// double.  Needs smem_bytes of dynamic shared memory and blocks of TX*TY*TZ threads.
+template <int D, typename T>
+struct TiledElasticOp {
+  static constexpr int NPN = D;
+  static constexpr int TX = (D == 2) ? 16 : 8, TY = (D == 2) ? 8 : 4, TZ = (D == 2) ? 1 : 4;
+  static constexpr int THREADS = TX * TY * TZ;
+  static constexpr int HX = TX + 2, HY = TY + 2, HZ = (D == 2) ? 1 : TZ + 2;   // halo node box
+  static constexpr int CX = TX + 1, CY = TY + 1, CZ = (D == 2) ? 1 : TZ + 1;   // cells touching the tile
+  static constexpr int P = KP<D>::P;
+  static constexpr int NS = (D == 2) ? 3 : 6;                                  // symmetric stress entries
+  static constexpr size_t smem_bytes = sizeof(T) * ((size_t)HX * HY * HZ * D + (size_t)CX * CY * CZ * P * NS);
+  Grid g;
+  const T *coef;
+  const uint8_t *dir;   // per DOF
+  T lam, mu, vol;
+  T ih[3];
+  int ntile[3];
+  long long ntiles;
+
+  __device__ __forceinline__ static int sidx(int i, int j) {   // symmetric index
+    if (i == j) return i;
+    const int a = i < j ? i : j, b = i < j ? j : i;
+    return (D == 2) ? 2 : (a == 0 ? (b == 1 ? 3 : 4) : 5);
+  }
+
+  template <class X, class F>
+  __device__ void sweep(const X &x, F &&f) const {
+    extern __shared__ __align__(16) unsigned char fo_dyn_smem[];
+    T *U = reinterpret_cast<T *>(fo_dyn_smem);                 // [HZ][HY][HX][D]
+    T *S = U + HX * HY * HZ * D;                                // [CZ][CY][CX][P][NS]
+    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const int i0 = (int)(t % ntile[0]) * TX;
+      const int j0 = (int)((t / ntile[0]) % ntile[1]) * TY;
+      const int k0 = (D == 3) ? (int)(t / ((long long)ntile[0] * ntile[1])) * TZ : 0;
+      __syncthreads();   // the previous tile's shared data is no longer read
+      // stage 1: field on the halo box [i0-1, i0+TX] x [j0-1, j0+TY] (x [k0-1, k0+TZ])
+      for (int s = threadIdx.x; s < HX * HY * HZ; s += blockDim.x) {
+        const int hx = s % HX, hy = (s / HX) % HY, hz = s / (HX * HY);
+        const int gi = i0 - 1 + hx, gj = j0 - 1 + hy, gk = (D == 3) ? k0 - 1 + hz : 0;
+        const bool in = gi >= 0 && gi < (int)g.nn[0] && gj >= 0 && gj < (int)g.nn[1] &&
+                        (D == 2 || (gk >= 0 && gk < (int)g.nn[2]));
+        const long long a = gi + g.stride[1] * gj + (D == 3 ? g.stride[2] * gk : 0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) U[s * D + c] = in ? (T)x(a * D + c) : T(0);
+      }
+      __syncthreads();
+      // stage 2: scaled stress of the P simplices of every cell [i0-1, i0+TX-1] x ...
+      for (int cs = threadIdx.x; cs < CX * CY * CZ; cs += blockDim.x) {
+        const int cx = cs % CX, cy = (cs / CX) % CY, cz = cs / (CX * CY);
+        const int gi = i0 - 1 + cx, gj = j0 - 1 + cy, gk = (D == 3) ? k0 - 1 + cz : 0;
+        if (gi < 0 || gi >= g.n[0] || gj < 0 || gj >= g.n[1] || (D == 3 && (gk < 0 || gk >= g.n[2]))) continue;
+        const long long e0 = (long long)P * (gi + g.cstride[1] * gj + (D == 3 ? g.cstride[2] * gk : 0));
+        // field at the 2^D cell corners; corner bit k set = +1 along axis k
+        T uc[1 << D][D];
+#pragma unroll
+        for (int b = 0; b < (1 << D); ++b) {
+          const int h = (cx + (b & 1)) + HX * ((cy + ((b >> 1) & 1)) + HY * (D == 3 ? cz + ((b >> 2) & 1) : 0));
+#pragma unroll
+          for (int i = 0; i < D; ++i) uc[b][i] = U[h * D + i];
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          // walk the Kuhn path of permutation p from the cell corner
+          T du[D][D];
+          int at = 0;
+#pragma unroll
+          for (int l = 0; l < D; ++l) {
+            const int ax = kperm<D>(p, l);
+            const int next = at | (1 << ax);
+#pragma unroll
+            for (int i = 0; i < D; ++i) du[i][ax] = (uc[next][i] - uc[at][i]) * ih[ax];
+            at = next;
+          }
+          T tr = 0;
+#pragma unroll
+          for (int i = 0; i < D; ++i) tr += du[i][i];
+          const T w = coef[e0 + p] * vol;
+          T *Se = S + ((size_t)cs * P + p) * NS;
+#pragma unroll
+          for (int i = 0; i < D; ++i) Se[i] = w * (lam * tr + 2 * mu * du[i][i]);
+#pragma unroll
+          for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = i + 1; j < D; ++j) Se[sidx(i, j)] = w * mu * (du[i][j] + du[j][i]);
+        }
+      }
+      __syncthreads();
+      // stage 3: rows of the tile's nodes
+      const int gi = i0 + tx, gj = j0 + ty, gk = k0 + tz;
+      if (gi < (int)g.nn[0] && gj < (int)g.nn[1] && (D == 2 || gk < (int)g.nn[2])) {
+        const long long a = gi + g.stride[1] * gj + (D == 3 ? g.stride[2] * gk : 0);
+        double out[D];
+        const int hself = (tx + 1) + HX * ((ty + 1) + HY * (D == 3 ? tz + 1 : 0));
+        T acc[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) acc[i] = 0;
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+#pragma unroll
+          for (int m = 0; m <= D; ++m) {
+            int c[3] = {gi, gj, gk};
+#pragma unroll
+            for (int l = 0; l < D; ++l)
+              if (l < m) c[kperm<D>(p, l)] -= 1;
+            bool ok = true;
+#pragma unroll
+            for (int k = 0; k < D; ++k) ok = ok && c[k] >= 0 && c[k] < g.n[k];
+            if (!ok) continue;
+            const int cx = c[0] - (i0 - 1), cy = c[1] - (j0 - 1), cz = (D == 3) ? c[2] - (k0 - 1) : 0;
+            const T *Se = S + ((size_t)((cx + CX * (cy + CY * cz)) * P + p)) * NS;
+            if (m >= 1) {
+              const int j = kperm<D>(p, m - 1);
+#pragma unroll
+              for (int i = 0; i < D; ++i) acc[i] += ih[j] * Se[sidx(i, j)];
+            }
+            if (m < D) {
+              const int j = kperm<D>(p, m);
+#pragma unroll
+              for (int i = 0; i < D; ++i) acc[i] -= ih[j] * Se[sidx(i, j)];
+            }
+          }
+#pragma unroll
+        for (int i = 0; i < D; ++i) out[i] = dir[a * D + i] ? (double)U[hself * D + i] : (double)acc[i];
+        f(a, out);
+      }
+    }
+  }
+
+  template <class F>
+  __device__ void each(F &&f) const {
+    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const int gi = (int)(t % ntile[0]) * TX + tx;
+      const int gj = (int)((t / ntile[0]) % ntile[1]) * TY + ty;
+      const int gk = (D == 3) ? (int)(t / ((long long)ntile[0] * ntile[1])) * TZ + tz : 0;
+      if (gi < (int)g.nn[0] && gj < (int)g.nn[1] && (D == 2 || gk < (int)g.nn[2]))
+        f(gi + g.stride[1] * gj + (D == 3 ? g.stride[2] * gk : 0));
+    }
+  }
+};
+
 // --------------------------------------------------------------- operator construction
 template <int D, typename T>
 inline ScalarStateOp<D, T> make_scalar_op(const fo_problem *p) {
@@ -436,3 +618,22 @@ inline VelocityOp<D, T> make_velocity_op(const fo_problem *p) {
   return op;
 }
 
+
+template <int D, typename T>
+inline TiledElasticOp<D, T> make_tiled_elastic_op(const fo_problem *p) {
+  const Grid &g = p->mesh->g;
+  using Op = TiledElasticOp<D, T>;
+  Op op;
+  op.g = g;
+  op.coef = std::is_same<T, float>::value ? (const T *)p->coef32 : (const T *)p->coef;
+  op.dir = p->dir;
+  op.lam = (T)p->lame_lambda;
+  op.mu = (T)p->lame_mu;
+  op.vol = (T)g.vol_e;
+  for (int a = 0; a < 3; ++a) op.ih[a] = (T)g.inv_h[a];
+  op.ntile[0] = (int)((g.nn[0] + Op::TX - 1) / Op::TX);
+  op.ntile[1] = (int)((g.nn[1] + Op::TY - 1) / Op::TY);
+  op.ntile[2] = (D == 3) ? (int)((g.nn[2] + Op::TZ - 1) / Op::TZ) : 1;
+  op.ntiles = (long long)op.ntile[0] * op.ntile[1] * op.ntile[2];
+  return op;
+}
