@@ -126,7 +126,22 @@ typedef struct {
   double omega0_lo[4][3];   /* strictly inside one box (use +-inf for open sides)       */
   double omega0_hi[4][3];
   int velocity_dirichlet;   /* 1: H = H^1_0(D)^d                                        */
+  /* Task-parallel batch (Sec. 5.3: one PDE family with varying parameters), FO_HELMHOLTZ
+   * only.  n_inst >= 1 makes the problem a batch of n_inst <= FO_MAX_INSTANCES instances
+   * sharing the mesh, phi and A_e; instance i solves
+   *   -div(A k_i grad u_i) + omega_i^2 u_i = f_i   (same Dirichlet faces),
+   * its cost is J_i = int f_i u_i (adjoint p_i = -u_i), and the batch cost is sum_i J_i.
+   * inst_k[i], inst_omega[i] and inst_f[i * N_n + a] are host arrays, copied at creation;
+   * the single-problem fields k, omega and f_nodal are ignored.  0 = a single problem.
+   * Batched fields (FO_FIELD_U, FO_FIELD_P, FO_FIELD_LOAD) are instance-minor:
+   * value of instance i at node a at index a * n_inst + i.                              */
+  int n_inst;
+  const double *inst_k;
+  const double *inst_omega;
+  const double *inst_f;
 } fo_model_desc;
+
+#define FO_MAX_INSTANCES 128
 
 typedef struct {
   int precision;            /* FO_FP64 or FO_MIXED                                      */
@@ -263,6 +278,35 @@ FO_API fo_status fo_apply(fo_problem *prob, int op, const double *x, double *y, 
 #define FO_NOALLOC_MAX_DOFS 258048      /* (16 MiB / 8 - 32768 header doubles) / 8 vectors */
 FO_API fo_status fo_state_solve_noalloc(fo_problem *prob, const double *b, double *x, const fo_solve_opts *o,
                                         fo_solve_stats *stats);
+
+/* ------------------------------------------------------------ batch (TP) ----- */
+/* A batch problem (fo_model_desc.n_inst >= 1) goes through the same calls as a single
+ * problem: fo_coefficients, fo_state_solve / fo_adjoint_solve (all instances in one
+ * persistent cooperative launch), fo_functionals (J = sum_i J_i), fo_shape_derivative
+ * (b = sum_i b_i + lambda * volume term), fo_descent, fo_levelset_step and fo_opt_step.
+ * The calls below are batch-only (FO_EINVAL on a single problem). */
+
+/* Per-instance costs J_i = F_i . u_i of the current state (n_inst values, host). */
+FO_API fo_status fo_batch_costs(fo_problem *prob, double *J_inst);
+/* Per-instance results of the last batched state or adjoint solve (host arrays of n_inst,
+ * either may be NULL): inner Krylov iterations in which the instance was active, summed over
+ * refinement steps, and the final FP64 relative residual ||b_i - K_i x_i|| / ||b_i||. */
+FO_API fo_status fo_batch_solve_info(fo_problem *prob, int *inst_iters, double *inst_res);
+
+/* Launch shape of the batched persistent solver. */
+typedef struct {
+  int block;                /* threads per block (a warp owns a node)                   */
+  int blocks_per_sm;        /* co-resident blocks per SM; grid = blocks_per_sm * SMs   */
+  double us_per_iteration;  /* tuning run time / its Krylov iterations                  */
+  int candidates;           /* launch shapes timed                                     */
+  int tile[3];              /* nodes per shared-memory tile along x, y, z              */
+} fo_tune_result;
+/* Time the batched solver's candidate launch shapes (node tile x threads per block x blocks
+ * per SM, within the device's shared-memory and co-residency limits) on this problem for `precision` (FO_FP64 or
+ * FO_MIXED): each runs a fixed number of Krylov iterations on the current coefficients and
+ * loads, writing a scratch solution only.  The fastest shape is kept on the problem and used
+ * by later solves whose opts->grid_blocks is 0; the first such solve tunes by itself. */
+FO_API fo_status fo_batch_autotune(fo_problem *prob, int precision, fo_tune_result *out);
 
 /* ------------------------------------------------------------- host-only ----- */
 /* PPL state with r = 0.999, delta0 = 0.5, alpha = 2000, beta = 0.5, z = lambda = mu = 0. */

@@ -35,7 +35,14 @@ class ModelDesc(C.Structure):
                 ("point_vec", D43), ("n_tractions", C.c_int), ("traction_face", C.c_int * 4),
                 ("traction_vec", D43), ("volume_target", C.c_double), ("alpha_mass", C.c_double),
                 ("normal_penalty", C.c_double), ("omega0_weight", C.c_double), ("n_omega0", C.c_int),
-                ("omega0_lo", D43), ("omega0_hi", D43), ("velocity_dirichlet", C.c_int)]
+                ("omega0_lo", D43), ("omega0_hi", D43), ("velocity_dirichlet", C.c_int),
+                ("n_inst", C.c_int), ("inst_k", C.POINTER(C.c_double)), ("inst_omega", C.POINTER(C.c_double)),
+                ("inst_f", C.POINTER(C.c_double))]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("us_per_iteration", C.c_double),
+                ("candidates", C.c_int), ("tile", C.c_int * 3)]
 
 
 class SolveOpts(C.Structure):
@@ -74,6 +81,8 @@ DP = C.POINTER(C.c_double)
 ST = C.c_int
 
 # name -> (restype, argtypes)
+FO_MAX_INSTANCES = 128
+
 PROTOTYPES = {
     "fo_ctx_create": (ST, [C.c_int, VP, C.c_size_t, C.POINTER(VP)]),
     "fo_ctx_destroy": (ST, [VP]),
@@ -105,6 +114,9 @@ PROTOTYPES = {
     "fo_get": (ST, [VP, C.c_int, VP]),
     "fo_set": (ST, [VP, C.c_int, VP, C.c_int]),
     "fo_apply": (ST, [VP, C.c_int, VP, VP, C.c_int]),
+    "fo_batch_costs": (ST, [VP, DP]),
+    "fo_batch_solve_info": (ST, [VP, C.POINTER(C.c_int), DP]),
+    "fo_batch_autotune": (ST, [VP, C.c_int, C.POINTER(TuneResult)]),
     "fo_ppl_init": (None, [C.POINTER(PPLState), C.c_int]),
     "fo_ppl_update": (None, [C.POINTER(PPLState), DP, C.c_double, DP, DP]),
     "fo_adaptime": (None, [C.c_double, C.POINTER(RunOptions), DP, C.POINTER(C.c_int)]),

@@ -61,9 +61,11 @@ def run_options(dfactor=1e-2, lv_time=(1e-3, 1e-1), lv_iter=(8, 16), smooth=Fals
 
 def model_desc(kind, a_in=1.0, a_out=1e-3, E=1.0, nu=0.3, k=1.0, omega=0.0, dirichlet=(), f_nodal=None,
                point_loads=(), tractions=(), volume=0.0, alpha_mass=0.1, normal_penalty=0.0, omega0_weight=0.0,
-               omega0_boxes=(), velocity_dirichlet=False):
+               omega0_boxes=(), velocity_dirichlet=False, inst_k=None, inst_omega=None, inst_f=None):
     """Build a fo_model_desc.  dirichlet: [(axis, side)]; point_loads: [(node, vec)];
-    tractions: [(axis, side, vec)]; omega0_boxes: [(lo, hi)] with strict inequalities."""
+    tractions: [(axis, side, vec)]; omega0_boxes: [(lo, hi)] with strict inequalities.
+    A task-parallel batch (kind FO_HELMHOLTZ): inst_k, inst_omega [n_inst] and
+    inst_f [n_inst, N_n]."""
     d = _lib.ModelDesc()
     d.kind, d.a_in, d.a_out, d.E, d.nu, d.k, d.omega = kind, a_in, a_out, E, nu, k, omega
     mask = 0
@@ -94,7 +96,16 @@ def model_desc(kind, a_in=1.0, a_out=1e-3, E=1.0, nu=0.3, k=1.0, omega=0.0, diri
             d.omega0_lo[i][c] = lo[c] if c < len(lo) else -np.inf
             d.omega0_hi[i][c] = hi[c] if c < len(hi) else np.inf
     d.velocity_dirichlet = int(bool(velocity_dirichlet))
-    d._keep = keep                       # keep f alive until fo_problem_create copied it
+    kept = [keep]
+    if inst_k is not None:
+        ik, io = _f64(inst_k), _f64(inst_omega)
+        iF = _f64(inst_f).reshape(len(ik), -1)
+        if len(io) != len(ik):
+            raise ValueError("inst_k and inst_omega differ in length")
+        d.n_inst = len(ik)
+        d.inst_k, d.inst_omega, d.inst_f = _dp(ik), _dp(io), _dp(iF)
+        kept += [ik, io, iF]
+    d._keep = kept                       # keep the arrays alive until fo_problem_create copied them
     return d
 
 
@@ -183,6 +194,7 @@ class Problem:
         self.handle = h
         self.kind = desc.kind
         self.ncomp = mesh.dim if desc.kind == FO_ELASTIC else 1
+        self.n_inst = int(desc.n_inst)       # 0: a single problem
 
     def _chk(self, st, what):
         return self.ctx.check(st, what)
@@ -255,10 +267,29 @@ class Problem:
                                        C.byref(log)), "fo_opt_step")
         return log
 
+    def batch_costs(self):
+        """Per-instance costs J_i of a batch."""
+        out = np.empty(self.n_inst)
+        self._chk(self.lib.fo_batch_costs(self.handle, _dp(out)), "fo_batch_costs")
+        return out
+
+    def batch_solve_info(self):
+        """(active iterations, final relative residual) per instance of the last batched solve."""
+        it = np.empty(self.n_inst, dtype=np.int32)
+        res = np.empty(self.n_inst)
+        self._chk(self.lib.fo_batch_solve_info(self.handle, it.ctypes.data_as(C.POINTER(C.c_int)), _dp(res)),
+                  "fo_batch_solve_info")
+        return it, res
+
+    def batch_autotune(self, precision=_lib.FO_MIXED):
+        r = _lib.TuneResult()
+        self._chk(self.lib.fo_batch_autotune(self.handle, precision, C.byref(r)), "fo_batch_autotune")
+        return r
+
     def _field_len(self, field):
         m = self.mesh
         if field in (FO_FIELD_U, FO_FIELD_P, FO_FIELD_LOAD):
-            return self.ncomp * m.num_nodes
+            return self.ncomp * m.num_nodes * max(self.n_inst, 1)
         if field in (FO_FIELD_THETA, FO_FIELD_RHS):
             return m.dim * m.num_nodes
         if field in (FO_FIELD_COEF, FO_FIELD_CHI, FO_FIELD_OMEGA0):
@@ -268,6 +299,8 @@ class Problem:
     def get(self, field):
         out = np.empty(self._field_len(field))
         self._chk(self.lib.fo_get(self.handle, field, out.ctypes.data_as(C.c_void_p)), "fo_get")
+        if self.n_inst and field in (FO_FIELD_U, FO_FIELD_P, FO_FIELD_LOAD):
+            return out.reshape(-1, self.n_inst)  # [N_n, n_inst]
         return out
 
     def set(self, field, values):

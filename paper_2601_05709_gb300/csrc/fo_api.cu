@@ -273,6 +273,7 @@ extern "C" fo_status fo_problem_destroy(fo_problem *p) {
   if (!p) return FO_EINVAL;
   fo_ctx *ctx = p->ctx;
   cudaStreamSynchronize(ctx->stream);
+  fo_batch_destroy(p);
   std::vector<std::pair<void **, size_t>> list;
   prob_bytes_fields(p, list);
   for (auto &e : list) {
@@ -302,6 +303,8 @@ extern "C" fo_status fo_problem_create(fo_mesh *m, const fo_model_desc *desc, fo
       return fo_fail(ctx, FO_EINVAL, "bad traction face");
   if (desc->kind == FO_ELASTIC && !(desc->nu > -1.0 && desc->nu < 0.5 && desc->E > 0))
     return fo_fail(ctx, FO_EINVAL, "bad elastic parameters");
+  if (desc->n_inst < 0 || (desc->n_inst > 0 && desc->kind != FO_HELMHOLTZ))
+    return fo_fail(ctx, FO_EINVAL, "a task-parallel batch (n_inst > 0) is a FO_HELMHOLTZ family");
   fo_problem *p = new fo_problem();
   p->ctx = ctx;
   p->mesh = m;
@@ -315,6 +318,11 @@ extern "C" fo_status fo_problem_create(fo_mesh *m, const fo_model_desc *desc, fo
   }
   if (desc->kind == FO_HELMHOLTZ && !(desc->k > 0)) p->desc.k = 1.0;
   if (desc->kind == FO_HEAT) p->desc.k = 1.0;
+  p->desc.inst_k = p->desc.inst_omega = p->desc.inst_f = nullptr;
+  if (desc->n_inst > 0) {   // batch: A_e alone in coef; k_i, omega_i, f_i per instance
+    p->desc.k = 1.0;
+    p->desc.omega = 0.0;
+  }
   std::vector<std::pair<void **, size_t>> list;
   prob_bytes_fields(p, list);
   fo_status st = FO_OK;
@@ -336,6 +344,7 @@ extern "C" fo_status fo_problem_create(fo_mesh *m, const fo_model_desc *desc, fo
   if (st == FO_OK) st = fo_launch_masks(p);
   if (st == FO_OK) st = fo_launch_loads(p);
   if (st == FO_OK) st = fo_launch_velocity_diag(p);
+  if (st == FO_OK && desc->n_inst > 0) st = fo_batch_create(p, desc);
   if (st == FO_OK) st = fo_cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "problem setup");
   if (st != FO_OK) {
     fo_problem_destroy(p);
@@ -371,7 +380,8 @@ extern "C" fo_status fo_initial_level(fo_problem *p, int count, const double *ce
 extern "C" fo_status fo_coefficients(fo_problem *p) {
   if (!p) return FO_EINVAL;
   FO_TRY(fo_launch_coefficients(p));
-  FO_TRY(fo_launch_state_diag(p));
+  if (p->batch) FO_TRY(fo_batch_prepare(p));
+  else FO_TRY(fo_launch_state_diag(p));
   p->coef_valid = true;
   return FO_OK;
 }
@@ -382,7 +392,7 @@ extern "C" fo_status fo_state_solve(fo_problem *p, const fo_solve_opts *o, fo_so
   fo_solve_opts_default(&def);
   if (!o) o = &def;
   if (!p->coef_valid) FO_TRY(fo_coefficients(p));
-  fo_status s = fo_state_pcg(p, p->load, p->u, o, st);
+  fo_status s = p->batch ? fo_batch_state(p, false, o, st) : fo_state_pcg(p, p->load, p->u, o, st);
   if (s == FO_OK || s == FO_ENOCONV) p->u_valid = true;
   return s;
 }
@@ -398,6 +408,7 @@ extern "C" fo_status fo_adjoint_solve(fo_problem *p, const fo_solve_opts *o, fo_
   fo_solve_opts_default(&def);
   if (!o) o = &def;
   if (!p->coef_valid) FO_TRY(fo_coefficients(p));
+  if (p->batch) return fo_batch_state(p, true, o, st);
   double c = p->desc.kind == FO_ELASTIC ? -2.0 : -1.0;
   double *b = p->rhs;   // reuse the RHS buffer as the adjoint load (d*N_n >= N_dof)
   k_scale<<<fo_blocks_for(p->ndof), FO_BLOCK, 0, p->ctx->stream>>>(p->load, b, c, p->ndof);
@@ -414,7 +425,8 @@ extern "C" fo_status fo_functionals(fo_problem *p, double *J, double *C) {
   if (!p) return FO_EINVAL;
   if (!p->coef_valid) FO_TRY(fo_coefficients(p));
   double j = 0, vol = 0;
-  FO_TRY(fo_launch_functionals(p, &j, &vol));
+  if (p->batch) FO_TRY(fo_batch_functionals(p, &j, &vol, nullptr));
+  else FO_TRY(fo_launch_functionals(p, &j, &vol));
   if (J) *J = j;
   if (C) *C = p->desc.volume_target > 0 ? vol / p->desc.volume_target : vol;
   if (!std::isfinite(j) || !std::isfinite(vol)) return fo_fail(p->ctx, FO_ENAN, "non-finite functional");
@@ -424,7 +436,8 @@ extern "C" fo_status fo_functionals(fo_problem *p, double *J, double *C) {
 extern "C" fo_status fo_shape_derivative(fo_problem *p, double lambda, double *rhs_out) {
   if (!p) return FO_EINVAL;
   if (!p->coef_valid) FO_TRY(fo_coefficients(p));
-  FO_TRY(fo_launch_shape_rhs(p, lambda));
+  if (p->batch) FO_TRY(fo_batch_shape_rhs(p, lambda));
+  else FO_TRY(fo_launch_shape_rhs(p, lambda));
   p->rhs_valid = true;
   p->last_lambda = lambda;
   if (rhs_out) {
@@ -485,6 +498,58 @@ extern "C" fo_status fo_reinit(fo_problem *p, int nsteps, double t_final, double
   return s;
 }
 
+// Batched fields (U, P, LOAD of a task-parallel batch) are [N_n][nip] on the device, with
+// instance i in lane lane_of[i], and [N_n][n_inst] in the caller's order at the interface.
+static double *batch_field(fo_problem *p, int field) {
+  if (!p->batch) return nullptr;
+  switch (field) {
+    case FO_FIELD_U: return p->batch->U;
+    case FO_FIELD_P: return p->batch->P;
+    case FO_FIELD_LOAD: return p->batch->B;
+    default: return nullptr;
+  }
+}
+
+static fo_status batch_to_host(fo_problem *p, const double *dev, double *out, int on_device) {
+  fo_ctx *ctx = p->ctx;
+  const size_t NN = (size_t)p->mesh->g.num_nodes, nip = p->batch->nip, n = p->batch->n_inst;
+  std::vector<double> tmp(NN * nip), outv;
+  FO_CU(ctx, cudaMemcpyAsync(tmp.data(), dev, sizeof(double) * NN * nip, cudaMemcpyDeviceToHost, ctx->stream));
+  FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  double *dst = out;
+  if (on_device) {
+    outv.resize(NN * n);
+    dst = outv.data();
+  }
+  const std::vector<int> &lane = p->batch->lane_of;
+  for (size_t a = 0; a < NN; ++a)
+    for (size_t i = 0; i < n; ++i) dst[a * n + i] = tmp[a * nip + lane[i]];
+  if (on_device) {
+    FO_CU(ctx, cudaMemcpyAsync(out, dst, sizeof(double) * NN * n, cudaMemcpyHostToDevice, ctx->stream));
+    FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return FO_OK;
+}
+
+static fo_status batch_from_host(fo_problem *p, double *dev, const double *v, int on_device) {
+  fo_ctx *ctx = p->ctx;
+  const size_t NN = (size_t)p->mesh->g.num_nodes, nip = p->batch->nip, n = p->batch->n_inst;
+  std::vector<double> in, tmp(NN * nip, 0.0);
+  const double *src = v;
+  if (on_device) {
+    in.resize(NN * n);
+    FO_CU(ctx, cudaMemcpyAsync(in.data(), v, sizeof(double) * NN * n, cudaMemcpyDeviceToHost, ctx->stream));
+    FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    src = in.data();
+  }
+  const std::vector<int> &lane = p->batch->lane_of;
+  for (size_t a = 0; a < NN; ++a)
+    for (size_t i = 0; i < n; ++i) tmp[a * nip + lane[i]] = src[a * n + i];
+  FO_CU(ctx, cudaMemcpyAsync(dev, tmp.data(), sizeof(double) * NN * nip, cudaMemcpyHostToDevice, ctx->stream));
+  FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  return FO_OK;
+}
+
 static double *field_ptr(fo_problem *p, int field, size_t *n, bool *is_u8) {
   const Grid &g = p->mesh->g;
   *is_u8 = false;
@@ -504,6 +569,7 @@ static double *field_ptr(fo_problem *p, int field, size_t *n, bool *is_u8) {
 
 extern "C" fo_status fo_get(fo_problem *p, int field, double *out) {
   if (!p || !out) return FO_EINVAL;
+  if (double *bf = batch_field(p, field)) return batch_to_host(p, bf, out, 0);
   size_t n;
   bool u8;
   double *src = field_ptr(p, field, &n, &u8);
@@ -528,6 +594,13 @@ extern "C" fo_status fo_get(fo_problem *p, int field, double *out) {
 
 extern "C" fo_status fo_set(fo_problem *p, int field, const double *v, int on_device) {
   if (!p || !v) return FO_EINVAL;
+  if (p->batch && field == FO_FIELD_U) {
+    FO_TRY(batch_from_host(p, p->batch->U, v, on_device));
+    p->u_valid = true;
+    return FO_OK;
+  }
+  if (p->batch && (field == FO_FIELD_P || field == FO_FIELD_LOAD))
+    return fo_fail(p->ctx, FO_EINVAL, "field %d cannot be set", field);
   size_t n;
   bool u8;
   double *dst = field_ptr(p, field, &n, &u8);
@@ -559,6 +632,17 @@ extern "C" fo_status fo_apply(fo_problem *p, int op, const double *x, double *y,
     default: return fo_fail(ctx, FO_EINVAL, "unknown operator %d", op);
   }
   if ((op == FO_OP_STATE || op == FO_OP_STATE_FP32) && !p->coef_valid) FO_TRY(fo_coefficients(p));
+  if (p->batch && (op == FO_OP_STATE || op == FO_OP_STATE_FP32)) {   // all instances, [N_n][n_inst]
+    const size_t nx = (size_t)g.num_nodes * p->batch->nip;
+    double *bx, *by;
+    FO_TRY(fo_alloc(ctx, (void **)&bx, sizeof(double) * 2 * nx));
+    by = bx + nx;
+    fo_status r = batch_from_host(p, bx, x, on_device);
+    if (r == FO_OK) r = fo_batch_apply(p, bx, by, op == FO_OP_STATE_FP32);
+    if (r == FO_OK) r = batch_to_host(p, by, y, on_device);
+    fo_free(ctx, bx, sizeof(double) * 2 * nx);
+    return r;
+  }
   double *dx, *dy;
   FO_TRY(fo_alloc(ctx, (void **)&dx, sizeof(double) * n));
   fo_status st = fo_alloc(ctx, (void **)&dy, sizeof(double) * n);

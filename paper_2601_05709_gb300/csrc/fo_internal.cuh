@@ -56,6 +56,29 @@ struct Scratch {
   size_t bytes = 0;
 };
 
+// Task-parallel batch of screened Helmholtz instances on one mesh.  Fields are
+// instance-minor with the instance count padded to nip = 32, 64 or 128: the value
+// of instance i at node a sits at a * nip + i, so a warp that owns a node reads each
+// field's row with coalesced loads (lane l holds instances l, l + 32, ...).  Padding
+// instances have k = 1, omega = 0 and a zero source, hence a zero solution.
+struct fo_batch {
+  int n_inst = 0, nip = 0;
+  std::vector<int> lane_of;                 // caller's instance i lives in lane lane_of[i]
+  std::vector<double> h_k, h_omega;         // per lane
+  double *kk = nullptr, *w2 = nullptr;      // [nip] k_i and omega_i^2
+  double *f = nullptr;                      // [N_n][nip] nodal sources
+  double *B = nullptr;                      // [N_n][nip] loads F_i (0 on Dirichlet nodes)
+  double *U = nullptr, *P = nullptr;        // [N_n][nip] states and explicit adjoints
+  double *WK = nullptr, *WM = nullptr;      // [N_n][S] stiffness (A-weighted) / mass stencils
+  float *WK32 = nullptr, *WM32 = nullptr;   // the same in FP32
+  double *dinv = nullptr;                   // [N_n][nip] Jacobi inverse diagonal
+  float *dinv32 = nullptr;
+  int *inst_iters = nullptr;                // [nip] last solve: active iterations
+  double *inst_res = nullptr;               // [nip] last solve: final relative residual
+  int tuned_ts[2] = {0, 0}, tuned_block[2] = {0, 0}, tuned_bpsm[2] = {0, 0};   // per precision (FO_FP64, FO_MIXED)
+  double tuned_us[2] = {0, 0};
+};
+
 struct fo_problem {
   fo_ctx *ctx;
   fo_mesh *mesh;
@@ -91,6 +114,7 @@ struct fo_problem {
   double transport_dt = 0, transport_h = 0;
   int transport_smooth = 0;
   double last_lambda = 0;
+  fo_batch *batch = nullptr;     // non-null for a task-parallel batch (FO_HELMHOLTZ)
 };
 
 // status helpers
@@ -317,6 +341,14 @@ inline int fo_blocks_for(long long n, int block = FO_BLOCK, int cap = 1 << 20) {
 
 // internal entry points implemented across translation units
 fo_status fo_launch_coefficients(fo_problem *p);
+// task-parallel batch (fo_batch.cu)
+fo_status fo_batch_create(fo_problem *p, const fo_model_desc *desc);
+void fo_batch_destroy(fo_problem *p);
+fo_status fo_batch_prepare(fo_problem *p);     // stencils and Jacobi diagonal from A_e
+fo_status fo_batch_state(fo_problem *p, bool adjoint, const fo_solve_opts *o, fo_solve_stats *st);
+fo_status fo_batch_functionals(fo_problem *p, double *J, double *vol, double *J_inst);
+fo_status fo_batch_shape_rhs(fo_problem *p, double lambda);
+fo_status fo_batch_apply(fo_problem *p, const double *x, double *y, bool fp32);
 fo_status fo_launch_loads(fo_problem *p);
 fo_status fo_launch_masks(fo_problem *p);
 fo_status fo_launch_state_diag(fo_problem *p);

@@ -619,6 +619,7 @@ extern "C" fo_status fo_state_solve_noalloc(fo_problem *p, const double *b, doub
   if (!o) o = &def;
   if (o->precision != FO_FP64)
     return fo_fail(p->ctx, FO_EINVAL, "fo_state_solve_noalloc runs the FP64 solve only");
+  if (p->batch) return fo_fail(p->ctx, FO_EINVAL, "fo_state_solve_noalloc takes a single problem");
   if (p->ndof > (long long)FO_NOALLOC_MAX_DOFS)
     return fo_fail(p->ctx, FO_EINVAL, "%lld DOFs exceed the no-allocation limit of %d (a %d MiB device array)",
                    p->ndof, (int)FO_NOALLOC_MAX_DOFS, FO_NOALLOC_SCRATCH_BYTES >> 20);

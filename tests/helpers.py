@@ -120,3 +120,36 @@ def cantilever3d(n=(12, 6, 6)):
     return case(dim=3, n=n, lo=(0, 0, 0), hi=(2, 1, 1), kind=1, dirichlet=[(0, 0)],
                 tractions=[(0, 1, (0.0, 0.0, -1.0))], volume=1.0, alpha_mass=0.1, normal_penalty=1e4,
                 omega0_weight=1e4, omega0_boxes=[((1.90, 0.35, 0.35), (np.inf, 0.65, 0.65))])
+
+
+def batch_case(dim=2, n=(16, 16), n_inst=5, seed=1, a_in=1.0, a_out=1e-3, volume=0.0, alpha_mass=0.1,
+               velocity_dirichlet=False):
+    """A task-parallel batch: k_i ~ U[0.5, 2], omega_i ~ U[0, 5], Fourier sources (8 modes,
+    N(0, 1) amplitudes, seeded), Dirichlet on x = 0, on the unit box."""
+    from paper_2601_05709_gb300 import workloads
+    k, om, amp = workloads.batch_parameters(n_inst, seed)
+    return dict(dim=dim, n=tuple(n), n_inst=n_inst, k=k, omega=om, amp=amp, a_in=a_in, a_out=a_out,
+                volume=volume, alpha_mass=alpha_mass, velocity_dirichlet=velocity_dirichlet)
+
+
+def _batch_sources(coords, amp):
+    from paper_2601_05709_gb300 import workloads
+    return workloads.fourier_loads(coords[:, :2], amp)
+
+
+def oracle_batch(c):
+    from oracle.batch import Batch
+    m = BoxMesh(c["dim"], c["n"], (0.0,) * c["dim"], (1.0,) * c["dim"])
+    vform = ovel.VelocityForm(alpha_mass=c["alpha_mass"], dirichlet=c["velocity_dirichlet"])
+    return Batch(m, c["k"], c["omega"], _batch_sources(m.coords, c["amp"]), dirichlet_faces=[(0, 0)],
+                 a_in=c["a_in"], a_out=c["a_out"], volume_target=c["volume"], vform=vform)
+
+
+def gpu_batch(ctx, c):
+    from paper_2601_05709_gb300 import api
+    mesh = ctx.mesh_box(c["dim"], c["n"], (0.0,) * c["dim"], (1.0,) * c["dim"])
+    _, coords = mesh.copy_out()
+    desc = api.model_desc(2, a_in=c["a_in"], a_out=c["a_out"], dirichlet=[(0, 0)], volume=c["volume"],
+                          alpha_mass=c["alpha_mass"], velocity_dirichlet=c["velocity_dirichlet"],
+                          inst_k=c["k"], inst_omega=c["omega"], inst_f=_batch_sources(coords, c["amp"]))
+    return mesh, mesh.problem(desc)

@@ -1,0 +1,152 @@
+"""GPU parity of the task-parallel batch (many screened Helmholtz instances on one mesh)
+against the oracle's per-instance definitions, and batch-vs-alone reproducibility."""
+import numpy as np
+import pytest
+
+from oracle import fem
+from oracle import shape as oshape
+from oracle import velocity as ovel
+from paper_2601_05709_gb300 import api
+from paper_2601_05709_gb300.api import FO_FIELD_LOAD, FO_FIELD_P, FO_FIELD_RHS, FO_FIELD_THETA, FO_FIELD_U
+from paper_2601_05709_gb300 import workloads
+from tests.helpers import assert_solve_parity, batch_case, close_scaled, gpu_batch, oracle_batch, rel
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "2d_5": dict(dim=2, n=(24, 20), n_inst=5, seed=1),          # one 32-lane slab, 27 padding lanes
+    "2d_40": dict(dim=2, n=(17, 13), n_inst=40, seed=2),        # two slabs
+    "3d_33": dict(dim=3, n=(6, 5, 4), n_inst=33, seed=3),       # 3D, two slabs
+}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def _setup(ctx, name):
+    c = batch_case(**CASES[name])
+    ob = oracle_batch(c)
+    mesh, prob = gpu_batch(ctx, c)
+    phi = workloads.phi_cos(ob.mesh.coords[:, :2]) if c["dim"] == 2 else workloads.phi_bumps(
+        ob.mesh.coords, workloads.bump_centres(np.zeros(3), np.ones(3), 6, seed=0), 0.2, 0.2)
+    prob.set_levelset(phi)
+    return c, ob, prob, phi
+
+
+def _K(ob, i, A):
+    return ob.problem(i).stiffness(A)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_batch_loads_and_operator(ctx, name):
+    c, ob, prob, phi = _setup(ctx, name)
+    prob.coefficients()
+    F = prob.get(FO_FIELD_LOAD)
+    Fref = ob.loads()
+    assert F.shape == Fref.shape
+    assert close_scaled(F, Fref, 1e-13)
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(F.shape)
+    dirm = ob.problem(0).dirichlet() == 1
+    x[dirm, :] = 0.0                       # Dirichlet columns are eliminated
+    y = prob.apply(api.FO_OP_STATE, x)
+    y32 = prob.apply(api.FO_OP_STATE_FP32, x)
+    A, _ = oshape.coefficient(phi, ob.mesh.cells, ob.a_in, ob.a_out)
+    for i in range(c["n_inst"]):
+        yr = _K(ob, i, A) @ x[:, i]
+        free = ~dirm
+        assert close_scaled(y[free, i], yr[free], 1e-13), i
+        assert close_scaled(y32[free, i], yr[free], 1e-5), i
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("precision", [api.FO_FP64, api.FO_MIXED])
+def test_batch_state_parity(ctx, name, precision):
+    c, ob, prob, phi = _setup(ctx, name)
+    U_ref, A, chi = ob.state(phi)
+    st = prob.state_solve(api.solve_opts(precision=precision, rtol=1e-12))
+    U = prob.get(FO_FIELD_U)
+    its, res = prob.batch_solve_info()
+    assert np.all(res <= 1e-10), res
+    F = ob.loads()
+    free = ob.problem(0).dirichlet() == 0
+    for i in range(c["n_inst"]):
+        assert_solve_parity(_K(ob, i, A), F[:, i], free, U[:, i], U_ref[:, i], 1e-10, omega_max=1e-10)
+    assert np.all(U[~free] == 0.0)
+    # J = sum_i F_i . u_i, per instance and summed
+    J_inst = prob.batch_costs()
+    J_ref = ob.costs(U_ref, A)
+    assert np.max(np.abs(J_inst - J_ref) / np.abs(J_ref)) <= 1e-9
+    J, Cv = prob.functionals()
+    assert abs(J - J_ref.sum()) <= 1e-9 * np.abs(J_ref).sum()
+    vol, _ = fem.geometry(ob.mesh.coords, ob.mesh.cells)
+    assert abs(Cv - np.sum(vol * chi)) <= 1e-13
+    assert st.iterations > 0
+
+
+@pytest.mark.parametrize("name", ["2d_5", "3d_33"])
+def test_batch_adjoint_and_shape(ctx, name):
+    c, ob, prob, phi = _setup(ctx, name)
+    opts = api.solve_opts(precision=api.FO_FP64, rtol=1e-12)
+    prob.state_solve(opts)
+    prob.adjoint_solve(opts)
+    U, P = prob.get(FO_FIELD_U), prob.get(FO_FIELD_P)
+    assert rel(P, -U) <= 1e-9                  # explicit adjoint = closed form p_i = -u_i
+    b = prob.shape_derivative(0.0)
+    # oracle tensors evaluated on the GPU state isolate the assembly from the solve
+    _, A, chi = ob.state(phi)
+    b_ref = ob.rhs(U, A, chi, 0.0)
+    assert close_scaled(b, b_ref, 1e-11)
+    lam = 0.3
+    b2 = prob.shape_derivative(lam)
+    ob.volume_target = 1.0
+    assert close_scaled(b2, ob.rhs(U, A, chi, lam), 1e-11)
+
+
+@pytest.mark.parametrize("precision", [api.FO_FP64, api.FO_MIXED])
+def test_batch_instance_equals_alone(ctx, precision):
+    """Instance i in the batch and the same instance alone give the same bits (same launch
+    shape; reductions are per instance and in a fixed order)."""
+    c = batch_case(**CASES["2d_40"])
+    mesh, prob = gpu_batch(ctx, c)
+    _, coords = mesh.copy_out()
+    phi = workloads.phi_cos(coords)
+    prob.set_levelset(phi)
+    opts = api.solve_opts(precision=precision, rtol=1e-12, grid_blocks=96)
+    prob.state_solve(opts)
+    U = prob.get(FO_FIELD_U)
+    for i in (0, 17, 39):
+        ci = dict(c, n_inst=1, k=c["k"][i:i + 1], omega=c["omega"][i:i + 1], amp=c["amp"][i:i + 1])
+        _, pi = gpu_batch(ctx, ci)
+        pi.set_levelset(phi)
+        pi.state_solve(opts)
+        ui = pi.get(FO_FIELD_U)[:, 0]
+        assert np.array_equal(ui, U[:, i]), (i, np.max(np.abs(ui - U[:, i])))
+
+
+def test_batch_opt_step_matches_oracle(ctx):
+    """One Algorithm-1 iteration of a batch: summed cost, summed tensors, velocity, transport."""
+    from oracle import levelset as olev, ppl as oppl
+    c = batch_case(dim=2, n=(20, 20), n_inst=6, seed=4, alpha_mass=0.01, velocity_dirichlet=True)
+    ob = oracle_batch(c)
+    mesh, prob = gpu_batch(ctx, c)
+    phi = workloads.phi_cos(ob.mesh.coords)
+    prob.set_levelset(phi)
+    ro = api.run_options()
+    log = prob.opt_step(0, ro)
+    U_ref, A, chi = ob.state(phi)
+    J_ref = ob.cost(U_ref, A)
+    assert abs(log.J - J_ref) <= 1e-9 * abs(J_ref)
+    b_ref = ob.rhs(U_ref, A, chi, 0.0)
+    assert close_scaled(prob.get(FO_FIELD_RHS), b_ref, 1e-8)
+    theta_ref, Btt_ref = ovel.solve(ob.mesh, ob.vform, b_ref)
+    assert rel(prob.get(FO_FIELD_THETA), theta_ref) <= 1e-7
+    assert abs(log.Btt - Btt_ref) <= 1e-7 * abs(Btt_ref)
+    t_end, ns = oppl.adaptime(Btt_ref, ro.dfactor, (ro.t_min, ro.t_max), (ro.s_min, ro.s_max))
+    assert ns == log.nsteps
+    phi_ref = olev.transport(ob.mesh, phi, theta_ref, t_end, ns, ob.mesh.diameter(), False)
+    assert rel(prob.get(api.FO_FIELD_PHI), phi_ref) <= 1e-7
