@@ -199,14 +199,14 @@ struct BatchArgs {
   int *inst_iters;
   double *inst_res;
   double rtol2, inner_rtol2;
-  int maxit, inner_maxit, max_outer, warm;
+  int maxit, inner_maxit, warm;
 };
 
 template <int NIP>
 struct BatchShared {
   double tot[3 * NIP];
-  double alpha[NIP], beta[NIP], gam[NIP], gam0[NIP], bn2[NIP], rn2p[NIP], rn2pp[NIP], res[NIP];
-  int act[NIP], done[NIP], iters[NIP];
+  double alpha[NIP], beta[NIP], gam[NIP], gref[NIP], bn2[NIP], rn2p[NIP], rn2pp[NIP], res[NIP];
+  int act[NIP], done[NIP], iters[NIP], upd[NIP], kloc[NIP];
 };
 
 // Sum NCOL columns of per-instance values over the whole grid; totals land in sh.tot
@@ -269,7 +269,6 @@ __global__ void __launch_bounds__(256) k_batch_solve(BatchArgs A, BatchVecs<T> V
   constexpr int HX = TX + 2, HY = TY + 2, HZ = (D == 3) ? TZ + 2 : 1, NH = HX * HY * HZ, NT = TX * TY * TZ;
   constexpr int S = ST<D>::S, NIP = 32 * NJ;
   constexpr bool F64 = std::is_same<T, double>::value;
-  constexpr int NC = F64 ? 3 : 2;   // gamma = (r, u), delta = (w, u) [, rho = (r, r)]
   extern __shared__ __align__(16) unsigned char fo_batch_smem[];
   T *smU = reinterpret_cast<T *>(fo_batch_smem);             // [NH][NIP] during a sweep
   T *sW = smU + (size_t)NH * NIP;                             // [NT][2 S] own-node weights
@@ -295,302 +294,372 @@ __global__ void __launch_bounds__(256) k_batch_solve(BatchArgs A, BatchVecs<T> V
   for (int t = threadIdx.x; t < NIP; t += blockDim.x) {
     sh.iters[t] = 0;
     sh.done[t] = 0;
+    sh.act[t] = 0;
+    sh.upd[t] = 1;
     sh.rn2p[t] = sh.rn2pp[t] = INFINITY;
     sh.res[t] = 0.0;
     sh.bn2[t] = 0.0;
+    sh.alpha[t] = sh.beta[t] = sh.gam[t] = sh.gref[t] = 0.0;
+    sh.kloc[t] = 0;
   }
   __syncthreads();
 
-  int sweeps = 0, applies = 0, outer = 0, err = DEV_OK;
-  bool ok = true;
-  for (outer = 0;; ++outer) {
-    // ---- x += d (FP64) ----------------------------------------------------------------
+  // ---- phases ------------------------------------------------------------------------
+  // X += x (FP64) and x = 0 for the instances being updated; on the first call X = 0
+  // unless warm-started.
+  auto accumulate = [&](bool start) {
+    bool mine[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) mine[j] = sh.upd[lane + 32 * j] != 0;
     for (long long a = first; a < N; a += step)
 #pragma unroll
       for (int j = 0; j < NJ; ++j) {
+        if (!mine[j]) continue;
         const long long q = a * NIP + lane + 32 * j;
-        if (outer == 0) {
+        if (start) {
           if (!A.warm) A.X[q] = 0.0;
         } else {
           A.X[q] += (double)V.x[q];
         }
+        V.x[q] = T(0);
       }
-    if (!(ok = grid_sync(A.bar))) break;
-    // ---- r = b - K x (FP64); inner start vectors -------------------------------------
-    {
-      double red[2][NJ];
+  };
+  // r = b - K X in FP64 for the instances being updated, stored rounded to T in buffer set
+  // `buf` (the one the next sweep reads), with the start vectors of a fresh recurrence:
+  // w = s = 0 in that set and p = 0.
+  auto residual = [&](int buf, double (&red)[2][NJ]) {
+    T *rbuf = V.r[buf], *wbuf = V.w[buf], *sbuf = V.s[buf];
+    bool mine[NJ];
 #pragma unroll
-      for (int j = 0; j < NJ; ++j) red[0][j] = red[1][j] = 0.0;
-      for (long long a = first; a < N; a += step) {
-        int idx[3];
-        node_ijk(g, a, idx);
-        double yk[NJ], ym[NJ];
+    for (int j = 0; j < NJ; ++j) {
+      red[0][j] = red[1][j] = 0.0;
+      mine[j] = sh.upd[lane + 32 * j] != 0;
+    }
+    for (long long a = first; a < N; a += step) {
+      int idx[3];
+      node_ijk(g, a, idx);
+      double yk[NJ], ym[NJ];
 #pragma unroll
-        for (int j = 0; j < NJ; ++j) yk[j] = ym[j] = 0.0;
+      for (int j = 0; j < NJ; ++j) yk[j] = ym[j] = 0.0;
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-          const long long nb = slot_node<D>(g, idx, a, s);
-          if (nb < 0) continue;
-          const double wk = A.WK[a * S + s], wm = A.WM[a * S + s];
-          if (s > 0 && wk == 0.0 && wm == 0.0) continue;
-#pragma unroll
-          for (int j = 0; j < NJ; ++j) {
-            const double xv = A.X[nb * NIP + lane + 32 * j];
-            yk[j] = fma(wk, xv, yk[j]);
-            ym[j] = fma(wm, xv, ym[j]);
-          }
-        }
+      for (int s = 0; s < S; ++s) {
+        const long long nb = slot_node<D>(g, idx, a, s);
+        if (nb < 0) continue;
+        const double wk = A.WK[a * S + s], wm = A.WM[a * S + s];
+        if (s > 0 && wk == 0.0 && wm == 0.0) continue;
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
-          const long long q = a * NIP + lane + 32 * j;
-          const double b = A.bscale * A.B[q];
-          const double r = b - fma(kk64[j], yk[j], w264[j] * ym[j]);
-          red[0][j] += r * r;
-          red[1][j] += b * b;
-          V.r[1][q] = (T)r;
-          V.w[1][q] = T(0);
-          V.s[1][q] = T(0);
-          V.p[q] = T(0);
-          V.x[q] = T(0);
+          if (!mine[j]) continue;
+          const double xv = A.X[nb * NIP + lane + 32 * j];
+          yk[j] = fma(wk, xv, yk[j]);
+          ym[j] = fma(wm, xv, ym[j]);
         }
       }
-      if (!(ok = batch_allreduce<2, NJ>(A, red, part, sh))) break;
-    }
-    ++applies;
-    int nan = 0, open = 0;
-    for (int t = threadIdx.x; t < NIP; t += blockDim.x) {
-      const double rn2 = sh.tot[t];
-      if (outer == 0) sh.bn2[t] = sh.tot[NIP + t];
-      const double bn2 = sh.bn2[t];
-      if (!isfinite(rn2)) nan = 1;
-      const bool conv = rn2 <= A.rtol2 * bn2 || rn2 == 0.0;
-      // the FP64 residual stops falling at its rounding floor: two consecutive refinement
-      // steps that fail to halve it end the instance (x is as accurate as FP64 allows)
-      const bool floor = outer >= 2 && rn2 > 0.25 * sh.rn2p[t] && sh.rn2p[t] > 0.25 * sh.rn2pp[t];
-      sh.res[t] = bn2 > 0.0 ? sqrt(rn2 / bn2) : sqrt(rn2);
-      sh.rn2pp[t] = sh.rn2p[t];
-      sh.rn2p[t] = rn2;
-      sh.done[t] = (conv || floor) ? 1 : 0;
-      sh.act[t] = sh.done[t] ? 0 : 1;
-      sh.alpha[t] = sh.beta[t] = sh.gam[t] = sh.gam0[t] = 0.0;
-      open |= sh.act[t];
-    }
-    if (__syncthreads_or(nan)) {
-      err = DEV_NAN;
-      break;
-    }
-    if (!__syncthreads_or(open)) break;
-    if (outer >= A.max_outer || sweeps >= A.maxit) {
-      err = DEV_NOCONV;
-      break;
-    }
-    // ---- inner PCG on K d = r ----------------------------------------------------------
-    for (int k = 0;; ++k) {
-      T al[NJ], be[NJ];
-      bool on[NJ];   // this lane's instances still iterate; frozen ones are skipped
 #pragma unroll
       for (int j = 0; j < NJ; ++j) {
-        al[j] = (T)sh.alpha[lane + 32 * j];
-        be[j] = (T)sh.beta[lane + 32 * j];
-        on[j] = sh.act[lane + 32 * j] != 0;
+        if (!mine[j]) continue;
+        const long long q = a * NIP + lane + 32 * j;
+        const double b = A.bscale * A.B[q];
+        const double r = b - fma(kk64[j], yk[j], w264[j] * ym[j]);
+        red[0][j] += r * r;
+        red[1][j] += b * b;
+        rbuf[q] = (T)r;
+        wbuf[q] = T(0);
+        sbuf[q] = T(0);
+        V.p[q] = T(0);
       }
-      const int ob = (k + 1) & 1, nb_ = k & 1;
-      const T *ro = V.r[ob], *wo = V.w[ob], *so = V.s[ob];
-      T *rn = V.r[nb_], *wn = V.w[nb_], *sn = V.s[nb_];
-      double dacc[NC][NJ];
-      T cacc[NC][NJ];
+    }
+  };
+  // One pass over the tiles: step k of the recurrence.  Reads r_{k-1}, w_{k-1}, s_{k-2} from
+  // buffer set (k+1)&1, writes r_k, s_{k-1}, w_k to set k&1 and updates p, x; dot products
+  // (r_k, u_k), (w_k, u_k) and, in FP64, (r_k, r_k).
+  auto sweep = [&](int k, double (&dacc)[3][NJ]) {
+    T al[NJ], be[NJ];
+    bool on[NJ];   // this lane's instances still iterate; frozen ones are skipped
 #pragma unroll
-      for (int c = 0; c < NC; ++c)
+    for (int j = 0; j < NJ; ++j) {
+      al[j] = (T)sh.alpha[lane + 32 * j];
+      be[j] = (T)sh.beta[lane + 32 * j];
+      on[j] = sh.act[lane + 32 * j] != 0 && sh.upd[lane + 32 * j] == 0;   // running, not waiting
+    }
+    const int ob = (k + 1) & 1, nb_ = k & 1;
+    const T *ro = V.r[ob], *wo = V.w[ob], *so = V.s[ob];
+    T *rn = V.r[nb_], *wn = V.w[nb_], *sn = V.s[nb_];
+    T cacc[3][NJ];
 #pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-          dacc[c][j] = 0.0;
-          cacc[c][j] = T(0);
-        }
-      int chunk = 0;
-      auto count = [&]() {   // FP32 partial dot products go to FP64 every DOT_CHUNK nodes
-        if (!F64 && ++chunk == DOT_CHUNK) {
-          chunk = 0;
+    for (int c = 0; c < 3; ++c)
 #pragma unroll
-          for (int c = 0; c < NC; ++c)
+      for (int j = 0; j < NJ; ++j) {
+        dacc[c][j] = 0.0;
+        cacc[c][j] = T(0);
+      }
+    int chunk = 0;
+    auto count = [&]() {   // FP32 partial dot products go to FP64 every DOT_CHUNK nodes
+      if (!F64 && ++chunk == DOT_CHUNK) {
+        chunk = 0;
 #pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-              dacc[c][j] += (double)cacc[c][j];
-              cacc[c][j] = T(0);
-            }
-        }
-      };
-      for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int i0 = (int)(tile % ntx) * TX, j0 = (int)((tile / ntx) % nty) * TY;
-        const int k0 = (D == 3) ? (int)(tile / ((long long)ntx * nty)) * TZ : 0;
-        // stage 1: u_k on the halo box, recurrences on the own nodes.  A warp takes two halo
-        // nodes at a time and issues all their loads before any store, so that several rows
-        // per warp are in flight; lanes of frozen instances neither load nor store.
-        for (int h0 = warp; h0 < NH; h0 += 2 * nw) {
-          long long aa[2];
-          int oo[2];
-          bool in[2], ow[2];
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int h = h0 + u * nw;
-            const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
-            const int gi = i0 - 1 + hx, gj = j0 - 1 + hy, gk = (D == 3) ? k0 - 1 + hz : 0;
-            in[u] = h < NH && gi >= 0 && gi < nn0 && gj >= 0 && gj < nn1 && (D == 2 || (gk >= 0 && gk < nn2));
-            ow[u] = in[u] && hx >= 1 && hx <= TX && hy >= 1 && hy <= TY && (D == 2 || (hz >= 1 && hz <= TZ));
-            aa[u] = in[u] ? gi + g.stride[1] * gj + (D == 3 ? g.stride[2] * gk : 0) : 0;
-            oo[u] = (hx - 1) + TX * ((hy - 1) + TY * (D == 3 ? hz - 1 : 0));
+          for (int j = 0; j < NJ; ++j) {
+            dacc[c][j] += (double)cacc[c][j];
+            cacc[c][j] = T(0);
           }
-          T rq[2][NJ], dq[2][NJ], sq[2][NJ], wq[2][NJ], pq[2][NJ], xq[2][NJ], wt[2][2];
+      }
+    };
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int i0 = (int)(tile % ntx) * TX, j0 = (int)((tile / ntx) % nty) * TY;
+      const int k0 = (D == 3) ? (int)(tile / ((long long)ntx * nty)) * TZ : 0;
+      // stage 1: u_k on the halo box, recurrences on the own nodes.  A warp takes UB halo
+      // nodes at a time and issues all their loads before any store, so that several rows
+      // per warp are in flight; lanes of frozen or waiting instances neither load nor store.
+      constexpr int UB = 4 / NJ;   // rows in flight per warp: UB * NJ = 4
+      for (int h0 = warp; h0 < NH; h0 += UB * nw) {
+        long long aa[UB];
+        int oo[UB];
+        bool in[UB], ow[UB];
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < UB; ++u) {
+          const int h = h0 + u * nw;
+          const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+          const int gi = i0 - 1 + hx, gj = j0 - 1 + hy, gk = (D == 3) ? k0 - 1 + hz : 0;
+          in[u] = h < NH && gi >= 0 && gi < nn0 && gj >= 0 && gj < nn1 && (D == 2 || (gk >= 0 && gk < nn2));
+          ow[u] = in[u] && hx >= 1 && hx <= TX && hy >= 1 && hy <= TY && (D == 2 || (hz >= 1 && hz <= TZ));
+          aa[u] = in[u] ? gi + g.stride[1] * gj + (D == 3 ? g.stride[2] * gk : 0) : 0;
+          oo[u] = (hx - 1) + TX * ((hy - 1) + TY * (D == 3 ? hz - 1 : 0));
+        }
+        T rq[UB][NJ], dq[UB][NJ], sq[UB][NJ], wq[UB][NJ], pq[UB][NJ], xq[UB][NJ], wt[UB][2];
 #pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-              rq[u][j] = dq[u][j] = sq[u][j] = wq[u][j] = pq[u][j] = xq[u][j] = T(0);
-              if (in[u] && on[j]) {
-                const long long q = aa[u] * NIP + lane + 32 * j;
-                rq[u][j] = ro[q];
-                dq[u][j] = V.dinv[q];
-                sq[u][j] = so[q];
-                wq[u][j] = wo[q];
-                if (ow[u]) {
-                  pq[u][j] = V.p[q];
-                  xq[u][j] = V.x[q];
-                }
-              }
-            }
-            wt[u][0] = wt[u][1] = T(0);
-            if (ow[u] && lane < S) {
-              wt[u][0] = V.WK[aa[u] * S + lane];
-              wt[u][1] = V.WM[aa[u] * S + lane];
-            }
-          }
+        for (int u = 0; u < UB; ++u) {
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int h = h0 + u * nw;
-            if (h >= NH) continue;
-            T *su = smU + (size_t)h * NIP + lane;
-            if (!in[u]) {
-#pragma unroll
-              for (int j = 0; j < NJ; ++j) su[32 * j] = T(0);
-              continue;
-            }
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-              if (!on[j]) continue;
-              const T sv = fma(be[j], sq[u][j], wq[u][j]);
-              const T rv = fma(-al[j], sv, rq[u][j]);
-              const T uv = dq[u][j] * rv;
-              su[32 * j] = uv;
+          for (int j = 0; j < NJ; ++j) {
+            rq[u][j] = dq[u][j] = sq[u][j] = wq[u][j] = pq[u][j] = xq[u][j] = T(0);
+            if (in[u] && on[j]) {
+              const long long q = aa[u] * NIP + lane + 32 * j;
+              rq[u][j] = ro[q];
+              dq[u][j] = V.dinv[q];
+              sq[u][j] = so[q];
+              wq[u][j] = wo[q];
               if (ow[u]) {
-                const long long q = aa[u] * NIP + lane + 32 * j;
-                rn[q] = rv;
-                sn[q] = sv;
-                const T p_new = fma(be[j], pq[u][j], dq[u][j] * rq[u][j]);
-                V.x[q] = fma(al[j], p_new, xq[u][j]);
-                V.p[q] = p_new;
-                cacc[0][j] = fma(rv, uv, cacc[0][j]);
-                if (NC == 3) cacc[NC - 1][j] = fma(rv, rv, cacc[NC - 1][j]);
+                pq[u][j] = V.p[q];
+                xq[u][j] = V.x[q];
               }
-            }
-            if (ow[u]) {
-              if (lane < S) {
-                sW[oo[u] * 2 * S + lane] = wt[u][0];
-                sW[oo[u] * 2 * S + S + lane] = wt[u][1];
-              }
-              count();
             }
           }
+          wt[u][0] = wt[u][1] = T(0);
+          if (ow[u] && lane < S) {
+            wt[u][0] = V.WK[aa[u] * S + lane];
+            wt[u][1] = V.WM[aa[u] * S + lane];
+          }
         }
-        __syncthreads();
-        // stage 2: w_k = K u_k on the own nodes, from the shared field and weights
-        for (int o = warp; o < NT; o += nw) {
-          const int ox = o % TX, oy = (o / TX) % TY, oz = o / (TX * TY);
-          const int gi = i0 + ox, gj = j0 + oy, gk = k0 + oz;
-          if (gi >= nn0 || gj >= nn1 || (D == 3 && gk >= nn2)) continue;
-          const long long a = gi + g.stride[1] * gj + (D == 3 ? g.stride[2] * gk : 0);
-          const int h = (ox + 1) + HX * ((oy + 1) + HY * (D == 3 ? oz + 1 : 0));
-          const T *sw = sW + o * 2 * S;
-          T yk[NJ], ym[NJ];
 #pragma unroll
-          for (int j = 0; j < NJ; ++j) yk[j] = ym[j] = T(0);
+        for (int u = 0; u < UB; ++u) {
+          const int h = h0 + u * nw;
+          if (h >= NH) continue;
+          T *su = smU + (size_t)h * NIP + lane;
+          if (!in[u]) {
 #pragma unroll
-          for (int s = 0; s < S; ++s) {
-            const T wk = sw[s], wm = sw[S + s];
-            if (s > 0 && wk == T(0) && wm == T(0)) continue;   // absent or Dirichlet neighbour
-            int dl[3];
-            slot_offset<D>(s, dl);
-            const T *su = smU + (size_t)(h + dl[0] + HX * (dl[1] + HY * dl[2])) * NIP + lane;
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-              if (!on[j]) continue;
-              const T uv = su[32 * j];
-              yk[j] = fma(wk, uv, yk[j]);
-              ym[j] = fma(wm, uv, ym[j]);
-            }
+            for (int j = 0; j < NJ; ++j) su[32 * j] = T(0);
+            continue;
           }
 #pragma unroll
           for (int j = 0; j < NJ; ++j) {
             if (!on[j]) continue;
-            const long long q = a * NIP + lane + 32 * j;
-            const T w_new = fma(kk[j], yk[j], w2[j] * ym[j]);
-            wn[q] = w_new;
-            cacc[1][j] = fma(w_new, smU[(size_t)h * NIP + lane + 32 * j], cacc[1][j]);
+            // s_{k-1} = w_{k-1} + b s_{k-2},  r_k = r_{k-1} - a s_{k-1},  u_k = D^{-1} r_k
+            const T sv = fma(be[j], sq[u][j], wq[u][j]);
+            const T rv = fma(-al[j], sv, rq[u][j]);
+            const T uv = dq[u][j] * rv;
+            su[32 * j] = uv;
+            if (ow[u]) {
+              const long long q = aa[u] * NIP + lane + 32 * j;
+              rn[q] = rv;
+              sn[q] = sv;
+              const T p_new = fma(be[j], pq[u][j], dq[u][j] * rq[u][j]);   // p_{k-1} = u_{k-1} + b p_{k-2}
+              V.x[q] = fma(al[j], p_new, xq[u][j]);                        // x_k = x_{k-1} + a p_{k-1}
+              V.p[q] = p_new;
+              cacc[0][j] = fma(rv, uv, cacc[0][j]);
+              if (F64) cacc[2][j] = fma(rv, rv, cacc[2][j]);
+            }
           }
-          count();
-        }
-        __syncthreads();   // the next tile overwrites the shared stencil field
-      }
-#pragma unroll
-      for (int c = 0; c < NC; ++c)
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) dacc[c][j] += (double)cacc[c][j];
-      if (!(ok = batch_allreduce<NC, NJ>(A, dacc, part, sh))) break;
-      ++sweeps;
-      ++applies;
-      int nan2 = 0, open2 = 0;
-      for (int t = threadIdx.x; t < NIP; t += blockDim.x) {
-        if (!sh.act[t]) continue;
-        const double gm = sh.tot[t], dl = sh.tot[NIP + t];
-        if (!isfinite(gm) || !isfinite(dl)) nan2 = 1;
-        if (k > 0) sh.iters[t] += 1;
-        if (k == 0) sh.gam0[t] = gm;
-        bool stop;
-        if (F64) stop = sh.tot[(NC - 1) * NIP + t] <= A.rtol2 * sh.bn2[t];
-        else stop = gm <= A.inner_rtol2 * sh.gam0[t];
-        stop = stop || gm == 0.0 || k >= A.inner_maxit || sweeps >= A.maxit;
-        double alpha = 0.0, beta = 0.0;
-        if (!stop) {
-          double den = dl;
-          if (k > 0) {
-            beta = gm / sh.gam[t];
-            den = dl - beta * gm / sh.alpha[t];
+          if (ow[u]) {
+            if (lane < S) {
+              sW[oo[u] * 2 * S + lane] = wt[u][0];
+              sW[oo[u] * 2 * S + S + lane] = wt[u][1];
+            }
+            count();
           }
-          if (!(den > 0.0)) stop = true;   // loss of positive definiteness in rounding
-          else alpha = gm / den;
-        }
-        if (stop) {
-          sh.act[t] = 0;
-          sh.alpha[t] = sh.beta[t] = 0.0;
-        } else {
-          sh.alpha[t] = alpha;
-          sh.beta[t] = beta;
-          sh.gam[t] = gm;
-          open2 = 1;
         }
       }
-      if (__syncthreads_or(nan2)) {
-        err = DEV_NAN;
-        ok = false;
-        break;
+      __syncthreads();
+      // stage 2: w_k = K u_k on the own nodes, from the shared field and weights
+      for (int o = warp; o < NT; o += nw) {
+        const int ox = o % TX, oy = (o / TX) % TY, oz = o / (TX * TY);
+        const int gi = i0 + ox, gj = j0 + oy, gk = k0 + oz;
+        if (gi >= nn0 || gj >= nn1 || (D == 3 && gk >= nn2)) continue;
+        const long long a = gi + g.stride[1] * gj + (D == 3 ? g.stride[2] * gk : 0);
+        const int h = (ox + 1) + HX * ((oy + 1) + HY * (D == 3 ? oz + 1 : 0));
+        const T *sw = sW + o * 2 * S;
+        T yk[NJ], ym[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) yk[j] = ym[j] = T(0);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const T wk = sw[s], wm = sw[S + s];
+          if (s > 0 && wk == T(0) && wm == T(0)) continue;   // absent or Dirichlet neighbour
+          int dl[3];
+          slot_offset<D>(s, dl);
+          const T *su = smU + (size_t)(h + dl[0] + HX * (dl[1] + HY * dl[2])) * NIP + lane;
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) {
+            if (!on[j]) continue;
+            const T uv = su[32 * j];
+            yk[j] = fma(wk, uv, yk[j]);
+            ym[j] = fma(wm, uv, ym[j]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          if (!on[j]) continue;
+          const long long q = a * NIP + lane + 32 * j;
+          const T w_new = fma(kk[j], yk[j], w2[j] * ym[j]);
+          wn[q] = w_new;
+          cacc[1][j] = fma(w_new, smU[(size_t)h * NIP + lane + 32 * j], cacc[1][j]);
+        }
+        count();
       }
-      if (!__syncthreads_or(open2)) break;
+      __syncthreads();   // the next tile overwrites the shared stencil field
     }
-    if (!ok) break;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) dacc[c][j] += (double)cacc[c][j];
+  };
+  // Per-instance test of the FP64 residual: converged, or at its rounding floor (two
+  // consecutive checks that fail to halve it: x is as accurate as FP64 allows).
+  auto check_residual = [&](bool first_check, int &nan, int &open) {
+    for (int t = threadIdx.x; t < NIP; t += blockDim.x) {
+      if (!sh.upd[t]) {
+        open |= sh.act[t];
+        continue;
+      }
+      const double rn2 = sh.tot[t];
+      if (first_check) sh.bn2[t] = sh.tot[NIP + t];
+      const double bn2 = sh.bn2[t];
+      if (!isfinite(rn2)) nan = 1;
+      const bool conv = rn2 <= A.rtol2 * bn2 || rn2 == 0.0;
+      const bool floor = rn2 > 0.25 * sh.rn2p[t] && sh.rn2p[t] > 0.25 * sh.rn2pp[t];
+      sh.res[t] = bn2 > 0.0 ? sqrt(rn2 / bn2) : sqrt(rn2);
+      sh.rn2pp[t] = sh.rn2p[t];
+      sh.rn2p[t] = rn2;
+      if (conv || floor) sh.done[t] = 1;
+      sh.act[t] = sh.done[t] ? 0 : 1;
+      if (sh.done[t]) sh.alpha[t] = sh.beta[t] = 0.0;
+      open |= sh.act[t];
+    }
+  };
+  int sweeps = 0, applies = 0, updates = 0, err = DEV_OK;
+  bool ok = true;
+  double red[2][NJ];
+  double dacc[3][NJ];
+  accumulate(true);
+  if (!(ok = grid_sync(A.bar))) goto finish;
+  residual(1, red);
+  if (!(ok = batch_allreduce<2, NJ>(A, red, part, sh))) goto finish;
+  ++applies;
+  {
+    int nan = 0, open = 0;
+    check_residual(true, nan, open);
+    for (int t = threadIdx.x; t < NIP; t += blockDim.x) sh.upd[t] = 0;
+    if (__syncthreads_or(nan)) {
+      err = DEV_NAN;
+      goto finish;
+    }
+    if (!__syncthreads_or(open)) goto finish;
   }
+  // Iterative refinement, per instance.  Each instance runs PCG on K d = r from d = 0 until
+  // its inner test holds -- FP64: ||r_k||_2 <= rtol ||b||_2 (the recurrence residual);
+  // mixed: (r_k, u_k) <= inner_rtol^2 (r_0, u_0) -- then its d is added to the FP64
+  // solution, the FP64 residual b - K x is formed and tested, and, unless it meets rtol (or
+  // has reached its rounding floor), the instance restarts PCG from it.  Each instance moves
+  // on its own schedule and its trajectory depends on its own data only; the others keep
+  // iterating meanwhile.
+  for (int k = 0;; ++k) {
+    sweep(k, dacc);
+    if (!(ok = batch_allreduce<3, NJ>(A, dacc, part, sh))) goto finish;
+    ++sweeps;
+    ++applies;
+    int nan2 = 0, running = 0, waiting = 0;
+    const bool at_cap = sweeps >= A.maxit;
+    for (int t = threadIdx.x; t < NIP; t += blockDim.x) {
+      if (!sh.act[t]) continue;
+      if (sh.upd[t]) {   // inner solve ended earlier: idles (frozen) until its refinement step
+        waiting += 1;
+        continue;
+      }
+      const double gm = sh.tot[t], dl = sh.tot[NIP + t];
+      if (!isfinite(gm) || !isfinite(dl)) nan2 = 1;
+      const int kl = sh.kloc[t];   // step of the instance's current inner solve
+      if (kl > 0) sh.iters[t] += 1;
+      if (kl == 0) sh.gref[t] = gm;
+      bool stop = F64 ? sh.tot[2 * NIP + t] <= A.rtol2 * sh.bn2[t] : gm <= A.inner_rtol2 * sh.gref[t];
+      stop = stop || !(gm > 0.0) || kl >= A.inner_maxit || at_cap;
+      // b = gamma_k / gamma_{k-1},  a = gamma_k / (delta_k - b gamma_k / a_{k-1})
+      double beta = 0.0, den = dl;
+      if (!stop && kl > 0) {
+        beta = gm / sh.gam[t];
+        den = dl - beta * gm / sh.alpha[t];
+      }
+      if (!(den > 0.0)) stop = true;   // breakdown in rounding: refine and restart
+      if (stop) {
+        sh.alpha[t] = sh.beta[t] = 0.0;
+        sh.upd[t] = 1;
+        waiting += 1;
+      } else {
+        sh.alpha[t] = gm / den;
+        sh.beta[t] = beta;
+        sh.gam[t] = gm;
+        sh.kloc[t] = kl + 1;
+        running += 1;
+      }
+    }
+    if (__syncthreads_or(nan2)) {
+      err = DEV_NAN;
+      goto finish;
+    }
+    // Refinement steps are grouped: one FP64 residual pass serves every waiting instance, and
+    // it runs once a quarter of the active instances wait or nothing else iterates.  Waiting
+    // changes no instance's state, so the grouping does not change any result.
+    const int nrun = __syncthreads_count(running), nwait = __syncthreads_count(waiting);
+    if (nwait == 0 || (nrun > 0 && 4 * nwait < nrun + nwait && !at_cap)) continue;
+    // refinement step of the instances whose inner solve ended
+    accumulate(false);
+    if (!(ok = grid_sync(A.bar))) goto finish;
+    residual(k & 1, red);
+    if (!(ok = batch_allreduce<2, NJ>(A, red, part, sh))) goto finish;
+    ++applies;
+    ++updates;
+    int nan = 0, open = 0;
+    check_residual(false, nan, open);
+    for (int t = threadIdx.x; t < NIP; t += blockDim.x)
+      if (sh.upd[t]) {
+        sh.kloc[t] = 0;
+        sh.upd[t] = 0;
+      }
+    if (__syncthreads_or(nan)) {
+      err = DEV_NAN;
+      goto finish;
+    }
+    if (!__syncthreads_or(open)) break;
+    if (at_cap) {
+      err = DEV_NOCONV;
+      break;
+    }
+  }
+finish:
   if (blockIdx.x == 0) {
     if (threadIdx.x == 0) {
       A.status[DS_ITERS] = sweeps;
       A.status[DS_APPLIES] = applies;
-      A.status[DS_FLAG] = outer;
+      A.status[DS_FLAG] = updates;
       if (err != DEV_OK) atomicCAS(A.status + DS_ERR, DEV_OK, err);
     }
     for (int t = threadIdx.x; t < NIP; t += blockDim.x) {
@@ -905,7 +974,7 @@ static size_t batch_scratch_bytes(long long nn, int nip, int grid) {
 
 template <typename T>
 static fo_status batch_launch_t(fo_problem *p, const double *B, double bscale, double *X, const fo_solve_opts *o,
-                                int max_outer, const BatchLaunch &L, int warm) {
+                                const BatchLaunch &L, int warm) {
   fo_batch *bt = p->batch;
   fo_ctx *ctx = p->ctx;
   const Grid &g = p->mesh->g;
@@ -932,7 +1001,6 @@ static fo_status batch_launch_t(fo_problem *p, const double *B, double bscale, d
   A.inner_rtol2 = o->inner_rtol * o->inner_rtol;
   A.maxit = o->maxit;
   A.inner_maxit = std::is_same<T, double>::value ? o->maxit : o->inner_maxit;
-  A.max_outer = max_outer;
   A.warm = warm;
   T *v = (T *)(A.totals + 3 * nip);
   const size_t n = (size_t)nn * nip;
@@ -965,9 +1033,9 @@ static fo_status batch_launch_t(fo_problem *p, const double *B, double bscale, d
 }
 
 static fo_status batch_dispatch(fo_problem *p, int precision, const double *B, double bscale, double *X,
-                                const fo_solve_opts *o, int max_outer, const BatchLaunch &L, int warm) {
-  if (precision == FO_MIXED) return batch_launch_t<float>(p, B, bscale, X, o, max_outer, L, warm);
-  return batch_launch_t<double>(p, B, bscale, X, o, max_outer, L, warm);
+                                const fo_solve_opts *o, const BatchLaunch &L, int warm) {
+  if (precision == FO_MIXED) return batch_launch_t<float>(p, B, bscale, X, o, L, warm);
+  return batch_launch_t<double>(p, B, bscale, X, o, L, warm);
 }
 
 static long long batch_ntiles(const Grid &g, const BatchKernel &k) {
@@ -1072,7 +1140,7 @@ extern "C" fo_status fo_batch_autotune(fo_problem *p, int precision, fo_tune_res
         float ms = 0;
         for (int rep = 0; rep < 2 && st == FO_OK; ++rep) {
           cudaEventRecord(e0, ctx->stream);
-          st = batch_dispatch(p, precision, bt->B, 1.0, X, &o, 1, L, 0);
+          st = batch_dispatch(p, precision, bt->B, 1.0, X, &o, L, 0);
           cudaEventRecord(e1, ctx->stream);
           if (st == FO_OK) {
             fo_status r = batch_read(p, nullptr, &o);
@@ -1119,9 +1187,8 @@ fo_status fo_batch_state(fo_problem *p, bool adjoint, const fo_solve_opts *o, fo
   if (o->grid_blocks <= 0 && bt->tuned_block[prec == FO_MIXED ? 1 : 0] == 0) FO_TRY(fo_batch_autotune(p, prec, nullptr));
   BatchLaunch L;
   FO_TRY(batch_shape(p, prec, o->grid_blocks, &L));
-  const int max_outer = prec == FO_MIXED ? 60 : 4;
   double *X = adjoint ? bt->P : bt->U;
-  FO_TRY(batch_dispatch(p, prec, bt->B, adjoint ? -1.0 : 1.0, X, o, max_outer, L, adjoint ? 0 : o->warm_start));
+  FO_TRY(batch_dispatch(p, prec, bt->B, adjoint ? -1.0 : 1.0, X, o, L, adjoint ? 0 : o->warm_start));
   fo_solve_stats s;
   memset(&s, 0, sizeof s);
   fo_status r = batch_read(p, &s, o);
