@@ -224,6 +224,9 @@ FO_API fo_status fo_set_levelset(fo_problem *prob, const double *phi, int on_dev
  * ord = 2 or 0 (0 means the infinity norm); centers [count][d] and radii on the host. */
 FO_API fo_status fo_initial_level(fo_problem *prob, int count, const double *centers, const double *radii,
                            double factor, int ord);
+/* Random-bump level set: phi(x) = sum_k exp(-|x - c_k|^2 / (2 width^2)) - offset, terms
+ * added in k order; centers [count][d] on the host (the bumps are the holes of Omega). */
+FO_API fo_status fo_levelset_bumps(fo_problem *prob, int count, const double *centers, double width, double offset);
 /* Element coefficient A_e and chi_e from phi (one-point rule: the vertex values of phi
  * summed in vertex order; < 0 is inside, eqs heat_AOmega / compli_AOmega). */
 FO_API fo_status fo_coefficients(fo_problem *prob);
@@ -307,6 +310,77 @@ typedef struct {
  * loads, writing a scratch solution only.  The fastest shape is kept on the problem and used
  * by later solves whose opts->grid_blocks is 0; the first such solve tunes by itself. */
 FO_API fo_status fo_batch_autotune(fo_problem *prob, int precision, fo_tune_result *out);
+
+/* --------------------------------------------------------------- serving ----- */
+/* A request is one Algorithm-1 step without the transport (state solve, explicit adjoint
+ * solve, cost and constraint, shape derivative, velocity) on its own box mesh.  A server
+ * runs `executors` requests at once, each on its own context and CUDA stream, so that the
+ * device work of different requests overlaps; requests wait in a FIFO queue and are admitted
+ * in order when an executor is free and the in-flight requests' device memory plus theirs
+ * fits in mem_budget.  A request's memory estimate is exact for the library's allocations
+ * (fo_request_device_bytes).  The device work of a request is the same whether it runs
+ * alone or in a mix (same kernels, launch shapes and reduction order), so its results are
+ * the same bits. */
+typedef struct {
+  int dim;                  /* 2 or 3                                                   */
+  int n[3];                 /* cells per axis                                           */
+  double lo[3], hi[3];      /* box                                                      */
+  fo_model_desc model;      /* FO_HEAT or FO_ELASTIC (batches are not served); f_nodal  */
+                            /* (N_n values) is copied at submit                         */
+  int n_bumps;              /* > 0: phi = sum of Gaussian bumps - offset (fo_levelset_bumps) */
+  const double *bump_centers; /* [n_bumps][dim], copied at submit                       */
+  double bump_width, bump_offset;
+  const double *phi;        /* n_bumps == 0: N_n nodal level set, copied at submit      */
+  double lambda;            /* multiplier of the volume term in S                       */
+  fo_solve_opts state;      /* state and adjoint solves                                 */
+  fo_solve_opts velocity;
+  double *theta_out;        /* optional host array of d*N_n, written before completion; */
+                            /* it must stay valid until the request completes           */
+} fo_request;
+
+typedef struct {
+  fo_status status;         /* FO_OK, FO_ENOCONV (results written), or the failing call's */
+  char message[128];        /* fo_last_error text of a failing call                     */
+  double J, C, Btt;         /* cost, constraint, B(theta, theta)                        */
+  fo_solve_stats state, adjoint, velocity;
+  int64_t dofs;             /* N_dof of the state                                       */
+  size_t device_bytes;      /* the admission estimate                                   */
+  double submit_ms, start_ms, end_ms;   /* host steady clock, ms since server creation  */
+} fo_result;
+
+typedef struct {
+  int executors;            /* requests in flight at once (default 8)                   */
+  size_t mem_budget;        /* device bytes in-flight requests may hold (default 8 GiB) */
+  int queue_capacity;       /* queued requests before fo_submit says FO_EBUSY (4096)    */
+  double dry_run_ms;        /* > 0: executors sleep this long instead of any device    */
+                            /* work (tests of queueing and admission without a GPU)     */
+} fo_server_opts;
+
+typedef struct {
+  int64_t submitted, completed, failed, rejected;
+  int64_t peak_in_flight;   /* most requests running at once                           */
+  size_t peak_bytes;        /* most admitted device memory at once                     */
+} fo_server_stats;
+
+typedef struct fo_server fo_server;
+FO_API void fo_server_opts_default(fo_server_opts *o);
+/* Device memory the library allocates for a request (mesh, problem fields, solver scratch). */
+FO_API size_t fo_request_device_bytes(const fo_request *rq);
+/* The server's executors use ctx's device; ctx receives create-time errors only (it may be
+ * NULL for a dry-run server).  Destroy the server only when no other thread waits on it. */
+FO_API fo_status fo_server_create(fo_ctx *ctx, const fo_server_opts *opts, fo_server **out);
+/* Stops admitting, cancels queued requests (FO_ESTATE), waits for the running ones. */
+FO_API fo_status fo_server_destroy(fo_server *srv);
+/* Queue a request; its host arrays are copied.  FO_EBUSY when the queue is full,
+ * FO_ENOMEM_BUDGET when it alone needs more than mem_budget, FO_EINVAL on a bad request. */
+FO_API fo_status fo_submit(fo_server *srv, const fo_request *rq, uint64_t *ticket);
+/* Non-blocking: *done = 1 and *res filled once the request has completed. */
+FO_API fo_status fo_poll(fo_server *srv, uint64_t ticket, fo_result *res, int *done);
+/* Wait at most timeout_s seconds: FO_ETIMEOUT if the request has not completed by then. */
+FO_API fo_status fo_wait(fo_server *srv, uint64_t ticket, double timeout_s, fo_result *res);
+/* Forget a completed request (its result is no longer kept). */
+FO_API fo_status fo_release(fo_server *srv, uint64_t ticket);
+FO_API fo_status fo_server_get_stats(fo_server *srv, fo_server_stats *out);
 
 /* ------------------------------------------------------------- host-only ----- */
 /* PPL state with r = 0.999, delta0 = 0.5, alpha = 2000, beta = 0.5, z = lambda = mu = 0. */

@@ -55,6 +55,31 @@ class SolveStats(C.Structure):
                 ("rel_residual", C.c_double)]
 
 
+class Request(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("model", ModelDesc), ("n_bumps", C.c_int), ("bump_centers", C.POINTER(C.c_double)),
+                ("bump_width", C.c_double), ("bump_offset", C.c_double), ("phi", C.POINTER(C.c_double)),
+                ("lam", C.c_double), ("state", SolveOpts), ("velocity", SolveOpts),
+                ("theta_out", C.POINTER(C.c_double))]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("message", C.c_char * 128), ("J", C.c_double), ("C", C.c_double),
+                ("Btt", C.c_double), ("state", SolveStats), ("adjoint", SolveStats), ("velocity", SolveStats),
+                ("dofs", C.c_int64), ("device_bytes", C.c_size_t), ("submit_ms", C.c_double),
+                ("start_ms", C.c_double), ("end_ms", C.c_double)]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("executors", C.c_int), ("mem_budget", C.c_size_t), ("queue_capacity", C.c_int),
+                ("dry_run_ms", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("rejected", C.c_int64),
+                ("peak_in_flight", C.c_int64), ("peak_bytes", C.c_size_t)]
+
+
 class RunOptions(C.Structure):
     _fields_ = [("dfactor", C.c_double), ("t_min", C.c_double), ("t_max", C.c_double), ("s_min", C.c_int),
                 ("s_max", C.c_int), ("smooth", C.c_int), ("reinit_step", C.c_int), ("reinit_steps", C.c_int),
@@ -114,6 +139,16 @@ PROTOTYPES = {
     "fo_get": (ST, [VP, C.c_int, VP]),
     "fo_set": (ST, [VP, C.c_int, VP, C.c_int]),
     "fo_apply": (ST, [VP, C.c_int, VP, VP, C.c_int]),
+    "fo_levelset_bumps": (ST, [VP, C.c_int, DP, C.c_double, C.c_double]),
+    "fo_server_opts_default": (None, [C.POINTER(ServerOpts)]),
+    "fo_request_device_bytes": (C.c_size_t, [C.POINTER(Request)]),
+    "fo_server_create": (ST, [VP, C.POINTER(ServerOpts), C.POINTER(VP)]),
+    "fo_server_destroy": (ST, [VP]),
+    "fo_submit": (ST, [VP, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    "fo_poll": (ST, [VP, C.c_uint64, C.POINTER(Result), C.POINTER(C.c_int)]),
+    "fo_wait": (ST, [VP, C.c_uint64, C.c_double, C.POINTER(Result)]),
+    "fo_release": (ST, [VP, C.c_uint64]),
+    "fo_server_get_stats": (ST, [VP, C.POINTER(ServerStats)]),
     "fo_batch_costs": (ST, [VP, DP]),
     "fo_batch_solve_info": (ST, [VP, C.POINTER(C.c_int), DP]),
     "fo_batch_autotune": (ST, [VP, C.c_int, C.POINTER(TuneResult)]),

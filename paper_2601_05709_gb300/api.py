@@ -352,3 +352,109 @@ def adaptime(Btt, opts=None):
     t, n = C.c_double(), C.c_int()
     lib.fo_adaptime(Btt, C.byref(opts), C.byref(t), C.byref(n))
     return t.value, n.value
+
+
+# ------------------------------------------------------------------------------ serving
+class ServedRequest:
+    """A request for Server.submit: one optimisation step (state, explicit adjoint, cost,
+    shape derivative, velocity) on its own box mesh.  `desc` is a model_desc (FO_HEAT or
+    FO_ELASTIC); the level set is Gaussian bumps (centers [k, dim]) or nodal values phi."""
+
+    def __init__(self, dim, n, desc, lo=None, hi=None, centers=None, width=0.1, offset=0.2, phi=None, lam=0.0,
+                 state=None, velocity=None, want_theta=False):
+        r = _lib.Request()
+        r.dim = dim
+        for a in range(3):
+            r.n[a] = int(n[a]) if a < dim else 1
+            r.lo[a] = (lo[a] if lo is not None else 0.0) if a < dim else 0.0
+            r.hi[a] = (hi[a] if hi is not None else 1.0) if a < dim else 1.0
+        r.model = desc
+        self._keep = [desc]
+        if centers is not None:
+            c = _f64(centers).reshape(-1)
+            r.n_bumps = len(c) // dim
+            r.bump_centers = _dp(c)
+            r.bump_width, r.bump_offset = width, offset
+            self._keep.append(c)
+        else:
+            ph = _f64(phi)
+            r.phi = _dp(ph)
+            self._keep.append(ph)
+        r.lam = lam
+        r.state = state if state is not None else solve_opts()
+        r.velocity = velocity if velocity is not None else solve_opts()
+        nn = int(np.prod([int(n[a]) + 1 for a in range(dim)]))
+        self.theta = np.empty(dim * nn) if want_theta else None
+        if want_theta:
+            r.theta_out = _dp(self.theta)
+        self.struct = r
+
+    def device_bytes(self):
+        return int(_lib.load().fo_request_device_bytes(C.byref(self.struct)))
+
+
+class Server:
+    """Continuous-batching request server (fo_server_*): FIFO admission by device memory,
+    `executors` requests in flight on their own streams."""
+
+    def __init__(self, ctx=None, executors=8, mem_budget=8 << 30, queue_capacity=4096, dry_run_ms=0.0):
+        self.lib = _lib.load()
+        o = _lib.ServerOpts()
+        self.lib.fo_server_opts_default(C.byref(o))
+        o.executors, o.mem_budget, o.queue_capacity, o.dry_run_ms = executors, mem_budget, queue_capacity, dry_run_ms
+        h = C.c_void_p()
+        st = self.lib.fo_server_create(ctx.handle if ctx is not None else None, C.byref(o), C.byref(h))
+        if st != FO_OK:
+            raise FormoptError(st, "fo_server_create failed")
+        self.handle = h
+        self._pending = {}          # ticket -> request (keeps its output array alive)
+
+    def submit(self, req):
+        """Returns (status, ticket); status FO_EBUSY / FO_ENOMEM_BUDGET / FO_EINVAL leave no ticket."""
+        t = C.c_uint64()
+        st = self.lib.fo_submit(self.handle, C.byref(req.struct), C.byref(t))
+        if st == FO_OK:
+            self._pending[t.value] = req
+            return st, t.value
+        return st, None
+
+    def poll(self, ticket):
+        r = _lib.Result()
+        done = C.c_int()
+        st = self.lib.fo_poll(self.handle, ticket, C.byref(r), C.byref(done))
+        if st != FO_OK:
+            raise FormoptError(st, "fo_poll")
+        return bool(done.value), (r if done.value else None)
+
+    def wait(self, ticket, timeout_s=60.0):
+        """The result, or None when the request has not completed within timeout_s."""
+        r = _lib.Result()
+        st = self.lib.fo_wait(self.handle, ticket, float(timeout_s), C.byref(r))
+        if st == _lib.FO_ETIMEOUT:
+            return None
+        if st != FO_OK:
+            raise FormoptError(st, "fo_wait")
+        return r
+
+    def release(self, ticket):
+        st = self.lib.fo_release(self.handle, ticket)
+        if st != FO_OK:
+            raise FormoptError(st, "fo_release")
+        self._pending.pop(ticket, None)
+
+    def stats(self):
+        s = _lib.ServerStats()
+        self.lib.fo_server_get_stats(self.handle, C.byref(s))
+        return s
+
+    def close(self):
+        if self.handle:
+            self.lib.fo_server_destroy(self.handle)
+            self.handle = None
+            self._pending.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -245,28 +245,60 @@ extern "C" fo_status fo_mesh_copy_out(const fo_mesh *m, int32_t *cells, double *
 }
 
 // ------------------------------------------------------------------------------- problem
+// Sizes of a problem's device fields, in the order of prob_bytes_fields.
+static std::vector<size_t> problem_field_sizes(int d, long long NN, long long NT, long long ND, bool with_f) {
+  const size_t S = (d == 2) ? 7 : 15;
+  std::vector<size_t> v = {
+      sizeof(double) * NN,     sizeof(double) * NT,     sizeof(float) * NT,       (size_t)NT,
+      (size_t)NT,              (size_t)ND,              (size_t)NN,               sizeof(double) * ND,
+      sizeof(double) * ND,     sizeof(double) * ND,     sizeof(double) * d * NN,  sizeof(double) * d * NN,
+      sizeof(double) * ND,     sizeof(float) * ND,      sizeof(double) * d * NN,  sizeof(double) * S * NN,
+      sizeof(double) * S * NN, sizeof(double) * NN,     sizeof(double) * FO_RED_DOUBLES,
+      64,                      sizeof(int) * DS_COUNT,
+  };
+  if (with_f) v.push_back(sizeof(double) * NN);
+  return v;
+}
+
 static size_t prob_bytes_fields(const fo_problem *p, std::vector<std::pair<void **, size_t>> &list) {
   const Grid &g = p->mesh->g;
-  const long long NN = g.num_nodes, NT = g.num_elems, ND = p->ndof;
-  const int d = g.dim;
-  const int S = (d == 2) ? 7 : 15;
-  list = {
-      {(void **)&p->phi, sizeof(double) * NN},       {(void **)&p->coef, sizeof(double) * NT},
-      {(void **)&p->coef32, sizeof(float) * NT},     {(void **)&p->chi, NT},
-      {(void **)&p->omega0, NT},                     {(void **)&p->dir, ND},
-      {(void **)&p->vdir, NN},                       {(void **)&p->load, sizeof(double) * ND},
-      {(void **)&p->u, sizeof(double) * ND},         {(void **)&p->p, sizeof(double) * ND},
-      {(void **)&p->rhs, sizeof(double) * d * NN},   {(void **)&p->theta, sizeof(double) * d * NN},
-      {(void **)&p->dinv_state, sizeof(double) * ND}, {(void **)&p->dinv_state32, sizeof(float) * ND},
-      {(void **)&p->dinv_vel, sizeof(double) * d * NN}, {(void **)&p->L, sizeof(double) * S * NN},
-      {(void **)&p->R, sizeof(double) * S * NN},     {(void **)&p->dinvL, sizeof(double) * NN},
-      {(void **)&p->red, sizeof(double) * FO_RED_DOUBLES},
-      {(void **)&p->bar, 64},                        {(void **)&p->dev_status, sizeof(int) * DS_COUNT},
+  const std::vector<size_t> sz =
+      problem_field_sizes(g.dim, g.num_nodes, g.num_elems, p->ndof, p->f || p->desc.kind != FO_ELASTIC);
+  std::vector<void **> ptr = {
+      (void **)&p->phi,        (void **)&p->coef,         (void **)&p->coef32,       (void **)&p->chi,
+      (void **)&p->omega0,     (void **)&p->dir,          (void **)&p->vdir,         (void **)&p->load,
+      (void **)&p->u,          (void **)&p->p,            (void **)&p->rhs,          (void **)&p->theta,
+      (void **)&p->dinv_state, (void **)&p->dinv_state32, (void **)&p->dinv_vel,     (void **)&p->L,
+      (void **)&p->R,          (void **)&p->dinvL,        (void **)&p->red,
+      (void **)&p->bar,        (void **)&p->dev_status,
   };
-  if (p->f || p->desc.kind != FO_ELASTIC) list.push_back({(void **)&p->f, sizeof(double) * NN});
+  if (sz.size() > ptr.size()) ptr.push_back((void **)&p->f);
+  list.clear();
   size_t s = 0;
-  for (auto &e : list) s += e.second;
+  for (size_t i = 0; i < sz.size(); ++i) {
+    list.push_back({ptr[i], sz[i]});
+    s += sz[i];
+  }
   return s;
+}
+
+// Device bytes allocated for a box mesh and a single (non-batch) problem on it, with the
+// largest solver scratch of its state / adjoint (precision) and velocity solves and the
+// transient bump-centre array; what a served request holds at most.
+size_t fo_problem_footprint(int dim, const int n[3], int kind, int precision, int n_bumps) {
+  long long NN = 1, cells = 1;
+  for (int a = 0; a < dim; ++a) {
+    NN *= (long long)n[a] + 1;
+    cells *= n[a];
+  }
+  const long long NT = cells * (dim == 2 ? 2 : 6);
+  const long long ND = NN * (kind == FO_ELASTIC ? dim : 1);
+  size_t total = sizeof(int32_t) * NT * (dim + 1) + sizeof(double) * NN * dim;   // mesh
+  for (size_t b : problem_field_sizes(dim, NN, NT, ND, kind != FO_ELASTIC)) total += b;
+  const size_t state = sizeof(double) * (precision == FO_MIXED ? 11 : 8) * (size_t)ND;
+  const size_t vel = sizeof(double) * 8 * (size_t)dim * NN;
+  const size_t bumps = sizeof(double) * (size_t)std::max(n_bumps, 0) * dim;
+  return total + std::max(std::max(state, vel), bumps);
 }
 
 extern "C" fo_status fo_problem_destroy(fo_problem *p) {
@@ -375,6 +407,13 @@ extern "C" fo_status fo_initial_level(fo_problem *p, int count, const double *ce
   if (!p || count < 1 || !centers || !radii || (ord != 2 && ord != 0)) return FO_EINVAL;
   p->coef_valid = false;
   return fo_launch_initial_level(p, count, centers, radii, factor, ord);
+}
+
+extern "C" fo_status fo_levelset_bumps(fo_problem *p, int count, const double *centers, double width,
+                                       double offset) {
+  if (!p || count < 1 || !centers || !(width > 0)) return FO_EINVAL;
+  p->coef_valid = false;
+  return fo_launch_phi_bumps(p, count, centers, width, offset);
 }
 
 extern "C" fo_status fo_coefficients(fo_problem *p) {

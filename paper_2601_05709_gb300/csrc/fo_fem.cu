@@ -714,3 +714,41 @@ fo_status fo_launch_initial_level(fo_problem *p, int count, const double *center
   fo_free(ctx, d_cr, sizeof(double) * cr.size());
   return st;
 }
+
+// ------------------------------------------------------------------ Gaussian-bump level set
+// phi(x) = sum_k exp(-|x - c_k|^2 / (2 width^2)) - offset, the terms added in k order
+// (the random-bump initial shapes of the 3D and serving workloads).
+__global__ void k_phi_bumps(int dim, long long nn, const double *coords, int count, const double *c, double inv2w2,
+                            double offset, double *phi) {
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < nn; a += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < count; ++k) {
+      double d2 = 0.0;
+      for (int j = 0; j < dim; ++j) {
+        const double d = coords[a * dim + j] - c[k * dim + j];
+        d2 += d * d;
+      }
+      s += exp(-d2 * inv2w2);
+    }
+    phi[a] = s - offset;
+  }
+}
+
+fo_status fo_launch_phi_bumps(fo_problem *p, int count, const double *centers, double width, double offset) {
+  const Grid &g = p->mesh->g;
+  fo_ctx *ctx = p->ctx;
+  const size_t nc = (size_t)count * g.dim;
+  double *d_c;
+  FO_TRY(fo_alloc(ctx, (void **)&d_c, sizeof(double) * nc));
+  fo_status st = fo_cuda_check(ctx, cudaMemcpyAsync(d_c, centers, sizeof(double) * nc, cudaMemcpyHostToDevice,
+                                                    ctx->stream), "copy bump centres");
+  if (st == FO_OK) {
+    k_phi_bumps<<<fo_blocks_for(g.num_nodes, FO_BLOCK, 65536), FO_BLOCK, 0, ctx->stream>>>(
+        g.dim, g.num_nodes, p->mesh->d_coords, count, d_c, 1.0 / (2.0 * width * width), offset, p->phi);
+    fo_note_launch(1);
+    st = fo_cuda_check(ctx, cudaGetLastError(), "bump level set");
+  }
+  if (st == FO_OK) st = fo_cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "bump level set sync");
+  fo_free(ctx, d_c, sizeof(double) * nc);
+  return st;
+}

@@ -359,6 +359,8 @@ fo_status fo_launch_velocity_apply(fo_problem *p, const double *x, double *y);
 fo_status fo_launch_functionals(fo_problem *p, double *J, double *vol);
 fo_status fo_launch_shape_rhs(fo_problem *p, double lambda);
 fo_status fo_launch_mesh_build(fo_mesh *m);
+size_t fo_problem_footprint(int dim, const int n[3], int kind, int precision, int n_bumps);
+fo_status fo_launch_phi_bumps(fo_problem *p, int count, const double *centers, double width, double offset);
 fo_status fo_launch_initial_level(fo_problem *p, int count, const double *centers, const double *radii,
                                   double factor, int ord);
 fo_status fo_state_pcg(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st);
