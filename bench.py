@@ -13,6 +13,18 @@ iterations of the workload).  Reinitialisation is not inside these iterations (o
 its scheme is unstable for the transported level sets, in the oracle as on the GPU); one
 reinitialisation of the final level set (20 steps, pseudo-time 0.02) is timed separately.
 
+Two more workloads are measured in the same run and reported as objects of the same line:
+  batch   -- 64 screened Helmholtz instances (k_i ~ U[0.5, 2], omega_i ~ U[0, 5], seeded
+             8-mode Fourier sources) on one 512 x 512 Kuhn mesh of the unit square sharing
+             phi0 = cos(4 pi x) cos(4 pi y) + 0.3: the batched state solve to a relative
+             FP64 residual of 1e-8 (FP32 inner PCG + FP64 refinement, and FP64), the summed
+             shape derivative and one velocity solve, against the plain FP64 solves of the same
+             instances one at a time;
+  serving -- a seeded sample of the request stream (exponential inter-arrivals of mean 5 ms;
+             2D n ~ exp U[ln 64, ln 1024] or 3D n ~ exp U[ln 32, ln 96] cells per axis; heat or
+             elasticity; 20 Gaussian bumps) served with 8 concurrent executors and FP32 inner
+             solves, against the same requests run one after another in FP64.
+
 Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead (on the host
 cores, a bounded sample of the same iterations).  Multi-GPU (torchrun): every rank runs an
 independent replica of the workload (the step does not shard); rank 0 prints.
@@ -46,6 +58,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--l2-flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=12)
+    ap.add_argument("--batch-n", type=int, default=512, help="cells per axis of the batch mesh")
+    ap.add_argument("--batch-maxit", type=int, default=400000, help="cap on batched iterations (profiling runs)")
+    ap.add_argument("--batch-only", action="store_true", help="run the batch leg only (profiling)")
     return ap.parse_args()
 
 
@@ -169,6 +187,13 @@ print(json.dumps({{"times": times[{warm}:], "J": log["J"]}}))
 
 def cpu_model():
     try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
         for ln in open("/proc/cpuinfo"):
             if ln.lower().startswith(("model name", "cpu model")):
                 return ln.split(":", 1)[1].strip()
@@ -197,6 +222,152 @@ def run_reference(args, rank, world):
         "e2e": {"value": value, "unit": "opt-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------ batch (c4)
+BATCH_N, BATCH_INST = 512, 64
+
+
+def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True):
+    """Batched vs one-at-a-time state solves of the 64-instance Helmholtz family, to a relative
+    FP64 residual of 1e-8; then the summed shape derivative and one velocity solve."""
+    import numpy as np
+    import torch
+    from paper_2601_05709_gb300 import workloads
+    mesh = ctx.mesh_box(2, (n, n), (0.0, 0.0), (1.0, 1.0))
+    _, coords = mesh.copy_out()
+    k, om, amp = workloads.batch_parameters(BATCH_INST, 1)
+    f = workloads.fourier_loads(coords, amp)
+    phi = workloads.phi_cos(coords)
+    desc = api.model_desc(api.FO_HELMHOLTZ, a_in=1.0, a_out=1e-3, dirichlet=[(0, 0)], alpha_mass=0.01,
+                          velocity_dirichlet=True, inst_k=k, inst_omega=om, inst_f=f)
+    prob = mesh.problem(desc)
+    prob.set_levelset(phi)
+    prob.coefficients()
+    nfree = mesh.num_nodes - (n + 1)
+    out = {"workload": f"{BATCH_INST} screened Helmholtz instances on a {n}x{n} Kuhn mesh "
+                       f"({2 * n * n} triangles, {mesh.num_nodes} nodes), ersatz 1e-3, Dirichlet x=0",
+           "rtol": 1e-8}
+    tune = {}
+    for prec, name in ((api.FO_MIXED, "mixed"), (api.FO_FP64, "fp64")):
+        r = prob.batch_autotune(prec)
+        tune[name] = {"tile": list(r.tile), "block": r.block, "blocks_per_sm": r.blocks_per_sm,
+                      "us_per_iteration_all_active": r.us_per_iteration, "candidates": r.candidates}
+    out["autotune"] = tune
+    for prec, name in ((api.FO_MIXED, "mixed"), (api.FO_FP64, "fp64")):
+        prob.set(api.FO_FIELD_U, np.zeros((mesh.num_nodes, BATCH_INST)))
+        o = api.solve_opts(precision=prec, rtol=1e-8, inner_rtol=1e-3, maxit=maxit, inner_maxit=100000)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = prob.state_solve(o, allow_noconv=maxit < 400000)
+        dt = time.perf_counter() - t0
+        its, res = prob.batch_solve_info()
+        out["batched_" + name] = {
+            "seconds": dt, "sweeps": st.iterations, "refinement_passes": st.outer_iterations,
+            "inst_iterations": {"min": int(its.min()), "mean": float(its.mean()), "max": int(its.max())},
+            "max_rel_residual": float(res.max()),
+            "gdof_iters_per_s": nfree * float(its.sum()) / dt / 1e9}
+    # summed tensors and the velocity solve (the rest of a batched step without transport)
+    t0 = time.perf_counter()
+    J, C = prob.functionals()
+    prob.shape_derivative(0.0, copy=False)
+    Btt, vst = prob.descent(api.solve_opts(rtol=1e-8))
+    out["shape_and_velocity_seconds"] = time.perf_counter() - t0
+    out["J"] = J
+    # plain FP64 one instance at a time (the single-problem path of the same library)
+    tot_t, tot_it = 0.0, 0
+    for i in range(BATCH_INST if plain else 0):
+        p1 = mesh.problem(api.model_desc(api.FO_HELMHOLTZ, a_in=1.0, a_out=1e-3, k=k[i], omega=om[i],
+                                         dirichlet=[(0, 0)], f_nodal=f[i]))
+        p1.set_levelset(phi)
+        p1.coefficients()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s1 = p1.state_solve(api.solve_opts(rtol=1e-8, maxit=400000))
+        tot_t += time.perf_counter() - t0
+        tot_it += s1.iterations
+        p1.close()
+    if plain:
+        out["plain_fp64_one_at_a_time"] = {"seconds": tot_t, "iterations": tot_it,
+                                           "gdof_iters_per_s": nfree * tot_it / tot_t / 1e9}
+        out["speedup_time_to_solution_mixed_vs_plain"] = tot_t / out["batched_mixed"]["seconds"]
+    # roofline of the batched FP32 sweep: per DOF and iteration it moves r, w, s, D^{-1}, p, x
+    # in and r, w, s, p, x out (11 x 4 bytes), measured with every instance active (autotune)
+    us = tune["mixed"]["us_per_iteration_all_active"]
+    achieved = 44.0 * mesh.num_nodes * 64 / (us * 1e-6) / 1e9
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out["roofline"] = {"bound": "hbm", "kernel": "k_batch_solve<2, 2, float, tile>", "achieved": achieved,
+                       "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                       "note": "algorithmic 44 B per DOF-iteration; the tuning run's time per iteration "
+                               "includes its two FP64 residual passes"}
+    prob.close()
+    mesh.close() if hasattr(mesh, "close") else None
+    return out
+
+
+# ---------------------------------------------------------------------- serving (c5)
+def serving_stream(count, seed=2):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out, t = [], 0.0
+    for rid in range(count):
+        t += rng.exponential(5.0)
+        dim = 2 if rng.random() < 0.5 else 3
+        if dim == 2:
+            n = int(round(np.exp(rng.uniform(np.log(64), np.log(1024)))))
+        else:
+            n = int(round(np.exp(rng.uniform(np.log(32), np.log(96)))))
+        heat = rng.random() < 0.5
+        centers = np.random.default_rng(rid).random((20, dim))
+        out.append((t, dim, n, heat, centers))
+    return out
+
+
+def bench_serving(api, ctx, count):
+    import numpy as np
+    items = serving_stream(count)
+
+    def desc(dim, n, heat):
+        if heat:
+            return api.model_desc(api.FO_HEAT, dirichlet=[(0, 0)], alpha_mass=0.01, velocity_dirichlet=True,
+                                  f_nodal=np.ones((n + 1) ** dim))
+        vec = (0.0, -1.0) if dim == 2 else (0.0, 0.0, -1.0)
+        return api.model_desc(api.FO_ELASTIC, dirichlet=[(0, 0)], tractions=[(0, 1, vec)], alpha_mass=0.1,
+                              normal_penalty=1e4)
+
+    def run(executors, prec, pace):
+        srv = api.Server(ctx, executors=executors, mem_budget=8 << 30)
+        tickets = []
+        t0 = time.perf_counter()
+        for (ta, dim, n, heat, centers) in items:
+            if pace:
+                d = t0 + ta / 1000.0 - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+            r = api.ServedRequest(dim, (n,) * dim, desc(dim, n, heat), centers=centers, width=0.1, offset=0.2,
+                                  state=api.solve_opts(precision=prec, rtol=1e-8), velocity=api.solve_opts(rtol=1e-8))
+            st, t = srv.submit(r)
+            if st != 0:
+                raise RuntimeError(f"submit failed with status {st}")
+            tickets.append(t)
+        res = [srv.wait(t, 1200.0) for t in tickets]
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+        srv.close()
+        lat = np.array([r.end_ms - r.submit_ms for r in res])
+        dofit = sum(r.dofs * (r.state.operator_applies + r.adjoint.operator_applies) for r in res)
+        return {"executors": executors, "precision": "mixed" if prec == api.FO_MIXED else "fp64",
+                "seconds": wall, "requests_per_s": len(res) / wall,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "state_gdof_iters_per_s": dofit / wall / 1e9, "peak_in_flight": int(stats.peak_in_flight),
+                "peak_admitted_gb": stats.peak_bytes / 1e9, "failed": int(stats.failed)}
+
+    served = run(8, api.FO_MIXED, True)
+    serial = run(1, api.FO_FP64, True)
+    return {"sample": f"first {count} requests of the seeded stream (of 2,000)",
+            "sizes": [f"{d}D n={n} {'heat' if h else 'elastic'}" for (_, d, n, h, _) in items],
+            "served_mixed": served, "serial_fp64": serial,
+            "throughput_ratio": served["requests_per_s"] / serial["requests_per_s"]}
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -228,6 +399,15 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = api.Context(local, stream=stream.cuda_stream)
     ctx.set_timing(True)
+    if args.batch_only:
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except OSError:
+            pass
+        print(json.dumps(bench_batch(api, ctx, stream, peaks, args.batch_n, args.batch_maxit, plain=False)), flush=True)
+        ctx.close()
+        return
     mesh, prob = make_problem(api, ctx)
     opts = run_options(api, args.precision)
     ppl = api.PPL(1)
@@ -289,13 +469,17 @@ def main():
     except OSError:
         pass
     NT = 2 * NX * NY
-    flop_per_it = 210.0 * mesh.num_nodes + 12.0 * 2 * mesh.num_nodes     # elastic apply + CG vector updates
+    # algorithmic FP64 work of a PCG iteration: per simplex the scaled stress (Jacobian by path
+    # differences, trace, three stress entries: 22 flops), per node its two-component row from
+    # the stresses of its six simplices (48 flops) and the CG recurrences and dots (12 flops
+    # per DOF)
+    flop_per_it = 22.0 * NT + 48.0 * mesh.num_nodes + 12.0 * 2 * mesh.num_nodes
     bytes_per_it = 96.0 * 2 * mesh.num_nodes + 8.0 * NT
     if args.precision == "fp64":
         achieved = flop_per_it * state_iters / (state_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s (FP64)",
                 "frac": achieved / 1.25, "traffic": None,
-                "kernel": "k_pcg<2, ElasticStateOp<2,double>, double, 1>",
+                "kernel": "k_pcg<2, TiledElasticOp<2,double>, double, 1>",
                 "note": "FP64 peak 1.25 TFLOP/s nominal (probe measured 1.19); L2-resident working set "
                         f"(~{bytes_per_it / 1e6:.1f} MB/iteration), so HBM is not the bound",
                 "hbm_frac_of_measured": bytes_per_it * state_iters / (state_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
@@ -303,7 +487,7 @@ def main():
         achieved = bytes_per_it / 2 * state_iters / (state_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
                 "frac": achieved / peaks.get("hbm_gbs", 6800.0), "traffic": None,
-                "kernel": "k_pcg<2, ElasticStateOp<2,float>, float, 1>"}
+                "kernel": "k_pcg<2, TiledElasticOp<2,float>, double, 1>"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "opt-iters/s", "n_gpus": world, "steps": args.steps,
@@ -344,6 +528,10 @@ def main():
         e2e_s = time.perf_counter() - t0
         line["e2e"] = {"value": args.steps / e2e_s, "unit": "opt-iters/s",
                        "h2d_bytes_per_step": 8 * mesh2.num_nodes, "d2h_bytes_per_step": 8 * mesh2.num_nodes}
+    if rank == 0 and not args.no_batch:
+        line["batch"] = bench_batch(api, ctx, stream, peaks, args.batch_n, args.batch_maxit)
+    if rank == 0 and not args.no_serving:
+        line["serving"] = bench_serving(api, ctx, args.serving_requests)
     if cpu is not None:
         line["cpu_baseline"] = {"value": len(cpu["times"]) / sum(cpu["times"]), "unit": "opt-iters/s", "cores": 1,
                                 "kind": "oracle", "cpu": cpu_model(),
