@@ -248,7 +248,9 @@ extern "C" fo_status fo_mesh_copy_out(const fo_mesh *m, int32_t *cells, double *
 // Sizes of a problem's device fields, in the order of prob_bytes_fields.
 static std::vector<size_t> problem_field_sizes(int d, long long NN, long long NT, long long ND, bool with_f) {
   const size_t S = (d == 2) ? 7 : 15;
+  const size_t npn = (size_t)(ND / NN);   // state components per node
   std::vector<size_t> v = {
+      sizeof(double) * S * npn * npn * NN, sizeof(float) * S * npn * npn * NN, sizeof(double) * S * d * NN,
       sizeof(double) * NN,     sizeof(double) * NT,     sizeof(float) * NT,       (size_t)NT,
       (size_t)NT,              (size_t)ND,              (size_t)NN,               sizeof(double) * ND,
       sizeof(double) * ND,     sizeof(double) * ND,     sizeof(double) * d * NN,  sizeof(double) * d * NN,
@@ -265,6 +267,7 @@ static size_t prob_bytes_fields(const fo_problem *p, std::vector<std::pair<void 
   const std::vector<size_t> sz =
       problem_field_sizes(g.dim, g.num_nodes, g.num_elems, p->ndof, p->f || p->desc.kind != FO_ELASTIC);
   std::vector<void **> ptr = {
+      (void **)&p->Wst,        (void **)&p->Wst32,        (void **)&p->Wvel,
       (void **)&p->phi,        (void **)&p->coef,         (void **)&p->coef32,       (void **)&p->chi,
       (void **)&p->omega0,     (void **)&p->dir,          (void **)&p->vdir,         (void **)&p->load,
       (void **)&p->u,          (void **)&p->p,            (void **)&p->rhs,          (void **)&p->theta,

@@ -328,16 +328,252 @@ __global__ void k_f2d(const float *x, double *y, long long n) {
     y[i] = (double)x[i];
 }
 
+// ------------------------------------------------------------------ stored stencils
+// grad lambda_l of the Kuhn simplex p: e_{pi_{l-1}} / h - e_{pi_l} / h (sparse)
+template <int D>
+__device__ __forceinline__ void kuhn_grad(const Grid &g, int p, int l, double gr[3]) {
+  gr[0] = gr[1] = gr[2] = 0.0;
+  if (l >= 1) gr[kperm<D>(p, l - 1)] += g.inv_h[kperm<D>(p, l - 1)];
+  if (l < D) gr[kperm<D>(p, l)] -= g.inv_h[kperm<D>(p, l)];
+}
+
+// Stored rows are kept in difference form: slot 0 holds the row sum R (an NPN x NPN block, or
+// its diagonal), slots s >= 1 the neighbour blocks W_s, and the row is applied as
+//   (A x)_a = R x_a + sum_{s >= 1} W_s (x_{nb(s)} - x_a),
+// which is the same operator.  R is formed from the exact row sums of the element matrices: the
+// stiffness rows sum to zero exactly (sum_l grad lambda_l = 0), so R holds only the mass-type and
+// penalty terms, minus the weights of eliminated Dirichlet columns.  Rounding in the stored
+// weights then perturbs the operator like rounding in the differences of a matrix-free apply:
+// it keeps the constant (rigid translation) kernel, which matters in FP32 for these
+// ill-conditioned systems.  Dirichlet DOFs: identity row, eliminated column.  The Jacobi
+// inverse diagonal of the (eliminated) operator is written alongside.
+//
+// State rows of node a, summed over the simplices (p, m) around it (the node is vertex m):
+// scalar (NPN = 1): A_e|e| grad lambda_m . grad lambda_l + omega^2 |e| (1 + delta_ml) / ((D+1)(D+2))
+// with A_e = coef (A times k); elastic (NPN = D): the block
+// A_e|e| [lam (g_m)_i (g_l)_j + mu (g_m)_j (g_l)_i + mu delta_ij g_m . g_l] coupling component i of
+// the node with component j of vertex l (plane strain / 3D Lame constants).
+template <int D, int NPN>
+__global__ void k_state_stencil(Grid g, const double *coef, const uint8_t *dir, double lam, double mu, double w2,
+                                double *W, float *W32, double *dinv, float *dinv32) {
+  constexpr int S = ST<D>::S, BLK = NPN * NPN;
+  const long long N = g.num_nodes;
+  const double mref = g.vol_e / ((D + 1) * (D + 2));
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < N; a += (long long)gridDim.x * blockDim.x) {
+    int idx[3];
+    node_ijk(g, a, idx);
+    double w[S][BLK];
+    double R[BLK];
+#pragma unroll
+    for (int k = 0; k < BLK; ++k) R[k] = 0.0;
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int k = 0; k < BLK; ++k) w[s][k] = 0.0;
+#pragma unroll
+    for (int p = 0; p < KP<D>::P; ++p)
+#pragma unroll
+      for (int m = 0; m <= D; ++m) {
+        long long e;
+        if (!elem_of<D>(g, idx, p, m, e)) continue;
+        const double Av = coef[e] * g.vol_e;
+        double gm[3];
+        kuhn_grad<D>(g, p, m, gm);
+        if (NPN == 1 && w2 != 0.0) R[0] += w2 * mref * (D + 2);   // mass row sum
+#pragma unroll
+        for (int l = 0; l <= D; ++l) {
+          const int sl = rel_slot<D>(p, m, l);
+          double gl[3];
+          kuhn_grad<D>(g, p, l, gl);
+          double dot = 0.0;
+#pragma unroll
+          for (int k = 0; k < D; ++k) dot += gm[k] * gl[k];
+          if (NPN == 1) {
+            w[sl][0] += Av * dot + (w2 != 0.0 ? w2 * mref * (l == m ? 2.0 : 1.0) : 0.0);
+          } else {
+#pragma unroll
+            for (int i = 0; i < NPN; ++i)
+#pragma unroll
+              for (int j = 0; j < NPN; ++j)
+                w[sl][i * NPN + j] += Av * (lam * gm[i] * gl[j] + mu * gm[j] * gl[i] + (i == j ? mu * dot : 0.0));
+          }
+        }
+      }
+    // eliminated Dirichlet columns leave the row: their weight comes off the row sum
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const long long nb = slot_node<D>(g, idx, a, s);
+#pragma unroll
+      for (int j = 0; j < NPN; ++j)
+        if (nb >= 0 && dir[nb * NPN + j])
+#pragma unroll
+          for (int i = 0; i < NPN; ++i) {
+            R[i * NPN + j] -= w[s][i * NPN + j];
+            w[s][i * NPN + j] = 0.0;
+          }
+    }
+#pragma unroll
+    for (int i = 0; i < NPN; ++i) {
+      const double diag = dir[a * NPN + i] ? 1.0 : w[0][i * NPN + i];
+      dinv[a * NPN + i] = 1.0 / diag;
+      dinv32[a * NPN + i] = (float)(1.0 / diag);
+      if (dir[a * NPN + i]) {   // identity row
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+          for (int j = 0; j < NPN; ++j) w[s][i * NPN + j] = 0.0;
+#pragma unroll
+        for (int j = 0; j < NPN; ++j) R[i * NPN + j] = (i == j) ? 1.0 : 0.0;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < BLK; ++k) w[0][k] = R[k];
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int k = 0; k < BLK; ++k) {
+        W[(s * BLK + k) * N + a] = w[s][k];
+        W32[(s * BLK + k) * N + a] = (float)w[s][k];
+      }
+  }
+}
+
+// Rows of the velocity form B of node a (component-diagonal), in difference form as above: for
+// every component the P1 Laplacian plus (alpha + gamma_0 chi_Omega0) times the consistent mass;
+// for component c on a face normal to axis c also gamma_b times the facet mass of that face (the
+// normal penalty couples only the normal component on an axis-aligned box).  H^1_0: identity
+// rows on boundary nodes, eliminated columns.
+template <int D>
+__global__ void k_velocity_stencil(Grid g, const uint8_t *omega0, const uint8_t *vdir, double alpha, double gamma0,
+                                   double gammab, double *W, double *dinv) {
+  constexpr int S = ST<D>::S;
+  const long long N = g.num_nodes;
+  const double mref = g.vol_e / ((D + 1) * (D + 2));
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < N; a += (long long)gridDim.x * blockDim.x) {
+    int idx[3];
+    node_ijk(g, a, idx);
+    double w[S][D], R[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) R[c] = 0.0;
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int c = 0; c < D; ++c) w[s][c] = 0.0;
+    if (vdir[a]) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        R[c] = 1.0;
+        dinv[a * D + c] = 1.0;
+      }
+    } else {
+#pragma unroll
+      for (int p = 0; p < KP<D>::P; ++p)
+#pragma unroll
+        for (int m = 0; m <= D; ++m) {
+          long long e;
+          if (!elem_of<D>(g, idx, p, m, e)) continue;
+          const double wm = (alpha + (omega0[e] ? gamma0 : 0.0)) * mref;
+#pragma unroll
+          for (int c = 0; c < D; ++c) R[c] += wm * (D + 2);
+          double gm[3];
+          kuhn_grad<D>(g, p, m, gm);
+#pragma unroll
+          for (int l = 0; l <= D; ++l) {
+            const int sl = rel_slot<D>(p, m, l);
+            double gl[3];
+            kuhn_grad<D>(g, p, l, gl);
+            double dot = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) dot += gm[k] * gl[k];
+            const double v = g.vol_e * dot + wm * (l == m ? 2.0 : 1.0);
+#pragma unroll
+            for (int c = 0; c < D; ++c) w[sl][c] += v;
+          }
+        }
+      if (gammab != 0.0) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          if (!(idx[c] == 0 || idx[c] == g.n[c])) continue;
+          const double fm = gammab * g.facet_area[c] / (D * (D + 1));   // facet mass unit
+          if (D == 2) {
+            const int o = 1 - c;
+#pragma unroll
+            for (int sg = -1; sg <= 1; sg += 2) {
+              if (idx[o] + sg < 0 || idx[o] + sg > g.n[o]) continue;
+              int dl[3] = {0, 0, 0};
+              dl[o] = sg;
+              w[0][c] += 2.0 * fm;
+              w[stencil_slot<D>(dl)][c] += fm;
+              R[c] += 3.0 * fm;
+            }
+          } else {
+            const int o1 = c == 0 ? 1 : 0, o2 = c == 2 ? 1 : 2;
+#pragma unroll
+            for (int q = 0; q < 2; ++q)   // face-local Kuhn triangles, paths (o1, o2) and (o2, o1)
+#pragma unroll
+              for (int m = 0; m <= 2; ++m) {
+                const int ax[2] = {q == 0 ? o1 : o2, q == 0 ? o2 : o1};
+                int cc[3] = {idx[0], idx[1], idx[2]};
+                for (int l = 0; l < m; ++l) cc[ax[l]] -= 1;
+                if (cc[o1] < 0 || cc[o1] >= g.n[o1] || cc[o2] < 0 || cc[o2] >= g.n[o2]) continue;
+                w[0][c] += 2.0 * fm;
+                R[c] += 4.0 * fm;
+#pragma unroll
+                for (int l = 0; l <= 2; ++l) {
+                  if (l == m) continue;
+                  int dl[3] = {0, 0, 0};
+                  for (int j = 0; j < 2; ++j) {
+                    if (l > m && j >= m && j < l) dl[ax[j]] += 1;
+                    if (l < m && j >= l && j < m) dl[ax[j]] -= 1;
+                  }
+                  w[stencil_slot<D>(dl)][c] += fm;
+                }
+              }
+          }
+        }
+      }
+#pragma unroll
+      for (int s = 1; s < S; ++s) {
+        const long long nb = slot_node<D>(g, idx, a, s);
+        if (nb >= 0 && vdir[nb])
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            R[c] -= w[s][c];
+            w[s][c] = 0.0;
+          }
+      }
+#pragma unroll
+      for (int c = 0; c < D; ++c) dinv[a * D + c] = 1.0 / w[0][c];
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) w[0][c] = R[c];
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int c = 0; c < D; ++c) W[(s * D + c) * N + a] = w[s][c];
+  }
+}
+
 fo_status fo_launch_state_diag(fo_problem *p) {
   const Grid &g = p->mesh->g;
   int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
   cudaStream_t s = p->ctx->stream;
+  // the state operator's stencil rows (from the current coefficients) and its Jacobi diagonal
+  const double w2 = p->desc.kind == FO_HELMHOLTZ ? p->desc.omega * p->desc.omega : 0.0;
+  double *di = p->dinv_state;
+  float *di32 = p->dinv_state32;
   if (p->desc.kind == FO_ELASTIC) {
-    if (g.dim == 2) k_diag_inv<2><<<blocks, FO_BLOCK, 0, s>>>(make_elastic_op<2, double>(p), p->dinv_state, p->dinv_state32);
-    else k_diag_inv<3><<<blocks, FO_BLOCK, 0, s>>>(make_elastic_op<3, double>(p), p->dinv_state, p->dinv_state32);
+    if (g.dim == 2)
+      k_state_stencil<2, 2><<<blocks, FO_BLOCK, 0, s>>>(g, p->coef, p->dir, p->lame_lambda, p->lame_mu, 0.0, p->Wst,
+                                                         p->Wst32, di, di32);
+    else
+      k_state_stencil<3, 3><<<blocks, FO_BLOCK, 0, s>>>(g, p->coef, p->dir, p->lame_lambda, p->lame_mu, 0.0, p->Wst,
+                                                         p->Wst32, di, di32);
   } else {
-    if (g.dim == 2) k_diag_inv<2><<<blocks, FO_BLOCK, 0, s>>>(make_scalar_op<2, double>(p), p->dinv_state, p->dinv_state32);
-    else k_diag_inv<3><<<blocks, FO_BLOCK, 0, s>>>(make_scalar_op<3, double>(p), p->dinv_state, p->dinv_state32);
+    if (g.dim == 2)
+      k_state_stencil<2, 1><<<blocks, FO_BLOCK, 0, s>>>(g, p->coef, p->dir, 0.0, 0.0, w2, p->Wst, p->Wst32, di, di32);
+    else
+      k_state_stencil<3, 1><<<blocks, FO_BLOCK, 0, s>>>(g, p->coef, p->dir, 0.0, 0.0, w2, p->Wst, p->Wst32, di, di32);
   }
   fo_note_launch(1);
   FO_CU(p->ctx, cudaGetLastError());
@@ -345,10 +581,13 @@ fo_status fo_launch_state_diag(fo_problem *p) {
 }
 
 fo_status fo_launch_velocity_diag(fo_problem *p) {
+  // the velocity form does not depend on phi: its stencil is built once per problem
   const Grid &g = p->mesh->g;
   int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
-  if (g.dim == 2) k_diag_inv<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(make_velocity_op<2, double>(p), p->dinv_vel, (float *)nullptr);
-  else k_diag_inv<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(make_velocity_op<3, double>(p), p->dinv_vel, (float *)nullptr);
+  cudaStream_t s = p->ctx->stream;
+  const double gb = p->desc.normal_penalty, g0 = p->desc.omega0_weight, al = p->desc.alpha_mass;
+  if (g.dim == 2) k_velocity_stencil<2><<<blocks, FO_BLOCK, 0, s>>>(g, p->omega0, p->vdir, al, g0, gb, p->Wvel, p->dinv_vel);
+  else k_velocity_stencil<3><<<blocks, FO_BLOCK, 0, s>>>(g, p->omega0, p->vdir, al, g0, gb, p->Wvel, p->dinv_vel);
   fo_note_launch(1);
   FO_CU(p->ctx, cudaGetLastError());
   return FO_OK;
@@ -360,21 +599,21 @@ fo_status fo_launch_state_apply(fo_problem *p, const double *x, double *y, bool 
   cudaStream_t s = p->ctx->stream;
   if (p->desc.kind == FO_ELASTIC) {
     if (g.dim == 2) {
-      auto op = make_elastic_op<2, double>(p);
+      auto op = make_elastic_stencil<2, double>(p);
       if (mask) k_apply<2><<<blocks, FO_BLOCK, 0, s>>>(op, MaskedX<double>{x, p->dir}, y);
       else k_apply<2><<<blocks, FO_BLOCK, 0, s>>>(op, VecX<double>{x}, y);
     } else {
-      auto op = make_elastic_op<3, double>(p);
+      auto op = make_elastic_stencil<3, double>(p);
       if (mask) k_apply<3><<<blocks, FO_BLOCK, 0, s>>>(op, MaskedX<double>{x, p->dir}, y);
       else k_apply<3><<<blocks, FO_BLOCK, 0, s>>>(op, VecX<double>{x}, y);
     }
   } else {
     if (g.dim == 2) {
-      auto op = make_scalar_op<2, double>(p);
+      auto op = make_scalar_stencil<2, double>(p);
       if (mask) k_apply<2><<<blocks, FO_BLOCK, 0, s>>>(op, MaskedX<double>{x, p->dir}, y);
       else k_apply<2><<<blocks, FO_BLOCK, 0, s>>>(op, VecX<double>{x}, y);
     } else {
-      auto op = make_scalar_op<3, double>(p);
+      auto op = make_scalar_stencil<3, double>(p);
       if (mask) k_apply<3><<<blocks, FO_BLOCK, 0, s>>>(op, MaskedX<double>{x, p->dir}, y);
       else k_apply<3><<<blocks, FO_BLOCK, 0, s>>>(op, VecX<double>{x}, y);
     }
@@ -411,11 +650,11 @@ fo_status fo_launch_state_apply32(fo_problem *p, const double *x, double *y) {
   cudaStream_t s = p->ctx->stream;
   MaskedCastX<float> mx{x, p->dir};
   if (p->desc.kind == FO_ELASTIC) {
-    if (g.dim == 2) k_apply32<2><<<blocks, FO_BLOCK, 0, s>>>(make_elastic_op<2, float>(p), mx, y);
-    else k_apply32<3><<<blocks, FO_BLOCK, 0, s>>>(make_elastic_op<3, float>(p), mx, y);
+    if (g.dim == 2) k_apply32<2><<<blocks, FO_BLOCK, 0, s>>>(make_elastic_stencil<2, float>(p), mx, y);
+    else k_apply32<3><<<blocks, FO_BLOCK, 0, s>>>(make_elastic_stencil<3, float>(p), mx, y);
   } else {
-    if (g.dim == 2) k_apply32<2><<<blocks, FO_BLOCK, 0, s>>>(make_scalar_op<2, float>(p), mx, y);
-    else k_apply32<3><<<blocks, FO_BLOCK, 0, s>>>(make_scalar_op<3, float>(p), mx, y);
+    if (g.dim == 2) k_apply32<2><<<blocks, FO_BLOCK, 0, s>>>(make_scalar_stencil<2, float>(p), mx, y);
+    else k_apply32<3><<<blocks, FO_BLOCK, 0, s>>>(make_scalar_stencil<3, float>(p), mx, y);
   }
   fo_note_launch(1);
   FO_CU(p->ctx, cudaGetLastError());
@@ -427,9 +666,9 @@ fo_status fo_launch_velocity_apply(fo_problem *p, const double *x, double *y) {
   int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
   // H^1_0: boundary columns are dropped (rows are identity), as in the reduced system
   if (g.dim == 2)
-    k_apply<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(make_velocity_op<2, double>(p), NodeMaskedX<double, 2>{x, p->vdir}, y);
+    k_apply<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(make_velocity_stencil<2>(p), NodeMaskedX<double, 2>{x, p->vdir}, y);
   else
-    k_apply<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(make_velocity_op<3, double>(p), NodeMaskedX<double, 3>{x, p->vdir}, y);
+    k_apply<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(make_velocity_stencil<3>(p), NodeMaskedX<double, 3>{x, p->vdir}, y);
   fo_note_launch(1);
   FO_CU(p->ctx, cudaGetLastError());
   return FO_OK;

@@ -103,6 +103,9 @@ struct fo_problem {
   double *dinv_state = nullptr;  // N_dof
   float *dinv_state32 = nullptr; // N_dof
   double *dinv_vel = nullptr;    // d * N_n
+  double *Wst = nullptr;         // state operator rows, stencil form [S][ncomp^2][N_n]
+  float *Wst32 = nullptr;        // the same in FP32
+  double *Wvel = nullptr;        // velocity operator rows, [S][d][N_n] (component diagonal)
   double *L = nullptr, *R = nullptr;   // transport stencils [S][N_n]
   double *dinvL = nullptr;       // N_n
   double *red = nullptr;         // reduction partials

@@ -473,19 +473,16 @@ static fo_status state_solve_impl(fo_problem *p, const Op64 &op64, const OpMixed
 
 fo_status fo_state_pcg(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st) {
   const Grid &g = p->mesh->g;
+  // stored-stencil operators: FP64 rows for the FP64 solve and the refinement residual, FP32
+  // rows for the inner solve of the mixed path
   if (p->desc.kind == FO_ELASTIC) {
     if (g.dim == 2)
-      return state_solve_impl<2>(p, make_tiled_elastic_op<2, double>(p), make_tiled_elastic_op<2, float>(p), b, x,
-                                 o, st);
-    return state_solve_impl<3>(p, make_tiled_elastic_op<3, double>(p), make_tiled_elastic_op<3, float>(p), b, x, o,
-                               st);
+      return state_solve_impl<2>(p, make_elastic_stencil<2, double>(p), make_elastic_stencil<2, float>(p), b, x, o, st);
+    return state_solve_impl<3>(p, make_elastic_stencil<3, double>(p), make_elastic_stencil<3, float>(p), b, x, o, st);
   }
-  if (g.dim == 2) {
-    const auto s32 = make_scalar_op<2, float>(p);
-    return state_solve_impl<2>(p, make_scalar_op<2, double>(p), Fp32ApplyOp<decltype(s32)>{s32, s32.g}, b, x, o, st);
-  }
-  const auto s32 = make_scalar_op<3, float>(p);
-  return state_solve_impl<3>(p, make_scalar_op<3, double>(p), Fp32ApplyOp<decltype(s32)>{s32, s32.g}, b, x, o, st);
+  if (g.dim == 2)
+    return state_solve_impl<2>(p, make_scalar_stencil<2, double>(p), make_scalar_stencil<2, float>(p), b, x, o, st);
+  return state_solve_impl<3>(p, make_scalar_stencil<3, double>(p), make_scalar_stencil<3, float>(p), b, x, o, st);
 }
 
 template <int D>
@@ -504,7 +501,7 @@ static fo_status velocity_impl(fo_problem *p, const fo_solve_opts *o, double *Bt
   a.maxit = o->maxit;
   a.warm = o->warm_start;
   SolveOut out;
-  FO_TRY(run_pcg<D>(p, make_velocity_op<D, double>(p), a, g.num_nodes, o->grid_blocks, &out));
+  FO_TRY(run_pcg<D>(p, make_velocity_stencil<D>(p), a, g.num_nodes, o->grid_blocks, &out));
   double rr = 0, bb = 0, bx = 0;
   for (int s = 0; s < D; ++s) {
     rr += out.out[s * 4];
@@ -626,9 +623,9 @@ extern "C" fo_status fo_state_solve_noalloc(fo_problem *p, const double *b, doub
   if (!p->coef_valid) FO_TRY(fo_coefficients(p));   // launches kernels, allocates nothing
   const Grid &g = p->mesh->g;
   if (p->desc.kind == FO_ELASTIC) {
-    if (g.dim == 2) return noalloc_pcg<2>(p, make_elastic_op<2, double>(p), b, x, o, st);
-    return noalloc_pcg<3>(p, make_elastic_op<3, double>(p), b, x, o, st);
+    if (g.dim == 2) return noalloc_pcg<2>(p, make_elastic_stencil<2, double>(p), b, x, o, st);
+    return noalloc_pcg<3>(p, make_elastic_stencil<3, double>(p), b, x, o, st);
   }
-  if (g.dim == 2) return noalloc_pcg<2>(p, make_scalar_op<2, double>(p), b, x, o, st);
-  return noalloc_pcg<3>(p, make_scalar_op<3, double>(p), b, x, o, st);
+  if (g.dim == 2) return noalloc_pcg<2>(p, make_scalar_stencil<2, double>(p), b, x, o, st);
+  return noalloc_pcg<3>(p, make_scalar_stencil<3, double>(p), b, x, o, st);
 }

@@ -431,6 +431,59 @@ struct VelocityOp {
 //   row_m = sum_{(p,m)} S_e[:, pi_{m-1}] / h_{pi_{m-1}} - S_e[:, pi_m] / h_{pi_m}.
 // T is the element arithmetic (double, or float for the mixed path); rows are returned in
 // double.  Needs smem_bytes of dynamic shared memory and blocks of TX*TY*TZ threads.
+// ---- stored per-node stencils --------------------------------------------------------------
+// A problem's operator kept as its matrix rows in stencil form: for every stencil slot s (the
+// node itself, then its Kuhn neighbours) an NPN x NPN block (FULL) or only its diagonal (the
+// velocity form, whose component systems are decoupled).  Slot-major layout
+// W[(s * BLK + k) * N_n + a], so that a warp's loads of one entry are coalesced.  Rows are in
+// difference form: slot 0 holds the row sum R and the row is
+//   (A x)_a = R x_a + sum_{s >= 1} W_s (x_{nb(s)} - x_a)
+// (R is exact, the stiffness rows summing to zero), so that rounding in the stored weights,
+// FP32 ones included, keeps the operator's constant kernel as a matrix-free apply that
+// differences the field does.  Dirichlet rows are identity rows and Dirichlet columns are
+// eliminated (the builders bake both in).  An apply costs a subtraction and an FMA per stored
+// entry; on GB300, whose FP64 rate is 1/58 of its FP32 rate, that is several times less FP64
+// work than recomputing element matrices, and a single problem's stencils stay resident in the
+// 129 MB L2.  Built once per coefficient update (state) or once per problem (velocity).
+template <int D, int NPN_, bool FULL, typename T>
+struct StencilOp {
+  static constexpr int NPN = NPN_;
+  static constexpr int BLK = FULL ? NPN * NPN : NPN;
+  Grid g;
+  FO_NODE_OWNERSHIP(T)
+  const T *W;
+
+  template <class X>
+  __device__ __forceinline__ void row(long long a, const int idx[3], const X &x, T out[NPN]) const {
+    const long long N = g.num_nodes;
+    T acc[NPN], xa[NPN];
+#pragma unroll
+    for (int j = 0; j < NPN; ++j) xa[j] = (T)x(a * NPN + j);
+#pragma unroll
+    for (int c = 0; c < NPN; ++c) acc[c] = T(0);
+#pragma unroll
+    for (int s = 0; s < ST<D>::S; ++s) {
+      const long long nb = slot_node<D>(g, idx, a, s);
+      if (nb < 0) continue;
+      T xv[NPN];   // x_a on slot 0, x_nb - x_a on the others
+#pragma unroll
+      for (int j = 0; j < NPN; ++j) xv[j] = s == 0 ? xa[j] : (T)x(nb * NPN + j) - xa[j];
+      if (FULL) {
+#pragma unroll
+        for (int i = 0; i < NPN; ++i)
+#pragma unroll
+          for (int j = 0; j < NPN; ++j) acc[i] = fma(W[(s * BLK + i * NPN + j) * N + a], xv[j], acc[i]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < NPN; ++c) acc[c] = fma(W[(s * BLK + c) * N + a], xv[c], acc[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NPN; ++c) out[c] = acc[c];
+  }
+
+};
+
 template <int D, typename T>
 struct TiledElasticOp {
   static constexpr int NPN = D;
@@ -635,5 +688,28 @@ inline TiledElasticOp<D, T> make_tiled_elastic_op(const fo_problem *p) {
   op.ntile[1] = (int)((g.nn[1] + Op::TY - 1) / Op::TY);
   op.ntile[2] = (D == 3) ? (int)((g.nn[2] + Op::TZ - 1) / Op::TZ) : 1;
   op.ntiles = (long long)op.ntile[0] * op.ntile[1] * op.ntile[2];
+  return op;
+}
+
+// Stored-stencil operators of a problem (state: scalar or elastic; velocity).
+template <int D, typename T>
+inline StencilOp<D, 1, true, T> make_scalar_stencil(const fo_problem *p) {
+  StencilOp<D, 1, true, T> op;
+  op.g = p->mesh->g;
+  op.W = std::is_same<T, float>::value ? (const T *)p->Wst32 : (const T *)p->Wst;
+  return op;
+}
+template <int D, typename T>
+inline StencilOp<D, D, true, T> make_elastic_stencil(const fo_problem *p) {
+  StencilOp<D, D, true, T> op;
+  op.g = p->mesh->g;
+  op.W = std::is_same<T, float>::value ? (const T *)p->Wst32 : (const T *)p->Wst;
+  return op;
+}
+template <int D>
+inline StencilOp<D, D, false, double> make_velocity_stencil(const fo_problem *p) {
+  StencilOp<D, D, false, double> op;
+  op.g = p->mesh->g;
+  op.W = p->Wvel;
   return op;
 }
