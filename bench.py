@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precond", choices=["jacobi", "mg"], default="mg", help="state-solve preconditioner")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--l2-flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
@@ -68,9 +69,10 @@ def parse():
 
 
 # ------------------------------------------------------------------------------ problem
-def run_options(api, precision):
+def run_options(api, precision, precond="mg"):
     prec = api.FO_MIXED if precision == "mixed" else api.FO_FP64
-    state = api.solve_opts(precision=prec, rtol=1e-12, warm_start=1)
+    pc = api.FO_PC_MG if precond == "mg" else api.FO_PC_JACOBI
+    state = api.solve_opts(precision=prec, rtol=1e-12, warm_start=1, precond=pc)
     vel = api.solve_opts(rtol=1e-12, warm_start=1)
     tr = api.solve_opts(rtol=1e-12)
     # no reinitialisation inside the 50 iterations: on this mesh the reinitialisation scheme
@@ -409,7 +411,7 @@ def main():
         ctx.close()
         return
     mesh, prob = make_problem(api, ctx)
-    opts = run_options(api, args.precision)
+    opts = run_options(api, args.precision, args.precond)
     ppl = api.PPL(1)
     flush = torch.empty(max(args.l2_flush_mb, 1) * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2
 

@@ -151,7 +151,12 @@ typedef struct {
   double inner_rtol;        /* FO_MIXED: relative reduction asked of each FP32 solve    */
   int inner_maxit;          /* FO_MIXED: cap per FP32 solve                             */
   int grid_blocks;          /* 0 = autotuned; else blocks of the persistent kernel      */
+  int precond;              /* state solves: FO_PC_JACOBI, or FO_PC_MG (FP64 CG with an */
+                            /* FP32 geometric-multigrid V-cycle as preconditioner)      */
 } fo_solve_opts;
+
+#define FO_PC_JACOBI 0
+#define FO_PC_MG     1
 
 typedef struct {
   int iterations;           /* Krylov iterations (FP64, or total inner FP32)            */

@@ -15,6 +15,7 @@ STATUS_NAMES = {0: "FO_OK", -1: "FO_EINVAL", -2: "FO_ENOMEM", -3: "FO_ENOMEM_BUD
 
 FO_HEAT, FO_ELASTIC, FO_HELMHOLTZ = 0, 1, 2
 FO_FP64, FO_MIXED = 0, 1
+FO_PC_JACOBI, FO_PC_MG = 0, 1
 (FO_FIELD_PHI, FO_FIELD_U, FO_FIELD_P, FO_FIELD_THETA, FO_FIELD_RHS, FO_FIELD_COEF, FO_FIELD_CHI,
  FO_FIELD_LOAD, FO_FIELD_OMEGA0) = range(9)
 FO_OP_STATE, FO_OP_VELOCITY, FO_OP_TRANSPORT_L, FO_OP_TRANSPORT_R, FO_OP_STATE_FP32 = range(5)
@@ -47,7 +48,8 @@ class TuneResult(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int), ("warm_start", C.c_int),
-                ("inner_rtol", C.c_double), ("inner_maxit", C.c_int), ("grid_blocks", C.c_int)]
+                ("inner_rtol", C.c_double), ("inner_maxit", C.c_int), ("grid_blocks", C.c_int),
+                ("precond", C.c_int)]
 
 
 class SolveStats(C.Structure):

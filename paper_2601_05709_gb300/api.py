@@ -9,7 +9,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (FO_ELASTIC, FO_FIELD_CHI, FO_FIELD_COEF, FO_FIELD_LOAD, FO_FIELD_OMEGA0, FO_FIELD_P,
+from ._lib import (FO_PC_JACOBI, FO_PC_MG, FO_ELASTIC, FO_FIELD_CHI, FO_FIELD_COEF, FO_FIELD_LOAD, FO_FIELD_OMEGA0, FO_FIELD_P,
                    FO_FIELD_PHI, FO_FIELD_RHS, FO_FIELD_THETA, FO_FIELD_U, FO_FP64, FO_HEAT, FO_HELMHOLTZ,
                    FO_MIXED, FO_OP_STATE, FO_OP_STATE_FP32, FO_OP_TRANSPORT_L, FO_OP_TRANSPORT_R,
                    FO_OP_VELOCITY, FO_OK, FormoptError)
@@ -31,11 +31,11 @@ def _is_device(x):
 
 
 def solve_opts(precision=FO_FP64, rtol=1e-12, maxit=200000, warm_start=0, inner_rtol=1e-3, inner_maxit=20000,
-               grid_blocks=0):
+               grid_blocks=0, precond=0):
     o = _lib.SolveOpts()
     _lib.load().fo_solve_opts_default(C.byref(o))
     o.precision, o.rtol, o.maxit, o.warm_start = precision, rtol, maxit, int(warm_start)
-    o.inner_rtol, o.inner_maxit, o.grid_blocks = inner_rtol, inner_maxit, grid_blocks
+    o.inner_rtol, o.inner_maxit, o.grid_blocks, o.precond = inner_rtol, inner_maxit, grid_blocks, precond
     return o
 
 

@@ -131,17 +131,15 @@ static double mesh_diameter(const Grid &g) {
   return std::sqrt(std::pow(6.0 * std::sqrt(2.0) * D / NT, 2.0 / 3.0));
 }
 
-extern "C" fo_status fo_mesh_box(fo_ctx *ctx, int dim, const int n[3], const double lo[3], const double hi[3],
-                                 fo_mesh **out) {
-  if (!ctx || !out || !n || !lo || !hi) return FO_EINVAL;
-  *out = nullptr;
-  if (dim != 2 && dim != 3) return fo_fail(ctx, FO_EINVAL, "dim must be 2 or 3");
-  Grid g{};
+// The structured Kuhn grid of the box (lo, hi) with n cells per axis; false on bad extents or
+// more nodes than int32 connectivity allows.
+bool fo_grid_make(int dim, const int n[3], const double lo[3], const double hi[3], Grid &g) {
+  g = Grid{};
   g.dim = dim;
   long long nodes = 1, cells = 1;
   for (int a = 0; a < 3; ++a) {
     if (a < dim) {
-      if (n[a] < 1 || !(hi[a] > lo[a])) return fo_fail(ctx, FO_EINVAL, "bad extent on axis %d", a);
+      if (n[a] < 1 || !(hi[a] > lo[a])) return false;
       g.n[a] = n[a];
       g.lo[a] = lo[a];
       g.hi[a] = hi[a];
@@ -164,7 +162,7 @@ extern "C" fo_status fo_mesh_box(fo_ctx *ctx, int dim, const int n[3], const dou
     nodes *= g.nn[a];
     cells *= g.n[a];
   }
-  if (nodes > (1ll << 31) - 1) return fo_fail(ctx, FO_EINVAL, "mesh too large for int32 connectivity");
+  if (nodes > (1ll << 31) - 1) return false;
   g.num_nodes = nodes;
   g.num_cells = cells;
   g.num_elems = cells * (dim == 2 ? 2 : 6);
@@ -176,6 +174,16 @@ extern "C" fo_status fo_mesh_box(fo_ctx *ctx, int dim, const int n[3], const dou
       g.facet_area[a] = g.h[o1] * g.h[o2] / 2.0;
     }
   }
+  return true;
+}
+
+extern "C" fo_status fo_mesh_box(fo_ctx *ctx, int dim, const int n[3], const double lo[3], const double hi[3],
+                                 fo_mesh **out) {
+  if (!ctx || !out || !n || !lo || !hi) return FO_EINVAL;
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return fo_fail(ctx, FO_EINVAL, "dim must be 2 or 3");
+  Grid g{};
+  if (!fo_grid_make(dim, n, lo, hi, g)) return fo_fail(ctx, FO_EINVAL, "bad extents or mesh too large");
   fo_mesh *m = new fo_mesh();
   m->ctx = ctx;
   m->g = g;
@@ -309,6 +317,7 @@ extern "C" fo_status fo_problem_destroy(fo_problem *p) {
   fo_ctx *ctx = p->ctx;
   cudaStreamSynchronize(ctx->stream);
   fo_batch_destroy(p);
+  fo_mg_destroy(p);
   std::vector<std::pair<void **, size_t>> list;
   prob_bytes_fields(p, list);
   for (auto &e : list) {
@@ -425,6 +434,7 @@ extern "C" fo_status fo_coefficients(fo_problem *p) {
   if (p->batch) FO_TRY(fo_batch_prepare(p));
   else FO_TRY(fo_launch_state_diag(p));
   p->coef_valid = true;
+  p->coef_epoch += 1;
   return FO_OK;
 }
 

@@ -554,30 +554,30 @@ __global__ void k_velocity_stencil(Grid g, const uint8_t *omega0, const uint8_t 
   }
 }
 
-fo_status fo_launch_state_diag(fo_problem *p) {
-  const Grid &g = p->mesh->g;
+// The state operator's stencil rows on grid g (the problem's grid or a coarser one) from
+// element coefficients `coef` and the Dirichlet mask `dir` of that grid.
+fo_status fo_launch_stencil_on(fo_problem *p, const Grid &g, const double *coef, const uint8_t *dir, double *W,
+                               float *W32, double *di, float *di32) {
   int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
   cudaStream_t s = p->ctx->stream;
-  // the state operator's stencil rows (from the current coefficients) and its Jacobi diagonal
   const double w2 = p->desc.kind == FO_HELMHOLTZ ? p->desc.omega * p->desc.omega : 0.0;
-  double *di = p->dinv_state;
-  float *di32 = p->dinv_state32;
   if (p->desc.kind == FO_ELASTIC) {
     if (g.dim == 2)
-      k_state_stencil<2, 2><<<blocks, FO_BLOCK, 0, s>>>(g, p->coef, p->dir, p->lame_lambda, p->lame_mu, 0.0, p->Wst,
-                                                         p->Wst32, di, di32);
+      k_state_stencil<2, 2><<<blocks, FO_BLOCK, 0, s>>>(g, coef, dir, p->lame_lambda, p->lame_mu, 0.0, W, W32, di, di32);
     else
-      k_state_stencil<3, 3><<<blocks, FO_BLOCK, 0, s>>>(g, p->coef, p->dir, p->lame_lambda, p->lame_mu, 0.0, p->Wst,
-                                                         p->Wst32, di, di32);
+      k_state_stencil<3, 3><<<blocks, FO_BLOCK, 0, s>>>(g, coef, dir, p->lame_lambda, p->lame_mu, 0.0, W, W32, di, di32);
   } else {
-    if (g.dim == 2)
-      k_state_stencil<2, 1><<<blocks, FO_BLOCK, 0, s>>>(g, p->coef, p->dir, 0.0, 0.0, w2, p->Wst, p->Wst32, di, di32);
-    else
-      k_state_stencil<3, 1><<<blocks, FO_BLOCK, 0, s>>>(g, p->coef, p->dir, 0.0, 0.0, w2, p->Wst, p->Wst32, di, di32);
+    if (g.dim == 2) k_state_stencil<2, 1><<<blocks, FO_BLOCK, 0, s>>>(g, coef, dir, 0.0, 0.0, w2, W, W32, di, di32);
+    else k_state_stencil<3, 1><<<blocks, FO_BLOCK, 0, s>>>(g, coef, dir, 0.0, 0.0, w2, W, W32, di, di32);
   }
   fo_note_launch(1);
   FO_CU(p->ctx, cudaGetLastError());
   return FO_OK;
+}
+
+fo_status fo_launch_state_diag(fo_problem *p) {
+  // the state operator's stencil rows (from the current coefficients) and its Jacobi diagonal
+  return fo_launch_stencil_on(p, p->mesh->g, p->coef, p->dir, p->Wst, p->Wst32, p->dinv_state, p->dinv_state32);
 }
 
 fo_status fo_launch_velocity_diag(fo_problem *p) {

@@ -79,6 +79,21 @@ struct fo_batch {
   double tuned_us[2] = {0, 0};
 };
 
+// Geometric multigrid hierarchy of a problem's state operator (fo_mg.cu): level 0 is the
+// problem's grid, level l halves every axis of level l-1.
+#define MG_MAX_LEVELS 10
+struct fo_mg {
+  int L = 0, npn = 1;
+  long long built_epoch = -1;
+  Grid g[MG_MAX_LEVELS];
+  float *b[MG_MAX_LEVELS] = {}, *z0[MG_MAX_LEVELS] = {}, *z1[MG_MAX_LEVELS] = {}, *t[MG_MAX_LEVELS] = {};
+  double *coef[MG_MAX_LEVELS] = {}, *W64[MG_MAX_LEVELS] = {}, *dinv64[MG_MAX_LEVELS] = {};
+  float *W32[MG_MAX_LEVELS] = {}, *dinv32[MG_MAX_LEVELS] = {};
+  uint8_t *dir[MG_MAX_LEVELS] = {};
+  void *dev = nullptr;                     // device copy of the level table
+  std::vector<unsigned char> host;         // its host image (kept alive for the async copy)
+};
+
 struct fo_problem {
   fo_ctx *ctx;
   fo_mesh *mesh;
@@ -118,6 +133,8 @@ struct fo_problem {
   int transport_smooth = 0;
   double last_lambda = 0;
   fo_batch *batch = nullptr;     // non-null for a task-parallel batch (FO_HELMHOLTZ)
+  fo_mg *mg = nullptr;           // multigrid hierarchy, built on the first multigrid solve
+  long long coef_epoch = 0;      // incremented by every coefficient update
 };
 
 // status helpers
@@ -334,6 +351,24 @@ __device__ __forceinline__ void grid_total(const double *partials, double *smem_
   __syncthreads();
 }
 
+// Block-sum the NR values, publish the block partial, wait for the grid, and sum all
+// partials in a fixed order into stot.  Consecutive reductions alternate between two
+// partial buffers: a block that races ahead to the next reduction cannot overwrite a
+// partial that a slower block is still summing (it passed the barrier in between).
+template <int NR>
+__device__ __forceinline__ bool reduce_grid(double (&v)[NR], double *sred, double *stot, double *partials, int &rk,
+                                            const GridBar &bar) {
+  block_sum<NR>(v, sred);
+  double *part = partials + (size_t)(rk & 1) * gridDim.x * NR;
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) part[(size_t)blockIdx.x * NR + j] = v[j];
+  if (!grid_sync(bar)) return false;
+  grid_total<NR>(part, stot);
+  ++rk;
+  return true;
+}
+
 // ---- host launch helpers ------------------------------------------------------------------
 inline int fo_blocks_for(long long n, int block = FO_BLOCK, int cap = 1 << 20) {
   long long b = (n + block - 1) / block;
@@ -352,6 +387,12 @@ fo_status fo_batch_state(fo_problem *p, bool adjoint, const fo_solve_opts *o, fo
 fo_status fo_batch_functionals(fo_problem *p, double *J, double *vol, double *J_inst);
 fo_status fo_batch_shape_rhs(fo_problem *p, double lambda);
 fo_status fo_batch_apply(fo_problem *p, const double *x, double *y, bool fp32);
+// multigrid (fo_mg.cu)
+fo_status fo_state_pcg_mg(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st);
+void fo_mg_destroy(fo_problem *p);
+size_t fo_mg_bytes(int dim, const int n[3], int npn);
+fo_status fo_launch_stencil_on(fo_problem *p, const Grid &g, const double *coef, const uint8_t *dir, double *W,
+                               float *W32, double *dinv, float *dinv32);
 fo_status fo_launch_loads(fo_problem *p);
 fo_status fo_launch_masks(fo_problem *p);
 fo_status fo_launch_state_diag(fo_problem *p);
@@ -362,6 +403,7 @@ fo_status fo_launch_velocity_apply(fo_problem *p, const double *x, double *y);
 fo_status fo_launch_functionals(fo_problem *p, double *J, double *vol);
 fo_status fo_launch_shape_rhs(fo_problem *p, double lambda);
 fo_status fo_launch_mesh_build(fo_mesh *m);
+bool fo_grid_make(int dim, const int n[3], const double lo[3], const double hi[3], Grid &g);
 size_t fo_problem_footprint(int dim, const int n[3], int kind, int precision, int n_bumps);
 fo_status fo_launch_phi_bumps(fo_problem *p, int count, const double *centers, double width, double offset);
 fo_status fo_launch_initial_level(fo_problem *p, int count, const double *centers, const double *radii,

@@ -81,24 +81,6 @@ struct PcgArgs {
   int warm;
 };
 
-// Block-sum the NR values, publish the block partial, wait for the grid, and sum all
-// partials in a fixed order into stot.  Consecutive reductions alternate between two
-// partial buffers: a block that races ahead to the next reduction cannot overwrite a
-// partial that a slower block is still summing (it passed the barrier in between).
-template <int NR>
-__device__ __forceinline__ bool reduce_grid(double (&v)[NR], double *sred, double *stot, double *partials, int &rk,
-                                            const GridBar &bar) {
-  block_sum<NR>(v, sred);
-  double *part = partials + (size_t)(rk & 1) * gridDim.x * NR;
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int j = 0; j < NR; ++j) part[(size_t)blockIdx.x * NR + j] = v[j];
-  if (!grid_sync(bar)) return false;
-  grid_total<NR>(part, stot);
-  ++rk;
-  return true;
-}
-
 // u_{i+1} at any DOF, formed from the previous iteration's r, w, s (see the file comment)
 template <typename T, int NC>
 struct NextU {
@@ -473,6 +455,7 @@ static fo_status state_solve_impl(fo_problem *p, const Op64 &op64, const OpMixed
 
 fo_status fo_state_pcg(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st) {
   const Grid &g = p->mesh->g;
+  if (o->precond == FO_PC_MG && !p->batch) return fo_state_pcg_mg(p, b, x, o, st);
   // stored-stencil operators: FP64 rows for the FP64 solve and the refinement residual, FP32
   // rows for the inner solve of the mixed path
   if (p->desc.kind == FO_ELASTIC) {

@@ -1,0 +1,618 @@
+// Geometric multigrid preconditioner for the state solve: an FP64 conjugate-gradient loop whose
+// preconditioner is one FP32 V-cycle, all in one persistent cooperative launch.
+//
+// The Kuhn triangulation is nested under uniform refinement (each simplex of the grid with
+// n/2 cells per axis is the union of 2^d simplices of the grid with n cells), so the P1 spaces
+// are nested and the Galerkin coarse operator P^T A P is exactly the P1 operator of the coarse
+// grid with each coarse element's coefficient the mean of its 2^d fine children's (A is
+// piecewise constant; the mass terms have constant coefficients).  Coarse rows are therefore
+// built by the same stencil builder as the fine ones, from restricted coefficients.  P is P1
+// interpolation along the Kuhn edges: a fine node with index parities b in {0,1}^d takes the
+// mean of the coarse nodes (i - b)/2 and (i + b)/2; the restriction is P^T.  Smoother: damped
+// Jacobi, nu1 = nu2 sweeps; coarsest level: nuc sweeps.  Levels of at most MG_BLOCK_DOFS
+// unknowns are run by block 0 alone with block barriers only (a grid barrier per sweep would
+// dominate their tiny work); the rest by the whole grid with grid barriers.
+//
+// The V-cycle is a fixed linear map (same sweeps and damping every call), symmetric up to
+// FP32 rounding, so plain PCG applies; the CG residual, directions and dot products are FP64
+// and the CG stops on ||b - A x||_2 (recurrence) <= rtol ||b||_2.
+#include <cmath>
+#include <cstring>
+#include <algorithm>
+#include <vector>
+
+#include "fo_internal.cuh"
+#include "fo_ops.cuh"
+
+#define MG_BLOCK_DOFS 1024
+
+struct MgLevelDev {
+  Grid g;
+  const float *W;       // difference-form stencil rows [S][BLK][N]
+  const float *dinv;    // [N * NPN]
+  const uint8_t *dir;   // [N * NPN]
+  float *b, *z[2], *t;  // right-hand side, iterate (ping-pong), residual
+};
+
+struct MgDev {
+  int L, Lg;            // levels; levels >= Lg run in block 0 alone
+  float omega;
+  int nu, nuc;
+  MgLevelDev lv[MG_MAX_LEVELS];
+};
+
+struct MgCg {
+  const double *W64;    // fine FP64 stencil rows
+  const double *b;      // right-hand side (zero on Dirichlet DOFs)
+  double *x;            // solution (start value when warm)
+  double *r, *p[2], *s, *z;
+  double *partials, *out;
+  int *status;
+  GridBar bar;
+  double rtol2;
+  int maxit, warm;
+};
+
+// ------------------------------------------------------------------ level operations
+template <int D, int NPN>
+struct MgOps {
+  using Op = StencilOp<D, NPN, true, float>;
+  static __device__ __forceinline__ Op op(const MgLevelDev &L) {
+    Op o;
+    o.g = L.g;
+    o.W = L.W;
+    return o;
+  }
+  // one damped Jacobi sweep z_out = z_in + omega D^{-1} (b - A z_in) over nodes [first, N) step
+  static __device__ void sweep(const MgLevelDev &L, const float *zin, float *zout, float omega, long long first,
+                               long long step) {
+    const Op o = op(L);
+    for (long long a = first; a < L.g.num_nodes; a += step) {
+      int idx[3];
+      node_ijk(L.g, a, idx);
+      float az[NPN];
+      o.row(a, idx, VecX<float>{zin}, az);
+#pragma unroll
+      for (int c = 0; c < NPN; ++c) {
+        const long long k = a * NPN + c;
+        zout[k] = zin[k] + omega * L.dinv[k] * (L.b[k] - az[c]);
+      }
+    }
+  }
+  static __device__ void residual(const MgLevelDev &L, const float *z, long long first, long long step) {
+    const Op o = op(L);
+    for (long long a = first; a < L.g.num_nodes; a += step) {
+      int idx[3];
+      node_ijk(L.g, a, idx);
+      float az[NPN];
+      o.row(a, idx, VecX<float>{z}, az);
+#pragma unroll
+      for (int c = 0; c < NPN; ++c) L.t[a * NPN + c] = L.b[a * NPN + c] - az[c];
+    }
+  }
+  // coarse b = P^T t (fine residual), and the coarse level's first sweep from zero
+  static __device__ void restrict_(const MgLevelDev &F, const MgLevelDev &C, float omega, long long first,
+                                   long long step) {
+    for (long long c = first; c < C.g.num_nodes; c += step) {
+      int ic[3];
+      node_ijk(C.g, c, ic);
+      int ifn[3] = {2 * ic[0], D >= 2 ? 2 * ic[1] : 0, D == 3 ? 2 * ic[2] : 0};
+      const long long f0 = ifn[0] + F.g.stride[1] * ifn[1] + (D == 3 ? F.g.stride[2] * ifn[2] : 0);
+      float v[NPN];
+#pragma unroll
+      for (int j = 0; j < NPN; ++j) v[j] = F.t[f0 * NPN + j];
+#pragma unroll
+      for (int s = 1; s < ST<D>::S; ++s) {
+        const long long nb = slot_node<D>(F.g, ifn, f0, s);
+        if (nb < 0) continue;
+#pragma unroll
+        for (int j = 0; j < NPN; ++j) v[j] += 0.5f * F.t[nb * NPN + j];
+      }
+#pragma unroll
+      for (int j = 0; j < NPN; ++j) {
+        const long long k = c * NPN + j;
+        const float bk = C.dir[k] ? 0.f : v[j];
+        C.b[k] = bk;
+        C.z[0][k] = omega * C.dinv[k] * bk;
+      }
+    }
+  }
+  // fine z += P (coarse z)
+  static __device__ void prolong(const MgLevelDev &F, float *zf, const MgLevelDev &C, const float *zc,
+                                 long long first, long long step) {
+    for (long long a = first; a < F.g.num_nodes; a += step) {
+      int idx[3];
+      node_ijk(F.g, a, idx);
+      long long c1 = 0, c2 = 0;
+      bool mid = false;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const int bit = idx[k] & 1;
+        mid |= bit != 0;
+        c1 += (long long)((idx[k] - bit) / 2) * C.g.stride[k];
+        c2 += (long long)((idx[k] + bit) / 2) * C.g.stride[k];
+      }
+#pragma unroll
+      for (int j = 0; j < NPN; ++j) {
+        const long long k = a * NPN + j;
+        if (F.dir[k]) continue;
+        const float v = mid ? 0.5f * (zc[c1 * NPN + j] + zc[c2 * NPN + j]) : zc[c1 * NPN + j];
+        zf[k] += v;
+      }
+    }
+  }
+};
+
+// The V-cycle on levels l >= from, in block 0 alone (block barriers), starting from b_from and
+// z_from[0] (its first sweep from zero already taken).  zc[l]: buffer holding level l's iterate.
+template <int D, int NPN>
+__device__ void mg_block_cycle(const MgDev &mg, int from, int *zc) {
+  using M = MgOps<D, NPN>;
+  const long long t = threadIdx.x, st = blockDim.x;
+  for (int l = from; l < mg.L; ++l) {
+    const MgLevelDev &L = mg.lv[l];
+    const int sweeps = (l == mg.L - 1) ? mg.nuc : mg.nu;
+    int c = 0;
+    for (int j = 1; j < sweeps; ++j) {
+      __syncthreads();
+      M::sweep(L, L.z[c], L.z[c ^ 1], mg.omega, t, st);
+      c ^= 1;
+    }
+    zc[l] = c;
+    if (l == mg.L - 1) break;
+    __syncthreads();
+    M::residual(L, L.z[c], t, st);
+    __syncthreads();
+    M::restrict_(L, mg.lv[l + 1], mg.omega, t, st);
+  }
+  for (int l = mg.L - 2; l >= from; --l) {
+    const MgLevelDev &L = mg.lv[l];
+    __syncthreads();
+    M::prolong(L, L.z[zc[l]], mg.lv[l + 1], mg.lv[l + 1].z[zc[l + 1]], t, st);
+    int c = zc[l];
+    for (int j = 0; j < mg.nu; ++j) {
+      __syncthreads();
+      M::sweep(L, L.z[c], L.z[c ^ 1], mg.omega, t, st);
+      c ^= 1;
+    }
+    zc[l] = c;
+  }
+  __syncthreads();
+}
+
+// The V-cycle from level 0, whose b and first sweep were written by the caller before a grid
+// barrier.  Returns false if a grid barrier failed; level 0's result is in z[zc[0]].
+template <int D, int NPN>
+__device__ bool mg_vcycle(const MgDev &mg, int *zc, const GridBar &bar) {
+  using M = MgOps<D, NPN>;
+  const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x, step = (long long)gridDim.x * blockDim.x;
+  const int Lg = mg.Lg;
+  if (Lg == 0) {   // everything is small: block 0 runs the whole cycle
+    if (blockIdx.x == 0) mg_block_cycle<D, NPN>(mg, 0, zc);
+    return grid_sync(bar);
+  }
+  for (int l = 0; l < Lg; ++l) {
+    const MgLevelDev &L = mg.lv[l];
+    const bool coarsest = l == mg.L - 1;
+    const int sweeps = coarsest ? mg.nuc : mg.nu;
+    int c = 0;
+    for (int j = 1; j < sweeps; ++j) {
+      M::sweep(L, L.z[c], L.z[c ^ 1], mg.omega, first, step);
+      c ^= 1;
+      if (!grid_sync(bar)) return false;
+    }
+    zc[l] = c;
+    if (coarsest) break;
+    M::residual(L, L.z[c], first, step);
+    if (!grid_sync(bar)) return false;
+    M::restrict_(L, mg.lv[l + 1], mg.omega, first, step);
+    if (!grid_sync(bar)) return false;
+  }
+  if (Lg < mg.L) {   // the other blocks know the block-run levels' final buffers (fixed)
+    if (blockIdx.x == 0) mg_block_cycle<D, NPN>(mg, Lg, zc);
+    if (!grid_sync(bar)) return false;
+  }
+  for (int l = std::min(Lg, mg.L - 1) - 1; l >= 0; --l) {
+    const MgLevelDev &L = mg.lv[l];
+    M::prolong(L, L.z[zc[l]], mg.lv[l + 1], mg.lv[l + 1].z[zc[l + 1]], first, step);
+    if (!grid_sync(bar)) return false;
+    int c = zc[l];
+    for (int j = 0; j < mg.nu; ++j) {
+      M::sweep(L, L.z[c], L.z[c ^ 1], mg.omega, first, step);
+      c ^= 1;
+      if (l > 0 || j + 1 < mg.nu)
+        if (!grid_sync(bar)) return false;
+    }
+    zc[l] = c;
+  }
+  return true;
+}
+
+// Buffer index of each level's final iterate after a V-cycle: fixed by the sweep counts, so
+// every block knows it without communication.
+__host__ __device__ inline void mg_final_buffers(int L, int Lg, int nu, int nuc, int *zc) {
+  for (int l = 0; l < L; ++l) {
+    const int sweeps = (l == L - 1) ? nuc : nu;
+    int c = (sweeps - 1) & 1;                      // after the down sweeps
+    if (l < L - 1) c = (c + nu) & 1;               // after the post sweeps
+    zc[l] = c;
+  }
+  (void)Lg;
+}
+
+template <int D, int NPN>
+__global__ void __launch_bounds__(FO_BLOCK) k_pcg_mg(const MgDev *mgp, MgCg C) {
+  __shared__ MgDev mg;
+  __shared__ double sred[32 * 3];
+  __shared__ double stot[3];
+  {
+    const int *src = reinterpret_cast<const int *>(mgp);
+    int *dst = reinterpret_cast<int *>(&mg);
+    for (int i = threadIdx.x; i < (int)(sizeof(MgDev) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  using M = MgOps<D, NPN>;
+  const MgLevelDev &L0 = mg.lv[0];
+  const Grid &g = L0.g;
+  const long long N = g.num_nodes;
+  const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x, step = (long long)gridDim.x * blockDim.x;
+  StencilOp<D, NPN, true, double> A;
+  A.g = g;
+  A.W = C.W64;
+  int rk = 0, zc[MG_MAX_LEVELS];
+  mg_final_buffers(mg.L, mg.Lg, mg.nu, mg.nuc, zc);
+  const int zfin = zc[0];
+
+  // r = b - A x;  level-0 right-hand side and first sweep;  ||b||^2
+  double v[3] = {0.0, 0.0, 0.0};
+  for (long long a = first; a < N; a += step) {
+    int idx[3];
+    node_ijk(g, a, idx);
+    double ax[NPN];
+    if (C.warm) A.row(a, idx, VecX<double>{C.x}, ax);
+#pragma unroll
+    for (int c = 0; c < NPN; ++c) {
+      const long long k = a * NPN + c;
+      if (!C.warm) {
+        C.x[k] = 0.0;
+        ax[c] = 0.0;
+      }
+      const double rk0 = C.b[k] - ax[c];
+      C.r[k] = rk0;
+      C.p[0][k] = 0.0;
+      const float bf = (float)rk0;
+      L0.b[k] = bf;
+      L0.z[0][k] = mg.omega * L0.dinv[k] * bf;
+      v[1] += C.b[k] * C.b[k];
+    }
+  }
+  if (!grid_sync(C.bar)) goto fail;
+  if (!mg_vcycle<D, NPN>(mg, zc, C.bar)) goto fail;
+  {
+    // z = M r; gamma = (r, z); rho = (r, r)
+    double gam = 0.0, bb = 0.0;
+    v[0] = v[2] = 0.0;
+    for (long long a = first; a < N; a += step)
+#pragma unroll
+      for (int c = 0; c < NPN; ++c) {
+        const long long k = a * NPN + c;
+        const double zk = (double)L0.z[zfin][k];
+        C.z[k] = zk;
+        v[0] += C.r[k] * zk;
+        v[2] += C.r[k] * C.r[k];
+      }
+    if (!reduce_grid<3>(v, sred, stot, C.partials, rk, C.bar)) goto fail;
+    gam = stot[0];
+    bb = stot[1];
+    double rho = stot[2];
+    double beta = 0.0;
+    int it = 0;
+    int cur = 0;
+    while (rho > C.rtol2 * bb && it < C.maxit && gam > 0.0) {
+      // p = z + beta p_old (formed at neighbours on the fly); s = A p; (p, s)
+      double ps[1] = {0.0};
+      const double *po = C.p[cur];
+      double *pn = C.p[cur ^ 1];
+      for (long long a = first; a < N; a += step) {
+        int idx[3];
+        node_ijk(g, a, idx);
+        double ap[NPN];
+        A.row(a, idx, CombX<double, 1>{C.z, po, {beta}}, ap);
+#pragma unroll
+        for (int c = 0; c < NPN; ++c) {
+          const long long k = a * NPN + c;
+          const double pk = C.z[k] + beta * po[k];
+          pn[k] = pk;
+          C.s[k] = ap[c];
+          ps[0] += pk * ap[c];
+        }
+      }
+      if (!reduce_grid<1>(ps, sred, stot, C.partials, rk, C.bar)) goto fail;
+      const double alpha = gam / stot[0];
+      if (!(stot[0] > 0.0)) break;   // lost positive definiteness in rounding: stop with x as is
+      cur ^= 1;
+      // x += alpha p; r -= alpha s; level-0 right-hand side and first sweep
+      for (long long a = first; a < N; a += step)
+#pragma unroll
+        for (int c = 0; c < NPN; ++c) {
+          const long long k = a * NPN + c;
+          C.x[k] += alpha * pn[k];
+          const double rk1 = C.r[k] - alpha * C.s[k];
+          C.r[k] = rk1;
+          const float bf = (float)rk1;
+          L0.b[k] = bf;
+          L0.z[0][k] = mg.omega * L0.dinv[k] * bf;
+        }
+      if (!grid_sync(C.bar)) goto fail;
+      if (!mg_vcycle<D, NPN>(mg, zc, C.bar)) goto fail;
+      double w[2] = {0.0, 0.0};
+      for (long long a = first; a < N; a += step)
+#pragma unroll
+        for (int c = 0; c < NPN; ++c) {
+          const long long k = a * NPN + c;
+          const double zk = (double)L0.z[zfin][k];
+          C.z[k] = zk;
+          w[0] += C.r[k] * zk;
+          w[1] += C.r[k] * C.r[k];
+        }
+      if (!reduce_grid<2>(w, sred, stot, C.partials, rk, C.bar)) goto fail;
+      beta = stot[0] / gam;
+      gam = stot[0];
+      rho = stot[1];
+      ++it;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      C.out[0] = rho;
+      C.out[1] = bb;
+      C.status[DS_ITERS] = it;
+      if (rho > C.rtol2 * bb && it >= C.maxit) atomicCAS(C.status + DS_ERR, DEV_OK, DEV_NOCONV);
+    }
+    return;
+  }
+fail:
+  return;
+}
+
+// ===================================================================================== host
+template <int D>
+__global__ void k_mg_restrict_coef(Grid gc, Grid gf, const double *coef_f, double *coef_c) {
+  constexpr int P = KP<D>::P;
+  for (long long ec = blockIdx.x * (long long)blockDim.x + threadIdx.x; ec < gc.num_elems;
+       ec += (long long)gridDim.x * blockDim.x) {
+    const long long cell = ec / P;
+    const int pc = (int)(ec % P);
+    int ci[3];
+    ci[0] = (int)(cell % gc.n[0]);
+    const long long t = cell / gc.n[0];
+    ci[1] = (int)(t % gc.n[1]);
+    ci[2] = (int)(t / gc.n[1]);
+    double sum = 0.0;
+    for (int o = 0; o < (1 << D); ++o) {
+      int fi[3] = {2 * ci[0] + (o & 1), 2 * ci[1] + ((o >> 1) & 1), D == 3 ? 2 * ci[2] + ((o >> 2) & 1) : 0};
+      const long long fcell = fi[0] + gf.cstride[1] * fi[1] + (D == 3 ? gf.cstride[2] * fi[2] : 0);
+      for (int pf = 0; pf < P; ++pf) {
+        // the coarse simplex holding fine simplex pf of the fine cell at offset o: axes sorted
+        // by offset (descending), ties in the fine simplex's own axis order
+        int order[3], n = 0;
+        for (int ob = 1; ob >= 0; --ob)
+          for (int l = 0; l < D; ++l) {
+            const int ax = kperm<D>(pf, l);
+            if (((o >> ax) & 1) == ob) order[n++] = ax;
+          }
+        int q = -1;
+        for (int cand = 0; cand < P && q < 0; ++cand) {
+          bool same = true;
+          for (int l = 0; l < D; ++l) same = same && kperm<D>(cand, l) == order[l];
+          if (same) q = cand;
+        }
+        if (q == pc) sum += coef_f[(long long)P * fcell + pf];
+      }
+    }
+    coef_c[ec] = sum / (double)(1 << D);
+  }
+}
+
+__global__ void k_mg_coarse_dir(Grid gc, Grid gf, int npn, const uint8_t *dir_f, uint8_t *dir_c) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < gc.num_nodes;
+       c += (long long)gridDim.x * blockDim.x) {
+    int ic[3];
+    node_ijk(gc, c, ic);
+    const long long f = 2LL * ic[0] + gf.stride[1] * 2LL * ic[1] + (gc.dim == 3 ? gf.stride[2] * 2LL * ic[2] : 0);
+    for (int j = 0; j < npn; ++j) dir_c[c * npn + j] = dir_f[f * npn + j];
+  }
+}
+
+static size_t mg_level_bytes(const Grid &g, int npn, bool coarse) {
+  const size_t N = (size_t)g.num_nodes, S = g.dim == 2 ? 7 : 15, BLK = (size_t)npn * npn;
+  size_t b = sizeof(float) * 4 * N * npn;                           // b, z[2], t
+  if (coarse)
+    b += sizeof(double) * g.num_elems + sizeof(double) * S * BLK * N + sizeof(float) * S * BLK * N +
+         sizeof(double) * N * npn + sizeof(float) * N * npn + N * npn;   // coef, W64, W32, dinv, dinv32, dir
+  return b;
+}
+
+static void mg_free(fo_problem *p) {
+  fo_mg *mg = p->mg;
+  if (!mg) return;
+  fo_ctx *ctx = p->ctx;
+  for (int l = 0; l < mg->L; ++l) {
+    const size_t N = (size_t)mg->g[l].num_nodes * mg->npn, S = mg->g[l].dim == 2 ? 7 : 15,
+                 BLK = (size_t)mg->npn * mg->npn, Nn = (size_t)mg->g[l].num_nodes;
+    fo_free(ctx, mg->b[l], sizeof(float) * N);
+    fo_free(ctx, mg->z0[l], sizeof(float) * N);
+    fo_free(ctx, mg->z1[l], sizeof(float) * N);
+    fo_free(ctx, mg->t[l], sizeof(float) * N);
+    if (l > 0) {
+      fo_free(ctx, mg->coef[l], sizeof(double) * mg->g[l].num_elems);
+      fo_free(ctx, mg->W64[l], sizeof(double) * S * BLK * Nn);
+      fo_free(ctx, mg->W32[l], sizeof(float) * S * BLK * Nn);
+      fo_free(ctx, mg->dinv64[l], sizeof(double) * N);
+      fo_free(ctx, mg->dinv32[l], sizeof(float) * N);
+      fo_free(ctx, mg->dir[l], N);
+    }
+  }
+  fo_free(ctx, mg->dev, sizeof(MgDev));
+  delete mg;
+  p->mg = nullptr;
+}
+
+void fo_mg_destroy(fo_problem *p) { mg_free(p); }
+
+// Levels: halve every axis while all are even and the coarse grid keeps >= 2 cells per axis.
+static int mg_plan(const Grid &g0, Grid *g, int max_levels) {
+  g[0] = g0;
+  int L = 1;
+  while (L < max_levels) {
+    const Grid &f = g[L - 1];
+    int n[3] = {1, 1, 1};
+    bool ok = true;
+    for (int a = 0; a < f.dim; ++a) {
+      if (f.n[a] % 2 != 0 || f.n[a] / 2 < 2) ok = false;
+      n[a] = f.n[a] / 2;
+    }
+    if (!ok) break;
+    if (!fo_grid_make(f.dim, n, f.lo, f.hi, g[L])) break;
+    ++L;
+  }
+  return L;
+}
+
+size_t fo_mg_bytes(int dim, const int n[3], int npn) {
+  Grid g0;
+  if (!fo_grid_make(dim, n, (const double[3]){0, 0, 0}, (const double[3]){1, 1, 1}, g0)) return 0;
+  Grid g[MG_MAX_LEVELS];
+  const int L = mg_plan(g0, g, MG_MAX_LEVELS);
+  size_t b = sizeof(MgDev);
+  for (int l = 0; l < L; ++l) b += mg_level_bytes(g[l], npn, l > 0);
+  return b;
+}
+
+// Build (first call) and refresh (each coefficient update) the hierarchy.
+static fo_status mg_prepare(fo_problem *p) {
+  fo_ctx *ctx = p->ctx;
+  const Grid &g0 = p->mesh->g;
+  const int npn = p->ncomp;
+  if (!p->mg) {
+    fo_mg *mg = new fo_mg();
+    p->mg = mg;
+    mg->npn = npn;
+    mg->L = mg_plan(g0, mg->g, MG_MAX_LEVELS);
+    for (int l = 0; l < mg->L; ++l) {
+      const size_t N = (size_t)mg->g[l].num_nodes * npn, S = g0.dim == 2 ? 7 : 15, BLK = (size_t)npn * npn,
+                   Nn = (size_t)mg->g[l].num_nodes;
+      FO_TRY(fo_alloc(ctx, (void **)&mg->b[l], sizeof(float) * N));
+      FO_TRY(fo_alloc(ctx, (void **)&mg->z0[l], sizeof(float) * N));
+      FO_TRY(fo_alloc(ctx, (void **)&mg->z1[l], sizeof(float) * N));
+      FO_TRY(fo_alloc(ctx, (void **)&mg->t[l], sizeof(float) * N));
+      if (l > 0) {
+        FO_TRY(fo_alloc(ctx, (void **)&mg->coef[l], sizeof(double) * mg->g[l].num_elems));
+        FO_TRY(fo_alloc(ctx, (void **)&mg->W64[l], sizeof(double) * S * BLK * Nn));
+        FO_TRY(fo_alloc(ctx, (void **)&mg->W32[l], sizeof(float) * S * BLK * Nn));
+        FO_TRY(fo_alloc(ctx, (void **)&mg->dinv64[l], sizeof(double) * N));
+        FO_TRY(fo_alloc(ctx, (void **)&mg->dinv32[l], sizeof(float) * N));
+        FO_TRY(fo_alloc(ctx, (void **)&mg->dir[l], N));
+      }
+    }
+    FO_TRY(fo_alloc(ctx, (void **)&mg->dev, sizeof(MgDev)));
+    mg->built_epoch = -1;
+  }
+  fo_mg *mg = p->mg;
+  if (mg->built_epoch == p->coef_epoch) return FO_OK;
+  cudaStream_t s = ctx->stream;
+  for (int l = 1; l < mg->L; ++l) {
+    const Grid &gc = mg->g[l], &gf = mg->g[l - 1];
+    const uint8_t *df = l == 1 ? p->dir : mg->dir[l - 1];
+    const int blocks = fo_blocks_for(gc.num_elems, FO_BLOCK, 65536);
+    if (gc.dim == 2) k_mg_restrict_coef<2><<<blocks, FO_BLOCK, 0, s>>>(gc, gf, l == 1 ? p->coef : mg->coef[l - 1], mg->coef[l]);
+    else k_mg_restrict_coef<3><<<blocks, FO_BLOCK, 0, s>>>(gc, gf, l == 1 ? p->coef : mg->coef[l - 1], mg->coef[l]);
+    k_mg_coarse_dir<<<fo_blocks_for(gc.num_nodes, FO_BLOCK, 65536), FO_BLOCK, 0, s>>>(gc, gf, npn, df, mg->dir[l]);
+    fo_note_launch(2);
+    FO_TRY(fo_launch_stencil_on(p, gc, mg->coef[l], mg->dir[l], mg->W64[l], mg->W32[l], mg->dinv64[l], mg->dinv32[l]));
+  }
+  MgDev h;
+  memset(&h, 0, sizeof h);
+  h.L = mg->L;
+  h.Lg = mg->L;
+  for (int l = 0; l < mg->L; ++l)
+    if ((long long)mg->g[l].num_nodes * npn <= MG_BLOCK_DOFS) {
+      h.Lg = l;
+      break;
+    }
+  h.omega = npn == 1 ? 0.8f : 0.6f;
+  h.nu = 2;
+  h.nuc = 16;
+  for (int l = 0; l < mg->L; ++l) {
+    MgLevelDev &d = h.lv[l];
+    d.g = mg->g[l];
+    d.W = l == 0 ? p->Wst32 : mg->W32[l];
+    d.dinv = l == 0 ? p->dinv_state32 : mg->dinv32[l];
+    d.dir = l == 0 ? p->dir : mg->dir[l];
+    d.b = mg->b[l];
+    d.z[0] = mg->z0[l];
+    d.z[1] = mg->z1[l];
+    d.t = mg->t[l];
+  }
+  mg->host.resize(sizeof(MgDev));
+  memcpy(mg->host.data(), &h, sizeof(MgDev));
+  FO_CU(ctx, cudaMemcpyAsync(mg->dev, mg->host.data(), sizeof(MgDev), cudaMemcpyHostToDevice, s));
+  FO_CU(ctx, cudaGetLastError());
+  mg->built_epoch = p->coef_epoch;
+  return FO_OK;
+}
+
+template <int D, int NPN>
+static fo_status mg_solve_t(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st) {
+  fo_ctx *ctx = p->ctx;
+  const long long n = p->ndof;
+  double *buf;
+  FO_TRY(fo_scratch(p, sizeof(double) * 6 * n, (void **)&buf));
+  MgCg C{};
+  C.W64 = p->Wst;
+  C.b = b;
+  C.x = x;
+  C.r = buf;
+  C.p[0] = buf + n;
+  C.p[1] = buf + 2 * n;
+  C.s = buf + 3 * n;
+  C.z = buf + 4 * n;
+  C.partials = p->red;
+  C.out = p->red + (FO_RED_DOUBLES - 64);
+  C.status = p->dev_status;
+  C.bar = GridBar{p->bar, p->dev_status + DS_ERR, 2000000000ull};
+  C.rtol2 = o->rtol * o->rtol;
+  C.maxit = o->maxit;
+  C.warm = o->warm_start;
+  auto kern = k_pcg_mg<D, NPN>;
+  int grid;
+  FO_TRY(fo_cooperative_grid(p, (const void *)kern, FO_BLOCK, 0, p->mesh->g.num_nodes, o->grid_blocks, &grid));
+  const MgDev *mgp = (const MgDev *)p->mg->dev;
+  void *argv[] = {(void *)&mgp, (void *)&C};
+  FO_CU(ctx, cudaMemsetAsync(p->bar, 0, 64, ctx->stream));
+  FO_CU(ctx, cudaMemsetAsync(p->dev_status, 0, sizeof(int) * DS_COUNT, ctx->stream));
+  FO_CU(ctx, cudaLaunchCooperativeKernel((const void *)kern, grid, FO_BLOCK, argv, 0, ctx->stream));
+  fo_note_launch(1);
+  FO_CU(ctx, cudaGetLastError());
+  FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars, C.out, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars + 32, p->dev_status, sizeof(int) * DS_COUNT, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+  FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  const int *hs = (const int *)(ctx->h_scalars + 32);
+  if (st) {
+    memset(st, 0, sizeof *st);
+    st->iterations = hs[DS_ITERS];
+    st->operator_applies = hs[DS_ITERS] + 1 + (o->warm_start ? 1 : 0);
+    st->outer_iterations = 1;
+    st->rel_residual = ctx->h_scalars[1] > 0 ? std::sqrt(ctx->h_scalars[0] / ctx->h_scalars[1]) : 0.0;
+  }
+  if (hs[DS_ERR] == DEV_TIMEOUT) return fo_fail(ctx, FO_ETIMEOUT, "grid barrier timed out in the multigrid PCG");
+  if (hs[DS_ERR] == DEV_NOCONV) return fo_fail(ctx, FO_ENOCONV, "multigrid PCG reached maxit=%d", o->maxit);
+  if (!std::isfinite(ctx->h_scalars[0])) return fo_fail(ctx, FO_ENAN, "NaN in the multigrid PCG");
+  return FO_OK;
+}
+
+fo_status fo_state_pcg_mg(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st) {
+  FO_TRY(mg_prepare(p));
+  const int d = p->mesh->g.dim;
+  if (p->desc.kind == FO_ELASTIC) return d == 2 ? mg_solve_t<2, 2>(p, b, x, o, st) : mg_solve_t<3, 3>(p, b, x, o, st);
+  return d == 2 ? mg_solve_t<2, 1>(p, b, x, o, st) : mg_solve_t<3, 1>(p, b, x, o, st);
+}

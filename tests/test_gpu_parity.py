@@ -35,8 +35,9 @@ def ctx(api):
     c.close()
 
 
-def tight(api, precision=None):
-    return api.solve_opts(precision=api.FO_FP64 if precision is None else precision, rtol=1e-13, maxit=400000)
+def tight(api, precision=None, precond=0):
+    return api.solve_opts(precision=api.FO_FP64 if precision is None else precision, rtol=1e-13, maxit=400000,
+                          precond=precond)
 
 
 # ------------------------------------------------------------------------------- mesh
@@ -165,13 +166,16 @@ def test_velocity_apply(ctx, api, c):
     cantilever3d((12, 6, 6)),
     case(dim=2, n=(40, 40), kind=2, k=0.8, omega=4.0, f=lambda X: np.cos(np.pi * X[:, 0]) + X[:, 1], dirichlet=[(0, 0)]),
 ])
-def test_state_solve_fp64(ctx, api, c):
+@pytest.mark.parametrize("pc", [0, 1], ids=["jacobi", "multigrid"])
+def test_state_solve_fp64(ctx, api, c, pc):
     mesh, prob = gpu_problem(ctx, c)
     op = oracle_problem(c)
     phi = (workloads.phi_cos(op.mesh.coords) if c["dim"] == 2 else
            workloads.phi_bumps(op.mesh.coords, workloads.bump_centres(c["lo"], c["hi"], 8, 0), 0.25, 0.2))
     prob.set_levelset(phi)
-    st = prob.state_solve(tight(api))
+    st = prob.state_solve(tight(api, precond=pc))
+    if pc == 1 and all(n % 4 == 0 for n in c["n"]):
+        assert st.iterations < 400, st.iterations   # at least two coarse levels: multigrid rates
     u = prob.get(api._lib.FO_FIELD_U)
     u_ref, A, chi = op.state(phi)
     K, F, free = op.stiffness(A), op.load(), op.dirichlet() == 0
