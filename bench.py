@@ -73,7 +73,7 @@ def run_options(api, precision, precond="mg"):
     prec = api.FO_MIXED if precision == "mixed" else api.FO_FP64
     pc = api.FO_PC_MG if precond == "mg" else api.FO_PC_JACOBI
     state = api.solve_opts(precision=prec, rtol=1e-12, warm_start=1, precond=pc)
-    vel = api.solve_opts(rtol=1e-12, warm_start=1)
+    vel = api.solve_opts(rtol=1e-12, warm_start=1, precond=pc)
     tr = api.solve_opts(rtol=1e-12)
     # no reinitialisation inside the 50 iterations: on this mesh the reinitialisation scheme
     # (Sec. 5.7) is unstable for the level sets the transport produces (the oracle shows the

@@ -442,10 +442,14 @@ __global__ void k_state_stencil(Grid g, const double *coef, const uint8_t *dir, 
 // every component the P1 Laplacian plus (alpha + gamma_0 chi_Omega0) times the consistent mass;
 // for component c on a face normal to axis c also gamma_b times the facet mass of that face (the
 // normal penalty couples only the normal component on an axis-aligned box).  H^1_0: identity
-// rows on boundary nodes, eliminated columns.
+// rows on boundary nodes, eliminated columns.  The mass-type coefficient of element e is
+// mcoef[e] when given (coarse multigrid levels: children means), else alpha + gamma_0 chi_Omega0;
+// the H^1_0 mask of node a is vmask[a * vstride].  FP32 copies are written when W32 / dinv32
+// are given.
 template <int D>
-__global__ void k_velocity_stencil(Grid g, const uint8_t *omega0, const uint8_t *vdir, double alpha, double gamma0,
-                                   double gammab, double *W, double *dinv) {
+__global__ void k_velocity_stencil(Grid g, const uint8_t *omega0, const double *mcoef, const uint8_t *vmask,
+                                   int vstride, double alpha, double gamma0, double gammab, double *W, float *W32,
+                                   double *dinv, float *dinv32) {
   constexpr int S = ST<D>::S;
   const long long N = g.num_nodes;
   const double mref = g.vol_e / ((D + 1) * (D + 2));
@@ -459,11 +463,12 @@ __global__ void k_velocity_stencil(Grid g, const uint8_t *omega0, const uint8_t 
     for (int s = 0; s < S; ++s)
 #pragma unroll
       for (int c = 0; c < D; ++c) w[s][c] = 0.0;
-    if (vdir[a]) {
+    if (vmask[a * vstride]) {
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         R[c] = 1.0;
         dinv[a * D + c] = 1.0;
+        if (dinv32) dinv32[a * D + c] = 1.0f;
       }
     } else {
 #pragma unroll
@@ -472,7 +477,7 @@ __global__ void k_velocity_stencil(Grid g, const uint8_t *omega0, const uint8_t 
         for (int m = 0; m <= D; ++m) {
           long long e;
           if (!elem_of<D>(g, idx, p, m, e)) continue;
-          const double wm = (alpha + (omega0[e] ? gamma0 : 0.0)) * mref;
+          const double wm = (mcoef ? mcoef[e] : alpha + (omega0[e] ? gamma0 : 0.0)) * mref;
 #pragma unroll
           for (int c = 0; c < D; ++c) R[c] += wm * (D + 2);
           double gm[3];
@@ -535,7 +540,7 @@ __global__ void k_velocity_stencil(Grid g, const uint8_t *omega0, const uint8_t 
 #pragma unroll
       for (int s = 1; s < S; ++s) {
         const long long nb = slot_node<D>(g, idx, a, s);
-        if (nb >= 0 && vdir[nb])
+        if (nb >= 0 && vmask[nb * vstride])
 #pragma unroll
           for (int c = 0; c < D; ++c) {
             R[c] -= w[s][c];
@@ -543,14 +548,20 @@ __global__ void k_velocity_stencil(Grid g, const uint8_t *omega0, const uint8_t 
           }
       }
 #pragma unroll
-      for (int c = 0; c < D; ++c) dinv[a * D + c] = 1.0 / w[0][c];
+      for (int c = 0; c < D; ++c) {
+        dinv[a * D + c] = 1.0 / w[0][c];
+        if (dinv32) dinv32[a * D + c] = (float)(1.0 / w[0][c]);
+      }
     }
 #pragma unroll
     for (int c = 0; c < D; ++c) w[0][c] = R[c];
 #pragma unroll
     for (int s = 0; s < S; ++s)
 #pragma unroll
-      for (int c = 0; c < D; ++c) W[(s * D + c) * N + a] = w[s][c];
+      for (int c = 0; c < D; ++c) {
+        W[(s * D + c) * N + a] = w[s][c];
+        if (W32) W32[(s * D + c) * N + a] = (float)w[s][c];
+      }
   }
 }
 
@@ -580,14 +591,34 @@ fo_status fo_launch_state_diag(fo_problem *p) {
   return fo_launch_stencil_on(p, p->mesh->g, p->coef, p->dir, p->Wst, p->Wst32, p->dinv_state, p->dinv_state32);
 }
 
+// Velocity rows on grid g (the problem's or a coarser one) from a per-element mass-type
+// coefficient and a per-DOF H^1_0 mask of that grid (component 0 of each node is read).
+fo_status fo_launch_velocity_stencil_on(fo_problem *p, const Grid &g, const double *mcoef, const uint8_t *dofmask,
+                                        double *W, float *W32, double *dinv, float *dinv32) {
+  const int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
+  cudaStream_t s = p->ctx->stream;
+  const double gb = p->desc.normal_penalty;
+  if (g.dim == 2)
+    k_velocity_stencil<2><<<blocks, FO_BLOCK, 0, s>>>(g, nullptr, mcoef, dofmask, 2, 0.0, 0.0, gb, W, W32, dinv, dinv32);
+  else
+    k_velocity_stencil<3><<<blocks, FO_BLOCK, 0, s>>>(g, nullptr, mcoef, dofmask, 3, 0.0, 0.0, gb, W, W32, dinv, dinv32);
+  fo_note_launch(1);
+  FO_CU(p->ctx, cudaGetLastError());
+  return FO_OK;
+}
+
 fo_status fo_launch_velocity_diag(fo_problem *p) {
   // the velocity form does not depend on phi: its stencil is built once per problem
   const Grid &g = p->mesh->g;
   int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
   cudaStream_t s = p->ctx->stream;
   const double gb = p->desc.normal_penalty, g0 = p->desc.omega0_weight, al = p->desc.alpha_mass;
-  if (g.dim == 2) k_velocity_stencil<2><<<blocks, FO_BLOCK, 0, s>>>(g, p->omega0, p->vdir, al, g0, gb, p->Wvel, p->dinv_vel);
-  else k_velocity_stencil<3><<<blocks, FO_BLOCK, 0, s>>>(g, p->omega0, p->vdir, al, g0, gb, p->Wvel, p->dinv_vel);
+  if (g.dim == 2)
+    k_velocity_stencil<2><<<blocks, FO_BLOCK, 0, s>>>(g, p->omega0, nullptr, p->vdir, 1, al, g0, gb, p->Wvel, nullptr,
+                                                      p->dinv_vel, nullptr);
+  else
+    k_velocity_stencil<3><<<blocks, FO_BLOCK, 0, s>>>(g, p->omega0, nullptr, p->vdir, 1, al, g0, gb, p->Wvel, nullptr,
+                                                      p->dinv_vel, nullptr);
   fo_note_launch(1);
   FO_CU(p->ctx, cudaGetLastError());
   return FO_OK;

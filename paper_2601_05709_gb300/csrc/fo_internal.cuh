@@ -83,7 +83,8 @@ struct fo_batch {
 // problem's grid, level l halves every axis of level l-1.
 #define MG_MAX_LEVELS 10
 struct fo_mg {
-  int L = 0, npn = 1;
+  int L = 0, npn = 1, blk = 1;             // components per node, stencil entries per slot
+  bool own0 = false;                       // level 0's FP32 rows, diagonal, mask owned here
   long long built_epoch = -1;
   Grid g[MG_MAX_LEVELS];
   float *b[MG_MAX_LEVELS] = {}, *z0[MG_MAX_LEVELS] = {}, *z1[MG_MAX_LEVELS] = {}, *t[MG_MAX_LEVELS] = {};
@@ -133,7 +134,8 @@ struct fo_problem {
   int transport_smooth = 0;
   double last_lambda = 0;
   fo_batch *batch = nullptr;     // non-null for a task-parallel batch (FO_HELMHOLTZ)
-  fo_mg *mg = nullptr;           // multigrid hierarchy, built on the first multigrid solve
+  fo_mg *mg = nullptr;           // state multigrid hierarchy, built on the first multigrid solve
+  fo_mg *mgv = nullptr;          // velocity multigrid hierarchy (the form is fixed: built once)
   long long coef_epoch = 0;      // incremented by every coefficient update
 };
 
@@ -390,7 +392,10 @@ fo_status fo_batch_apply(fo_problem *p, const double *x, double *y, bool fp32);
 // multigrid (fo_mg.cu)
 fo_status fo_state_pcg_mg(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st);
 void fo_mg_destroy(fo_problem *p);
-size_t fo_mg_bytes(int dim, const int n[3], int npn);
+size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0);
+fo_status fo_velocity_pcg_mg(fo_problem *p, const fo_solve_opts *o, double *Btt, fo_solve_stats *st);
+fo_status fo_launch_velocity_stencil_on(fo_problem *p, const Grid &g, const double *mcoef, const uint8_t *dofmask,
+                                        double *W, float *W32, double *dinv, float *dinv32);
 fo_status fo_launch_stencil_on(fo_problem *p, const Grid &g, const double *coef, const uint8_t *dir, double *W,
                                float *W32, double *dinv, float *dinv32);
 fo_status fo_launch_loads(fo_problem *p);

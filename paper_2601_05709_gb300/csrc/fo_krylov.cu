@@ -503,6 +503,7 @@ static fo_status velocity_impl(fo_problem *p, const fo_solve_opts *o, double *Bt
 }
 
 fo_status fo_velocity_pcg(fo_problem *p, const fo_solve_opts *o, double *Btt, fo_solve_stats *st) {
+  if (o->precond == FO_PC_MG) return fo_velocity_pcg_mg(p, o, Btt, st);
   if (p->mesh->g.dim == 2) return velocity_impl<2>(p, o, Btt, st);
   return velocity_impl<3>(p, o, Btt, st);
 }

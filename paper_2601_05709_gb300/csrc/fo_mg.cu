@@ -54,9 +54,9 @@ struct MgCg {
 };
 
 // ------------------------------------------------------------------ level operations
-template <int D, int NPN>
+template <int D, int NPN, bool FULL>
 struct MgOps {
-  using Op = StencilOp<D, NPN, true, float>;
+  using Op = StencilOp<D, NPN, FULL, float>;
   static __device__ __forceinline__ Op op(const MgLevelDev &L) {
     Op o;
     o.g = L.g;
@@ -145,9 +145,9 @@ struct MgOps {
 
 // The V-cycle on levels l >= from, in block 0 alone (block barriers), starting from b_from and
 // z_from[0] (its first sweep from zero already taken).  zc[l]: buffer holding level l's iterate.
-template <int D, int NPN>
+template <int D, int NPN, bool FULL>
 __device__ void mg_block_cycle(const MgDev &mg, int from, int *zc) {
-  using M = MgOps<D, NPN>;
+  using M = MgOps<D, NPN, FULL>;
   const long long t = threadIdx.x, st = blockDim.x;
   for (int l = from; l < mg.L; ++l) {
     const MgLevelDev &L = mg.lv[l];
@@ -182,13 +182,13 @@ __device__ void mg_block_cycle(const MgDev &mg, int from, int *zc) {
 
 // The V-cycle from level 0, whose b and first sweep were written by the caller before a grid
 // barrier.  Returns false if a grid barrier failed; level 0's result is in z[zc[0]].
-template <int D, int NPN>
+template <int D, int NPN, bool FULL>
 __device__ bool mg_vcycle(const MgDev &mg, int *zc, const GridBar &bar) {
-  using M = MgOps<D, NPN>;
+  using M = MgOps<D, NPN, FULL>;
   const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x, step = (long long)gridDim.x * blockDim.x;
   const int Lg = mg.Lg;
   if (Lg == 0) {   // everything is small: block 0 runs the whole cycle
-    if (blockIdx.x == 0) mg_block_cycle<D, NPN>(mg, 0, zc);
+    if (blockIdx.x == 0) mg_block_cycle<D, NPN, FULL>(mg, 0, zc);
     return grid_sync(bar);
   }
   for (int l = 0; l < Lg; ++l) {
@@ -209,7 +209,7 @@ __device__ bool mg_vcycle(const MgDev &mg, int *zc, const GridBar &bar) {
     if (!grid_sync(bar)) return false;
   }
   if (Lg < mg.L) {   // the other blocks know the block-run levels' final buffers (fixed)
-    if (blockIdx.x == 0) mg_block_cycle<D, NPN>(mg, Lg, zc);
+    if (blockIdx.x == 0) mg_block_cycle<D, NPN, FULL>(mg, Lg, zc);
     if (!grid_sync(bar)) return false;
   }
   for (int l = std::min(Lg, mg.L - 1) - 1; l >= 0; --l) {
@@ -240,137 +240,173 @@ __host__ __device__ inline void mg_final_buffers(int L, int Lg, int nu, int nuc,
   (void)Lg;
 }
 
-template <int D, int NPN>
+// NC independent systems share the loop: NC = 1 for a coupled system (scalar, or elastic
+// blocks), NC = NPN for the component-decoupled velocity form (one CG recurrence per
+// component, DOF k belonging to system k % NC); the loop stops when the summed residual meets
+// rtol.  Ends with the dot product b . x (for B(theta, theta) of the velocity solve).
+template <int D, int NPN, bool FULL, int NC>
 __global__ void __launch_bounds__(FO_BLOCK) k_pcg_mg(const MgDev *mgp, MgCg C) {
   __shared__ MgDev mg;
-  __shared__ double sred[32 * 3];
-  __shared__ double stot[3];
+  __shared__ double sred[32 * 3 * NC];
+  __shared__ double stot[3 * NC];
   {
     const int *src = reinterpret_cast<const int *>(mgp);
     int *dst = reinterpret_cast<int *>(&mg);
     for (int i = threadIdx.x; i < (int)(sizeof(MgDev) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
   }
   __syncthreads();
-  using M = MgOps<D, NPN>;
   const MgLevelDev &L0 = mg.lv[0];
   const Grid &g = L0.g;
   const long long N = g.num_nodes;
   const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x, step = (long long)gridDim.x * blockDim.x;
-  StencilOp<D, NPN, true, double> A;
+  StencilOp<D, NPN, FULL, double> A;
   A.g = g;
   A.W = C.W64;
   int rk = 0, zc[MG_MAX_LEVELS];
   mg_final_buffers(mg.L, mg.Lg, mg.nu, mg.nuc, zc);
   const int zfin = zc[0];
+  auto sys = [](int c) { return NC == 1 ? 0 : c; };
+  double gam[NC], bb[NC], rho[NC], beta[NC];
+  int it = 0, cur = 0;
+  double rr = 0.0, bbt = 0.0;
 
   // r = b - A x;  level-0 right-hand side and first sweep;  ||b||^2
-  double v[3] = {0.0, 0.0, 0.0};
-  for (long long a = first; a < N; a += step) {
-    int idx[3];
-    node_ijk(g, a, idx);
-    double ax[NPN];
-    if (C.warm) A.row(a, idx, VecX<double>{C.x}, ax);
-#pragma unroll
-    for (int c = 0; c < NPN; ++c) {
-      const long long k = a * NPN + c;
-      if (!C.warm) {
-        C.x[k] = 0.0;
-        ax[c] = 0.0;
-      }
-      const double rk0 = C.b[k] - ax[c];
-      C.r[k] = rk0;
-      C.p[0][k] = 0.0;
-      const float bf = (float)rk0;
-      L0.b[k] = bf;
-      L0.z[0][k] = mg.omega * L0.dinv[k] * bf;
-      v[1] += C.b[k] * C.b[k];
-    }
-  }
-  if (!grid_sync(C.bar)) goto fail;
-  if (!mg_vcycle<D, NPN>(mg, zc, C.bar)) goto fail;
   {
-    // z = M r; gamma = (r, z); rho = (r, r)
-    double gam = 0.0, bb = 0.0;
-    v[0] = v[2] = 0.0;
+    double v[3 * NC];
+#pragma unroll
+    for (int j = 0; j < 3 * NC; ++j) v[j] = 0.0;
+    for (long long a = first; a < N; a += step) {
+      int idx[3];
+      node_ijk(g, a, idx);
+      double ax[NPN];
+      if (C.warm) A.row(a, idx, VecX<double>{C.x}, ax);
+#pragma unroll
+      for (int c = 0; c < NPN; ++c) {
+        const long long k = a * NPN + c;
+        if (!C.warm) {
+          C.x[k] = 0.0;
+          ax[c] = 0.0;
+        }
+        const double rk0 = C.b[k] - ax[c];
+        C.r[k] = rk0;
+        C.p[0][k] = 0.0;
+        const float bf = (float)rk0;
+        L0.b[k] = bf;
+        L0.z[0][k] = mg.omega * L0.dinv[k] * bf;
+        v[NC + sys(c)] += C.b[k] * C.b[k];
+      }
+    }
+    if (!grid_sync(C.bar)) return;
+    if (!mg_vcycle<D, NPN, FULL>(mg, zc, C.bar)) return;
+    // z = M r; gamma_c = (r, z)_c; rho_c = (r, r)_c
     for (long long a = first; a < N; a += step)
 #pragma unroll
       for (int c = 0; c < NPN; ++c) {
         const long long k = a * NPN + c;
         const double zk = (double)L0.z[zfin][k];
         C.z[k] = zk;
-        v[0] += C.r[k] * zk;
-        v[2] += C.r[k] * C.r[k];
+        v[sys(c)] += C.r[k] * zk;
+        v[2 * NC + sys(c)] += C.r[k] * C.r[k];
       }
-    if (!reduce_grid<3>(v, sred, stot, C.partials, rk, C.bar)) goto fail;
-    gam = stot[0];
-    bb = stot[1];
-    double rho = stot[2];
-    double beta = 0.0;
-    int it = 0;
-    int cur = 0;
-    while (rho > C.rtol2 * bb && it < C.maxit && gam > 0.0) {
-      // p = z + beta p_old (formed at neighbours on the fly); s = A p; (p, s)
-      double ps[1] = {0.0};
-      const double *po = C.p[cur];
-      double *pn = C.p[cur ^ 1];
-      for (long long a = first; a < N; a += step) {
-        int idx[3];
-        node_ijk(g, a, idx);
-        double ap[NPN];
-        A.row(a, idx, CombX<double, 1>{C.z, po, {beta}}, ap);
+    if (!reduce_grid<3 * NC>(v, sred, stot, C.partials, rk, C.bar)) return;
 #pragma unroll
-        for (int c = 0; c < NPN; ++c) {
-          const long long k = a * NPN + c;
-          const double pk = C.z[k] + beta * po[k];
-          pn[k] = pk;
-          C.s[k] = ap[c];
-          ps[0] += pk * ap[c];
-        }
-      }
-      if (!reduce_grid<1>(ps, sred, stot, C.partials, rk, C.bar)) goto fail;
-      const double alpha = gam / stot[0];
-      if (!(stot[0] > 0.0)) break;   // lost positive definiteness in rounding: stop with x as is
-      cur ^= 1;
-      // x += alpha p; r -= alpha s; level-0 right-hand side and first sweep
-      for (long long a = first; a < N; a += step)
-#pragma unroll
-        for (int c = 0; c < NPN; ++c) {
-          const long long k = a * NPN + c;
-          C.x[k] += alpha * pn[k];
-          const double rk1 = C.r[k] - alpha * C.s[k];
-          C.r[k] = rk1;
-          const float bf = (float)rk1;
-          L0.b[k] = bf;
-          L0.z[0][k] = mg.omega * L0.dinv[k] * bf;
-        }
-      if (!grid_sync(C.bar)) goto fail;
-      if (!mg_vcycle<D, NPN>(mg, zc, C.bar)) goto fail;
-      double w[2] = {0.0, 0.0};
-      for (long long a = first; a < N; a += step)
-#pragma unroll
-        for (int c = 0; c < NPN; ++c) {
-          const long long k = a * NPN + c;
-          const double zk = (double)L0.z[zfin][k];
-          C.z[k] = zk;
-          w[0] += C.r[k] * zk;
-          w[1] += C.r[k] * C.r[k];
-        }
-      if (!reduce_grid<2>(w, sred, stot, C.partials, rk, C.bar)) goto fail;
-      beta = stot[0] / gam;
-      gam = stot[0];
-      rho = stot[1];
-      ++it;
+    for (int q = 0; q < NC; ++q) {
+      gam[q] = stot[q];
+      bb[q] = stot[NC + q];
+      rho[q] = stot[2 * NC + q];
+      beta[q] = 0.0;
+      rr += rho[q];
+      bbt += bb[q];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      C.out[0] = rho;
-      C.out[1] = bb;
-      C.status[DS_ITERS] = it;
-      if (rho > C.rtol2 * bb && it >= C.maxit) atomicCAS(C.status + DS_ERR, DEV_OK, DEV_NOCONV);
-    }
-    return;
   }
-fail:
-  return;
+  for (;;) {
+    bool live = false;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) live = live || gam[q] > 0.0;
+    if (!(rr > C.rtol2 * bbt) || it >= C.maxit || !live) break;
+    // p = z + beta p_old (formed at neighbours on the fly); s = A p; (p, s)_c
+    double ps[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) ps[q] = 0.0;
+    const double *po = C.p[cur];
+    double *pn = C.p[cur ^ 1];
+    CombX<double, NC> pv{C.z, po, {}};
+#pragma unroll
+    for (int q = 0; q < NC; ++q) pv.beta[q] = beta[q];
+    for (long long a = first; a < N; a += step) {
+      int idx[3];
+      node_ijk(g, a, idx);
+      double ap[NPN];
+      A.row(a, idx, pv, ap);
+#pragma unroll
+      for (int c = 0; c < NPN; ++c) {
+        const long long k = a * NPN + c;
+        const double pk = C.z[k] + beta[sys(c)] * po[k];
+        pn[k] = pk;
+        C.s[k] = ap[c];
+        ps[sys(c)] += pk * ap[c];
+      }
+    }
+    if (!reduce_grid<NC>(ps, sred, stot, C.partials, rk, C.bar)) return;
+    double alpha[NC];
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      alpha[q] = gam[q] > 0.0 ? gam[q] / stot[q] : 0.0;
+      ok = ok && (gam[q] <= 0.0 || stot[q] > 0.0);
+    }
+    if (!ok) break;   // lost positive definiteness in rounding: stop with x as is
+    cur ^= 1;
+    // x += alpha p; r -= alpha s; level-0 right-hand side and first sweep
+    for (long long a = first; a < N; a += step)
+#pragma unroll
+      for (int c = 0; c < NPN; ++c) {
+        const long long k = a * NPN + c;
+        C.x[k] += alpha[sys(c)] * pn[k];
+        const double rk1 = C.r[k] - alpha[sys(c)] * C.s[k];
+        C.r[k] = rk1;
+        const float bf = (float)rk1;
+        L0.b[k] = bf;
+        L0.z[0][k] = mg.omega * L0.dinv[k] * bf;
+      }
+    if (!grid_sync(C.bar)) return;
+    if (!mg_vcycle<D, NPN, FULL>(mg, zc, C.bar)) return;
+    double w[2 * NC];
+#pragma unroll
+    for (int j = 0; j < 2 * NC; ++j) w[j] = 0.0;
+    for (long long a = first; a < N; a += step)
+#pragma unroll
+      for (int c = 0; c < NPN; ++c) {
+        const long long k = a * NPN + c;
+        const double zk = (double)L0.z[zfin][k];
+        C.z[k] = zk;
+        w[sys(c)] += C.r[k] * zk;
+        w[NC + sys(c)] += C.r[k] * C.r[k];
+      }
+    if (!reduce_grid<2 * NC>(w, sred, stot, C.partials, rk, C.bar)) return;
+    rr = 0.0;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      beta[q] = gam[q] > 0.0 ? stot[q] / gam[q] : 0.0;
+      gam[q] = stot[q];
+      rho[q] = stot[NC + q];
+      rr += rho[q];
+    }
+    ++it;
+  }
+  // b . x
+  double bx[1] = {0.0};
+  for (long long a = first; a < N; a += step)
+#pragma unroll
+    for (int c = 0; c < NPN; ++c) bx[0] += C.b[a * NPN + c] * C.x[a * NPN + c];
+  if (!reduce_grid<1>(bx, sred, stot, C.partials, rk, C.bar)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    C.out[0] = rr;
+    C.out[1] = bbt;
+    C.out[2] = stot[0];
+    C.status[DS_ITERS] = it;
+    if (rr > C.rtol2 * bbt && it >= C.maxit) atomicCAS(C.status + DS_ERR, DEV_OK, DEV_NOCONV);
+  }
 }
 
 // ===================================================================================== host
@@ -422,42 +458,7 @@ __global__ void k_mg_coarse_dir(Grid gc, Grid gf, int npn, const uint8_t *dir_f,
   }
 }
 
-static size_t mg_level_bytes(const Grid &g, int npn, bool coarse) {
-  const size_t N = (size_t)g.num_nodes, S = g.dim == 2 ? 7 : 15, BLK = (size_t)npn * npn;
-  size_t b = sizeof(float) * 4 * N * npn;                           // b, z[2], t
-  if (coarse)
-    b += sizeof(double) * g.num_elems + sizeof(double) * S * BLK * N + sizeof(float) * S * BLK * N +
-         sizeof(double) * N * npn + sizeof(float) * N * npn + N * npn;   // coef, W64, W32, dinv, dinv32, dir
-  return b;
-}
-
-static void mg_free(fo_problem *p) {
-  fo_mg *mg = p->mg;
-  if (!mg) return;
-  fo_ctx *ctx = p->ctx;
-  for (int l = 0; l < mg->L; ++l) {
-    const size_t N = (size_t)mg->g[l].num_nodes * mg->npn, S = mg->g[l].dim == 2 ? 7 : 15,
-                 BLK = (size_t)mg->npn * mg->npn, Nn = (size_t)mg->g[l].num_nodes;
-    fo_free(ctx, mg->b[l], sizeof(float) * N);
-    fo_free(ctx, mg->z0[l], sizeof(float) * N);
-    fo_free(ctx, mg->z1[l], sizeof(float) * N);
-    fo_free(ctx, mg->t[l], sizeof(float) * N);
-    if (l > 0) {
-      fo_free(ctx, mg->coef[l], sizeof(double) * mg->g[l].num_elems);
-      fo_free(ctx, mg->W64[l], sizeof(double) * S * BLK * Nn);
-      fo_free(ctx, mg->W32[l], sizeof(float) * S * BLK * Nn);
-      fo_free(ctx, mg->dinv64[l], sizeof(double) * N);
-      fo_free(ctx, mg->dinv32[l], sizeof(float) * N);
-      fo_free(ctx, mg->dir[l], N);
-    }
-  }
-  fo_free(ctx, mg->dev, sizeof(MgDev));
-  delete mg;
-  p->mg = nullptr;
-}
-
-void fo_mg_destroy(fo_problem *p) { mg_free(p); }
-
+// ------------------------------------------------------------------------- hierarchies
 // Levels: halve every axis while all are even and the coarse grid keeps >= 2 cells per axis.
 static int mg_plan(const Grid &g0, Grid *g, int max_levels) {
   g[0] = g0;
@@ -477,76 +478,105 @@ static int mg_plan(const Grid &g0, Grid *g, int max_levels) {
   return L;
 }
 
-size_t fo_mg_bytes(int dim, const int n[3], int npn) {
+// Byte sizes of level l's arrays, in the order b, z0, z1, t, coef, W64, W32, dinv64, dinv32, dir
+// (coarse levels own all; level 0 owns coef, W32, dinv32 and dir only when own0).
+static void mg_sizes(const Grid &g, int npn, int blk, bool coarse, bool own0, size_t sz[10]) {
+  const size_t N = (size_t)g.num_nodes, S = g.dim == 2 ? 7 : 15;
+  for (int i = 0; i < 4; ++i) sz[i] = sizeof(float) * N * npn;
+  sz[4] = (coarse || own0) ? sizeof(double) * g.num_elems : 0;
+  sz[5] = coarse ? sizeof(double) * S * blk * N : 0;
+  sz[6] = (coarse || own0) ? sizeof(float) * S * blk * N : 0;
+  sz[7] = coarse ? sizeof(double) * N * npn : 0;
+  sz[8] = (coarse || own0) ? sizeof(float) * N * npn : 0;
+  sz[9] = (coarse || own0) ? N * npn : 0;
+}
+
+static void **mg_slot(fo_mg *mg, int l, int i) {
+  switch (i) {
+    case 0: return (void **)&mg->b[l];
+    case 1: return (void **)&mg->z0[l];
+    case 2: return (void **)&mg->z1[l];
+    case 3: return (void **)&mg->t[l];
+    case 4: return (void **)&mg->coef[l];
+    case 5: return (void **)&mg->W64[l];
+    case 6: return (void **)&mg->W32[l];
+    case 7: return (void **)&mg->dinv64[l];
+    case 8: return (void **)&mg->dinv32[l];
+    default: return (void **)&mg->dir[l];
+  }
+}
+
+static void mg_release(fo_ctx *ctx, fo_mg *&mg) {
+  if (!mg) return;
+  for (int l = 0; l < mg->L; ++l) {
+    size_t sz[10];
+    mg_sizes(mg->g[l], mg->npn, mg->blk, l > 0, mg->own0, sz);
+    for (int i = 0; i < 10; ++i)
+      if (sz[i]) fo_free(ctx, *mg_slot(mg, l, i), sz[i]);
+  }
+  fo_free(ctx, mg->dev, sizeof(MgDev));
+  delete mg;
+  mg = nullptr;
+}
+
+void fo_mg_destroy(fo_problem *p) {
+  mg_release(p->ctx, p->mg);
+  mg_release(p->ctx, p->mgv);
+}
+
+size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0) {
   Grid g0;
-  if (!fo_grid_make(dim, n, (const double[3]){0, 0, 0}, (const double[3]){1, 1, 1}, g0)) return 0;
+  const double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+  if (!fo_grid_make(dim, n, lo, hi, g0)) return 0;
   Grid g[MG_MAX_LEVELS];
   const int L = mg_plan(g0, g, MG_MAX_LEVELS);
   size_t b = sizeof(MgDev);
-  for (int l = 0; l < L; ++l) b += mg_level_bytes(g[l], npn, l > 0);
+  for (int l = 0; l < L; ++l) {
+    size_t sz[10];
+    mg_sizes(g[l], npn, blk, l > 0, own0, sz);
+    for (int i = 0; i < 10; ++i) b += sz[i];
+  }
   return b;
 }
 
-// Build (first call) and refresh (each coefficient update) the hierarchy.
-static fo_status mg_prepare(fo_problem *p) {
-  fo_ctx *ctx = p->ctx;
-  const Grid &g0 = p->mesh->g;
-  const int npn = p->ncomp;
-  if (!p->mg) {
-    fo_mg *mg = new fo_mg();
-    p->mg = mg;
-    mg->npn = npn;
-    mg->L = mg_plan(g0, mg->g, MG_MAX_LEVELS);
-    for (int l = 0; l < mg->L; ++l) {
-      const size_t N = (size_t)mg->g[l].num_nodes * npn, S = g0.dim == 2 ? 7 : 15, BLK = (size_t)npn * npn,
-                   Nn = (size_t)mg->g[l].num_nodes;
-      FO_TRY(fo_alloc(ctx, (void **)&mg->b[l], sizeof(float) * N));
-      FO_TRY(fo_alloc(ctx, (void **)&mg->z0[l], sizeof(float) * N));
-      FO_TRY(fo_alloc(ctx, (void **)&mg->z1[l], sizeof(float) * N));
-      FO_TRY(fo_alloc(ctx, (void **)&mg->t[l], sizeof(float) * N));
-      if (l > 0) {
-        FO_TRY(fo_alloc(ctx, (void **)&mg->coef[l], sizeof(double) * mg->g[l].num_elems));
-        FO_TRY(fo_alloc(ctx, (void **)&mg->W64[l], sizeof(double) * S * BLK * Nn));
-        FO_TRY(fo_alloc(ctx, (void **)&mg->W32[l], sizeof(float) * S * BLK * Nn));
-        FO_TRY(fo_alloc(ctx, (void **)&mg->dinv64[l], sizeof(double) * N));
-        FO_TRY(fo_alloc(ctx, (void **)&mg->dinv32[l], sizeof(float) * N));
-        FO_TRY(fo_alloc(ctx, (void **)&mg->dir[l], N));
-      }
-    }
-    FO_TRY(fo_alloc(ctx, (void **)&mg->dev, sizeof(MgDev)));
-    mg->built_epoch = -1;
+static fo_status mg_alloc(fo_ctx *ctx, fo_mg *&out, const Grid &g0, int npn, int blk, bool own0) {
+  fo_mg *mg = new fo_mg();
+  out = mg;
+  mg->npn = npn;
+  mg->blk = blk;
+  mg->own0 = own0;
+  mg->L = mg_plan(g0, mg->g, MG_MAX_LEVELS);
+  for (int l = 0; l < mg->L; ++l) {
+    size_t sz[10];
+    mg_sizes(mg->g[l], npn, blk, l > 0, own0, sz);
+    for (int i = 0; i < 10; ++i)
+      if (sz[i]) FO_TRY(fo_alloc(ctx, mg_slot(mg, l, i), sz[i]));
   }
-  fo_mg *mg = p->mg;
-  if (mg->built_epoch == p->coef_epoch) return FO_OK;
-  cudaStream_t s = ctx->stream;
-  for (int l = 1; l < mg->L; ++l) {
-    const Grid &gc = mg->g[l], &gf = mg->g[l - 1];
-    const uint8_t *df = l == 1 ? p->dir : mg->dir[l - 1];
-    const int blocks = fo_blocks_for(gc.num_elems, FO_BLOCK, 65536);
-    if (gc.dim == 2) k_mg_restrict_coef<2><<<blocks, FO_BLOCK, 0, s>>>(gc, gf, l == 1 ? p->coef : mg->coef[l - 1], mg->coef[l]);
-    else k_mg_restrict_coef<3><<<blocks, FO_BLOCK, 0, s>>>(gc, gf, l == 1 ? p->coef : mg->coef[l - 1], mg->coef[l]);
-    k_mg_coarse_dir<<<fo_blocks_for(gc.num_nodes, FO_BLOCK, 65536), FO_BLOCK, 0, s>>>(gc, gf, npn, df, mg->dir[l]);
-    fo_note_launch(2);
-    FO_TRY(fo_launch_stencil_on(p, gc, mg->coef[l], mg->dir[l], mg->W64[l], mg->W32[l], mg->dinv64[l], mg->dinv32[l]));
-  }
+  FO_TRY(fo_alloc(ctx, (void **)&mg->dev, sizeof(MgDev)));
+  return FO_OK;
+}
+
+// Level table to the device; level 0's FP32 rows, FP32 inverse diagonal and Dirichlet mask.
+static fo_status mg_upload(fo_ctx *ctx, fo_mg *mg, const float *W0, const float *dinv0, const uint8_t *dir0,
+                           float omega) {
   MgDev h;
   memset(&h, 0, sizeof h);
   h.L = mg->L;
   h.Lg = mg->L;
   for (int l = 0; l < mg->L; ++l)
-    if ((long long)mg->g[l].num_nodes * npn <= MG_BLOCK_DOFS) {
+    if ((long long)mg->g[l].num_nodes * mg->npn <= MG_BLOCK_DOFS) {
       h.Lg = l;
       break;
     }
-  h.omega = npn == 1 ? 0.8f : 0.6f;
+  h.omega = omega;
   h.nu = 2;
   h.nuc = 16;
   for (int l = 0; l < mg->L; ++l) {
     MgLevelDev &d = h.lv[l];
     d.g = mg->g[l];
-    d.W = l == 0 ? p->Wst32 : mg->W32[l];
-    d.dinv = l == 0 ? p->dinv_state32 : mg->dinv32[l];
-    d.dir = l == 0 ? p->dir : mg->dir[l];
+    d.W = l == 0 ? W0 : mg->W32[l];
+    d.dinv = l == 0 ? dinv0 : mg->dinv32[l];
+    d.dir = l == 0 ? dir0 : mg->dir[l];
     d.b = mg->b[l];
     d.z[0] = mg->z0[l];
     d.z[1] = mg->z1[l];
@@ -554,20 +584,94 @@ static fo_status mg_prepare(fo_problem *p) {
   }
   mg->host.resize(sizeof(MgDev));
   memcpy(mg->host.data(), &h, sizeof(MgDev));
-  FO_CU(ctx, cudaMemcpyAsync(mg->dev, mg->host.data(), sizeof(MgDev), cudaMemcpyHostToDevice, s));
+  FO_CU(ctx, cudaMemcpyAsync(mg->dev, mg->host.data(), sizeof(MgDev), cudaMemcpyHostToDevice, ctx->stream));
   FO_CU(ctx, cudaGetLastError());
+  return FO_OK;
+}
+
+// restrict a per-element coefficient and the per-DOF Dirichlet mask from level l-1 to level l
+static void mg_restrict_level(fo_ctx *ctx, fo_mg *mg, int l, const double *coef_f, const uint8_t *dir_f) {
+  const Grid &gc = mg->g[l], &gf = mg->g[l - 1];
+  cudaStream_t s = ctx->stream;
+  const int blocks = fo_blocks_for(gc.num_elems, FO_BLOCK, 65536);
+  if (gc.dim == 2) k_mg_restrict_coef<2><<<blocks, FO_BLOCK, 0, s>>>(gc, gf, coef_f, mg->coef[l]);
+  else k_mg_restrict_coef<3><<<blocks, FO_BLOCK, 0, s>>>(gc, gf, coef_f, mg->coef[l]);
+  k_mg_coarse_dir<<<fo_blocks_for(gc.num_nodes, FO_BLOCK, 65536), FO_BLOCK, 0, s>>>(gc, gf, mg->npn, dir_f, mg->dir[l]);
+  fo_note_launch(2);
+}
+
+// State hierarchy: rebuilt after every coefficient update (coarse coefficients are the
+// children means of the current A_e).
+static fo_status mg_prepare_state(fo_problem *p) {
+  fo_ctx *ctx = p->ctx;
+  if (!p->mg) {
+    FO_TRY(mg_alloc(ctx, p->mg, p->mesh->g, p->ncomp, p->ncomp * p->ncomp, false));
+    p->mg->built_epoch = -1;
+  }
+  fo_mg *mg = p->mg;
+  if (mg->built_epoch == p->coef_epoch) return FO_OK;
+  for (int l = 1; l < mg->L; ++l) {
+    mg_restrict_level(ctx, mg, l, l == 1 ? p->coef : mg->coef[l - 1], l == 1 ? p->dir : mg->dir[l - 1]);
+    FO_TRY(fo_launch_stencil_on(p, mg->g[l], mg->coef[l], mg->dir[l], mg->W64[l], mg->W32[l], mg->dinv64[l],
+                                mg->dinv32[l]));
+  }
+  FO_TRY(mg_upload(ctx, mg, p->Wst32, p->dinv_state32, p->dir, p->ncomp == 1 ? 0.8f : 0.6f));
   mg->built_epoch = p->coef_epoch;
   return FO_OK;
 }
 
-template <int D, int NPN>
-static fo_status mg_solve_t(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st) {
+__global__ void k_vel_mass_coef(long long ne, const uint8_t *omega0, double alpha, double gamma0, double *mc) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x)
+    mc[e] = alpha + (omega0[e] ? gamma0 : 0.0);
+}
+__global__ void k_vel_dof_mask(long long nn, int d, const uint8_t *vdir, int on, uint8_t *mask) {
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < nn; a += (long long)gridDim.x * blockDim.x)
+    for (int c = 0; c < d; ++c) mask[a * d + c] = on && vdir[a];
+}
+// -b on the velocity DOFs, zero on H^1_0 rows
+__global__ void k_vel_rhs(long long nn, int d, const double *b, const uint8_t *mask, double *out) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nn * d; k += (long long)gridDim.x * blockDim.x)
+    out[k] = mask[k] ? 0.0 : -b[k];
+}
+
+// Velocity hierarchy: the form does not depend on phi, so it is built once.  Level 0's rows
+// are the problem's velocity rows; coarse levels carry the children mean of the mass-type
+// coefficient alpha + gamma_0 chi_Omega0 and the same normal penalty on their faces.
+static fo_status mg_prepare_velocity(fo_problem *p) {
+  if (p->mgv) return FO_OK;
   fo_ctx *ctx = p->ctx;
-  const long long n = p->ndof;
+  const Grid &g0 = p->mesh->g;
+  const int d = g0.dim;
+  FO_TRY(mg_alloc(ctx, p->mgv, g0, d, d, true));
+  fo_mg *mg = p->mgv;
+  cudaStream_t s = ctx->stream;
+  const double al = p->desc.alpha_mass, ga0 = p->desc.omega0_weight, gb = p->desc.normal_penalty;
+  k_vel_mass_coef<<<fo_blocks_for(g0.num_elems, FO_BLOCK, 65536), FO_BLOCK, 0, s>>>(g0.num_elems, p->omega0, al, ga0,
+                                                                                   mg->coef[0]);
+  k_vel_dof_mask<<<fo_blocks_for(g0.num_nodes, FO_BLOCK, 65536), FO_BLOCK, 0, s>>>(
+      g0.num_nodes, d, p->vdir, p->desc.velocity_dirichlet ? 1 : 0, mg->dir[0]);
+  fo_note_launch(2);
+  // level 0 again with FP32 copies (same rows as the problem's FP64 ones)
+  FO_TRY(fo_launch_velocity_stencil_on(p, g0, mg->coef[0], mg->dir[0], p->Wvel, mg->W32[0], p->dinv_vel,
+                                       mg->dinv32[0]));
+  for (int l = 1; l < mg->L; ++l) {
+    mg_restrict_level(ctx, mg, l, mg->coef[l - 1], mg->dir[l - 1]);
+    FO_TRY(fo_launch_velocity_stencil_on(p, mg->g[l], mg->coef[l], mg->dir[l], mg->W64[l], mg->W32[l], mg->dinv64[l],
+                                         mg->dinv32[l]));
+  }
+  FO_TRY(mg_upload(ctx, mg, mg->W32[0], mg->dinv32[0], mg->dir[0], 0.8f));
+  return FO_OK;
+}
+
+// ------------------------------------------------------------------------------ solves
+template <int D, int NPN, bool FULL, int NC>
+static fo_status mg_run(fo_problem *p, fo_mg *mg, const double *W64, const double *b, double *x, long long n,
+                        const fo_solve_opts *o, fo_solve_stats *st, double *bx) {
+  fo_ctx *ctx = p->ctx;
   double *buf;
   FO_TRY(fo_scratch(p, sizeof(double) * 6 * n, (void **)&buf));
   MgCg C{};
-  C.W64 = p->Wst;
+  C.W64 = W64;
   C.b = b;
   C.x = x;
   C.r = buf;
@@ -582,17 +686,17 @@ static fo_status mg_solve_t(fo_problem *p, const double *b, double *x, const fo_
   C.rtol2 = o->rtol * o->rtol;
   C.maxit = o->maxit;
   C.warm = o->warm_start;
-  auto kern = k_pcg_mg<D, NPN>;
+  auto kern = k_pcg_mg<D, NPN, FULL, NC>;
   int grid;
   FO_TRY(fo_cooperative_grid(p, (const void *)kern, FO_BLOCK, 0, p->mesh->g.num_nodes, o->grid_blocks, &grid));
-  const MgDev *mgp = (const MgDev *)p->mg->dev;
+  const MgDev *mgp = (const MgDev *)mg->dev;
   void *argv[] = {(void *)&mgp, (void *)&C};
   FO_CU(ctx, cudaMemsetAsync(p->bar, 0, 64, ctx->stream));
   FO_CU(ctx, cudaMemsetAsync(p->dev_status, 0, sizeof(int) * DS_COUNT, ctx->stream));
   FO_CU(ctx, cudaLaunchCooperativeKernel((const void *)kern, grid, FO_BLOCK, argv, 0, ctx->stream));
   fo_note_launch(1);
   FO_CU(ctx, cudaGetLastError());
-  FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars, C.out, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars, C.out, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars + 32, p->dev_status, sizeof(int) * DS_COUNT, cudaMemcpyDeviceToHost,
                              ctx->stream));
   FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
@@ -604,15 +708,39 @@ static fo_status mg_solve_t(fo_problem *p, const double *b, double *x, const fo_
     st->outer_iterations = 1;
     st->rel_residual = ctx->h_scalars[1] > 0 ? std::sqrt(ctx->h_scalars[0] / ctx->h_scalars[1]) : 0.0;
   }
+  if (bx) *bx = ctx->h_scalars[2];
   if (hs[DS_ERR] == DEV_TIMEOUT) return fo_fail(ctx, FO_ETIMEOUT, "grid barrier timed out in the multigrid PCG");
-  if (hs[DS_ERR] == DEV_NOCONV) return fo_fail(ctx, FO_ENOCONV, "multigrid PCG reached maxit=%d", o->maxit);
   if (!std::isfinite(ctx->h_scalars[0])) return fo_fail(ctx, FO_ENAN, "NaN in the multigrid PCG");
+  if (hs[DS_ERR] == DEV_NOCONV) return fo_fail(ctx, FO_ENOCONV, "multigrid PCG reached maxit=%d", o->maxit);
   return FO_OK;
 }
 
 fo_status fo_state_pcg_mg(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st) {
-  FO_TRY(mg_prepare(p));
+  FO_TRY(mg_prepare_state(p));
   const int d = p->mesh->g.dim;
-  if (p->desc.kind == FO_ELASTIC) return d == 2 ? mg_solve_t<2, 2>(p, b, x, o, st) : mg_solve_t<3, 3>(p, b, x, o, st);
-  return d == 2 ? mg_solve_t<2, 1>(p, b, x, o, st) : mg_solve_t<3, 1>(p, b, x, o, st);
+  const long long n = p->ndof;
+  if (p->desc.kind == FO_ELASTIC)
+    return d == 2 ? mg_run<2, 2, true, 1>(p, p->mg, p->Wst, b, x, n, o, st, nullptr)
+                  : mg_run<3, 3, true, 1>(p, p->mg, p->Wst, b, x, n, o, st, nullptr);
+  return d == 2 ? mg_run<2, 1, true, 1>(p, p->mg, p->Wst, b, x, n, o, st, nullptr)
+                : mg_run<3, 1, true, 1>(p, p->mg, p->Wst, b, x, n, o, st, nullptr);
+}
+
+// Velocity solve B theta = -b with multigrid: the d component systems share one launch.
+fo_status fo_velocity_pcg_mg(fo_problem *p, const fo_solve_opts *o, double *Btt, fo_solve_stats *st) {
+  FO_TRY(mg_prepare_velocity(p));
+  const Grid &g = p->mesh->g;
+  const int d = g.dim;
+  const long long n = (long long)d * g.num_nodes;
+  double *rhs;
+  FO_TRY(fo_scratch(p, sizeof(double) * 7 * n, (void **)&rhs));
+  rhs += 6 * n;   // after the solver's six vectors
+  k_vel_rhs<<<fo_blocks_for(n, FO_BLOCK, 65536), FO_BLOCK, 0, p->ctx->stream>>>(g.num_nodes, d, p->rhs, p->mgv->dir[0],
+                                                                               rhs);
+  fo_note_launch(1);
+  double bx = 0.0;
+  fo_status r = d == 2 ? mg_run<2, 2, false, 2>(p, p->mgv, p->Wvel, rhs, p->theta, n, o, st, &bx)
+                       : mg_run<3, 3, false, 3>(p, p->mgv, p->Wvel, rhs, p->theta, n, o, st, &bx);
+  if (Btt) *Btt = bx;   // B(theta, theta) = -b . theta
+  return r;
 }

@@ -246,14 +246,15 @@ def test_shape_rhs(ctx, api, c, lam):
 
 
 @pytest.mark.parametrize("c", [case(**HEAT2D), cantilever2d((128, 64)), cantilever3d((10, 5, 5))])
-def test_descent(ctx, api, c):
+@pytest.mark.parametrize("pc", [0, 1], ids=["jacobi", "multigrid"])
+def test_descent(ctx, api, c, pc):
     mesh, prob = gpu_problem(ctx, c)
     op = oracle_problem(c)
     prob.set_levelset(np.zeros(op.mesh.num_nodes) - 1.0)
     prob.coefficients()
     b = workloads.smooth_field(op.mesh.coords, c["dim"], 23)
     prob.set(api._lib.FO_FIELD_RHS, b)
-    Btt, st = prob.descent(tight(api))
+    Btt, st = prob.descent(tight(api, precond=pc))
     theta = prob.get(api._lib.FO_FIELD_THETA)
     theta_ref, Btt_ref = ovel.solve(op.mesh, op.vform, b)
     assert rel(theta, theta_ref) <= 1e-10, (rel(theta, theta_ref), st.iterations)
