@@ -196,7 +196,7 @@ fo_status fo_launch_stencil_apply(fo_problem *p, const double *S, const double *
 // Gram-Schmidt with one reorthogonalisation pass (CGS2), each pass one fused grid
 // reduction; the Hessenberg matrix, Givens rotations and the small triangular solve live in
 // shared memory and are computed identically by every block from the same reduction totals.
-#define GM_M 24
+#define GM_M 16
 #define GM_NR (GM_M + 2)
 
 struct KrylovBufs {
@@ -222,9 +222,89 @@ __device__ __forceinline__ bool ls_reduce(double (&v)[NR], double *sred, double 
 struct GmresShared {
   double sred[32 * GM_NR];
   double stot[GM_NR];
+  double col[GM_M + 1];          // the new Hessenberg column (before the rotations)
   double H[(GM_M + 1) * GM_M];   // column-major: H[j * (GM_M + 1) + i]
   double cs[GM_M], sn[GM_M], g[GM_M + 1], y[GM_M];
 };
+
+// One Arnoldi step at compile-time index J: w = M D^{-1} v_J, two Gram-Schmidt passes against
+// v_0..v_J (each one fused grid reduction of J + 1 dot products, the second with |w|^2), and
+// v_{J+1} = w / |w|.  Every loop runs over exactly the J + 1 basis vectors, so no lane issues
+// work for vectors that do not exist yet.  Leaves the column (h_0..h_J, |w|) in sh.col.
+template <int D, int J>
+__device__ bool arnoldi_step(const Grid &g, const double *M, const double *dinv, const KrylovBufs &K,
+                             GmresShared &sh, double *partials, int &rk, const GridBar &bar) {
+  const long long N = g.num_nodes;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long gs = (long long)gridDim.x * blockDim.x;
+  const double *Vj = K.V + (size_t)J * N;
+  double h1[J + 1];
+#pragma unroll
+  for (int i = 0; i <= J; ++i) h1[i] = 0.0;
+  for (long long a = tid; a < N; a += gs) {
+    int idx[3];
+    node_ijk(g, a, idx);
+    double wa = 0.0;
+#pragma unroll
+    for (int s = 0; s < ST<D>::S; ++s) {
+      const long long nb = slot_node<D>(g, idx, a, s);
+      if (nb >= 0) wa += M[s * N + a] * (dinv[nb] * Vj[nb]);
+    }
+    K.w[a] = wa;
+#pragma unroll
+    for (int i = 0; i <= J; ++i) h1[i] += K.V[(size_t)i * N + a] * wa;
+  }
+  if (!ls_reduce<J + 1>(h1, sh.sred, sh.stot, partials, rk, bar)) return false;
+  double hc[J + 1];
+#pragma unroll
+  for (int i = 0; i <= J; ++i) hc[i] = sh.stot[i];
+  double h2[J + 2];
+#pragma unroll
+  for (int i = 0; i < J + 2; ++i) h2[i] = 0.0;
+  for (long long a = tid; a < N; a += gs) {
+    double wa = K.w[a];
+#pragma unroll
+    for (int i = 0; i <= J; ++i) wa -= hc[i] * K.V[(size_t)i * N + a];
+    K.w[a] = wa;
+#pragma unroll
+    for (int i = 0; i <= J; ++i) h2[i] += K.V[(size_t)i * N + a] * wa;
+    h2[J + 1] += wa * wa;
+  }
+  if (!ls_reduce<J + 2>(h2, sh.sred, sh.stot, partials, rk, bar)) return false;
+  double hn2 = sh.stot[J + 1];
+  double h2c[J + 1];
+#pragma unroll
+  for (int i = 0; i <= J; ++i) {
+    h2c[i] = sh.stot[i];
+    hc[i] += h2c[i];
+    hn2 -= h2c[i] * h2c[i];
+  }
+  const double hnext = sqrt(fmax(hn2, 0.0));
+  double *Vn = K.V + (size_t)(J + 1) * N;
+  const double inv = hnext > 0.0 ? 1.0 / hnext : 0.0;
+  for (long long a = tid; a < N; a += gs) {
+    double wa = K.w[a];
+#pragma unroll
+    for (int i = 0; i <= J; ++i) wa -= h2c[i] * K.V[(size_t)i * N + a];
+    Vn[a] = wa * inv;
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i <= J; ++i) sh.col[i] = hc[i];
+    sh.col[J + 1] = hnext;
+  }
+  return true;
+}
+
+template <int D, int J>
+__device__ __forceinline__ bool arnoldi_dispatch(int j, const Grid &g, const double *M, const double *dinv,
+                                                 const KrylovBufs &K, GmresShared &sh, double *partials, int &rk,
+                                                 const GridBar &bar) {
+  if constexpr (J + 1 < GM_M) {
+    if (j != J) return arnoldi_dispatch<D, J + 1>(j, g, M, dinv, K, sh, partials, rk, bar);
+  }
+  return arnoldi_step<D, J>(g, M, dinv, K, sh, partials, rk, bar);
+}
 
 // Solve M x = rhs (x holds the start value).  When Rm is given, the first residual pass
 // also forms rhs = Rm x (the transport's right-hand side R phi^n, gathered from the same
@@ -289,69 +369,13 @@ __device__ int gmres_solve(const Grid &g, const double *M, const double *dinv, c
     int j = 0;
     bool done = false;
     for (; j < GM_M; ++j) {
-      const double *Vj = K.V + (size_t)j * N;
-      // ---- w = M D^{-1} v_j and h_i = v_i . w (first Gram-Schmidt pass)
-      double h1[GM_NR];
-#pragma unroll
-      for (int i = 0; i < GM_NR; ++i) h1[i] = 0.0;
-      for (long long a = tid; a < N; a += gs) {
-        int idx[3];
-        node_ijk(g, a, idx);
-        double wa = 0.0;
-#pragma unroll
-        for (int s = 0; s < ST<D>::S; ++s) {
-          const long long nb = slot_node<D>(g, idx, a, s);
-          if (nb >= 0) wa += M[s * N + a] * (dinv[nb] * Vj[nb]);
-        }
-        K.w[a] = wa;
-#pragma unroll
-        for (int i = 0; i < GM_M; ++i)
-          if (i <= j) h1[i] += K.V[(size_t)i * N + a] * wa;
-      }
-      if (!ls_reduce<GM_NR>(h1, sh.sred, sh.stot, partials, rk, bar)) { *ok = false; return total; }
-      double hc[GM_M];
-#pragma unroll
-      for (int i = 0; i < GM_M; ++i) hc[i] = (i <= j) ? sh.stot[i] : 0.0;
-      // ---- w -= V h; second pass h2 = V^T w and |w|^2
-      double h2[GM_NR];
-#pragma unroll
-      for (int i = 0; i < GM_NR; ++i) h2[i] = 0.0;
-      for (long long a = tid; a < N; a += gs) {
-        double wa = K.w[a];
-#pragma unroll
-        for (int i = 0; i < GM_M; ++i)
-          if (i <= j) wa -= hc[i] * K.V[(size_t)i * N + a];
-        K.w[a] = wa;
-#pragma unroll
-        for (int i = 0; i < GM_M; ++i)
-          if (i <= j) h2[i] += K.V[(size_t)i * N + a] * wa;
-        h2[GM_M] += wa * wa;
-      }
-      if (!ls_reduce<GM_NR>(h2, sh.sred, sh.stot, partials, rk, bar)) { *ok = false; return total; }
-      double hn2 = sh.stot[GM_M];
-      double h2c[GM_M];
-#pragma unroll
-      for (int i = 0; i < GM_M; ++i) {
-        h2c[i] = (i <= j) ? sh.stot[i] : 0.0;
-        hc[i] += h2c[i];
-        hn2 -= h2c[i] * h2c[i];
-      }
-      const double hnext = sqrt(fmax(hn2, 0.0));
-      // ---- v_{j+1} = (w - V h2) / hnext
-      double *Vn = K.V + (size_t)(j + 1) * N;
-      const double inv = hnext > 0.0 ? 1.0 / hnext : 0.0;
-      for (long long a = tid; a < N; a += gs) {
-        double wa = K.w[a];
-#pragma unroll
-        for (int i = 0; i < GM_M; ++i)
-          if (i <= j) wa -= h2c[i] * K.V[(size_t)i * N + a];
-        Vn[a] = wa * inv;
-      }
+      if (!arnoldi_dispatch<D, 0>(j, g, M, dinv, K, sh, partials, rk, bar)) { *ok = false; return total; }
+      __syncthreads();
+      const double hnext = sh.col[j + 1];
       // ---- Hessenberg column, Givens rotations, residual estimate (same in every block)
       if (threadIdx.x == 0) {
         double col[GM_M + 1];
-        for (int i = 0; i <= j; ++i) col[i] = hc[i];
-        col[j + 1] = hnext;
+        for (int i = 0; i <= j + 1; ++i) col[i] = sh.col[i];
         for (int i = 0; i < j; ++i) {
           const double t = sh.cs[i] * col[i] + sh.sn[i] * col[i + 1];
           col[i + 1] = -sh.sn[i] * col[i] + sh.cs[i] * col[i + 1];
