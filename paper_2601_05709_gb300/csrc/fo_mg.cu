@@ -24,7 +24,7 @@
 #include "fo_internal.cuh"
 #include "fo_ops.cuh"
 
-#define MG_BLOCK_DOFS 1024
+#define MG_BLOCK_DOFS 2048
 
 struct MgLevelDev {
   Grid g;
@@ -645,7 +645,7 @@ static fo_status mg_prepare_velocity(fo_problem *p) {
   FO_TRY(mg_alloc(ctx, p->mgv, g0, d, d, true));
   fo_mg *mg = p->mgv;
   cudaStream_t s = ctx->stream;
-  const double al = p->desc.alpha_mass, ga0 = p->desc.omega0_weight, gb = p->desc.normal_penalty;
+  const double al = p->desc.alpha_mass, ga0 = p->desc.omega0_weight;
   k_vel_mass_coef<<<fo_blocks_for(g0.num_elems, FO_BLOCK, 65536), FO_BLOCK, 0, s>>>(g0.num_elems, p->omega0, al, ga0,
                                                                                    mg->coef[0]);
   k_vel_dof_mask<<<fo_blocks_for(g0.num_nodes, FO_BLOCK, 65536), FO_BLOCK, 0, s>>>(
