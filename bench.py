@@ -337,7 +337,7 @@ def bench_serving(api, ctx, count):
         return api.model_desc(api.FO_ELASTIC, dirichlet=[(0, 0)], tractions=[(0, 1, vec)], alpha_mass=0.1,
                               normal_penalty=1e4)
 
-    def run(executors, prec, pace):
+    def run(executors, prec, pace, pc=api.FO_PC_MG):
         srv = api.Server(ctx, executors=executors, mem_budget=8 << 30)
         tickets = []
         t0 = time.perf_counter()
@@ -347,7 +347,8 @@ def bench_serving(api, ctx, count):
                 if d > 0:
                     time.sleep(d)
             r = api.ServedRequest(dim, (n,) * dim, desc(dim, n, heat), centers=centers, width=0.1, offset=0.2,
-                                  state=api.solve_opts(precision=prec, rtol=1e-8), velocity=api.solve_opts(rtol=1e-8))
+                                  state=api.solve_opts(precision=prec, rtol=1e-8, precond=pc),
+                                  velocity=api.solve_opts(rtol=1e-8, precond=pc))
             st, t = srv.submit(r)
             if st != 0:
                 raise RuntimeError(f"submit failed with status {st}")
@@ -359,17 +360,20 @@ def bench_serving(api, ctx, count):
         lat = np.array([r.end_ms - r.submit_ms for r in res])
         dofit = sum(r.dofs * (r.state.operator_applies + r.adjoint.operator_applies) for r in res)
         return {"executors": executors, "precision": "mixed" if prec == api.FO_MIXED else "fp64",
+                "preconditioner": "multigrid" if pc == api.FO_PC_MG else "jacobi",
                 "seconds": wall, "requests_per_s": len(res) / wall,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "state_gdof_iters_per_s": dofit / wall / 1e9, "peak_in_flight": int(stats.peak_in_flight),
                 "peak_admitted_gb": stats.peak_bytes / 1e9, "failed": int(stats.failed)}
 
-    served = run(8, api.FO_MIXED, True)
-    serial = run(1, api.FO_FP64, True)
+    served = run(8, api.FO_FP64, True)                          # multigrid-preconditioned FP64 CG
+    serial = run(1, api.FO_FP64, True, api.FO_PC_JACOBI)        # plain FP64 (Jacobi) one at a time
+    serial_mg = run(1, api.FO_FP64, True)
     return {"sample": f"first {count} requests of the seeded stream (of 2,000)",
             "sizes": [f"{d}D n={n} {'heat' if h else 'elastic'}" for (_, d, n, h, _) in items],
-            "served_mixed": served, "serial_fp64": serial,
-            "throughput_ratio": served["requests_per_s"] / serial["requests_per_s"]}
+            "served": served, "serial_plain_fp64": serial, "serial_multigrid": serial_mg,
+            "throughput_ratio_vs_plain": served["requests_per_s"] / serial["requests_per_s"],
+            "throughput_ratio_vs_serial_multigrid": served["requests_per_s"] / serial_mg["requests_per_s"]}
 
 
 # ----------------------------------------------------------------------------- our arm

@@ -151,8 +151,10 @@ typedef struct {
   double inner_rtol;        /* FO_MIXED: relative reduction asked of each FP32 solve    */
   int inner_maxit;          /* FO_MIXED: cap per FP32 solve                             */
   int grid_blocks;          /* 0 = autotuned; else blocks of the persistent kernel      */
-  int precond;              /* state solves: FO_PC_JACOBI, or FO_PC_MG (FP64 CG with an */
-                            /* FP32 geometric-multigrid V-cycle as preconditioner)      */
+  int precond;              /* FO_PC_JACOBI, or FO_PC_MG: FP64 CG with an FP32 geometric- */
+                            /* multigrid V-cycle as preconditioner (state and velocity  */
+                            /* solves of single problems, on grids that halve down to a */
+                            /* coarsest level of <= 8192 unknowns; else Jacobi)         */
 } fo_solve_opts;
 
 #define FO_PC_JACOBI 0

@@ -393,6 +393,7 @@ fo_status fo_batch_apply(fo_problem *p, const double *x, double *y, bool fp32);
 fo_status fo_state_pcg_mg(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st);
 void fo_mg_destroy(fo_problem *p);
 size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0);
+bool fo_mg_applicable(const Grid &g0, int npn);
 fo_status fo_velocity_pcg_mg(fo_problem *p, const fo_solve_opts *o, double *Btt, fo_solve_stats *st);
 fo_status fo_launch_velocity_stencil_on(fo_problem *p, const Grid &g, const double *mcoef, const uint8_t *dofmask,
                                         double *W, float *W32, double *dinv, float *dinv32);

@@ -455,7 +455,7 @@ static fo_status state_solve_impl(fo_problem *p, const Op64 &op64, const OpMixed
 
 fo_status fo_state_pcg(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st) {
   const Grid &g = p->mesh->g;
-  if (o->precond == FO_PC_MG && !p->batch) return fo_state_pcg_mg(p, b, x, o, st);
+  if (o->precond == FO_PC_MG && !p->batch && fo_mg_applicable(g, p->ncomp)) return fo_state_pcg_mg(p, b, x, o, st);
   // stored-stencil operators: FP64 rows for the FP64 solve and the refinement residual, FP32
   // rows for the inner solve of the mixed path
   if (p->desc.kind == FO_ELASTIC) {
@@ -503,7 +503,7 @@ static fo_status velocity_impl(fo_problem *p, const fo_solve_opts *o, double *Bt
 }
 
 fo_status fo_velocity_pcg(fo_problem *p, const fo_solve_opts *o, double *Btt, fo_solve_stats *st) {
-  if (o->precond == FO_PC_MG) return fo_velocity_pcg_mg(p, o, Btt, st);
+  if (o->precond == FO_PC_MG && fo_mg_applicable(p->mesh->g, p->mesh->g.dim)) return fo_velocity_pcg_mg(p, o, Btt, st);
   if (p->mesh->g.dim == 2) return velocity_impl<2>(p, o, Btt, st);
   return velocity_impl<3>(p, o, Btt, st);
 }

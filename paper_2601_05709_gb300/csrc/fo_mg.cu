@@ -524,6 +524,15 @@ void fo_mg_destroy(fo_problem *p) {
   mg_release(p->ctx, p->mgv);
 }
 
+// Multigrid pays when the hierarchy reaches a small coarsest level; grids whose cell counts
+// are not divisible by enough powers of two (odd sizes) keep the Jacobi-preconditioned CG.
+#define MG_COARSEST_MAX_DOFS 8192
+bool fo_mg_applicable(const Grid &g0, int npn) {
+  Grid g[MG_MAX_LEVELS];
+  const int L = mg_plan(g0, g, MG_MAX_LEVELS);
+  return L >= 2 && g[L - 1].num_nodes * npn <= MG_COARSEST_MAX_DOFS;
+}
+
 size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0) {
   Grid g0;
   const double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};

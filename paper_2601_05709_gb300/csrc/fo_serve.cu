@@ -65,10 +65,19 @@ extern "C" void fo_server_opts_default(fo_server_opts *o) {
 }
 
 extern "C" size_t fo_request_device_bytes(const fo_request *rq) {
-  if (!rq) return 0;
-  return fo_problem_footprint(rq->dim, rq->n, rq->model.kind,
-                              std::max(rq->state.precision, rq->velocity.precision) == FO_MIXED ? FO_MIXED : FO_FP64,
-                              rq->n_bumps);
+  if (!rq || (rq->dim != 2 && rq->dim != 3)) return 0;
+  size_t b = fo_problem_footprint(rq->dim, rq->n, rq->model.kind,
+                                  std::max(rq->state.precision, rq->velocity.precision) == FO_MIXED ? FO_MIXED : FO_FP64,
+                                  rq->n_bumps);
+  // multigrid hierarchies, when asked for and when the grid coarsens far enough to use them
+  Grid g0;
+  const double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+  if (!fo_grid_make(rq->dim, rq->n, lo, hi, g0)) return b;
+  const int nc = rq->model.kind == FO_ELASTIC ? rq->dim : 1;
+  if (rq->state.precond == FO_PC_MG && fo_mg_applicable(g0, nc)) b += fo_mg_bytes(rq->dim, rq->n, nc, nc * nc, false);
+  if (rq->velocity.precond == FO_PC_MG && fo_mg_applicable(g0, rq->dim))
+    b += fo_mg_bytes(rq->dim, rq->n, rq->dim, rq->dim, true);
+  return b;
 }
 
 static bool request_valid(const fo_request *rq) {

@@ -87,12 +87,19 @@ def test_served_equals_direct_api(ctx):
     assert np.array_equal(prob.get(api.FO_FIELD_THETA), rq.theta)
 
 
-@pytest.mark.parametrize("kind,dim,n,prec", [(FO_HEAT, 2, 20, api.FO_FP64), (FO_ELASTIC, 2, 16, api.FO_MIXED),
-                                             (FO_ELASTIC, 3, 5, api.FO_FP64)])
-def test_request_footprint_exact(kind, dim, n, prec):
+@pytest.mark.parametrize("kind,dim,n,prec,pc", [(FO_HEAT, 2, 20, api.FO_FP64, 0), (FO_ELASTIC, 2, 16, api.FO_MIXED, 0),
+                                                (FO_ELASTIC, 3, 5, api.FO_FP64, 0),
+                                                (FO_ELASTIC, 2, 64, api.FO_FP64, api.FO_PC_MG),
+                                                (FO_HEAT, 3, 16, api.FO_FP64, api.FO_PC_MG),
+                                                (FO_HEAT, 2, 63, api.FO_FP64, api.FO_PC_MG)])
+def test_request_footprint_exact(kind, dim, n, prec, pc):
+    """The estimate equals what the request allocates, multigrid hierarchies included (the
+    odd 63x63 grid cannot coarsen, so it falls back to Jacobi and holds no hierarchy)."""
     c2 = api.Context(0)
     phi = workloads.phi_cos(np.random.default_rng(0).random((int((n + 1) ** dim), dim)))
-    rq = api.ServedRequest(dim, (n,) * dim, _desc(kind, dim), phi=phi, state=api.solve_opts(precision=prec, rtol=1e-9))
+    rq = api.ServedRequest(dim, (n,) * dim, _desc(kind, dim), phi=phi,
+                           state=api.solve_opts(precision=prec, rtol=1e-9, precond=pc),
+                           velocity=api.solve_opts(precond=pc))
     mesh = c2.mesh_box(dim, (n,) * dim, (0.0,) * dim, (1.0,) * dim)
     prob = mesh.problem(_desc(kind, dim))
     prob.set_levelset(phi)
@@ -100,7 +107,7 @@ def test_request_footprint_exact(kind, dim, n, prec):
     prob.state_solve(rq.struct.state, allow_noconv=True)
     prob.adjoint_solve(rq.struct.state)
     prob.shape_derivative(0.0, copy=False)
-    prob.descent(api.solve_opts())
+    prob.descent(rq.struct.velocity)
     assert c2.memory() == rq.device_bytes()
     c2.close()
 

@@ -88,3 +88,13 @@ def test_destroy_cancels_queued():
     srv.close()
     dt = time.time() - t0
     assert dt < 0.6, dt                      # one running request (<= 300 ms), not four
+
+
+def test_footprint_counts_multigrid_only_where_it_applies():
+    def req(n, pc):
+        r = _req(n, api.FO_ELASTIC)
+        r.struct.state.precond = pc
+        r.struct.velocity.precond = pc
+        return r.device_bytes()
+    assert req(64, api.FO_PC_MG) > req(64, api.FO_PC_JACOBI)    # 64 halves down to a small coarsest grid
+    assert req(63, api.FO_PC_MG) == req(63, api.FO_PC_JACOBI)   # odd: no hierarchy, Jacobi fallback
