@@ -269,6 +269,20 @@ def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True):
             "inst_iterations": {"min": int(its.min()), "mean": float(its.mean()), "max": int(its.max())},
             "max_rel_residual": float(res.max()),
             "gdof_iters_per_s": nfree * float(its.sum()) / dt / 1e9}
+    # batched FP64 CG with a per-instance FP32 multigrid V-cycle (first call builds the hierarchy)
+    om_mg = api.solve_opts(rtol=1e-8, maxit=1000, precond=api.FO_PC_MG)
+    for rep in range(2):
+        prob.set(api.FO_FIELD_U, np.zeros((mesh.num_nodes, BATCH_INST)))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = prob.state_solve(om_mg)
+        dt = time.perf_counter() - t0
+    its, res = prob.batch_solve_info()
+    out["batched_multigrid"] = {
+        "seconds": dt, "iterations": st.iterations,
+        "inst_iterations": {"min": int(its.min()), "mean": float(its.mean()), "max": int(its.max())},
+        "max_rel_residual": float(res.max()), "ms_per_iteration": dt * 1e3 / max(st.iterations, 1),
+        "gdof_iters_per_s": nfree * float(its.sum()) / dt / 1e9}
     # summed tensors and the velocity solve (the rest of a batched step without transport)
     t0 = time.perf_counter()
     J, C = prob.functionals()
@@ -293,6 +307,25 @@ def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True):
         out["plain_fp64_one_at_a_time"] = {"seconds": tot_t, "iterations": tot_it,
                                            "gdof_iters_per_s": nfree * tot_it / tot_t / 1e9}
         out["speedup_time_to_solution_mixed_vs_plain"] = tot_t / out["batched_mixed"]["seconds"]
+    # the single-problem multigrid solve, one instance at a time
+    tot_t, tot_it = 0.0, 0
+    for i in range(BATCH_INST if plain else 0):
+        p1 = mesh.problem(api.model_desc(api.FO_HELMHOLTZ, a_in=1.0, a_out=1e-3, k=k[i], omega=om[i],
+                                         dirichlet=[(0, 0)], f_nodal=f[i]))
+        p1.set_levelset(phi)
+        p1.coefficients()
+        for rep in range(2 if i == 0 else 1):      # the first call of the first builds kernels' state
+            p1.set(api.FO_FIELD_U, np.zeros(mesh.num_nodes))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s1 = p1.state_solve(api.solve_opts(rtol=1e-8, maxit=1000, precond=api.FO_PC_MG))
+            dt1 = time.perf_counter() - t0
+        tot_t += dt1
+        tot_it += s1.iterations
+        p1.close()
+    if plain:
+        out["plain_multigrid_one_at_a_time"] = {"seconds": tot_t, "iterations": tot_it}
+        out["speedup_time_to_solution_batched_vs_plain_multigrid"] = tot_t / out["batched_multigrid"]["seconds"]
     # roofline of the batched FP32 sweep: per DOF and iteration it moves r, w, s, D^{-1}, p, x
     # in and r, w, s, p, x out (11 x 4 bytes), measured with every instance active (autotune)
     us = tune["mixed"]["us_per_iteration_all_active"]

@@ -294,9 +294,10 @@ static size_t prob_bytes_fields(const fo_problem *p, std::vector<std::pair<void 
 }
 
 // Device bytes allocated for a box mesh and a single (non-batch) problem on it, with the
-// largest solver scratch of its state / adjoint (precision) and velocity solves and the
-// transient bump-centre array; what a served request holds at most.
-size_t fo_problem_footprint(int dim, const int n[3], int kind, int precision, int n_bumps) {
+// largest solver scratch of its state / adjoint and velocity solves (state_vecs, vel_vecs
+// FP64 vectors of their systems) and the transient bump-centre array; what a served request
+// holds at most, multigrid hierarchies aside.
+size_t fo_problem_footprint(int dim, const int n[3], int kind, int state_vecs, int vel_vecs, int n_bumps) {
   long long NN = 1, cells = 1;
   for (int a = 0; a < dim; ++a) {
     NN *= (long long)n[a] + 1;
@@ -306,8 +307,8 @@ size_t fo_problem_footprint(int dim, const int n[3], int kind, int precision, in
   const long long ND = NN * (kind == FO_ELASTIC ? dim : 1);
   size_t total = sizeof(int32_t) * NT * (dim + 1) + sizeof(double) * NN * dim;   // mesh
   for (size_t b : problem_field_sizes(dim, NN, NT, ND, kind != FO_ELASTIC)) total += b;
-  const size_t state = sizeof(double) * (precision == FO_MIXED ? 11 : 8) * (size_t)ND;
-  const size_t vel = sizeof(double) * 8 * (size_t)dim * NN;
+  const size_t state = sizeof(double) * state_vecs * (size_t)ND;
+  const size_t vel = sizeof(double) * vel_vecs * (size_t)dim * NN;
   const size_t bumps = sizeof(double) * (size_t)std::max(n_bumps, 0) * dim;
   return total + std::max(std::max(state, vel), bumps);
 }

@@ -87,8 +87,10 @@ __global__ void k_batch_stencil(Grid g, const double *coef, const uint8_t *dir, 
     for (int s = 0; s < S; ++s) {
       WK[a * S + s] = wk[s];
       WM[a * S + s] = wm[s];
-      WK32[a * S + s] = (float)wk[s];
-      WM32[a * S + s] = (float)wm[s];
+      if (WK32) {
+        WK32[a * S + s] = (float)wk[s];
+        WM32[a * S + s] = (float)wm[s];
+      }
     }
   }
 }
@@ -836,6 +838,7 @@ static size_t batch_bytes(const fo_problem *p, std::vector<std::pair<void **, si
 
 void fo_batch_destroy(fo_problem *p) {
   if (!p->batch) return;
+  fo_bmg_destroy(p);
   std::vector<std::pair<void **, size_t>> list;
   batch_bytes(p, list);
   for (auto &e : list) {
@@ -902,17 +905,25 @@ fo_status fo_batch_create(fo_problem *p, const fo_model_desc *desc) {
   return FO_OK;
 }
 
+// WK, WM (FP64, node-major) of grid g from a per-element coefficient and Dirichlet mask; FP32
+// copies when WK32 / WM32 are given.
+void fo_launch_batch_stencil(cudaStream_t s, const Grid &g, const double *coef, const uint8_t *dir, double *WK,
+                             double *WM, float *WK32, float *WM32) {
+  const int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
+  if (g.dim == 2) k_batch_stencil<2><<<blocks, FO_BLOCK, 0, s>>>(g, coef, dir, WK, WM, WK32, WM32);
+  else k_batch_stencil<3><<<blocks, FO_BLOCK, 0, s>>>(g, coef, dir, WK, WM, WK32, WM32);
+  fo_note_launch(1);
+}
+
 fo_status fo_batch_prepare(fo_problem *p) {
   fo_batch *bt = p->batch;
   const Grid &g = p->mesh->g;
   cudaStream_t s = p->ctx->stream;
-  const int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
-  if (g.dim == 2) k_batch_stencil<2><<<blocks, FO_BLOCK, 0, s>>>(g, p->coef, p->dir, bt->WK, bt->WM, bt->WK32, bt->WM32);
-  else k_batch_stencil<3><<<blocks, FO_BLOCK, 0, s>>>(g, p->coef, p->dir, bt->WK, bt->WM, bt->WK32, bt->WM32);
+  fo_launch_batch_stencil(s, g, p->coef, p->dir, bt->WK, bt->WM, bt->WK32, bt->WM32);
   const int b2 = fo_blocks_for(g.num_nodes * bt->nip, FO_BLOCK, 65536);
   k_batch_dinv<<<b2, FO_BLOCK, 0, s>>>(g.num_nodes, batch_S(g), bt->nip, bt->WK, bt->WM, bt->kk, bt->w2, bt->dinv,
                                         bt->dinv32);
-  fo_note_launch(2);
+  fo_note_launch(1);
   FO_CU(p->ctx, cudaGetLastError());
   return FO_OK;
 }
@@ -1080,7 +1091,7 @@ static fo_status batch_shape(fo_problem *p, int precision, int requested, BatchL
   return FO_OK;
 }
 
-static fo_status batch_read(fo_problem *p, fo_solve_stats *st, const fo_solve_opts *o) {
+fo_status fo_batch_read(fo_problem *p, fo_solve_stats *st, const fo_solve_opts *o) {
   fo_ctx *ctx = p->ctx;
   FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars + 32, p->dev_status, sizeof(int) * DS_COUNT, cudaMemcpyDeviceToHost,
                              ctx->stream));
@@ -1143,7 +1154,7 @@ extern "C" fo_status fo_batch_autotune(fo_problem *p, int precision, fo_tune_res
           st = batch_dispatch(p, precision, bt->B, 1.0, X, &o, L, 0);
           cudaEventRecord(e1, ctx->stream);
           if (st == FO_OK) {
-            fo_status r = batch_read(p, nullptr, &o);
+            fo_status r = fo_batch_read(p, nullptr, &o);
             if (r != FO_OK && r != FO_ENOCONV) st = r;
           }
         }
@@ -1183,15 +1194,17 @@ extern "C" fo_status fo_batch_autotune(fo_problem *p, int precision, fo_tune_res
 
 fo_status fo_batch_state(fo_problem *p, bool adjoint, const fo_solve_opts *o, fo_solve_stats *st) {
   fo_batch *bt = p->batch;
+  double *X = adjoint ? bt->P : bt->U;
+  if (o->precond == FO_PC_MG && fo_mg_applicable(p->mesh->g, 1))
+    return fo_batch_state_mg(p, bt->B, adjoint ? -1.0 : 1.0, X, o, adjoint ? 0 : o->warm_start, st);
   const int prec = o->precision == FO_MIXED ? FO_MIXED : FO_FP64;
   if (o->grid_blocks <= 0 && bt->tuned_block[prec == FO_MIXED ? 1 : 0] == 0) FO_TRY(fo_batch_autotune(p, prec, nullptr));
   BatchLaunch L;
   FO_TRY(batch_shape(p, prec, o->grid_blocks, &L));
-  double *X = adjoint ? bt->P : bt->U;
   FO_TRY(batch_dispatch(p, prec, bt->B, adjoint ? -1.0 : 1.0, X, o, L, adjoint ? 0 : o->warm_start));
   fo_solve_stats s;
   memset(&s, 0, sizeof s);
-  fo_status r = batch_read(p, &s, o);
+  fo_status r = fo_batch_read(p, &s, o);
   if (st) *st = s;
   return r;
 }

@@ -77,6 +77,7 @@ struct fo_batch {
   double *inst_res = nullptr;               // [nip] last solve: final relative residual
   int tuned_ts[2] = {0, 0}, tuned_block[2] = {0, 0}, tuned_bpsm[2] = {0, 0};   // per precision (FO_FP64, FO_MIXED)
   double tuned_us[2] = {0, 0};
+  struct fo_bmg *mg = nullptr;              // multigrid hierarchy of the batched operator
 };
 
 // Geometric multigrid hierarchy of a problem's state operator (fo_mg.cu): level 0 is the
@@ -394,6 +395,16 @@ fo_status fo_state_pcg_mg(fo_problem *p, const double *b, double *x, const fo_so
 void fo_mg_destroy(fo_problem *p);
 size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0);
 bool fo_mg_applicable(const Grid &g0, int npn);
+int fo_mg_plan(const Grid &g0, Grid *g, int max_levels);
+void fo_mg_restrict(fo_ctx *ctx, const Grid &gc, const Grid &gf, int npn, const double *coef_f, const uint8_t *dir_f,
+                    double *coef_c, uint8_t *dir_c);
+// batched multigrid (fo_batch_mg.cu) and the batch stencil builder it shares (fo_batch.cu)
+void fo_launch_batch_stencil(cudaStream_t s, const Grid &g, const double *coef, const uint8_t *dir, double *WK,
+                             double *WM, float *WK32, float *WM32);
+fo_status fo_batch_state_mg(fo_problem *p, const double *B, double bscale, double *X, const fo_solve_opts *o, int warm,
+                            fo_solve_stats *st);
+void fo_bmg_destroy(fo_problem *p);
+fo_status fo_batch_read(fo_problem *p, fo_solve_stats *st, const fo_solve_opts *o);   // stats of the last batched solve
 fo_status fo_velocity_pcg_mg(fo_problem *p, const fo_solve_opts *o, double *Btt, fo_solve_stats *st);
 fo_status fo_launch_velocity_stencil_on(fo_problem *p, const Grid &g, const double *mcoef, const uint8_t *dofmask,
                                         double *W, float *W32, double *dinv, float *dinv32);
@@ -410,7 +421,7 @@ fo_status fo_launch_functionals(fo_problem *p, double *J, double *vol);
 fo_status fo_launch_shape_rhs(fo_problem *p, double lambda);
 fo_status fo_launch_mesh_build(fo_mesh *m);
 bool fo_grid_make(int dim, const int n[3], const double lo[3], const double hi[3], Grid &g);
-size_t fo_problem_footprint(int dim, const int n[3], int kind, int precision, int n_bumps);
+size_t fo_problem_footprint(int dim, const int n[3], int kind, int state_vecs, int vel_vecs, int n_bumps);
 fo_status fo_launch_phi_bumps(fo_problem *p, int count, const double *centers, double width, double offset);
 fo_status fo_launch_initial_level(fo_problem *p, int count, const double *centers, const double *radii,
                                   double factor, int ord);

@@ -460,7 +460,7 @@ __global__ void k_mg_coarse_dir(Grid gc, Grid gf, int npn, const uint8_t *dir_f,
 
 // ------------------------------------------------------------------------- hierarchies
 // Levels: halve every axis while all are even and the coarse grid keeps >= 2 cells per axis.
-static int mg_plan(const Grid &g0, Grid *g, int max_levels) {
+int fo_mg_plan(const Grid &g0, Grid *g, int max_levels) {
   g[0] = g0;
   int L = 1;
   while (L < max_levels) {
@@ -529,7 +529,7 @@ void fo_mg_destroy(fo_problem *p) {
 #define MG_COARSEST_MAX_DOFS 8192
 bool fo_mg_applicable(const Grid &g0, int npn) {
   Grid g[MG_MAX_LEVELS];
-  const int L = mg_plan(g0, g, MG_MAX_LEVELS);
+  const int L = fo_mg_plan(g0, g, MG_MAX_LEVELS);
   return L >= 2 && g[L - 1].num_nodes * npn <= MG_COARSEST_MAX_DOFS;
 }
 
@@ -538,7 +538,7 @@ size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0) {
   const double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
   if (!fo_grid_make(dim, n, lo, hi, g0)) return 0;
   Grid g[MG_MAX_LEVELS];
-  const int L = mg_plan(g0, g, MG_MAX_LEVELS);
+  const int L = fo_mg_plan(g0, g, MG_MAX_LEVELS);
   size_t b = sizeof(MgDev);
   for (int l = 0; l < L; ++l) {
     size_t sz[10];
@@ -554,7 +554,7 @@ static fo_status mg_alloc(fo_ctx *ctx, fo_mg *&out, const Grid &g0, int npn, int
   mg->npn = npn;
   mg->blk = blk;
   mg->own0 = own0;
-  mg->L = mg_plan(g0, mg->g, MG_MAX_LEVELS);
+  mg->L = fo_mg_plan(g0, mg->g, MG_MAX_LEVELS);
   for (int l = 0; l < mg->L; ++l) {
     size_t sz[10];
     mg_sizes(mg->g[l], npn, blk, l > 0, own0, sz);
@@ -598,15 +598,21 @@ static fo_status mg_upload(fo_ctx *ctx, fo_mg *mg, const float *W0, const float 
   return FO_OK;
 }
 
-// restrict a per-element coefficient and the per-DOF Dirichlet mask from level l-1 to level l
-static void mg_restrict_level(fo_ctx *ctx, fo_mg *mg, int l, const double *coef_f, const uint8_t *dir_f) {
-  const Grid &gc = mg->g[l], &gf = mg->g[l - 1];
+// Coarse per-element coefficient (children means) and per-DOF Dirichlet mask of grid gc from
+// those of the grid gf it halves.
+void fo_mg_restrict(fo_ctx *ctx, const Grid &gc, const Grid &gf, int npn, const double *coef_f, const uint8_t *dir_f,
+                    double *coef_c, uint8_t *dir_c) {
   cudaStream_t s = ctx->stream;
   const int blocks = fo_blocks_for(gc.num_elems, FO_BLOCK, 65536);
-  if (gc.dim == 2) k_mg_restrict_coef<2><<<blocks, FO_BLOCK, 0, s>>>(gc, gf, coef_f, mg->coef[l]);
-  else k_mg_restrict_coef<3><<<blocks, FO_BLOCK, 0, s>>>(gc, gf, coef_f, mg->coef[l]);
-  k_mg_coarse_dir<<<fo_blocks_for(gc.num_nodes, FO_BLOCK, 65536), FO_BLOCK, 0, s>>>(gc, gf, mg->npn, dir_f, mg->dir[l]);
+  if (gc.dim == 2) k_mg_restrict_coef<2><<<blocks, FO_BLOCK, 0, s>>>(gc, gf, coef_f, coef_c);
+  else k_mg_restrict_coef<3><<<blocks, FO_BLOCK, 0, s>>>(gc, gf, coef_f, coef_c);
+  k_mg_coarse_dir<<<fo_blocks_for(gc.num_nodes, FO_BLOCK, 65536), FO_BLOCK, 0, s>>>(gc, gf, npn, dir_f, dir_c);
   fo_note_launch(2);
+}
+
+// restrict a per-element coefficient and the per-DOF Dirichlet mask from level l-1 to level l
+static void mg_restrict_level(fo_ctx *ctx, fo_mg *mg, int l, const double *coef_f, const uint8_t *dir_f) {
+  fo_mg_restrict(ctx, mg->g[l], mg->g[l - 1], mg->npn, coef_f, dir_f, mg->coef[l], mg->dir[l]);
 }
 
 // State hierarchy: rebuilt after every coefficient update (coarse coefficients are the

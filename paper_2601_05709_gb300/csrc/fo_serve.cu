@@ -66,17 +66,18 @@ extern "C" void fo_server_opts_default(fo_server_opts *o) {
 
 extern "C" size_t fo_request_device_bytes(const fo_request *rq) {
   if (!rq || (rq->dim != 2 && rq->dim != 3)) return 0;
-  size_t b = fo_problem_footprint(rq->dim, rq->n, rq->model.kind,
-                                  std::max(rq->state.precision, rq->velocity.precision) == FO_MIXED ? FO_MIXED : FO_FP64,
-                                  rq->n_bumps);
-  // multigrid hierarchies, when asked for and when the grid coarsens far enough to use them
   Grid g0;
   const double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
-  if (!fo_grid_make(rq->dim, rq->n, lo, hi, g0)) return b;
+  if (!fo_grid_make(rq->dim, rq->n, lo, hi, g0)) return 0;
+  // multigrid where asked for and where the grid coarsens far enough to use it; solver
+  // scratch: multigrid CG 6 (state) / 7 (velocity) vectors, Jacobi CG 8, mixed refinement 11
   const int nc = rq->model.kind == FO_ELASTIC ? rq->dim : 1;
-  if (rq->state.precond == FO_PC_MG && fo_mg_applicable(g0, nc)) b += fo_mg_bytes(rq->dim, rq->n, nc, nc * nc, false);
-  if (rq->velocity.precond == FO_PC_MG && fo_mg_applicable(g0, rq->dim))
-    b += fo_mg_bytes(rq->dim, rq->n, rq->dim, rq->dim, true);
+  const bool smg = rq->state.precond == FO_PC_MG && fo_mg_applicable(g0, nc);
+  const bool vmg = rq->velocity.precond == FO_PC_MG && fo_mg_applicable(g0, rq->dim);
+  const int svecs = smg ? 6 : (rq->state.precision == FO_MIXED ? 11 : 8);
+  size_t b = fo_problem_footprint(rq->dim, rq->n, rq->model.kind, svecs, vmg ? 7 : 8, rq->n_bumps);
+  if (smg) b += fo_mg_bytes(rq->dim, rq->n, nc, nc * nc, false);
+  if (vmg) b += fo_mg_bytes(rq->dim, rq->n, rq->dim, rq->dim, true);
   return b;
 }
 

@@ -20,6 +20,14 @@ CASES = {
 }
 
 
+# grids that halve at least twice, for the batched multigrid
+MG_CASES = {
+    "2d_mg_40": dict(dim=2, n=(32, 24), n_inst=40, seed=4),    # 32x24 -> 16x12 -> 8x6 -> 4x3
+    "3d_mg_5": dict(dim=3, n=(8, 8, 4), n_inst=5, seed=5),      # 8x8x4 -> 4x4x2
+    "2d_mg_70": dict(dim=2, n=(16, 16), n_inst=70, seed=6),     # four 32-lane slabs
+}
+
+
 @pytest.fixture(scope="module")
 def ctx():
     c = api.Context(0)
@@ -28,7 +36,7 @@ def ctx():
 
 
 def _setup(ctx, name):
-    c = batch_case(**CASES[name])
+    c = batch_case(**(CASES[name] if name in CASES else MG_CASES[name]))
     ob = oracle_batch(c)
     mesh, prob = gpu_batch(ctx, c)
     phi = workloads.phi_cos(ob.mesh.coords[:, :2]) if c["dim"] == 2 else workloads.phi_bumps(
@@ -126,6 +134,50 @@ def test_batch_instance_equals_alone(ctx, precision):
         pi.state_solve(opts)
         ui = pi.get(FO_FIELD_U)[:, 0]
         assert np.array_equal(ui, U[:, i]), (i, np.max(np.abs(ui - U[:, i])))
+
+
+@pytest.mark.parametrize("name", list(MG_CASES) + ["2d_5"])
+def test_batch_state_multigrid_parity(ctx, name):
+    """Batched FP64 CG with a per-instance FP32 V-cycle: every instance meets the oracle's
+    solution, in few iterations; the explicit adjoint is -u."""
+    c, ob, prob, phi = _setup(ctx, name)
+    U_ref, A, chi = ob.state(phi)
+    opts = api.solve_opts(rtol=1e-12, precond=api.FO_PC_MG)
+    st = prob.state_solve(opts)
+    U = prob.get(FO_FIELD_U)
+    its, res = prob.batch_solve_info()
+    assert np.all(res <= 1e-12), res
+    assert 0 < st.iterations <= 100 and np.all(its <= st.iterations), its
+    F = ob.loads()
+    free = ob.problem(0).dirichlet() == 0
+    for i in range(c["n_inst"]):
+        assert_solve_parity(_K(ob, i, A), F[:, i], free, U[:, i], U_ref[:, i], 1e-10, omega_max=1e-10)
+    assert np.all(U[~free] == 0.0)
+    prob.adjoint_solve(opts)
+    assert rel(prob.get(FO_FIELD_P), -U) <= 1e-10
+    # the Jacobi-preconditioned batch reaches the same solution
+    prob.state_solve(api.solve_opts(rtol=1e-12))
+    assert rel(prob.get(FO_FIELD_U), U) <= 1e-10
+
+
+def test_batch_multigrid_instance_equals_alone(ctx):
+    """An instance's multigrid-preconditioned solve in the batch and alone give the same bits."""
+    c = batch_case(**MG_CASES["2d_mg_40"])
+    mesh, prob = gpu_batch(ctx, c)
+    _, coords = mesh.copy_out()
+    phi = workloads.phi_cos(coords)
+    prob.set_levelset(phi)
+    opts = api.solve_opts(rtol=1e-12, grid_blocks=64, precond=api.FO_PC_MG)
+    prob.state_solve(opts)
+    U = prob.get(FO_FIELD_U)
+    its, _ = prob.batch_solve_info()
+    for i in (0, 21, 39):
+        ci = dict(c, n_inst=1, k=c["k"][i:i + 1], omega=c["omega"][i:i + 1], amp=c["amp"][i:i + 1])
+        _, pi = gpu_batch(ctx, ci)
+        pi.set_levelset(phi)
+        pi.state_solve(opts)
+        assert np.array_equal(pi.get(FO_FIELD_U)[:, 0], U[:, i]), i
+        assert pi.batch_solve_info()[0][0] == its[i]
 
 
 def test_batch_opt_step_matches_oracle(ctx):
