@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--batch-n", type=int, default=512, help="cells per axis of the batch mesh")
     ap.add_argument("--batch-maxit", type=int, default=400000, help="cap on batched iterations (profiling runs)")
     ap.add_argument("--batch-only", action="store_true", help="run the batch leg only (profiling)")
+    ap.add_argument("--batch-mg-only", action="store_true", help="with --batch-only: the multigrid solve only")
     return ap.parse_args()
 
 
@@ -230,7 +231,7 @@ def run_reference(args, rank, world):
 BATCH_N, BATCH_INST = 512, 64
 
 
-def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True):
+def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True, mg_only=False):
     """Batched vs one-at-a-time state solves of the 64-instance Helmholtz family, to a relative
     FP64 residual of 1e-8; then the summed shape derivative and one velocity solve."""
     import numpy as np
@@ -251,12 +252,12 @@ def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True):
                        f"({2 * n * n} triangles, {mesh.num_nodes} nodes), ersatz 1e-3, Dirichlet x=0",
            "rtol": 1e-8}
     tune = {}
-    for prec, name in ((api.FO_MIXED, "mixed"), (api.FO_FP64, "fp64")):
+    for prec, name in () if mg_only else ((api.FO_MIXED, "mixed"), (api.FO_FP64, "fp64")):
         r = prob.batch_autotune(prec)
         tune[name] = {"tile": list(r.tile), "block": r.block, "blocks_per_sm": r.blocks_per_sm,
                       "us_per_iteration_all_active": r.us_per_iteration, "candidates": r.candidates}
     out["autotune"] = tune
-    for prec, name in ((api.FO_MIXED, "mixed"), (api.FO_FP64, "fp64")):
+    for prec, name in () if mg_only else ((api.FO_MIXED, "mixed"), (api.FO_FP64, "fp64")):
         prob.set(api.FO_FIELD_U, np.zeros((mesh.num_nodes, BATCH_INST)))
         o = api.solve_opts(precision=prec, rtol=1e-8, inner_rtol=1e-3, maxit=maxit, inner_maxit=100000)
         torch.cuda.synchronize()
@@ -326,6 +327,9 @@ def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True):
     if plain:
         out["plain_multigrid_one_at_a_time"] = {"seconds": tot_t, "iterations": tot_it}
         out["speedup_time_to_solution_batched_vs_plain_multigrid"] = tot_t / out["batched_multigrid"]["seconds"]
+    if mg_only:
+        prob.close()
+        return out
     # roofline of the batched FP32 sweep: per DOF and iteration it moves r, w, s, D^{-1}, p, x
     # in and r, w, s, p, x out (11 x 4 bytes), measured with every instance active (autotune)
     us = tune["mixed"]["us_per_iteration_all_active"]
@@ -338,6 +342,30 @@ def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True):
     prob.close()
     mesh.close() if hasattr(mesh, "close") else None
     return out
+
+
+def mg_state_bytes_per_iteration(nx, ny, c):
+    """Algorithmic bytes of one iteration of the multigrid-preconditioned state CG on an nx x ny
+    Kuhn grid with c components per node (7 stencil slots of c x c blocks).  Outer FP64 CG: the
+    FP64 rows once (7 c^2 8 B per node) and its vectors (132 B per DOF: p, s, x, r, z reads and
+    writes, the level-0 right-hand side and first sweep).  FP32 V-cycle, per level: four
+    stencil passes (one pre-sweep after the fused first one, the residual, two post-sweeps),
+    each reading the FP32 rows (7 c^2 4 B per node) and 16 B per DOF of vectors, plus the
+    transfers (restriction 12 B, prolongation 18 B per node and component); the coarsest
+    level's 15 sweeps."""
+    levels = [(nx, ny)]
+    while all(n % 2 == 0 and n // 2 >= 2 for n in levels[-1]):
+        levels.append((levels[-1][0] // 2, levels[-1][1] // 2))
+    n0 = (nx + 1) * (ny + 1)
+    total = n0 * (7 * c * c * 8 + 132 * c)
+    for li, (a, b) in enumerate(levels):
+        nl = (a + 1) * (b + 1)
+        per_pass = 7 * c * c * 4 + 16 * c
+        if li == len(levels) - 1:
+            total += 15 * nl * per_pass
+        else:
+            total += nl * (4 * per_pass + 30 * c)
+    return float(total)
 
 
 # ---------------------------------------------------------------------- serving (c5)
@@ -444,7 +472,8 @@ def main():
             peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         except OSError:
             pass
-        print(json.dumps(bench_batch(api, ctx, stream, peaks, args.batch_n, args.batch_maxit, plain=False)), flush=True)
+        print(json.dumps(bench_batch(api, ctx, stream, peaks, args.batch_n, args.batch_maxit, plain=False,
+                                     mg_only=args.batch_mg_only)), flush=True)
         ctx.close()
         return
     mesh, prob = make_problem(api, ctx)
@@ -507,26 +536,28 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
-    NT = 2 * NX * NY
-    # algorithmic FP64 work of a PCG iteration: per simplex the scaled stress (Jacobian by path
-    # differences, trace, three stress entries: 22 flops), per node its two-component row from
-    # the stresses of its six simplices (48 flops) and the CG recurrences and dots (12 flops
-    # per DOF)
-    flop_per_it = 22.0 * NT + 48.0 * mesh.num_nodes + 12.0 * 2 * mesh.num_nodes
-    bytes_per_it = 96.0 * 2 * mesh.num_nodes + 8.0 * NT
-    if args.precision == "fp64":
+    if args.precond == "mg":
+        bpi = mg_state_bytes_per_iteration(NX, NY, 2)
+        launch_ms = state_ms / len(logs)                  # one state solve (one k_pcg_mg launch) per step
+        its_per_launch = state_iters / len(logs)
+        achieved = bpi * its_per_launch / (launch_ms / 1e3) / 1e9
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": "k_pcg_mg<2, 2, true, 1>",
+                "algorithmic_bytes_per_iteration": bpi, "iterations_per_launch": its_per_launch,
+                "launch_ms": launch_ms,
+                "note": "peak = measured HBM copy bandwidth; the state hierarchy (~15 MB) stays in L2, so the "
+                        "kernel is bound by the latency of its ~40 grid barriers per iteration, not by HBM; "
+                        "launch_ms is the state phase (hierarchy rebuild + solve) on the launching stream"}
+    else:
+        NT = 2 * NX * NY
+        # FP64 work of a Jacobi-PCG iteration: per node its two-component difference-form row
+        # (7 slots x 2x2 blocks: 56 flops) and the CG recurrences and dots (12 flops per DOF)
+        flop_per_it = (56.0 + 24.0) * mesh.num_nodes
         achieved = flop_per_it * state_iters / (state_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s (FP64)",
-                "frac": achieved / 1.25, "traffic": None,
-                "kernel": "k_pcg<2, TiledElasticOp<2,double>, double, 1>",
-                "note": "FP64 peak 1.25 TFLOP/s nominal (probe measured 1.19); L2-resident working set "
-                        f"(~{bytes_per_it / 1e6:.1f} MB/iteration), so HBM is not the bound",
-                "hbm_frac_of_measured": bytes_per_it * state_iters / (state_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
-    else:
-        achieved = bytes_per_it / 2 * state_iters / (state_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
-                "frac": achieved / peaks.get("hbm_gbs", 6800.0), "traffic": None,
-                "kernel": "k_pcg<2, TiledElasticOp<2,float>, double, 1>"}
+                "frac": achieved / 1.25, "traffic": None, "kernel": "k_pcg<2, StencilOp<2,2,true,double>>",
+                "note": "FP64 peak 1.25 TFLOP/s nominal (probe measured 1.19)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "opt-iters/s", "n_gpus": world, "steps": args.steps,

@@ -58,7 +58,7 @@ struct BmgCg {
   const double *kk, *w2;     // [nip] k_i, omega_i^2
   const double *B;           // loads [N][nip]; the right-hand side is bscale * B
   double bscale;
-  double *X, *r, *p, *s;     // [N][nip]
+  double *X, *r, *p[2], *s;  // [N][nip]; the directions double-buffered (gathered at neighbours)
   double *partials;          // [2 nip][G]
   double *totals;            // [2 nip]
   int *status;
@@ -185,6 +185,352 @@ struct BmgOps {
   }
 };
 
+// ------------------------------------------------------------------ tiled grid passes
+// Levels run by the whole grid are swept tile by tile: a block stages with cp.async (many
+// independent 16-byte copies in flight, zero-filled outside the grid) the rows it needs --
+// the iterate on the tile's halo box, its own right-hand sides and stencil rows -- and then
+// forms its own nodes' rows from shared memory, a warp per node and a lane per instance.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// A tile of TX x TY (x TZ) own nodes and its halo box, one node wider on every side (every
+// Kuhn neighbour is within one step per axis).  Own dimensions are even, so that the coarse
+// nodes the halo interpolates from form a (T/2 + 2)-wide box.
+template <int D, int TX_, int TY_, int TZ_>
+struct Tile {
+  static constexpr int TX = TX_, TY = TY_, TZ = D == 3 ? TZ_ : 1;
+  static constexpr int HX = TX + 2, HY = TY + 2, HZ = D == 3 ? TZ + 2 : 1;
+  static constexpr int NH = HX * HY * HZ, NT = TX * TY * TZ;
+  static_assert(TX % 2 == 0 && TY % 2 == 0 && (D == 2 || TZ % 2 == 0), "even tiles");
+  __host__ __device__ static long long count(const Grid &g) {
+    return ((g.nn[0] + TX - 1) / TX) * ((g.nn[1] + TY - 1) / TY) * (D == 3 ? (g.nn[2] + TZ - 1) / TZ : 1);
+  }
+  __device__ static void origin(const Grid &g, long long t, int o[3]) {
+    const long long ntx = (g.nn[0] + TX - 1) / TX, nty = (g.nn[1] + TY - 1) / TY;
+    o[0] = (int)(t % ntx) * TX;
+    const long long r = t / ntx;
+    o[1] = (int)(r % nty) * TY;
+    o[2] = D == 3 ? (int)(r / nty) * TZ : 0;
+  }
+  // node of halo slot h (-1 outside the grid)
+  __device__ static long long halo_node(const Grid &g, const int o[3], int h) {
+    const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+    const int x = o[0] - 1 + hx, y = o[1] - 1 + hy, z = D == 3 ? o[2] - 1 + hz : 0;
+    if (x < 0 || x >= g.nn[0] || y < 0 || y >= g.nn[1]) return -1;
+    if (D == 3 && (z < 0 || z >= g.nn[2])) return -1;
+    return x + g.stride[1] * y + (D == 3 ? g.stride[2] * z : 0);
+  }
+  // node of own slot t (-1 outside the grid) and its halo slot
+  __device__ static long long own_node(const Grid &g, const int o[3], int t, int &hs) {
+    const int tx = t % TX, ty = (t / TX) % TY, tz = t / (TX * TY);
+    hs = (tx + 1) + HX * (ty + 1) + (D == 3 ? HX * HY * (tz + 1) : 0);
+    const int x = o[0] + tx, y = o[1] + ty, z = o[2] + tz;
+    if (x >= g.nn[0] || y >= g.nn[1] || (D == 3 && z >= g.nn[2])) return -1;
+    return x + g.stride[1] * y + (D == 3 ? g.stride[2] * z : 0);
+  }
+  __device__ static int slot_shift(int s) {
+    int dl[3];
+    slot_offset<D>(s, dl);
+    return dl[0] + HX * dl[1] + (D == 3 ? HX * HY * dl[2] : 0);
+  }
+};
+
+// Tile shapes per dimension and instance slab count: FP32 stencil passes, restriction (coarse
+// tile), FP64 operator pass.  The 32- and 64-lane kernels share shapes, so an instance's
+// reductions run in the same order in both.
+template <int D, int NJ>
+struct BmgTiles;
+template <> struct BmgTiles<2, 1> { using T32 = Tile<2, 16, 8, 1>; using TR = Tile<2, 8, 4, 1>; using T64 = Tile<2, 16, 4, 1>; };
+template <> struct BmgTiles<2, 2> { using T32 = Tile<2, 16, 8, 1>; using TR = Tile<2, 8, 4, 1>; using T64 = Tile<2, 16, 4, 1>; };
+template <> struct BmgTiles<2, 4> { using T32 = Tile<2, 8, 4, 1>; using TR = Tile<2, 8, 2, 1>; using T64 = Tile<2, 8, 2, 1>; };
+template <> struct BmgTiles<3, 1> { using T32 = Tile<3, 4, 4, 4>; using TR = Tile<3, 4, 2, 2>; using T64 = Tile<3, 4, 2, 2>; };
+template <> struct BmgTiles<3, 2> { using T32 = Tile<3, 4, 4, 4>; using TR = Tile<3, 4, 2, 2>; using T64 = Tile<3, 4, 2, 2>; };
+template <> struct BmgTiles<3, 4> { using T32 = Tile<3, 4, 2, 2>; using TR = Tile<3, 2, 2, 2>; using T64 = Tile<3, 2, 2, 2>; };
+
+template <int D, int NJ>
+struct BmgTiled {
+  using TL = typename BmgTiles<D, NJ>::T32;
+  using TR = typename BmgTiles<D, NJ>::TR;
+  using T6 = typename BmgTiles<D, NJ>::T64;
+  using Coef = typename BmgOps<D, NJ>::Coef;
+  static constexpr int S = ST<D>::S, NIP = 32 * NJ;
+  static constexpr int CH32 = NIP * 4 / 16, CH64 = NIP * 8 / 16;   // 16-byte chunks per row
+  // coarse box behind a T32 halo; fine box behind a coarse TR tile
+  static constexpr int CHX = TL::TX / 2 + 2, CHY = TL::TY / 2 + 2, CHZ = D == 3 ? TL::TZ / 2 + 2 : 1;
+  static constexpr int NC = CHX * CHY * CHZ;
+  static constexpr int FRX = 2 * TR::TX + 1, FRY = 2 * TR::TY + 1, FRZ = D == 3 ? 2 * TR::TZ + 1 : 1;
+  static constexpr int NFR = FRX * FRY * FRZ;
+  static constexpr size_t smem_stencil =
+      4 * ((size_t)TL::NH * NIP + (size_t)TL::NT * NIP + (size_t)NC * NIP + 2 * (S + 1) * (size_t)TL::NT) + TL::NH;
+  static constexpr size_t smem_restrict = 4 * ((size_t)NFR * NIP + 2 * (size_t)TR::NT) + TR::NT;
+  static constexpr size_t smem_apply = 12 * (size_t)T6::NH * NIP + 16 * (size_t)S * T6::NT;
+  static constexpr size_t smem_reduce = 8 * ((size_t)BMG_WARPS * 2 * NIP + 2 * NIP);
+  static constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+  static constexpr size_t smem = (cmax(cmax(smem_stencil, smem_restrict), cmax(smem_apply, smem_reduce)) + 15) / 16 * 16;
+
+  // MODE 0: z_out = z_in + omega D^{-1} (b - A z_in).  MODE 1: the same after adding the
+  // prolongated coarse correction P z_c to z_in on the fly (prolongation and first post-sweep
+  // in one pass; the corrected iterate is never stored).  MODE 2: t = b - A z_in.
+  template <int MODE>
+  static __device__ void stencil_pass(const BmgLevel &L, const float *zin, float *out, float omega, const Coef &cf,
+                                      const BmgLevel *C, const float *zc, unsigned char *smem, int lane) {
+    const Grid &g = L.g;
+    const long long N = g.num_nodes;
+    float *sz = reinterpret_cast<float *>(smem);
+    float *sb = sz + TL::NH * NIP;
+    float *sc = sb + TL::NT * NIP;
+    float *swK = sc + NC * NIP;
+    float *swM = swK + (S + 1) * TL::NT;
+    unsigned char *sdir = reinterpret_cast<unsigned char *>(swM + (S + 1) * TL::NT);
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const long long ntile = TL::count(g);
+    for (long long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+      int o[3];
+      TL::origin(g, tile, o);
+      __syncthreads();   // the previous tile's shared data is consumed
+      for (int c = threadIdx.x; c < TL::NH * CH32; c += blockDim.x) {
+        const int h = c / CH32, k = c - h * CH32;
+        const long long nb = TL::halo_node(g, o, h);
+        cp_async16(sz + h * NIP + 4 * k, zin + (nb < 0 ? 0 : nb * NIP) + 4 * k, nb >= 0);
+      }
+      for (int c = threadIdx.x; c < TL::NT * CH32; c += blockDim.x) {
+        const int t = c / CH32, k = c - t * CH32;
+        int hs;
+        const long long a = TL::own_node(g, o, t, hs);
+        cp_async16(sb + t * NIP + 4 * k, L.b + (a < 0 ? 0 : a * NIP) + 4 * k, a >= 0);
+      }
+      for (int c = threadIdx.x; c < (S + 1) * TL::NT; c += blockDim.x) {
+        const int s = c / TL::NT, t = c - s * TL::NT;
+        int hs;
+        const long long a = TL::own_node(g, o, t, hs);
+        const long long off = a < 0 ? 0 : (long long)s * N + a;
+        cp_async4(swK + c, L.SK + off, a >= 0);
+        cp_async4(swM + c, L.SM + off, a >= 0);
+      }
+      const int co[3] = {o[0] / 2 - 1, o[1] / 2 - 1, D == 3 ? o[2] / 2 - 1 : 0};
+      if (MODE == 1) {
+        const Grid &gc = C->g;
+        for (int c = threadIdx.x; c < NC * CH32; c += blockDim.x) {
+          const int q = c / CH32, k = c - q * CH32;
+          const int x = co[0] + q % CHX, y = co[1] + (q / CHX) % CHY, z = co[2] + q / (CHX * CHY);
+          const bool in = x >= 0 && x < gc.nn[0] && y >= 0 && y < gc.nn[1] && (D == 2 || (z >= 0 && z < gc.nn[2]));
+          const long long cn = in ? x + gc.stride[1] * y + (D == 3 ? gc.stride[2] * z : 0) : 0;
+          cp_async16(sc + q * NIP + 4 * k, zc + cn * NIP + 4 * k, in);
+        }
+        for (int h = threadIdx.x; h < TL::NH; h += blockDim.x) {
+          const long long nb = TL::halo_node(g, o, h);
+          sdir[h] = nb < 0 ? 1 : L.dir[nb];
+        }
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      if (MODE == 1) {   // halo iterate += P z_c (Dirichlet nodes and nodes outside untouched)
+        for (int h = warp; h < TL::NH; h += nw) {
+          if (sdir[h]) continue;
+          const int f[3] = {o[0] - 1 + h % TL::HX, o[1] - 1 + (h / TL::HX) % TL::HY,
+                            D == 3 ? o[2] - 1 + h / (TL::HX * TL::HY) : 0};
+          const int cst[3] = {1, CHX, CHX * CHY};
+          int q1 = 0, q2 = 0;
+          bool mid = false;
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const int bit = f[k] & 1;
+            mid |= bit != 0;
+            q1 += ((f[k] - bit) / 2 - co[k]) * cst[k];
+            q2 += ((f[k] + bit) / 2 - co[k]) * cst[k];
+          }
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) {
+            const int i = lane + 32 * j;
+            const float v = mid ? __fmul_rn(0.5f, __fadd_rn(sc[q1 * NIP + i], sc[q2 * NIP + i])) : sc[q1 * NIP + i];
+            sz[h * NIP + i] = __fadd_rn(sz[h * NIP + i], v);
+          }
+        }
+        __syncthreads();
+      }
+      for (int t = warp; t < TL::NT; t += nw) {
+        int hs;
+        const long long a = TL::own_node(g, o, t, hs);
+        if (a < 0) continue;
+        const float rk = swK[t], rm = swM[t], dk = swK[S * TL::NT + t], dm = swM[S * TL::NT + t];
+        float za[NJ], az[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          za[j] = sz[hs * NIP + lane + 32 * j];
+          az[j] = __fmul_rn(fmaf(cf.k[j], rk, __fmul_rn(cf.w[j], rm)), za[j]);
+        }
+#pragma unroll
+        for (int s = 1; s < S; ++s) {
+          const float wk = swK[s * TL::NT + t], wm = swM[s * TL::NT + t];
+          if (wk == 0.f && wm == 0.f) continue;
+          const int hn = hs + TL::slot_shift(s);
+#pragma unroll
+          for (int j = 0; j < NJ; ++j)
+            az[j] = fmaf(fmaf(cf.k[j], wk, __fmul_rn(cf.w[j], wm)), __fsub_rn(sz[hn * NIP + lane + 32 * j], za[j]),
+                         az[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const int i = lane + 32 * j;
+          const float bq = sb[t * NIP + i];
+          if (MODE == 2) {
+            out[a * NIP + i] = __fsub_rn(bq, az[j]);
+          } else {
+            const float dg = fmaf(cf.k[j], dk, __fmul_rn(cf.w[j], dm));
+            out[a * NIP + i] = __fadd_rn(za[j], __fdiv_rn(__fmul_rn(omega, __fsub_rn(bq, az[j])), dg));
+          }
+        }
+      }
+    }
+  }
+
+  // coarse b = P^T t (zero on coarse Dirichlet nodes) and the coarse level's first sweep
+  static __device__ void restrict_pass(const BmgLevel &F, const BmgLevel &C, float omega, const Coef &cf,
+                                       unsigned char *smem, int lane) {
+    const Grid &gc = C.g, &gf = F.g;
+    const long long Nc = gc.num_nodes;
+    float *st = reinterpret_cast<float *>(smem);
+    float *sdk = st + NFR * NIP;
+    float *sdm = sdk + TR::NT;
+    unsigned char *sdc = reinterpret_cast<unsigned char *>(sdm + TR::NT);
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const long long ntile = TR::count(gc);
+    for (long long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+      int co[3];
+      TR::origin(gc, tile, co);
+      __syncthreads();
+      const int fo[3] = {2 * co[0] - 1, 2 * co[1] - 1, D == 3 ? 2 * co[2] - 1 : 0};
+      for (int c = threadIdx.x; c < NFR * CH32; c += blockDim.x) {
+        const int q = c / CH32, k = c - q * CH32;
+        const int x = fo[0] + q % FRX, y = fo[1] + (q / FRX) % FRY, z = fo[2] + q / (FRX * FRY);
+        const bool in = x >= 0 && x < gf.nn[0] && y >= 0 && y < gf.nn[1] && (D == 2 || (z >= 0 && z < gf.nn[2]));
+        const long long fn = in ? x + gf.stride[1] * y + (D == 3 ? gf.stride[2] * z : 0) : 0;
+        cp_async16(st + q * NIP + 4 * k, F.t + fn * NIP + 4 * k, in);
+      }
+      for (int t = threadIdx.x; t < TR::NT; t += blockDim.x) {
+        int hs;
+        const long long cn = TR::own_node(gc, co, t, hs);
+        sdk[t] = cn < 0 ? 1.f : C.SK[S * Nc + cn];
+        sdm[t] = cn < 0 ? 0.f : C.SM[S * Nc + cn];
+        sdc[t] = cn < 0 ? 1 : C.dir[cn];
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      for (int t = warp; t < TR::NT; t += nw) {
+        int hs;
+        const long long cn = TR::own_node(gc, co, t, hs);
+        if (cn < 0) continue;
+        const int tx = t % TR::TX, ty = (t / TR::TX) % TR::TY, tz = t / (TR::TX * TR::TY);
+        const int q0 = (2 * tx + 1) + FRX * (2 * ty + 1) + (D == 3 ? FRX * FRY * (2 * tz + 1) : 0);
+        float v[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) v[j] = st[q0 * NIP + lane + 32 * j];
+#pragma unroll
+        for (int s = 1; s < S; ++s) {
+          int dl[3];
+          slot_offset<D>(s, dl);
+          const int q = q0 + dl[0] + FRX * dl[1] + (D == 3 ? FRX * FRY * dl[2] : 0);
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) v[j] = fmaf(0.5f, st[q * NIP + lane + 32 * j], v[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const long long qq = cn * NIP + lane + 32 * j;
+          const float bk = sdc[t] ? 0.f : v[j];
+          C.b[qq] = bk;
+          C.z[0][qq] = __fdiv_rn(__fmul_rn(omega, bk), fmaf(cf.k[j], sdk[t], __fmul_rn(cf.w[j], sdm[t])));
+        }
+      }
+    }
+  }
+
+  // p_new = z + beta p_old (formed on the halo in shared memory), s = A p_new in FP64 from the
+  // plain node-major FP64 rows; writes p_new and s of the own nodes; dot += (p_new, s).
+  static __device__ void apply_pass(const Grid &g, const double *WK, const double *WM, const double *pold,
+                                    const float *z, double *pnew, double *sout, const double (&beta)[NJ],
+                                    const double (&kk)[NJ], const double (&w2)[NJ], double (&dot)[NJ],
+                                    unsigned char *smem, int lane) {
+    double *sp = reinterpret_cast<double *>(smem);
+    float *szz = reinterpret_cast<float *>(sp + T6::NH * NIP);
+    double *swK = reinterpret_cast<double *>(szz + T6::NH * NIP);
+    double *swM = swK + S * T6::NT;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const long long ntile = T6::count(g);
+    for (long long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+      int o[3];
+      T6::origin(g, tile, o);
+      __syncthreads();
+      for (int c = threadIdx.x; c < T6::NH * CH64; c += blockDim.x) {
+        const int h = c / CH64, k = c - h * CH64;
+        const long long nb = T6::halo_node(g, o, h);
+        cp_async16(sp + h * NIP + 2 * k, pold + (nb < 0 ? 0 : nb * NIP) + 2 * k, nb >= 0);
+      }
+      for (int c = threadIdx.x; c < T6::NH * CH32; c += blockDim.x) {
+        const int h = c / CH32, k = c - h * CH32;
+        const long long nb = T6::halo_node(g, o, h);
+        cp_async16(szz + h * NIP + 4 * k, z + (nb < 0 ? 0 : nb * NIP) + 4 * k, nb >= 0);
+      }
+      for (int c = threadIdx.x; c < S * T6::NT; c += blockDim.x) {
+        const int t = c / S, s = c - t * S;
+        int hs;
+        const long long a = T6::own_node(g, o, t, hs);
+        const long long off = a < 0 ? 0 : a * S + s;
+        cp_async8(swK + c, WK + off, a >= 0);
+        cp_async8(swM + c, WM + off, a >= 0);
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      for (int h = warp; h < T6::NH; h += nw)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const int q = h * NIP + lane + 32 * j;
+          sp[q] = fma(beta[j], sp[q], (double)szz[q]);
+        }
+      __syncthreads();
+      for (int t = warp; t < T6::NT; t += nw) {
+        int hs;
+        const long long a = T6::own_node(g, o, t, hs);
+        if (a < 0) continue;
+        double yk[NJ], ym[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) yk[j] = ym[j] = 0.0;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const double wk = swK[t * S + s], wm = swM[t * S + s];
+          if (s > 0 && wk == 0.0 && wm == 0.0) continue;
+          const int hn = hs + T6::slot_shift(s);
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) {
+            const double xv = sp[hn * NIP + lane + 32 * j];
+            yk[j] = fma(wk, xv, yk[j]);
+            ym[j] = fma(wm, xv, ym[j]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const int i = lane + 32 * j;
+          const double y = fma(kk[j], yk[j], __dmul_rn(w2[j], ym[j]));
+          const double pv = sp[hs * NIP + i];
+          pnew[a * NIP + i] = pv;
+          sout[a * NIP + i] = y;
+          dot[j] = fma(pv, y, dot[j]);
+        }
+      }
+    }
+  }
+};
+
 // Buffer index of each level's final iterate after a V-cycle (fixed by the sweep counts).
 __host__ __device__ inline void bmg_final_buffers(int L, int nu, int nuc, int *zc) {
   for (int l = 0; l < L; ++l) {
@@ -234,14 +580,12 @@ __device__ void bmg_block_cycle(const BmgDev &mg, const typename BmgOps<D, NJ>::
 }
 
 // One V-cycle from level 0, whose b and first sweep were written before a grid barrier.
-// Level 0's result ends in z[zc[0]], written by the warp that owns each node (no barrier
-// after the last sweep: the caller reads own nodes first).
+// Level 0's result ends in z[zc[0]], written by the warp that owns each node's tile slot (no
+// barrier after the last sweep: the caller's next pass reads it only after one).
 template <int D, int NJ>
 __device__ bool bmg_vcycle(const BmgDev &mg, const typename BmgOps<D, NJ>::Coef &cf, int *zc, const GridBar &bar,
-                           int lane) {
-  using O = BmgOps<D, NJ>;
-  const long long nw = blockDim.x >> 5;
-  const long long first = blockIdx.x * nw + (threadIdx.x >> 5), step = (long long)gridDim.x * nw;
+                           unsigned char *smem, int lane) {
+  using TP = BmgTiled<D, NJ>;
   const int Lg = mg.Lg;
   if (Lg == 0) {
     if (blockIdx.x == 0) bmg_block_cycle<D, NJ>(mg, cf, 0, zc, lane);
@@ -253,28 +597,28 @@ __device__ bool bmg_vcycle(const BmgDev &mg, const typename BmgOps<D, NJ>::Coef 
     const int sweeps = coarsest ? mg.nuc : mg.nu;
     int c = 0;
     for (int j = 1; j < sweeps; ++j) {
-      O::sweep(L, L.z[c], L.z[c ^ 1], mg.omega, cf, first, step, lane);
+      TP::template stencil_pass<0>(L, L.z[c], L.z[c ^ 1], mg.omega, cf, nullptr, nullptr, smem, lane);
       c ^= 1;
       if (!grid_sync(bar)) return false;
     }
     zc[l] = c;
     if (coarsest) break;
-    O::residual(L, L.z[c], cf, first, step, lane);
+    TP::template stencil_pass<2>(L, L.z[c], L.t, mg.omega, cf, nullptr, nullptr, smem, lane);
     if (!grid_sync(bar)) return false;
-    O::restrict_(L, mg.lv[l + 1], mg.omega, cf, first, step, lane);
+    TP::restrict_pass(L, mg.lv[l + 1], mg.omega, cf, smem, lane);
     if (!grid_sync(bar)) return false;
   }
   if (Lg < mg.L) {
     if (blockIdx.x == 0) bmg_block_cycle<D, NJ>(mg, cf, Lg, zc, lane);
     if (!grid_sync(bar)) return false;
   }
-  for (int l = std::min(Lg, mg.L - 1) - 1; l >= 0; --l) {
+  for (int l = (Lg < mg.L - 1 ? Lg : mg.L - 1) - 1; l >= 0; --l) {
     const BmgLevel &L = mg.lv[l];
-    O::prolong(L, L.z[zc[l]], mg.lv[l + 1], mg.lv[l + 1].z[zc[l + 1]], first, step, lane);
-    if (!grid_sync(bar)) return false;
+    const BmgLevel &C = mg.lv[l + 1];
     int c = zc[l];
     for (int j = 0; j < mg.nu; ++j) {
-      O::sweep(L, L.z[c], L.z[c ^ 1], mg.omega, cf, first, step, lane);
+      if (j == 0) TP::template stencil_pass<1>(L, L.z[c], L.z[c ^ 1], mg.omega, cf, &C, C.z[zc[l + 1]], smem, lane);
+      else TP::template stencil_pass<0>(L, L.z[c], L.z[c ^ 1], mg.omega, cf, nullptr, nullptr, smem, lane);
       c ^= 1;
       if (l > 0 || j + 1 < mg.nu)
         if (!grid_sync(bar)) return false;
@@ -291,6 +635,7 @@ __device__ bool bmg_allreduce(const BmgCg &C, const double (&v)[NCOL][NJ], doubl
   constexpr int NIP = 32 * NJ;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int G = (int)gridDim.x;
+  __syncthreads();   // the scratch may still be read by the previous pass or reduction
 #pragma unroll
   for (int c = 0; c < NCOL; ++c)
 #pragma unroll
@@ -321,9 +666,11 @@ template <int D, int NJ>
 __global__ void __launch_bounds__(32 * BMG_WARPS, 2) k_bmg_pcg(const BmgDev *mgp, BmgCg C) {
   constexpr int S = ST<D>::S, NIP = 32 * NJ;
   using O = BmgOps<D, NJ>;
+  using TP = BmgTiled<D, NJ>;
+  extern __shared__ __align__(16) unsigned char bmg_smem[];
   __shared__ BmgDev mg;
-  __shared__ double part[BMG_WARPS * 2 * NIP];
-  __shared__ double tot[2 * NIP];
+  double *part = reinterpret_cast<double *>(bmg_smem);   // reduction scratch between passes
+  double *tot = part + BMG_WARPS * 2 * NIP;
   {
     const int *src = reinterpret_cast<const int *>(mgp);
     int *dst = reinterpret_cast<int *>(&mg);
@@ -349,33 +696,12 @@ __global__ void __launch_bounds__(32 * BMG_WARPS, 2) k_bmg_pcg(const BmgDev *mgp
   const int zfin = zc[0];
   const float omega = mg.omega;
 
-  // y = A_i x at node a in FP64 (plain-form rows)
-  auto apply64 = [&](long long a, const int *idx, const double *x, double (&y)[NJ]) {
-    double yk[NJ], ym[NJ];
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) yk[j] = ym[j] = 0.0;
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      const long long nb = slot_node<D>(g, idx, a, s);
-      if (nb < 0) continue;
-      const double wk = C.WK[a * S + s], wm = C.WM[a * S + s];
-      if (s > 0 && wk == 0.0 && wm == 0.0) continue;
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const double xv = x[nb * NIP + lane + 32 * j];
-        yk[j] = fma(wk, xv, yk[j]);
-        ym[j] = fma(wm, xv, ym[j]);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) y[j] = fma(kk[j], yk[j], __dmul_rn(w2[j], ym[j]));
-  };
-
   double bb[NJ], rr[NJ], gam[NJ];
   bool done[NJ];
   int its[NJ];
   bool nan_seen = false;
-  // r = b - A x; p = 0; level-0 right-hand side and first sweep; ||b||^2, ||r||^2
+  // r = b - A x; p = 0; level-0 right-hand side and first sweep; ||b||^2, ||r||^2 (once per
+  // solve: warp per node)
   {
     double v[2][NJ];
 #pragma unroll
@@ -384,19 +710,35 @@ __global__ void __launch_bounds__(32 * BMG_WARPS, 2) k_bmg_pcg(const BmgDev *mgp
       int idx[3];
       node_ijk(g, a, idx);
       double ax[NJ];
-      if (C.warm) apply64(a, idx, C.X, ax);
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) ax[j] = 0.0;
+      if (C.warm) {
+        double yk[NJ], ym[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) yk[j] = ym[j] = 0.0;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const long long nb = slot_node<D>(g, idx, a, s);
+          if (nb < 0) continue;
+          const double wk = C.WK[a * S + s], wm = C.WM[a * S + s];
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) {
+            const double xv = C.X[nb * NIP + lane + 32 * j];
+            yk[j] = fma(wk, xv, yk[j]);
+            ym[j] = fma(wm, xv, ym[j]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) ax[j] = fma(kk[j], yk[j], __dmul_rn(w2[j], ym[j]));
+      }
       const float dk = L0.SK[S * N + a], dm = L0.SM[S * N + a];
 #pragma unroll
       for (int j = 0; j < NJ; ++j) {
         const long long q = a * NIP + lane + 32 * j;
         const double bq = C.bscale * C.B[q];
-        if (!C.warm) {
-          C.X[q] = 0.0;
-          ax[j] = 0.0;
-        }
         const double r0 = bq - ax[j];
         C.r[q] = r0;
-        C.p[q] = 0.0;
+        C.p[0][q] = 0.0;
         const float bf = (float)r0;
         L0.b[q] = bf;
         L0.z[0][q] = __fdiv_rn(__fmul_rn(omega, bf), fmaf(cf.k[j], dk, __fmul_rn(cf.w[j], dm)));
@@ -413,26 +755,53 @@ __global__ void __launch_bounds__(32 * BMG_WARPS, 2) k_bmg_pcg(const BmgDev *mgp
       its[j] = 0;
       gam[j] = 0.0;
     }
+    if (!C.warm)   // X = 0 (after every block has read X for the residual: none did)
+      for (long long a = first; a < N; a += step)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) C.X[a * NIP + lane + 32 * j] = 0.0;
   }
-  int it = 0;
+  int it = 0, cur = 0;
   for (;;) {
     bool all = true;
 #pragma unroll
     for (int j = 0; j < NJ; ++j) all = all && done[j];
     all = __all_sync(0xffffffffu, all);
     if (all || it >= C.maxit) break;
-    if (!bmg_vcycle<D, NJ>(mg, cf, zc, C.bar, lane)) return;
+    if (!bmg_vcycle<D, NJ>(mg, cf, zc, C.bar, bmg_smem, lane)) return;
     const float *z = L0.z[zfin];
-    // gamma = (r, z)
+    // gamma = (r, z), in the tile order of the last sweep (each z read by the thread that
+    // wrote it: no barrier needed), four nodes at a time
     double v1[1][NJ];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) v1[0][j] = 0.0;
-    for (long long a = first; a < N; a += step)
+    {
+      using TL = typename TP::TL;
+      const long long ntile = TL::count(g);
+      for (long long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        int o[3];
+        TL::origin(g, tile, o);
+        for (int t0 = warp; t0 < TL::NT; t0 += 4 * nw) {
+          double rv[4][NJ];
+          float zv[4][NJ];
 #pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const long long q = a * NIP + lane + 32 * j;
-        v1[0][j] = fma(C.r[q], (double)z[q], v1[0][j]);
+          for (int u = 0; u < 4; ++u) {
+            int hs;
+            const int t = t0 + u * nw;
+            long long a = t < TL::NT ? TL::own_node(g, o, t, hs) : -1;
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+              const long long q = (a < 0 ? 0 : a) * NIP + lane + 32 * j;
+              rv[u][j] = a < 0 ? 0.0 : C.r[q];
+              zv[u][j] = a < 0 ? 0.f : z[q];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) v1[0][j] = fma(rv[u][j], (double)zv[u][j], v1[0][j]);
+        }
       }
+    }
     if (!bmg_allreduce<1, NJ>(C, v1, part, tot)) return;
     double beta[NJ];
 #pragma unroll
@@ -441,29 +810,11 @@ __global__ void __launch_bounds__(32 * BMG_WARPS, 2) k_bmg_pcg(const BmgDev *mgp
       beta[j] = (it > 0 && gam[j] > 0.0) ? gn / gam[j] : 0.0;
       gam[j] = gn;
     }
-    // p = z + beta p
-    for (long long a = first; a < N; a += step)
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const long long q = a * NIP + lane + 32 * j;
-        C.p[q] = fma(beta[j], C.p[q], (double)z[q]);
-      }
-    if (!grid_sync(C.bar)) return;
-    // s = A p; (p, s)
+    // p_new = z + beta p_old, s = A p_new, (p_new, s)
 #pragma unroll
     for (int j = 0; j < NJ; ++j) v1[0][j] = 0.0;
-    for (long long a = first; a < N; a += step) {
-      int idx[3];
-      node_ijk(g, a, idx);
-      double sv[NJ];
-      apply64(a, idx, C.p, sv);
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const long long q = a * NIP + lane + 32 * j;
-        C.s[q] = sv[j];
-        v1[0][j] = fma(C.p[q], sv[j], v1[0][j]);
-      }
-    }
+    TP::apply_pass(g, C.WK, C.WM, C.p[cur], z, C.p[cur ^ 1], C.s, beta, kk, w2, v1[0], bmg_smem, lane);
+    cur ^= 1;
     if (!bmg_allreduce<1, NJ>(C, v1, part, tot)) return;
     double alpha[NJ];
 #pragma unroll
@@ -478,18 +829,39 @@ __global__ void __launch_bounds__(32 * BMG_WARPS, 2) k_bmg_pcg(const BmgDev *mgp
     // x += alpha p; r -= alpha s; next level-0 right-hand side and first sweep; ||r||^2
 #pragma unroll
     for (int j = 0; j < NJ; ++j) v1[0][j] = 0.0;
-    for (long long a = first; a < N; a += step) {
-      const float dk = L0.SK[S * N + a], dm = L0.SM[S * N + a];
+    const double *pc = C.p[cur];
+    for (long long a0 = first; a0 < N; a0 += 2 * step) {
+      double xv[2][NJ], pv[2][NJ], rv[2][NJ], sv[2][NJ];
+      float dk[2], dm[2];
 #pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const long long q = a * NIP + lane + 32 * j;
-        C.X[q] = fma(alpha[j], C.p[q], C.X[q]);
-        const double r1 = fma(-alpha[j], C.s[q], C.r[q]);
-        C.r[q] = r1;
-        const float bf = (float)r1;
-        L0.b[q] = bf;
-        L0.z[0][q] = __fdiv_rn(__fmul_rn(omega, bf), fmaf(cf.k[j], dk, __fmul_rn(cf.w[j], dm)));
-        v1[0][j] = fma(r1, r1, v1[0][j]);
+      for (int u = 0; u < 2; ++u) {
+        const long long a = a0 + u * step, ac = a < N ? a : 0;
+        dk[u] = L0.SK[S * N + ac];
+        dm[u] = L0.SM[S * N + ac];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const long long q = ac * NIP + lane + 32 * j;
+          xv[u][j] = C.X[q];
+          pv[u][j] = pc[q];
+          rv[u][j] = C.r[q];
+          sv[u][j] = C.s[q];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const long long a = a0 + u * step;
+        if (a >= N) continue;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const long long q = a * NIP + lane + 32 * j;
+          C.X[q] = fma(alpha[j], pv[u][j], xv[u][j]);
+          const double r1 = fma(-alpha[j], sv[u][j], rv[u][j]);
+          C.r[q] = r1;
+          const float bf = (float)r1;
+          L0.b[q] = bf;
+          L0.z[0][q] = __fdiv_rn(__fmul_rn(omega, bf), fmaf(cf.k[j], dk[u], __fmul_rn(cf.w[j], dm[u])));
+          v1[0][j] = fma(r1, r1, v1[0][j]);
+        }
       }
     }
     if (!bmg_allreduce<1, NJ>(C, v1, part, tot)) return;
@@ -558,7 +930,7 @@ struct fo_bmg {
   uint8_t *dir[MG_MAX_LEVELS] = {};
   float *SK[MG_MAX_LEVELS] = {}, *SM[MG_MAX_LEVELS] = {};
   float *b[MG_MAX_LEVELS] = {}, *z0[MG_MAX_LEVELS] = {}, *z1[MG_MAX_LEVELS] = {}, *t[MG_MAX_LEVELS] = {};
-  double *r = nullptr, *p = nullptr, *s = nullptr, *partials = nullptr;
+  double *r = nullptr, *p0 = nullptr, *p1 = nullptr, *s = nullptr, *partials = nullptr;
   void *dev = nullptr;
   std::vector<unsigned char> host;
   std::vector<std::pair<void **, size_t>> allocs;
@@ -572,10 +944,20 @@ void fo_bmg_destroy(fo_problem *p) {
   p->batch->mg = nullptr;
 }
 
-using BmgKernel = void (*)(const BmgDev *, BmgCg);
+struct BmgKernel {
+  void (*fn)(const BmgDev *, BmgCg) = nullptr;
+  size_t smem = 0;
+};
+template <int D, int NJ>
+static BmgKernel bmg_entry() {
+  BmgKernel k;
+  k.fn = k_bmg_pcg<D, NJ>;
+  k.smem = BmgTiled<D, NJ>::smem;
+  return k;
+}
 static BmgKernel bmg_kernel(int dim, int nj) {
-  if (dim == 2) return nj == 1 ? k_bmg_pcg<2, 1> : (nj == 2 ? k_bmg_pcg<2, 2> : k_bmg_pcg<2, 4>);
-  return nj == 1 ? k_bmg_pcg<3, 1> : (nj == 2 ? k_bmg_pcg<3, 2> : k_bmg_pcg<3, 4>);
+  if (dim == 2) return nj == 1 ? bmg_entry<2, 1>() : (nj == 2 ? bmg_entry<2, 2>() : bmg_entry<2, 4>());
+  return nj == 1 ? bmg_entry<3, 1>() : (nj == 2 ? bmg_entry<3, 2>() : bmg_entry<3, 4>());
 }
 
 static fo_status bmg_alloc(fo_problem *p) {
@@ -588,8 +970,9 @@ static fo_status bmg_alloc(fo_problem *p) {
   const int S = p->mesh->g.dim == 2 ? 7 : 15;
   const size_t nip = (size_t)bt->nip;
   int per_sm = 0;
-  FO_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)bmg_kernel(p->mesh->g.dim, bt->nip / 32),
-                                                          32 * BMG_WARPS, 0));
+  const BmgKernel k = bmg_kernel(p->mesh->g.dim, bt->nip / 32);
+  FO_CU(ctx, cudaFuncSetAttribute((const void *)k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
+  FO_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k.fn, 32 * BMG_WARPS, k.smem));
   if (per_sm < 1) return fo_fail(ctx, FO_ECUDA, "batched multigrid kernel does not fit on an SM");
   mg->grid_cap = std::min(per_sm * ctx->num_sms, 4096);
   auto add = [&](void **ptr, size_t bytes) { mg->allocs.push_back({ptr, bytes}); };
@@ -610,7 +993,8 @@ static fo_status bmg_alloc(fo_problem *p) {
   }
   const size_t n0 = (size_t)mg->g[0].num_nodes * nip;
   add((void **)&mg->r, sizeof(double) * n0);
-  add((void **)&mg->p, sizeof(double) * n0);
+  add((void **)&mg->p0, sizeof(double) * n0);
+  add((void **)&mg->p1, sizeof(double) * n0);
   add((void **)&mg->s, sizeof(double) * n0);
   add((void **)&mg->partials, sizeof(double) * (2 * nip * (size_t)mg->grid_cap + 2 * nip));
   add(&mg->dev, sizeof(BmgDev));
@@ -693,7 +1077,8 @@ fo_status fo_batch_state_mg(fo_problem *p, const double *B, double bscale, doubl
   C.bscale = bscale;
   C.X = X;
   C.r = mg->r;
-  C.p = mg->p;
+  C.p[0] = mg->p0;
+  C.p[1] = mg->p1;
   C.s = mg->s;
   C.partials = mg->partials;
   C.totals = mg->partials + (size_t)2 * nip * grid;
@@ -708,8 +1093,9 @@ fo_status fo_batch_state_mg(fo_problem *p, const double *B, double bscale, doubl
   FO_CU(ctx, cudaMemsetAsync(p->bar, 0, 64, ctx->stream));
   FO_CU(ctx, cudaMemsetAsync(p->dev_status, 0, sizeof(int) * DS_COUNT, ctx->stream));
   void *argv[] = {(void *)&dev, (void *)&C};
-  FO_CU(ctx, cudaLaunchCooperativeKernel((const void *)bmg_kernel(g.dim, nip / 32), (int)grid, 32 * BMG_WARPS, argv, 0,
-                                         ctx->stream));
+  const BmgKernel k = bmg_kernel(g.dim, nip / 32);
+  FO_CU(ctx, cudaFuncSetAttribute((const void *)k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
+  FO_CU(ctx, cudaLaunchCooperativeKernel((const void *)k.fn, (int)grid, 32 * BMG_WARPS, argv, k.smem, ctx->stream));
   fo_note_launch(1);
   FO_CU(ctx, cudaGetLastError());
   fo_solve_stats s;
