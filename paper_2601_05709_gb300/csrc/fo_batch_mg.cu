@@ -17,7 +17,9 @@
 // R = P^T, damped Jacobi with nu sweeps before and after, nuc on the coarsest level.  Fields
 // are instance-minor [N_l][nip]: a warp owns a node and lane l holds instances l, l + 32, ...,
 // so a neighbour row is one coalesced 128-byte load per 32 instances and the stencil rows are
-// read once for all of them.  Levels of at most BMG_BLOCK_NODES nodes run in block 0 alone.
+// read once for all of them.  The coarse levels (at most BMG_INST_NODES nodes) run one instance
+// per block, the instance's vectors in shared memory and a thread per node, with block barriers
+// only.
 //
 // Outer loop: one FP64 CG recurrence per instance on the FP64 stencils of the fine grid,
 // stopping instance i when ||b_i - A_i x_i||_2 (recurrence) <= rtol ||b_i||_2; a converged
@@ -37,7 +39,7 @@
 #include "fo_ops.cuh"
 
 #define BMG_WARPS 8              // warps per block
-#define BMG_BLOCK_NODES 96       // levels of at most this many nodes run in block 0 alone
+#define BMG_INST_NODES 1100      // levels of at most this many nodes run one instance per block
 
 struct BmgLevel {
   Grid g;
@@ -47,7 +49,7 @@ struct BmgLevel {
 };
 
 struct BmgDev {
-  int L, Lg;              // levels; levels >= Lg run in block 0 alone
+  int L, Lg;              // levels; levels >= Lg run one instance per block in shared memory
   int nu, nuc;
   float omega;
   BmgLevel lv[MG_MAX_LEVELS];
@@ -67,122 +69,21 @@ struct BmgCg {
   double *inst_res;
   double rtol2;
   int maxit, warm;
+  // mixed-precision refinement: inner CG vectors [N][nip]; the correction d accumulates in
+  // FP64 (an FP32 copy would carry rounding noise that A amplifies by its largest eigenvalue)
+  double *d64;
+  float *q32[2], *s32;
+  double inner_rtol2;
+  int inner_maxit;
 };
 
-// ------------------------------------------------------------------ level operations
+// ------------------------------------------------------------------ instance scalars
+// A lane's instances' k_i and omega_i^2 in FP32 (the V-cycle's arithmetic).
 template <int D, int NJ>
 struct BmgOps {
-  static constexpr int S = ST<D>::S, NIP = 32 * NJ;
   struct Coef {
     float k[NJ], w[NJ];
   };
-  // (A_i z)(a), D_i(a) and z(a) for the lane's instances
-  static __device__ __forceinline__ void row(const BmgLevel &L, long long a, const int *idx, const float *z,
-                                             const Coef &c, int lane, float (&za)[NJ], float (&az)[NJ],
-                                             float (&dg)[NJ]) {
-    const long long N = L.g.num_nodes;
-    const float rk = L.SK[a], rm = L.SM[a], dk = L.SK[S * N + a], dm = L.SM[S * N + a];
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      za[j] = z[a * NIP + lane + 32 * j];
-      az[j] = __fmul_rn(fmaf(c.k[j], rk, __fmul_rn(c.w[j], rm)), za[j]);
-      dg[j] = fmaf(c.k[j], dk, __fmul_rn(c.w[j], dm));
-    }
-#pragma unroll
-    for (int s = 1; s < S; ++s) {
-      const long long nb = slot_node<D>(L.g, idx, a, s);
-      if (nb < 0) continue;
-      const float wk = L.SK[s * N + a], wm = L.SM[s * N + a];
-      if (wk == 0.f && wm == 0.f) continue;   // eliminated Dirichlet column (warp-uniform)
-#pragma unroll
-      for (int j = 0; j < NJ; ++j)
-        az[j] = fmaf(fmaf(c.k[j], wk, __fmul_rn(c.w[j], wm)), __fsub_rn(z[nb * NIP + lane + 32 * j], za[j]), az[j]);
-    }
-  }
-  // z_out = z_in + omega D^{-1} (b - A z_in) on nodes first, first + step, ...
-  static __device__ void sweep(const BmgLevel &L, const float *zin, float *zout, float omega, const Coef &c,
-                               long long first, long long step, int lane) {
-    for (long long a = first; a < L.g.num_nodes; a += step) {
-      int idx[3];
-      node_ijk(L.g, a, idx);
-      float za[NJ], az[NJ], dg[NJ];
-      row(L, a, idx, zin, c, lane, za, az, dg);
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const long long q = a * NIP + lane + 32 * j;
-        zout[q] = __fadd_rn(za[j], __fdiv_rn(__fmul_rn(omega, __fsub_rn(L.b[q], az[j])), dg[j]));
-      }
-    }
-  }
-  static __device__ void residual(const BmgLevel &L, const float *z, const Coef &c, long long first, long long step,
-                                  int lane) {
-    for (long long a = first; a < L.g.num_nodes; a += step) {
-      int idx[3];
-      node_ijk(L.g, a, idx);
-      float za[NJ], az[NJ], dg[NJ];
-      row(L, a, idx, z, c, lane, za, az, dg);
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const long long q = a * NIP + lane + 32 * j;
-        L.t[q] = L.b[q] - az[j];
-      }
-    }
-  }
-  // coarse b = P^T t (fine residual; zero on coarse Dirichlet nodes) and the coarse level's
-  // first sweep from zero
-  static __device__ void restrict_(const BmgLevel &F, const BmgLevel &C, float omega, const Coef &c, long long first,
-                                   long long step, int lane) {
-    const long long Nc = C.g.num_nodes;
-    for (long long cn = first; cn < Nc; cn += step) {
-      int ic[3];
-      node_ijk(C.g, cn, ic);
-      int ifn[3] = {2 * ic[0], D >= 2 ? 2 * ic[1] : 0, D == 3 ? 2 * ic[2] : 0};
-      const long long f0 = ifn[0] + F.g.stride[1] * ifn[1] + (D == 3 ? F.g.stride[2] * ifn[2] : 0);
-      float v[NJ];
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) v[j] = F.t[f0 * NIP + lane + 32 * j];
-#pragma unroll
-      for (int s = 1; s < S; ++s) {
-        const long long nb = slot_node<D>(F.g, ifn, f0, s);
-        if (nb < 0) continue;
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) v[j] = fmaf(0.5f, F.t[nb * NIP + lane + 32 * j], v[j]);
-      }
-      const bool dirc = C.dir[cn] != 0;
-      const float dk = C.SK[S * Nc + cn], dm = C.SM[S * Nc + cn];
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const long long q = cn * NIP + lane + 32 * j;
-        const float bk = dirc ? 0.f : v[j];
-        C.b[q] = bk;
-        C.z[0][q] = __fdiv_rn(__fmul_rn(omega, bk), fmaf(c.k[j], dk, __fmul_rn(c.w[j], dm)));
-      }
-    }
-  }
-  // fine z += P (coarse z), Dirichlet nodes untouched
-  static __device__ void prolong(const BmgLevel &F, float *zf, const BmgLevel &C, const float *zc, long long first,
-                                 long long step, int lane) {
-    for (long long a = first; a < F.g.num_nodes; a += step) {
-      if (F.dir[a]) continue;
-      int idx[3];
-      node_ijk(F.g, a, idx);
-      long long c1 = 0, c2 = 0;
-      bool mid = false;
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const int bit = idx[k] & 1;
-        mid |= bit != 0;
-        c1 += (long long)((idx[k] - bit) / 2) * C.g.stride[k];
-        c2 += (long long)((idx[k] + bit) / 2) * C.g.stride[k];
-      }
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const int i = lane + 32 * j;
-        const float v = mid ? __fmul_rn(0.5f, __fadd_rn(zc[c1 * NIP + i], zc[c2 * NIP + i])) : zc[c1 * NIP + i];
-        zf[a * NIP + i] = __fadd_rn(zf[a * NIP + i], v);
-      }
-    }
-  }
 };
 
 // ------------------------------------------------------------------ tiled grid passes
@@ -247,22 +148,23 @@ struct Tile {
 };
 
 // Tile shapes per dimension and instance slab count: FP32 stencil passes, restriction (coarse
-// tile), FP64 operator pass.  The 32- and 64-lane kernels share shapes, so an instance's
+// tile), FP64 operator passes, FP32 operator pass of the refinement's inner CG.  The 32- and 64-lane kernels share shapes, so an instance's
 // reductions run in the same order in both.
 template <int D, int NJ>
 struct BmgTiles;
-template <> struct BmgTiles<2, 1> { using T32 = Tile<2, 16, 8, 1>; using TR = Tile<2, 8, 4, 1>; using T64 = Tile<2, 16, 4, 1>; };
-template <> struct BmgTiles<2, 2> { using T32 = Tile<2, 16, 8, 1>; using TR = Tile<2, 8, 4, 1>; using T64 = Tile<2, 16, 4, 1>; };
-template <> struct BmgTiles<2, 4> { using T32 = Tile<2, 8, 4, 1>; using TR = Tile<2, 8, 2, 1>; using T64 = Tile<2, 8, 2, 1>; };
-template <> struct BmgTiles<3, 1> { using T32 = Tile<3, 4, 4, 4>; using TR = Tile<3, 4, 2, 2>; using T64 = Tile<3, 4, 2, 2>; };
-template <> struct BmgTiles<3, 2> { using T32 = Tile<3, 4, 4, 4>; using TR = Tile<3, 4, 2, 2>; using T64 = Tile<3, 4, 2, 2>; };
-template <> struct BmgTiles<3, 4> { using T32 = Tile<3, 4, 2, 2>; using TR = Tile<3, 2, 2, 2>; using T64 = Tile<3, 2, 2, 2>; };
+template <> struct BmgTiles<2, 1> { using T32 = Tile<2, 16, 8, 1>; using TR = Tile<2, 8, 4, 1>; using T64 = Tile<2, 16, 4, 1>; using TA = T32; };
+template <> struct BmgTiles<2, 2> { using T32 = Tile<2, 16, 8, 1>; using TR = Tile<2, 8, 4, 1>; using T64 = Tile<2, 16, 4, 1>; using TA = T32; };
+template <> struct BmgTiles<2, 4> { using T32 = Tile<2, 8, 4, 1>; using TR = Tile<2, 8, 2, 1>; using T64 = Tile<2, 8, 2, 1>; using TA = T32; };
+template <> struct BmgTiles<3, 1> { using T32 = Tile<3, 4, 4, 4>; using TR = Tile<3, 4, 2, 2>; using T64 = Tile<3, 4, 2, 2>; using TA = T64; };
+template <> struct BmgTiles<3, 2> { using T32 = Tile<3, 4, 4, 4>; using TR = Tile<3, 4, 2, 2>; using T64 = Tile<3, 4, 2, 2>; using TA = T64; };
+template <> struct BmgTiles<3, 4> { using T32 = Tile<3, 4, 2, 2>; using TR = Tile<3, 2, 2, 2>; using T64 = Tile<3, 2, 2, 2>; using TA = T64; };
 
 template <int D, int NJ>
 struct BmgTiled {
   using TL = typename BmgTiles<D, NJ>::T32;
   using TR = typename BmgTiles<D, NJ>::TR;
   using T6 = typename BmgTiles<D, NJ>::T64;
+  using TA = typename BmgTiles<D, NJ>::TA;
   using Coef = typename BmgOps<D, NJ>::Coef;
   static constexpr int S = ST<D>::S, NIP = 32 * NJ;
   static constexpr int CH32 = NIP * 4 / 16, CH64 = NIP * 8 / 16;   // 16-byte chunks per row
@@ -276,8 +178,12 @@ struct BmgTiled {
   static constexpr size_t smem_restrict = 4 * ((size_t)NFR * NIP + 2 * (size_t)TR::NT) + TR::NT;
   static constexpr size_t smem_apply = 12 * (size_t)T6::NH * NIP + 16 * (size_t)S * T6::NT;
   static constexpr size_t smem_reduce = 8 * ((size_t)BMG_WARPS * 2 * NIP + 2 * NIP);
+  static constexpr size_t smem_apply32 = 8 * (size_t)TA::NH * NIP + 8 * (size_t)(S + 1) * TA::NT;
+  static constexpr size_t smem_resid64 = 8 * ((size_t)T6::NH * NIP + (size_t)T6::NT * NIP + 2 * (size_t)S * T6::NT);
   static constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
-  static constexpr size_t smem = (cmax(cmax(smem_stencil, smem_restrict), cmax(smem_apply, smem_reduce)) + 15) / 16 * 16;
+  static constexpr size_t smem =
+      (cmax(cmax(cmax(smem_stencil, smem_restrict), cmax(smem_apply, smem_reduce)), cmax(smem_apply32, smem_resid64)) +
+       15) / 16 * 16;
 
   // MODE 0: z_out = z_in + omega D^{-1} (b - A z_in).  MODE 1: the same after adding the
   // prolongated coarse correction P z_c to z_in on the fly (prolongation and first post-sweep
@@ -529,6 +435,162 @@ struct BmgTiled {
       }
     }
   }
+
+  // Inner CG of the refinement (FP32): q_new = z + beta q_old (on the halo in shared memory),
+  // s = A_i q_new with the level's FP32 difference-form rows; writes q_new and s of the own
+  // nodes; dot += (q_new, s) (FP32 over a warp's nodes of a tile, FP64 across tiles).
+  static __device__ void apply32_pass(const BmgLevel &L, const float *qold, const float *z, float *qnew, float *sout,
+                                      const float (&beta)[NJ], const Coef &cf, double (&dot)[NJ], unsigned char *smem,
+                                      int lane) {
+    const Grid &g = L.g;
+    const long long N = g.num_nodes;
+    float *sq = reinterpret_cast<float *>(smem);
+    float *szz = sq + TA::NH * NIP;
+    float *swK = szz + TA::NH * NIP;
+    float *swM = swK + (S + 1) * TA::NT;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const long long ntile = TA::count(g);
+    for (long long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+      int o[3];
+      TA::origin(g, tile, o);
+      __syncthreads();
+      for (int c = threadIdx.x; c < TA::NH * CH32; c += blockDim.x) {
+        const int h = c / CH32, k = c - h * CH32;
+        const long long nb = TA::halo_node(g, o, h);
+        const long long off = (nb < 0 ? 0 : nb * NIP) + 4 * k;
+        cp_async16(sq + h * NIP + 4 * k, qold + off, nb >= 0);
+        cp_async16(szz + h * NIP + 4 * k, z + off, nb >= 0);
+      }
+      for (int c = threadIdx.x; c < (S + 1) * TA::NT; c += blockDim.x) {
+        const int s = c / TA::NT, t = c - s * TA::NT;
+        int hs;
+        const long long a = TA::own_node(g, o, t, hs);
+        const long long off = a < 0 ? 0 : (long long)s * N + a;
+        cp_async4(swK + c, L.SK + off, a >= 0);
+        cp_async4(swM + c, L.SM + off, a >= 0);
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      for (int h = warp; h < TA::NH; h += nw)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const int q = h * NIP + lane + 32 * j;
+          sq[q] = fmaf(beta[j], sq[q], szz[q]);
+        }
+      __syncthreads();
+      float df[NJ];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) df[j] = 0.f;
+      for (int t = warp; t < TA::NT; t += nw) {
+        int hs;
+        const long long a = TA::own_node(g, o, t, hs);
+        if (a < 0) continue;
+        const float rk = swK[t], rm = swM[t];
+        float pa[NJ], y[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          pa[j] = sq[hs * NIP + lane + 32 * j];
+          y[j] = __fmul_rn(fmaf(cf.k[j], rk, __fmul_rn(cf.w[j], rm)), pa[j]);
+        }
+#pragma unroll
+        for (int s = 1; s < S; ++s) {
+          const float wk = swK[s * TA::NT + t], wm = swM[s * TA::NT + t];
+          if (wk == 0.f && wm == 0.f) continue;
+          const int hn = hs + TA::slot_shift(s);
+#pragma unroll
+          for (int j = 0; j < NJ; ++j)
+            y[j] = fmaf(fmaf(cf.k[j], wk, __fmul_rn(cf.w[j], wm)), __fsub_rn(sq[hn * NIP + lane + 32 * j], pa[j]), y[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const int i = lane + 32 * j;
+          qnew[a * NIP + i] = pa[j];
+          sout[a * NIP + i] = y[j];
+          df[j] = fmaf(pa[j], y[j], df[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) dot[j] += (double)df[j];
+    }
+  }
+
+  // r = bscale B - A_i X in FP64 from the plain node-major FP64 rows (X = 0 when !use_x);
+  // rr += ||r||^2, bb += ||bscale B||^2.
+  static __device__ void residual64_pass(const Grid &g, const double *WK, const double *WM, const double *X, bool use_x,
+                                         const double *B, double bscale, double *r64, const double (&kk)[NJ],
+                                         const double (&w2)[NJ], double (&rr)[NJ], double (&bb)[NJ],
+                                         unsigned char *smem, int lane) {
+    double *sx = reinterpret_cast<double *>(smem);
+    double *sB = sx + T6::NH * NIP;
+    double *swK = sB + T6::NT * NIP;
+    double *swM = swK + S * T6::NT;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const long long ntile = T6::count(g);
+    for (long long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+      int o[3];
+      T6::origin(g, tile, o);
+      __syncthreads();
+      if (use_x)
+        for (int c = threadIdx.x; c < T6::NH * CH64; c += blockDim.x) {
+          const int h = c / CH64, k = c - h * CH64;
+          const long long nb = T6::halo_node(g, o, h);
+          cp_async16(sx + h * NIP + 2 * k, X + (nb < 0 ? 0 : nb * NIP) + 2 * k, nb >= 0);
+        }
+      for (int c = threadIdx.x; c < T6::NT * CH64; c += blockDim.x) {
+        const int t = c / CH64, k = c - t * CH64;
+        int hs;
+        const long long a = T6::own_node(g, o, t, hs);
+        cp_async16(sB + t * NIP + 2 * k, B + (a < 0 ? 0 : a * NIP) + 2 * k, a >= 0);
+      }
+      if (use_x)
+        for (int c = threadIdx.x; c < S * T6::NT; c += blockDim.x) {
+          const int t = c / S, s = c - t * S;
+          int hs;
+          const long long a = T6::own_node(g, o, t, hs);
+          const long long off = a < 0 ? 0 : a * S + s;
+          cp_async8(swK + c, WK + off, a >= 0);
+          cp_async8(swM + c, WM + off, a >= 0);
+        }
+      cp_async_wait_all();
+      __syncthreads();
+      for (int t = warp; t < T6::NT; t += nw) {
+        int hs;
+        const long long a = T6::own_node(g, o, t, hs);
+        if (a < 0) continue;
+        double ax[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) ax[j] = 0.0;
+        if (use_x) {
+          double yk[NJ], ym[NJ];
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) yk[j] = ym[j] = 0.0;
+#pragma unroll
+          for (int s = 0; s < S; ++s) {
+            const double wk = swK[t * S + s], wm = swM[t * S + s];
+            if (s > 0 && wk == 0.0 && wm == 0.0) continue;
+            const int hn = hs + T6::slot_shift(s);
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+              const double xv = sx[hn * NIP + lane + 32 * j];
+              yk[j] = fma(wk, xv, yk[j]);
+              ym[j] = fma(wm, xv, ym[j]);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) ax[j] = fma(kk[j], yk[j], __dmul_rn(w2[j], ym[j]));
+        }
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const int i = lane + 32 * j;
+          const double bq = __dmul_rn(bscale, sB[t * NIP + i]);
+          const double r = __dsub_rn(bq, ax[j]);
+          r64[a * NIP + i] = r;
+          rr[j] = fma(r, r, rr[j]);
+          bb[j] = fma(bq, bq, bb[j]);
+        }
+      }
+    }
+  }
 };
 
 // Buffer index of each level's final iterate after a V-cycle (fixed by the sweep counts).
@@ -541,54 +603,161 @@ __host__ __device__ inline void bmg_final_buffers(int L, int nu, int nuc, int *z
   }
 }
 
-// Levels >= from in block 0 alone (block barriers), from b_from and z_from[0] (first sweep
-// taken).
-template <int D, int NJ>
-__device__ void bmg_block_cycle(const BmgDev &mg, const typename BmgOps<D, NJ>::Coef &cf, int from, int *zc,
-                                int lane) {
-  using O = BmgOps<D, NJ>;
-  const long long w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int l = from; l < mg.L; ++l) {
+// Levels >= from, one instance per block (instances blockIdx.x, blockIdx.x + G, ...): the
+// instance's vectors of these levels live in shared memory (b, z0, z1, t of every level), a
+// thread per node; the rows are read through L1.  Starts from b_from and z_from[0] in global
+// memory and writes level `from`'s final iterate back to z_from[zc[from]].
+template <int D>
+__device__ void bmg_inst_cycle(const BmgDev &mg, const double *kk, const double *w2, int nip, int from, float *sm) {
+  constexpr int S = ST<D>::S;
+  const float omega = mg.omega;
+  auto vec = [&](int l, int q) {   // q: 0 b, 1 z0, 2 z1, 3 t
+    long long off = 0;
+    for (int m = from; m < l; ++m) off += 4 * mg.lv[m].g.num_nodes;
+    return sm + off + q * mg.lv[l].g.num_nodes;
+  };
+  auto row = [&](int l, long long a, const float *z, float ki, float wi, float &za, float &az, float &dg) {
     const BmgLevel &L = mg.lv[l];
-    const int sweeps = (l == mg.L - 1) ? mg.nuc : mg.nu;
-    int c = 0;
-    for (int j = 1; j < sweeps; ++j) {
-      __syncthreads();
-      O::sweep(L, L.z[c], L.z[c ^ 1], mg.omega, cf, w, nw, lane);
-      c ^= 1;
+    const long long N = L.g.num_nodes;
+    int idx[3];
+    node_ijk(L.g, a, idx);
+    const float rk = L.SK[a], rm = L.SM[a], dk = L.SK[S * N + a], dm = L.SM[S * N + a];
+    za = z[a];
+    az = __fmul_rn(fmaf(ki, rk, __fmul_rn(wi, rm)), za);
+    dg = fmaf(ki, dk, __fmul_rn(wi, dm));
+#pragma unroll
+    for (int s = 1; s < S; ++s) {
+      const long long nb = slot_node<D>(L.g, idx, a, s);
+      if (nb < 0) continue;
+      const float wk = L.SK[s * N + a], wm = L.SM[s * N + a];
+      if (wk == 0.f && wm == 0.f) continue;
+      az = fmaf(fmaf(ki, wk, __fmul_rn(wi, wm)), __fsub_rn(z[nb], za), az);
     }
-    zc[l] = c;
-    if (l == mg.L - 1) break;
-    __syncthreads();
-    O::residual(L, L.z[c], cf, w, nw, lane);
-    __syncthreads();
-    O::restrict_(L, mg.lv[l + 1], mg.omega, cf, w, nw, lane);
-  }
-  for (int l = mg.L - 2; l >= from; --l) {
-    const BmgLevel &L = mg.lv[l];
-    __syncthreads();
-    O::prolong(L, L.z[zc[l]], mg.lv[l + 1], mg.lv[l + 1].z[zc[l + 1]], w, nw, lane);
-    int c = zc[l];
-    for (int j = 0; j < mg.nu; ++j) {
-      __syncthreads();
-      O::sweep(L, L.z[c], L.z[c ^ 1], mg.omega, cf, w, nw, lane);
-      c ^= 1;
+  };
+  const int NIP = nip;
+  for (int inst = blockIdx.x; inst < nip; inst += gridDim.x) {
+    const float ki = (float)kk[inst], wi = (float)w2[inst];
+    __syncthreads();   // shared memory free
+    {
+      const BmgLevel &L = mg.lv[from];
+      float *b = vec(from, 0), *z0 = vec(from, 1);
+      for (long long a = threadIdx.x; a < L.g.num_nodes; a += blockDim.x) {
+        b[a] = L.b[a * NIP + inst];
+        z0[a] = L.z[0][a * NIP + inst];
+      }
     }
-    zc[l] = c;
+    int zl[MG_MAX_LEVELS];
+    for (int l = from; l < mg.L; ++l) {
+      const long long N = mg.lv[l].g.num_nodes;
+      const bool coarsest = l == mg.L - 1;
+      const int sweeps = coarsest ? mg.nuc : mg.nu;
+      float *b = vec(l, 0);
+      int c = 0;
+      for (int j = 1; j < sweeps; ++j) {
+        __syncthreads();
+        const float *zi = vec(l, 1 + c);
+        float *zo = vec(l, 2 - c);
+        for (long long a = threadIdx.x; a < N; a += blockDim.x) {
+          float za, az, dg;
+          row(l, a, zi, ki, wi, za, az, dg);
+          zo[a] = __fadd_rn(za, __fdiv_rn(__fmul_rn(omega, __fsub_rn(b[a], az)), dg));
+        }
+        c ^= 1;
+      }
+      zl[l] = c;
+      if (coarsest) break;
+      __syncthreads();
+      {
+        const float *zi = vec(l, 1 + c);
+        float *t = vec(l, 3);
+        for (long long a = threadIdx.x; a < N; a += blockDim.x) {
+          float za, az, dg;
+          row(l, a, zi, ki, wi, za, az, dg);
+          t[a] = __fsub_rn(b[a], az);
+        }
+      }
+      __syncthreads();
+      {   // restriction to level l + 1 and its first sweep from zero
+        const BmgLevel &F = mg.lv[l], &Cl = mg.lv[l + 1];
+        const long long Nc = Cl.g.num_nodes;
+        const float *t = vec(l, 3);
+        float *bc = vec(l + 1, 0), *zc0 = vec(l + 1, 1);
+        for (long long cn = threadIdx.x; cn < Nc; cn += blockDim.x) {
+          int ic[3];
+          node_ijk(Cl.g, cn, ic);
+          int ifn[3] = {2 * ic[0], 2 * ic[1], D == 3 ? 2 * ic[2] : 0};
+          const long long f0 = ifn[0] + F.g.stride[1] * ifn[1] + (D == 3 ? F.g.stride[2] * ifn[2] : 0);
+          float v = t[f0];
+#pragma unroll
+          for (int s = 1; s < S; ++s) {
+            const long long nb = slot_node<D>(F.g, ifn, f0, s);
+            if (nb >= 0) v = fmaf(0.5f, t[nb], v);
+          }
+          const float bk = Cl.dir[cn] ? 0.f : v;
+          bc[cn] = bk;
+          zc0[cn] = __fdiv_rn(__fmul_rn(omega, bk), fmaf(ki, Cl.SK[S * Nc + cn], __fmul_rn(wi, Cl.SM[S * Nc + cn])));
+        }
+      }
+    }
+    for (int l = mg.L - 2; l >= from; --l) {
+      const BmgLevel &F = mg.lv[l], &Cl = mg.lv[l + 1];
+      const long long N = F.g.num_nodes;
+      __syncthreads();
+      {   // z_l += P z_{l+1}
+        float *zf = vec(l, 1 + zl[l]);
+        const float *zcv = vec(l + 1, 1 + zl[l + 1]);
+        for (long long a = threadIdx.x; a < N; a += blockDim.x) {
+          if (F.dir[a]) continue;
+          int idx[3];
+          node_ijk(F.g, a, idx);
+          long long c1 = 0, c2 = 0;
+          bool mid = false;
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const int bit = idx[k] & 1;
+            mid |= bit != 0;
+            c1 += (long long)((idx[k] - bit) / 2) * Cl.g.stride[k];
+            c2 += (long long)((idx[k] + bit) / 2) * Cl.g.stride[k];
+          }
+          const float v = mid ? __fmul_rn(0.5f, __fadd_rn(zcv[c1], zcv[c2])) : zcv[c1];
+          zf[a] = __fadd_rn(zf[a], v);
+        }
+      }
+      int c = zl[l];
+      float *b = vec(l, 0);
+      for (int j = 0; j < mg.nu; ++j) {
+        __syncthreads();
+        const float *zi = vec(l, 1 + c);
+        float *zo = vec(l, 2 - c);
+        for (long long a = threadIdx.x; a < N; a += blockDim.x) {
+          float za, az, dg;
+          row(l, a, zi, ki, wi, za, az, dg);
+          zo[a] = __fadd_rn(za, __fdiv_rn(__fmul_rn(omega, __fsub_rn(b[a], az)), dg));
+        }
+        c ^= 1;
+      }
+      zl[l] = c;
+    }
+    __syncthreads();
+    {
+      const BmgLevel &L = mg.lv[from];
+      const float *zf = vec(from, 1 + zl[from]);
+      float *dst = L.z[zl[from]];
+      for (long long a = threadIdx.x; a < L.g.num_nodes; a += blockDim.x) dst[a * NIP + inst] = zf[a];
+    }
   }
-  __syncthreads();
 }
 
 // One V-cycle from level 0, whose b and first sweep were written before a grid barrier.
 // Level 0's result ends in z[zc[0]], written by the warp that owns each node's tile slot (no
 // barrier after the last sweep: the caller's next pass reads it only after one).
 template <int D, int NJ>
-__device__ bool bmg_vcycle(const BmgDev &mg, const typename BmgOps<D, NJ>::Coef &cf, int *zc, const GridBar &bar,
-                           unsigned char *smem, int lane) {
+__device__ bool bmg_vcycle(const BmgDev &mg, const typename BmgOps<D, NJ>::Coef &cf, const double *kk,
+                           const double *w2, int *zc, const GridBar &bar, unsigned char *smem, int lane) {
   using TP = BmgTiled<D, NJ>;
   const int Lg = mg.Lg;
   if (Lg == 0) {
-    if (blockIdx.x == 0) bmg_block_cycle<D, NJ>(mg, cf, 0, zc, lane);
+    bmg_inst_cycle<D>(mg, kk, w2, 32 * NJ, 0, reinterpret_cast<float *>(smem));
     return grid_sync(bar);
   }
   for (int l = 0; l < Lg; ++l) {
@@ -609,7 +778,7 @@ __device__ bool bmg_vcycle(const BmgDev &mg, const typename BmgOps<D, NJ>::Coef 
     if (!grid_sync(bar)) return false;
   }
   if (Lg < mg.L) {
-    if (blockIdx.x == 0) bmg_block_cycle<D, NJ>(mg, cf, Lg, zc, lane);
+    bmg_inst_cycle<D>(mg, kk, w2, 32 * NJ, Lg, reinterpret_cast<float *>(smem));
     if (!grid_sync(bar)) return false;
   }
   for (int l = (Lg < mg.L - 1 ? Lg : mg.L - 1) - 1; l >= 0; --l) {
@@ -767,7 +936,7 @@ __global__ void __launch_bounds__(32 * BMG_WARPS, 2) k_bmg_pcg(const BmgDev *mgp
     for (int j = 0; j < NJ; ++j) all = all && done[j];
     all = __all_sync(0xffffffffu, all);
     if (all || it >= C.maxit) break;
-    if (!bmg_vcycle<D, NJ>(mg, cf, zc, C.bar, bmg_smem, lane)) return;
+    if (!bmg_vcycle<D, NJ>(mg, cf, C.kk, C.w2, zc, C.bar, bmg_smem, lane)) return;
     const float *z = L0.z[zfin];
     // gamma = (r, z), in the tile order of the last sweep (each z read by the thread that
     // wrote it: no barrier needed), four nodes at a time
@@ -901,6 +1070,279 @@ __global__ void __launch_bounds__(32 * BMG_WARPS, 2) k_bmg_pcg(const BmgDev *mgp
   }
 }
 
+// Mixed precision: FP64 iterative refinement around an FP32 conjugate-gradient solve, the
+// same V-cycle as preconditioner.  Each refinement step forms the true residual
+// r = b - A x in FP64, hands r / ||r|| (per instance) to the FP32 CG, which runs until its
+// recursive residual is below inner_rtol (or inner_maxit), and adds ||r|| d to x in FP64.
+// Only the residual pass and the update of x use FP64 arithmetic; an iteration of the inner
+// CG moves FP32 vectors only.  An instance stops when its true residual meets rtol, or when a
+// refinement step fails to halve it (the residual has reached the rounding floor of its FP64
+// evaluation; the solve then reports non-convergence with the residual reached).
+template <int D, int NJ>
+__global__ void __launch_bounds__(32 * BMG_WARPS, 2) k_bmg_ir(const BmgDev *mgp, BmgCg C) {
+  constexpr int S = ST<D>::S, NIP = 32 * NJ;
+  using O = BmgOps<D, NJ>;
+  using TP = BmgTiled<D, NJ>;
+  extern __shared__ __align__(16) unsigned char bmg_smem[];
+  __shared__ BmgDev mg;
+  double *part = reinterpret_cast<double *>(bmg_smem);
+  double *tot = part + BMG_WARPS * 2 * NIP;
+  {
+    const int *src = reinterpret_cast<const int *>(mgp);
+    int *dst = reinterpret_cast<int *>(&mg);
+    for (int i = threadIdx.x; i < (int)(sizeof(BmgDev) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const long long first = blockIdx.x * (long long)nw + warp, step = (long long)gridDim.x * nw;
+  const BmgLevel &L0 = mg.lv[0];
+  const Grid &g = L0.g;
+  const long long N = g.num_nodes;
+  double kk[NJ], w2[NJ];
+  typename O::Coef cf;
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    kk[j] = C.kk[lane + 32 * j];
+    w2[j] = C.w2[lane + 32 * j];
+    cf.k[j] = (float)kk[j];
+    cf.w[j] = (float)w2[j];
+  }
+  int zc[MG_MAX_LEVELS];
+  bmg_final_buffers(mg.L, mg.nu, mg.nuc, zc);
+  const int zfin = zc[0];
+  const float omega = mg.omega;
+  float *r32 = L0.b;   // the inner residual is the V-cycle's level-0 right-hand side
+
+  double bb[NJ], rr[NJ];
+  int its[NJ];
+  bool nan_seen = false;
+  {
+    double v[2][NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) v[0][j] = v[1][j] = 0.0;
+    TP::residual64_pass(g, C.WK, C.WM, C.X, C.warm != 0, C.B, C.bscale, C.r, kk, w2, v[1], v[0], bmg_smem, lane);
+    if (!C.warm)
+      for (long long a = first; a < N; a += step)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) C.X[a * NIP + lane + 32 * j] = 0.0;
+    if (!bmg_allreduce<2, NJ>(C, v, part, tot)) return;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      bb[j] = tot[lane + 32 * j];
+      rr[j] = tot[NIP + lane + 32 * j];
+      its[j] = 0;
+    }
+  }
+  int total = 0, outer = 0;
+  bool stalled[NJ];
+  double rr_prev[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    stalled[j] = false;
+    rr_prev[j] = INFINITY;
+  }
+  for (;;) {
+    bool act[NJ], any = false;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      if (rr[j] != rr[j]) nan_seen = true;
+      // a step that did not halve the true residual has reached the FP64 floor of b - A x
+      if (rr[j] > 0.25 * rr_prev[j]) stalled[j] = true;
+      act[j] = !stalled[j] && rr[j] == rr[j] && rr[j] > C.rtol2 * bb[j];
+      any = any || act[j];
+    }
+    if (!__any_sync(0xffffffffu, any) || total >= C.maxit) break;
+    double scale[NJ];
+    float inv[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      scale[j] = act[j] ? sqrt(rr[j]) : 0.0;
+      inv[j] = act[j] ? (float)(1.0 / scale[j]) : 0.f;
+    }
+    // inner start: r32 = r / ||r||, d = 0, q = 0, level-0 first sweep
+    for (long long a = first; a < N; a += step) {
+      const float dk = L0.SK[S * N + a], dm = L0.SM[S * N + a];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const long long q = a * NIP + lane + 32 * j;
+        const float rf = __fmul_rn((float)C.r[q], inv[j]);
+        r32[q] = rf;
+        L0.z[0][q] = __fdiv_rn(__fmul_rn(omega, rf), fmaf(cf.k[j], dk, __fmul_rn(cf.w[j], dm)));
+        C.d64[q] = 0.0;
+        C.q32[0][q] = 0.f;
+      }
+    }
+    if (!grid_sync(C.bar)) return;
+    bool idone[NJ];
+    double gam[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      idone[j] = !act[j];
+      gam[j] = 0.0;
+    }
+    int cur = 0;
+    for (int ii = 0;; ++ii) {
+      bool all = true;
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) all = all && idone[j];
+      if (__all_sync(0xffffffffu, all) || ii >= C.inner_maxit || total >= C.maxit) break;
+      if (!bmg_vcycle<D, NJ>(mg, cf, C.kk, C.w2, zc, C.bar, bmg_smem, lane)) return;
+      const float *z = L0.z[zfin];
+      // gamma = (r32, z) in the tile order of the last sweep (own values, no barrier needed)
+      double v1[1][NJ];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) v1[0][j] = 0.0;
+      {
+        using TL = typename TP::TL;
+        const long long ntile = TL::count(g);
+        for (long long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+          int o[3];
+          TL::origin(g, tile, o);
+          float df[NJ];
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) df[j] = 0.f;
+          for (int t0 = warp; t0 < TL::NT; t0 += 4 * nw) {
+            float rv[4][NJ], zv[4][NJ];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              int hs;
+              const int t = t0 + u * nw;
+              const long long a = t < TL::NT ? TL::own_node(g, o, t, hs) : -1;
+#pragma unroll
+              for (int j = 0; j < NJ; ++j) {
+                const long long q = (a < 0 ? 0 : a) * NIP + lane + 32 * j;
+                rv[u][j] = a < 0 ? 0.f : r32[q];
+                zv[u][j] = a < 0 ? 0.f : z[q];
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int j = 0; j < NJ; ++j) df[j] = fmaf(rv[u][j], zv[u][j], df[j]);
+          }
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) v1[0][j] += (double)df[j];
+        }
+      }
+      if (!bmg_allreduce<1, NJ>(C, v1, part, tot)) return;
+      float beta[NJ];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const double gn = tot[lane + 32 * j];
+        beta[j] = (ii > 0 && gam[j] > 0.0) ? (float)(gn / gam[j]) : 0.f;
+        gam[j] = gn;
+      }
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) v1[0][j] = 0.0;
+      TP::apply32_pass(L0, C.q32[cur], z, C.q32[cur ^ 1], C.s32, beta, cf, v1[0], bmg_smem, lane);
+      cur ^= 1;
+      if (!bmg_allreduce<1, NJ>(C, v1, part, tot)) return;
+      float alpha[NJ];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const double sig = tot[lane + 32 * j];
+        alpha[j] = 0.f;
+        if (!idone[j]) {
+          if (sig > 0.0 && gam[j] > 0.0) alpha[j] = (float)(gam[j] / sig);
+          else idone[j] = true;
+        }
+      }
+      // d += alpha q; r32 -= alpha s; level-0 first sweep; ||r32||^2
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) v1[0][j] = 0.0;
+      const float *qc = C.q32[cur];
+      for (long long a0 = first; a0 < N; a0 += 4 * step) {
+        double dv[4][NJ];
+        float pv[4][NJ], rv[4][NJ], sv[4][NJ], dk[4], dm[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const long long a = a0 + u * step, ac = a < N ? a : 0;
+          dk[u] = L0.SK[S * N + ac];
+          dm[u] = L0.SM[S * N + ac];
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) {
+            const long long q = ac * NIP + lane + 32 * j;
+            dv[u][j] = C.d64[q];
+            pv[u][j] = qc[q];
+            rv[u][j] = r32[q];
+            sv[u][j] = C.s32[q];
+          }
+        }
+        float rf[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) rf[j] = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const long long a = a0 + u * step;
+          if (a >= N) continue;
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) {
+            const long long q = a * NIP + lane + 32 * j;
+            C.d64[q] = fma((double)alpha[j], (double)pv[u][j], dv[u][j]);
+            const float r1 = fmaf(-alpha[j], sv[u][j], rv[u][j]);
+            r32[q] = r1;
+            L0.z[0][q] = __fdiv_rn(__fmul_rn(omega, r1), fmaf(cf.k[j], dk[u], __fmul_rn(cf.w[j], dm[u])));
+            rf[j] = fmaf(r1, r1, rf[j]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) v1[0][j] += (double)rf[j];
+      }
+      if (!bmg_allreduce<1, NJ>(C, v1, part, tot)) return;
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        if (idone[j]) continue;
+        its[j] += 1;
+        const double r2 = tot[lane + 32 * j];
+        if (!(r2 > C.inner_rtol2)) idone[j] = true;   // met, or NaN (caught by the FP64 residual)
+      }
+      ++total;
+    }
+    // x += ||r|| d (FP64), then the true residual
+    for (long long a = first; a < N; a += step)
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const long long q = a * NIP + lane + 32 * j;
+        C.X[q] = fma(scale[j], C.d64[q], C.X[q]);
+      }
+    if (!grid_sync(C.bar)) return;
+    double v[2][NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) v[0][j] = v[1][j] = 0.0;
+    TP::residual64_pass(g, C.WK, C.WM, C.X, true, C.B, C.bscale, C.r, kk, w2, v[1], v[0], bmg_smem, lane);
+    if (!bmg_allreduce<2, NJ>(C, v, part, tot)) return;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      if (act[j]) rr_prev[j] = rr[j];
+      rr[j] = tot[NIP + lane + 32 * j];
+    }
+    ++outer;
+  }
+  bool conv = true;
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    conv = conv && rr[j] <= C.rtol2 * bb[j];
+    nan_seen = nan_seen || rr[j] != rr[j];
+  }
+  conv = __all_sync(0xffffffffu, conv);
+  nan_seen = __any_sync(0xffffffffu, nan_seen);
+  if (blockIdx.x == 0 && warp == 0) {
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const int i = lane + 32 * j;
+      C.inst_iters[i] = its[j];
+      C.inst_res[i] = bb[j] > 0.0 ? sqrt(rr[j] / bb[j]) : sqrt(rr[j]);
+    }
+    if (lane == 0) {
+      C.status[DS_ITERS] = total;
+      C.status[DS_APPLIES] = total + outer + 1;
+      C.status[DS_FLAG] = outer;
+      if (nan_seen) atomicCAS(C.status + DS_ERR, DEV_OK, DEV_NAN);
+      else if (!conv) atomicCAS(C.status + DS_ERR, DEV_OK, DEV_NOCONV);
+    }
+  }
+}
+
 // Difference-form FP32 rows (slot-major, slot S the diagonal) from plain node-major FP64 rows
 // whose Dirichlet columns are already zero.
 __global__ void k_bmg_rows(long long N, int S, const double *WK, const double *WM, float *SK, float *SM) {
@@ -931,6 +1373,8 @@ struct fo_bmg {
   float *SK[MG_MAX_LEVELS] = {}, *SM[MG_MAX_LEVELS] = {};
   float *b[MG_MAX_LEVELS] = {}, *z0[MG_MAX_LEVELS] = {}, *z1[MG_MAX_LEVELS] = {}, *t[MG_MAX_LEVELS] = {};
   double *r = nullptr, *p0 = nullptr, *p1 = nullptr, *s = nullptr, *partials = nullptr;
+  double *d64 = nullptr;
+  float *q0 = nullptr, *q1 = nullptr, *s32 = nullptr;
   void *dev = nullptr;
   std::vector<unsigned char> host;
   std::vector<std::pair<void **, size_t>> allocs;
@@ -949,15 +1393,17 @@ struct BmgKernel {
   size_t smem = 0;
 };
 template <int D, int NJ>
-static BmgKernel bmg_entry() {
+static BmgKernel bmg_entry(bool mixed) {
   BmgKernel k;
-  k.fn = k_bmg_pcg<D, NJ>;
+  k.fn = mixed ? k_bmg_ir<D, NJ> : k_bmg_pcg<D, NJ>;
   k.smem = BmgTiled<D, NJ>::smem;
   return k;
 }
-static BmgKernel bmg_kernel(int dim, int nj) {
-  if (dim == 2) return nj == 1 ? bmg_entry<2, 1>() : (nj == 2 ? bmg_entry<2, 2>() : bmg_entry<2, 4>());
-  return nj == 1 ? bmg_entry<3, 1>() : (nj == 2 ? bmg_entry<3, 2>() : bmg_entry<3, 4>());
+// FP64 CG (mixed = false) or FP64 refinement around an FP32 CG (mixed = true)
+static BmgKernel bmg_kernel(int dim, int nj, bool mixed) {
+  if (dim == 2)
+    return nj == 1 ? bmg_entry<2, 1>(mixed) : (nj == 2 ? bmg_entry<2, 2>(mixed) : bmg_entry<2, 4>(mixed));
+  return nj == 1 ? bmg_entry<3, 1>(mixed) : (nj == 2 ? bmg_entry<3, 2>(mixed) : bmg_entry<3, 4>(mixed));
 }
 
 static fo_status bmg_alloc(fo_problem *p) {
@@ -969,10 +1415,14 @@ static fo_status bmg_alloc(fo_problem *p) {
   mg->L = fo_mg_plan(p->mesh->g, mg->g, MG_MAX_LEVELS);
   const int S = p->mesh->g.dim == 2 ? 7 : 15;
   const size_t nip = (size_t)bt->nip;
-  int per_sm = 0;
-  const BmgKernel k = bmg_kernel(p->mesh->g.dim, bt->nip / 32);
-  FO_CU(ctx, cudaFuncSetAttribute((const void *)k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
-  FO_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k.fn, 32 * BMG_WARPS, k.smem));
+  int per_sm = 1 << 30;
+  for (int mixed = 0; mixed < 2; ++mixed) {   // one grid that both solvers can hold co-resident
+    const BmgKernel k = bmg_kernel(p->mesh->g.dim, bt->nip / 32, mixed != 0);
+    int v = 0;
+    FO_CU(ctx, cudaFuncSetAttribute((const void *)k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
+    FO_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, (const void *)k.fn, 32 * BMG_WARPS, k.smem));
+    per_sm = std::min(per_sm, v);
+  }
   if (per_sm < 1) return fo_fail(ctx, FO_ECUDA, "batched multigrid kernel does not fit on an SM");
   mg->grid_cap = std::min(per_sm * ctx->num_sms, 4096);
   auto add = [&](void **ptr, size_t bytes) { mg->allocs.push_back({ptr, bytes}); };
@@ -995,6 +1445,10 @@ static fo_status bmg_alloc(fo_problem *p) {
   add((void **)&mg->r, sizeof(double) * n0);
   add((void **)&mg->p0, sizeof(double) * n0);
   add((void **)&mg->p1, sizeof(double) * n0);
+  add((void **)&mg->d64, sizeof(double) * n0);
+  add((void **)&mg->q0, sizeof(float) * n0);
+  add((void **)&mg->q1, sizeof(float) * n0);
+  add((void **)&mg->s32, sizeof(float) * n0);
   add((void **)&mg->s, sizeof(double) * n0);
   add((void **)&mg->partials, sizeof(double) * (2 * nip * (size_t)mg->grid_cap + 2 * nip));
   add(&mg->dev, sizeof(BmgDev));
@@ -1028,12 +1482,20 @@ static fo_status bmg_prepare(fo_problem *p) {
   BmgDev h;
   memset(&h, 0, sizeof h);
   h.L = mg->L;
+  // levels from Lg down run one instance per block in shared memory: small enough, and their
+  // vectors (b, z0, z1, t of every such level) fit in the kernel's dynamic shared memory
   h.Lg = mg->L;
-  for (int l = 0; l < mg->L; ++l)
-    if (mg->g[l].num_nodes <= BMG_BLOCK_NODES) {
-      h.Lg = l;
-      break;
+  {
+    const size_t cap = bmg_kernel(mg->g[0].dim, bt->nip / 32, false).smem;
+    for (int l = 0; l < mg->L; ++l) {
+      size_t need = 0;
+      for (int m = l; m < mg->L; ++m) need += 16 * (size_t)mg->g[m].num_nodes;
+      if (mg->g[l].num_nodes <= BMG_INST_NODES && need <= cap) {
+        h.Lg = l;
+        break;
+      }
     }
+  }
   h.nu = 2;
   h.nuc = 16;
   h.omega = 0.8f;
@@ -1089,11 +1551,17 @@ fo_status fo_batch_state_mg(fo_problem *p, const double *B, double bscale, doubl
   C.rtol2 = o->rtol * o->rtol;
   C.maxit = o->maxit;
   C.warm = warm;
+  C.d64 = mg->d64;
+  C.q32[0] = mg->q0;
+  C.q32[1] = mg->q1;
+  C.s32 = mg->s32;
+  C.inner_rtol2 = o->inner_rtol * o->inner_rtol;
+  C.inner_maxit = std::max(o->inner_maxit, 1);
   const BmgDev *dev = (const BmgDev *)mg->dev;
   FO_CU(ctx, cudaMemsetAsync(p->bar, 0, 64, ctx->stream));
   FO_CU(ctx, cudaMemsetAsync(p->dev_status, 0, sizeof(int) * DS_COUNT, ctx->stream));
   void *argv[] = {(void *)&dev, (void *)&C};
-  const BmgKernel k = bmg_kernel(g.dim, nip / 32);
+  const BmgKernel k = bmg_kernel(g.dim, nip / 32, o->precision == FO_MIXED);
   FO_CU(ctx, cudaFuncSetAttribute((const void *)k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
   FO_CU(ctx, cudaLaunchCooperativeKernel((const void *)k.fn, (int)grid, 32 * BMG_WARPS, argv, k.smem, ctx->stream));
   fo_note_launch(1);

@@ -137,37 +137,47 @@ def test_batch_instance_equals_alone(ctx, precision):
 
 
 @pytest.mark.parametrize("name", list(MG_CASES) + ["2d_5"])
-def test_batch_state_multigrid_parity(ctx, name):
-    """Batched FP64 CG with a per-instance FP32 V-cycle: every instance meets the oracle's
-    solution, in few iterations; the explicit adjoint is -u."""
+@pytest.mark.parametrize("precision", [api.FO_FP64, api.FO_MIXED])
+def test_batch_state_multigrid_parity(ctx, name, precision):
+    """Batched CG with a per-instance FP32 V-cycle -- FP64 CG, or FP64 refinement around an
+    FP32 CG: every instance meets the oracle's solution, in few iterations; the explicit
+    adjoint is -u."""
     c, ob, prob, phi = _setup(ctx, name)
     U_ref, A, chi = ob.state(phi)
-    opts = api.solve_opts(rtol=1e-12, precond=api.FO_PC_MG)
+    # the refinement stops on the true FP64 residual, whose rounding floor on these
+    # ill-conditioned (ersatz 1e-3) instances is near 1e-12: ask for 1e-10 there
+    rtol = 1e-12 if precision == api.FO_FP64 else 1e-10
+    opts = api.solve_opts(precision=precision, rtol=rtol, precond=api.FO_PC_MG)
     st = prob.state_solve(opts)
     U = prob.get(FO_FIELD_U)
     its, res = prob.batch_solve_info()
-    assert np.all(res <= 1e-12), res
-    assert 0 < st.iterations <= 100 and np.all(its <= st.iterations), its
+    assert np.all(res <= rtol), res
+    cap = 100 if precision == api.FO_FP64 else 250
+    assert 0 < st.iterations <= cap and np.all(its <= st.iterations), its
+    if precision == api.FO_MIXED:
+        assert 2 <= st.outer_iterations <= 8, st.outer_iterations
     F = ob.loads()
     free = ob.problem(0).dirichlet() == 0
     for i in range(c["n_inst"]):
-        assert_solve_parity(_K(ob, i, A), F[:, i], free, U[:, i], U_ref[:, i], 1e-10, omega_max=1e-10)
+        assert_solve_parity(_K(ob, i, A), F[:, i], free, U[:, i], U_ref[:, i], 1e2 * rtol, omega_max=10 * rtol)
     assert np.all(U[~free] == 0.0)
     prob.adjoint_solve(opts)
-    assert rel(prob.get(FO_FIELD_P), -U) <= 1e-10
+    assert rel(prob.get(FO_FIELD_P), -U) <= 1e2 * rtol
     # the Jacobi-preconditioned batch reaches the same solution
     prob.state_solve(api.solve_opts(rtol=1e-12))
-    assert rel(prob.get(FO_FIELD_U), U) <= 1e-10
+    assert rel(prob.get(FO_FIELD_U), U) <= 1e2 * rtol
 
 
-def test_batch_multigrid_instance_equals_alone(ctx):
+@pytest.mark.parametrize("precision", [api.FO_FP64, api.FO_MIXED])
+def test_batch_multigrid_instance_equals_alone(ctx, precision):
     """An instance's multigrid-preconditioned solve in the batch and alone give the same bits."""
     c = batch_case(**MG_CASES["2d_mg_40"])
     mesh, prob = gpu_batch(ctx, c)
     _, coords = mesh.copy_out()
     phi = workloads.phi_cos(coords)
     prob.set_levelset(phi)
-    opts = api.solve_opts(rtol=1e-12, grid_blocks=64, precond=api.FO_PC_MG)
+    opts = api.solve_opts(precision=precision, rtol=1e-12 if precision == api.FO_FP64 else 1e-10, grid_blocks=64,
+                          precond=api.FO_PC_MG)
     prob.state_solve(opts)
     U = prob.get(FO_FIELD_U)
     its, _ = prob.batch_solve_info()
