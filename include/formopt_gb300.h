@@ -289,6 +289,14 @@ FO_API fo_status fo_apply(fo_problem *prob, int op, const double *x, double *y, 
 FO_API fo_status fo_state_solve_noalloc(fo_problem *prob, const double *b, double *x, const fo_solve_opts *o,
                                         fo_solve_stats *stats);
 
+/* Self-test of the bounded grid barrier that every persistent solver uses (no counterpart in
+ * the paper).  Launches `blocks` co-resident blocks (clamped to [2, number of SMs]) that meet
+ * at one grid barrier with a wait limit of limit_ms; block `skip` (or none when skip < 0)
+ * never arrives.  With skip < 0 the barrier is released: FO_OK, *gave_up = 0.  Otherwise
+ * every other block gives up after limit_ms: FO_ETIMEOUT, *gave_up = blocks - 1.  No block
+ * faults or hangs; the context stays usable.  limit_ms must be in (0, 10000]. */
+FO_API fo_status fo_selftest_barrier(fo_ctx *ctx, int blocks, int skip, double limit_ms, int *gave_up);
+
 /* ------------------------------------------------------------ batch (TP) ----- */
 /* A batch problem (fo_model_desc.n_inst >= 1) goes through the same calls as a single
  * problem: fo_coefficients, fo_state_solve / fo_adjoint_solve (all instances in one

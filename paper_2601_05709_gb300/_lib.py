@@ -129,6 +129,7 @@ PROTOTYPES = {
     "fo_coefficients": (ST, [VP]),
     "fo_state_solve": (ST, [VP, C.POINTER(SolveOpts), C.POINTER(SolveStats)]),
     "fo_state_solve_noalloc": (ST, [VP, VP, VP, C.POINTER(SolveOpts), C.POINTER(SolveStats)]),
+    "fo_selftest_barrier": (ST, [VP, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_int)]),
     "fo_adjoint_solve": (ST, [VP, C.POINTER(SolveOpts), C.POINTER(SolveStats)]),
     "fo_functionals": (ST, [VP, DP, DP]),
     "fo_shape_derivative": (ST, [VP, C.c_double, VP]),

@@ -137,6 +137,12 @@ class Context:
     def set_timing(self, on=True):
         self.check(self.lib.fo_ctx_set_timing(self.handle, int(bool(on))), "fo_ctx_set_timing")
 
+    def selftest_barrier(self, blocks, skip, limit_ms):
+        """(status, blocks that gave up) of the bounded grid barrier with block `skip` absent."""
+        g = C.c_int(0)
+        st = self.lib.fo_selftest_barrier(self.handle, int(blocks), int(skip), float(limit_ms), C.byref(g))
+        return st, g.value
+
     def mesh_box(self, dim, n, lo, hi):
         return Mesh(self, dim, n, lo, hi)
 

@@ -100,6 +100,39 @@ extern "C" fo_status fo_ctx_destroy(fo_ctx *ctx) {
   return FO_OK;
 }
 
+// One grid barrier; block `skip` never arrives, so the others run out their wait limit.
+__global__ void k_barrier_selftest(GridBar bar, int skip, int *gave_up) {
+  if ((int)blockIdx.x == skip) return;
+  const bool ok = grid_sync(bar);
+  if (threadIdx.x == 0 && !ok) atomicAdd(gave_up, 1);
+}
+
+extern "C" fo_status fo_selftest_barrier(fo_ctx *ctx, int blocks, int skip, double limit_ms, int *gave_up) {
+  if (!ctx || !gave_up || !(limit_ms > 0.0 && limit_ms <= 10000.0)) return FO_EINVAL;
+  const int G = std::max(2, std::min(blocks, ctx->num_sms));
+  if (skip >= G) return fo_fail(ctx, FO_EINVAL, "skip must be < the number of blocks (%d)", G);
+  int *words;   // [0] barrier counter, [1] error word, [2] blocks that gave up
+  FO_TRY(fo_alloc(ctx, (void **)&words, 64));
+  fo_status st = FO_OK;
+  int h[3] = {0, 0, 0};
+  if (cudaMemsetAsync(words, 0, 64, ctx->stream) != cudaSuccess) st = fo_fail(ctx, FO_ECUDA, "memset");
+  if (st == FO_OK) {
+    GridBar bar{reinterpret_cast<unsigned *>(words), words + 1, (unsigned long long)(limit_ms * 1e6)};
+    int *out = words + 2;
+    void *argv[] = {(void *)&bar, (void *)&skip, (void *)&out};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_barrier_selftest, G, 32, argv, 0, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, words, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) st = fo_cuda_check(ctx, e, "barrier self-test");
+    fo_note_launch(1);
+  }
+  fo_free(ctx, words, 64);
+  if (st != FO_OK) return st;
+  *gave_up = h[2];
+  if (h[1] == DEV_TIMEOUT) return fo_fail(ctx, FO_ETIMEOUT, "grid barrier gave up after %.1f ms", limit_ms);
+  return FO_OK;
+}
+
 extern "C" fo_status fo_ctx_set_timing(fo_ctx *ctx, int on) {
   if (!ctx) return FO_EINVAL;
   if (on && !ctx->ev[0])

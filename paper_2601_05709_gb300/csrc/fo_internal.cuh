@@ -244,7 +244,10 @@ __device__ __forceinline__ void slot_offset(int s, int delta[3]) {
 // One counter; block 0 adds 2^31 - (G - 1), every other block adds 1, so the top bit flips
 // exactly when all G blocks have arrived.  The counter must hold 0 at launch and the grid
 // must be co-resident (cooperative launch).  A wait longer than `limit_ns` sets the error
-// word to DEV_TIMEOUT and every block returns false from that barrier on.
+// word to DEV_TIMEOUT and returns false.  The error word is read only by a block that is
+// already waiting long (after 1024 polls), so a released barrier costs no extra round trip:
+// a block that timed out stops arriving, and every other block then leaves its next wait
+// early through the error word, or by its own time limit.
 __device__ __forceinline__ unsigned fo_ld_acquire(const unsigned *p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -282,6 +285,10 @@ __device__ __forceinline__ bool grid_sync(const GridBar &b) {
       if (++spins == 1024) t0 = fo_globaltimer();
       if (spins > 1024 && (spins & 255) == 0) {
         __nanosleep(64);
+        if (*(volatile int *)b.err == DEV_TIMEOUT) {   // another block gave up
+          ok = 0;
+          break;
+        }
         if (fo_globaltimer() - t0 > b.limit_ns) {
           atomicExch(b.err, DEV_TIMEOUT);
           ok = 0;
@@ -290,7 +297,6 @@ __device__ __forceinline__ bool grid_sync(const GridBar &b) {
       }
     }
     __threadfence();                               // other blocks' writes after the release
-    if (ok && *(volatile int *)b.err == DEV_TIMEOUT) ok = 0;
     s_ok = ok;
   }
   __syncthreads();
