@@ -25,6 +25,7 @@
 #include "fo_ops.cuh"
 
 #define MG_BLOCK_DOFS 2048
+#define MG_STAGE_MAX_BYTES (180 * 1024)   // shared memory block 0 may take for its levels
 
 struct MgLevelDev {
   Grid g;
@@ -51,6 +52,7 @@ struct MgCg {
   GridBar bar;
   double rtol2;
   int maxit, warm;
+  int stage;            // block 0 keeps the levels it runs alone in shared memory
 };
 
 // ------------------------------------------------------------------ level operations
@@ -180,15 +182,97 @@ __device__ void mg_block_cycle(const MgDev &mg, int from, int *zc) {
   __syncthreads();
 }
 
+// Shared-memory copy of the levels >= Lg that block 0 runs alone: their FP32 rows, inverse
+// diagonals and Dirichlet masks (constant during a solve: copied once per launch) and their
+// vectors b, z[2], t.  Bytes needed (each array 16-byte aligned): see mg_stage_bytes.
+template <int D, int NPN, bool FULL>
+__host__ __device__ inline size_t mg_stage_layout(const MgDev &mg, MgDev *out, unsigned char *base) {
+  constexpr int S = ST<D>::S, BLK = FULL ? NPN * NPN : NPN;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    unsigned char *p = base ? base + off : nullptr;
+    off += (bytes + 15) / 16 * 16;
+    return p;
+  };
+  for (int l = mg.Lg; l < mg.L; ++l) {
+    const size_t n = (size_t)mg.lv[l].g.num_nodes;
+    float *W = (float *)take(sizeof(float) * S * BLK * n);
+    float *dinv = (float *)take(sizeof(float) * NPN * n);
+    float *b = (float *)take(sizeof(float) * NPN * n);
+    float *z0 = (float *)take(sizeof(float) * NPN * n);
+    float *z1 = (float *)take(sizeof(float) * NPN * n);
+    float *t = (float *)take(sizeof(float) * NPN * n);
+    uint8_t *dir = (uint8_t *)take(NPN * n);
+    if (out) {
+      MgLevelDev &d = out->lv[l];
+      d.W = W;
+      d.dinv = dinv;
+      d.dir = dir;
+      d.b = b;
+      d.z[0] = z0;
+      d.z[1] = z1;
+      d.t = t;
+    }
+  }
+  return off;
+}
+
+// Block 0: the staged view mgs of mg (levels >= Lg in shared memory, constants copied).
+template <int D, int NPN, bool FULL>
+__device__ void mg_stage(const MgDev &mg, MgDev &mgs, unsigned char *smem) {
+  constexpr int S = ST<D>::S, BLK = FULL ? NPN * NPN : NPN;
+  {
+    const int *src = reinterpret_cast<const int *>(&mg);
+    int *dst = reinterpret_cast<int *>(&mgs);
+    for (int i = threadIdx.x; i < (int)(sizeof(MgDev) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mg_stage_layout<D, NPN, FULL>(mg, &mgs, smem);
+  __syncthreads();
+  for (int l = mg.Lg; l < mg.L; ++l) {
+    const long long n = mg.lv[l].g.num_nodes;
+    const MgLevelDev &G = mg.lv[l];
+    MgLevelDev &Sm = mgs.lv[l];
+    float *W = const_cast<float *>(Sm.W), *dinv = const_cast<float *>(Sm.dinv);
+    uint8_t *dir = const_cast<uint8_t *>(Sm.dir);
+    for (long long k = threadIdx.x; k < (long long)S * BLK * n; k += blockDim.x) W[k] = G.W[k];
+    for (long long k = threadIdx.x; k < NPN * n; k += blockDim.x) {
+      dinv[k] = G.dinv[k];
+      dir[k] = G.dir[k];
+    }
+  }
+  __syncthreads();
+}
+
+// The block cycle on the staged view: level `from`'s b and first sweep come from (and its
+// final iterate goes back to) global memory, where the grid passes read and write them.
+template <int D, int NPN, bool FULL>
+__device__ void mg_block_cycle_staged(const MgDev &mg, const MgDev &mgs, int from, int *zc) {
+  const MgLevelDev &G = mg.lv[from], &Sm = mgs.lv[from];
+  const long long n = G.g.num_nodes * NPN;
+  for (long long k = threadIdx.x; k < n; k += blockDim.x) {
+    Sm.b[k] = G.b[k];
+    Sm.z[0][k] = G.z[0][k];
+  }
+  __syncthreads();
+  mg_block_cycle<D, NPN, FULL>(mgs, from, zc);
+  const float *zs = Sm.z[zc[from]];
+  float *zg = G.z[zc[from]];
+  for (long long k = threadIdx.x; k < n; k += blockDim.x) zg[k] = zs[k];
+}
+
 // The V-cycle from level 0, whose b and first sweep were written by the caller before a grid
 // barrier.  Returns false if a grid barrier failed; level 0's result is in z[zc[0]].
 template <int D, int NPN, bool FULL>
-__device__ bool mg_vcycle(const MgDev &mg, int *zc, const GridBar &bar) {
+__device__ bool mg_vcycle(const MgDev &mg, const MgDev &mgs, bool staged, int *zc, const GridBar &bar) {
   using M = MgOps<D, NPN, FULL>;
   const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x, step = (long long)gridDim.x * blockDim.x;
   const int Lg = mg.Lg;
   if (Lg == 0) {   // everything is small: block 0 runs the whole cycle
-    if (blockIdx.x == 0) mg_block_cycle<D, NPN, FULL>(mg, 0, zc);
+    if (blockIdx.x == 0) {
+      if (staged) mg_block_cycle_staged<D, NPN, FULL>(mg, mgs, 0, zc);
+      else mg_block_cycle<D, NPN, FULL>(mg, 0, zc);
+    }
     return grid_sync(bar);
   }
   for (int l = 0; l < Lg; ++l) {
@@ -209,7 +293,10 @@ __device__ bool mg_vcycle(const MgDev &mg, int *zc, const GridBar &bar) {
     if (!grid_sync(bar)) return false;
   }
   if (Lg < mg.L) {   // the other blocks know the block-run levels' final buffers (fixed)
-    if (blockIdx.x == 0) mg_block_cycle<D, NPN, FULL>(mg, Lg, zc);
+    if (blockIdx.x == 0) {
+      if (staged) mg_block_cycle_staged<D, NPN, FULL>(mg, mgs, Lg, zc);
+      else mg_block_cycle<D, NPN, FULL>(mg, Lg, zc);
+    }
     if (!grid_sync(bar)) return false;
   }
   for (int l = std::min(Lg, mg.L - 1) - 1; l >= 0; --l) {
@@ -246,7 +333,9 @@ __host__ __device__ inline void mg_final_buffers(int L, int Lg, int nu, int nuc,
 // rtol.  Ends with the dot product b . x (for B(theta, theta) of the velocity solve).
 template <int D, int NPN, bool FULL, int NC>
 __global__ void __launch_bounds__(FO_BLOCK) k_pcg_mg(const MgDev *mgp, MgCg C) {
+  extern __shared__ __align__(16) unsigned char mg_dsmem[];
   __shared__ MgDev mg;
+  __shared__ MgDev mgs;   // block 0's view with the block-run levels in shared memory
   __shared__ double sred[32 * 3 * NC];
   __shared__ double stot[3 * NC];
   {
@@ -255,6 +344,8 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg_mg(const MgDev *mgp, MgCg C) {
     for (int i = threadIdx.x; i < (int)(sizeof(MgDev) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
   }
   __syncthreads();
+  const bool staged = C.stage != 0 && mg.Lg < mg.L;
+  if (staged && blockIdx.x == 0) mg_stage<D, NPN, FULL>(mg, mgs, mg_dsmem);
   const MgLevelDev &L0 = mg.lv[0];
   const Grid &g = L0.g;
   const long long N = g.num_nodes;
@@ -297,7 +388,7 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg_mg(const MgDev *mgp, MgCg C) {
       }
     }
     if (!grid_sync(C.bar)) return;
-    if (!mg_vcycle<D, NPN, FULL>(mg, zc, C.bar)) return;
+    if (!mg_vcycle<D, NPN, FULL>(mg, mgs, staged, zc, C.bar)) return;
     // z = M r; gamma_c = (r, z)_c; rho_c = (r, r)_c
     for (long long a = first; a < N; a += step)
 #pragma unroll
@@ -370,7 +461,7 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg_mg(const MgDev *mgp, MgCg C) {
         L0.z[0][k] = mg.omega * L0.dinv[k] * bf;
       }
     if (!grid_sync(C.bar)) return;
-    if (!mg_vcycle<D, NPN, FULL>(mg, zc, C.bar)) return;
+    if (!mg_vcycle<D, NPN, FULL>(mg, mgs, staged, zc, C.bar)) return;
     double w[2 * NC];
 #pragma unroll
     for (int j = 0; j < 2 * NC; ++j) w[j] = 0.0;
@@ -704,11 +795,25 @@ static fo_status mg_run(fo_problem *p, fo_mg *mg, const double *W64, const doubl
   auto kern = k_pcg_mg<D, NPN, FULL, NC>;
   int grid;
   FO_TRY(fo_cooperative_grid(p, (const void *)kern, FO_BLOCK, 0, p->mesh->g.num_nodes, o->grid_blocks, &grid));
+  // Block 0 keeps the levels it runs alone in shared memory when they fit and the launch
+  // keeps its grid (the extra shared memory per block may lower the co-resident count).
+  size_t smem = 0;
+  {
+    const MgDev *h = reinterpret_cast<const MgDev *>(mg->host.data());
+    const size_t bytes = h->Lg < h->L ? mg_stage_layout<D, NPN, FULL>(*h, nullptr, nullptr) : 0;
+    if (bytes > 0 && bytes <= MG_STAGE_MAX_BYTES) {
+      FO_CU(ctx, cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      int g1 = 0;
+      FO_TRY(fo_cooperative_grid(p, (const void *)kern, FO_BLOCK, bytes, p->mesh->g.num_nodes, o->grid_blocks, &g1));
+      if (g1 == grid) smem = bytes;
+    }
+  }
+  C.stage = smem > 0;
   const MgDev *mgp = (const MgDev *)mg->dev;
   void *argv[] = {(void *)&mgp, (void *)&C};
   FO_CU(ctx, cudaMemsetAsync(p->bar, 0, 64, ctx->stream));
   FO_CU(ctx, cudaMemsetAsync(p->dev_status, 0, sizeof(int) * DS_COUNT, ctx->stream));
-  FO_CU(ctx, cudaLaunchCooperativeKernel((const void *)kern, grid, FO_BLOCK, argv, 0, ctx->stream));
+  FO_CU(ctx, cudaLaunchCooperativeKernel((const void *)kern, grid, FO_BLOCK, argv, smem, ctx->stream));
   fo_note_launch(1);
   FO_CU(ctx, cudaGetLastError());
   FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars, C.out, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
