@@ -92,6 +92,9 @@ struct fo_mg {
   double *coef[MG_MAX_LEVELS] = {}, *W64[MG_MAX_LEVELS] = {}, *dinv64[MG_MAX_LEVELS] = {};
   float *W32[MG_MAX_LEVELS] = {}, *dinv32[MG_MAX_LEVELS] = {};
   uint8_t *dir[MG_MAX_LEVELS] = {};
+  int nd = 0;                              // coarsest level's unknowns when solved directly
+  float *ainv = nullptr;                   // [nd][nd] its inverse (FP32)
+  double *awork = nullptr;                 // [nd][2 nd] Gauss-Jordan work array
   void *dev = nullptr;                     // device copy of the level table
   std::vector<unsigned char> host;         // its host image (kept alive for the async copy)
 };
@@ -275,13 +278,15 @@ __device__ __forceinline__ bool grid_sync(const GridBar &b) {
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned inc = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1)) : 1u;
-    __threadfence();                               // this block's writes before the arrival
-    unsigned old = atomicAdd(b.count, inc);
-    volatile unsigned *cnt = b.count;
+    // arrival with release semantics (the block's writes, ordered before it by the block
+    // barrier above, become visible to every block that acquires the released count);
+    // polling with acquire loads orders the other blocks' writes before this block's reads
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(b.count), "r"(inc) : "memory");
     int ok = 1;
     unsigned long long t0 = 0;
     unsigned spins = 0;
-    while (((old ^ *cnt) & 0x80000000u) == 0) {
+    while (((old ^ fo_ld_acquire(b.count)) & 0x80000000u) == 0) {
       if (++spins == 1024) t0 = fo_globaltimer();
       if (spins > 1024 && (spins & 255) == 0) {
         __nanosleep(64);
@@ -296,7 +301,6 @@ __device__ __forceinline__ bool grid_sync(const GridBar &b) {
         }
       }
     }
-    __threadfence();                               // other blocks' writes after the release
     s_ok = ok;
   }
   __syncthreads();

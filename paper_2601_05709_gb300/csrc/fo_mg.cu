@@ -9,7 +9,8 @@
 // built by the same stencil builder as the fine ones, from restricted coefficients.  P is P1
 // interpolation along the Kuhn edges: a fine node with index parities b in {0,1}^d takes the
 // mean of the coarse nodes (i - b)/2 and (i + b)/2; the restriction is P^T.  Smoother: damped
-// Jacobi, nu1 = nu2 sweeps; coarsest level: nuc sweeps.  Levels of at most MG_BLOCK_DOFS
+// Jacobi, nu1 = nu2 sweeps; coarsest level: an exact solve with its precomputed inverse when
+// it has at most MG_DIRECT_MAX unknowns, else nuc sweeps.  Levels of at most MG_BLOCK_DOFS
 // unknowns are run by block 0 alone with block barriers only (a grid barrier per sweep would
 // dominate their tiny work); the rest by the whole grid with grid barriers.
 //
@@ -26,6 +27,8 @@
 
 #define MG_BLOCK_DOFS 2048
 #define MG_STAGE_MAX_BYTES (180 * 1024)   // shared memory block 0 may take for its levels
+#define MG_DIRECT_MAX 128                 // coarsest levels of at most this many unknowns are
+                                          // solved with a precomputed inverse
 
 struct MgLevelDev {
   Grid g;
@@ -39,6 +42,8 @@ struct MgDev {
   int L, Lg;            // levels; levels >= Lg run in block 0 alone
   float omega;
   int nu, nuc;
+  int nd;               // > 0: the coarsest level is solved with its inverse ainv [nd][nd]
+  const float *ainv;
   MgLevelDev lv[MG_MAX_LEVELS];
 };
 
@@ -155,6 +160,18 @@ __device__ void mg_block_cycle(const MgDev &mg, int from, int *zc) {
     const MgLevelDev &L = mg.lv[l];
     const int sweeps = (l == mg.L - 1) ? mg.nuc : mg.nu;
     int c = 0;
+    if (l == mg.L - 1 && mg.nd > 0) {   // exact coarse solve, into the sweeps' final buffer
+      c = (sweeps - 1) & 1;
+      __syncthreads();
+      for (long long i = t; i < mg.nd; i += st) {
+        const float *row = mg.ainv + i * mg.nd;
+        float acc = 0.f;
+        for (int k = 0; k < mg.nd; ++k) acc = fmaf(row[k], L.b[k], acc);
+        L.z[c][i] = acc;
+      }
+      zc[l] = c;
+      break;
+    }
     for (int j = 1; j < sweeps; ++j) {
       __syncthreads();
       M::sweep(L, L.z[c], L.z[c ^ 1], mg.omega, t, st);
@@ -194,6 +211,10 @@ __host__ __device__ inline size_t mg_stage_layout(const MgDev &mg, MgDev *out, u
     off += (bytes + 15) / 16 * 16;
     return p;
   };
+  if (mg.nd > 0) {
+    float *a = (float *)take(sizeof(float) * (size_t)mg.nd * mg.nd);
+    if (out) out->ainv = a;
+  }
   for (int l = mg.Lg; l < mg.L; ++l) {
     const size_t n = (size_t)mg.lv[l].g.num_nodes;
     float *W = (float *)take(sizeof(float) * S * BLK * n);
@@ -229,6 +250,8 @@ __device__ void mg_stage(const MgDev &mg, MgDev &mgs, unsigned char *smem) {
   __syncthreads();
   if (threadIdx.x == 0) mg_stage_layout<D, NPN, FULL>(mg, &mgs, smem);
   __syncthreads();
+  if (mg.nd > 0)
+    for (int k = threadIdx.x; k < mg.nd * mg.nd; k += blockDim.x) const_cast<float *>(mgs.ainv)[k] = mg.ainv[k];
   for (int l = mg.Lg; l < mg.L; ++l) {
     const long long n = mg.lv[l].g.num_nodes;
     const MgLevelDev &G = mg.lv[l];
@@ -549,6 +572,85 @@ __global__ void k_mg_coarse_dir(Grid gc, Grid gf, int npn, const uint8_t *dir_f,
   }
 }
 
+// Inverse of the coarsest level's operator, for the exact coarse solve.  One block: the dense
+// n x n matrix (n = nodes x components <= MG_DIRECT_MAX) is assembled from the level's FP64
+// difference-form rows -- A[(a,c),(a,k)] = R_ck - sum_s W_s,ck, A[(a,c),(nb_s,k)] = W_s,ck --
+// next to the identity, and reduced by Gauss-Jordan elimination without pivoting (the matrix is
+// symmetric positive definite: Dirichlet rows are identity rows and their columns eliminated),
+// in FP64; the inverse is stored in FP32.
+template <int D, int NPN, bool FULL>
+__global__ void k_mg_coarse_inverse(Grid g, const double *W, int n, double *A, float *ainv) {
+  constexpr int S = ST<D>::S, BLK = FULL ? NPN * NPN : NPN;
+  const long long N = g.num_nodes;
+  const int w2 = 2 * n;
+  __shared__ double f[MG_DIRECT_MAX];
+  for (int k = threadIdx.x; k < n * w2; k += blockDim.x) {
+    const int i = k / w2, j = k - i * w2;
+    A[k] = (j - n == i) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (long long a = 0; a < N; ++a) {
+      int idx[3];
+      node_ijk(g, a, idx);
+      for (int c = 0; c < NPN; ++c)
+        for (int k = 0; k < NPN; ++k) {
+          if (!FULL && k != c) continue;
+          const int e = FULL ? c * NPN + k : c;
+          const long long r = a * NPN + c;
+          double diag = W[(0 * BLK + e) * N + a];
+          for (int s = 1; s < S; ++s) {
+            const long long nb = slot_node<D>(g, idx, a, s);
+            if (nb < 0) continue;
+            const double w = W[((long long)s * BLK + e) * N + a];
+            diag -= w;
+            A[r * w2 + nb * NPN + k] += w;
+          }
+          A[r * w2 + a * NPN + k] += diag;
+        }
+    }
+  __syncthreads();
+  for (int p = 0; p < n; ++p) {
+    const double piv = A[(long long)p * w2 + p];
+    __syncthreads();
+    for (int j = threadIdx.x; j < w2; j += blockDim.x) A[(long long)p * w2 + j] /= piv;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) f[i] = (i == p) ? 0.0 : A[(long long)i * w2 + p];
+    __syncthreads();
+    for (int k = threadIdx.x; k < n * w2; k += blockDim.x) {
+      const int i = k / w2, j = k - i * w2;
+      if (i != p) A[k] -= f[i] * A[(long long)p * w2 + j];
+    }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < n * n; k += blockDim.x) {
+    const int i = k / n, j = k - i * n;
+    ainv[k] = (float)A[(long long)i * w2 + n + j];
+  }
+}
+
+static int mg_direct_unknowns(const Grid *g, int L, int npn) {
+  if (L < 2) return 0;
+  const long long n = g[L - 1].num_nodes * npn;
+  return n <= MG_DIRECT_MAX ? (int)n : 0;
+}
+
+static void mg_build_inverse(fo_ctx *ctx, fo_mg *mg) {
+  if (mg->nd == 0) return;
+  const Grid &gc = mg->g[mg->L - 1];
+  const double *W = mg->W64[mg->L - 1];
+  cudaStream_t s = ctx->stream;
+  if (gc.dim == 2) {
+    if (mg->npn == 1) k_mg_coarse_inverse<2, 1, true><<<1, 256, 0, s>>>(gc, W, mg->nd, mg->awork, mg->ainv);
+    else if (mg->blk == 4) k_mg_coarse_inverse<2, 2, true><<<1, 256, 0, s>>>(gc, W, mg->nd, mg->awork, mg->ainv);
+    else k_mg_coarse_inverse<2, 2, false><<<1, 256, 0, s>>>(gc, W, mg->nd, mg->awork, mg->ainv);
+  } else {
+    if (mg->npn == 1) k_mg_coarse_inverse<3, 1, true><<<1, 256, 0, s>>>(gc, W, mg->nd, mg->awork, mg->ainv);
+    else if (mg->blk == 9) k_mg_coarse_inverse<3, 3, true><<<1, 256, 0, s>>>(gc, W, mg->nd, mg->awork, mg->ainv);
+    else k_mg_coarse_inverse<3, 3, false><<<1, 256, 0, s>>>(gc, W, mg->nd, mg->awork, mg->ainv);
+  }
+  fo_note_launch(1);
+}
+
 // ------------------------------------------------------------------------- hierarchies
 // Levels: halve every axis while all are even and the coarse grid keeps >= 2 cells per axis.
 int fo_mg_plan(const Grid &g0, Grid *g, int max_levels) {
@@ -605,6 +707,10 @@ static void mg_release(fo_ctx *ctx, fo_mg *&mg) {
     for (int i = 0; i < 10; ++i)
       if (sz[i]) fo_free(ctx, *mg_slot(mg, l, i), sz[i]);
   }
+  if (mg->nd > 0) {
+    fo_free(ctx, mg->ainv, sizeof(float) * mg->nd * mg->nd);
+    fo_free(ctx, mg->awork, 2 * sizeof(double) * mg->nd * mg->nd);
+  }
   fo_free(ctx, mg->dev, sizeof(MgDev));
   delete mg;
   mg = nullptr;
@@ -636,7 +742,8 @@ size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0) {
     mg_sizes(g[l], npn, blk, l > 0, own0, sz);
     for (int i = 0; i < 10; ++i) b += sz[i];
   }
-  return b;
+  const size_t nd = (size_t)mg_direct_unknowns(g, L, npn);
+  return b + nd * nd * (sizeof(float) + 2 * sizeof(double));
 }
 
 static fo_status mg_alloc(fo_ctx *ctx, fo_mg *&out, const Grid &g0, int npn, int blk, bool own0) {
@@ -651,6 +758,11 @@ static fo_status mg_alloc(fo_ctx *ctx, fo_mg *&out, const Grid &g0, int npn, int
     mg_sizes(mg->g[l], npn, blk, l > 0, own0, sz);
     for (int i = 0; i < 10; ++i)
       if (sz[i]) FO_TRY(fo_alloc(ctx, mg_slot(mg, l, i), sz[i]));
+  }
+  mg->nd = mg_direct_unknowns(mg->g, mg->L, npn);
+  if (mg->nd > 0) {
+    FO_TRY(fo_alloc(ctx, (void **)&mg->ainv, sizeof(float) * mg->nd * mg->nd));
+    FO_TRY(fo_alloc(ctx, (void **)&mg->awork, 2 * sizeof(double) * mg->nd * mg->nd));
   }
   FO_TRY(fo_alloc(ctx, (void **)&mg->dev, sizeof(MgDev)));
   return FO_OK;
@@ -671,6 +783,8 @@ static fo_status mg_upload(fo_ctx *ctx, fo_mg *mg, const float *W0, const float 
   h.omega = omega;
   h.nu = 2;
   h.nuc = 16;
+  h.nd = mg->nd;
+  h.ainv = mg->ainv;
   for (int l = 0; l < mg->L; ++l) {
     MgLevelDev &d = h.lv[l];
     d.g = mg->g[l];
@@ -721,6 +835,7 @@ static fo_status mg_prepare_state(fo_problem *p) {
     FO_TRY(fo_launch_stencil_on(p, mg->g[l], mg->coef[l], mg->dir[l], mg->W64[l], mg->W32[l], mg->dinv64[l],
                                 mg->dinv32[l]));
   }
+  mg_build_inverse(ctx, mg);
   FO_TRY(mg_upload(ctx, mg, p->Wst32, p->dinv_state32, p->dir, p->ncomp == 1 ? 0.8f : 0.6f));
   mg->built_epoch = p->coef_epoch;
   return FO_OK;
@@ -765,6 +880,7 @@ static fo_status mg_prepare_velocity(fo_problem *p) {
     FO_TRY(fo_launch_velocity_stencil_on(p, mg->g[l], mg->coef[l], mg->dir[l], mg->W64[l], mg->W32[l], mg->dinv64[l],
                                          mg->dinv32[l]));
   }
+  mg_build_inverse(ctx, mg);
   FO_TRY(mg_upload(ctx, mg, mg->W32[0], mg->dinv32[0], mg->dir[0], 0.8f));
   return FO_OK;
 }
