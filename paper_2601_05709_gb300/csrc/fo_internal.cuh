@@ -94,7 +94,6 @@ struct fo_mg {
   uint8_t *dir[MG_MAX_LEVELS] = {};
   int nd = 0;                              // coarsest level's unknowns when solved directly
   float *ainv = nullptr;                   // [nd][nd] its inverse (FP32)
-  double *awork = nullptr;                 // [nd][2 nd] Gauss-Jordan work array
   void *dev = nullptr;                     // device copy of the level table
   std::vector<unsigned char> host;         // its host image (kept alive for the async copy)
 };
@@ -405,7 +404,7 @@ fo_status fo_state_pcg_mg(fo_problem *p, const double *b, double *x, const fo_so
 void fo_mg_destroy(fo_problem *p);
 size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0);
 bool fo_mg_applicable(const Grid &g0, int npn);
-int fo_mg_plan(const Grid &g0, Grid *g, int max_levels);
+int fo_mg_plan(const Grid &g0, Grid *g, int max_levels, long long stop_unknowns = 0, int npn = 1);
 void fo_mg_restrict(fo_ctx *ctx, const Grid &gc, const Grid &gf, int npn, const double *coef_f, const uint8_t *dir_f,
                     double *coef_c, uint8_t *dir_c);
 // batched multigrid (fo_batch_mg.cu) and the batch stencil builder it shares (fo_batch.cu)

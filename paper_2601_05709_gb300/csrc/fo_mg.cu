@@ -27,7 +27,7 @@
 
 #define MG_BLOCK_DOFS 2048
 #define MG_STAGE_MAX_BYTES (180 * 1024)   // shared memory block 0 may take for its levels
-#define MG_DIRECT_MAX 128                 // coarsest levels of at most this many unknowns are
+#define MG_DIRECT_MAX 64                  // coarsest levels of at most this many unknowns are
                                           // solved with a precomputed inverse
 
 struct MgLevelDev {
@@ -573,59 +573,84 @@ __global__ void k_mg_coarse_dir(Grid gc, Grid gf, int npn, const uint8_t *dir_f,
 }
 
 // Inverse of the coarsest level's operator, for the exact coarse solve.  One block: the dense
-// n x n matrix (n = nodes x components <= MG_DIRECT_MAX) is assembled from the level's FP64
-// difference-form rows -- A[(a,c),(a,k)] = R_ck - sum_s W_s,ck, A[(a,c),(nb_s,k)] = W_s,ck --
-// next to the identity, and reduced by Gauss-Jordan elimination without pivoting (the matrix is
-// symmetric positive definite: Dirichlet rows are identity rows and their columns eliminated),
-// in FP64; the inverse is stored in FP32.
+// n x n matrix (n = nodes x components <= MG_DIRECT_MAX) is assembled in shared memory from
+// the level's FP64 difference-form rows -- A[(a,c),(a,k)] = R_ck - sum_s W_s,ck and
+// A[(a,c),(nb_s,k)] = W_s,ck, a thread per node -- and inverted in place by Gauss-Jordan
+// elimination without pivoting (the matrix is symmetric positive definite: Dirichlet rows are
+// identity rows and their columns eliminated), in FP64; the inverse is stored in FP32.
 template <int D, int NPN, bool FULL>
-__global__ void k_mg_coarse_inverse(Grid g, const double *W, int n, double *A, float *ainv) {
+__global__ void k_mg_coarse_inverse(Grid g, const double *W, int n, float *ainv) {
   constexpr int S = ST<D>::S, BLK = FULL ? NPN * NPN : NPN;
+  extern __shared__ __align__(16) double A[];   // [n][n]
+  __shared__ double piv;
   const long long N = g.num_nodes;
-  const int w2 = 2 * n;
-  __shared__ double f[MG_DIRECT_MAX];
-  for (int k = threadIdx.x; k < n * w2; k += blockDim.x) {
-    const int i = k / w2, j = k - i * w2;
-    A[k] = (j - n == i) ? 1.0 : 0.0;
-  }
+  for (int k = threadIdx.x; k < n * n; k += blockDim.x) A[k] = 0.0;
   __syncthreads();
-  if (threadIdx.x == 0)
-    for (long long a = 0; a < N; ++a) {
-      int idx[3];
-      node_ijk(g, a, idx);
-      for (int c = 0; c < NPN; ++c)
-        for (int k = 0; k < NPN; ++k) {
-          if (!FULL && k != c) continue;
-          const int e = FULL ? c * NPN + k : c;
-          const long long r = a * NPN + c;
-          double diag = W[(0 * BLK + e) * N + a];
-          for (int s = 1; s < S; ++s) {
-            const long long nb = slot_node<D>(g, idx, a, s);
-            if (nb < 0) continue;
-            const double w = W[((long long)s * BLK + e) * N + a];
-            diag -= w;
-            A[r * w2 + nb * NPN + k] += w;
-          }
-          A[r * w2 + a * NPN + k] += diag;
+  for (long long a = threadIdx.x; a < N; a += blockDim.x) {   // rows of node a only
+    int idx[3];
+    node_ijk(g, a, idx);
+    for (int c = 0; c < NPN; ++c)
+      for (int k = 0; k < NPN; ++k) {
+        if (!FULL && k != c) continue;
+        const int e = FULL ? c * NPN + k : c;
+        const long long r = a * NPN + c;
+        double diag = W[(long long)e * N + a];
+        for (int s = 1; s < S; ++s) {
+          const long long nb = slot_node<D>(g, idx, a, s);
+          if (nb < 0) continue;
+          const double w = W[((long long)s * BLK + e) * N + a];
+          diag -= w;
+          A[r * n + nb * NPN + k] += w;
         }
-    }
-  __syncthreads();
+        A[r * n + a * NPN + k] += diag;
+      }
+  }
   for (int p = 0; p < n; ++p) {
-    const double piv = A[(long long)p * w2 + p];
     __syncthreads();
-    for (int j = threadIdx.x; j < w2; j += blockDim.x) A[(long long)p * w2 + j] /= piv;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) f[i] = (i == p) ? 0.0 : A[(long long)i * w2 + p];
+    if (threadIdx.x == 0) piv = 1.0 / A[p * n + p];
     __syncthreads();
-    for (int k = threadIdx.x; k < n * w2; k += blockDim.x) {
-      const int i = k / w2, j = k - i * w2;
-      if (i != p) A[k] -= f[i] * A[(long long)p * w2 + j];
+    const double q = piv;
+    for (int k = threadIdx.x; k < n * n; k += blockDim.x) {   // outside row and column p
+      const int i = k / n, j = k - i * n;
+      if (i != p && j != p) A[k] -= A[i * n + p] * A[p * n + j] * q;
     }
     __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+      if (k != p) {
+        A[p * n + k] *= q;
+        A[k * n + p] *= -q;
+      }
+    if (threadIdx.x == 0) A[p * n + p] = q;
   }
-  for (int k = threadIdx.x; k < n * n; k += blockDim.x) {
-    const int i = k / n, j = k - i * n;
-    ainv[k] = (float)A[(long long)i * w2 + n + j];
+  __syncthreads();
+  for (int k = threadIdx.x; k < n * n; k += blockDim.x) ainv[k] = (float)A[k];
+}
+
+static void mg_build_inverse(fo_ctx *ctx, fo_mg *mg) {
+  if (mg->nd == 0) return;
+  const Grid &gc = mg->g[mg->L - 1];
+  const double *W = mg->W64[mg->L - 1];
+  cudaStream_t s = ctx->stream;
+  const size_t smem = sizeof(double) * mg->nd * mg->nd;
+  auto run = [&](auto kern) {
+    cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<1, 256, smem, s>>>(gc, W, mg->nd, mg->ainv);
+  };
+  if (gc.dim == 2) {
+    if (mg->npn == 1) run(k_mg_coarse_inverse<2, 1, true>);
+    else if (mg->blk == 4) run(k_mg_coarse_inverse<2, 2, true>);
+    else run(k_mg_coarse_inverse<2, 2, false>);
+  } else {
+    if (mg->npn == 1) run(k_mg_coarse_inverse<3, 1, true>);
+    else if (mg->blk == 9) run(k_mg_coarse_inverse<3, 3, true>);
+    else run(k_mg_coarse_inverse<3, 3, false>);
   }
+  fo_note_launch(1);
+}
+
+// The single-problem hierarchy ends at the first level small enough to be solved directly.
+static int mg_plan_single(const Grid &g0, Grid *g, int npn) {
+  return fo_mg_plan(g0, g, MG_MAX_LEVELS, MG_DIRECT_MAX, npn);
 }
 
 static int mg_direct_unknowns(const Grid *g, int L, int npn) {
@@ -634,30 +659,17 @@ static int mg_direct_unknowns(const Grid *g, int L, int npn) {
   return n <= MG_DIRECT_MAX ? (int)n : 0;
 }
 
-static void mg_build_inverse(fo_ctx *ctx, fo_mg *mg) {
-  if (mg->nd == 0) return;
-  const Grid &gc = mg->g[mg->L - 1];
-  const double *W = mg->W64[mg->L - 1];
-  cudaStream_t s = ctx->stream;
-  if (gc.dim == 2) {
-    if (mg->npn == 1) k_mg_coarse_inverse<2, 1, true><<<1, 256, 0, s>>>(gc, W, mg->nd, mg->awork, mg->ainv);
-    else if (mg->blk == 4) k_mg_coarse_inverse<2, 2, true><<<1, 256, 0, s>>>(gc, W, mg->nd, mg->awork, mg->ainv);
-    else k_mg_coarse_inverse<2, 2, false><<<1, 256, 0, s>>>(gc, W, mg->nd, mg->awork, mg->ainv);
-  } else {
-    if (mg->npn == 1) k_mg_coarse_inverse<3, 1, true><<<1, 256, 0, s>>>(gc, W, mg->nd, mg->awork, mg->ainv);
-    else if (mg->blk == 9) k_mg_coarse_inverse<3, 3, true><<<1, 256, 0, s>>>(gc, W, mg->nd, mg->awork, mg->ainv);
-    else k_mg_coarse_inverse<3, 3, false><<<1, 256, 0, s>>>(gc, W, mg->nd, mg->awork, mg->ainv);
-  }
-  fo_note_launch(1);
-}
 
 // ------------------------------------------------------------------------- hierarchies
-// Levels: halve every axis while all are even and the coarse grid keeps >= 2 cells per axis.
-int fo_mg_plan(const Grid &g0, Grid *g, int max_levels) {
+// Levels: halve every axis while all are even and the coarse grid keeps >= 2 cells per axis;
+// with stop_unknowns > 0, also stop at the first level of at most that many unknowns (npn per
+// node).
+int fo_mg_plan(const Grid &g0, Grid *g, int max_levels, long long stop_unknowns, int npn) {
   g[0] = g0;
   int L = 1;
   while (L < max_levels) {
     const Grid &f = g[L - 1];
+    if (stop_unknowns > 0 && f.num_nodes * npn <= stop_unknowns) break;
     int n[3] = {1, 1, 1};
     bool ok = true;
     for (int a = 0; a < f.dim; ++a) {
@@ -709,7 +721,6 @@ static void mg_release(fo_ctx *ctx, fo_mg *&mg) {
   }
   if (mg->nd > 0) {
     fo_free(ctx, mg->ainv, sizeof(float) * mg->nd * mg->nd);
-    fo_free(ctx, mg->awork, 2 * sizeof(double) * mg->nd * mg->nd);
   }
   fo_free(ctx, mg->dev, sizeof(MgDev));
   delete mg;
@@ -726,7 +737,7 @@ void fo_mg_destroy(fo_problem *p) {
 #define MG_COARSEST_MAX_DOFS 8192
 bool fo_mg_applicable(const Grid &g0, int npn) {
   Grid g[MG_MAX_LEVELS];
-  const int L = fo_mg_plan(g0, g, MG_MAX_LEVELS);
+  const int L = mg_plan_single(g0, g, npn);
   return L >= 2 && g[L - 1].num_nodes * npn <= MG_COARSEST_MAX_DOFS;
 }
 
@@ -735,7 +746,7 @@ size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0) {
   const double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
   if (!fo_grid_make(dim, n, lo, hi, g0)) return 0;
   Grid g[MG_MAX_LEVELS];
-  const int L = fo_mg_plan(g0, g, MG_MAX_LEVELS);
+  const int L = mg_plan_single(g0, g, npn);
   size_t b = sizeof(MgDev);
   for (int l = 0; l < L; ++l) {
     size_t sz[10];
@@ -743,7 +754,7 @@ size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0) {
     for (int i = 0; i < 10; ++i) b += sz[i];
   }
   const size_t nd = (size_t)mg_direct_unknowns(g, L, npn);
-  return b + nd * nd * (sizeof(float) + 2 * sizeof(double));
+  return b + nd * nd * sizeof(float);
 }
 
 static fo_status mg_alloc(fo_ctx *ctx, fo_mg *&out, const Grid &g0, int npn, int blk, bool own0) {
@@ -752,7 +763,7 @@ static fo_status mg_alloc(fo_ctx *ctx, fo_mg *&out, const Grid &g0, int npn, int
   mg->npn = npn;
   mg->blk = blk;
   mg->own0 = own0;
-  mg->L = fo_mg_plan(g0, mg->g, MG_MAX_LEVELS);
+  mg->L = mg_plan_single(g0, mg->g, npn);
   for (int l = 0; l < mg->L; ++l) {
     size_t sz[10];
     mg_sizes(mg->g[l], npn, blk, l > 0, own0, sz);
@@ -762,7 +773,6 @@ static fo_status mg_alloc(fo_ctx *ctx, fo_mg *&out, const Grid &g0, int npn, int
   mg->nd = mg_direct_unknowns(mg->g, mg->L, npn);
   if (mg->nd > 0) {
     FO_TRY(fo_alloc(ctx, (void **)&mg->ainv, sizeof(float) * mg->nd * mg->nd));
-    FO_TRY(fo_alloc(ctx, (void **)&mg->awork, 2 * sizeof(double) * mg->nd * mg->nd));
   }
   FO_TRY(fo_alloc(ctx, (void **)&mg->dev, sizeof(MgDev)));
   return FO_OK;
