@@ -185,6 +185,14 @@ __host__ __device__ __forceinline__ int kperm(int p, int l) {
 template <int D> struct KP { static constexpr int P = (D == 2) ? 2 : 6; };
 
 __device__ __forceinline__ void node_ijk(const Grid &g, long long a, int idx[3]) {
+  if (g.num_nodes <= 0xffffffffLL) {   // 32-bit division (every grid below 2^32 nodes)
+    const unsigned ua = (unsigned)a, n0 = (unsigned)g.nn[0], n1 = (unsigned)g.nn[1];
+    const unsigned t = ua / n0;
+    idx[0] = (int)(ua - t * n0);
+    idx[1] = (int)(t % n1);
+    idx[2] = (int)(t / n1);
+    return;
+  }
   idx[0] = (int)(a % g.nn[0]);
   long long t = a / g.nn[0];
   idx[1] = (int)(t % g.nn[1]);
