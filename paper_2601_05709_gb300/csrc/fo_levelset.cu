@@ -226,7 +226,27 @@ struct GmresShared {
   double col[GM_M + 1];          // the new Hessenberg column (before the rotations)
   double H[(GM_M + 1) * GM_M];   // column-major: H[j * (GM_M + 1) + i]
   double cs[GM_M], sn[GM_M], g[GM_M + 1], y[GM_M];
+  int rotated;                   // the step's column is already rotated into H
 };
+
+// Thread 0: apply the previous rotations to column j (col[0..j+1]), form the new one, update
+// the residual estimate g and store the rotated column in H.
+__device__ __forceinline__ void givens_column(GmresShared &sh, int j, double *col) {
+  for (int i = 0; i < j; ++i) {
+    const double t = sh.cs[i] * col[i] + sh.sn[i] * col[i + 1];
+    col[i + 1] = -sh.sn[i] * col[i] + sh.cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double rnorm = hypot(col[j], col[j + 1]);
+  const double c = rnorm > 0.0 ? col[j] / rnorm : 1.0, s = rnorm > 0.0 ? col[j + 1] / rnorm : 0.0;
+  sh.cs[j] = c;
+  sh.sn[j] = s;
+  col[j] = rnorm;
+  col[j + 1] = 0.0;
+  sh.g[j + 1] = -s * sh.g[j];
+  sh.g[j] = c * sh.g[j];
+  for (int i = 0; i <= j; ++i) sh.H[j * (GM_M + 1) + i] = col[i];
+}
 
 // One Arnoldi step at compile-time index J: w = M D^{-1} v_J, classical Gram-Schmidt against
 // v_0..v_J (one fused grid reduction of the J + 1 dot products and |w|^2), a second pass only
@@ -273,6 +293,14 @@ __device__ bool arnoldi_step(const Grid &g, const double *M, const double *dinv,
     const double hnext = sqrt(wp2);
     const double inv = hnext > 0.0 ? 1.0 / hnext : 0.0;
     double *Vn = K.V + (size_t)(J + 1) * N;
+    if (threadIdx.x == 0) {   // the column is final: rotate it now, overlapping the pass below
+      double col[J + 2];
+#pragma unroll
+      for (int i = 0; i <= J; ++i) col[i] = hc[i];
+      col[J + 1] = hnext;
+      givens_column(sh, J, col);
+      sh.rotated = 1;
+    }
     for (long long a = tid; a < N; a += gs) {
       double wa = K.w[a];
 #pragma unroll
@@ -397,27 +425,16 @@ __device__ int gmres_solve(const Grid &g, const double *M, const double *dinv, c
     int j = 0;
     bool done = false;
     for (; j < GM_M; ++j) {
+      if (threadIdx.x == 0) sh.rotated = 0;
+      __syncthreads();
       if (!arnoldi_dispatch<D, 0>(j, g, M, dinv, K, sh, partials, rk, bar)) { *ok = false; return total; }
       __syncthreads();
       const double hnext = sh.col[j + 1];
       // ---- Hessenberg column, Givens rotations, residual estimate (same in every block)
-      if (threadIdx.x == 0) {
+      if (threadIdx.x == 0 && !sh.rotated) {
         double col[GM_M + 1];
         for (int i = 0; i <= j + 1; ++i) col[i] = sh.col[i];
-        for (int i = 0; i < j; ++i) {
-          const double t = sh.cs[i] * col[i] + sh.sn[i] * col[i + 1];
-          col[i + 1] = -sh.sn[i] * col[i] + sh.cs[i] * col[i + 1];
-          col[i] = t;
-        }
-        const double rnorm = hypot(col[j], col[j + 1]);
-        const double c = rnorm > 0.0 ? col[j] / rnorm : 1.0, s = rnorm > 0.0 ? col[j + 1] / rnorm : 0.0;
-        sh.cs[j] = c;
-        sh.sn[j] = s;
-        col[j] = rnorm;
-        col[j + 1] = 0.0;
-        sh.g[j + 1] = -s * sh.g[j];
-        sh.g[j] = c * sh.g[j];
-        for (int i = 0; i <= j; ++i) sh.H[j * (GM_M + 1) + i] = col[i];
+        givens_column(sh, j, col);
       }
       __syncthreads();
       ++total;
