@@ -297,8 +297,10 @@ def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True, mg
     t0 = time.perf_counter()
     J, C = prob.functionals()
     prob.shape_derivative(0.0, copy=False)
-    Btt, vst = prob.descent(api.solve_opts(rtol=1e-8))
+    Btt, vst = prob.descent(api.solve_opts(rtol=1e-8, precond=api.FO_PC_MG))
+    torch.cuda.synchronize()
     out["shape_and_velocity_seconds"] = time.perf_counter() - t0
+    out["velocity_iterations"] = vst.iterations
     out["J"] = J
     # plain FP64 one instance at a time (the single-problem path of the same library)
     tot_t, tot_it = 0.0, 0
