@@ -564,8 +564,11 @@ def main():
         its_per_launch = state_iters / len(logs)
         achieved = bpi * its_per_launch / (launch_ms / 1e3) / 1e9
         hbm = peaks.get("hbm_gbs", 6800.0)
+        # DRAM bytes of one launch of this kernel, from the committed ncu capture of the same build
+        # (profiles/k_pcg_mg_state_cantilever2d.md): the hierarchy is read once, then served from L2
+        traffic = 14.11e6 + 0.78e6
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": "k_pcg_mg<2, 2, true, 1>",
+                "traffic": traffic, "kernel": "k_pcg_mg<2, 2, true, 1>",
                 "algorithmic_bytes_per_iteration": bpi, "iterations_per_launch": its_per_launch,
                 "launch_ms": launch_ms,
                 "note": "peak = measured HBM copy bandwidth; the state hierarchy (~15 MB) stays in L2, so the "

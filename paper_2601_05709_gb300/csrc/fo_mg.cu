@@ -40,7 +40,9 @@ struct MgLevelDev {
 
 struct MgDev {
   int L, Lg;            // levels; levels >= Lg run in block 0 alone
-  float omega;
+  float omega;          // damping of the coarsest level's sweeps
+  float om[2];          // damping of the two smoothing sweeps: om[0] then om[1] before the coarse
+                        // correction, om[1] then om[0] after it (the V-cycle stays symmetric)
   int nu, nuc;
   int nd;               // > 0: the coarsest level is solved with its inverse ainv [nd][nd]
   const float *ainv;
@@ -174,7 +176,7 @@ __device__ void mg_block_cycle(const MgDev &mg, int from, int *zc) {
     }
     for (int j = 1; j < sweeps; ++j) {
       __syncthreads();
-      M::sweep(L, L.z[c], L.z[c ^ 1], mg.omega, t, st);
+      M::sweep(L, L.z[c], L.z[c ^ 1], l == mg.L - 1 ? mg.omega : mg.om[j & 1], t, st);
       c ^= 1;
     }
     zc[l] = c;
@@ -182,7 +184,7 @@ __device__ void mg_block_cycle(const MgDev &mg, int from, int *zc) {
     __syncthreads();
     M::residual(L, L.z[c], t, st);
     __syncthreads();
-    M::restrict_(L, mg.lv[l + 1], mg.omega, t, st);
+    M::restrict_(L, mg.lv[l + 1], l + 1 == mg.L - 1 ? mg.omega : mg.om[0], t, st);
   }
   for (int l = mg.L - 2; l >= from; --l) {
     const MgLevelDev &L = mg.lv[l];
@@ -191,7 +193,7 @@ __device__ void mg_block_cycle(const MgDev &mg, int from, int *zc) {
     int c = zc[l];
     for (int j = 0; j < mg.nu; ++j) {
       __syncthreads();
-      M::sweep(L, L.z[c], L.z[c ^ 1], mg.omega, t, st);
+      M::sweep(L, L.z[c], L.z[c ^ 1], mg.om[1 - (j & 1)], t, st);
       c ^= 1;
     }
     zc[l] = c;
@@ -304,7 +306,7 @@ __device__ bool mg_vcycle(const MgDev &mg, const MgDev &mgs, bool staged, int *z
     const int sweeps = coarsest ? mg.nuc : mg.nu;
     int c = 0;
     for (int j = 1; j < sweeps; ++j) {
-      M::sweep(L, L.z[c], L.z[c ^ 1], mg.omega, first, step);
+      M::sweep(L, L.z[c], L.z[c ^ 1], coarsest ? mg.omega : mg.om[j & 1], first, step);
       c ^= 1;
       if (!grid_sync(bar)) return false;
     }
@@ -312,7 +314,7 @@ __device__ bool mg_vcycle(const MgDev &mg, const MgDev &mgs, bool staged, int *z
     if (coarsest) break;
     M::residual(L, L.z[c], first, step);
     if (!grid_sync(bar)) return false;
-    M::restrict_(L, mg.lv[l + 1], mg.omega, first, step);
+    M::restrict_(L, mg.lv[l + 1], l + 1 == mg.L - 1 ? mg.omega : mg.om[0], first, step);
     if (!grid_sync(bar)) return false;
   }
   if (Lg < mg.L) {   // the other blocks know the block-run levels' final buffers (fixed)
@@ -328,7 +330,7 @@ __device__ bool mg_vcycle(const MgDev &mg, const MgDev &mgs, bool staged, int *z
     if (!grid_sync(bar)) return false;
     int c = zc[l];
     for (int j = 0; j < mg.nu; ++j) {
-      M::sweep(L, L.z[c], L.z[c ^ 1], mg.omega, first, step);
+      M::sweep(L, L.z[c], L.z[c ^ 1], mg.om[1 - (j & 1)], first, step);
       c ^= 1;
       if (l > 0 || j + 1 < mg.nu)
         if (!grid_sync(bar)) return false;
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg_mg(const MgDev *mgp, MgCg C) {
         C.p[0][k] = 0.0;
         const float bf = (float)rk0;
         L0.b[k] = bf;
-        L0.z[0][k] = mg.omega * L0.dinv[k] * bf;
+        L0.z[0][k] = (mg.L == 1 ? mg.omega : mg.om[0]) * L0.dinv[k] * bf;
         v[NC + sys(c)] += C.b[k] * C.b[k];
       }
     }
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg_mg(const MgDev *mgp, MgCg C) {
         C.r[k] = rk1;
         const float bf = (float)rk1;
         L0.b[k] = bf;
-        L0.z[0][k] = mg.omega * L0.dinv[k] * bf;
+        L0.z[0][k] = (mg.L == 1 ? mg.omega : mg.om[0]) * L0.dinv[k] * bf;
       }
     if (!grid_sync(C.bar)) return;
     if (!mg_vcycle<D, NPN, FULL>(mg, mgs, staged, zc, C.bar)) return;
@@ -791,6 +793,8 @@ static fo_status mg_upload(fo_ctx *ctx, fo_mg *mg, const float *W0, const float 
       break;
     }
   h.omega = omega;
+  h.om[0] = omega;
+  h.om[1] = omega;
   h.nu = 2;
   h.nuc = 16;
   h.nd = mg->nd;
