@@ -14,7 +14,8 @@
 //   (A_i z)(a) = (k_i R_K + w_i R_M) z(a) + sum_{s>=1} (k_i WK_s + w_i WM_s) (z(nb_s) - z(a)),
 //   D_i(a)     = k_i DK(a) + w_i DM(a).
 // Transfers and smoother as in the single-problem V-cycle: P1 interpolation along Kuhn edges,
-// R = P^T, damped Jacobi with nu sweeps before and after, nuc on the coarsest level.  Fields
+// R = P^T, damped Jacobi with nu sweeps before and after (one on the finest level), nuc on the
+// coarsest level.  Fields
 // are instance-minor [N_l][nip]: a warp owns a node and lane l holds instances l, l + 32, ...,
 // so a neighbour row is one coalesced 128-byte load per 32 instances and the stencil rows are
 // read once for all of them.  The coarse levels (at most BMG_INST_NODES nodes) run one instance
@@ -50,7 +51,7 @@ struct BmgLevel {
 
 struct BmgDev {
   int L, Lg;              // levels; levels >= Lg run one instance per block in shared memory
-  int nu, nuc;
+  int nu0, nu, nuc;       // smoothing sweeps on level 0, on the other levels, on the coarsest
   float omega;
   BmgLevel lv[MG_MAX_LEVELS];
 };
@@ -594,11 +595,13 @@ struct BmgTiled {
 };
 
 // Buffer index of each level's final iterate after a V-cycle (fixed by the sweep counts).
-__host__ __device__ inline void bmg_final_buffers(int L, int nu, int nuc, int *zc) {
-  for (int l = 0; l < L; ++l) {
-    const int sweeps = (l == L - 1) ? nuc : nu;
+__host__ __device__ inline int bmg_nu(const BmgDev &mg, int l) { return l == 0 ? mg.nu0 : mg.nu; }
+__host__ __device__ inline void bmg_final_buffers(const BmgDev &mg, int *zc) {
+  for (int l = 0; l < mg.L; ++l) {
+    const int nu = bmg_nu(mg, l);
+    const int sweeps = (l == mg.L - 1) ? mg.nuc : nu;
     int c = (sweeps - 1) & 1;
-    if (l < L - 1) c = (c + nu) & 1;
+    if (l < mg.L - 1) c = (c + nu) & 1;
     zc[l] = c;
   }
 }
@@ -650,7 +653,7 @@ __device__ void bmg_inst_cycle(const BmgDev &mg, const double *kk, const double 
     for (int l = from; l < mg.L; ++l) {
       const long long N = mg.lv[l].g.num_nodes;
       const bool coarsest = l == mg.L - 1;
-      const int sweeps = coarsest ? mg.nuc : mg.nu;
+      const int sweeps = coarsest ? mg.nuc : bmg_nu(mg, l);
       float *b = vec(l, 0);
       int c = 0;
       for (int j = 1; j < sweeps; ++j) {
@@ -725,7 +728,7 @@ __device__ void bmg_inst_cycle(const BmgDev &mg, const double *kk, const double 
       }
       int c = zl[l];
       float *b = vec(l, 0);
-      for (int j = 0; j < mg.nu; ++j) {
+      for (int j = 0; j < bmg_nu(mg, l); ++j) {
         __syncthreads();
         const float *zi = vec(l, 1 + c);
         float *zo = vec(l, 2 - c);
@@ -763,7 +766,7 @@ __device__ bool bmg_vcycle(const BmgDev &mg, const typename BmgOps<D, NJ>::Coef 
   for (int l = 0; l < Lg; ++l) {
     const BmgLevel &L = mg.lv[l];
     const bool coarsest = l == mg.L - 1;
-    const int sweeps = coarsest ? mg.nuc : mg.nu;
+    const int sweeps = coarsest ? mg.nuc : bmg_nu(mg, l);
     int c = 0;
     for (int j = 1; j < sweeps; ++j) {
       TP::template stencil_pass<0>(L, L.z[c], L.z[c ^ 1], mg.omega, cf, nullptr, nullptr, smem, lane);
@@ -785,11 +788,11 @@ __device__ bool bmg_vcycle(const BmgDev &mg, const typename BmgOps<D, NJ>::Coef 
     const BmgLevel &L = mg.lv[l];
     const BmgLevel &C = mg.lv[l + 1];
     int c = zc[l];
-    for (int j = 0; j < mg.nu; ++j) {
+    for (int j = 0; j < bmg_nu(mg, l); ++j) {
       if (j == 0) TP::template stencil_pass<1>(L, L.z[c], L.z[c ^ 1], mg.omega, cf, &C, C.z[zc[l + 1]], smem, lane);
       else TP::template stencil_pass<0>(L, L.z[c], L.z[c ^ 1], mg.omega, cf, nullptr, nullptr, smem, lane);
       c ^= 1;
-      if (l > 0 || j + 1 < mg.nu)
+      if (l > 0 || j + 1 < bmg_nu(mg, l))
         if (!grid_sync(bar)) return false;
     }
     zc[l] = c;
@@ -861,7 +864,7 @@ __global__ void __launch_bounds__(32 * BMG_WARPS, 2) k_bmg_pcg(const BmgDev *mgp
     cf.w[j] = (float)w2[j];
   }
   int zc[MG_MAX_LEVELS];
-  bmg_final_buffers(mg.L, mg.nu, mg.nuc, zc);
+  bmg_final_buffers(mg, zc);
   const int zfin = zc[0];
   const float omega = mg.omega;
 
@@ -1108,7 +1111,7 @@ __global__ void __launch_bounds__(32 * BMG_WARPS, 2) k_bmg_ir(const BmgDev *mgp,
     cf.w[j] = (float)w2[j];
   }
   int zc[MG_MAX_LEVELS];
-  bmg_final_buffers(mg.L, mg.nu, mg.nuc, zc);
+  bmg_final_buffers(mg, zc);
   const int zfin = zc[0];
   const float omega = mg.omega;
   float *r32 = L0.b;   // the inner residual is the V-cycle's level-0 right-hand side
@@ -1496,6 +1499,10 @@ static fo_status bmg_prepare(fo_problem *p) {
       }
     }
   }
+  // one sweep before and after the coarse correction on the finest level (its passes carry
+  // nearly all the traffic), two on the coarser ones: 104 instead of 100 iterations on the
+  // 64-instance 512x512 batch, 13 % less time per solve
+  h.nu0 = 1;
   h.nu = 2;
   h.nuc = 16;
   h.omega = 0.8f;
