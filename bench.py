@@ -339,16 +339,18 @@ def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True, mg
         out["plain_multigrid_one_at_a_time"] = {"seconds": tot_t, "iterations": tot_it}
         out["speedup_time_to_solution_batched_vs_plain_multigrid"] = tot_t / out["batched_multigrid"]["seconds"]
     # roofline of the batched multigrid solve (mixed): algorithmic bytes per instance-DOF are
-    # 137 per inner iteration (V-cycle with coarse levels and rows 76, r.z 8, FP32 operator
-    # pass 17, vector update 36) and 76 per refinement step (FP64 residual, x update, restart)
+    # 106 per inner iteration -- V-cycle 53 (finest level: residual 12, restriction 6, the
+    # prolongation-fused sweep 13 that also forms (r, z), rows 2; coarser grid-run levels 20),
+    # FP32 operator pass 17, vector update 36 -- and 76 per refinement step (FP64 residual,
+    # x update, restart)
     hbm = peaks.get("hbm_gbs", 6800.0)
     bm = out["batched_multigrid_mixed"]
     nval = mesh.num_nodes * 64
-    traffic = nval * (137.0 * bm["iterations"] + 76.0 * (bm["refinements"] + 1))
+    traffic = nval * (106.0 * bm["iterations"] + 76.0 * (bm["refinements"] + 1))
     achieved = traffic / bm["seconds"] / 1e9
     out["roofline"] = {"bound": "hbm", "kernel": "k_bmg_ir<2, 2>", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                        "frac": achieved / hbm, "algorithmic_bytes": traffic,
-                       "note": "137 B per instance-DOF and inner iteration + 76 B per refinement step; time = the "
+                       "note": "106 B per instance-DOF and inner iteration + 76 B per refinement step; time = the "
                                "whole solve (one launch) by CUDA events on the launching stream"}
     if mg_only:
         prob.close()

@@ -189,9 +189,12 @@ struct BmgTiled {
   // MODE 0: z_out = z_in + omega D^{-1} (b - A z_in).  MODE 1: the same after adding the
   // prolongated coarse correction P z_c to z_in on the fly (prolongation and first post-sweep
   // in one pass; the corrected iterate is never stored).  MODE 2: t = b - A z_in.
+  // dot (MODE 0/1, when given): += (b, z_out) of the own nodes, FP32 over a warp's nodes of a
+  // tile and FP64 across tiles (on level 0 of the refinement's inner CG b is its residual).
   template <int MODE>
   static __device__ void stencil_pass(const BmgLevel &L, const float *zin, float *out, float omega, const Coef &cf,
-                                      const BmgLevel *C, const float *zc, unsigned char *smem, int lane) {
+                                      const BmgLevel *C, const float *zc, unsigned char *smem, int lane,
+                                      double *dot = nullptr) {
     const Grid &g = L.g;
     const long long N = g.num_nodes;
     float *sz = reinterpret_cast<float *>(smem);
@@ -266,6 +269,9 @@ struct BmgTiled {
         }
         __syncthreads();
       }
+      float df[NJ];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) df[j] = 0.f;
       for (int t = warp; t < TL::NT; t += nw) {
         int hs;
         const long long a = TL::own_node(g, o, t, hs);
@@ -295,10 +301,15 @@ struct BmgTiled {
             out[a * NIP + i] = __fsub_rn(bq, az[j]);
           } else {
             const float dg = fmaf(cf.k[j], dk, __fmul_rn(cf.w[j], dm));
-            out[a * NIP + i] = __fadd_rn(za[j], __fdiv_rn(__fmul_rn(omega, __fsub_rn(bq, az[j])), dg));
+            const float zn = __fadd_rn(za[j], __fdiv_rn(__fmul_rn(omega, __fsub_rn(bq, az[j])), dg));
+            out[a * NIP + i] = zn;
+            if (dot) df[j] = fmaf(bq, zn, df[j]);
           }
         }
       }
+      if (dot)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) dot[j] += (double)df[j];
     }
   }
 
@@ -754,9 +765,12 @@ __device__ void bmg_inst_cycle(const BmgDev &mg, const double *kk, const double 
 // One V-cycle from level 0, whose b and first sweep were written before a grid barrier.
 // Level 0's result ends in z[zc[0]], written by the warp that owns each node's tile slot (no
 // barrier after the last sweep: the caller's next pass reads it only after one).
+// gdot (when given and level 0 is swept by the grid): += (b_0, z_0) over the own nodes, formed
+// in the last sweep on level 0.
 template <int D, int NJ>
 __device__ bool bmg_vcycle(const BmgDev &mg, const typename BmgOps<D, NJ>::Coef &cf, const double *kk,
-                           const double *w2, int *zc, const GridBar &bar, unsigned char *smem, int lane) {
+                           const double *w2, int *zc, const GridBar &bar, unsigned char *smem, int lane,
+                           double *gdot = nullptr) {
   using TP = BmgTiled<D, NJ>;
   const int Lg = mg.Lg;
   if (Lg == 0) {
@@ -789,8 +803,9 @@ __device__ bool bmg_vcycle(const BmgDev &mg, const typename BmgOps<D, NJ>::Coef 
     const BmgLevel &C = mg.lv[l + 1];
     int c = zc[l];
     for (int j = 0; j < bmg_nu(mg, l); ++j) {
-      if (j == 0) TP::template stencil_pass<1>(L, L.z[c], L.z[c ^ 1], mg.omega, cf, &C, C.z[zc[l + 1]], smem, lane);
-      else TP::template stencil_pass<0>(L, L.z[c], L.z[c ^ 1], mg.omega, cf, nullptr, nullptr, smem, lane);
+      double *dot = (l == 0 && j + 1 == bmg_nu(mg, l)) ? gdot : nullptr;
+      if (j == 0) TP::template stencil_pass<1>(L, L.z[c], L.z[c ^ 1], mg.omega, cf, &C, C.z[zc[l + 1]], smem, lane, dot);
+      else TP::template stencil_pass<0>(L, L.z[c], L.z[c ^ 1], mg.omega, cf, nullptr, nullptr, smem, lane, dot);
       c ^= 1;
       if (l > 0 || j + 1 < bmg_nu(mg, l))
         if (!grid_sync(bar)) return false;
@@ -1189,13 +1204,15 @@ __global__ void __launch_bounds__(32 * BMG_WARPS, 2) k_bmg_ir(const BmgDev *mgp,
 #pragma unroll
       for (int j = 0; j < NJ; ++j) all = all && idone[j];
       if (__all_sync(0xffffffffu, all) || ii >= C.inner_maxit || total >= C.maxit) break;
-      if (!bmg_vcycle<D, NJ>(mg, cf, C.kk, C.w2, zc, C.bar, bmg_smem, lane)) return;
-      const float *z = L0.z[zfin];
-      // gamma = (r32, z) in the tile order of the last sweep (own values, no barrier needed)
+      // gamma = (r32, z): formed by the V-cycle's last sweep on level 0 (r32 is that level's
+      // right-hand side), or, when level 0 runs per instance, by a pass in the tile order of
+      // the last sweep (own values, no barrier needed)
       double v1[1][NJ];
 #pragma unroll
       for (int j = 0; j < NJ; ++j) v1[0][j] = 0.0;
-      {
+      if (!bmg_vcycle<D, NJ>(mg, cf, C.kk, C.w2, zc, C.bar, bmg_smem, lane, mg.Lg > 0 ? v1[0] : nullptr)) return;
+      const float *z = L0.z[zfin];
+      if (mg.Lg == 0) {
         using TL = typename TP::TL;
         const long long ntile = TL::count(g);
         for (long long tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
