@@ -42,10 +42,13 @@ fo_status fo_alloc(fo_ctx *ctx, void **p, size_t bytes) {
   if (ctx->budget && ctx->in_use + bytes > ctx->budget)
     return fo_fail(ctx, FO_ENOMEM_BUDGET, "allocation of %zu bytes exceeds the budget (%zu of %zu in use)",
                    bytes, ctx->in_use, ctx->budget);
-  cudaError_t e = cudaMalloc(p, bytes);
+  // stream-ordered: neither the allocation nor the matching free synchronises the device,
+  // so contexts on other streams (the request server's executors) are not stalled; all of a
+  // context's work runs on its stream, where the memory is valid from this point on
+  cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
   if (e != cudaSuccess) {
     *p = nullptr;
-    return fo_cuda_check(ctx, e, "cudaMalloc");
+    return fo_cuda_check(ctx, e, "cudaMallocAsync");
   }
   ctx->in_use += bytes;
   return FO_OK;
@@ -53,7 +56,7 @@ fo_status fo_alloc(fo_ctx *ctx, void **p, size_t bytes) {
 
 void fo_free(fo_ctx *ctx, void *p, size_t bytes) {
   if (!p) return;
-  cudaFree(p);
+  cudaFreeAsync(p, ctx->stream);
   ctx->in_use -= std::min(ctx->in_use, bytes);
 }
 
