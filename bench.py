@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--l2-flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the c1 / c3 legs")
     ap.add_argument("--serving-requests", type=int, default=12)
     ap.add_argument("--batch-n", type=int, default=512, help="cells per axis of the batch mesh")
     ap.add_argument("--batch-maxit", type=int, default=400000, help="cap on batched iterations (profiling runs)")
@@ -395,6 +396,68 @@ def mg_state_bytes_per_iteration(nx, ny, c):
     return float(total)
 
 
+# ------------------------------------------------------------------- c1 and c3 legs
+def bench_configs(api, ctx, stream):
+    """Latency of one Algorithm-1 step on the 64x64 heat problem (c1) and, on the 3D cantilever
+    96x48x48 (c3), the multigrid state solve to 1e-8 and one full optimisation iteration."""
+    import numpy as np
+    import torch
+    from paper_2601_05709_gb300 import workloads
+
+    def timed(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = [fn(i) for i in range(reps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    mg = api.FO_PC_MG
+    ro = api.run_options(state=api.solve_opts(rtol=1e-12, warm_start=1, precond=mg),
+                         velocity=api.solve_opts(rtol=1e-12, warm_start=1, precond=mg))
+    out = {}
+    # c1: heat, f = 1, Dirichlet x = 0, velocity alpha = 0.01 on H^1_0, transport dfactor 1e-2
+    mesh = ctx.mesh_box(2, (64, 64), (0.0, 0.0), (1.0, 1.0))
+    _, coords = mesh.copy_out()
+    prob = mesh.problem(api.model_desc(api.FO_HEAT, dirichlet=[(0, 0)], f_nodal=np.ones(mesh.num_nodes),
+                                       alpha_mass=0.01, velocity_dirichlet=True))
+    prob.set_levelset(workloads.phi_cos(coords))
+    for i in range(3):
+        prob.opt_step(i, ro)
+    ms, logs = timed(lambda i: prob.opt_step(3 + i, ro), 10)
+    out["c1"] = {"workload": "heat compliance on a 64x64 Kuhn mesh of the unit square (8,192 triangles), "
+                             "phi0 = cos 4pi x cos 4pi y + 0.3, multigrid state and velocity",
+                 "ms_per_opt_step": ms, "opt_iters_per_s": 1e3 / ms,
+                 "state_iterations": float(np.mean([l.state.iterations for l in logs]))}
+    prob.close()
+    # c3: 3D elasticity cantilever, 20 Gaussian bumps
+    mesh = ctx.mesh_box(3, (96, 48, 48), (0.0, 0.0, 0.0), (2.0, 1.0, 1.0))
+    _, coords = mesh.copy_out()
+    prob = mesh.problem(api.model_desc(api.FO_ELASTIC, dirichlet=[(0, 0)], tractions=[(0, 1, (0.0, 0.0, -1.0))],
+                                       volume=1.0, alpha_mass=0.1, normal_penalty=1e4, omega0_weight=1e4,
+                                       omega0_boxes=[((1.90, 0.35, 0.35), (float("inf"), 0.65, 0.65))]))
+    phi = workloads.phi_bumps(coords, workloads.bump_centres((0, 0, 0), (2, 1, 1), 20, seed=0), 0.1, 0.2)
+    prob.set_levelset(phi)
+    prob.coefficients()
+    so = api.solve_opts(rtol=1e-8, precond=mg)
+    prob.state_solve(so)                                  # builds the hierarchy
+    ms_s, sts = timed(lambda i: prob.state_solve(so), 3)
+    ndof = 3 * mesh.num_nodes
+    it = sts[-1].iterations
+    ro3 = api.run_options(state=api.solve_opts(rtol=1e-8, warm_start=1, precond=mg),
+                          velocity=api.solve_opts(rtol=1e-8, warm_start=1, precond=mg))
+    prob.opt_step(0, ro3)
+    ms_o, logs = timed(lambda i: prob.opt_step(1 + i, ro3), 2)
+    out["c3"] = {"workload": "3D elasticity cantilever on a 96x48x48 Kuhn mesh of (0,2)x(0,1)^2 (1,327,104 tets, "
+                             f"{ndof} DOFs), 20 Gaussian bumps, traction (0,0,-1) on x = 2",
+                 "state_solve_ms": ms_s, "state_iterations": it, "state_rel_residual": sts[-1].rel_residual,
+                 "state_gdof_iters_per_s": ndof * it / (ms_s / 1e3) / 1e9,
+                 "ms_per_opt_step": ms_o, "opt_step_state_iterations": logs[-1].state.iterations}
+    prob.close()
+    return out
+
+
 # ---------------------------------------------------------------------- serving (c5)
 def serving_stream(count, seed=2):
     import numpy as np
@@ -638,6 +701,8 @@ def main():
                        "h2d_bytes_per_step": 8 * mesh2.num_nodes, "d2h_bytes_per_step": 8 * mesh2.num_nodes}
     if rank == 0 and not args.no_batch:
         line["batch"] = bench_batch(api, ctx, stream, peaks, args.batch_n, args.batch_maxit)
+    if rank == 0 and not args.no_configs:
+        line["configs"] = bench_configs(api, ctx, stream)
     if rank == 0 and not args.no_serving:
         line["serving"] = bench_serving(api, ctx, args.serving_requests)
     if cpu is not None:
