@@ -364,14 +364,19 @@ __device__ __forceinline__ bool arnoldi_dispatch(int j, const Grid &g, const dou
 
 // Solve M x = rhs (x holds the start value).  When Rm is given, the first residual pass
 // also forms rhs = Rm x (the transport's right-hand side R phi^n, gathered from the same
-// x before it changes).  With prev given (a sequence of solves, x = phi^n, prev = phi^{n-1}),
-// the solve starts from the linear extrapolation 2 phi^n - phi^{n-1} when extrap, else from
-// phi^n, and leaves phi^n in prev for the next one.  Returns the number of Arnoldi steps;
-// err / ok report failures.
+// x before it changes).  With prev given (a sequence of solves, x = phi^n, prev = phi^{n-1},
+// prev2 = phi^{n-2}), the solve starts from the polynomial extrapolation of order `order`
+// (0: phi^n; 1: 2 phi^n - phi^{n-1}; 2: 3 phi^n - 3 phi^{n-1} + phi^{n-2}) and shifts the
+// history for the next one.  Returns the number of Arnoldi steps; err / ok report failures.
 template <int D>
 __device__ int gmres_solve(const Grid &g, const double *M, const double *dinv, const double *Rm, double *x,
                            KrylovBufs K, double rtol2, int maxit, GmresShared &sh, double *partials, int &rk,
-                           const GridBar &bar, int *err, bool *ok, double *prev = nullptr, bool extrap = false) {
+                           const GridBar &bar, int *err, bool *ok, double *prev = nullptr, double *prev2 = nullptr,
+                           int order = 0) {
+  auto start = [&](long long k) {
+    const double xv = x[k];
+    return order == 0 ? xv : (order == 1 ? 2.0 * xv - prev[k] : 3.0 * (xv - prev[k]) + prev2[k]);
+  };
   const long long N = g.num_nodes;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long gs = (long long)gridDim.x * blockDim.x;
@@ -394,12 +399,12 @@ __device__ int gmres_solve(const Grid &g, const double *M, const double *dinv, c
           if (nb >= 0) {
             const double xv = x[nb];
             ra += Rm[s * N + a] * xv;
-            la += M[s * N + a] * (extrap ? 2.0 * xv - prev[nb] : xv);
+            la += M[s * N + a] * (order == 0 ? xv : start(nb));
           }
         }
         K.rhs[a] = ra;
         ra = ra - la;
-        if (prev) K.w[a] = extrap ? 2.0 * x[a] - prev[a] : x[a];   // the start value
+        if (prev) K.w[a] = start(a);   // the start value
       } else {
         double la = 0.0;
 #pragma unroll
@@ -420,6 +425,7 @@ __device__ int gmres_solve(const Grid &g, const double *M, const double *dinv, c
     const bool conv = rr <= rtol2 * bb;
     if (cycle == 0 && Rm && prev) {   // x <- the start value, prev <- phi^n (own nodes)
       for (long long a = tid; a < N; a += gs) {
+        prev2[a] = prev[a];
         prev[a] = x[a];
         x[a] = K.w[a];
       }
@@ -479,7 +485,7 @@ struct TransportArgs {
   KrylovBufs K;
   const double *L, *R, *dinv;
   double *phi;
-  double *prev;          // the previous substep's level set (start-value extrapolation)
+  double *prev, *prev2;  // the two previous substeps' level sets (start-value extrapolation)
   double rtol2;
   int maxit, nsteps;
   double *partials;
@@ -493,10 +499,11 @@ __global__ void __launch_bounds__(FO_BLOCK) k_transport_run(Grid g, TransportArg
   int rk = 0, err = DEV_OK, total = 0;
   bool ok = true;
   for (int step = 0; step < A.nsteps && err == DEV_OK; ++step) {
-    // L phi^{n+1} = R phi^n, started from phi^n (first substep) or from the linear
-    // extrapolation 2 phi^n - phi^{n-1}; rhs is formed in the first residual pass
+    // L phi^{n+1} = R phi^n, started from phi^n (first substep), then from the linear and
+    // the quadratic extrapolation of the previous level sets; rhs is formed in the first
+    // residual pass
     total += gmres_solve<D>(g, A.L, A.dinv, A.R, A.phi, A.K, A.rtol2, A.maxit, sh, A.partials, rk, A.bar, &err, &ok,
-                            A.prev, step > 0);
+                            A.prev, A.prev2, step < 2 ? step : 2);
     if (!ok) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -548,7 +555,8 @@ fo_status fo_transport_run(fo_problem *p, int nsteps, const fo_solve_opts *o, fo
   const Grid &g = p->mesh->g;
   const long long N = g.num_nodes;
   TransportArgs A{};
-  FO_TRY(krylov_bufs(p, 1, &A.K, &A.prev));
+  FO_TRY(krylov_bufs(p, 2, &A.K, &A.prev));
+  A.prev2 = A.prev + N;
   A.L = p->L;
   A.R = p->R;
   A.dinv = p->dinvL;
