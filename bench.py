@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--l2-flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--no-configs", action="store_true", help="skip the c1 / c3 legs")
+    ap.add_argument("--no-configs", action="store_true", help="skip the 64x64 heat and 3D cantilever legs")
     ap.add_argument("--serving-requests", type=int, default=12)
     ap.add_argument("--batch-n", type=int, default=512, help="cells per axis of the batch mesh")
     ap.add_argument("--batch-maxit", type=int, default=400000, help="cap on batched iterations (profiling runs)")
@@ -228,7 +228,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-# ------------------------------------------------------------------------ batch (c4)
+# --------------------------------------------- batch: 64 screened Helmholtz instances
 BATCH_N, BATCH_INST = 512, 64
 
 
@@ -396,10 +396,10 @@ def mg_state_bytes_per_iteration(nx, ny, c):
     return float(total)
 
 
-# ------------------------------------------------------------------- c1 and c3 legs
+# ------------------------------------------- 64x64 heat and 3D cantilever legs
 def bench_configs(api, ctx, stream):
-    """Latency of one Algorithm-1 step on the 64x64 heat problem (c1) and, on the 3D cantilever
-    96x48x48 (c3), the multigrid state solve to 1e-8 and one full optimisation iteration."""
+    """Latency of one Algorithm-1 step on the 64x64 heat problem and, on the 3D cantilever
+    96x48x48, the multigrid state solve to 1e-8 and one full optimisation iteration."""
     import numpy as np
     import torch
     from paper_2601_05709_gb300 import workloads
@@ -417,7 +417,7 @@ def bench_configs(api, ctx, stream):
     ro = api.run_options(state=api.solve_opts(rtol=1e-12, warm_start=1, precond=mg),
                          velocity=api.solve_opts(rtol=1e-12, warm_start=1, precond=mg))
     out = {}
-    # c1: heat, f = 1, Dirichlet x = 0, velocity alpha = 0.01 on H^1_0, transport dfactor 1e-2
+    # heat, f = 1, Dirichlet x = 0, velocity alpha = 0.01 on H^1_0, transport dfactor 1e-2
     mesh = ctx.mesh_box(2, (64, 64), (0.0, 0.0), (1.0, 1.0))
     _, coords = mesh.copy_out()
     prob = mesh.problem(api.model_desc(api.FO_HEAT, dirichlet=[(0, 0)], f_nodal=np.ones(mesh.num_nodes),
@@ -426,12 +426,12 @@ def bench_configs(api, ctx, stream):
     for i in range(3):
         prob.opt_step(i, ro)
     ms, logs = timed(lambda i: prob.opt_step(3 + i, ro), 10)
-    out["c1"] = {"workload": "heat compliance on a 64x64 Kuhn mesh of the unit square (8,192 triangles), "
+    out["heat2d_64x64"] = {"workload": "heat compliance on a 64x64 Kuhn mesh of the unit square (8,192 triangles), "
                              "phi0 = cos 4pi x cos 4pi y + 0.3, multigrid state and velocity",
                  "ms_per_opt_step": ms, "opt_iters_per_s": 1e3 / ms,
                  "state_iterations": float(np.mean([l.state.iterations for l in logs]))}
     prob.close()
-    # c3: 3D elasticity cantilever, 20 Gaussian bumps
+    # 3D elasticity cantilever, 20 Gaussian bumps
     mesh = ctx.mesh_box(3, (96, 48, 48), (0.0, 0.0, 0.0), (2.0, 1.0, 1.0))
     _, coords = mesh.copy_out()
     prob = mesh.problem(api.model_desc(api.FO_ELASTIC, dirichlet=[(0, 0)], tractions=[(0, 1, (0.0, 0.0, -1.0))],
@@ -449,7 +449,7 @@ def bench_configs(api, ctx, stream):
                           velocity=api.solve_opts(rtol=1e-8, warm_start=1, precond=mg))
     prob.opt_step(0, ro3)
     ms_o, logs = timed(lambda i: prob.opt_step(1 + i, ro3), 2)
-    out["c3"] = {"workload": "3D elasticity cantilever on a 96x48x48 Kuhn mesh of (0,2)x(0,1)^2 (1,327,104 tets, "
+    out["cantilever3d_96x48x48"] = {"workload": "3D elasticity cantilever on a 96x48x48 Kuhn mesh of (0,2)x(0,1)^2 (1,327,104 tets, "
                              f"{ndof} DOFs), 20 Gaussian bumps, traction (0,0,-1) on x = 2",
                  "state_solve_ms": ms_s, "state_iterations": it, "state_rel_residual": sts[-1].rel_residual,
                  "state_gdof_iters_per_s": ndof * it / (ms_s / 1e3) / 1e9,
@@ -458,7 +458,7 @@ def bench_configs(api, ctx, stream):
     return out
 
 
-# ---------------------------------------------------------------------- serving (c5)
+# ----------------------------------------------------- serving: stream of requests
 def serving_stream(count, seed=2):
     import numpy as np
     rng = np.random.default_rng(seed)
