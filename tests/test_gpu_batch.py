@@ -168,6 +168,19 @@ def test_batch_state_multigrid_parity(ctx, name, precision):
     assert rel(prob.get(FO_FIELD_U), U) <= 1e2 * rtol
 
 
+def test_batch_multigrid_falls_back_on_odd_grids(ctx):
+    """A 17x13 grid cannot be halved: asking for multigrid runs the Jacobi batch, with the
+    same solution and the same iteration counts as asking for it directly."""
+    c, ob, prob, phi = _setup(ctx, "2d_40")
+    st_mg = prob.state_solve(api.solve_opts(rtol=1e-12, precond=api.FO_PC_MG))
+    U_mg = prob.get(FO_FIELD_U)
+    its_mg, _ = prob.batch_solve_info()
+    st_j = prob.state_solve(api.solve_opts(rtol=1e-12))
+    its_j, res = prob.batch_solve_info()
+    assert np.array_equal(prob.get(FO_FIELD_U), U_mg) and np.array_equal(its_mg, its_j)
+    assert st_mg.iterations == st_j.iterations and np.all(res <= 1e-10)
+
+
 @pytest.mark.parametrize("precision", [api.FO_FP64, api.FO_MIXED])
 def test_batch_multigrid_instance_equals_alone(ctx, precision):
     """An instance's multigrid-preconditioned solve in the batch and alone give the same bits."""

@@ -196,6 +196,21 @@ def test_state_solve_fp64(ctx, api, c, pc):
     assert abs(C - C_ref) <= 1e-13 * abs(C_ref)
 
 
+def test_multigrid_falls_back_on_odd_grids(ctx, api):
+    """A 63x63 heat grid cannot be halved: asking for multigrid runs the Jacobi-PCG, bit for
+    bit."""
+    c = case(**dict(HEAT2D, n=(63, 63)))
+    op = oracle_problem(c)
+    phi = workloads.phi_cos(op.mesh.coords)
+    out = []
+    for pc in (1, 0):
+        mesh, prob = gpu_problem(ctx, c)
+        prob.set_levelset(phi)
+        st = prob.state_solve(tight(api, precond=pc))
+        out.append((st.iterations, prob.get(api._lib.FO_FIELD_U)))
+    assert out[0][0] == out[1][0] and np.array_equal(out[0][1], out[1][1])
+
+
 @pytest.mark.parametrize("c", [case(**HEAT2D), cantilever2d((128, 64)), cantilever3d((12, 6, 6))])
 def test_state_solve_mixed(ctx, api, c):
     mesh, prob = gpu_problem(ctx, c)
