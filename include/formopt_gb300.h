@@ -151,10 +151,15 @@ typedef struct {
   double inner_rtol;        /* FO_MIXED: relative reduction asked of each FP32 solve    */
   int inner_maxit;          /* FO_MIXED: cap per FP32 solve                             */
   int grid_blocks;          /* 0 = autotuned; else blocks of the persistent kernel      */
-  int precond;              /* FO_PC_JACOBI, or FO_PC_MG: FP64 CG with an FP32 geometric- */
-                            /* multigrid V-cycle as preconditioner (state and velocity  */
-                            /* solves of single problems, on grids that halve down to a */
-                            /* coarsest level of <= 8192 unknowns; else Jacobi)         */
+  int precond;              /* FO_PC_JACOBI, or FO_PC_MG: an FP32 geometric-multigrid   */
+                            /* V-cycle as preconditioner, on grids that halve at least  */
+                            /* once down to a coarsest level of <= 8192 unknowns (else  */
+                            /* the Jacobi solver runs).  Single problems (state,        */
+                            /* adjoint, velocity): FP64 CG whatever the precision.      */
+                            /* Batches (state, adjoint): FO_FP64 -> FP64 CG; FO_MIXED -> */
+                            /* FP64 refinement around an FP32 CG (inner_rtol,           */
+                            /* inner_maxit per refinement step), stopping an instance   */
+                            /* also when a step fails to halve its true residual.       */
 } fo_solve_opts;
 
 #define FO_PC_JACOBI 0
@@ -311,7 +316,8 @@ FO_API fo_status fo_batch_costs(fo_problem *prob, double *J_inst);
  * refinement steps, and the final FP64 relative residual ||b_i - K_i x_i|| / ||b_i||. */
 FO_API fo_status fo_batch_solve_info(fo_problem *prob, int *inst_iters, double *inst_res);
 
-/* Launch shape of the batched persistent solver. */
+/* Launch shape of the batched Jacobi solver (FO_PC_JACOBI; the batched multigrid uses two
+ * blocks of 256 threads per SM). */
 typedef struct {
   int block;                /* threads per block (a warp owns a node)                   */
   int blocks_per_sm;        /* co-resident blocks per SM; grid = blocks_per_sm * SMs   */
