@@ -41,6 +41,7 @@
 
 #define BMG_WARPS 8              // warps per block
 #define BMG_INST_NODES 1100      // levels of at most this many nodes run one instance per block
+#define BMG_DIRECT_MAX 64        // coarsest levels of at most this many nodes are solved exactly
 
 struct BmgLevel {
   Grid g;
@@ -52,6 +53,9 @@ struct BmgLevel {
 struct BmgDev {
   int L, Lg;              // levels; levels >= Lg run one instance per block in shared memory
   int nu0, nu, nuc;       // smoothing sweeps on level 0, on the other levels, on the coarsest
+  int nd;                 // > 0: the coarsest level (nd nodes) is solved with the instance's
+  const float *ainv;      // inverse of its operator, ainv[i][nd][nd], where direct[i] is set
+  const int *direct;
   float omega;
   BmgLevel lv[MG_MAX_LEVELS];
 };
@@ -667,6 +671,19 @@ __device__ void bmg_inst_cycle(const BmgDev &mg, const double *kk, const double 
       const int sweeps = coarsest ? mg.nuc : bmg_nu(mg, l);
       float *b = vec(l, 0);
       int c = 0;
+      if (coarsest && mg.nd > 0 && mg.direct[inst]) {   // exact solve, into the sweeps' last buffer
+        c = (sweeps - 1) & 1;
+        __syncthreads();
+        const float *A = mg.ainv + (size_t)inst * mg.nd * mg.nd;
+        float *zo = vec(l, 1 + c);
+        for (int a = threadIdx.x; a < mg.nd; a += blockDim.x) {
+          float acc = 0.f;
+          for (int k = 0; k < mg.nd; ++k) acc = fmaf(A[a * mg.nd + k], b[k], acc);
+          zo[a] = acc;
+        }
+        zl[l] = c;
+        break;
+      }
       for (int j = 1; j < sweeps; ++j) {
         __syncthreads();
         const float *zi = vec(l, 1 + c);
@@ -1383,6 +1400,64 @@ __global__ void k_bmg_rows(long long N, int S, const double *WK, const double *W
   }
 }
 
+// Inverse of instance i's operator k_i K + omega_i^2 M on the coarsest level (nd nodes, at most
+// BMG_DIRECT_MAX), one block per instance: the dense matrix from the level's plain FP64 rows
+// (Dirichlet rows identity, their columns eliminated), inverted in place in shared memory by
+// Gauss-Jordan elimination without pivoting (symmetric positive definite), stored in FP32.
+template <int D>
+__global__ void k_bmg_coarse_inverse(Grid g, const double *WK, const double *WM, const double *kk, const double *w2,
+                                     int nd, float *ainv, int *direct) {
+  constexpr int S = ST<D>::S;
+  __shared__ double A[BMG_DIRECT_MAX * BMG_DIRECT_MAX];
+  __shared__ double piv, dmax;
+  __shared__ int ok;
+  const int inst = blockIdx.x;
+  const double k = kk[inst], w = w2[inst];
+  for (int q = threadIdx.x; q < nd * nd; q += blockDim.x) A[q] = 0.0;
+  __syncthreads();
+  for (long long a = threadIdx.x; a < nd; a += blockDim.x) {
+    int idx[3];
+    node_ijk(g, a, idx);
+    for (int s = 0; s < S; ++s) {
+      const long long nb = slot_node<D>(g, idx, a, s);
+      if (nb < 0) continue;
+      A[a * nd + nb] += fma(k, WK[a * S + s], w * WM[a * S + s]);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    dmax = 0.0;
+    for (int a = 0; a < nd; ++a) dmax = fmax(dmax, fabs(A[a * nd + a]));
+    ok = 1;
+  }
+  for (int p = 0; p < nd; ++p) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // a pivot that is not clearly positive (a singular instance: no Dirichlet node and
+      // omega = 0) leaves the instance to the Jacobi sweeps
+      const double d = A[p * nd + p];
+      if (!(d > 1e-10 * dmax)) ok = 0;
+      piv = ok ? 1.0 / d : 0.0;
+    }
+    __syncthreads();
+    const double q = piv;
+    for (int e = threadIdx.x; e < nd * nd; e += blockDim.x) {
+      const int i = e / nd, j = e - i * nd;
+      if (i != p && j != p) A[e] -= A[i * nd + p] * A[p * nd + j] * q;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nd; e += blockDim.x)
+      if (e != p) {
+        A[p * nd + e] *= q;
+        A[e * nd + p] *= -q;
+      }
+    if (threadIdx.x == 0) A[p * nd + p] = q;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nd * nd; e += blockDim.x) ainv[(size_t)inst * nd * nd + e] = ok ? (float)A[e] : 0.f;
+  if (threadIdx.x == 0) direct[inst] = ok;
+}
+
 // ===================================================================================== host
 struct fo_bmg {
   int L = 0, nip = 0, grid_cap = 0;
@@ -1395,6 +1470,9 @@ struct fo_bmg {
   double *r = nullptr, *p0 = nullptr, *p1 = nullptr, *s = nullptr, *partials = nullptr;
   double *d64 = nullptr;
   float *q0 = nullptr, *q1 = nullptr, *s32 = nullptr;
+  int nd = 0;                 // coarsest nodes when it is solved exactly
+  float *ainv = nullptr;      // [nip][nd][nd]
+  int *direct = nullptr;      // [nip]
   void *dev = nullptr;
   std::vector<unsigned char> host;
   std::vector<std::pair<void **, size_t>> allocs;
@@ -1471,6 +1549,11 @@ static fo_status bmg_alloc(fo_problem *p) {
   add((void **)&mg->s32, sizeof(float) * n0);
   add((void **)&mg->s, sizeof(double) * n0);
   add((void **)&mg->partials, sizeof(double) * (2 * nip * (size_t)mg->grid_cap + 2 * nip));
+  if (mg->L >= 2 && mg->g[mg->L - 1].num_nodes <= BMG_DIRECT_MAX) {
+    mg->nd = (int)mg->g[mg->L - 1].num_nodes;
+    add((void **)&mg->ainv, sizeof(float) * nip * mg->nd * mg->nd);
+    add((void **)&mg->direct, sizeof(int) * nip);
+  }
   add(&mg->dev, sizeof(BmgDev));
   for (auto &e : mg->allocs) FO_TRY(fo_alloc(ctx, e.first, e.second));
   return FO_OK;
@@ -1523,6 +1606,18 @@ static fo_status bmg_prepare(fo_problem *p) {
   h.nu = 2;
   h.nuc = 16;
   h.omega = 0.8f;
+  if (mg->nd > 0 && h.Lg < h.L) {   // the coarsest level runs in the per-instance cycle
+    const int L1 = mg->L - 1;
+    const double *WK = L1 == 0 ? bt->WK : mg->WK[L1], *WM = L1 == 0 ? bt->WM : mg->WM[L1];
+    if (mg->g[0].dim == 2)
+      k_bmg_coarse_inverse<2><<<bt->nip, 256, 0, s>>>(mg->g[L1], WK, WM, bt->kk, bt->w2, mg->nd, mg->ainv, mg->direct);
+    else
+      k_bmg_coarse_inverse<3><<<bt->nip, 256, 0, s>>>(mg->g[L1], WK, WM, bt->kk, bt->w2, mg->nd, mg->ainv, mg->direct);
+    fo_note_launch(1);
+    h.nd = mg->nd;
+    h.ainv = mg->ainv;
+    h.direct = mg->direct;
+  }
   for (int l = 0; l < mg->L; ++l) {
     BmgLevel &d = h.lv[l];
     d.g = mg->g[l];
