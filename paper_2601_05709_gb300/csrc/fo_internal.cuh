@@ -315,25 +315,58 @@ __device__ __forceinline__ bool grid_sync(const GridBar &b) {
 }
 
 // ---- deterministic reductions -----------------------------------------------------------
-// Block sum of NR values (fixed shuffle tree, fixed warp order); result valid in thread 0.
+// Warp reduce-scatter of C values (slots 0..C-1 of v) at exchange distance O and below.  At
+// each distance a lane keeps one half of its values (the upper half when its lane bit O is
+// set), sends the other half to its partner and adds the partner's copy of the half it kept:
+// ceil(C/2) FP64 adds per level instead of C for a plain shuffle tree, which matters where
+// the FP64 pipe is narrow.  An odd middle slot is kept by both partners (a + b and b + a:
+// the same bits).  src(p, lane) is the value that slot p holds after all levels.
+template <int NR, int C, int O>
+struct WarpScatter {
+  static constexpr int HC = (C + 1) / 2;
+  using Next = WarpScatter<NR, HC, O / 2>;
+  static constexpr int CF = Next::CF;   // slots left after all levels
+  static __device__ __forceinline__ void run(double (&v)[NR], int lane) {
+    const bool up = (lane & O) != 0;
+#pragma unroll
+    for (int i = 0; i < C - HC; ++i) {
+      const double send = up ? v[i] : v[i + HC];
+      const double keep = up ? v[i + HC] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+    }
+    if (C & 1) v[HC - 1] += __shfl_xor_sync(0xffffffffu, v[HC - 1], O);
+    Next::run(v, lane);
+  }
+  static __device__ __forceinline__ int src(int p, int lane) {
+    const int q = Next::src(p, lane);   // the slot of this level's output
+    return (q < C - HC && (lane & O)) ? q + HC : q;
+  }
+};
+template <int NR, int C>
+struct WarpScatter<NR, C, 0> {
+  static constexpr int CF = C;
+  static __device__ __forceinline__ void run(double (&)[NR], int) {}
+  static __device__ __forceinline__ int src(int p, int) { return p; }
+};
+
+// Block sum of NR values (fixed exchange pattern, fixed warp order); result valid in thread 0.
 template <int NR>
 __device__ __forceinline__ void block_sum(double (&v)[NR], double *smem /* [32*NR] */) {
-#pragma unroll
-  for (int j = 0; j < NR; ++j)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  using WS = WarpScatter<NR, NR, 16>;
+  WS::run(v, lane);
   __syncthreads();
-  if (lane == 0)
+  // every lane holding a value writes it; lanes that hold the same value hold the same bits
 #pragma unroll
-    for (int j = 0; j < NR; ++j) smem[warp * NR + j] = v[j];
+  for (int k = 0; k < WS::CF; ++k) smem[warp * NR + WS::src(k, lane)] = v[k];
   __syncthreads();
   // value j is finished by warp j mod nw (the values proceed in parallel); its result goes
   // to smem[j], a slot only that warp reads
+  int top = 1;
+  while (top < nw) top <<= 1;
   for (int j = warp; j < NR; j += nw) {
     double t = (lane < nw) ? smem[lane * NR + j] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    for (int o = top >> 1; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
     if (lane == 0) smem[j] = t;
   }
   __syncthreads();

@@ -227,6 +227,8 @@ struct GmresShared {
   double H[(GM_M + 1) * GM_M];   // column-major: H[j * (GM_M + 1) + i]
   double cs[GM_M], sn[GM_M], g[GM_M + 1], y[GM_M];
   int rotated;                   // the step's column is already rotated into H
+  double scal[2];                // a step's |w - V h| and its inverse (thread 0 forms them)
+  int onepass;                   // the step takes one Gram-Schmidt pass
 };
 
 // Thread 0: apply the previous rotations to column j (col[0..j+1]), form the new one, update
@@ -282,16 +284,25 @@ __device__ bool arnoldi_step(const Grid &g, const double *M, const double *dinv,
     h1[J + 1] += wa * wa;
   }
   if (!ls_reduce<J + 2>(h1, sh.sred, sh.stot, partials, rk, bar)) return false;
-  double hc[J + 1], hh = 0.0;
+  // the step's scalars once per block (the FP64 pipe is narrow: 256 threads forming the same
+  // square root and quotient cost more than the pass over the vectors)
+  if (threadIdx.x == 0) {
+    double hh = 0.0;
 #pragma unroll
-  for (int i = 0; i <= J; ++i) {
-    hc[i] = sh.stot[i];
-    hh += hc[i] * hc[i];
+    for (int i = 0; i <= J; ++i) hh += sh.stot[i] * sh.stot[i];
+    const double ww = sh.stot[J + 1], wp2 = ww - hh;
+    sh.onepass = wp2 >= GM_ONEPASS * ww;
+    const double hn = sh.onepass ? sqrt(wp2) : 0.0;
+    sh.scal[0] = hn;
+    sh.scal[1] = hn > 0.0 ? 1.0 / hn : 0.0;
   }
-  const double ww = sh.stot[J + 1], wp2 = ww - hh;
-  if (wp2 >= GM_ONEPASS * ww) {   // one pass: v_{J+1} = (w - V h) / |w - V h|
-    const double hnext = sqrt(wp2);
-    const double inv = hnext > 0.0 ? 1.0 / hnext : 0.0;
+  __syncthreads();
+  double hc[J + 1];
+#pragma unroll
+  for (int i = 0; i <= J; ++i) hc[i] = sh.stot[i];
+  if (sh.onepass) {   // one pass: v_{J+1} = (w - V h) / |w - V h|
+    const double hnext = sh.scal[0];
+    const double inv = sh.scal[1];
     double *Vn = K.V + (size_t)(J + 1) * N;
     if (threadIdx.x == 0) {   // the column is final: rotate it now, overlapping the pass below
       double col[J + 2];
@@ -433,12 +444,15 @@ __device__ int gmres_solve(const Grid &g, const double *M, const double *dinv, c
     }
     if (conv) return total;
     if (total >= maxit) { *err = DEV_NOCONV; return total; }
-    const double beta = sqrt(rr);
-    for (long long a = tid; a < N; a += gs) K.V[a] /= beta;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {   // beta = |r| and its inverse, once per block
+      const double beta = sqrt(rr);
       sh.g[0] = beta;
+      sh.scal[1] = 1.0 / beta;
       for (int i = 1; i <= GM_M; ++i) sh.g[i] = 0.0;
     }
+    __syncthreads();
+    const double ib = sh.scal[1];
+    for (long long a = tid; a < N; a += gs) K.V[a] *= ib;
     if (!grid_sync(bar)) { *ok = false; return total; }
     int j = 0;
     bool done = false;

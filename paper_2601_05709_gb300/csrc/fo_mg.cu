@@ -357,12 +357,13 @@ __host__ __device__ inline void mg_final_buffers(int L, int Lg, int nu, int nuc,
 // component, DOF k belonging to system k % NC); the loop stops when the summed residual meets
 // rtol.  Ends with the dot product b . x (for B(theta, theta) of the velocity solve).
 template <int D, int NPN, bool FULL, int NC>
-__global__ void __launch_bounds__(FO_BLOCK) k_pcg_mg(const MgDev *mgp, MgCg C) {
+__global__ void __launch_bounds__(FO_BLOCK, D == 2 ? 1 : 2) k_pcg_mg(const MgDev *mgp, MgCg C) {
   extern __shared__ __align__(16) unsigned char mg_dsmem[];
   __shared__ MgDev mg;
   __shared__ MgDev mgs;   // block 0's view with the block-run levels in shared memory
   __shared__ double sred[32 * 3 * NC];
   __shared__ double stot[3 * NC];
+  __shared__ double scal[NC];   // a step's quotients, formed once per block by thread 0
   {
     const int *src = reinterpret_cast<const int *>(mgp);
     int *dst = reinterpret_cast<int *>(&mg);
@@ -464,11 +465,15 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg_mg(const MgDev *mgp, MgCg C) {
       }
     }
     if (!reduce_grid<NC>(ps, sred, stot, C.partials, rk, C.bar)) return;
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) scal[q] = gam[q] > 0.0 ? gam[q] / stot[q] : 0.0;
+    __syncthreads();
     double alpha[NC];
     bool ok = true;
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      alpha[q] = gam[q] > 0.0 ? gam[q] / stot[q] : 0.0;
+      alpha[q] = scal[q];
       ok = ok && (gam[q] <= 0.0 || stot[q] > 0.0);
     }
     if (!ok) break;   // lost positive definiteness in rounding: stop with x as is
@@ -500,10 +505,14 @@ __global__ void __launch_bounds__(FO_BLOCK) k_pcg_mg(const MgDev *mgp, MgCg C) {
         w[NC + sys(c)] += C.r[k] * C.r[k];
       }
     if (!reduce_grid<2 * NC>(w, sred, stot, C.partials, rk, C.bar)) return;
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) scal[q] = gam[q] > 0.0 ? stot[q] / gam[q] : 0.0;
+    __syncthreads();
     rr = 0.0;
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      beta[q] = gam[q] > 0.0 ? stot[q] / gam[q] : 0.0;
+      beta[q] = scal[q];
       gam[q] = stot[q];
       rho[q] = stot[NC + q];
       rr += rho[q];
