@@ -280,35 +280,55 @@ struct GridBar {
   unsigned long long limit_ns;
 };
 
+// Thread 0's part of the barrier: arrive, then wait (bounded).  Returns 0 on a time-out.
+__device__ __forceinline__ int grid_arrive_wait(const GridBar &b) {
+  unsigned inc = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1)) : 1u;
+  // arrival with release semantics (the block's writes, ordered before it by the block
+  // barrier before the call, become visible to every block that acquires the released
+  // count); polling with acquire loads orders the other blocks' writes before this block's reads
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(b.count), "r"(inc) : "memory");
+  int ok = 1;
+  unsigned long long t0 = 0;
+  unsigned spins = 0;
+  while (((old ^ fo_ld_acquire(b.count)) & 0x80000000u) == 0) {
+    if (++spins == 1024) t0 = fo_globaltimer();
+    if (spins > 1024 && (spins & 255) == 0) {
+      __nanosleep(64);
+      if (*(volatile int *)b.err == DEV_TIMEOUT) {   // another block gave up
+        ok = 0;
+        break;
+      }
+      if (fo_globaltimer() - t0 > b.limit_ns) {
+        atomicExch(b.err, DEV_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+  }
+  return ok;
+}
+
 __device__ __forceinline__ bool grid_sync(const GridBar &b) {
   __shared__ int s_ok;
   __syncthreads();
+  if (threadIdx.x == 0) s_ok = grid_arrive_wait(b);
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The barrier with block-local work `side` done by thread 32 while thread 0 waits for the
+// grid (work that only this block reads after the barrier, such as small serial FP64 chains
+// on shared-memory data).  With a single warp, thread 0 does it before arriving.
+template <class F>
+__device__ __forceinline__ bool grid_sync_side(const GridBar &b, F side) {
+  __shared__ int s_ok;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned inc = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1)) : 1u;
-    // arrival with release semantics (the block's writes, ordered before it by the block
-    // barrier above, become visible to every block that acquires the released count);
-    // polling with acquire loads orders the other blocks' writes before this block's reads
-    unsigned old;
-    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(b.count), "r"(inc) : "memory");
-    int ok = 1;
-    unsigned long long t0 = 0;
-    unsigned spins = 0;
-    while (((old ^ fo_ld_acquire(b.count)) & 0x80000000u) == 0) {
-      if (++spins == 1024) t0 = fo_globaltimer();
-      if (spins > 1024 && (spins & 255) == 0) {
-        __nanosleep(64);
-        if (*(volatile int *)b.err == DEV_TIMEOUT) {   // another block gave up
-          ok = 0;
-          break;
-        }
-        if (fo_globaltimer() - t0 > b.limit_ns) {
-          atomicExch(b.err, DEV_TIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    s_ok = ok;
+    if (blockDim.x <= 32) side();
+    s_ok = grid_arrive_wait(b);
+  } else if (threadIdx.x == 32) {
+    side();
   }
   __syncthreads();
   return s_ok != 0;

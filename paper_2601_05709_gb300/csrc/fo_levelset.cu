@@ -226,14 +226,13 @@ struct GmresShared {
   double col[GM_M + 1];          // the new Hessenberg column (before the rotations)
   double H[(GM_M + 1) * GM_M];   // column-major: H[j * (GM_M + 1) + i]
   double cs[GM_M], sn[GM_M], g[GM_M + 1], y[GM_M];
-  int rotated;                   // the step's column is already rotated into H
   double scal[2];                // a step's |w - V h| and its inverse (thread 0 forms them)
   int onepass;                   // the step takes one Gram-Schmidt pass
 };
 
 // Thread 0: apply the previous rotations to column j (col[0..j+1]), form the new one, update
 // the residual estimate g and store the rotated column in H.
-__device__ __forceinline__ void givens_column(GmresShared &sh, int j, double *col) {
+__device__ __noinline__ void givens_column(GmresShared &sh, int j, double *col) {
   for (int i = 0; i < j; ++i) {
     const double t = sh.cs[i] * col[i] + sh.sn[i] * col[i + 1];
     col[i + 1] = -sh.sn[i] * col[i] + sh.cs[i] * col[i + 1];
@@ -304,14 +303,6 @@ __device__ bool arnoldi_step(const Grid &g, const double *M, const double *dinv,
     const double hnext = sh.scal[0];
     const double inv = sh.scal[1];
     double *Vn = K.V + (size_t)(J + 1) * N;
-    if (threadIdx.x == 0) {   // the column is final: rotate it now, overlapping the pass below
-      double col[J + 2];
-#pragma unroll
-      for (int i = 0; i <= J; ++i) col[i] = hc[i];
-      col[J + 1] = hnext;
-      givens_column(sh, J, col);
-      sh.rotated = 1;
-    }
     for (long long a = tid; a < N; a += gs) {
       double wa = K.w[a];
 #pragma unroll
@@ -457,23 +448,22 @@ __device__ int gmres_solve(const Grid &g, const double *M, const double *dinv, c
     int j = 0;
     bool done = false;
     for (; j < GM_M; ++j) {
-      if (threadIdx.x == 0) sh.rotated = 0;
       __syncthreads();
       if (!arnoldi_dispatch<D, 0>(j, g, M, dinv, K, sh, partials, rk, bar)) { *ok = false; return total; }
-      __syncthreads();
+      // v_{j+1} complete before the next apply.  Meanwhile thread 32 rotates the Hessenberg
+      // column and updates the residual estimate (the same in every block): a serial FP64
+      // chain that would otherwise hold up its warp's share of the pass
+      const int jj = j;
+      if (!grid_sync_side(bar, [&] {
+            double col[GM_M + 1];
+            for (int i = 0; i <= jj + 1; ++i) col[i] = sh.col[i];
+            givens_column(sh, jj, col);
+          })) { *ok = false; return total; }
       const double hnext = sh.col[j + 1];
-      // ---- Hessenberg column, Givens rotations, residual estimate (same in every block)
-      if (threadIdx.x == 0 && !sh.rotated) {
-        double col[GM_M + 1];
-        for (int i = 0; i <= j + 1; ++i) col[i] = sh.col[i];
-        givens_column(sh, j, col);
-      }
-      __syncthreads();
       ++total;
       const double est = sh.g[j + 1] * sh.g[j + 1];
       done = !(est > rtol2 * bb) || hnext == 0.0 || total >= maxit;
       if (done) { ++j; break; }
-      if (!grid_sync(bar)) { *ok = false; return total; }   // v_{j+1} complete before the next apply
     }
     if (j > GM_M) j = GM_M;
     // ---- y = H^{-1} g (upper triangular, j x j), x += D^{-1} V y
