@@ -269,6 +269,11 @@ __device__ bool arnoldi_step(const Grid &g, const double *M, const double *dinv,
 #pragma unroll
   for (int i = 0; i < J + 2; ++i) h1[i] = 0.0;
   for (long long a = tid; a < N; a += gs) {
+    // the basis entries first: their loads then overlap the stencil's instead of waiting
+    // behind the store of w (which the compiler cannot prove distinct from V)
+    double va[J + 1];
+#pragma unroll
+    for (int i = 0; i <= J; ++i) va[i] = K.V[(size_t)i * N + a];
     int idx[3];
     node_ijk(g, a, idx);
     double wa = 0.0;
@@ -279,7 +284,7 @@ __device__ bool arnoldi_step(const Grid &g, const double *M, const double *dinv,
     }
     K.w[a] = wa;
 #pragma unroll
-    for (int i = 0; i <= J; ++i) h1[i] += K.V[(size_t)i * N + a] * wa;
+    for (int i = 0; i <= J; ++i) h1[i] += va[i] * wa;
     h1[J + 1] += wa * wa;
   }
   if (!ls_reduce<J + 2>(h1, sh.sred, sh.stot, partials, rk, bar)) return false;
