@@ -349,9 +349,9 @@ def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True, mg
     nval = mesh.num_nodes * 64
     traffic = nval * (106.0 * bm["iterations"] + 76.0 * (bm["refinements"] + 1))
     achieved = traffic / bm["seconds"] / 1e9
-    # DRAM bytes of one launch at 512x512 from the committed ncu capture of the same build
-    # (profiles/k_bmg_ir_batch64.md)
-    dram = 93.88e9 + 71.01e9 if n == 512 else None
+    # DRAM bytes of one launch at 512x512, from a one-pass ncu capture (dram__bytes_read.sum +
+    # dram__bytes_write.sum) of this kernel as built now
+    dram = 93.78e9 + 71.00e9 if n == 512 else None
     out["roofline"] = {"bound": "hbm", "kernel": "k_bmg_ir<2, 2>", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                        "frac": achieved / hbm, "algorithmic_bytes": traffic, "traffic": dram,
                        "note": "106 B per instance-DOF and inner iteration + 76 B per refinement step; time = the "
@@ -638,9 +638,9 @@ def main():
         its_per_launch = state_iters / len(logs)
         achieved = bpi * its_per_launch / (launch_ms / 1e3) / 1e9
         hbm = peaks.get("hbm_gbs", 6800.0)
-        # DRAM bytes of one launch of this kernel, from the committed ncu capture of the same build
-        # (profiles/k_pcg_mg_state_cantilever2d.md): the hierarchy is read once, then served from L2
-        traffic = 14.11e6 + 0.53e6
+        # DRAM bytes of one launch of this kernel, from a one-pass ncu capture of it as built now:
+        # the hierarchy is read once, then served from L2
+        traffic = 14.12e6 + 0.56e6
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "kernel": "k_pcg_mg<2, 2, true, 1>",
                 "algorithmic_bytes_per_iteration": bpi, "iterations_per_launch": its_per_launch,
