@@ -238,8 +238,15 @@ __device__ __noinline__ void givens_column(GmresShared &sh, int j, double *col) 
     col[i + 1] = -sh.sn[i] * col[i] + sh.cs[i] * col[i + 1];
     col[i] = t;
   }
-  const double rnorm = hypot(col[j], col[j + 1]);
-  const double c = rnorm > 0.0 ? col[j] / rnorm : 1.0, s = rnorm > 0.0 ? col[j + 1] / rnorm : 0.0;
+  // c, s from one reciprocal norm (no quotients on this serial chain)
+  const double a = col[j], b = col[j + 1];
+  double c = 1.0, s = 0.0, rnorm = 0.0;
+  if (a != 0.0 || b != 0.0) {
+    const double rh = rhypot(a, b);
+    c = a * rh;
+    s = b * rh;
+    rnorm = a * c + b * s;
+  }
   sh.cs[j] = c;
   sh.sn[j] = s;
   col[j] = rnorm;
@@ -288,17 +295,22 @@ __device__ bool arnoldi_step(const Grid &g, const double *M, const double *dinv,
     h1[J + 1] += wa * wa;
   }
   if (!ls_reduce<J + 2>(h1, sh.sred, sh.stot, partials, rk, bar)) return false;
-  // the step's scalars once per block (the FP64 pipe is narrow: 256 threads forming the same
-  // square root and quotient cost more than the pass over the vectors)
-  if (threadIdx.x == 0) {
-    double hh = 0.0;
+  // the step's scalars once per block, by warp 0 (the FP64 pipe is narrow: 256 threads
+  // forming the same square root and quotient cost more than the pass over the vectors, and a
+  // single thread's serial chain waits on FP64 latency): |h|^2 by a warp sum, then one
+  // reciprocal square root for |w - V h| and its inverse
+  if (threadIdx.x < 32) {
+    const int l = threadIdx.x;
+    double hh = l <= J ? sh.stot[l] * sh.stot[l] : 0.0;
 #pragma unroll
-    for (int i = 0; i <= J; ++i) hh += sh.stot[i] * sh.stot[i];
-    const double ww = sh.stot[J + 1], wp2 = ww - hh;
-    sh.onepass = wp2 >= GM_ONEPASS * ww;
-    const double hn = sh.onepass ? sqrt(wp2) : 0.0;
-    sh.scal[0] = hn;
-    sh.scal[1] = hn > 0.0 ? 1.0 / hn : 0.0;
+    for (int o = 16; o > 0; o >>= 1) hh += __shfl_xor_sync(0xffffffffu, hh, o);
+    if (l == 0) {
+      const double ww = sh.stot[J + 1], wp2 = ww - hh;
+      sh.onepass = wp2 >= GM_ONEPASS * ww;
+      const double r = (sh.onepass && wp2 > 0.0) ? rsqrt(wp2) : 0.0;
+      sh.scal[0] = wp2 * r;
+      sh.scal[1] = r;
+    }
   }
   __syncthreads();
   double hc[J + 1];
@@ -472,13 +484,20 @@ __device__ int gmres_solve(const Grid &g, const double *M, const double *dinv, c
     }
     if (j > GM_M) j = GM_M;
     // ---- y = H^{-1} g (upper triangular, j x j), x += D^{-1} V y
-    if (threadIdx.x == 0) {
+    // back substitution by columns in warp 0: lane k holds g_k less the solved terms and
+    // the reciprocal of H_kk; y_i = t_i / H_ii goes to every lane, which subtracts its H_ki y_i
+    if (threadIdx.x < 32) {
+      const int k = threadIdx.x;
+      double t = k < j ? sh.g[k] : 0.0;
+      const double d = k < j ? sh.H[k * (GM_M + 1) + k] : 0.0;
+      const double rinv = d != 0.0 ? 1.0 / d : 0.0;
+      double yk = 0.0;
       for (int i = j - 1; i >= 0; --i) {
-        double t = sh.g[i];
-        for (int k = i + 1; k < j; ++k) t -= sh.H[k * (GM_M + 1) + i] * sh.y[k];
-        const double d = sh.H[i * (GM_M + 1) + i];
-        sh.y[i] = d != 0.0 ? t / d : 0.0;
+        const double yi = __shfl_sync(0xffffffffu, t * rinv, i);
+        if (k == i) yk = yi;
+        if (k < i) t -= sh.H[i * (GM_M + 1) + k] * yi;
       }
+      if (k < j) sh.y[k] = yk;
     }
     __syncthreads();
     for (long long a = tid; a < N; a += gs) {
