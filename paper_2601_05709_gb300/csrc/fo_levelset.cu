@@ -243,9 +243,15 @@ __device__ __noinline__ void givens_column(GmresShared &sh, int j, double *col) 
   double c = 1.0, s = 0.0, rnorm = 0.0;
   if (a != 0.0 || b != 0.0) {
     const double rh = rhypot(a, b);
-    c = a * rh;
-    s = b * rh;
-    rnorm = a * c + b * s;
+    if (rh <= 1.0e300) {
+      c = a * rh;
+      s = b * rh;
+      rnorm = a * c + b * s;
+    } else {   // |(a, b)| below 1e-300: the reciprocal would overflow
+      rnorm = hypot(a, b);
+      c = a / rnorm;
+      s = b / rnorm;
+    }
   }
   sh.cs[j] = c;
   sh.sn[j] = s;
