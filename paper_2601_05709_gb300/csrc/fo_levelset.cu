@@ -226,12 +226,13 @@ struct GmresShared {
   double col[GM_M + 1];          // the new Hessenberg column (before the rotations)
   double H[(GM_M + 1) * GM_M];   // column-major: H[j * (GM_M + 1) + i]
   double cs[GM_M], sn[GM_M], g[GM_M + 1], y[GM_M];
-  double scal[2];                // a step's |w - V h| and its inverse (thread 0 forms them)
+  double scal[2];                // a step's |w - V h| and its inverse (formed by warp 0)
   int onepass;                   // the step takes one Gram-Schmidt pass
 };
 
-// Thread 0: apply the previous rotations to column j (col[0..j+1]), form the new one, update
-// the residual estimate g and store the rotated column in H.
+// One thread (thread 32, during the grid barrier after the step's pass): apply the previous
+// rotations to column j (col[0..j+1]), form the new one, update the residual estimate g and
+// store the rotated column in H.
 __device__ __noinline__ void givens_column(GmresShared &sh, int j, double *col) {
   for (int i = 0; i < j; ++i) {
     const double t = sh.cs[i] * col[i] + sh.sn[i] * col[i + 1];
