@@ -275,8 +275,8 @@ FO_API fo_status fo_apply(fo_problem *prob, int op, const double *x, double *y, 
 
 /* State solve that allocates no device memory.  The paper has no counterpart: this is for
  * callers that cannot let a library call cudaMalloc / cudaFree while they run -- those calls
- * may synchronise the whole device, they are not allowed while a stream is being captured,
- * and another framework's caching allocator may already hold the device memory.
+ * may synchronise the whole device (a stall a latency-bound loop cannot take), and another
+ * framework's caching allocator or a fixed memory budget may already own the device memory.
  * Computes the same FP64 Jacobi-PCG solve K_A x = b as fo_state_solve, but its working
  * memory (Krylov vectors, reduction partials, grid-barrier counter, status words) is one
  * fixed array of FO_NOALLOC_SCRATCH_BYTES that the library declares in device memory; every

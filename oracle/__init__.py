@@ -39,8 +39,12 @@ Module map (paper section / equation each follows):
 * ``solvers``   sparse direct solve, Jacobi-PCG, Jacobi-BiCGStab.
 
 Pins: every function is checked in ``tests/test_oracle_*.py`` against closed
-forms, textbook special cases, invariants, brute force and a Taylor test.
-Parity unpinned: ``levelset.reinit`` (the reinitialisation scheme has no
-closed-form answer; it is held only to property checks: sign preservation and
-|grad phi| -> 1 near the interface).
+forms, textbook special cases, invariants, brute force and a Taylor test.  The
+reinitialisation step (``levelset.reinit_step_system`` / ``reinit``) is pinned
+by the closed form of a step from a constant level set, the identity "AB2 with
+an equal history = explicit Euler", and a pointwise brute-force evaluation of
+one Euler and one AB2 step with finite-difference test-function gradients
+(``tests/test_oracle_pins_load_reinit.py``); the traction load
+(``fem.facet_load``) by hand-computed facets, subdivision quadrature and the
+face sums and first moments.
 """

@@ -19,6 +19,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
 
 #include "fo_internal.cuh"
 #include "fo_ops.cuh"
@@ -510,9 +511,8 @@ fo_status fo_velocity_pcg(fo_problem *p, const fo_solve_opts *o, double *Btt, fo
 
 // ============================================================ state solve without allocation
 // Some callers cannot let a library allocate device memory while they run: cudaMalloc and
-// cudaFree may synchronise the whole device (a stall in a latency-bound loop), they are not
-// allowed while a stream is being captured, and another framework's caching allocator may
-// already own the device memory.  fo_state_solve_noalloc gives them a state solve whose
+// cudaFree may synchronise the whole device (a stall in a latency-bound loop), and another
+// framework's caching allocator or a fixed memory budget may already own the device memory.  fo_state_solve_noalloc gives them a state solve whose
 // working memory -- the Krylov vectors, the reduction partials, the grid-barrier counter and
 // the status words of the persistent PCG -- is this fixed array, which every GPU that loads
 // the library holds until the process exits.  The caller passes the right-hand side and the
@@ -527,18 +527,27 @@ static __device__ __align__(256) double g_noalloc_scratch[FO_NOALLOC_DOUBLES];
 static fo_status noalloc_scratch_address(fo_ctx *ctx, double **out) {
   // The array's device address is looked up once per device, with that device current.
   // Host code cannot use the symbol itself: on the host it names a stand-in, not GPU memory.
+  // std::call_once publishes the address to every thread that calls later (two threads making
+  // their first call at once do not race), and the caller's current device is restored.
+  static std::once_flag once[64];
   static double *addr[64] = {};
-  static bool ready[64] = {};
+  static cudaError_t err[64] = {};
   const int dev = ctx->device;
   if (dev < 0 || dev >= 64) return fo_fail(ctx, FO_EINVAL, "device index out of range");
-  if (!ready[dev]) {
-    FO_CU(ctx, cudaSetDevice(dev));
+  std::call_once(once[dev], [dev]() {
+    int prev = -1;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e == cudaSuccess && prev != dev) e = cudaSetDevice(dev);
     void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return fo_cuda_check(ctx, e, "cudaGetSymbolAddress(no-alloc scratch)");
-    addr[dev] = (double *)p;
-    ready[dev] = true;
-  }
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (prev >= 0 && prev != dev) {
+      const cudaError_t r = cudaSetDevice(prev);
+      if (e == cudaSuccess) e = r;
+    }
+    err[dev] = e;
+    addr[dev] = e == cudaSuccess ? (double *)p : nullptr;
+  });
+  if (err[dev] != cudaSuccess) return fo_cuda_check(ctx, err[dev], "cudaGetSymbolAddress(no-alloc scratch)");
   *out = addr[dev];
   return FO_OK;
 }

@@ -244,11 +244,11 @@ __device__ __noinline__ void givens_column(GmresShared &sh, int j, double *col) 
   double c = 1.0, s = 0.0, rnorm = 0.0;
   if (a != 0.0 || b != 0.0) {
     const double rh = rhypot(a, b);
-    if (rh <= 1.0e300) {
+    if (rh >= 1.0e-300 && rh <= 1.0e300) {
       c = a * rh;
       s = b * rh;
       rnorm = a * c + b * s;
-    } else {   // |(a, b)| below 1e-300: the reciprocal would overflow
+    } else {   // |(a, b)| below 1e-300 or above 1e300: the reciprocal would overflow or be subnormal
       rnorm = hypot(a, b);
       c = a / rnorm;
       s = b / rnorm;

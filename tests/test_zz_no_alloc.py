@@ -1,8 +1,8 @@
 """fo_state_solve_noalloc: the state solve for callers that cannot let the library allocate.
 
 Such callers (a loop that cannot afford the device-wide synchronisation cudaMalloc/cudaFree
-may cause, code running while a stream is captured, a process whose device memory belongs
-to another framework's allocator) pass their own input and output buffers; the solver's
+may cause, a process whose device memory belongs to another framework's allocator or to a
+fixed budget) pass their own input and output buffers; the solver's
 working memory is a fixed array inside the library.  This file is collected last so that a
 run stopping at the first failure has already run every other test.
 
