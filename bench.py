@@ -63,10 +63,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the 64x64 heat and 3D cantilever legs")
     ap.add_argument("--serving-requests", type=int, default=12)
-    ap.add_argument("--batch-n", type=int, default=512, help="cells per axis of the batch mesh")
-    ap.add_argument("--batch-maxit", type=int, default=400000, help="cap on batched iterations (profiling runs)")
-    ap.add_argument("--batch-only", action="store_true", help="run the batch leg only (profiling)")
-    ap.add_argument("--batch-mg-only", action="store_true", help="with --batch-only: the multigrid solve only")
+    ap.add_argument("--no-precision-pair", action="store_true", help="skip the FP32-CG + FP64-refinement rerun")
     return ap.parse_args()
 
 
@@ -152,8 +149,11 @@ class ClockSampler:
 CPU_SAMPLE_ITERS = 4
 
 
-def oracle_sample(iters, warm=0):
-    """Time the FP64 oracle on iterations 0..iters-1 of the workload (single host thread).
+def oracle_sample(iters, warm=0, dump=None):
+    """Time the FP64 oracle on iterations warm..warm+iters-1 of the workload (single host thread),
+    after running iterations 0..warm-1 untimed, so that it times the same iterations as the GPU
+    arm's first timed ones.  Returns the per-iteration times and every iteration's J, C and
+    B(theta, theta); with `dump`, also saves iteration 0's state u and velocity theta there (npz).
 
     Runs in a fresh interpreter (spawned before any CUDA work in this one matters) with the
     BLAS / OpenMP thread pools pinned to one thread, so `cores` is 1."""
@@ -174,19 +174,85 @@ c, r = workloads.hole_lattice()
 phi = levelset.initial_level(m.coords, c, r)
 st = ppl.PPL(1)
 opts = oalg.RunOptions(dfactor=0.1, smooth=True, reinit_step=0)
-times = []
+times, J, C, B = [], [], [], []
 for i in range({iters + warm}):
     t = time.perf_counter()
     phi, log = oalg.opt_step(prob, phi, i, st, opts)
     times.append(time.perf_counter() - t)
-print(json.dumps({{"times": times[{warm}:], "J": log["J"]}}))
+    J.append(log["J"]); C.append(log["C"]); B.append(log["Btt"])
+    if i == 0 and {dump!r} is not None:
+        np.savez({dump!r}, u=log["u"], theta=log["theta"])
+print(json.dumps({{"times": times[{warm}:], "J": J, "C": C, "Btt": B}}))
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1200)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_omp_pcg(rtol=1e-8):
+    """The oracle's Jacobi-PCG (C, OpenMP over all host cores) on the cantilever's first state
+    system (phi0, free DOFs), from zero to ||r|| <= rtol ||b||: the all-cores CPU figure."""
+    code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from oracle import algorithm as oalg, levelset, pcg_omp
+from oracle.mesh import BoxMesh
+from paper_2601_05709_gb300 import workloads
+m = BoxMesh(2, ({NX}, {NY}), (0.0, 0.0), (2.0, 1.0))
+prob = oalg.Problem(mesh=m, kind=oalg.ELASTIC, a_in=1.0, a_out=1e-3, E=1.0, nu=0.3, dirichlet_faces=[(0, 0)],
+                    point_loads=[(int(m.node_id(np.array([{NX}, {NY // 2}]))), (0.0, -1.0))])
+c, r = workloads.hole_lattice()
+phi = levelset.initial_level(m.coords, c, r)
+from oracle import shape
+A, _ = shape.coefficient(phi, m.cells, 1.0, 1e-3)
+free = np.flatnonzero(prob.dirichlet() == 0)
+K = prob.stiffness(A)[free][:, free].tocsr()
+F = prob.load()[free]
+pcg_omp.pcg(K, F, rtol=1e-2)                      # warm the thread pool
+t = time.perf_counter()
+x, it, rr, nt = pcg_omp.pcg(K, F, rtol={rtol!r}, maxit=400000)
+dt = time.perf_counter() - t
+print(json.dumps({{"seconds": dt, "iterations": it, "rel_residual": rr, "threads": nt, "ndof_free": int(free.size)}}))
+"""
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env.pop(k, None)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1200)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    res["gdof_iters_per_s"] = res["ndof_free"] * res["iterations"] / res["seconds"] / 1e9
+    return res
+
+
+def gpu_same_system(api, ctx, stream, rtol=1e-8):
+    """Our Jacobi-PCG and multigrid CG on the same first state system, from zero to the same
+    relative residual, for the iteration-count and rate comparison with the CPU PCG."""
+    import numpy as np
+    import torch
+    out = {}
+    for name, pc in (("jacobi_pcg", api.FO_PC_JACOBI), ("multigrid_cg", api.FO_PC_MG)):
+        mesh, prob = make_problem(api, ctx)
+        prob.coefficients()
+        so = api.solve_opts(rtol=rtol, maxit=400000, precond=pc)
+        prob.state_solve(so)                              # first call: scratch, hierarchy
+        prob.set(api._lib.FO_FIELD_U, np.zeros(2 * mesh.num_nodes))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st = prob.state_solve(so)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        nfree = 2 * mesh.num_nodes - 2 * (NY + 1)
+        out[name] = {"seconds": sec, "iterations": st.iterations, "rel_residual": st.rel_residual,
+                     "gdof_iters_per_s": nfree * st.iterations / sec / 1e9}
+        prob.close()
+    return out
 
 
 def cpu_model():
@@ -209,16 +275,20 @@ def cpu_model():
 
 # ----------------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
+    """The oracle on the same iterations as our arm: W untimed, then K timed (at most the 50 of
+    the workload in total), on one host thread."""
     if rank != 0:
         return
-    iters = max(1, min(args.steps, CPU_SAMPLE_ITERS))
-    res = oracle_sample(iters, warm=0)
+    warm = max(0, min(args.warmup, 49))
+    iters = max(1, min(args.steps, 50 - warm))
+    res = oracle_sample(iters, warm=warm)
     total = sum(res["times"])
     value = iters / total
-    sample = f"iterations 0..{iters - 1} of the 50 (FP64 oracle, sparse direct solves)"
+    sample = (f"iterations {warm}..{warm + iters - 1} of the 50 after {warm} untimed ones "
+              "(FP64 oracle, sparse direct solves)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "opt-iters/s", "n_gpus": args.gpus,
-        "steps": iters, "warmup": 0, "ms_per_step": 1e3 * total / iters, "higher_is_better": True,
+        "steps": iters, "warmup": warm, "ms_per_step": 1e3 * total / iters, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "parallelism": "single host thread"},
         "cpu_baseline": {"value": value, "unit": "opt-iters/s", "cores": 1, "kind": "oracle", "sample": sample,
@@ -232,7 +302,7 @@ def run_reference(args, rank, world):
 BATCH_N, BATCH_INST = 512, 64
 
 
-def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True, mg_only=False):
+def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True):
     """Batched vs one-at-a-time state solves of the 64-instance Helmholtz family, to a relative
     FP64 residual of 1e-8; then the summed shape derivative and one velocity solve."""
     import numpy as np
@@ -253,12 +323,12 @@ def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True, mg
                        f"({2 * n * n} triangles, {mesh.num_nodes} nodes), ersatz 1e-3, Dirichlet x=0",
            "rtol": 1e-8}
     tune = {}
-    for prec, name in () if mg_only else ((api.FO_MIXED, "mixed"), (api.FO_FP64, "fp64")):
+    for prec, name in ((api.FO_MIXED, "mixed"), (api.FO_FP64, "fp64")):
         r = prob.batch_autotune(prec)
         tune[name] = {"tile": list(r.tile), "block": r.block, "blocks_per_sm": r.blocks_per_sm,
                       "us_per_iteration_all_active": r.us_per_iteration, "candidates": r.candidates}
     out["autotune"] = tune
-    for prec, name in () if mg_only else ((api.FO_MIXED, "mixed"), (api.FO_FP64, "fp64")):
+    for prec, name in ((api.FO_MIXED, "mixed"), (api.FO_FP64, "fp64")):
         prob.set(api.FO_FIELD_U, np.zeros((mesh.num_nodes, BATCH_INST)))
         o = api.solve_opts(precision=prec, rtol=1e-8, inner_rtol=1e-3, maxit=maxit, inner_maxit=100000)
         torch.cuda.synchronize()
@@ -356,9 +426,6 @@ def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True, mg
                        "frac": achieved / hbm, "algorithmic_bytes": traffic, "traffic": dram,
                        "note": "106 B per instance-DOF and inner iteration + 76 B per refinement step; time = the "
                                "whole solve (one launch) by CUDA events on the launching stream"}
-    if mg_only:
-        prob.close()
-        return out
     # the Jacobi batch's FP32 sweep: per DOF and iteration it moves r, w, s, D^{-1}, p, x in and
     # r, w, s, p, x out (11 x 4 bytes), measured with every instance active (autotune)
     us = tune["mixed"]["us_per_iteration_all_active"]
@@ -370,6 +437,20 @@ def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True, mg
     prob.close()
     mesh.close() if hasattr(mesh, "close") else None
     return out
+
+
+def survey_pcg_bytes(ndof, nt, nn, d, w):
+    """Algorithmic bytes of one PCG iteration on explicit connectivity: 9 vector passes of w-byte
+    values over the DOFs (read/write x, r, p; write and read q = A p; read the Jacobi diagonal),
+    plus per element its d+1 int32 vertex ids and a 1-byte coefficient flag, plus the FP64
+    coordinates of every node (geometry recomputed in registers)."""
+    return float(9 * w * ndof + nt * (4 * (d + 1) + 1) + nn * 8 * d)
+
+
+# DRAM bytes (read + write) of one state-solve CG launch, from one-pass ncu captures of the
+# kernels as built now (keyed by precision; absent until captured)
+C2_STATE_TRAFFIC = {}
+C3_STATE_TRAFFIC = {}
 
 
 def mg_state_bytes_per_iteration(nx, ny, c):
@@ -397,7 +478,7 @@ def mg_state_bytes_per_iteration(nx, ny, c):
 
 
 # ------------------------------------------- 64x64 heat and 3D cantilever legs
-def bench_configs(api, ctx, stream):
+def bench_configs(api, ctx, stream, peaks):
     """Latency of one Algorithm-1 step on the 64x64 heat problem and, on the 3D cantilever
     96x48x48, the multigrid state solve to 1e-8 and one full optimisation iteration."""
     import numpy as np
@@ -440,20 +521,48 @@ def bench_configs(api, ctx, stream):
     phi = workloads.phi_bumps(coords, workloads.bump_centres((0, 0, 0), (2, 1, 1), 20, seed=0), 0.1, 0.2)
     prob.set_levelset(phi)
     prob.coefficients()
-    so = api.solve_opts(rtol=1e-8, precond=mg)
-    prob.state_solve(so)                                  # builds the hierarchy
-    ms_s, sts = timed(lambda i: prob.state_solve(so), 3)
     ndof = 3 * mesh.num_nodes
-    it = sts[-1].iterations
-    ro3 = api.run_options(state=api.solve_opts(rtol=1e-8, warm_start=1, precond=mg),
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    solves = {}
+    # the configured solve: FP32 CG (FP32 rows and vectors, FP64 dots) inside FP64 refinement to
+    # 1e-8, preconditioned by the FP32 V-cycle; beside it the FP64 CG with the same V-cycle
+    for name, prec in (("mixed", api.FO_MIXED), ("fp64", api.FO_FP64)):
+        so = api.solve_opts(precision=prec, rtol=1e-8, inner_rtol=1e-4, precond=mg)
+        prob.state_solve(so)                              # builds the hierarchy (first call)
+        reps, kms = [], []
+        for _ in range(3):
+            ms1, st1 = timed(lambda i: prob.state_solve(so), 1)
+            reps.append(ms1)
+            kms.append(ctx.solve_kernel_ms())
+        st1 = st1[-1]
+        w = 4 if name == "mixed" else 8
+        bpi = survey_pcg_bytes(ndof, mesh.num_elems, mesh.num_nodes, 3, w)
+        kms_mean = sum(kms) / len(kms)
+        achieved = bpi * st1.iterations / (kms_mean / 1e3) / 1e9
+        solves[name] = {"solve_ms": sum(reps) / len(reps), "cg_kernel_ms": kms_mean,
+                        "iterations": st1.iterations, "refinements": st1.outer_iterations,
+                        "rel_residual": st1.rel_residual,
+                        "gdof_iters_per_s": ndof * st1.iterations / (sum(reps) / len(reps) / 1e3) / 1e9,
+                        "roofline": {"bound": "hbm", "kernel": "k_pcg_mg<3, 3, true, 1, %s>" % (
+                                         "float" if w == 4 else "double"),
+                                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                                     "algorithmic_bytes_per_iteration": bpi,
+                                     "traffic": C3_STATE_TRAFFIC.get(name),
+                                     "note": "algorithmic bytes = 9 vector passes + connectivity/flags/coordinates "
+                                             "per CG iteration x iterations / the CG launches' CUDA-event time "
+                                             "(of measured HBM peak)"}}
+    ro3 = api.run_options(state=api.solve_opts(precision=api.FO_MIXED, rtol=1e-8, inner_rtol=1e-4, warm_start=1,
+                                               precond=mg),
                           velocity=api.solve_opts(rtol=1e-8, warm_start=1, precond=mg))
     prob.opt_step(0, ro3)
     ms_o, logs = timed(lambda i: prob.opt_step(1 + i, ro3), 2)
     out["cantilever3d_96x48x48"] = {"workload": "3D elasticity cantilever on a 96x48x48 Kuhn mesh of (0,2)x(0,1)^2 (1,327,104 tets, "
                              f"{ndof} DOFs), 20 Gaussian bumps, traction (0,0,-1) on x = 2",
-                 "state_solve_ms": ms_s, "state_iterations": it, "state_rel_residual": sts[-1].rel_residual,
-                 "state_gdof_iters_per_s": ndof * it / (ms_s / 1e3) / 1e9,
-                 "ms_per_opt_step": ms_o, "opt_step_state_iterations": logs[-1].state.iterations}
+                 "state_solve": solves, "state_solve_ms": solves["mixed"]["solve_ms"],
+                 "state_iterations": solves["mixed"]["iterations"],
+                 "roofline": solves["mixed"]["roofline"],
+                 "ms_per_opt_step": ms_o, "opt_step_state_iterations": logs[-1].state.iterations,
+                 "opt_step_precision": "mixed (FP32 CG + FP64 refinement to 1e-8)"}
     prob.close()
     return out
 
@@ -527,6 +636,53 @@ def bench_serving(api, ctx, count):
             "throughput_ratio_vs_serial_multigrid": served["requests_per_s"] / serial_mg["requests_per_s"]}
 
 
+# ------------------------------------------- FP64 and mixed runs against the oracle
+def rerun(api, ctx, stream, precision, precond, warmup, steps, flush):
+    """The same optimisation again in another precision: per-iteration values, first-iteration
+    fields, and the device time of the timed iterations (CUDA events)."""
+    import torch
+    mesh, prob = make_problem(api, ctx)
+    opts = run_options(api, precision, precond)
+    ppl = api.PPL(1)
+    logs, first, ms = [], None, 0.0
+    for it in range(warmup + steps):
+        if it >= warmup:
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        logs.append(prob.opt_step(it, opts, ppl))
+        if it >= warmup:
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        if it == 0:
+            first = (prob.get(api._lib.FO_FIELD_U), prob.get(api._lib.FO_FIELD_THETA))
+    prob.close()
+    timed = logs[warmup:]
+    return {"logs": logs, "first": first, "opt_iters_per_s": steps / (ms / 1e3),
+            "state_ms_per_step": sum(l.ms_state for l in timed) / steps,
+            "state_kernel_ms_per_step": sum(l.ms_state_kernel for l in timed) / steps,
+            "state_iterations_per_step": sum(l.state.iterations for l in timed) / steps,
+            "refinements_per_step": sum(l.state.outer_iterations for l in timed) / steps}
+
+
+def errors_vs_oracle(logs, first, cpu, dump):
+    """Relative differences from the FP64 oracle, per result: J, C, B(theta, theta) of every
+    iteration the oracle ran (max over them and each one), and iteration 0's u and theta (max norm)."""
+    import numpy as np
+    n = min(len(logs), len(cpu["J"]))
+    out = {"iterations_compared": n}
+    for key, attr in (("J", "J"), ("C", "C"), ("Btt", "Btt")):
+        e = [abs(getattr(logs[i], attr) - cpu[key][i]) / abs(cpu[key][i]) for i in range(n)]
+        out[key] = {"max": max(e), "per_iteration": e}
+    if first is not None and dump and os.path.exists(dump):
+        ref = np.load(dump)
+        for name, got in (("u_iter0", first[0]), ("theta_iter0", first[1])):
+            r = ref[name.split("_")[0]]
+            out[name] = float(np.max(np.abs(got - r)) / np.max(np.abs(r)))
+    return out
+
+
 # ----------------------------------------------------------------------------- our arm
 def job_rate(seconds, units, world, dist=None, device="cuda"):
     """Whole-job rate of `world` ranks that each processed `units` in `seconds` of their own: the
@@ -550,9 +706,12 @@ def main():
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
     # the CPU baseline runs first, in its own interpreter, before this process touches CUDA
-    cpu = None
+    cpu = cpu_omp = None
+    dump = os.path.join(ROOT, "gpurun_out", "_oracle_iter0.npz") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) \
+        else os.path.join("/tmp", f"_oracle_iter0_{os.getpid()}.npz")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(CPU_SAMPLE_ITERS)
+        cpu = oracle_sample(CPU_SAMPLE_ITERS, warm=args.warmup, dump=dump)
+        cpu_omp = oracle_omp_pcg()
 
     import torch
     import __graft_entry__
@@ -567,24 +726,17 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = api.Context(local, stream=stream.cuda_stream)
     ctx.set_timing(True)
-    if args.batch_only:
-        peaks = {}
-        try:
-            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        except OSError:
-            pass
-        print(json.dumps(bench_batch(api, ctx, stream, peaks, args.batch_n, args.batch_maxit, plain=False,
-                                     mg_only=args.batch_mg_only)), flush=True)
-        ctx.close()
-        return
     mesh, prob = make_problem(api, ctx)
     opts = run_options(api, args.precision, args.precond)
     ppl = api.PPL(1)
     flush = torch.empty(max(args.l2_flush_mb, 1) * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2
 
     it = 0
+    warm_logs, first = [], None
     for _ in range(args.warmup):
-        prob.opt_step(it, opts, ppl)
+        warm_logs.append(prob.opt_step(it, opts, ppl))
+        if it == 0:
+            first = (prob.get(api._lib.FO_FIELD_U), prob.get(api._lib.FO_FIELD_THETA))
         it += 1
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -633,21 +785,27 @@ def main():
     except OSError:
         pass
     if args.precond == "mg":
-        bpi = mg_state_bytes_per_iteration(NX, NY, 2)
-        launch_ms = state_ms / len(logs)                  # one state solve (one k_pcg_mg launch) per step
+        # algorithmic bytes of one CG iteration in the survey's model (9 vector passes of the
+        # state DOFs plus connectivity, coefficient flags and coordinates), per launch of the
+        # state solve; the time is that launch alone (CUDA events around it, no hierarchy rebuild)
+        w = 8 if args.precision == "fp64" else 4
+        bpi = survey_pcg_bytes(2 * mesh.num_nodes, 2 * NX * NY, mesh.num_nodes, 2, w)
+        launch_ms = sum(l.ms_state_kernel for l in logs) / len(logs)
         its_per_launch = state_iters / len(logs)
         achieved = bpi * its_per_launch / (launch_ms / 1e3) / 1e9
         hbm = peaks.get("hbm_gbs", 6800.0)
         # DRAM bytes of one launch of this kernel, from a one-pass ncu capture of it as built now:
-        # the hierarchy is read once, then served from L2
-        traffic = 14.12e6 + 0.56e6
+        # the hierarchy is read once, then served from L2 (None until captured for this build)
+        traffic = C2_STATE_TRAFFIC.get(args.precision)
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": traffic, "kernel": "k_pcg_mg<2, 2, true, 1>",
+                "traffic": traffic, "kernel": "k_pcg_mg<2, 2, true, 1, %s>" % ("double" if w == 8 else "float"),
                 "algorithmic_bytes_per_iteration": bpi, "iterations_per_launch": its_per_launch,
                 "launch_ms": launch_ms,
-                "note": "peak = measured HBM copy bandwidth; the state hierarchy (~15 MB) stays in L2, so the "
-                        "kernel is bound by the latency of its ~40 grid barriers per iteration, not by HBM; "
-                        "launch_ms is the state phase (hierarchy rebuild + solve) on the launching stream"}
+                "implementation_bytes_per_iteration": mg_state_bytes_per_iteration(NX, NY, 2),
+                "note": "peak = measured HBM copy bandwidth (of measured); algorithmic bytes = 9 vector passes "
+                        "+ connectivity/flags/coordinates per CG iteration; the multigrid CG also streams its "
+                        "stored rows and V-cycle levels (implementation_bytes_per_iteration), all L2-resident "
+                        "(~15 MB), so the kernel is bound by the latency of its grid barriers, not by HBM"}
     else:
         NT = 2 * NX * NY
         # FP64 work of a Jacobi-PCG iteration: per node its two-component difference-form row
@@ -675,6 +833,21 @@ def main():
         "reinit_separate": reinit_info,
     }
 
+    # the same optimisation in the other precision (FP64 CG vs FP32 CG + FP64 refinement), each
+    # against the FP64 oracle on the iterations the CPU baseline ran
+    if rank == 0 and not args.no_precision_pair and args.precond == "mg":
+        other = "mixed" if args.precision == "fp64" else "fp64"
+        alt = rerun(api, ctx, stream, other, args.precond, args.warmup, args.steps, flush)
+        mine = {"opt_iters_per_s": value, "state_ms_per_step": phase["state"],
+                "state_kernel_ms_per_step": sum(l.ms_state_kernel for l in logs) / len(logs),
+                "state_iterations_per_step": state_iters / len(logs),
+                "refinements_per_step": sum(l.state.outer_iterations for l in logs) / len(logs)}
+        pair = {args.precision: mine, other: {k: v for k, v in alt.items() if k not in ("logs", "first")}}
+        if cpu is not None:
+            pair[args.precision]["error_vs_fp64_oracle"] = errors_vs_oracle(warm_logs + logs, first, cpu, dump)
+            pair[other]["error_vs_fp64_oracle"] = errors_vs_oracle(alt["logs"], alt["first"], cpu, dump)
+        line["precision_pair"] = pair
+
     # end to end through the C ABI with host buffers: phi in from pinned host memory, phi out
     if not args.no_e2e:
         import numpy as np
@@ -700,16 +873,25 @@ def main():
         line["e2e"] = {"value": e2e_value, "unit": "opt-iters/s",
                        "h2d_bytes_per_step": 8 * mesh2.num_nodes, "d2h_bytes_per_step": 8 * mesh2.num_nodes}
     if rank == 0 and not args.no_batch:
-        line["batch"] = bench_batch(api, ctx, stream, peaks, args.batch_n, args.batch_maxit)
+        line["batch"] = bench_batch(api, ctx, stream, peaks)
     if rank == 0 and not args.no_configs:
-        line["configs"] = bench_configs(api, ctx, stream)
+        line["configs"] = bench_configs(api, ctx, stream, peaks)
     if rank == 0 and not args.no_serving:
         line["serving"] = bench_serving(api, ctx, args.serving_requests)
     if cpu is not None:
         line["cpu_baseline"] = {"value": len(cpu["times"]) / sum(cpu["times"]), "unit": "opt-iters/s", "cores": 1,
                                 "kind": "oracle", "cpu": cpu_model(),
-                                "sample": f"iterations 0..{len(cpu['times']) - 1} of the same optimisation, "
-                                          "FP64 oracle with sparse direct solves, one host thread"}
+                                "sample": f"iterations {args.warmup}..{args.warmup + len(cpu['times']) - 1} of the "
+                                          f"same optimisation (the first timed ones of the GPU arm) after "
+                                          f"{args.warmup} untimed ones, FP64 oracle with sparse direct solves, "
+                                          "one host thread"}
+    if cpu_omp is not None:
+        gpu = gpu_same_system(api, ctx, stream)
+        line["cpu_baseline"]["openmp_pcg"] = dict(
+            cpu_omp, kind="oracle Jacobi-PCG (C, OpenMP)", cores=cpu_omp["threads"], cpu=cpu_model(),
+            sample="the cantilever's first state system (phi0, 66,048 free DOFs) from zero to 1e-8",
+            gpu_same_system=gpu,
+            iteration_ratio_gpu_jacobi_vs_cpu=gpu["jacobi_pcg"]["iterations"] / max(cpu_omp["iterations"], 1))
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

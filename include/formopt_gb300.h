@@ -154,8 +154,11 @@ typedef struct {
   int precond;              /* FO_PC_JACOBI, or FO_PC_MG: an FP32 geometric-multigrid   */
                             /* V-cycle as preconditioner, on grids that halve at least  */
                             /* once down to a coarsest level of <= 8192 unknowns (else  */
-                            /* the Jacobi solver runs).  Single problems (state,        */
-                            /* adjoint, velocity): FP64 CG whatever the precision.      */
+                            /* the Jacobi solver runs).  Single problems: FO_FP64 ->    */
+                            /* FP64 CG; FO_MIXED (state, adjoint) -> FP64 refinement     */
+                            /* around an FP32 CG (FP32 rows and vectors, FP64 dots;      */
+                            /* inner_rtol, inner_maxit per step); the velocity solve is */
+                            /* FP64 CG whatever the precision.                          */
                             /* Batches (state, adjoint): FO_FP64 -> FP64 CG; FO_MIXED -> */
                             /* FP64 refinement around an FP32 CG (inner_rtol,           */
                             /* inner_maxit per refinement step), stopping an instance   */
@@ -198,6 +201,10 @@ typedef struct {
    * fo_ctx_set_timing(ctx, 1) is on, else 0): coefficients + state solve, functionals,
    * shape derivative, velocity, transport (assembly + steps), reinitialisation */
   double ms_state, ms_functionals, ms_shape, ms_velocity, ms_transport, ms_reinit;
+  /* with timing on: device time of the persistent multigrid state-solve launch alone (no
+   * hierarchy rebuild; FO_MIXED: its FP32 CG launches summed over the refinement steps);
+   * 0 when the state solve ran another solver */
+  double ms_state_kernel;
 } fo_iter_log;
 
 /* ---------------------------------------------------------------- context ----- */
@@ -213,6 +220,10 @@ FO_API fo_status fo_ctx_memory(const fo_ctx *ctx, size_t *bytes_in_use);
 FO_API fo_status fo_ctx_set_timing(fo_ctx *ctx, int on);
 /* Number of kernels this library has launched in the process so far (all contexts). */
 FO_API fo_status fo_launch_count(unsigned long long *out);
+/* With timing on (fo_ctx_set_timing): device time in ms of the persistent multigrid CG
+ * launch(es) of the last multigrid state or adjoint solve alone (FO_MIXED: its FP32 CG launches
+ * summed over the refinement steps), measured with CUDA events on the context's stream. */
+FO_API fo_status fo_ctx_solve_kernel_ms(const fo_ctx *ctx, double *ms);
 /* wait for all work enqueued on the context's stream */
 FO_API fo_status fo_ctx_sync(fo_ctx *ctx);
 

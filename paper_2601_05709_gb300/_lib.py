@@ -100,7 +100,7 @@ class IterLog(C.Structure):
                 ("state", SolveStats), ("velocity", SolveStats), ("transport", SolveStats),
                 ("reinit_stats", SolveStats), ("ms_state", C.c_double), ("ms_functionals", C.c_double),
                 ("ms_shape", C.c_double), ("ms_velocity", C.c_double), ("ms_transport", C.c_double),
-                ("ms_reinit", C.c_double)]
+                ("ms_reinit", C.c_double), ("ms_state_kernel", C.c_double)]
 
 
 VP = C.c_void_p
@@ -117,6 +117,7 @@ PROTOTYPES = {
     "fo_ctx_memory": (ST, [VP, C.POINTER(C.c_size_t)]),
     "fo_ctx_sync": (ST, [VP]),
     "fo_ctx_set_timing": (ST, [VP, C.c_int]),
+    "fo_ctx_solve_kernel_ms": (ST, [VP, DP]),
     "fo_launch_count": (ST, [C.POINTER(C.c_ulonglong)]),
     "fo_mesh_box": (ST, [VP, C.c_int, C.POINTER(C.c_int), DP, DP, C.POINTER(VP)]),
     "fo_mesh_destroy": (ST, [VP]),

@@ -137,6 +137,12 @@ class Context:
     def set_timing(self, on=True):
         self.check(self.lib.fo_ctx_set_timing(self.handle, int(bool(on))), "fo_ctx_set_timing")
 
+    def solve_kernel_ms(self):
+        """Device time of the last multigrid state / adjoint solve's CG launch(es) (timing on)."""
+        v = C.c_double()
+        self.check(self.lib.fo_ctx_solve_kernel_ms(self.handle, C.byref(v)), "fo_ctx_solve_kernel_ms")
+        return v.value
+
     def selftest_barrier(self, blocks, skip, limit_ms):
         """(status, blocks that gave up) of the bounded grid barrier with block `skip` absent."""
         g = C.c_int(0)

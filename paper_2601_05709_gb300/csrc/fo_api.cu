@@ -98,6 +98,8 @@ extern "C" fo_status fo_ctx_destroy(fo_ctx *ctx) {
   if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
   for (auto &e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  for (auto &e : ctx->ev_solve)
+    if (e) cudaEventDestroy(e);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return FO_OK;
@@ -138,9 +140,17 @@ extern "C" fo_status fo_selftest_barrier(fo_ctx *ctx, int blocks, int skip, doub
 
 extern "C" fo_status fo_ctx_set_timing(fo_ctx *ctx, int on) {
   if (!ctx) return FO_EINVAL;
-  if (on && !ctx->ev[0])
+  if (on && !ctx->ev[0]) {
     for (auto &e : ctx->ev) FO_CU(ctx, cudaEventCreate(&e));
+    for (auto &e : ctx->ev_solve) FO_CU(ctx, cudaEventCreate(&e));
+  }
   ctx->timing = on ? 1 : 0;
+  return FO_OK;
+}
+
+extern "C" fo_status fo_ctx_solve_kernel_ms(const fo_ctx *ctx, double *ms) {
+  if (!ctx || !ms) return FO_EINVAL;
+  *ms = ctx->last_solve_ms;
   return FO_OK;
 }
 
@@ -846,8 +856,10 @@ extern "C" fo_status fo_opt_step(fo_problem *p, int iter, const fo_run_options *
   const double h = o->h > 0 ? o->h : p->mesh->h_diam;
   FO_TRY(mark(0));
   FO_TRY(fo_coefficients(p));
+  ctx->last_solve_ms = 0.0;
   fo_status s = fo_state_solve(p, &o->state, &lg.state);
   if (s != FO_OK) return s;
+  lg.ms_state_kernel = ctx->last_solve_ms;
   FO_TRY(mark(1));
   double J = 0, C = 0;
   FO_TRY(fo_functionals(p, &J, &C));

@@ -25,6 +25,9 @@ struct fo_ctx {
   // per-phase timing of fo_opt_step
   int timing = 0;
   cudaEvent_t ev[8] = {};
+  // with timing on: device time of the last persistent multigrid solve launch alone
+  cudaEvent_t ev_solve[2] = {};
+  double last_solve_ms = 0.0;
 };
 
 // Structured Kuhn grid: everything a kernel needs to enumerate nodes and elements.

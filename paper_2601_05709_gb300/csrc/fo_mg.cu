@@ -49,11 +49,15 @@ struct MgDev {
   MgLevelDev lv[MG_MAX_LEVELS];
 };
 
-struct MgCg {
-  const double *W64;    // fine FP64 stencil rows
-  const double *b;      // right-hand side (zero on Dirichlet DOFs)
-  double *x;            // solution (start value when warm)
-  double *r, *p[2], *s, *z;
+// Arguments of the CG loop.  V is the type of its vectors and of the fine operator's rows:
+// double for the FP64 CG, float for the inner CG of the mixed solve (FP64 refinement around an
+// FP32 CG); its dot products and scalars are FP64 either way.
+template <class V>
+struct MgCgT {
+  const V *W;           // fine stencil rows
+  const V *b;           // right-hand side (zero on Dirichlet DOFs)
+  V *x;                 // solution (start value when warm)
+  V *r, *p[2], *s, *z;
   double *partials, *out;
   int *status;
   GridBar bar;
@@ -61,6 +65,7 @@ struct MgCg {
   int maxit, warm;
   int stage;            // block 0 keeps the levels it runs alone in shared memory
 };
+using MgCg = MgCgT<double>;
 
 // ------------------------------------------------------------------ level operations
 template <int D, int NPN, bool FULL>
@@ -356,8 +361,8 @@ __host__ __device__ inline void mg_final_buffers(int L, int Lg, int nu, int nuc,
 // blocks), NC = NPN for the component-decoupled velocity form (one CG recurrence per
 // component, DOF k belonging to system k % NC); the loop stops when the summed residual meets
 // rtol.  Ends with the dot product b . x (for B(theta, theta) of the velocity solve).
-template <int D, int NPN, bool FULL, int NC>
-__global__ void __launch_bounds__(FO_BLOCK, D == 2 ? 1 : 2) k_pcg_mg(const MgDev *mgp, MgCg C) {
+template <int D, int NPN, bool FULL, int NC, class V = double>
+__global__ void __launch_bounds__(FO_BLOCK, D == 2 ? 1 : 2) k_pcg_mg(const MgDev *mgp, MgCgT<V> C) {
   extern __shared__ __align__(16) unsigned char mg_dsmem[];
   __shared__ MgDev mg;
   __shared__ MgDev mgs;   // block 0's view with the block-run levels in shared memory
@@ -376,9 +381,9 @@ __global__ void __launch_bounds__(FO_BLOCK, D == 2 ? 1 : 2) k_pcg_mg(const MgDev
   const Grid &g = L0.g;
   const long long N = g.num_nodes;
   const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x, step = (long long)gridDim.x * blockDim.x;
-  StencilOp<D, NPN, FULL, double> A;
+  StencilOp<D, NPN, FULL, V> A;
   A.g = g;
-  A.W = C.W64;
+  A.W = C.W;
   int rk = 0, zc[MG_MAX_LEVELS];
   mg_final_buffers(mg.L, mg.Lg, mg.nu, mg.nuc, zc);
   const int zfin = zc[0];
@@ -395,22 +400,22 @@ __global__ void __launch_bounds__(FO_BLOCK, D == 2 ? 1 : 2) k_pcg_mg(const MgDev
     for (long long a = first; a < N; a += step) {
       int idx[3];
       node_ijk(g, a, idx);
-      double ax[NPN];
-      if (C.warm) A.row(a, idx, VecX<double>{C.x}, ax);
+      V ax[NPN];
+      if (C.warm) A.row(a, idx, VecX<V>{C.x}, ax);
 #pragma unroll
       for (int c = 0; c < NPN; ++c) {
         const long long k = a * NPN + c;
         if (!C.warm) {
-          C.x[k] = 0.0;
-          ax[c] = 0.0;
+          C.x[k] = V(0);
+          ax[c] = V(0);
         }
-        const double rk0 = C.b[k] - ax[c];
+        const V rk0 = C.b[k] - ax[c];
         C.r[k] = rk0;
-        C.p[0][k] = 0.0;
+        C.p[0][k] = V(0);
         const float bf = (float)rk0;
         L0.b[k] = bf;
         L0.z[0][k] = (mg.L == 1 ? mg.omega : mg.om[0]) * L0.dinv[k] * bf;
-        v[NC + sys(c)] += C.b[k] * C.b[k];
+        v[NC + sys(c)] += (double)C.b[k] * (double)C.b[k];
       }
     }
     if (!grid_sync(C.bar)) return;
@@ -420,10 +425,10 @@ __global__ void __launch_bounds__(FO_BLOCK, D == 2 ? 1 : 2) k_pcg_mg(const MgDev
 #pragma unroll
       for (int c = 0; c < NPN; ++c) {
         const long long k = a * NPN + c;
-        const double zk = (double)L0.z[zfin][k];
+        const V zk = (V)L0.z[zfin][k];
         C.z[k] = zk;
-        v[sys(c)] += C.r[k] * zk;
-        v[2 * NC + sys(c)] += C.r[k] * C.r[k];
+        v[sys(c)] += (double)C.r[k] * (double)zk;
+        v[2 * NC + sys(c)] += (double)C.r[k] * (double)C.r[k];
       }
     if (!reduce_grid<3 * NC>(v, sred, stot, C.partials, rk, C.bar)) return;
 #pragma unroll
@@ -445,23 +450,23 @@ __global__ void __launch_bounds__(FO_BLOCK, D == 2 ? 1 : 2) k_pcg_mg(const MgDev
     double ps[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) ps[q] = 0.0;
-    const double *po = C.p[cur];
-    double *pn = C.p[cur ^ 1];
-    CombX<double, NC> pv{C.z, po, {}};
+    const V *po = C.p[cur];
+    V *pn = C.p[cur ^ 1];
+    CombX<V, NC> pv{C.z, po, {}};
 #pragma unroll
-    for (int q = 0; q < NC; ++q) pv.beta[q] = beta[q];
+    for (int q = 0; q < NC; ++q) pv.beta[q] = (V)beta[q];
     for (long long a = first; a < N; a += step) {
       int idx[3];
       node_ijk(g, a, idx);
-      double ap[NPN];
+      V ap[NPN];
       A.row(a, idx, pv, ap);
 #pragma unroll
       for (int c = 0; c < NPN; ++c) {
         const long long k = a * NPN + c;
-        const double pk = C.z[k] + beta[sys(c)] * po[k];
+        const V pk = C.z[k] + pv.beta[sys(c)] * po[k];
         pn[k] = pk;
         C.s[k] = ap[c];
-        ps[sys(c)] += pk * ap[c];
+        ps[sys(c)] += (double)pk * (double)ap[c];
       }
     }
     if (!reduce_grid<NC>(ps, sred, stot, C.partials, rk, C.bar)) return;
@@ -483,8 +488,8 @@ __global__ void __launch_bounds__(FO_BLOCK, D == 2 ? 1 : 2) k_pcg_mg(const MgDev
 #pragma unroll
       for (int c = 0; c < NPN; ++c) {
         const long long k = a * NPN + c;
-        C.x[k] += alpha[sys(c)] * pn[k];
-        const double rk1 = C.r[k] - alpha[sys(c)] * C.s[k];
+        C.x[k] += (V)alpha[sys(c)] * pn[k];
+        const V rk1 = C.r[k] - (V)alpha[sys(c)] * C.s[k];
         C.r[k] = rk1;
         const float bf = (float)rk1;
         L0.b[k] = bf;
@@ -499,10 +504,10 @@ __global__ void __launch_bounds__(FO_BLOCK, D == 2 ? 1 : 2) k_pcg_mg(const MgDev
 #pragma unroll
       for (int c = 0; c < NPN; ++c) {
         const long long k = a * NPN + c;
-        const double zk = (double)L0.z[zfin][k];
+        const V zk = (V)L0.z[zfin][k];
         C.z[k] = zk;
-        w[sys(c)] += C.r[k] * zk;
-        w[NC + sys(c)] += C.r[k] * C.r[k];
+        w[sys(c)] += (double)C.r[k] * (double)zk;
+        w[NC + sys(c)] += (double)C.r[k] * (double)C.r[k];
       }
     if (!reduce_grid<2 * NC>(w, sred, stot, C.partials, rk, C.bar)) return;
     if (threadIdx.x == 0)
@@ -523,7 +528,7 @@ __global__ void __launch_bounds__(FO_BLOCK, D == 2 ? 1 : 2) k_pcg_mg(const MgDev
   double bx[1] = {0.0};
   for (long long a = first; a < N; a += step)
 #pragma unroll
-    for (int c = 0; c < NPN; ++c) bx[0] += C.b[a * NPN + c] * C.x[a * NPN + c];
+    for (int c = 0; c < NPN; ++c) bx[0] += (double)C.b[a * NPN + c] * (double)C.x[a * NPN + c];
   if (!reduce_grid<1>(bx, sred, stot, C.partials, rk, C.bar)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     C.out[0] = rr;
@@ -909,29 +914,19 @@ static fo_status mg_prepare_velocity(fo_problem *p) {
 }
 
 // ------------------------------------------------------------------------------ solves
-template <int D, int NPN, bool FULL, int NC>
-static fo_status mg_run(fo_problem *p, fo_mg *mg, const double *W64, const double *b, double *x, long long n,
-                        const fo_solve_opts *o, fo_solve_stats *st, double *bx) {
+// One persistent launch of the CG loop with the arguments C (vectors bound by the caller).
+template <int D, int NPN, bool FULL, int NC, class V>
+static fo_status mg_launch(fo_problem *p, fo_mg *mg, MgCgT<V> C, const fo_solve_opts *o, double rtol, int maxit,
+                           int warm, fo_solve_stats *st, double *bx) {
   fo_ctx *ctx = p->ctx;
-  double *buf;
-  FO_TRY(fo_scratch(p, sizeof(double) * 6 * n, (void **)&buf));
-  MgCg C{};
-  C.W64 = W64;
-  C.b = b;
-  C.x = x;
-  C.r = buf;
-  C.p[0] = buf + n;
-  C.p[1] = buf + 2 * n;
-  C.s = buf + 3 * n;
-  C.z = buf + 4 * n;
   C.partials = p->red;
   C.out = p->red + (FO_RED_DOUBLES - 64);
   C.status = p->dev_status;
   C.bar = GridBar{p->bar, p->dev_status + DS_ERR, 2000000000ull};
-  C.rtol2 = o->rtol * o->rtol;
-  C.maxit = o->maxit;
-  C.warm = o->warm_start;
-  auto kern = k_pcg_mg<D, NPN, FULL, NC>;
+  C.rtol2 = rtol * rtol;
+  C.maxit = maxit;
+  C.warm = warm;
+  auto kern = k_pcg_mg<D, NPN, FULL, NC, V>;
   int grid;
   FO_TRY(fo_cooperative_grid(p, (const void *)kern, FO_BLOCK, 0, p->mesh->g.num_nodes, o->grid_blocks, &grid));
   // Block 0 keeps the levels it runs alone in shared memory when they fit and the launch
@@ -952,25 +947,156 @@ static fo_status mg_run(fo_problem *p, fo_mg *mg, const double *W64, const doubl
   void *argv[] = {(void *)&mgp, (void *)&C};
   FO_CU(ctx, cudaMemsetAsync(p->bar, 0, 64, ctx->stream));
   FO_CU(ctx, cudaMemsetAsync(p->dev_status, 0, sizeof(int) * DS_COUNT, ctx->stream));
+  const bool tm = ctx->timing != 0 && ctx->ev_solve[0] != nullptr;
+  if (tm) FO_CU(ctx, cudaEventRecord(ctx->ev_solve[0], ctx->stream));
   FO_CU(ctx, cudaLaunchCooperativeKernel((const void *)kern, grid, FO_BLOCK, argv, smem, ctx->stream));
   fo_note_launch(1);
   FO_CU(ctx, cudaGetLastError());
+  if (tm) FO_CU(ctx, cudaEventRecord(ctx->ev_solve[1], ctx->stream));
   FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars, C.out, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars + 32, p->dev_status, sizeof(int) * DS_COUNT, cudaMemcpyDeviceToHost,
                              ctx->stream));
   FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  if (tm) {
+    float ms = 0.f;
+    FO_CU(ctx, cudaEventElapsedTime(&ms, ctx->ev_solve[0], ctx->ev_solve[1]));
+    ctx->last_solve_ms += ms;
+  }
   const int *hs = (const int *)(ctx->h_scalars + 32);
   if (st) {
     memset(st, 0, sizeof *st);
     st->iterations = hs[DS_ITERS];
-    st->operator_applies = hs[DS_ITERS] + 1 + (o->warm_start ? 1 : 0);
+    st->operator_applies = hs[DS_ITERS] + 1 + (warm ? 1 : 0);
     st->outer_iterations = 1;
     st->rel_residual = ctx->h_scalars[1] > 0 ? std::sqrt(ctx->h_scalars[0] / ctx->h_scalars[1]) : 0.0;
   }
   if (bx) *bx = ctx->h_scalars[2];
   if (hs[DS_ERR] == DEV_TIMEOUT) return fo_fail(ctx, FO_ETIMEOUT, "grid barrier timed out in the multigrid PCG");
   if (!std::isfinite(ctx->h_scalars[0])) return fo_fail(ctx, FO_ENAN, "NaN in the multigrid PCG");
-  if (hs[DS_ERR] == DEV_NOCONV) return fo_fail(ctx, FO_ENOCONV, "multigrid PCG reached maxit=%d", o->maxit);
+  if (hs[DS_ERR] == DEV_NOCONV) return fo_fail(ctx, FO_ENOCONV, "multigrid PCG reached maxit=%d", maxit);
+  return FO_OK;
+}
+
+template <int D, int NPN, bool FULL, int NC>
+static fo_status mg_run(fo_problem *p, fo_mg *mg, const double *W64, const double *b, double *x, long long n,
+                        const fo_solve_opts *o, fo_solve_stats *st, double *bx) {
+  double *buf;
+  FO_TRY(fo_scratch(p, sizeof(double) * 6 * n, (void **)&buf));
+  MgCg C{};
+  C.W = W64;
+  C.b = b;
+  C.x = x;
+  C.r = buf;
+  C.p[0] = buf + n;
+  C.p[1] = buf + 2 * n;
+  C.s = buf + 3 * n;
+  C.z = buf + 4 * n;
+  return mg_launch<D, NPN, FULL, NC, double>(p, mg, C, o, o->rtol, o->maxit, o->warm_start, st, bx);
+}
+
+// ---- mixed: FP64 iterative refinement around the FP32 multigrid CG
+// r = b - A x with the FP64 rows; ||r||^2 and ||b||^2 as per-block partials
+__global__ void k_mg_ir_residual(const double *b, const double *ax, double *r, long long n, double *partials) {
+  __shared__ double sm[64];
+  double v[2] = {0, 0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double ri = b[i] - ax[i];
+    r[i] = ri;
+    v[0] += ri * ri;
+    v[1] += b[i] * b[i];
+  }
+  block_sum<2>(v, sm);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x * 2] = v[0];
+    partials[blockIdx.x * 2 + 1] = v[1];
+  }
+}
+// the two sums in a fixed order (deterministic)
+__global__ void k_mg_ir_total(const double *partials, int nblocks, double *out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (w >= 2) return;
+  double t = 0;
+  for (int b = lane; b < nblocks; b += 32) t += partials[(size_t)b * 2 + w];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  if (lane == 0) out[w] = t;
+}
+// the inner right-hand side: the residual scaled to unit norm, in FP32
+__global__ void k_mg_ir_scale(const double *r, double inv, float *b32, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b32[i] = (float)(r[i] * inv);
+}
+// x += scale * d (the correction accumulated in FP64)
+__global__ void k_mg_ir_update(double *x, const float *d, double scale, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = fma(scale, (double)d[i], x[i]);
+}
+
+// Each refinement step forms the true residual r = b - A x in FP64, solves A d = r / ||r|| with
+// the FP32 CG (FP32 rows and vectors, FP64 dot products) preconditioned by the same FP32
+// V-cycle to the relative reduction inner_rtol, and adds ||r|| d to x in FP64.  It stops when
+// ||r|| <= rtol ||b||, or when two consecutive steps fail to halve ||r|| (the FP64 residual's
+// own rounding floor is reached).
+template <int D, int NPN>
+static fo_status mg_state_mixed(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st) {
+  fo_ctx *ctx = p->ctx;
+  const long long n = p->ndof;
+  double *buf;
+  FO_TRY(fo_scratch(p, sizeof(double) * 2 * n + sizeof(float) * 7 * n + 256, (void **)&buf));
+  double *r64 = buf, *ax64 = buf + n;
+  float *f = reinterpret_cast<float *>(buf + 2 * n);
+  MgCgT<float> C{};
+  C.W = p->Wst32;
+  C.b = f;
+  C.x = f + n;
+  C.r = f + 2 * n;
+  C.p[0] = f + 3 * n;
+  C.p[1] = f + 4 * n;
+  C.s = f + 5 * n;
+  C.z = f + 6 * n;
+  const int blocks = fo_blocks_for(n, FO_BLOCK, 1024);
+  double *sums = p->red + (FO_RED_DOUBLES - 128);
+  if (!o->warm_start) FO_CU(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream));
+  fo_solve_stats s;
+  memset(&s, 0, sizeof s);
+  double bnorm2 = -1, prev_rn2 = INFINITY, prev2_rn2 = INFINITY;
+  const int max_outer = 60;
+  for (int outer = 0;; ++outer) {
+    FO_TRY(fo_launch_state_apply(p, x, ax64, true));
+    k_mg_ir_residual<<<blocks, FO_BLOCK, 0, ctx->stream>>>(b, ax64, r64, n, p->red);
+    k_mg_ir_total<<<1, 64, 0, ctx->stream>>>(p->red, blocks, sums);
+    fo_note_launch(2);
+    FO_CU(ctx, cudaGetLastError());
+    FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars, sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    const double rn2 = ctx->h_scalars[0];
+    if (bnorm2 < 0) bnorm2 = ctx->h_scalars[1];
+    s.operator_applies += 1;
+    s.rel_residual = bnorm2 > 0 ? std::sqrt(rn2 / bnorm2) : 0.0;
+    if (!std::isfinite(rn2)) return fo_fail(ctx, FO_ENAN, "NaN in the refinement residual");
+    if (rn2 <= o->rtol * o->rtol * bnorm2 || bnorm2 == 0 || rn2 == 0) break;
+    if (outer >= 2 && rn2 > 0.25 * prev_rn2 && prev_rn2 > 0.25 * prev2_rn2) break;
+    prev2_rn2 = prev_rn2;
+    prev_rn2 = rn2;
+    if (outer >= max_outer || s.iterations >= o->maxit) {
+      if (st) *st = s;
+      return fo_fail(ctx, FO_ENOCONV, "iterative refinement stalled at %.3e", s.rel_residual);
+    }
+    const double rn = std::sqrt(rn2);
+    k_mg_ir_scale<<<blocks, FO_BLOCK, 0, ctx->stream>>>(r64, 1.0 / rn, f, n);
+    fo_note_launch(1);
+    fo_solve_stats in;
+    const fo_status r = mg_launch<D, NPN, true, 1, float>(p, p->mg, C, o, o->inner_rtol, o->inner_maxit, 0, &in,
+                                                          nullptr);
+    if (r != FO_OK && r != FO_ENOCONV) return r;   // an inner cap only ends that step
+    s.iterations += in.iterations;
+    s.operator_applies += in.operator_applies;
+    s.outer_iterations = outer + 1;
+    k_mg_ir_update<<<blocks, FO_BLOCK, 0, ctx->stream>>>(x, C.x, rn, n);
+    fo_note_launch(1);
+    FO_CU(ctx, cudaGetLastError());
+  }
+  if (st) *st = s;
   return FO_OK;
 }
 
@@ -978,6 +1104,11 @@ fo_status fo_state_pcg_mg(fo_problem *p, const double *b, double *x, const fo_so
   FO_TRY(mg_prepare_state(p));
   const int d = p->mesh->g.dim;
   const long long n = p->ndof;
+  p->ctx->last_solve_ms = 0.0;
+  if (o->precision == FO_MIXED) {
+    if (p->desc.kind == FO_ELASTIC) return d == 2 ? mg_state_mixed<2, 2>(p, b, x, o, st) : mg_state_mixed<3, 3>(p, b, x, o, st);
+    return d == 2 ? mg_state_mixed<2, 1>(p, b, x, o, st) : mg_state_mixed<3, 1>(p, b, x, o, st);
+  }
   if (p->desc.kind == FO_ELASTIC)
     return d == 2 ? mg_run<2, 2, true, 1>(p, p->mg, p->Wst, b, x, n, o, st, nullptr)
                   : mg_run<3, 3, true, 1>(p, p->mg, p->Wst, b, x, n, o, st, nullptr);

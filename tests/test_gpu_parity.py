@@ -212,13 +212,17 @@ def test_multigrid_falls_back_on_odd_grids(ctx, api):
 
 
 @pytest.mark.parametrize("c", [case(**HEAT2D), cantilever2d((128, 64)), cantilever3d((12, 6, 6))])
-def test_state_solve_mixed(ctx, api, c):
+@pytest.mark.parametrize("pc", [0, 1], ids=["jacobi", "multigrid"])
+def test_state_solve_mixed(ctx, api, c, pc):
+    """FP64 refinement around an FP32 inner CG (Jacobi: FP32 operator, FP64 vectors; multigrid:
+    FP32 operator and vectors, FP32 V-cycle): 1e-8 of the oracle (the mixed target), backward
+    error at the FP64 level."""
     mesh, prob = gpu_problem(ctx, c)
     op = oracle_problem(c)
     phi = (workloads.phi_cos(op.mesh.coords) if c["dim"] == 2 else
            workloads.phi_bumps(op.mesh.coords, workloads.bump_centres(c["lo"], c["hi"], 8, 0), 0.25, 0.2))
     prob.set_levelset(phi)
-    st = prob.state_solve(api.solve_opts(precision=api.FO_MIXED, rtol=1e-12, inner_rtol=1e-3))
+    st = prob.state_solve(api.solve_opts(precision=api.FO_MIXED, rtol=1e-12, inner_rtol=1e-3, precond=pc))
     u = prob.get(api._lib.FO_FIELD_U)
     u_ref, A, _ = op.state(phi)
     assert rel(u, u_ref) <= 1e-8, (rel(u, u_ref), st.iterations, st.outer_iterations)
