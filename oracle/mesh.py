@@ -137,3 +137,65 @@ class BoxMesh:
                 inside &= (c[:, a] > lo[a]) & (c[:, a] < hi[a])
             mask |= inside
         return mask.astype(np.uint8)
+
+
+class ArrayMesh:
+    """A simplicial mesh given by arrays (the role of a Gmsh / DOLFINx mesh in Sec. 5.1):
+    coords [N_n, d] (FP64) and cells [N_T, d+1] (vertex ids, any order and orientation).
+
+    Boundary faces are those of the bounding box D = prod [lo_k, hi_k] of the nodes: a node
+    lies on face (axis, side) when its coordinate along `axis` equals the box's lower
+    (side 0) or upper (side 1) bound exactly; a boundary facet of that face is a facet of an
+    element whose d vertices all lie on it.  |D| is the sum of the element measures, so the
+    mesh diameter h of Sec. 5.6 keeps its meaning for meshes that do not fill a box.
+    """
+
+    def __init__(self, coords, cells):
+        self.coords = np.ascontiguousarray(coords, dtype=np.float64)
+        self.cells = np.ascontiguousarray(cells, dtype=np.int32)
+        self.dim = self.coords.shape[1]
+        if self.dim not in (2, 3) or self.cells.shape[1] != self.dim + 1:
+            raise ValueError("coords must be [N, 2] with triangles or [N, 3] with tetrahedra")
+        self.num_nodes = self.coords.shape[0]
+        self.num_elems = self.cells.shape[0]
+        self.lo = tuple(float(v) for v in self.coords.min(axis=0))
+        self.hi = tuple(float(v) for v in self.coords.max(axis=0))
+
+    @property
+    def num_dofs_vector(self):
+        return self.dim * self.num_nodes
+
+    def volume(self):
+        X = self.coords[self.cells]
+        E = np.swapaxes(X[:, 1:, :] - X[:, :1, :], 1, 2)
+        return float(np.sum(np.abs(np.linalg.det(E))) / math.factorial(self.dim))
+
+    def diameter(self):
+        """Mesh diameter h of Sec. 5.6 with |D| = the sum of the element measures (same reading
+        as BoxMesh.diameter: the square root of the printed expression)."""
+        D, NT = self.volume(), self.num_elems
+        if self.dim == 2:
+            return math.sqrt(4.0 * D / (NT * math.sqrt(3.0)))
+        return math.sqrt((6.0 * math.sqrt(2.0) * D / NT) ** (2.0 / 3.0))
+
+    def face_nodes(self, axis, side):
+        target = self.lo[axis] if side == 0 else self.hi[axis]
+        return self.coords[:, axis] == target
+
+    def dirichlet_mask(self, faces, ncomp):
+        on = np.zeros(self.num_nodes, dtype=bool)
+        for axis, side in faces:
+            on |= self.face_nodes(axis, side)
+        return np.repeat(on, ncomp).astype(np.uint8)
+
+    def boundary_facets(self, axis, side):
+        on = self.face_nodes(axis, side)
+        out = []
+        for m in range(self.dim + 1):
+            facet = np.delete(self.cells, m, axis=1)
+            keep = np.all(on[facet], axis=1)
+            out.append(facet[keep])
+        return np.concatenate(out, axis=0)
+
+    centroids = BoxMesh.centroids
+    subdomain_mask = BoxMesh.subdomain_mask

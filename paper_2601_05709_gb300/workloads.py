@@ -73,6 +73,69 @@ def fourier_loads(coords, amp):
     return amp @ basis
 
 
+def simplex_mesh(dim, n, lo, hi, jitter=0.0, seed=0, pattern="kuhn", shuffle=False):
+    """An input mesh given as arrays (coords [N_n, d], cells [N_T, d+1] int32), standing in for
+    the paper's Gmsh meshes: the box prod [lo_k, hi_k] with n_k cells per axis, each cell split
+    into simplices, then optionally perturbed and renumbered.
+
+    pattern: "kuhn" (every cell split along the same main diagonal: 2 triangles / 6 tets) or,
+    in 2D, "alternate" (cells split along alternating diagonals, a checkerboard).  jitter:
+    interior nodes move by U(-jitter/2, jitter/2) cell widths per axis (boundary nodes stay on
+    the box's faces).  shuffle: node ids, element order and each element's vertex order are
+    permuted at random.  Everything is seeded."""
+    rng = np.random.default_rng(seed)
+    n = [int(v) for v in n[:dim]]
+    lo = np.asarray(lo[:dim], dtype=np.float64)
+    hi = np.asarray(hi[:dim], dtype=np.float64)
+    shape = [v + 1 for v in n]
+    idx = np.stack(np.meshgrid(*[np.arange(s) for s in shape], indexing="ij"), axis=-1).reshape(-1, dim)
+    # node id: first axis fastest
+    def nid(ijk):
+        out = ijk[..., dim - 1]
+        for a in range(dim - 2, -1, -1):
+            out = ijk[..., a] + shape[a] * out
+        return out
+    order = np.argsort(nid(idx), kind="stable")
+    idx = idx[order]
+    h = (hi - lo) / np.asarray(n, dtype=np.float64)
+    coords = lo + idx * h
+    if jitter > 0:
+        inner = np.all((idx > 0) & (idx < np.asarray(n)), axis=1)
+        coords[inner] += (rng.random((int(inner.sum()), dim)) - 0.5) * jitter * h
+    corner = np.stack(np.meshgrid(*[np.arange(v) for v in n], indexing="ij"), axis=-1).reshape(-1, dim)
+    cells = []
+    if dim == 2:
+        for (i, j) in corner:
+            v00, v10 = nid(np.array([i, j])), nid(np.array([i + 1, j]))
+            v01, v11 = nid(np.array([i, j + 1])), nid(np.array([i + 1, j + 1]))
+            if pattern == "alternate" and (i + j) % 2 == 1:
+                cells += [(v00, v10, v01), (v10, v11, v01)]
+            else:
+                cells += [(v00, v10, v11), (v00, v01, v11)]
+    else:
+        perms = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+        for c in corner:
+            for perm in perms:
+                v = c.copy()
+                tet = [nid(v)]
+                for m in range(3):
+                    v = v.copy()
+                    v[perm[m]] += 1
+                    tet.append(nid(v))
+                cells.append(tuple(tet))
+    cells = np.asarray(cells, dtype=np.int64)
+    if shuffle:
+        newid = rng.permutation(coords.shape[0])
+        inv = np.empty_like(newid)
+        inv[newid] = np.arange(newid.size)
+        coords = coords[inv]
+        cells = newid[cells]
+        cells = cells[rng.permutation(cells.shape[0])]
+        for e in range(cells.shape[0]):
+            cells[e] = np.roll(cells[e], int(rng.integers(0, dim + 1)))
+    return np.ascontiguousarray(coords), np.ascontiguousarray(cells, dtype=np.int32)
+
+
 def random_field(n, seed, scale=1.0):
     return scale * np.random.default_rng(seed).standard_normal(n)
 

@@ -120,7 +120,8 @@ def test_served_heat_matches_oracle(ctx):
     phi = workloads.phi_cos(op.mesh.coords)
     desc = api.model_desc(FO_HEAT, dirichlet=[(0, 0)], f_nodal=np.ones(op.mesh.num_nodes), alpha_mass=0.01,
                           velocity_dirichlet=True)
-    rq = api.ServedRequest(2, (n, n), desc, phi=phi, state=api.solve_opts(rtol=1e-12), want_theta=True)
+    rq = api.ServedRequest(2, (n, n), desc, phi=phi, state=api.solve_opts(rtol=1e-13),
+                           velocity=api.solve_opts(rtol=1e-13), want_theta=True)
     srv = api.Server(ctx, executors=2)
     st, t = srv.submit(rq)
     r = srv.wait(t, 60.0)
@@ -131,5 +132,5 @@ def test_served_heat_matches_oracle(ctx):
     assert abs(r.J - J) <= 1e-10 * abs(J)
     from oracle import velocity as ovel
     theta, Btt = ovel.solve(op.mesh, op.vform, op.rhs(u, A, chi, 0.0))
-    assert rel(rq.theta, theta) <= 1e-8
-    assert abs(r.Btt - Btt) <= 1e-8 * abs(Btt)
+    assert close_scaled(rq.theta, theta, 1e-10), np.max(np.abs(rq.theta - theta))
+    assert abs(r.Btt - Btt) <= 1e-10 * abs(Btt)
