@@ -2,8 +2,9 @@
  * formopt_gb300.h -- C ABI of the GB300 (sm_103a) level-set shape-optimisation hot path.
  *
  * The library computes one iteration of the level-set algorithm of arXiv 2601.05709
- * (Algorithm 1, Sec. 4) on a fixed structured Kuhn simplicial mesh of a box D, with P1
- * finite elements:
+ * (Algorithm 1, Sec. 4) on a fixed simplicial mesh -- a structured Kuhn mesh of a box D
+ * (fo_mesh_box) or a general mesh given as arrays (fo_mesh_from_arrays) -- with P1 finite
+ * elements:
  *   state solve with the ersatz coefficient A_Omega(phi)     (Sec. 6.2 eq. compli_weak,
  *                                                             Sec. 6.3 eq. heat_weak)
  *   cost and volume constraint                               (eqs compli_cost, heat_cost,
@@ -232,6 +233,22 @@ FO_API fo_status fo_ctx_sync(fo_ctx *ctx);
  * replacing the paper's Gmsh meshes).  Connectivity and coordinates are built on the GPU. */
 FO_API fo_status fo_mesh_box(fo_ctx *ctx, int dim, const int n[3], const double lo[3], const double hi[3],
                       fo_mesh **out);
+/* A general simplicial mesh given as arrays (the role of the paper's Gmsh / DOLFINx meshes,
+ * Sec. 5.1 helpers and Sec. 6 examples): coords [nn][dim] FP64 and cells [nt][dim+1] int32
+ * vertex ids (any numbering, vertex order and orientation), host arrays copied before the call
+ * returns.  Box faces (face = 2*axis + side, as for fo_mesh_box) are those of the nodes'
+ * bounding box: a node lies on a face when its coordinate equals the box's bound exactly, and
+ * a boundary facet (a facet of one element only) belongs to a face when all its vertices do.
+ * Dirichlet faces, tractions, the H^1_0 velocity space and the normal penalty refer to these
+ * (the penalty uses every boundary facet with its outward normal).  Operators are assembled
+ * per coefficient update into the node graph (node-block CSR); solves are Jacobi-PCG (state,
+ * velocity; FO_MIXED: FP32 inner solves in FP64 refinement) and BiCGStab (transport,
+ * reinitialisation).  fo_mesh_query reports n = 0, the bounding box, and |D| = the sum of the
+ * element measures (which also defines h).  Task-parallel batches and serving need box meshes.
+ * FO_EINVAL on a vertex id out of range, a facet shared by more than two elements or a
+ * degenerate element; FO_ENAN on a non-finite coordinate. */
+FO_API fo_status fo_mesh_from_arrays(fo_ctx *ctx, int dim, int64_t nn, const double *coords, int64_t nt,
+                                     const int32_t *cells, fo_mesh **out);
 FO_API fo_status fo_mesh_destroy(fo_mesh *mesh);
 FO_API fo_status fo_mesh_query(const fo_mesh *mesh, fo_mesh_info *out);
 /* Copy connectivity (int32 [N_T][d+1]) and coordinates (f64 [N_n][d]) to host arrays;

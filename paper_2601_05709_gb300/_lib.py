@@ -120,6 +120,7 @@ PROTOTYPES = {
     "fo_ctx_solve_kernel_ms": (ST, [VP, DP]),
     "fo_launch_count": (ST, [C.POINTER(C.c_ulonglong)]),
     "fo_mesh_box": (ST, [VP, C.c_int, C.POINTER(C.c_int), DP, DP, C.POINTER(VP)]),
+    "fo_mesh_from_arrays": (ST, [VP, C.c_int, C.c_int64, VP, C.c_int64, VP, C.POINTER(VP)]),
     "fo_mesh_destroy": (ST, [VP]),
     "fo_mesh_query": (ST, [VP, C.POINTER(MeshInfo)]),
     "fo_mesh_copy_out": (ST, [VP, VP, VP]),

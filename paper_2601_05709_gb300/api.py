@@ -152,6 +152,10 @@ class Context:
     def mesh_box(self, dim, n, lo, hi):
         return Mesh(self, dim, n, lo, hi)
 
+    def mesh_from_arrays(self, coords, cells):
+        """A general simplicial mesh from node coordinates [N_n, d] and cells [N_T, d+1]."""
+        return Mesh(self, None, None, None, None, arrays=(coords, cells))
+
     def close(self):
         if self.handle:
             self.lib.fo_ctx_destroy(self.handle)
@@ -165,13 +169,21 @@ class Context:
 
 
 class Mesh:
-    def __init__(self, ctx, dim, n, lo, hi):
+    def __init__(self, ctx, dim, n, lo, hi, arrays=None):
         self.ctx = ctx
-        nn = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
-        lo3 = (C.c_double * 3)(*(list(lo) + [0.0] * (3 - len(lo))))
-        hi3 = (C.c_double * 3)(*(list(hi) + [1.0] * (3 - len(hi))))
         h = C.c_void_p()
-        ctx.check(ctx.lib.fo_mesh_box(ctx.handle, dim, nn, lo3, hi3, C.byref(h)), "fo_mesh_box")
+        if arrays is not None:
+            coords = np.ascontiguousarray(arrays[0], dtype=np.float64)
+            cells = np.ascontiguousarray(arrays[1], dtype=np.int32)
+            dim = coords.shape[1]
+            ctx.check(ctx.lib.fo_mesh_from_arrays(ctx.handle, dim, coords.shape[0], coords.ctypes.data_as(C.c_void_p),
+                                                  cells.shape[0], cells.ctypes.data_as(C.c_void_p), C.byref(h)),
+                      "fo_mesh_from_arrays")
+        else:
+            nn = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+            lo3 = (C.c_double * 3)(*(list(lo) + [0.0] * (3 - len(lo))))
+            hi3 = (C.c_double * 3)(*(list(hi) + [1.0] * (3 - len(hi))))
+            ctx.check(ctx.lib.fo_mesh_box(ctx.handle, dim, nn, lo3, hi3, C.byref(h)), "fo_mesh_box")
         self.handle = h
         info = _lib.MeshInfo()
         ctx.check(ctx.lib.fo_mesh_query(h, C.byref(info)), "fo_mesh_query")

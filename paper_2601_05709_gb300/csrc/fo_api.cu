@@ -7,6 +7,7 @@
 #include <atomic>
 
 #include "fo_internal.cuh"
+#include "fo_umesh.cuh"
 
 // ----------------------------------------------------------------------- launch counter
 static std::atomic<unsigned long long> g_launches{0};
@@ -248,6 +249,59 @@ extern "C" fo_status fo_mesh_box(fo_ctx *ctx, int dim, const int n[3], const dou
   return FO_OK;
 }
 
+extern "C" fo_status fo_mesh_from_arrays(fo_ctx *ctx, int dim, int64_t nn, const double *coords, int64_t nt,
+                                        const int32_t *cells, fo_mesh **out) {
+  if (!ctx || !out || !coords || !cells) return FO_EINVAL;
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return fo_fail(ctx, FO_EINVAL, "dim must be 2 or 3");
+  if (nn < dim + 1 || nt < 1 || nn > (1ll << 31) - 1 || nt * (dim + 1) > (1ll << 31) - 1)
+    return fo_fail(ctx, FO_EINVAL, "bad node or element count");
+  for (int64_t i = 0; i < nt * (dim + 1); ++i)
+    if (cells[i] < 0 || cells[i] >= nn) return fo_fail(ctx, FO_EINVAL, "vertex id %d out of range", (int)cells[i]);
+  for (int64_t i = 0; i < nn * dim; ++i)
+    if (!std::isfinite(coords[i])) return fo_fail(ctx, FO_ENAN, "non-finite coordinate");
+  fo_mesh *m = new fo_mesh();
+  m->ctx = ctx;
+  Grid &g = m->g;
+  g = Grid{};
+  g.dim = dim;
+  g.num_nodes = nn;
+  g.num_elems = nt;
+  g.num_cells = 0;
+  m->um = new fo_umesh();
+  m->um->dim = dim;
+  m->um->nn = nn;
+  m->um->nt = nt;
+  fo_status st = fo_alloc(ctx, (void **)&m->d_cells, sizeof(int32_t) * nt * (dim + 1));
+  if (st == FO_OK) st = fo_alloc(ctx, (void **)&m->d_coords, sizeof(double) * nn * dim);
+  if (st == FO_OK)
+    st = fo_cuda_check(ctx, cudaMemcpyAsync(m->d_cells, cells, sizeof(int32_t) * nt * (dim + 1), cudaMemcpyHostToDevice,
+                                            ctx->stream), "copy cells");
+  if (st == FO_OK)
+    st = fo_cuda_check(ctx, cudaMemcpyAsync(m->d_coords, coords, sizeof(double) * nn * dim, cudaMemcpyHostToDevice,
+                                            ctx->stream), "copy coords");
+  if (st == FO_OK) st = fo_umesh_build(m, coords, cells);
+  if (st == FO_OK) st = fo_cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "mesh setup");
+  if (st != FO_OK) {
+    fo_umesh_release(m);
+    fo_free(ctx, m->d_cells, sizeof(int32_t) * nt * (dim + 1));
+    fo_free(ctx, m->d_coords, sizeof(double) * nn * dim);
+    delete m;
+    return st;
+  }
+  for (int a = 0; a < 3; ++a) {
+    g.lo[a] = a < dim ? m->um->lo[a] : 0.0;
+    g.hi[a] = a < dim ? m->um->hi[a] : 0.0;
+    g.n[a] = 0;
+  }
+  const double D = m->um->volume;
+  m->h_diam = dim == 2 ? std::sqrt(4.0 * D / ((double)nt * std::sqrt(3.0)))
+                       : std::sqrt(std::pow(6.0 * std::sqrt(2.0) * D / (double)nt, 2.0 / 3.0));
+  ctx->meshes.push_back(m);
+  *out = m;
+  return FO_OK;
+}
+
 extern "C" fo_status fo_mesh_destroy(fo_mesh *m) {
   if (!m) return FO_EINVAL;
   fo_ctx *ctx = m->ctx;
@@ -257,6 +311,7 @@ extern "C" fo_status fo_mesh_destroy(fo_mesh *m) {
     else ++i;
   }
   const Grid &g = m->g;
+  fo_umesh_release(m);
   fo_free(ctx, m->d_cells, sizeof(int32_t) * g.num_elems * (g.dim + 1));
   fo_free(ctx, m->d_coords, sizeof(double) * g.num_nodes * g.dim);
   ctx->meshes.erase(std::remove(ctx->meshes.begin(), ctx->meshes.end(), m), ctx->meshes.end());
@@ -279,7 +334,7 @@ extern "C" fo_status fo_mesh_query(const fo_mesh *m, fo_mesh_info *out) {
   out->num_nodes = g.num_nodes;
   out->num_cells = g.num_cells;
   out->num_elems = g.num_elems;
-  out->volume = D;
+  out->volume = m->um ? m->um->volume : D;
   out->h = m->h_diam;
   return FO_OK;
 }
@@ -300,16 +355,20 @@ extern "C" fo_status fo_mesh_copy_out(const fo_mesh *m, int32_t *cells, double *
 
 // ------------------------------------------------------------------------------- problem
 // Sizes of a problem's device fields, in the order of prob_bytes_fields.
-static std::vector<size_t> problem_field_sizes(int d, long long NN, long long NT, long long ND, bool with_f) {
-  const size_t S = (d == 2) ? 7 : 15;
+// `entries`: stored operator entries per block slot -- S N_n on the structured grid (S stencil
+// slots per node), the node graph's nonzeros on a general mesh; `vel_blk`: entries per velocity
+// block (d: component-diagonal on the box grid; d^2 on a general mesh).
+static std::vector<size_t> problem_field_sizes(int d, long long NN, long long NT, long long ND, bool with_f,
+                                               long long entries, int vel_blk) {
+  const size_t E = (size_t)entries;
   const size_t npn = (size_t)(ND / NN);   // state components per node
   std::vector<size_t> v = {
-      sizeof(double) * S * npn * npn * NN, sizeof(float) * S * npn * npn * NN, sizeof(double) * S * d * NN,
+      sizeof(double) * E * npn * npn, sizeof(float) * E * npn * npn, sizeof(double) * E * vel_blk,
       sizeof(double) * NN,     sizeof(double) * NT,     sizeof(float) * NT,       (size_t)NT,
       (size_t)NT,              (size_t)ND,              (size_t)NN,               sizeof(double) * ND,
       sizeof(double) * ND,     sizeof(double) * ND,     sizeof(double) * d * NN,  sizeof(double) * d * NN,
-      sizeof(double) * ND,     sizeof(float) * ND,      sizeof(double) * d * NN,  sizeof(double) * S * NN,
-      sizeof(double) * S * NN, sizeof(double) * NN,     sizeof(double) * FO_RED_DOUBLES,
+      sizeof(double) * ND,     sizeof(float) * ND,      sizeof(double) * d * NN,  sizeof(double) * E,
+      sizeof(double) * E,      sizeof(double) * NN,     sizeof(double) * FO_RED_DOUBLES,
       64,                      sizeof(int) * DS_COUNT,
   };
   if (with_f) v.push_back(sizeof(double) * NN);
@@ -318,8 +377,10 @@ static std::vector<size_t> problem_field_sizes(int d, long long NN, long long NT
 
 static size_t prob_bytes_fields(const fo_problem *p, std::vector<std::pair<void **, size_t>> &list) {
   const Grid &g = p->mesh->g;
-  const std::vector<size_t> sz =
-      problem_field_sizes(g.dim, g.num_nodes, g.num_elems, p->ndof, p->f || p->desc.kind != FO_ELASTIC);
+  const long long entries = p->mesh->um ? p->mesh->um->nnz : (long long)(g.dim == 2 ? 7 : 15) * g.num_nodes;
+  const std::vector<size_t> sz = problem_field_sizes(g.dim, g.num_nodes, g.num_elems, p->ndof,
+                                                     p->f || p->desc.kind != FO_ELASTIC, entries,
+                                                     p->mesh->um ? g.dim * g.dim : g.dim);
   std::vector<void **> ptr = {
       (void **)&p->Wst,        (void **)&p->Wst32,        (void **)&p->Wvel,
       (void **)&p->phi,        (void **)&p->coef,         (void **)&p->coef32,       (void **)&p->chi,
@@ -352,7 +413,8 @@ size_t fo_problem_footprint(int dim, const int n[3], int kind, int state_vecs, i
   const long long NT = cells * (dim == 2 ? 2 : 6);
   const long long ND = NN * (kind == FO_ELASTIC ? dim : 1);
   size_t total = sizeof(int32_t) * NT * (dim + 1) + sizeof(double) * NN * dim;   // mesh
-  for (size_t b : problem_field_sizes(dim, NN, NT, ND, kind != FO_ELASTIC)) total += b;
+  for (size_t b : problem_field_sizes(dim, NN, NT, ND, kind != FO_ELASTIC, (dim == 2 ? 7 : 15) * NN, dim))
+    total += b;
   const size_t state = sizeof(double) * state_vecs * (size_t)ND;
   const size_t vel = sizeof(double) * vel_vecs * (size_t)dim * NN;
   const size_t bumps = sizeof(double) * (size_t)std::max(n_bumps, 0) * dim;
@@ -396,6 +458,8 @@ extern "C" fo_status fo_problem_create(fo_mesh *m, const fo_model_desc *desc, fo
     return fo_fail(ctx, FO_EINVAL, "bad elastic parameters");
   if (desc->n_inst < 0 || (desc->n_inst > 0 && desc->kind != FO_HELMHOLTZ))
     return fo_fail(ctx, FO_EINVAL, "a task-parallel batch (n_inst > 0) is a FO_HELMHOLTZ family");
+  if (m->um && desc->n_inst > 0)
+    return fo_fail(ctx, FO_EINVAL, "task-parallel batches run on box meshes (fo_mesh_box)");
   fo_problem *p = new fo_problem();
   p->ctx = ctx;
   p->mesh = m;
@@ -432,9 +496,15 @@ extern "C" fo_status fo_problem_create(fo_mesh *m, const fo_model_desc *desc, fo
   if (st == FO_OK) st = fo_cuda_check(ctx, cudaMemsetAsync(p->phi, 0, sizeof(double) * g.num_nodes, ctx->stream), "phi");
   if (st == FO_OK) st = fo_cuda_check(ctx, cudaMemsetAsync(p->u, 0, sizeof(double) * p->ndof, ctx->stream), "u");
   if (st == FO_OK) st = fo_cuda_check(ctx, cudaMemsetAsync(p->theta, 0, sizeof(double) * g.dim * g.num_nodes, ctx->stream), "theta");
-  if (st == FO_OK) st = fo_launch_masks(p);
-  if (st == FO_OK) st = fo_launch_loads(p);
-  if (st == FO_OK) st = fo_launch_velocity_diag(p);
+  if (m->um) {
+    if (st == FO_OK) st = fo_umesh_masks(p);
+    if (st == FO_OK) st = fo_umesh_loads(p);
+    if (st == FO_OK) st = fo_umesh_velocity_setup(p);
+  } else {
+    if (st == FO_OK) st = fo_launch_masks(p);
+    if (st == FO_OK) st = fo_launch_loads(p);
+    if (st == FO_OK) st = fo_launch_velocity_diag(p);
+  }
   if (st == FO_OK && desc->n_inst > 0) st = fo_batch_create(p, desc);
   if (st == FO_OK) st = fo_cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "problem setup");
   if (st != FO_OK) {
@@ -477,6 +547,12 @@ extern "C" fo_status fo_levelset_bumps(fo_problem *p, int count, const double *c
 
 extern "C" fo_status fo_coefficients(fo_problem *p) {
   if (!p) return FO_EINVAL;
+  if (p->mesh->um) {   // general mesh: coefficients and the assembled state operator
+    FO_TRY(fo_umesh_coefficients(p));
+    p->coef_valid = true;
+    p->coef_epoch += 1;
+    return FO_OK;
+  }
   FO_TRY(fo_launch_coefficients(p));
   if (p->batch) FO_TRY(fo_batch_prepare(p));
   else FO_TRY(fo_launch_state_diag(p));
@@ -525,6 +601,7 @@ extern "C" fo_status fo_functionals(fo_problem *p, double *J, double *C) {
   if (!p->coef_valid) FO_TRY(fo_coefficients(p));
   double j = 0, vol = 0;
   if (p->batch) FO_TRY(fo_batch_functionals(p, &j, &vol, nullptr));
+  else if (p->mesh->um) FO_TRY(fo_umesh_functionals(p, &j, &vol));
   else FO_TRY(fo_launch_functionals(p, &j, &vol));
   if (J) *J = j;
   if (C) *C = p->desc.volume_target > 0 ? vol / p->desc.volume_target : vol;
@@ -536,6 +613,7 @@ extern "C" fo_status fo_shape_derivative(fo_problem *p, double lambda, double *r
   if (!p) return FO_EINVAL;
   if (!p->coef_valid) FO_TRY(fo_coefficients(p));
   if (p->batch) FO_TRY(fo_batch_shape_rhs(p, lambda));
+  else if (p->mesh->um) FO_TRY(fo_umesh_shape_rhs(p, lambda));
   else FO_TRY(fo_launch_shape_rhs(p, lambda));
   p->rhs_valid = true;
   p->last_lambda = lambda;
@@ -564,7 +642,8 @@ extern "C" fo_status fo_descent(fo_problem *p, const fo_solve_opts *o, double *B
 
 extern "C" fo_status fo_transport_assemble(fo_problem *p, double dt, double h, int smooth) {
   if (!p || !(dt > 0) || !(h > 0)) return FO_EINVAL;
-  FO_TRY(fo_launch_transport_assemble(p, dt, h, smooth));
+  if (p->mesh->um) FO_TRY(fo_umesh_transport_assemble(p, dt, h, smooth));
+  else FO_TRY(fo_launch_transport_assemble(p, dt, h, smooth));
   p->transport_valid = true;
   p->transport_dt = dt;
   p->transport_h = h;
@@ -579,6 +658,15 @@ extern "C" fo_status fo_levelset_step(fo_problem *p, double t_end, int nsteps, d
   fo_solve_opts_default(&def);
   if (!o) o = &def;
   double dt = t_end / nsteps;
+  if (p->mesh->um) {   // general mesh: assembly and all substeps' BiCGStab solves
+    fo_status s = fo_umesh_levelset_step(p, t_end, nsteps, h, smooth, o, st);
+    p->transport_valid = true;
+    p->transport_dt = dt;
+    p->transport_h = h;
+    p->transport_smooth = smooth;
+    p->coef_valid = false;
+    return s;
+  }
   if (!(p->transport_valid && p->transport_dt == dt && p->transport_h == h && p->transport_smooth == smooth))
     FO_TRY(fo_transport_assemble(p, dt, h, smooth));
   fo_status s = fo_transport_run(p, nsteps, o, st);
@@ -592,7 +680,8 @@ extern "C" fo_status fo_reinit(fo_problem *p, int nsteps, double t_final, double
   fo_solve_opts def;
   fo_solve_opts_default(&def);
   if (!o) o = &def;
-  fo_status s = fo_reinit_run(p, nsteps, t_final / nsteps, h, o, st);
+  fo_status s = p->mesh->um ? fo_umesh_reinit(p, nsteps, t_final, h, o, st)
+                            : fo_reinit_run(p, nsteps, t_final / nsteps, h, o, st);
   p->coef_valid = false;
   return s;
 }
@@ -753,7 +842,11 @@ extern "C" fo_status fo_apply(fo_problem *p, int op, const double *x, double *y,
   cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   st = fo_cuda_check(ctx, cudaMemcpyAsync(dx, x, sizeof(double) * n, kin, ctx->stream), "apply in");
   if (st == FO_OK) {
-    if (op == FO_OP_STATE) st = fo_launch_state_apply(p, dx, dy, true);
+    if (p->mesh->um) {
+      if (op == FO_OP_STATE || op == FO_OP_STATE_FP32) st = fo_umesh_state_apply(p, dx, dy, op == FO_OP_STATE_FP32);
+      else if (op == FO_OP_VELOCITY) st = fo_umesh_velocity_apply(p, dx, dy);
+      else st = fo_umesh_transport_apply(p, op == FO_OP_TRANSPORT_L ? 0 : 1, dx, dy);
+    } else if (op == FO_OP_STATE) st = fo_launch_state_apply(p, dx, dy, true);
     else if (op == FO_OP_STATE_FP32) st = fo_launch_state_apply32(p, dx, dy);
     else if (op == FO_OP_VELOCITY) st = fo_launch_velocity_apply(p, dx, dy);
     else st = fo_launch_stencil_apply(p, op == FO_OP_TRANSPORT_L ? p->L : p->R, dx, dy);

@@ -5,6 +5,7 @@
 
 #include "fo_internal.cuh"
 #include "fo_ops.cuh"
+#include "fo_umesh.cuh"
 
 // -------------------------------------------------------------------------- mesh build
 // Coordinates lo + (hi - lo) * i / n in that operation order; connectivity of simplex
@@ -625,6 +626,7 @@ fo_status fo_launch_velocity_diag(fo_problem *p) {
 }
 
 fo_status fo_launch_state_apply(fo_problem *p, const double *x, double *y, bool mask) {
+  if (p->mesh->um) return fo_umesh_state_apply(p, x, y, false);   // general mesh (input masked)
   const Grid &g = p->mesh->g;
   int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
   cudaStream_t s = p->ctx->stream;

@@ -45,9 +45,11 @@ struct Grid {
   double facet_area[3];  // measure of a boundary facet on a face normal to axis a
 };
 
+struct fo_umesh;
 struct fo_mesh {
   fo_ctx *ctx;
-  Grid g;
+  Grid g;                       // general meshes: dim, num_nodes, num_elems and the box only
+  fo_umesh *um = nullptr;       // non-null for a mesh given as arrays (fo_mesh_from_arrays)
   int32_t *d_cells = nullptr;   // [N_T][d+1]
   double *d_coords = nullptr;   // [N_n][d]
   double h_diam = 0;

@@ -23,6 +23,7 @@
 
 #include "fo_internal.cuh"
 #include "fo_ops.cuh"
+#include "fo_umesh.cuh"
 
 // ----------------------------------------------------------------------------- scratch
 fo_status fo_scratch(fo_problem *p, size_t bytes, void **out) {
@@ -456,6 +457,7 @@ static fo_status state_solve_impl(fo_problem *p, const Op64 &op64, const OpMixed
 
 fo_status fo_state_pcg(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st) {
   const Grid &g = p->mesh->g;
+  if (p->mesh->um) return fo_umesh_state_pcg(p, b, x, o, st);   // general mesh: Jacobi-PCG
   if (o->precond == FO_PC_MG && !p->batch && fo_mg_applicable(g, p->ncomp)) return fo_state_pcg_mg(p, b, x, o, st);
   // stored-stencil operators: FP64 rows for the FP64 solve and the refinement residual, FP32
   // rows for the inner solve of the mixed path
@@ -467,6 +469,53 @@ fo_status fo_state_pcg(fo_problem *p, const double *b, double *x, const fo_solve
   if (g.dim == 2)
     return state_solve_impl<2>(p, make_scalar_stencil<2, double>(p), make_scalar_stencil<2, float>(p), b, x, o, st);
   return state_solve_impl<3>(p, make_scalar_stencil<3, double>(p), make_scalar_stencil<3, float>(p), b, x, o, st);
+}
+
+// General meshes: the assembled node-block operators (FP64 rows; FP32 rows for the inner
+// solves of the mixed path) under the same Jacobi-PCG and refinement driver.
+fo_status fo_umesh_state_pcg(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st) {
+  const fo_mesh *m = p->mesh;
+  if (p->ncomp == 1)
+    return state_solve_impl<2>(p, make_csr_op<1>(m, (const double *)p->Wst), make_csr_op<1>(m, (const float *)p->Wst32),
+                               b, x, o, st);
+  if (m->um->dim == 2)
+    return state_solve_impl<2>(p, make_csr_op<2>(m, (const double *)p->Wst), make_csr_op<2>(m, (const float *)p->Wst32),
+                               b, x, o, st);
+  return state_solve_impl<3>(p, make_csr_op<3>(m, (const double *)p->Wst), make_csr_op<3>(m, (const float *)p->Wst32),
+                             b, x, o, st);
+}
+
+// General meshes: B theta = -b as one coupled system (the normal penalty n n^T of a facet
+// that is not axis-aligned couples the components); B(theta, theta) = -b . theta.
+template <int D>
+static fo_status umesh_velocity_impl(fo_problem *p, const fo_solve_opts *o, double *Btt, fo_solve_stats *st) {
+  const long long nn = p->mesh->um->nn, n = (long long)D * nn;
+  double *buf;
+  FO_TRY(fo_scratch(p, sizeof(double) * 8 * n, (void **)&buf));
+  PcgArgs<1, double> a{};
+  bind_vectors(a, p->theta, buf, n);
+  a.b = p->rhs;
+  a.bscale = -1.0;
+  a.bmask = p->desc.velocity_dirichlet ? p->vdir : nullptr;
+  a.dinv = p->dinv_vel;
+  a.rtol2 = o->rtol * o->rtol;
+  a.maxit = o->maxit;
+  a.warm = o->warm_start;
+  SolveOut out;
+  FO_TRY(run_pcg<D>(p, make_csr_op<D>(p->mesh, (const double *)p->Wvel), a, nn, o->grid_blocks, &out));
+  if (Btt) *Btt = out.out[2];
+  if (st) {
+    st->iterations = out.status[DS_ITERS];
+    st->operator_applies = out.status[DS_ITERS] + 1 + (o->warm_start ? 1 : 0);
+    st->outer_iterations = 1;
+    st->rel_residual = out.out[1] > 0 ? std::sqrt(out.out[0] / out.out[1]) : 0.0;
+  }
+  if (out.status[DS_ERR] == DEV_NOCONV) return fo_fail(p->ctx, FO_ENOCONV, "velocity PCG reached maxit");
+  return FO_OK;
+}
+
+fo_status fo_umesh_velocity_pcg(fo_problem *p, const fo_solve_opts *o, double *Btt, fo_solve_stats *st) {
+  return p->mesh->um->dim == 2 ? umesh_velocity_impl<2>(p, o, Btt, st) : umesh_velocity_impl<3>(p, o, Btt, st);
 }
 
 template <int D>
@@ -504,6 +553,7 @@ static fo_status velocity_impl(fo_problem *p, const fo_solve_opts *o, double *Bt
 }
 
 fo_status fo_velocity_pcg(fo_problem *p, const fo_solve_opts *o, double *Btt, fo_solve_stats *st) {
+  if (p->mesh->um) return fo_umesh_velocity_pcg(p, o, Btt, st);
   if (o->precond == FO_PC_MG && fo_mg_applicable(p->mesh->g, p->mesh->g.dim)) return fo_velocity_pcg_mg(p, o, Btt, st);
   if (p->mesh->g.dim == 2) return velocity_impl<2>(p, o, Btt, st);
   return velocity_impl<3>(p, o, Btt, st);
@@ -610,6 +660,7 @@ extern "C" fo_status fo_state_solve_noalloc(fo_problem *p, const double *b, doub
   if (o->precision != FO_FP64)
     return fo_fail(p->ctx, FO_EINVAL, "fo_state_solve_noalloc runs the FP64 solve only");
   if (p->batch) return fo_fail(p->ctx, FO_EINVAL, "fo_state_solve_noalloc takes a single problem");
+  if (p->mesh->um) return fo_fail(p->ctx, FO_EINVAL, "fo_state_solve_noalloc takes a box mesh");
   if (p->ndof > (long long)FO_NOALLOC_MAX_DOFS)
     return fo_fail(p->ctx, FO_EINVAL, "%lld DOFs exceed the no-allocation limit of %d (a %d MiB device array)",
                    p->ndof, (int)FO_NOALLOC_MAX_DOFS, FO_NOALLOC_SCRATCH_BYTES >> 20);

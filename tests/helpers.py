@@ -153,3 +153,50 @@ def gpu_batch(ctx, c):
                           alpha_mass=c["alpha_mass"], velocity_dirichlet=c["velocity_dirichlet"],
                           inst_k=c["k"], inst_omega=c["omega"], inst_f=_batch_sources(coords, c["amp"]))
     return mesh, mesh.problem(desc)
+
+
+# ------------------------------------------------------------------ meshes given as arrays
+def umesh(dim=2, n=(8, 6), hi=None, jitter=0.3, seed=0, pattern="kuhn", shuffle=True):
+    """A seeded general simplicial mesh (coords, cells) of the box (0, hi): jittered interior,
+    shuffled numbering (workloads.simplex_mesh)."""
+    from paper_2601_05709_gb300 import workloads
+    hi = tuple(hi) if hi is not None else (1.0,) * dim
+    return workloads.simplex_mesh(dim, n, (0.0,) * dim, hi, jitter=jitter, seed=seed, pattern=pattern, shuffle=shuffle)
+
+
+def node_at(coords, x):
+    """Index of the node at coordinates x (exact match)."""
+    hit = np.flatnonzero(np.all(np.abs(coords - np.asarray(x, dtype=np.float64)[None, :]) < 1e-12, axis=1))
+    assert hit.size == 1, x
+    return int(hit[0])
+
+
+def oracle_umesh_problem(coords, cells, c):
+    """The oracle problem of case dict c (point loads given by coordinates) on an array mesh."""
+    from oracle.mesh import ArrayMesh
+    m = ArrayMesh(coords, cells)
+    f = None
+    if c["f"] is not None:
+        f = c["f"](m.coords) if callable(c["f"]) else np.asarray(c["f"], dtype=np.float64)
+    pl = [(node_at(m.coords, x), vec) for x, vec in c["point_loads"]]
+    vform = ovel.VelocityForm(alpha_mass=c["alpha_mass"], normal_penalty=c["normal_penalty"],
+                              omega0_weight=c["omega0_weight"], omega0_boxes=c["omega0_boxes"],
+                              dirichlet=c["velocity_dirichlet"])
+    return oalg.Problem(mesh=m, kind=c["kind"], a_in=c["a_in"], a_out=c["a_out"], E=c["E"], nu=c["nu"],
+                        dirichlet_faces=c["dirichlet"], f_nodal=f, point_loads=pl, tractions=c["tractions"],
+                        volume_target=c["volume"], k=c["k"], omega=c["omega"], vform=vform)
+
+
+def gpu_umesh_problem(ctx, coords, cells, c):
+    from paper_2601_05709_gb300 import api
+    mesh = ctx.mesh_from_arrays(coords, cells)
+    f = None
+    if c["f"] is not None:
+        f = c["f"](coords) if callable(c["f"]) else np.asarray(c["f"], dtype=np.float64)
+    pl = [(node_at(coords, x), vec) for x, vec in c["point_loads"]]
+    desc = api.model_desc(c["kind"], a_in=c["a_in"], a_out=c["a_out"], E=c["E"], nu=c["nu"], k=c["k"],
+                          omega=c["omega"], dirichlet=c["dirichlet"], f_nodal=f, point_loads=pl,
+                          tractions=c["tractions"], volume=c["volume"], alpha_mass=c["alpha_mass"],
+                          normal_penalty=c["normal_penalty"], omega0_weight=c["omega0_weight"],
+                          omega0_boxes=c["omega0_boxes"], velocity_dirichlet=c["velocity_dirichlet"])
+    return mesh, mesh.problem(desc)
