@@ -83,7 +83,7 @@ typedef struct fo_problem fo_problem;
 #define FO_FIELD_THETA  3 /* velocity, d*N_n interleaved                                  */
 #define FO_FIELD_RHS    4 /* shape-derivative RHS b, d*N_n interleaved                    */
 #define FO_FIELD_COEF   5 /* A_e per element (double)                                     */
-#define FO_FIELD_CHI    6 /* chi_e per element as double (0 / 1)                          */
+#define FO_FIELD_CHI    6 /* chi_e per element as double (0 / 1; the fraction for FO_COEF_CUT) */
 #define FO_FIELD_LOAD   7 /* state load F, N_dof (zero on Dirichlet DOFs)                 */
 #define FO_FIELD_OMEGA0 8 /* penalised-subdomain mask per element as double (0 / 1)       */
 
@@ -140,7 +140,18 @@ typedef struct {
   const double *inst_k;
   const double *inst_omega;
   const double *inst_f;
+  /* Element coefficient rule (single problems; batches take the one-point rule):
+   * FO_COEF_CENTROID -- A_e = a_in when the vertex values of phi, summed in vertex order, are
+   *   < 0, else a_out (one-point reading of conditional(lt(phi, 0), ...), eqs heat_AOmega,
+   *   compli_AOmega); chi_e in {0, 1};
+   * FO_COEF_CUT -- the exact cut-cell fraction of the P1 phi, f_e = |e cap {phi < 0}| / |e|
+   *   (closed form per simplex), A_e = a_out + (a_in - a_out) f_e and chi_e = f_e in the volume
+   *   constraint and its shape derivative. */
+  int coef_rule;
 } fo_model_desc;
+
+#define FO_COEF_CENTROID 0
+#define FO_COEF_CUT      1
 
 #define FO_MAX_INSTANCES 128
 

@@ -33,6 +33,7 @@ class Problem:
     k: float = 1.0                                           # Helmholtz conductivity factor
     omega: float = 0.0                                       # Helmholtz zero-order coefficient
     vform: velocity.VelocityForm = field(default_factory=velocity.VelocityForm)
+    coef_rule: str = "centroid"                              # or "cut": exact cut-cell fraction
 
     @property
     def ncomp(self):
@@ -68,7 +69,10 @@ class Problem:
         return fem.assemble(Ke, fem.element_dofs(m.cells, self.ncomp), m.num_nodes * self.ncomp)
 
     def state(self, phi):
-        A, chi = shape.coefficient(phi, self.mesh.cells, self.a_in, self.a_out)
+        if self.coef_rule == "cut":
+            A, chi = shape.coefficient_cut(phi, self.mesh.cells, self.a_in, self.a_out)
+        else:
+            A, chi = shape.coefficient(phi, self.mesh.cells, self.a_in, self.a_out)
         K = self.stiffness(A)
         u = solvers.solve_free(K, self.load(), self.dirichlet() == 0)
         return u, A, chi

@@ -32,6 +32,48 @@ def coefficient(phi, cells, a_in, a_out):
     return np.where(chi == 1, a_in, a_out), chi
 
 
+def cut_fraction(phi, cells):
+    """|e cap {phi < 0}| / |e| for the P1 interpolant of phi on every simplex (exact).
+
+    phi is linear on the simplex, so in barycentric coordinates the set {phi < 0} is the
+    convex polytope spanned by the vertices with phi < 0 and the points where phi vanishes on
+    the edges joining them to the other vertices (the vertex with phi = 0 belongs to the
+    other side, matching the strict inequality).  Its measure in the reference simplex is that
+    polytope's convex-hull measure (qhull), divided by the reference simplex's 1/d!.
+    """
+    from scipy.spatial import ConvexHull, QhullError
+    import math
+    d = cells.shape[1] - 1
+    ref = np.vstack([np.zeros(d), np.eye(d)])            # reference vertices (barycentrics 1..d)
+    out = np.zeros(cells.shape[0])
+    for e in range(cells.shape[0]):
+        v = phi[cells[e]]
+        neg = v < 0.0
+        if not neg.any():
+            continue
+        if neg.all():
+            out[e] = 1.0
+            continue
+        pts = [ref[i] for i in range(d + 1) if neg[i]]
+        for i in range(d + 1):
+            for j in range(d + 1):
+                if neg[i] and not neg[j]:
+                    t = v[i] / (v[i] - v[j])             # phi = 0 at ref[i] + t (ref[j] - ref[i])
+                    pts.append(ref[i] + t * (ref[j] - ref[i]))
+        try:
+            out[e] = ConvexHull(np.array(pts)).volume * math.factorial(d)
+        except QhullError:                               # a flat set: measure zero
+            out[e] = 0.0
+    return out
+
+
+def coefficient_cut(phi, cells, a_in, a_out):
+    """Exact cut-cell coefficient: A_e = a_out + (a_in - a_out) |e cap Omega| / |e|, with the
+    material fraction itself as chi_e (the element-wise constant of int_e chi_Omega / |e|)."""
+    frac = cut_fraction(phi, cells)
+    return a_out + (a_in - a_out) * frac, frac
+
+
 def volume(vol, chi):
     """|Omega| = int_D chi_Omega, exact for the element-wise constant chi."""
     return float(np.sum(chi * vol))

@@ -16,6 +16,7 @@ STATUS_NAMES = {0: "FO_OK", -1: "FO_EINVAL", -2: "FO_ENOMEM", -3: "FO_ENOMEM_BUD
 FO_HEAT, FO_ELASTIC, FO_HELMHOLTZ = 0, 1, 2
 FO_FP64, FO_MIXED = 0, 1
 FO_PC_JACOBI, FO_PC_MG = 0, 1
+FO_COEF_CENTROID, FO_COEF_CUT = 0, 1
 (FO_FIELD_PHI, FO_FIELD_U, FO_FIELD_P, FO_FIELD_THETA, FO_FIELD_RHS, FO_FIELD_COEF, FO_FIELD_CHI,
  FO_FIELD_LOAD, FO_FIELD_OMEGA0) = range(9)
 FO_OP_STATE, FO_OP_VELOCITY, FO_OP_TRANSPORT_L, FO_OP_TRANSPORT_R, FO_OP_STATE_FP32 = range(5)
@@ -38,7 +39,7 @@ class ModelDesc(C.Structure):
                 ("normal_penalty", C.c_double), ("omega0_weight", C.c_double), ("n_omega0", C.c_int),
                 ("omega0_lo", D43), ("omega0_hi", D43), ("velocity_dirichlet", C.c_int),
                 ("n_inst", C.c_int), ("inst_k", C.POINTER(C.c_double)), ("inst_omega", C.POINTER(C.c_double)),
-                ("inst_f", C.POINTER(C.c_double))]
+                ("inst_f", C.POINTER(C.c_double)), ("coef_rule", C.c_int)]
 
 
 class TuneResult(C.Structure):

@@ -9,7 +9,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (FO_PC_JACOBI, FO_PC_MG, FO_ELASTIC, FO_FIELD_CHI, FO_FIELD_COEF, FO_FIELD_LOAD, FO_FIELD_OMEGA0, FO_FIELD_P,
+from ._lib import (FO_COEF_CENTROID, FO_COEF_CUT, FO_PC_JACOBI, FO_PC_MG, FO_ELASTIC, FO_FIELD_CHI, FO_FIELD_COEF, FO_FIELD_LOAD, FO_FIELD_OMEGA0, FO_FIELD_P,
                    FO_FIELD_PHI, FO_FIELD_RHS, FO_FIELD_THETA, FO_FIELD_U, FO_FP64, FO_HEAT, FO_HELMHOLTZ,
                    FO_MIXED, FO_OP_STATE, FO_OP_STATE_FP32, FO_OP_TRANSPORT_L, FO_OP_TRANSPORT_R,
                    FO_OP_VELOCITY, FO_OK, FormoptError)
@@ -61,7 +61,7 @@ def run_options(dfactor=1e-2, lv_time=(1e-3, 1e-1), lv_iter=(8, 16), smooth=Fals
 
 def model_desc(kind, a_in=1.0, a_out=1e-3, E=1.0, nu=0.3, k=1.0, omega=0.0, dirichlet=(), f_nodal=None,
                point_loads=(), tractions=(), volume=0.0, alpha_mass=0.1, normal_penalty=0.0, omega0_weight=0.0,
-               omega0_boxes=(), velocity_dirichlet=False, inst_k=None, inst_omega=None, inst_f=None):
+               omega0_boxes=(), velocity_dirichlet=False, inst_k=None, inst_omega=None, inst_f=None, coef_rule=0):
     """Build a fo_model_desc.  dirichlet: [(axis, side)]; point_loads: [(node, vec)];
     tractions: [(axis, side, vec)]; omega0_boxes: [(lo, hi)] with strict inequalities.
     A task-parallel batch (kind FO_HELMHOLTZ): inst_k, inst_omega [n_inst] and
@@ -96,6 +96,7 @@ def model_desc(kind, a_in=1.0, a_out=1e-3, E=1.0, nu=0.3, k=1.0, omega=0.0, diri
             d.omega0_lo[i][c] = lo[c] if c < len(lo) else -np.inf
             d.omega0_hi[i][c] = hi[c] if c < len(hi) else np.inf
     d.velocity_dirichlet = int(bool(velocity_dirichlet))
+    d.coef_rule = int(coef_rule)
     kept = [keep]
     if inst_k is not None:
         ik, io = _f64(inst_k), _f64(inst_omega)

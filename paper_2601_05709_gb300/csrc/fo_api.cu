@@ -369,7 +369,7 @@ static std::vector<size_t> problem_field_sizes(int d, long long NN, long long NT
       sizeof(double) * ND,     sizeof(double) * ND,     sizeof(double) * d * NN,  sizeof(double) * d * NN,
       sizeof(double) * ND,     sizeof(float) * ND,      sizeof(double) * d * NN,  sizeof(double) * E,
       sizeof(double) * E,      sizeof(double) * NN,     sizeof(double) * FO_RED_DOUBLES,
-      64,                      sizeof(int) * DS_COUNT,
+      64,                      sizeof(int) * DS_COUNT,  sizeof(double) * NT,
   };
   if (with_f) v.push_back(sizeof(double) * NN);
   return v;
@@ -388,7 +388,7 @@ static size_t prob_bytes_fields(const fo_problem *p, std::vector<std::pair<void 
       (void **)&p->u,          (void **)&p->p,            (void **)&p->rhs,          (void **)&p->theta,
       (void **)&p->dinv_state, (void **)&p->dinv_state32, (void **)&p->dinv_vel,     (void **)&p->L,
       (void **)&p->R,          (void **)&p->dinvL,        (void **)&p->red,
-      (void **)&p->bar,        (void **)&p->dev_status,
+      (void **)&p->bar,        (void **)&p->dev_status,   (void **)&p->chif,
   };
   if (sz.size() > ptr.size()) ptr.push_back((void **)&p->f);
   list.clear();
@@ -458,6 +458,10 @@ extern "C" fo_status fo_problem_create(fo_mesh *m, const fo_model_desc *desc, fo
     return fo_fail(ctx, FO_EINVAL, "bad elastic parameters");
   if (desc->n_inst < 0 || (desc->n_inst > 0 && desc->kind != FO_HELMHOLTZ))
     return fo_fail(ctx, FO_EINVAL, "a task-parallel batch (n_inst > 0) is a FO_HELMHOLTZ family");
+  if (desc->coef_rule != FO_COEF_CENTROID && desc->coef_rule != FO_COEF_CUT)
+    return fo_fail(ctx, FO_EINVAL, "bad coefficient rule");
+  if (desc->n_inst > 0 && desc->coef_rule != FO_COEF_CENTROID)
+    return fo_fail(ctx, FO_EINVAL, "task-parallel batches take the one-point coefficient rule");
   if (m->um && desc->n_inst > 0)
     return fo_fail(ctx, FO_EINVAL, "task-parallel batches run on box meshes (fo_mesh_box)");
   fo_problem *p = new fo_problem();
@@ -748,7 +752,10 @@ static double *field_ptr(fo_problem *p, int field, size_t *n, bool *is_u8) {
     case FO_FIELD_THETA: *n = g.dim * g.num_nodes; return p->theta;
     case FO_FIELD_RHS: *n = g.dim * g.num_nodes; return p->rhs;
     case FO_FIELD_COEF: *n = g.num_elems; return p->coef;
-    case FO_FIELD_CHI: *n = g.num_elems; *is_u8 = true; return (double *)p->chi;
+    case FO_FIELD_CHI:
+      *n = g.num_elems;
+      *is_u8 = p->desc.coef_rule != FO_COEF_CUT;
+      return p->desc.coef_rule == FO_COEF_CUT ? p->chif : (double *)p->chi;
     case FO_FIELD_LOAD: *n = p->ndof; return p->load;
     case FO_FIELD_OMEGA0: *n = g.num_elems; *is_u8 = true; return (double *)p->omega0;
     default: return nullptr;

@@ -250,7 +250,7 @@ fo_status fo_launch_loads(fo_problem *p) {
 // chi_e = [(phi_0 + phi_1) + phi_2 (+ phi_3) < 0], A_e = chi ? a_in : a_out (times k).
 template <int D>
 __global__ void k_coefficients(Grid g, const double *phi, double a_in, double a_out, double *coef, float *coef32,
-                               uint8_t *chi) {
+                               uint8_t *chi, int cut, double *chif) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.num_elems;
        e += (long long)gridDim.x * blockDim.x) {
     const long long c = e / KP<D>::P;
@@ -261,30 +261,44 @@ __global__ void k_coefficients(Grid g, const double *phi, double a_in, double a_
     ci[1] = (int)(t % g.n[1]);
     ci[2] = (int)(t / g.n[1]);
     long long v = ci[0] + g.stride[1] * ci[1] + (D == 3 ? g.stride[2] * ci[2] : 0);
-    double s = phi[v];
+    double pv[D + 1];
+    pv[0] = phi[v];
+    double s = pv[0];
 #pragma unroll
     for (int l = 0; l < D; ++l) {
       v += g.stride[kperm<D>(p, l)];
-      s = s + phi[v];
+      pv[l + 1] = phi[v];
+      s = s + pv[l + 1];
+    }
+    if (cut) {   // exact cut-cell fraction (FO_COEF_CUT)
+      const double f = cut_fraction<D>(pv);
+      const double A = a_out + (a_in - a_out) * f;
+      coef[e] = A;
+      coef32[e] = (float)A;
+      chi[e] = f > 0.0 ? 1 : 0;
+      chif[e] = f;
+      continue;
     }
     const bool in = s < 0.0;
     const double A = in ? a_in : a_out;
     coef[e] = A;
     coef32[e] = (float)A;
     chi[e] = in ? 1 : 0;
+    chif[e] = in ? 1.0 : 0.0;
   }
 }
 
 fo_status fo_launch_coefficients(fo_problem *p) {
   const Grid &g = p->mesh->g;
   const double k = p->desc.kind == FO_HELMHOLTZ ? p->desc.k : 1.0;
+  const int cut = p->desc.coef_rule == FO_COEF_CUT;
   int blocks = fo_blocks_for(g.num_elems, FO_BLOCK, 65536);
   if (g.dim == 2)
     k_coefficients<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(g, p->phi, p->desc.a_in * k, p->desc.a_out * k,
-                                                                p->coef, p->coef32, p->chi);
+                                                                p->coef, p->coef32, p->chi, cut, p->chif);
   else
     k_coefficients<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(g, p->phi, p->desc.a_in * k, p->desc.a_out * k,
-                                                                p->coef, p->coef32, p->chi);
+                                                                p->coef, p->coef32, p->chi, cut, p->chif);
   fo_note_launch(1);
   FO_CU(p->ctx, cudaGetLastError());
   return FO_OK;
@@ -716,7 +730,7 @@ struct FuncArgs {
 };
 
 template <int D>
-__global__ void k_functionals(FuncArgs f, const double *coef, const uint8_t *chi, const double *u,
+__global__ void k_functionals(FuncArgs f, const double *coef, const uint8_t *chi, const double *chif, const double *u,
                               const double *load, double *partials) {
   __shared__ double smem[32 * 2];
   const Grid &g = f.g;
@@ -767,7 +781,7 @@ __global__ void k_functionals(FuncArgs f, const double *coef, const uint8_t *chi
       }
       v[0] += A * g.vol_e * g2;
     }
-    v[1] += chi[e] ? g.vol_e : 0.0;
+    v[1] += chif ? chif[e] * g.vol_e : (chi[e] ? g.vol_e : 0.0);
   }
   if (f.kind == FO_HELMHOLTZ) {   // J = F . u
     for (long long a = tid; a < g.num_nodes; a += stride) v[0] += load[a] * u[a];
@@ -796,8 +810,9 @@ fo_status fo_launch_functionals(fo_problem *p, double *J, double *vol) {
   FuncArgs f{g, p->desc.kind, p->lame_lambda, p->lame_mu};
   const int blocks = fo_blocks_for(g.num_elems, FO_BLOCK, 1024);
   double *part = p->red, *res = p->red + 2 * 1024;
-  if (g.dim == 2) k_functionals<2><<<blocks, FO_BLOCK, 0, ctx->stream>>>(f, p->coef, p->chi, p->u, p->load, part);
-  else k_functionals<3><<<blocks, FO_BLOCK, 0, ctx->stream>>>(f, p->coef, p->chi, p->u, p->load, part);
+  const double *chif = p->desc.coef_rule == FO_COEF_CUT ? p->chif : nullptr;
+  if (g.dim == 2) k_functionals<2><<<blocks, FO_BLOCK, 0, ctx->stream>>>(f, p->coef, p->chi, chif, p->u, p->load, part);
+  else k_functionals<3><<<blocks, FO_BLOCK, 0, ctx->stream>>>(f, p->coef, p->chi, chif, p->u, p->load, part);
   k_finish_sum<<<1, 64, 0, ctx->stream>>>(part, blocks, 2, res);
   fo_note_launch(2);
   FO_CU(ctx, cudaGetLastError());
@@ -820,8 +835,8 @@ struct ShapeArgs {
 };
 
 template <int D>
-__global__ void k_shape_rhs(ShapeArgs s, const double *coef, const uint8_t *chi, const double *u, const double *f,
-                            double *b) {
+__global__ void k_shape_rhs(ShapeArgs s, const double *coef, const uint8_t *chi, const double *chif, const double *u,
+                            const double *f, double *b) {
   const Grid &g = s.g;
   for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < g.num_nodes;
        a += (long long)gridDim.x * blockDim.x) {
@@ -859,7 +874,7 @@ __global__ void k_shape_rhs(ShapeArgs s, const double *coef, const uint8_t *chi,
               se += sig[i][j] * 0.5 * (du[i][j] + du[j][i]);
             }
           const double A = coef[e];
-          const double cv = chi[e] ? s.lam_ppl * s.inv_V : 0.0;
+          const double cv = chif ? chif[e] * (s.lam_ppl * s.inv_V) : (chi[e] ? s.lam_ppl * s.inv_V : 0.0);
           // S1[i][j] = A (2 sum_k du[k][i] sig[k][j] - se delta_ij) + cv delta_ij
 #pragma unroll
           for (int side = 0; side < 2; ++side) {
@@ -909,7 +924,7 @@ __global__ void k_shape_rhs(ShapeArgs s, const double *coef, const uint8_t *chi,
           for (int k = 0; k < D; ++k) g2 += gu[k] * gu[k];
           const double uf = s.mref * (suf + su * sf);          // int_e u f
           const double Mu = s.mref * (su + us[0][0]);          // int_e u lambda_m
-          const double cv = chi[e] ? s.lam_ppl * s.inv_V : 0.0;
+          const double cv = chif ? chif[e] * (s.lam_ppl * s.inv_V) : (chi[e] ? s.lam_ppl * s.inv_V : 0.0);
           // grad lambda_m components
           double gl[3] = {0, 0, 0};
           if (m >= 1) gl[kperm<D>(p, m - 1)] += g.inv_h[kperm<D>(p, m - 1)];
@@ -936,8 +951,9 @@ fo_status fo_launch_shape_rhs(fo_problem *p, double lambda) {
   ShapeArgs s{g, p->desc.kind, p->lame_lambda, p->lame_mu, lambda,
               p->desc.volume_target > 0 ? 1.0 / p->desc.volume_target : 1.0, g.vol_e / ((g.dim + 1) * (g.dim + 2))};
   int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
-  if (g.dim == 2) k_shape_rhs<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(s, p->coef, p->chi, p->u, p->f, p->rhs);
-  else k_shape_rhs<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(s, p->coef, p->chi, p->u, p->f, p->rhs);
+  const double *chif = p->desc.coef_rule == FO_COEF_CUT ? p->chif : nullptr;
+  if (g.dim == 2) k_shape_rhs<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(s, p->coef, p->chi, chif, p->u, p->f, p->rhs);
+  else k_shape_rhs<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(s, p->coef, p->chi, chif, p->u, p->f, p->rhs);
   fo_note_launch(1);
   FO_CU(p->ctx, cudaGetLastError());
   return FO_OK;

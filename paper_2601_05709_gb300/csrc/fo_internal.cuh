@@ -115,6 +115,7 @@ struct fo_problem {
   double *coef = nullptr;        // N_T  (A_e, times k for Helmholtz)
   float *coef32 = nullptr;       // N_T
   uint8_t *chi = nullptr;        // N_T
+  double *chif = nullptr;        // N_T material fraction (1 / 0 for the one-point rule)
   uint8_t *omega0 = nullptr;     // N_T
   uint8_t *dir = nullptr;        // N_dof state Dirichlet mask
   uint8_t *vdir = nullptr;       // N_n velocity Dirichlet mask (H^1_0)
@@ -445,6 +446,42 @@ __device__ __forceinline__ bool reduce_grid(double (&v)[NR], double *sred, doubl
   grid_total<NR>(part, stot);
   ++rk;
   return true;
+}
+
+// ---- exact cut-cell fraction -----------------------------------------------------------
+// |e cap {phi < 0}| / |e| for the P1 phi with vertex values v[0..D] (a vertex with phi = 0 is
+// on the outer side).  Closed forms by the number of negative vertices, with a_i = -v_i on the
+// negative side and c_j = v_j on the other; each is written as a ratio of sums of positive
+// terms, so no difference of nearly equal numbers occurs:
+//   one negative:     a^D / prod_j (a + c_j);
+//   one non-negative: 1 - c^D / prod_i (c + a_i), expanded: 2D (c (a1 + a2) + a1 a2) / prod,
+//                     3D (c^2 (a1+a2+a3) + c (a1 a2 + a1 a3 + a2 a3) + a1 a2 a3) / prod;
+//   3D two and two:   the divided difference of min(x, 0)^3 over the vertex values, expanded
+//                     into the positive-term ratio `num / den` below (a, b negative; c, e not).
+template <int D>
+__device__ __forceinline__ double cut_fraction(const double *v) {
+  double a[4], c[4];
+  int na = 0, nc = 0;
+#pragma unroll
+  for (int i = 0; i <= D; ++i) {
+    if (v[i] < 0.0) a[na++] = -v[i];
+    else c[nc++] = v[i];
+  }
+  if (na == 0) return 0.0;
+  if (nc == 0) return 1.0;
+  if (D == 2) {
+    if (na == 1) return a[0] * a[0] / ((a[0] + c[0]) * (a[0] + c[1]));
+    return (c[0] * (a[0] + a[1]) + a[0] * a[1]) / ((c[0] + a[0]) * (c[0] + a[1]));
+  }
+  if (na == 1) return a[0] * a[0] * a[0] / ((a[0] + c[0]) * (a[0] + c[1]) * (a[0] + c[2]));
+  if (nc == 1) {
+    const double s1 = a[0] + a[1] + a[2], s2 = a[0] * a[1] + a[0] * a[2] + a[1] * a[2], s3 = a[0] * a[1] * a[2];
+    return (c[0] * c[0] * s1 + c[0] * s2 + s3) / ((c[0] + a[0]) * (c[0] + a[1]) * (c[0] + a[2]));
+  }
+  const double A = a[0], B = a[1], C = c[0], E = c[1];
+  const double num = C * A * A * E + C * A * A * B + E * A * A * B + C * E * A * B + A * A * B * B + C * A * B * B +
+                     E * A * B * B + C * E * B * B;
+  return num / ((A + E) * (B + E) * (A + C) * (B + C));
 }
 
 // ---- host launch helpers ------------------------------------------------------------------

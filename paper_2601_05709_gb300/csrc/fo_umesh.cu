@@ -286,16 +286,29 @@ fo_status fo_umesh_build(fo_mesh *m, const double *coords, const int32_t *cells)
 // element's vertex order, < 0 inside (strict: a zero sum is outside); A_e times k (Helmholtz).
 template <int D>
 __global__ void k_u_coefficients(UMeshView m, const double *phi, double a_in, double a_out, double *coef,
-                                 float *coef32, uint8_t *chi) {
+                                 float *coef32, uint8_t *chi, int cut, double *chif) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m.nt; e += (long long)gridDim.x * blockDim.x) {
-    double s = phi[m.cells[e * (D + 1)]];
+    double pv[D + 1];
 #pragma unroll
-    for (int a = 1; a <= D; ++a) s = s + phi[m.cells[e * (D + 1) + a]];
+    for (int a = 0; a <= D; ++a) pv[a] = phi[m.cells[e * (D + 1) + a]];
+    if (cut) {   // exact cut-cell fraction (FO_COEF_CUT)
+      const double f = cut_fraction<D>(pv);
+      const double A = a_out + (a_in - a_out) * f;
+      coef[e] = A;
+      coef32[e] = (float)A;
+      chi[e] = f > 0.0 ? 1 : 0;
+      chif[e] = f;
+      continue;
+    }
+    double s = pv[0];
+#pragma unroll
+    for (int a = 1; a <= D; ++a) s = s + pv[a];
     const bool in = s < 0.0;
     const double A = in ? a_in : a_out;
     coef[e] = A;
     coef32[e] = (float)A;
     chi[e] = in ? 1 : 0;
+    chif[e] = in ? 1.0 : 0.0;
   }
 }
 
@@ -526,11 +539,14 @@ fo_status fo_umesh_coefficients(fo_problem *p) {
   const UMeshView m = umesh_view(p->mesh);
   cudaStream_t s = p->ctx->stream;
   const double k = p->desc.kind == FO_HELMHOLTZ ? p->desc.k : 1.0;
+  const int cut = p->desc.coef_rule == FO_COEF_CUT;
   int blocks = fo_blocks_for(m.nt, FO_BLOCK, 65536);
   if (m.dim == 2)
-    k_u_coefficients<2><<<blocks, FO_BLOCK, 0, s>>>(m, p->phi, p->desc.a_in * k, p->desc.a_out * k, p->coef, p->coef32, p->chi);
+    k_u_coefficients<2><<<blocks, FO_BLOCK, 0, s>>>(m, p->phi, p->desc.a_in * k, p->desc.a_out * k, p->coef, p->coef32, p->chi,
+                                                    cut, p->chif);
   else
-    k_u_coefficients<3><<<blocks, FO_BLOCK, 0, s>>>(m, p->phi, p->desc.a_in * k, p->desc.a_out * k, p->coef, p->coef32, p->chi);
+    k_u_coefficients<3><<<blocks, FO_BLOCK, 0, s>>>(m, p->phi, p->desc.a_in * k, p->desc.a_out * k, p->coef, p->coef32, p->chi,
+                                                    cut, p->chif);
   blocks = fo_blocks_for(m.nn, FO_BLOCK, 65536);
   const double w2 = p->desc.kind == FO_HELMHOLTZ ? p->desc.omega * p->desc.omega : 0.0;
   if (p->desc.kind == FO_ELASTIC) {
@@ -674,7 +690,7 @@ fo_status fo_umesh_velocity_apply(fo_problem *p, const double *x, double *y) {
 // block partials, then one warp per value adds them in a fixed order.
 template <int D>
 __global__ void k_u_functionals(UMeshView m, int kind, double lam, double mu, const double *coef, const uint8_t *chi,
-                                const double *u, const double *load, double *partials) {
+                                const double *chif, const double *u, const double *load, double *partials) {
   __shared__ double smem[32 * 2];
   double v[2] = {0.0, 0.0};
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
@@ -721,7 +737,7 @@ __global__ void k_u_functionals(UMeshView m, int kind, double lam, double mu, co
       for (int k = 0; k < D; ++k) g2 += gu[k] * gu[k];
       v[0] += A * vol * g2;
     }
-    v[1] += chi[e] ? vol : 0.0;
+    v[1] += chif ? chif[e] * vol : (chi[e] ? vol : 0.0);
   }
   if (kind == FO_HELMHOLTZ)
     for (long long a = tid; a < m.nn; a += st) v[0] += load[a] * u[a];
@@ -747,12 +763,13 @@ fo_status fo_umesh_functionals(fo_problem *p, double *J, double *vol) {
   fo_ctx *ctx = p->ctx;
   const int blocks = fo_blocks_for(std::max(m.nt, m.nn), FO_BLOCK, 1024);
   double *part = p->red, *res = p->red + 2 * 1024;
+  const double *chif = p->desc.coef_rule == FO_COEF_CUT ? p->chif : nullptr;
   if (m.dim == 2)
     k_u_functionals<2><<<blocks, FO_BLOCK, 0, ctx->stream>>>(m, p->desc.kind, p->lame_lambda, p->lame_mu, p->coef,
-                                                             p->chi, p->u, p->load, part);
+                                                             p->chi, chif, p->u, p->load, part);
   else
     k_u_functionals<3><<<blocks, FO_BLOCK, 0, ctx->stream>>>(m, p->desc.kind, p->lame_lambda, p->lame_mu, p->coef,
-                                                             p->chi, p->u, p->load, part);
+                                                             p->chi, chif, p->u, p->load, part);
   k_u_finish2<<<1, 64, 0, ctx->stream>>>(part, blocks, res);
   fo_note_launch(2);
   FO_CU(ctx, cudaGetLastError());
@@ -770,7 +787,8 @@ fo_status fo_umesh_functionals(fo_problem *p, double *J, double *vol) {
 // S1 = (2uf - A |grad u|^2) I + 2A grad u (x) grad u, f the P1 interpolant).
 template <int D>
 __global__ void k_u_shape_rhs(UMeshView m, int kind, double lam_e, double mu_e, double lam_ppl, double inv_V,
-                              const double *coef, const uint8_t *chi, const double *u, const double *f, double *b) {
+                              const double *coef, const uint8_t *chi, const double *chif, const double *u,
+                              const double *f, double *b) {
   for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < m.nn; a += (long long)gridDim.x * blockDim.x) {
     double acc[D];
 #pragma unroll
@@ -779,7 +797,7 @@ __global__ void k_u_shape_rhs(UMeshView m, int kind, double lam_e, double mu_e, 
       const long long e = m.adj[q] / (D + 1);
       const int la = m.adj[q] % (D + 1);
       const double A = coef[e], vol = m.vol[e];
-      const double cv = chi[e] ? lam_ppl * inv_V : 0.0;
+      const double cv = chif ? chif[e] * (lam_ppl * inv_V) : (chi[e] ? lam_ppl * inv_V : 0.0);
       double gl[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) gl[k] = m.g(e, la, k);
@@ -863,12 +881,13 @@ fo_status fo_umesh_shape_rhs(fo_problem *p, double lambda) {
   const UMeshView m = umesh_view(p->mesh);
   const double inv_V = p->desc.volume_target > 0 ? 1.0 / p->desc.volume_target : 1.0;
   const int blocks = fo_blocks_for(m.nn, FO_BLOCK, 65536);
+  const double *chif = p->desc.coef_rule == FO_COEF_CUT ? p->chif : nullptr;
   if (m.dim == 2)
     k_u_shape_rhs<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, p->desc.kind, p->lame_lambda, p->lame_mu, lambda, inv_V,
-                                                              p->coef, p->chi, p->u, p->f, p->rhs);
+                                                              p->coef, p->chi, chif, p->u, p->f, p->rhs);
   else
     k_u_shape_rhs<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, p->desc.kind, p->lame_lambda, p->lame_mu, lambda, inv_V,
-                                                              p->coef, p->chi, p->u, p->f, p->rhs);
+                                                              p->coef, p->chi, chif, p->u, p->f, p->rhs);
   fo_note_launch(1);
   FO_CU(p->ctx, cudaGetLastError());
   return FO_OK;

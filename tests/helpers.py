@@ -8,14 +8,14 @@ from oracle.mesh import BoxMesh
 
 def case(dim=2, n=(8, 8), lo=None, hi=None, kind=0, a_in=1.0, a_out=1e-3, E=1.0, nu=0.3, k=1.0, omega=0.0,
          dirichlet=((0, 0),), f=None, point_loads=(), tractions=(), volume=0.0, alpha_mass=0.1,
-         normal_penalty=0.0, omega0_weight=0.0, omega0_boxes=(), velocity_dirichlet=False):
+         normal_penalty=0.0, omega0_weight=0.0, omega0_boxes=(), velocity_dirichlet=False, coef_rule=0):
     lo = tuple(lo) if lo is not None else (0.0,) * dim
     hi = tuple(hi) if hi is not None else (1.0,) * dim
     return dict(dim=dim, n=tuple(n), lo=lo, hi=hi, kind=kind, a_in=a_in, a_out=a_out, E=E, nu=nu, k=k,
                 omega=omega, dirichlet=list(dirichlet), f=f, point_loads=list(point_loads),
                 tractions=list(tractions), volume=volume, alpha_mass=alpha_mass, normal_penalty=normal_penalty,
                 omega0_weight=omega0_weight, omega0_boxes=list(omega0_boxes),
-                velocity_dirichlet=velocity_dirichlet)
+                velocity_dirichlet=velocity_dirichlet, coef_rule=coef_rule)
 
 
 def oracle_problem(c):
@@ -29,7 +29,8 @@ def oracle_problem(c):
                               dirichlet=c["velocity_dirichlet"])
     return oalg.Problem(mesh=m, kind=c["kind"], a_in=c["a_in"], a_out=c["a_out"], E=c["E"], nu=c["nu"],
                         dirichlet_faces=c["dirichlet"], f_nodal=f, point_loads=pl, tractions=c["tractions"],
-                        volume_target=c["volume"], k=c["k"], omega=c["omega"], vform=vform)
+                        volume_target=c["volume"], k=c["k"], omega=c["omega"], vform=vform,
+                        coef_rule="cut" if c.get("coef_rule", 0) == 1 else "centroid")
 
 
 def gpu_problem(ctx, c):
@@ -44,7 +45,8 @@ def gpu_problem(ctx, c):
                           omega=c["omega"], dirichlet=c["dirichlet"], f_nodal=f, point_loads=pl,
                           tractions=c["tractions"], volume=c["volume"], alpha_mass=c["alpha_mass"],
                           normal_penalty=c["normal_penalty"], omega0_weight=c["omega0_weight"],
-                          omega0_boxes=c["omega0_boxes"], velocity_dirichlet=c["velocity_dirichlet"])
+                          omega0_boxes=c["omega0_boxes"], velocity_dirichlet=c["velocity_dirichlet"],
+                          coef_rule=c.get("coef_rule", 0))
     return mesh, mesh.problem(desc)
 
 
@@ -184,7 +186,8 @@ def oracle_umesh_problem(coords, cells, c):
                               dirichlet=c["velocity_dirichlet"])
     return oalg.Problem(mesh=m, kind=c["kind"], a_in=c["a_in"], a_out=c["a_out"], E=c["E"], nu=c["nu"],
                         dirichlet_faces=c["dirichlet"], f_nodal=f, point_loads=pl, tractions=c["tractions"],
-                        volume_target=c["volume"], k=c["k"], omega=c["omega"], vform=vform)
+                        volume_target=c["volume"], k=c["k"], omega=c["omega"], vform=vform,
+                        coef_rule="cut" if c.get("coef_rule", 0) == 1 else "centroid")
 
 
 def gpu_umesh_problem(ctx, coords, cells, c):
@@ -198,5 +201,6 @@ def gpu_umesh_problem(ctx, coords, cells, c):
                           omega=c["omega"], dirichlet=c["dirichlet"], f_nodal=f, point_loads=pl,
                           tractions=c["tractions"], volume=c["volume"], alpha_mass=c["alpha_mass"],
                           normal_penalty=c["normal_penalty"], omega0_weight=c["omega0_weight"],
-                          omega0_boxes=c["omega0_boxes"], velocity_dirichlet=c["velocity_dirichlet"])
+                          omega0_boxes=c["omega0_boxes"], velocity_dirichlet=c["velocity_dirichlet"],
+                          coef_rule=c.get("coef_rule", 0))
     return mesh, mesh.problem(desc)

@@ -317,11 +317,19 @@ def test_transport_cantilever_size_bench_options(ctx, api):
     prob.set(api._lib.FO_FIELD_THETA, theta)
     prob.set_levelset(phi)
     h, t_end, ns = m.diameter(), 1e-3, 8
-    st = prob.levelset_step(t_end, ns, h, True, api.solve_opts(rtol=1e-12))
-    out = prob.get(api._lib.FO_FIELD_PHI)
     ref = levelset.transport(m, phi, theta, t_end, ns, h, True)
-    assert close_scaled(out, ref, 1e-10), np.max(np.abs(out - ref))
+    # the benchmark's GMRES tolerance (||r|| <= 1e-12 ||b|| per substep): every node within
+    # 1e-9 of the level set's scale (8 substeps, each leaving up to rtol of ||b|| in the residual,
+    # amplified by the Petrov-Galerkin matrix's condition number ~1e2)
+    prob.levelset_step(t_end, ns, h, True, api.solve_opts(rtol=1e-12))
+    out = prob.get(api._lib.FO_FIELD_PHI)
+    assert close_scaled(out, ref, 1e-9), np.max(np.abs(out - ref))
     assert np.max(np.abs(out - phi)) > 1e-4          # the level set moved
+    # solved to 1e-14: the discrete scheme itself agrees to 1e-11
+    prob.set_levelset(phi)
+    prob.levelset_step(t_end, ns, h, True, api.solve_opts(rtol=1e-14, maxit=100000))
+    out = prob.get(api._lib.FO_FIELD_PHI)
+    assert close_scaled(out, ref, 1e-11), np.max(np.abs(out - ref))
 
 
 @pytest.mark.parametrize("dim,n", [(2, (24, 24)), (3, (6, 6, 5))])
