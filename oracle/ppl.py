@@ -54,3 +54,23 @@ def adaptime(Btt, dfactor=1e-2, lv_time=(1e-3, 1e-1), lv_iter=(8, 16), floor=1e-
     s = (smax - smin) * ((t_end - tmin) / (tmax - tmin)) ** (1.0 / 6.0) + smin
     s = min(max(s, smin), smax)
     return t_end, int(math.floor(s + 0.5))
+
+
+def stop_check(values, C=None, start_to_check=30, tol=1e-2, ctrn_tol=1e-2, prev=10):
+    """Stopping criterion of Sec. 5.7 at iteration i = len(values) - 1.
+
+    values: J(Omega^0..i) for a problem without constraints, L(Omega^0..i, ...) with them; C:
+    the constraint vector C(Omega^i) (None without constraints).  Stops when i > start_to_check
+    and max_{j in I(i)} |v_i - v_j| < tol |v_i| with I(i) = {i - prev, ..., i - 1}, and, with
+    constraints, also |C - 1|_inf < ctrn_tol.
+    """
+    i = len(values) - 1
+    if i <= start_to_check or i < prev:
+        return False
+    vi = values[i]
+    spread = max(abs(vi - values[j]) for j in range(i - prev, i))
+    if not spread < tol * abs(vi):
+        return False
+    if C is not None and len(np.atleast_1d(C)):
+        return bool(np.max(np.abs(np.atleast_1d(C) - 1.0)) < ctrn_tol)
+    return True
