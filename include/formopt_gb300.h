@@ -148,6 +148,20 @@ typedef struct {
    *   (closed form per simplex), A_e = a_out + (a_in - a_out) f_e and chi_e = f_e in the volume
    *   constraint and its shape derivative. */
   int coef_rule;
+  /* Several load cases (CompliancePlus / HeatPlus, eq. compli_plus: J = sum_k J(u_k), u_k the
+   * state of load case k; single problems only).  n_cases in [0, 4] (0 or 1: one case);
+   * point load i and traction t belong to case point_case[i] and traction_case[t]; f_nodal
+   * belongs to case 0.  State-sized fields (FO_FIELD_U, FO_FIELD_P, FO_FIELD_LOAD) then hold
+   * n_cases blocks of N_dof, case-major.  The shape derivative sums the cases' tensors. */
+  int n_cases;
+  int point_case[4];
+  int traction_case[4];
+  /* Several volume constraints (Sec. 5.4 with N_c = n_volume <= 4; single problems only):
+   * C_j = |Omega cap R_j| / volume_V[j], R_j the elements whose centroid lies strictly inside
+   * the box (volume_lo[j], volume_hi[j]) (use +-inf for open sides); S^C_j = chi chi_Rj / V_j I.
+   * n_volume = 0: the single constraint |Omega| / volume_target when volume_target > 0. */
+  int n_volume;
+  double volume_lo[4][3], volume_hi[4][3], volume_V[4];
 } fo_model_desc;
 
 #define FO_COEF_CENTROID 0
@@ -217,6 +231,8 @@ typedef struct {
    * hierarchy rebuild; FO_MIXED: its FP32 CG launches summed over the refinement steps);
    * 0 when the state solve ran another solver */
   double ms_state_kernel;
+  int nc;                   /* constraints of this iteration (0 = none)                 */
+  double Cv[4], lambdav[4]; /* C_j and lambda_j of every constraint (C, lambda = [0])    */
 } fo_iter_log;
 
 /* ---------------------------------------------------------------- context ----- */
@@ -291,6 +307,13 @@ FO_API fo_status fo_functionals(fo_problem *prob, double *J, double *C);
 /* Velocity RHS b[d*a + k] = sum_e int_e S0_k psi_a + (S1 grad psi_a)_k with
  * S = S^J + lambda S^C (eq. S0andS1).  rhs_out (host, d*N_n) may be NULL. */
 FO_API fo_status fo_shape_derivative(fo_problem *prob, double lambda, double *rhs_out);
+/* Cost and every constraint: J (summed over the load cases) and C[0..nc) with nc the
+ * problem's number of constraints (n_volume, or 1 when volume_target > 0, or 0); C may be NULL
+ * when nc = 0; FO_EINVAL when nc differs from the problem's.  Synchronises. */
+FO_API fo_status fo_functionals_v(fo_problem *prob, double *J, double *C, int nc);
+/* Velocity RHS with one multiplier per constraint: S = sum_k S^J(u_k) + sum_j lambda_j S^C_j
+ * (eq. S0andS1, Sec. 5.4); nc as for fo_functionals_v; rhs_out (host) may be NULL. */
+FO_API fo_status fo_shape_derivative_v(fo_problem *prob, const double *lambda, int nc, double *rhs_out);
 /* Velocity solve B theta = -b (eq. velocity); Btt = B(theta, theta) = -b . theta. */
 FO_API fo_status fo_descent(fo_problem *prob, const fo_solve_opts *opts, double *Btt, fo_solve_stats *stats);
 /* Build the transport matrices L, R for time step dt (eq. weak_transport, tau of
@@ -450,6 +473,19 @@ FO_API void fo_ppl_update(fo_ppl *s, const double *C, double J, double *lambda_o
 /* Adaptive time (eqs tend, steps): t_end clamped to [t_min, t_max] with B(theta, theta)
  * floored at 1e-12, steps clamped to [s_min, s_max] and rounded half away from zero. */
 FO_API void fo_adaptime(double Btt, const fo_run_options *opts, double *t_end, int *nsteps);
+/* Stopping criterion of Sec. 5.7 at iteration i = n - 1: values[0..n) are J (no constraints)
+ * or L (with constraints) of iterations 0..i; C the constraint vector of iteration i (nc
+ * values, nc = 0 without constraints).  *stop = 1 when i > start_to_check and
+ * max_{i - prev <= j < i} |v_i - v_j| < tol |v_i|, and, with constraints, max_j |C_j - 1| <
+ * ctrn_tol.  Defaults (fo_stop_opts_default): 30, 1e-2, 1e-2, 10 (cost_tol = lgrn_tol = tol). */
+typedef struct {
+  int start_to_check;
+  double tol;
+  double ctrn_tol;
+  int prev;
+} fo_stop_opts;
+FO_API void fo_stop_opts_default(fo_stop_opts *o);
+FO_API void fo_stop_check(const double *values, int n, const double *C, int nc, const fo_stop_opts *o, int *stop);
 /* Default run options of runDP (Sec. 5.1) and default solver options. */
 FO_API void fo_run_options_default(fo_run_options *opts);
 FO_API void fo_solve_opts_default(fo_solve_opts *opts);

@@ -39,7 +39,9 @@ class ModelDesc(C.Structure):
                 ("normal_penalty", C.c_double), ("omega0_weight", C.c_double), ("n_omega0", C.c_int),
                 ("omega0_lo", D43), ("omega0_hi", D43), ("velocity_dirichlet", C.c_int),
                 ("n_inst", C.c_int), ("inst_k", C.POINTER(C.c_double)), ("inst_omega", C.POINTER(C.c_double)),
-                ("inst_f", C.POINTER(C.c_double)), ("coef_rule", C.c_int)]
+                ("inst_f", C.POINTER(C.c_double)), ("coef_rule", C.c_int), ("n_cases", C.c_int),
+                ("point_case", C.c_int * 4), ("traction_case", C.c_int * 4), ("n_volume", C.c_int),
+                ("volume_lo", D43), ("volume_hi", D43), ("volume_V", C.c_double * 4)]
 
 
 class TuneResult(C.Structure):
@@ -101,7 +103,12 @@ class IterLog(C.Structure):
                 ("state", SolveStats), ("velocity", SolveStats), ("transport", SolveStats),
                 ("reinit_stats", SolveStats), ("ms_state", C.c_double), ("ms_functionals", C.c_double),
                 ("ms_shape", C.c_double), ("ms_velocity", C.c_double), ("ms_transport", C.c_double),
-                ("ms_reinit", C.c_double), ("ms_state_kernel", C.c_double)]
+                ("ms_reinit", C.c_double), ("ms_state_kernel", C.c_double), ("nc", C.c_int),
+                ("Cv", C.c_double * 4), ("lambdav", C.c_double * 4)]
+
+
+class StopOpts(C.Structure):
+    _fields_ = [("start_to_check", C.c_int), ("tol", C.c_double), ("ctrn_tol", C.c_double), ("prev", C.c_int)]
 
 
 VP = C.c_void_p
@@ -122,6 +129,10 @@ PROTOTYPES = {
     "fo_launch_count": (ST, [C.POINTER(C.c_ulonglong)]),
     "fo_mesh_box": (ST, [VP, C.c_int, C.POINTER(C.c_int), DP, DP, C.POINTER(VP)]),
     "fo_mesh_from_arrays": (ST, [VP, C.c_int, C.c_int64, VP, C.c_int64, VP, C.POINTER(VP)]),
+    "fo_functionals_v": (ST, [VP, DP, DP, C.c_int]),
+    "fo_shape_derivative_v": (ST, [VP, DP, C.c_int, DP]),
+    "fo_stop_opts_default": (None, [VP]),
+    "fo_stop_check": (None, [DP, C.c_int, DP, C.c_int, VP, C.POINTER(C.c_int)]),
     "fo_mesh_destroy": (ST, [VP]),
     "fo_mesh_query": (ST, [VP, C.POINTER(MeshInfo)]),
     "fo_mesh_copy_out": (ST, [VP, VP, VP]),

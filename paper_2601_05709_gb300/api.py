@@ -61,7 +61,8 @@ def run_options(dfactor=1e-2, lv_time=(1e-3, 1e-1), lv_iter=(8, 16), smooth=Fals
 
 def model_desc(kind, a_in=1.0, a_out=1e-3, E=1.0, nu=0.3, k=1.0, omega=0.0, dirichlet=(), f_nodal=None,
                point_loads=(), tractions=(), volume=0.0, alpha_mass=0.1, normal_penalty=0.0, omega0_weight=0.0,
-               omega0_boxes=(), velocity_dirichlet=False, inst_k=None, inst_omega=None, inst_f=None, coef_rule=0):
+               omega0_boxes=(), velocity_dirichlet=False, inst_k=None, inst_omega=None, inst_f=None, coef_rule=0,
+               load_cases=None, volume_regions=None):
     """Build a fo_model_desc.  dirichlet: [(axis, side)]; point_loads: [(node, vec)];
     tractions: [(axis, side, vec)]; omega0_boxes: [(lo, hi)] with strict inequalities.
     A task-parallel batch (kind FO_HELMHOLTZ): inst_k, inst_omega [n_inst] and
@@ -97,6 +98,35 @@ def model_desc(kind, a_in=1.0, a_out=1e-3, E=1.0, nu=0.3, k=1.0, omega=0.0, diri
             d.omega0_hi[i][c] = hi[c] if c < len(hi) else np.inf
     d.velocity_dirichlet = int(bool(velocity_dirichlet))
     d.coef_rule = int(coef_rule)
+    if load_cases is not None:
+        # several load cases: [(point_loads, tractions)] per case (f_nodal belongs to case 0)
+        pts = [(k, pl) for k, (pls, _) in enumerate(load_cases) for pl in pls]
+        trs = [(k, tr) for k, (_, trl) in enumerate(load_cases) for tr in trl]
+        if len(load_cases) > 4 or len(pts) > 4 or len(trs) > 4:
+            raise ValueError("at most 4 load cases, 4 point loads and 4 tractions")
+        d.n_cases = len(load_cases)
+        d.n_point_loads = len(pts)
+        for i, (k, (node, vec)) in enumerate(pts):
+            d.point_case[i] = k
+            d.point_node[i] = int(node)
+            for c, v in enumerate(vec):
+                d.point_vec[i][c] = v
+        d.n_tractions = len(trs)
+        for i, (k, (axis, side, vec)) in enumerate(trs):
+            d.traction_case[i] = k
+            d.traction_face[i] = 2 * axis + side
+            for c, v in enumerate(vec):
+                d.traction_vec[i][c] = v
+    if volume_regions is not None:
+        # several volume constraints: [(lo, hi, V)] boxes on the element centroid
+        if len(volume_regions) > 4:
+            raise ValueError("at most 4 volume constraints")
+        d.n_volume = len(volume_regions)
+        for j, (lo, hi, V) in enumerate(volume_regions):
+            d.volume_V[j] = V
+            for c in range(3):
+                d.volume_lo[j][c] = lo[c] if c < len(lo) else -np.inf
+                d.volume_hi[j][c] = hi[c] if c < len(hi) else np.inf
     kept = [keep]
     if inst_k is not None:
         ik, io = _f64(inst_k), _f64(inst_omega)
@@ -220,6 +250,8 @@ class Problem:
         self.kind = desc.kind
         self.ncomp = mesh.dim if desc.kind == FO_ELASTIC else 1
         self.n_inst = int(desc.n_inst)       # 0: a single problem
+        self.n_cases = max(int(desc.n_cases), 1)
+        self.nc = int(desc.n_volume) if desc.n_volume > 0 else (1 if desc.volume_target > 0 else 0)
 
     def _chk(self, st, what):
         return self.ctx.check(st, what)
@@ -314,7 +346,7 @@ class Problem:
     def _field_len(self, field):
         m = self.mesh
         if field in (FO_FIELD_U, FO_FIELD_P, FO_FIELD_LOAD):
-            return self.ncomp * m.num_nodes * max(self.n_inst, 1)
+            return self.ncomp * m.num_nodes * max(self.n_inst, 1) * self.n_cases
         if field in (FO_FIELD_THETA, FO_FIELD_RHS):
             return m.dim * m.num_nodes
         if field in (FO_FIELD_COEF, FO_FIELD_CHI, FO_FIELD_OMEGA0):
@@ -326,6 +358,22 @@ class Problem:
         self._chk(self.lib.fo_get(self.handle, field, out.ctypes.data_as(C.c_void_p)), "fo_get")
         if self.n_inst and field in (FO_FIELD_U, FO_FIELD_P, FO_FIELD_LOAD):
             return out.reshape(-1, self.n_inst)  # [N_n, n_inst]
+        if self.n_cases > 1 and field in (FO_FIELD_U, FO_FIELD_P, FO_FIELD_LOAD):
+            return out.reshape(self.n_cases, -1)  # [n_cases, N_dof]
+        return out
+
+    def functionals_v(self):
+        """(J summed over the load cases, C[0..nc)) with nc the problem's constraint count."""
+        J = C.c_double()
+        cv = np.zeros(max(self.nc, 1))
+        self._chk(self.lib.fo_functionals_v(self.handle, C.byref(J), _dp(cv), self.nc), "fo_functionals_v")
+        return J.value, cv[: self.nc]
+
+    def shape_derivative_v(self, lams, copy=True):
+        lv = _f64(np.atleast_1d(lams)) if self.nc else np.zeros(1)
+        out = np.empty(self.mesh.dim * self.mesh.num_nodes) if copy else None
+        self._chk(self.lib.fo_shape_derivative_v(self.handle, _dp(lv), self.nc, _dp(out) if copy else None),
+                  "fo_shape_derivative_v")
         return out
 
     def set(self, field, values):
@@ -369,6 +417,19 @@ def launch_count():
     v = C.c_ulonglong()
     _lib.load().fo_launch_count(C.byref(v))
     return v.value
+
+
+def stop_check(values, constraints=None, start_to_check=30, tol=1e-2, ctrn_tol=1e-2, prev=10):
+    """The stopping criterion of Sec. 5.7 (fo_stop_check) at iteration len(values) - 1: values are
+    J (no constraints) or L of iterations 0..i, constraints the vector C of iteration i."""
+    lib = _lib.load()
+    o = _lib.StopOpts(start_to_check, tol, ctrn_tol, prev)
+    v = _f64(values)
+    nc = 0 if constraints is None else len(np.atleast_1d(constraints))
+    cv = _f64(np.atleast_1d(constraints)) if nc else np.zeros(1)
+    stop = C.c_int(0)
+    lib.fo_stop_check(_dp(v), len(v), _dp(cv), nc, C.byref(o), C.byref(stop))
+    return bool(stop.value)
 
 
 def adaptime(Btt, opts=None):

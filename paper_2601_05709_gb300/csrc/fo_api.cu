@@ -359,17 +359,17 @@ extern "C" fo_status fo_mesh_copy_out(const fo_mesh *m, int32_t *cells, double *
 // slots per node), the node graph's nonzeros on a general mesh; `vel_blk`: entries per velocity
 // block (d: component-diagonal on the box grid; d^2 on a general mesh).
 static std::vector<size_t> problem_field_sizes(int d, long long NN, long long NT, long long ND, bool with_f,
-                                               long long entries, int vel_blk) {
+                                               long long entries, int vel_blk, int ncases = 1) {
   const size_t E = (size_t)entries;
   const size_t npn = (size_t)(ND / NN);   // state components per node
   std::vector<size_t> v = {
       sizeof(double) * E * npn * npn, sizeof(float) * E * npn * npn, sizeof(double) * E * vel_blk,
       sizeof(double) * NN,     sizeof(double) * NT,     sizeof(float) * NT,       (size_t)NT,
-      (size_t)NT,              (size_t)ND,              (size_t)NN,               sizeof(double) * ND,
-      sizeof(double) * ND,     sizeof(double) * ND,     sizeof(double) * d * NN,  sizeof(double) * d * NN,
+      (size_t)NT,              (size_t)ND,              (size_t)NN,               sizeof(double) * ND * ncases,
+      sizeof(double) * ND * ncases, sizeof(double) * ND * ncases, sizeof(double) * d * NN, sizeof(double) * d * NN,
       sizeof(double) * ND,     sizeof(float) * ND,      sizeof(double) * d * NN,  sizeof(double) * E,
       sizeof(double) * E,      sizeof(double) * NN,     sizeof(double) * FO_RED_DOUBLES,
-      64,                      sizeof(int) * DS_COUNT,  sizeof(double) * NT,
+      64,                      sizeof(int) * DS_COUNT,  sizeof(double) * NT,     (size_t)NT,
   };
   if (with_f) v.push_back(sizeof(double) * NN);
   return v;
@@ -380,7 +380,7 @@ static size_t prob_bytes_fields(const fo_problem *p, std::vector<std::pair<void 
   const long long entries = p->mesh->um ? p->mesh->um->nnz : (long long)(g.dim == 2 ? 7 : 15) * g.num_nodes;
   const std::vector<size_t> sz = problem_field_sizes(g.dim, g.num_nodes, g.num_elems, p->ndof,
                                                      p->f || p->desc.kind != FO_ELASTIC, entries,
-                                                     p->mesh->um ? g.dim * g.dim : g.dim);
+                                                     p->mesh->um ? g.dim * g.dim : g.dim, p->ncases);
   std::vector<void **> ptr = {
       (void **)&p->Wst,        (void **)&p->Wst32,        (void **)&p->Wvel,
       (void **)&p->phi,        (void **)&p->coef,         (void **)&p->coef32,       (void **)&p->chi,
@@ -388,7 +388,7 @@ static size_t prob_bytes_fields(const fo_problem *p, std::vector<std::pair<void 
       (void **)&p->u,          (void **)&p->p,            (void **)&p->rhs,          (void **)&p->theta,
       (void **)&p->dinv_state, (void **)&p->dinv_state32, (void **)&p->dinv_vel,     (void **)&p->L,
       (void **)&p->R,          (void **)&p->dinvL,        (void **)&p->red,
-      (void **)&p->bar,        (void **)&p->dev_status,   (void **)&p->chif,
+      (void **)&p->bar,        (void **)&p->dev_status,   (void **)&p->chif,         (void **)&p->regmask,
   };
   if (sz.size() > ptr.size()) ptr.push_back((void **)&p->f);
   list.clear();
@@ -460,6 +460,18 @@ extern "C" fo_status fo_problem_create(fo_mesh *m, const fo_model_desc *desc, fo
     return fo_fail(ctx, FO_EINVAL, "a task-parallel batch (n_inst > 0) is a FO_HELMHOLTZ family");
   if (desc->coef_rule != FO_COEF_CENTROID && desc->coef_rule != FO_COEF_CUT)
     return fo_fail(ctx, FO_EINVAL, "bad coefficient rule");
+  if (desc->n_cases < 0 || desc->n_cases > 4 || desc->n_volume < 0 || desc->n_volume > 4)
+    return fo_fail(ctx, FO_EINVAL, "at most 4 load cases and 4 volume constraints");
+  for (int i = 0; i < desc->n_point_loads; ++i)
+    if (desc->point_case[i] < 0 || desc->point_case[i] >= std::max(desc->n_cases, 1))
+      return fo_fail(ctx, FO_EINVAL, "point load case out of range");
+  for (int i = 0; i < desc->n_tractions; ++i)
+    if (desc->traction_case[i] < 0 || desc->traction_case[i] >= std::max(desc->n_cases, 1))
+      return fo_fail(ctx, FO_EINVAL, "traction case out of range");
+  for (int j = 0; j < desc->n_volume; ++j)
+    if (!(desc->volume_V[j] > 0)) return fo_fail(ctx, FO_EINVAL, "volume targets must be positive");
+  if (desc->n_inst > 0 && (desc->n_cases > 1 || desc->n_volume > 0))
+    return fo_fail(ctx, FO_EINVAL, "task-parallel batches take one load and at most one volume constraint");
   if (desc->n_inst > 0 && desc->coef_rule != FO_COEF_CENTROID)
     return fo_fail(ctx, FO_EINVAL, "task-parallel batches take the one-point coefficient rule");
   if (m->um && desc->n_inst > 0)
@@ -471,6 +483,8 @@ extern "C" fo_status fo_problem_create(fo_mesh *m, const fo_model_desc *desc, fo
   p->desc.f_nodal = nullptr;
   p->ncomp = desc->kind == FO_ELASTIC ? g.dim : 1;
   p->ndof = g.num_nodes * p->ncomp;
+  p->ncases = std::max(desc->n_cases, 1);
+  p->nvol = desc->n_volume;
   if (desc->kind == FO_ELASTIC) {
     p->lame_lambda = desc->E * desc->nu / ((1.0 + desc->nu) * (1.0 - 2.0 * desc->nu));
     p->lame_mu = desc->E / (2.0 * (1.0 + desc->nu));
@@ -498,7 +512,8 @@ extern "C" fo_status fo_problem_create(fo_mesh *m, const fo_model_desc *desc, fo
       st = fo_cuda_check(ctx, cudaMemsetAsync(p->f, 0, sizeof(double) * g.num_nodes, ctx->stream), "zero f");
   }
   if (st == FO_OK) st = fo_cuda_check(ctx, cudaMemsetAsync(p->phi, 0, sizeof(double) * g.num_nodes, ctx->stream), "phi");
-  if (st == FO_OK) st = fo_cuda_check(ctx, cudaMemsetAsync(p->u, 0, sizeof(double) * p->ndof, ctx->stream), "u");
+  if (st == FO_OK)
+    st = fo_cuda_check(ctx, cudaMemsetAsync(p->u, 0, sizeof(double) * p->ndof * p->ncases, ctx->stream), "u");
   if (st == FO_OK) st = fo_cuda_check(ctx, cudaMemsetAsync(p->theta, 0, sizeof(double) * g.dim * g.num_nodes, ctx->stream), "theta");
   if (m->um) {
     if (st == FO_OK) st = fo_umesh_masks(p);
@@ -571,7 +586,25 @@ extern "C" fo_status fo_state_solve(fo_problem *p, const fo_solve_opts *o, fo_so
   fo_solve_opts_default(&def);
   if (!o) o = &def;
   if (!p->coef_valid) FO_TRY(fo_coefficients(p));
-  fo_status s = p->batch ? fo_batch_state(p, false, o, st) : fo_state_pcg(p, p->load, p->u, o, st);
+  fo_status s;
+  if (p->batch) s = fo_batch_state(p, false, o, st);
+  else if (p->ncases == 1) s = fo_state_pcg(p, p->load, p->u, o, st);
+  else {   // one solve per load case (eq. compli_plus); statistics summed, worst residual kept
+    fo_solve_stats tot;
+    memset(&tot, 0, sizeof tot);
+    s = FO_OK;
+    for (int k = 0; k < p->ncases && (s == FO_OK || s == FO_ENOCONV); ++k) {
+      fo_solve_stats sk;
+      memset(&sk, 0, sizeof sk);
+      const fo_status sk_st = fo_state_pcg(p, p->load + (size_t)k * p->ndof, p->u + (size_t)k * p->ndof, o, &sk);
+      if (sk_st != FO_OK) s = sk_st;
+      tot.iterations += sk.iterations;
+      tot.outer_iterations += sk.outer_iterations;
+      tot.operator_applies += sk.operator_applies;
+      tot.rel_residual = std::max(tot.rel_residual, sk.rel_residual);
+    }
+    if (st) *st = tot;
+  }
   if (s == FO_OK || s == FO_ENOCONV) p->u_valid = true;
   return s;
 }
@@ -590,31 +623,119 @@ extern "C" fo_status fo_adjoint_solve(fo_problem *p, const fo_solve_opts *o, fo_
   if (p->batch) return fo_batch_state(p, true, o, st);
   double c = p->desc.kind == FO_ELASTIC ? -2.0 : -1.0;
   double *b = p->rhs;   // reuse the RHS buffer as the adjoint load (d*N_n >= N_dof)
-  k_scale<<<fo_blocks_for(p->ndof), FO_BLOCK, 0, p->ctx->stream>>>(p->load, b, c, p->ndof);
-  fo_note_launch(1);
-  FO_CU(p->ctx, cudaGetLastError());
   fo_solve_opts oo = *o;
   oo.warm_start = 0;
-  fo_status s = fo_state_pcg(p, b, p->p, &oo, st);
+  fo_status s = FO_OK;
+  for (int k = 0; k < p->ncases && s == FO_OK; ++k) {   // one adjoint per load case
+    k_scale<<<fo_blocks_for(p->ndof), FO_BLOCK, 0, p->ctx->stream>>>(p->load + (size_t)k * p->ndof, b, c, p->ndof);
+    fo_note_launch(1);
+    FO_CU(p->ctx, cudaGetLastError());
+    s = fo_state_pcg(p, b, p->p + (size_t)k * p->ndof, &oo, st);
+  }
   p->rhs_valid = false;
   return s;
 }
 
+// Number of constraints of a problem: the region constraints, else |Omega| / V when V > 0.
+static int problem_nc(const fo_problem *p) { return p->nvol > 0 ? p->nvol : (p->desc.volume_target > 0 ? 1 : 0); }
+
+// J summed over the load cases and |Omega|.
+static fo_status cost_and_volume(fo_problem *p, double *J, double *vol) {
+  if (!p->coef_valid) FO_TRY(fo_coefficients(p));
+  double j = 0, v = 0;
+  if (p->batch) FO_TRY(fo_batch_functionals(p, &j, &v, nullptr));
+  else
+    for (int k = 0; k < p->ncases; ++k) {
+      double jk = 0;
+      const double *u = p->u + (size_t)k * p->ndof, *F = p->load + (size_t)k * p->ndof;
+      if (p->mesh->um) FO_TRY(fo_umesh_functionals_on(p, u, F, &jk, &v));
+      else FO_TRY(fo_launch_functionals_on(p, u, F, &jk, &v));
+      j += jk;
+    }
+  if (!std::isfinite(j) || !std::isfinite(v)) return fo_fail(p->ctx, FO_ENAN, "non-finite functional");
+  *J = j;
+  *vol = v;
+  return FO_OK;
+}
+
 extern "C" fo_status fo_functionals(fo_problem *p, double *J, double *C) {
   if (!p) return FO_EINVAL;
-  if (!p->coef_valid) FO_TRY(fo_coefficients(p));
   double j = 0, vol = 0;
-  if (p->batch) FO_TRY(fo_batch_functionals(p, &j, &vol, nullptr));
-  else if (p->mesh->um) FO_TRY(fo_umesh_functionals(p, &j, &vol));
-  else FO_TRY(fo_launch_functionals(p, &j, &vol));
+  FO_TRY(cost_and_volume(p, &j, &vol));
   if (J) *J = j;
-  if (C) *C = p->desc.volume_target > 0 ? vol / p->desc.volume_target : vol;
-  if (!std::isfinite(j) || !std::isfinite(vol)) return fo_fail(p->ctx, FO_ENAN, "non-finite functional");
+  if (C) {
+    if (p->nvol > 0) {
+      double c[4];
+      FO_TRY(fo_functionals_v(p, nullptr, c, p->nvol));
+      *C = c[0];
+    } else {
+      *C = p->desc.volume_target > 0 ? vol / p->desc.volume_target : vol;
+    }
+  }
+  return FO_OK;
+}
+
+extern "C" fo_status fo_functionals_v(fo_problem *p, double *J, double *C, int nc) {
+  if (!p) return FO_EINVAL;
+  if (nc != problem_nc(p) || (nc > 0 && !C))
+    return fo_fail(p->ctx, FO_EINVAL, "the problem has %d constraints", problem_nc(p));
+  double j = 0, vol = 0;
+  FO_TRY(cost_and_volume(p, &j, &vol));
+  if (J) *J = j;
+  if (p->nvol > 0) {
+    double rv[4];
+    FO_TRY(fo_region_volumes(p, p->mesh->um ? p->mesh->um->vol : nullptr, rv));
+    for (int q = 0; q < p->nvol; ++q) C[q] = rv[q] / p->desc.volume_V[q];
+  } else if (nc == 1) {
+    C[0] = vol / p->desc.volume_target;
+  }
+  return FO_OK;
+}
+
+extern "C" fo_status fo_shape_derivative_v(fo_problem *p, const double *lambda, int nc, double *rhs_out) {
+  if (!p) return FO_EINVAL;
+  if (nc != problem_nc(p) || (nc > 0 && !lambda))
+    return fo_fail(p->ctx, FO_EINVAL, "the problem has %d constraints", problem_nc(p));
+  if (p->batch || (p->ncases == 1 && p->nvol == 0)) return fo_shape_derivative(p, nc ? lambda[0] : 0.0, rhs_out);
+  if (!p->coef_valid) FO_TRY(fo_coefficients(p));
+  fo_ctx *ctx = p->ctx;
+  const Grid &g = p->mesh->g;
+  const long long NN = g.num_nodes, NT = g.num_elems;
+  // zero state and source (for the constraint terms and the source-free cases) and one weight array
+  double *z;
+  FO_TRY(fo_scratch(p, sizeof(double) * (std::max<long long>(p->ndof, NN) + NT), (void **)&z));
+  double *w = z + std::max<long long>(p->ndof, NN);
+  FO_CU(ctx, cudaMemsetAsync(z, 0, sizeof(double) * std::max<long long>(p->ndof, NN), ctx->stream));
+  const double *chif = p->desc.coef_rule == FO_COEF_CUT ? p->chif : nullptr;
+  const double invV = p->desc.volume_target > 0 ? 1.0 / p->desc.volume_target : 1.0;
+  auto shape = [&](const double *u, const double *f, double lam, const double *wt, double iv, int add) {
+    return p->mesh->um ? fo_umesh_shape_rhs_ex(p, u, f, lam, wt, iv, add) : fo_launch_shape_rhs_ex(p, u, f, lam, wt, iv, add);
+  };
+  for (int k = 0; k < p->ncases; ++k) {   // sum_k b^J(u_k) (+ lambda b^C with one constraint)
+    const double lam = (p->nvol == 0 && k == 0 && nc == 1) ? lambda[0] : 0.0;
+    const double *f = (k == 0) ? p->f : z;
+    FO_TRY(shape(p->u + (size_t)k * p->ndof, f ? f : z, lam, chif, invV, k > 0));
+  }
+  for (int q = 0; q < p->nvol; ++q) {     // + lambda_j b^C_j: S1 = chi chi_Rj / V_j I (u = 0)
+    if (lambda[q] == 0.0) continue;
+    FO_TRY(fo_region_weight(p, q, w));
+    FO_TRY(shape(z, z, lambda[q], w, 1.0 / p->desc.volume_V[q], 1));
+  }
+  p->rhs_valid = true;
+  p->last_lambda = nc ? lambda[0] : 0.0;
+  if (rhs_out) {
+    FO_CU(ctx, cudaMemcpyAsync(rhs_out, p->rhs, sizeof(double) * g.dim * NN, cudaMemcpyDeviceToHost, ctx->stream));
+    FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   return FO_OK;
 }
 
 extern "C" fo_status fo_shape_derivative(fo_problem *p, double lambda, double *rhs_out) {
   if (!p) return FO_EINVAL;
+  if (!p->batch && (p->ncases > 1 || p->nvol > 0)) {   // one multiplier: the first constraint's
+    double lv[4] = {lambda, 0, 0, 0};
+    return fo_shape_derivative_v(p, lv, problem_nc(p), rhs_out);
+  }
   if (!p->coef_valid) FO_TRY(fo_coefficients(p));
   if (p->batch) FO_TRY(fo_batch_shape_rhs(p, lambda));
   else if (p->mesh->um) FO_TRY(fo_umesh_shape_rhs(p, lambda));
@@ -747,8 +868,8 @@ static double *field_ptr(fo_problem *p, int field, size_t *n, bool *is_u8) {
   *is_u8 = false;
   switch (field) {
     case FO_FIELD_PHI: *n = g.num_nodes; return p->phi;
-    case FO_FIELD_U: *n = p->ndof; return p->u;
-    case FO_FIELD_P: *n = p->ndof; return p->p;
+    case FO_FIELD_U: *n = p->ndof * p->ncases; return p->u;
+    case FO_FIELD_P: *n = p->ndof * p->ncases; return p->p;
     case FO_FIELD_THETA: *n = g.dim * g.num_nodes; return p->theta;
     case FO_FIELD_RHS: *n = g.dim * g.num_nodes; return p->rhs;
     case FO_FIELD_COEF: *n = g.num_elems; return p->coef;
@@ -756,7 +877,7 @@ static double *field_ptr(fo_problem *p, int field, size_t *n, bool *is_u8) {
       *n = g.num_elems;
       *is_u8 = p->desc.coef_rule != FO_COEF_CUT;
       return p->desc.coef_rule == FO_COEF_CUT ? p->chif : (double *)p->chi;
-    case FO_FIELD_LOAD: *n = p->ndof; return p->load;
+    case FO_FIELD_LOAD: *n = p->ndof * p->ncases; return p->load;
     case FO_FIELD_OMEGA0: *n = g.num_elems; *is_u8 = true; return (double *)p->omega0;
     default: return nullptr;
   }
@@ -911,6 +1032,36 @@ extern "C" void fo_adaptime(double Btt, const fo_run_options *o, double *t_end, 
   if (nsteps) *nsteps = (int)std::floor(s + 0.5);
 }
 
+extern "C" void fo_stop_opts_default(fo_stop_opts *o) {
+  if (!o) return;
+  o->start_to_check = 30;
+  o->tol = 1e-2;
+  o->ctrn_tol = 1e-2;
+  o->prev = 10;
+}
+
+// Stopping criterion (Sec. 5.7): at i = n - 1 > start_to_check, the largest difference of
+// values[i] from the previous `prev` values below tol |values[i]|, and max |C_j - 1| below
+// ctrn_tol when there are constraints.
+extern "C" void fo_stop_check(const double *values, int n, const double *C, int nc, const fo_stop_opts *o, int *stop) {
+  if (!stop) return;
+  *stop = 0;
+  fo_stop_opts def;
+  fo_stop_opts_default(&def);
+  if (!o) o = &def;
+  const int i = n - 1;
+  if (!values || i <= o->start_to_check || i < o->prev || o->prev < 1) return;
+  double spread = 0;
+  for (int j = i - o->prev; j < i; ++j) spread = std::max(spread, std::fabs(values[i] - values[j]));
+  if (!(spread < o->tol * std::fabs(values[i]))) return;
+  if (nc > 0 && C) {
+    double err = 0;
+    for (int q = 0; q < nc; ++q) err = std::max(err, std::fabs(C[q] - 1.0));
+    if (!(err < o->ctrn_tol)) return;
+  }
+  *stop = 1;
+}
+
 extern "C" void fo_solve_opts_default(fo_solve_opts *o) {
   if (!o) return;
   memset(o, 0, sizeof *o);
@@ -961,24 +1112,27 @@ extern "C" fo_status fo_opt_step(fo_problem *p, int iter, const fo_run_options *
   if (s != FO_OK) return s;
   lg.ms_state_kernel = ctx->last_solve_ms;
   FO_TRY(mark(1));
-  double J = 0, C = 0;
-  FO_TRY(fo_functionals(p, &J, &C));
+  const int nc = problem_nc(p);
+  double J = 0, Cv[4] = {0, 0, 0, 0}, lv[4] = {0, 0, 0, 0};
+  FO_TRY(fo_functionals_v(p, &J, Cv, nc));
   FO_TRY(mark(2));
   lg.J = J;
   lg.L = J;
-  double lam = 0;
-  if (p->desc.volume_target > 0) {
-    lg.C = C;
-    if (ppl) {
-      double lv[4] = {0, 0, 0, 0};
-      double Cv[4] = {C, 0, 0, 0};
+  lg.nc = nc;
+  if (nc > 0) {
+    lg.C = Cv[0];
+    if (ppl) {   // one PPL update of the whole constraint vector (Sec. 5.4)
+      if (ppl->nc != nc) return fo_fail(ctx, FO_EINVAL, "the PPL state has %d constraints, the problem %d", ppl->nc, nc);
       fo_ppl_update(ppl, Cv, J, lv, &lg.L);
-      lam = lv[0];
     }
   }
-  lg.lambda = lam;
+  for (int q = 0; q < 4; ++q) {
+    lg.Cv[q] = Cv[q];
+    lg.lambdav[q] = lv[q];
+  }
+  lg.lambda = lv[0];
   FO_TRY(mark(3));
-  FO_TRY(fo_shape_derivative(p, lam, nullptr));
+  FO_TRY(fo_shape_derivative_v(p, lv, nc, nullptr));
   FO_TRY(mark(4));
   double Btt = 0;
   s = fo_descent(p, &o->velocity, &Btt, &lg.velocity);

@@ -61,10 +61,13 @@ struct MaskArgs {
   int vel_dirichlet;
   int n_omega0;
   double o_lo[4][3], o_hi[4][3];
+  int n_vol;                       // constraint regions (bit j of regmask)
+  double v_lo[4][3], v_hi[4][3];
 };
 
 template <int D>
-__global__ void k_masks(MaskArgs m, const double *coords, uint8_t *dir, uint8_t *vdir, uint8_t *omega0) {
+__global__ void k_masks(MaskArgs m, const double *coords, uint8_t *dir, uint8_t *vdir, uint8_t *omega0,
+                        uint8_t *regmask) {
   const Grid &g = m.g;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -110,6 +113,17 @@ __global__ void k_masks(MaskArgs m, const double *coords, uint8_t *dir, uint8_t 
       in = in || ok;
     }
     omega0[e] = in ? 1 : 0;
+    unsigned rm = 0;
+    for (int b = 0; b < m.n_vol; ++b) {
+      bool ok = true;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double x = s[k] / (double)(D + 1);
+        ok = ok && (x > m.v_lo[b][k]) && (x < m.v_hi[b][k]);
+      }
+      if (ok) rm |= 1u << b;
+    }
+    regmask[e] = (uint8_t)rm;
   }
 }
 
@@ -125,11 +139,16 @@ fo_status fo_launch_masks(fo_problem *p) {
     for (int k = 0; k < 3; ++k) {
       m.o_lo[b][k] = p->desc.omega0_lo[b][k];
       m.o_hi[b][k] = p->desc.omega0_hi[b][k];
+      m.v_lo[b][k] = p->desc.volume_lo[b][k];
+      m.v_hi[b][k] = p->desc.volume_hi[b][k];
     }
+  m.n_vol = p->nvol;
   long long n = g.num_nodes > g.num_elems ? g.num_nodes : g.num_elems;
   int blocks = fo_blocks_for(n, FO_BLOCK, 65536);
-  if (g.dim == 2) k_masks<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, p->mesh->d_coords, p->dir, p->vdir, p->omega0);
-  else k_masks<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, p->mesh->d_coords, p->dir, p->vdir, p->omega0);
+  if (g.dim == 2)
+    k_masks<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, p->mesh->d_coords, p->dir, p->vdir, p->omega0, p->regmask);
+  else
+    k_masks<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, p->mesh->d_coords, p->dir, p->vdir, p->omega0, p->regmask);
   fo_note_launch(1);
   FO_CU(p->ctx, cudaGetLastError());
   return FO_OK;
@@ -208,40 +227,49 @@ __global__ void k_point_loads(int n, const long long *node, const double *vec, i
     }
 }
 
+// One load vector per load case k (case-major at p->load + k N_dof): f in case 0 only, each
+// case's own tractions and point loads.
 fo_status fo_launch_loads(fo_problem *p) {
   const Grid &g = p->mesh->g;
   fo_ctx *ctx = p->ctx;
-  LoadArgs L{};
-  L.g = g;
-  L.ncomp = p->ncomp;
-  L.n_tr = p->desc.n_tractions;
-  for (int t = 0; t < 4; ++t) {
-    L.tr_face[t] = p->desc.traction_face[t];
-    for (int k = 0; k < 3; ++k) L.tr_vec[t][k] = p->desc.traction_vec[t][k];
-  }
-  L.mref = g.vol_e / ((g.dim + 1) * (g.dim + 2));
-  const double *f = (p->desc.kind != FO_ELASTIC) ? p->f : nullptr;
-  int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
-  if (g.dim == 2) k_loads<2><<<blocks, FO_BLOCK, 0, ctx->stream>>>(L, f, p->dir, p->load);
-  else k_loads<3><<<blocks, FO_BLOCK, 0, ctx->stream>>>(L, f, p->dir, p->load);
-  fo_note_launch(1);
-  FO_CU(ctx, cudaGetLastError());
-  if (p->desc.n_point_loads > 0) {
-    // stage the point loads through the reduction buffer (fits: <= 4 * (1 + 3) doubles)
-    long long nodes[4];
-    double vec[12];
-    for (int i = 0; i < 4; ++i) {
-      nodes[i] = p->desc.point_node[i];
-      for (int c = 0; c < 3; ++c) vec[i * 3 + c] = p->desc.point_vec[i][c];
+  for (int k = 0; k < p->ncases; ++k) {
+    double *F = p->load + (size_t)k * p->ndof;
+    LoadArgs L{};
+    L.g = g;
+    L.ncomp = p->ncomp;
+    for (int t = 0; t < p->desc.n_tractions; ++t) {
+      if (p->desc.traction_case[t] != k && p->ncases > 1) continue;
+      L.tr_face[L.n_tr] = p->desc.traction_face[t];
+      for (int c = 0; c < 3; ++c) L.tr_vec[L.n_tr][c] = p->desc.traction_vec[t][c];
+      ++L.n_tr;
     }
-    char *stage = (char *)p->red;
-    FO_CU(ctx, cudaMemcpyAsync(stage, nodes, sizeof nodes, cudaMemcpyHostToDevice, ctx->stream));
-    FO_CU(ctx, cudaMemcpyAsync(stage + 64, vec, sizeof vec, cudaMemcpyHostToDevice, ctx->stream));
-    k_point_loads<<<1, 1, 0, ctx->stream>>>(p->desc.n_point_loads, (const long long *)stage,
-                                            (const double *)(stage + 64), p->ncomp, p->dir, p->load);
+    L.mref = g.vol_e / ((g.dim + 1) * (g.dim + 2));
+    const double *f = (p->desc.kind != FO_ELASTIC && k == 0) ? p->f : nullptr;
+    int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
+    if (g.dim == 2) k_loads<2><<<blocks, FO_BLOCK, 0, ctx->stream>>>(L, f, p->dir, F);
+    else k_loads<3><<<blocks, FO_BLOCK, 0, ctx->stream>>>(L, f, p->dir, F);
     fo_note_launch(1);
     FO_CU(ctx, cudaGetLastError());
-    FO_CU(ctx, cudaStreamSynchronize(ctx->stream));   // host staging arrays go out of scope
+    long long nodes[4];
+    double vec[12];
+    int np = 0;
+    for (int i = 0; i < p->desc.n_point_loads; ++i) {
+      if (p->desc.point_case[i] != k && p->ncases > 1) continue;
+      nodes[np] = p->desc.point_node[i];
+      for (int c = 0; c < 3; ++c) vec[np * 3 + c] = p->desc.point_vec[i][c];
+      ++np;
+    }
+    if (np > 0) {
+      // stage the point loads through the reduction buffer (fits: <= 4 * (1 + 3) doubles)
+      char *stage = (char *)p->red;
+      FO_CU(ctx, cudaMemcpyAsync(stage, nodes, sizeof(long long) * np, cudaMemcpyHostToDevice, ctx->stream));
+      FO_CU(ctx, cudaMemcpyAsync(stage + 64, vec, sizeof(double) * 3 * np, cudaMemcpyHostToDevice, ctx->stream));
+      k_point_loads<<<1, 1, 0, ctx->stream>>>(np, (const long long *)stage, (const double *)(stage + 64), p->ncomp,
+                                              p->dir, F);
+      fo_note_launch(1);
+      FO_CU(ctx, cudaGetLastError());
+      FO_CU(ctx, cudaStreamSynchronize(ctx->stream));   // host staging arrays go out of scope
+    }
   }
   return FO_OK;
 }
@@ -804,15 +832,15 @@ __global__ void k_finish_sum(const double *partials, int nblocks, int nr, double
   if (lane == 0) out[w] = t;
 }
 
-fo_status fo_launch_functionals(fo_problem *p, double *J, double *vol) {
+fo_status fo_launch_functionals_on(fo_problem *p, const double *u, const double *load, double *J, double *vol) {
   const Grid &g = p->mesh->g;
   fo_ctx *ctx = p->ctx;
   FuncArgs f{g, p->desc.kind, p->lame_lambda, p->lame_mu};
   const int blocks = fo_blocks_for(g.num_elems, FO_BLOCK, 1024);
   double *part = p->red, *res = p->red + 2 * 1024;
   const double *chif = p->desc.coef_rule == FO_COEF_CUT ? p->chif : nullptr;
-  if (g.dim == 2) k_functionals<2><<<blocks, FO_BLOCK, 0, ctx->stream>>>(f, p->coef, p->chi, chif, p->u, p->load, part);
-  else k_functionals<3><<<blocks, FO_BLOCK, 0, ctx->stream>>>(f, p->coef, p->chi, chif, p->u, p->load, part);
+  if (g.dim == 2) k_functionals<2><<<blocks, FO_BLOCK, 0, ctx->stream>>>(f, p->coef, p->chi, chif, u, load, part);
+  else k_functionals<3><<<blocks, FO_BLOCK, 0, ctx->stream>>>(f, p->coef, p->chi, chif, u, load, part);
   k_finish_sum<<<1, 64, 0, ctx->stream>>>(part, blocks, 2, res);
   fo_note_launch(2);
   FO_CU(ctx, cudaGetLastError());
@@ -820,6 +848,58 @@ fo_status fo_launch_functionals(fo_problem *p, double *J, double *vol) {
   FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
   *J = ctx->h_scalars[0];
   *vol = ctx->h_scalars[1];
+  return FO_OK;
+}
+
+fo_status fo_launch_functionals(fo_problem *p, double *J, double *vol) {
+  return fo_launch_functionals_on(p, p->u, p->load, J, vol);
+}
+
+// Volume of Omega in each constraint region: sum_e w_e |e| [e in R_j], w_e = chif_e (the
+// material fraction, 0 / 1 for the one-point rule); |e| constant on the box grid (vol null).
+__global__ void k_region_volumes(long long ne, const double *vol, double vol_e, const double *chif,
+                                 const uint8_t *regmask, int nreg, double *partials) {
+  __shared__ double smem[32 * 4];
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
+    const double w = chif[e] * (vol ? vol[e] : vol_e);
+    const unsigned rm = regmask[e];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j < nreg && ((rm >> j) & 1u)) v[j] += w;
+  }
+  block_sum<4>(v, smem);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) partials[blockIdx.x * 4 + j] = v[j];
+}
+
+// w_e = chif_e [e in R_j]: the weights of constraint j's volume term in the shape derivative
+__global__ void k_region_weight(long long ne, const double *chif, const uint8_t *regmask, int j, double *w) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x)
+    w[e] = ((regmask[e] >> j) & 1u) ? chif[e] : 0.0;
+}
+
+fo_status fo_region_volumes(fo_problem *p, const double *vol, double *out) {
+  fo_ctx *ctx = p->ctx;
+  const long long ne = p->mesh->g.num_elems;
+  const int blocks = fo_blocks_for(ne, FO_BLOCK, 1024);
+  double *part = p->red, *res = p->red + 4 * 1024;
+  k_region_volumes<<<blocks, FO_BLOCK, 0, ctx->stream>>>(ne, vol, p->mesh->g.vol_e, p->chif, p->regmask, p->nvol, part);
+  k_finish_sum<<<1, 128, 0, ctx->stream>>>(part, blocks, 4, res);
+  fo_note_launch(2);
+  FO_CU(ctx, cudaGetLastError());
+  FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int j = 0; j < 4; ++j) out[j] = ctx->h_scalars[j];
+  return FO_OK;
+}
+
+fo_status fo_region_weight(fo_problem *p, int j, double *w) {
+  const long long ne = p->mesh->g.num_elems;
+  k_region_weight<<<fo_blocks_for(ne, FO_BLOCK, 65536), FO_BLOCK, 0, p->ctx->stream>>>(ne, p->chif, p->regmask, j, w);
+  fo_note_launch(1);
+  FO_CU(p->ctx, cudaGetLastError());
   return FO_OK;
 }
 
@@ -836,7 +916,7 @@ struct ShapeArgs {
 
 template <int D>
 __global__ void k_shape_rhs(ShapeArgs s, const double *coef, const uint8_t *chi, const double *chif, const double *u,
-                            const double *f, double *b) {
+                            const double *f, double *b, int add) {
   const Grid &g = s.g;
   for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < g.num_nodes;
        a += (long long)gridDim.x * blockDim.x) {
@@ -940,8 +1020,24 @@ __global__ void k_shape_rhs(ShapeArgs s, const double *coef, const uint8_t *chi,
         }
     }
 #pragma unroll
-    for (int k = 0; k < D; ++k) b[a * D + k] = acc[k];
+    for (int k = 0; k < D; ++k) b[a * D + k] = add ? b[a * D + k] + acc[k] : acc[k];
   }
+}
+
+// b (+)= the RHS of state u (source f) with multiplier lambda on the volume weights w
+// (chi_e, or any element weights, over V = 1 / inv_V); add = 0 overwrites b.
+fo_status fo_launch_shape_rhs_ex(fo_problem *p, const double *u, const double *f, double lambda, const double *w,
+                                 double inv_V, int add) {
+  const Grid &g = p->mesh->g;
+  if (p->desc.kind == FO_HELMHOLTZ)
+    return fo_fail(p->ctx, FO_EINVAL, "the single-instance shape derivative covers FO_HEAT and FO_ELASTIC");
+  ShapeArgs s{g, p->desc.kind, p->lame_lambda, p->lame_mu, lambda, inv_V, g.vol_e / ((g.dim + 1) * (g.dim + 2))};
+  int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
+  if (g.dim == 2) k_shape_rhs<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(s, p->coef, p->chi, w, u, f, p->rhs, add);
+  else k_shape_rhs<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(s, p->coef, p->chi, w, u, f, p->rhs, add);
+  fo_note_launch(1);
+  FO_CU(p->ctx, cudaGetLastError());
+  return FO_OK;
 }
 
 fo_status fo_launch_shape_rhs(fo_problem *p, double lambda) {
@@ -952,8 +1048,8 @@ fo_status fo_launch_shape_rhs(fo_problem *p, double lambda) {
               p->desc.volume_target > 0 ? 1.0 / p->desc.volume_target : 1.0, g.vol_e / ((g.dim + 1) * (g.dim + 2))};
   int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
   const double *chif = p->desc.coef_rule == FO_COEF_CUT ? p->chif : nullptr;
-  if (g.dim == 2) k_shape_rhs<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(s, p->coef, p->chi, chif, p->u, p->f, p->rhs);
-  else k_shape_rhs<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(s, p->coef, p->chi, chif, p->u, p->f, p->rhs);
+  if (g.dim == 2) k_shape_rhs<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(s, p->coef, p->chi, chif, p->u, p->f, p->rhs, 0);
+  else k_shape_rhs<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(s, p->coef, p->chi, chif, p->u, p->f, p->rhs, 0);
   fo_note_launch(1);
   FO_CU(p->ctx, cudaGetLastError());
   return FO_OK;

@@ -116,6 +116,9 @@ struct fo_problem {
   float *coef32 = nullptr;       // N_T
   uint8_t *chi = nullptr;        // N_T
   double *chif = nullptr;        // N_T material fraction (1 / 0 for the one-point rule)
+  uint8_t *regmask = nullptr;    // N_T bit j: the element lies in constraint region j
+  int ncases = 1;                // load cases (u, p, load hold ncases blocks of N_dof)
+  int nvol = 0;                  // region constraints (0: the single |Omega| / V, if any)
   uint8_t *omega0 = nullptr;     // N_T
   uint8_t *dir = nullptr;        // N_dof state Dirichlet mask
   uint8_t *vdir = nullptr;       // N_n velocity Dirichlet mask (H^1_0)
@@ -494,6 +497,12 @@ inline int fo_blocks_for(long long n, int block = FO_BLOCK, int cap = 1 << 20) {
 
 // internal entry points implemented across translation units
 fo_status fo_launch_coefficients(fo_problem *p);
+// several load cases and constraints (fo_fem.cu)
+fo_status fo_launch_functionals_on(fo_problem *p, const double *u, const double *load, double *J, double *vol);
+fo_status fo_launch_shape_rhs_ex(fo_problem *p, const double *u, const double *f, double lambda, const double *w,
+                                 double inv_V, int add);
+fo_status fo_region_volumes(fo_problem *p, const double *vol, double *out);
+fo_status fo_region_weight(fo_problem *p, int j, double *w);
 // task-parallel batch (fo_batch.cu)
 fo_status fo_batch_create(fo_problem *p, const fo_model_desc *desc);
 void fo_batch_destroy(fo_problem *p);

@@ -389,6 +389,36 @@ static fo_status state_solve_impl(fo_problem *p, const Op64 &op64, const OpMixed
     s.operator_applies = s.iterations + 1 + (o->warm_start ? 1 : 0);
     s.outer_iterations = 1;
     s.rel_residual = out.out[1] > 0 ? std::sqrt(out.out[0] / out.out[1]) : 0.0;
+    // The single-reduction recurrence updates its residual recursively; over thousands of
+    // iterations that residual drifts from b - A x.  Check the true residual and, while it is
+    // above rtol, restart from x (the warm start forms b - A x afresh): at most two restarts.
+    if (out.status[DS_ERR] != DEV_NOCONV) {
+      fo_ctx *ctx = p->ctx;
+      double *ax64 = buf, *r64 = buf + n;   // the solver's scratch, free after the launch
+      const int blocks = fo_blocks_for(n, FO_BLOCK, 1024);
+      for (int restart = 0; restart < 3; ++restart) {
+        FO_TRY(fo_launch_state_apply(p, x, ax64, true));
+        k_residual_norms<<<blocks, FO_BLOCK, 0, ctx->stream>>>(b, ax64, r64, n, p->red);
+        k_finish_sum2<<<1, 64, 0, ctx->stream>>>(p->red, blocks, out_area(p) + 8);
+        fo_note_launch(2);
+        FO_CU(ctx, cudaGetLastError());
+        FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars, out_area(p) + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+        FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+        const double rn2 = ctx->h_scalars[0], bn2 = ctx->h_scalars[1];
+        s.operator_applies += 1;
+        s.rel_residual = bn2 > 0 ? std::sqrt(rn2 / bn2) : 0.0;
+        if (!(rn2 > o->rtol * o->rtol * bn2) || restart == 2 || s.iterations >= o->maxit) break;
+        a.warm = 1;
+        a.maxit = o->maxit - s.iterations;
+        bind_vectors(a, x, buf, n);
+        FO_TRY(run_pcg<D>(p, op64, a, g.num_nodes, o->grid_blocks, &out));
+        s.iterations += out.status[DS_ITERS];
+        s.operator_applies += out.status[DS_ITERS] + 2;
+        s.outer_iterations += 1;
+        if (out.status[DS_ERR] == DEV_NOCONV) break;
+      }
+    }
     if (st) *st = s;
     if (out.status[DS_ERR] == DEV_NOCONV) return fo_fail(p->ctx, FO_ENOCONV, "PCG reached maxit=%d", o->maxit);
     return FO_OK;

@@ -316,13 +316,15 @@ struct UMaskArgs {
   uint32_t faces;
   int ncomp, vel_dirichlet, n_omega0;
   double o_lo[4][3], o_hi[4][3];
+  int n_vol;
+  double v_lo[4][3], v_hi[4][3];
 };
 
 // State Dirichlet mask per DOF (nodes on a selected box face), the H^1_0 velocity mask (nodes
 // on any box face), and Omega_0 per element: its centroid (vertex coordinates summed in vertex
 // order, then / (d+1)) strictly inside one of the boxes (Sec. 5.7, eq. sub_dom).
 template <int D>
-__global__ void k_u_masks(UMeshView m, UMaskArgs a, uint8_t *dir, uint8_t *vdir, uint8_t *omega0) {
+__global__ void k_u_masks(UMeshView m, UMaskArgs a, uint8_t *dir, uint8_t *vdir, uint8_t *omega0, uint8_t *regmask) {
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
   for (long long i = tid; i < m.nn; i += st) {
     const uint32_t fm = m.face_mask[i];
@@ -349,6 +351,17 @@ __global__ void k_u_masks(UMeshView m, UMaskArgs a, uint8_t *dir, uint8_t *vdir,
       in = in || ok;
     }
     omega0[e] = in ? 1 : 0;
+    unsigned rm = 0;
+    for (int b = 0; b < a.n_vol; ++b) {
+      bool ok = true;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double x = s[k] / (double)(D + 1);
+        ok = ok && (x > a.v_lo[b][k]) && (x < a.v_hi[b][k]);
+      }
+      if (ok) rm |= 1u << b;
+    }
+    regmask[e] = (uint8_t)rm;
   }
 }
 
@@ -363,10 +376,13 @@ fo_status fo_umesh_masks(fo_problem *p) {
     for (int k = 0; k < 3; ++k) {
       a.o_lo[b][k] = p->desc.omega0_lo[b][k];
       a.o_hi[b][k] = p->desc.omega0_hi[b][k];
+      a.v_lo[b][k] = p->desc.volume_lo[b][k];
+      a.v_hi[b][k] = p->desc.volume_hi[b][k];
     }
+  a.n_vol = p->nvol;
   const int blocks = fo_blocks_for(std::max(m.nn, m.nt), FO_BLOCK, 65536);
-  if (m.dim == 2) k_u_masks<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, a, p->dir, p->vdir, p->omega0);
-  else k_u_masks<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, a, p->dir, p->vdir, p->omega0);
+  if (m.dim == 2) k_u_masks<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, a, p->dir, p->vdir, p->omega0, p->regmask);
+  else k_u_masks<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, a, p->dir, p->vdir, p->omega0, p->regmask);
   fo_note_launch(1);
   FO_CU(p->ctx, cudaGetLastError());
   return FO_OK;
@@ -418,24 +434,29 @@ __global__ void k_u_loads(UMeshView m, ULoadArgs L, const double *f, const uint8
 
 fo_status fo_umesh_loads(fo_problem *p) {
   const UMeshView m = umesh_view(p->mesh);
-  ULoadArgs L{};
-  L.ncomp = p->ncomp;
-  L.n_tr = p->desc.n_tractions;
-  for (int t = 0; t < L.n_tr; ++t) {
-    L.tr_face[t] = p->desc.traction_face[t];
-    for (int c = 0; c < 3; ++c) L.tr_vec[t][c] = p->desc.traction_vec[t][c];
+  for (int kc = 0; kc < p->ncases; ++kc) {
+    ULoadArgs L{};
+    L.ncomp = p->ncomp;
+    for (int t = 0; t < p->desc.n_tractions; ++t) {
+      if (p->desc.traction_case[t] != kc && p->ncases > 1) continue;
+      L.tr_face[L.n_tr] = p->desc.traction_face[t];
+      for (int c = 0; c < 3; ++c) L.tr_vec[L.n_tr][c] = p->desc.traction_vec[t][c];
+      ++L.n_tr;
+    }
+    for (int t = 0; t < p->desc.n_point_loads; ++t) {
+      if (p->desc.point_case[t] != kc && p->ncases > 1) continue;
+      L.pt_node[L.n_pt] = p->desc.point_node[t];
+      for (int c = 0; c < 3; ++c) L.pt_vec[L.n_pt][c] = p->desc.point_vec[t][c];
+      ++L.n_pt;
+    }
+    const double *f = (p->desc.kind != FO_ELASTIC && kc == 0) ? p->f : nullptr;
+    double *F = p->load + (size_t)kc * p->ndof;
+    const int blocks = fo_blocks_for(m.nn, FO_BLOCK, 65536);
+    if (m.dim == 2) k_u_loads<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, L, f, p->dir, F);
+    else k_u_loads<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, L, f, p->dir, F);
+    fo_note_launch(1);
+    FO_CU(p->ctx, cudaGetLastError());
   }
-  L.n_pt = p->desc.n_point_loads;
-  for (int t = 0; t < L.n_pt; ++t) {
-    L.pt_node[t] = p->desc.point_node[t];
-    for (int c = 0; c < 3; ++c) L.pt_vec[t][c] = p->desc.point_vec[t][c];
-  }
-  const double *f = (p->desc.kind != FO_ELASTIC) ? p->f : nullptr;
-  const int blocks = fo_blocks_for(m.nn, FO_BLOCK, 65536);
-  if (m.dim == 2) k_u_loads<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, L, f, p->dir, p->load);
-  else k_u_loads<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, L, f, p->dir, p->load);
-  fo_note_launch(1);
-  FO_CU(p->ctx, cudaGetLastError());
   return FO_OK;
 }
 
@@ -758,7 +779,7 @@ __global__ void k_u_finish2(const double *partials, int nblocks, double *out) {
   if (lane == 0) out[w] = t;
 }
 
-fo_status fo_umesh_functionals(fo_problem *p, double *J, double *vol) {
+fo_status fo_umesh_functionals_on(fo_problem *p, const double *u, const double *load, double *J, double *vol) {
   const UMeshView m = umesh_view(p->mesh);
   fo_ctx *ctx = p->ctx;
   const int blocks = fo_blocks_for(std::max(m.nt, m.nn), FO_BLOCK, 1024);
@@ -766,10 +787,10 @@ fo_status fo_umesh_functionals(fo_problem *p, double *J, double *vol) {
   const double *chif = p->desc.coef_rule == FO_COEF_CUT ? p->chif : nullptr;
   if (m.dim == 2)
     k_u_functionals<2><<<blocks, FO_BLOCK, 0, ctx->stream>>>(m, p->desc.kind, p->lame_lambda, p->lame_mu, p->coef,
-                                                             p->chi, chif, p->u, p->load, part);
+                                                             p->chi, chif, u, load, part);
   else
     k_u_functionals<3><<<blocks, FO_BLOCK, 0, ctx->stream>>>(m, p->desc.kind, p->lame_lambda, p->lame_mu, p->coef,
-                                                             p->chi, chif, p->u, p->load, part);
+                                                             p->chi, chif, u, load, part);
   k_u_finish2<<<1, 64, 0, ctx->stream>>>(part, blocks, res);
   fo_note_launch(2);
   FO_CU(ctx, cudaGetLastError());
@@ -780,6 +801,10 @@ fo_status fo_umesh_functionals(fo_problem *p, double *J, double *vol) {
   return FO_OK;
 }
 
+fo_status fo_umesh_functionals(fo_problem *p, double *J, double *vol) {
+  return fo_umesh_functionals_on(p, p->u, p->load, J, vol);
+}
+
 // ------------------------------------------------------------------ shape derivative RHS
 // b[d a + i] = sum over the node's elements of |e| (S1 grad lambda_a)_i + int_e S0_i lambda_a,
 // S1 = S1^J + lambda chi_e / V I (eq. S0andS1; S^J of Sec. 6.2 for elasticity with p = -2u:
@@ -788,7 +813,7 @@ fo_status fo_umesh_functionals(fo_problem *p, double *J, double *vol) {
 template <int D>
 __global__ void k_u_shape_rhs(UMeshView m, int kind, double lam_e, double mu_e, double lam_ppl, double inv_V,
                               const double *coef, const uint8_t *chi, const double *chif, const double *u,
-                              const double *f, double *b) {
+                              const double *f, double *b, int add) {
   for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < m.nn; a += (long long)gridDim.x * blockDim.x) {
     double acc[D];
 #pragma unroll
@@ -871,8 +896,25 @@ __global__ void k_u_shape_rhs(UMeshView m, int kind, double lam_e, double mu_e, 
       }
     }
 #pragma unroll
-    for (int k = 0; k < D; ++k) b[a * D + k] = acc[k];
+    for (int k = 0; k < D; ++k) b[a * D + k] = add ? b[a * D + k] + acc[k] : acc[k];
   }
+}
+
+fo_status fo_umesh_shape_rhs_ex(fo_problem *p, const double *u, const double *f, double lambda, const double *w,
+                                double inv_V, int add) {
+  if (p->desc.kind == FO_HELMHOLTZ)
+    return fo_fail(p->ctx, FO_EINVAL, "the single-instance shape derivative covers FO_HEAT and FO_ELASTIC");
+  const UMeshView m = umesh_view(p->mesh);
+  const int blocks = fo_blocks_for(m.nn, FO_BLOCK, 65536);
+  if (m.dim == 2)
+    k_u_shape_rhs<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, p->desc.kind, p->lame_lambda, p->lame_mu, lambda, inv_V,
+                                                              p->coef, p->chi, w, u, f, p->rhs, add);
+  else
+    k_u_shape_rhs<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, p->desc.kind, p->lame_lambda, p->lame_mu, lambda, inv_V,
+                                                              p->coef, p->chi, w, u, f, p->rhs, add);
+  fo_note_launch(1);
+  FO_CU(p->ctx, cudaGetLastError());
+  return FO_OK;
 }
 
 fo_status fo_umesh_shape_rhs(fo_problem *p, double lambda) {
@@ -884,10 +926,10 @@ fo_status fo_umesh_shape_rhs(fo_problem *p, double lambda) {
   const double *chif = p->desc.coef_rule == FO_COEF_CUT ? p->chif : nullptr;
   if (m.dim == 2)
     k_u_shape_rhs<2><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, p->desc.kind, p->lame_lambda, p->lame_mu, lambda, inv_V,
-                                                              p->coef, p->chi, chif, p->u, p->f, p->rhs);
+                                                              p->coef, p->chi, chif, p->u, p->f, p->rhs, 0);
   else
     k_u_shape_rhs<3><<<blocks, FO_BLOCK, 0, p->ctx->stream>>>(m, p->desc.kind, p->lame_lambda, p->lame_mu, lambda, inv_V,
-                                                              p->coef, p->chi, chif, p->u, p->f, p->rhs);
+                                                              p->coef, p->chi, chif, p->u, p->f, p->rhs, 0);
   fo_note_launch(1);
   FO_CU(p->ctx, cudaGetLastError());
   return FO_OK;

@@ -170,6 +170,9 @@ fo_status fo_umesh_state_apply(fo_problem *p, const double *x, double *y, bool f
 fo_status fo_umesh_velocity_apply(fo_problem *p, const double *x, double *y);
 fo_status fo_umesh_functionals(fo_problem *p, double *J, double *vol);
 fo_status fo_umesh_shape_rhs(fo_problem *p, double lambda);
+fo_status fo_umesh_shape_rhs_ex(fo_problem *p, const double *u, const double *f, double lambda, const double *w,
+                                double inv_V, int add);
+fo_status fo_umesh_functionals_on(fo_problem *p, const double *u, const double *load, double *J, double *vol);
 fo_status fo_umesh_transport_assemble(fo_problem *p, double dt, double h, int smooth);
 fo_status fo_umesh_transport_apply(fo_problem *p, int which, const double *x, double *y);
 fo_status fo_umesh_levelset_step(fo_problem *p, double t_end, int nsteps, double h, int smooth,
