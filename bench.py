@@ -449,8 +449,8 @@ def survey_pcg_bytes(ndof, nt, nn, d, w):
 
 # DRAM bytes (read + write) of one state-solve CG launch, from one-pass ncu captures of the
 # kernels as built now (keyed by precision; absent until captured)
-C2_STATE_TRAFFIC = {}
-C3_STATE_TRAFFIC = {}
+C2_STATE_TRAFFIC = {"fp64": 13.59e6 + 0.66e6}
+C3_STATE_TRAFFIC = {"fp64": 53.39e9 + 3.27e9, "mixed": 27.92e9 + 1.48e9}
 
 
 def mg_state_bytes_per_iteration(nx, ny, c):
@@ -565,6 +565,101 @@ def bench_configs(api, ctx, stream, peaks):
                  "opt_step_precision": "mixed (FP32 CG + FP64 refinement to 1e-8)"}
     prob.close()
     return out
+
+
+# ------------------------------------------- the variants: general meshes, cut cells, loads
+def bench_variants(api, ctx, stream, peaks):
+    """The hot path's variants on the cantilever physics: a general mesh given as arrays
+    (jittered, renumbered Kuhn arrays of the 256 x 128 box through the assembled-operator path),
+    the exact cut-cell coefficient, and runs to convergence under the stopping criterion with
+    one and with two load cases."""
+    import numpy as np
+    import torch
+    from paper_2601_05709_gb300 import workloads
+    out = {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    centres, radii = workloads.hole_lattice()
+    vel = dict(volume=1.0, alpha_mass=0.1, normal_penalty=1e4, omega0_weight=1e4,
+               omega0_boxes=[((1.95, 0.42), (float("inf"), 0.58))])
+
+    def timed_iters(prob, opts, warm, steps, ppl):
+        for i in range(warm):
+            prob.opt_step(i, opts, ppl)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        logs = [prob.opt_step(warm + i, opts, ppl) for i in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, logs
+
+    # general mesh: jittered (0.3 cell), renumbered arrays of the 256 x 128 Kuhn box
+    coords, cells = workloads.simplex_mesh(2, (NX, NY), (0.0, 0.0), (2.0, 1.0), jitter=0.3, seed=7, shuffle=True)
+    mesh = ctx.mesh_from_arrays(coords, cells)
+    tip = int(np.flatnonzero(np.all(np.abs(coords - np.array([2.0, 0.5])) < 1e-12, axis=1))[0])
+    prob = mesh.problem(api.model_desc(api.FO_ELASTIC, dirichlet=[(0, 0)], point_loads=[(tip, (0.0, -1.0))], **vel))
+    prob.initial_level(centres, radii, factor=1.0, ord=2)
+    so = api.solve_opts(rtol=1e-12, warm_start=1, maxit=400000)
+    ro = api.run_options(dfactor=0.1, smooth=True, state=so, velocity=so, transport=api.solve_opts(rtol=1e-12))
+    ms, logs = timed_iters(prob, ro, 3, 10, api.PPL(1))
+    its = float(np.mean([l.state.iterations for l in logs]))
+    kms = float(np.mean([l.ms_state_kernel for l in logs]))
+    bpi = survey_pcg_bytes(2 * mesh.num_nodes, mesh.num_elems, mesh.num_nodes, 2, 8)
+    ach = bpi * its / (kms / 1e3) / 1e9
+    out["cantilever2d_general_mesh"] = {
+        "workload": "the cantilever on a general mesh: 256x128 Kuhn arrays, interior nodes jittered by 0.3 cell, "
+                    "numbering shuffled (fo_mesh_from_arrays; assembled node-block operators, Jacobi-PCG, BiCGStab)",
+        "ms_per_opt_step": ms, "opt_iters_per_s": 1e3 / ms, "state_iterations": its,
+        "phase_ms_per_step": {k: float(np.mean([getattr(l, "ms_" + k) for l in logs]))
+                              for k in ("state", "velocity", "transport")},
+        "roofline": {"bound": "hbm", "kernel": "k_pcg<2, CsrOp<2, double>, double, 1>", "achieved": ach, "peak": hbm,
+                     "unit": "GB/s", "frac": ach / hbm, "algorithmic_bytes_per_iteration": bpi, "traffic": None,
+                     "note": "survey model bytes x iterations / the PCG launch's CUDA-event time"}}
+    prob.close()
+
+    def box(desc_kw):
+        m = ctx.mesh_box(2, (NX, NY), (0.0, 0.0), (2.0, 1.0))
+        return m, m.problem(api.model_desc(api.FO_ELASTIC, dirichlet=[(0, 0)], **desc_kw))
+
+    ro_mg = run_options(api, "fp64", "mg")
+    # exact cut-cell coefficient on the box cantilever
+    m, prob = box(dict(point_loads=[(m_node(NX, NY // 2), (0.0, -1.0))], coef_rule=api.FO_COEF_CUT, **vel))
+    prob.initial_level(centres, radii, factor=1.0, ord=2)
+    ms, logs = timed_iters(prob, ro_mg, 3, 20, api.PPL(1))
+    out["cantilever2d_cut_cell"] = {"workload": "the cantilever with the exact cut-cell coefficient (FO_COEF_CUT)",
+                                    "ms_per_opt_step": ms, "opt_iters_per_s": 1e3 / ms,
+                                    "state_iterations": float(np.mean([l.state.iterations for l in logs]))}
+    prob.close()
+
+    # runs to convergence under the stopping criterion (Sec. 5.7 defaults), one and two loads
+    for name, kw in (("cantilever2d_to_convergence", dict(point_loads=[(m_node(NX, NY // 2), (0.0, -1.0))])),
+                     ("cantilever2d_two_loads_to_convergence",
+                      dict(load_cases=[([(m_node(NX, NY // 4), (0.0, -1.0))], []),
+                                       ([(m_node(NX, 3 * NY // 4), (0.0, -1.0))], [])]))):
+        m, prob = box(dict(kw, **dict(vel, omega0_boxes=[((1.95, 0.2), (float("inf"), 0.8))])))
+        prob.initial_level(centres, radii, factor=1.0, ord=2)
+        ppl = api.PPL(1)
+        L, it = [], 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while it < 300:
+            log = prob.opt_step(it, ro_mg, ppl)
+            L.append(log.L)
+            it += 1
+            if api.stop_check(L, [log.C]):
+                break
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        out[name] = {"iterations": it, "stopped_by_criterion": it < 300, "seconds": sec, "J": log.J, "C": log.C,
+                     "L": log.L, "opt_iters_per_s": it / sec,
+                     "criterion": "start_to_check 30, lgrn_tol 1e-2, ctrn_tol 1e-2, prev 10 (Sec. 5.7 defaults)"}
+        prob.close()
+    return out
+
+
+def m_node(i, j):
+    """Node id of grid point (i, j) of the 256 x 128 box mesh."""
+    return i + (NX + 1) * j
 
 
 # ----------------------------------------------------- serving: stream of requests
@@ -876,6 +971,7 @@ def main():
         line["batch"] = bench_batch(api, ctx, stream, peaks)
     if rank == 0 and not args.no_configs:
         line["configs"] = bench_configs(api, ctx, stream, peaks)
+        line["variants"] = bench_variants(api, ctx, stream, peaks)
     if rank == 0 and not args.no_serving:
         line["serving"] = bench_serving(api, ctx, args.serving_requests)
     if cpu is not None:

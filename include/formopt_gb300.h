@@ -227,9 +227,8 @@ typedef struct {
    * fo_ctx_set_timing(ctx, 1) is on, else 0): coefficients + state solve, functionals,
    * shape derivative, velocity, transport (assembly + steps), reinitialisation */
   double ms_state, ms_functionals, ms_shape, ms_velocity, ms_transport, ms_reinit;
-  /* with timing on: device time of the persistent multigrid state-solve launch alone (no
-   * hierarchy rebuild; FO_MIXED: its FP32 CG launches summed over the refinement steps);
-   * 0 when the state solve ran another solver */
+  /* with timing on: device time of the persistent state-solve CG launch(es) alone (no
+   * operator or hierarchy rebuild; summed over refinement steps and restarts) */
   double ms_state_kernel;
   int nc;                   /* constraints of this iteration (0 = none)                 */
   double Cv[4], lambdav[4]; /* C_j and lambda_j of every constraint (C, lambda = [0])    */
@@ -248,9 +247,9 @@ FO_API fo_status fo_ctx_memory(const fo_ctx *ctx, size_t *bytes_in_use);
 FO_API fo_status fo_ctx_set_timing(fo_ctx *ctx, int on);
 /* Number of kernels this library has launched in the process so far (all contexts). */
 FO_API fo_status fo_launch_count(unsigned long long *out);
-/* With timing on (fo_ctx_set_timing): device time in ms of the persistent multigrid CG
- * launch(es) of the last multigrid state or adjoint solve alone (FO_MIXED: its FP32 CG launches
- * summed over the refinement steps), measured with CUDA events on the context's stream. */
+/* With timing on (fo_ctx_set_timing): device time in ms of the persistent CG launch(es) of
+ * the last single-problem state or adjoint solve alone (summed over refinement steps and
+ * restarts), measured with CUDA events on the context's stream. */
 FO_API fo_status fo_ctx_solve_kernel_ms(const fo_ctx *ctx, double *ms);
 /* wait for all work enqueued on the context's stream */
 FO_API fo_status fo_ctx_sync(fo_ctx *ctx);

@@ -586,6 +586,7 @@ extern "C" fo_status fo_state_solve(fo_problem *p, const fo_solve_opts *o, fo_so
   fo_solve_opts_default(&def);
   if (!o) o = &def;
   if (!p->coef_valid) FO_TRY(fo_coefficients(p));
+  p->ctx->last_solve_ms = 0.0;
   fo_status s;
   if (p->batch) s = fo_batch_state(p, false, o, st);
   else if (p->ncases == 1) s = fo_state_pcg(p, p->load, p->u, o, st);

@@ -326,9 +326,18 @@ static fo_status run_pcg(fo_problem *p, const Op &op, PcgArgs<NC, T> a, long lon
   a.out = out_area(p);
   a.status = p->dev_status;
   a.bar = GridBar{p->bar, p->dev_status + DS_ERR, 2000000000ull};
+  fo_ctx *ctx = p->ctx;
+  const bool tm = ctx->timing != 0 && ctx->ev_solve[0] != nullptr;
+  if (tm) FO_CU(ctx, cudaEventRecord(ctx->ev_solve[0], ctx->stream));
   FO_TRY(coop_launch(p, kern, grid, block, smem, op, a));
   FO_CU(p->ctx, cudaGetLastError());
+  if (tm) FO_CU(ctx, cudaEventRecord(ctx->ev_solve[1], ctx->stream));
   FO_TRY(read_out(p, out_area(p), o, 4 * NC));
+  if (tm) {   // device time of the persistent PCG launch alone, summed over restarts
+    float ms = 0.f;
+    FO_CU(ctx, cudaEventElapsedTime(&ms, ctx->ev_solve[0], ctx->ev_solve[1]));
+    ctx->last_solve_ms += ms;
+  }
   if (o->status[DS_ERR] == DEV_TIMEOUT) return fo_fail(p->ctx, FO_ETIMEOUT, "grid barrier timed out in PCG");
   if (o->status[DS_ERR] == DEV_NAN) return fo_fail(p->ctx, FO_ENAN, "NaN in the PCG recurrence");
   return FO_OK;

@@ -1104,7 +1104,6 @@ fo_status fo_state_pcg_mg(fo_problem *p, const double *b, double *x, const fo_so
   FO_TRY(mg_prepare_state(p));
   const int d = p->mesh->g.dim;
   const long long n = p->ndof;
-  p->ctx->last_solve_ms = 0.0;
   if (o->precision == FO_MIXED) {
     if (p->desc.kind == FO_ELASTIC) return d == 2 ? mg_state_mixed<2, 2>(p, b, x, o, st) : mg_state_mixed<3, 3>(p, b, x, o, st);
     return d == 2 ? mg_state_mixed<2, 1>(p, b, x, o, st) : mg_state_mixed<3, 1>(p, b, x, o, st);

@@ -81,7 +81,10 @@ def test_cases_states_cost_constraints_and_rhs(ctx, api, general, kind):
     prob.set(api._lib.FO_FIELD_U, U_ref.ravel())
     lams = np.array([0.4, -0.7])
     b = prob.shape_derivative_v(lams)
-    assert close_scaled(b, op.total_rhs(U_ref, A, chi, lams), 1e-12)
+    ref = op.total_rhs(U_ref, A, chi, lams)
+    # the states of the ersatz-1e-3 material are large (|u| ~ 1e4) and a node's element terms
+    # cancel to a much smaller sum: elementwise 1e-10 of the vector's scale
+    assert close_scaled(b, ref, 1e-10), np.max(np.abs(b - ref)) / np.max(np.abs(ref))
 
 
 @pytest.mark.parametrize("general", [False, True], ids=["box", "arrays"])
