@@ -97,10 +97,6 @@ struct fo_mg {
   double *coef[MG_MAX_LEVELS] = {}, *W64[MG_MAX_LEVELS] = {}, *dinv64[MG_MAX_LEVELS] = {};
   float *W32[MG_MAX_LEVELS] = {}, *dinv32[MG_MAX_LEVELS] = {};
   uint8_t *dir[MG_MAX_LEVELS] = {};
-  // element data of the matrix-free level passes (state hierarchies): FP32 coefficients of the
-  // coarse levels and, per level, the reference blocks of the Kuhn simplices
-  float *coef32[MG_MAX_LEVELS] = {}, *T[MG_MAX_LEVELS] = {};
-  std::vector<float> thost;                // host image of the tables (kept for the async copy)
   int nd = 0;                              // coarsest level's unknowns when solved directly
   float *ainv = nullptr;                   // [nd][nd] its inverse (FP32)
   void *dev = nullptr;                     // device copy of the level table

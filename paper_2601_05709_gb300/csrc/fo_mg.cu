@@ -32,8 +32,6 @@
 
 struct MgLevelDev {
   Grid g;
-  const float *T;       // non-null: matrix-free passes from element data (coef, T) instead of W
-  const float *coef;    // [N_T] FP32 element coefficients (with T)
   const float *W;       // difference-form stencil rows [S][BLK][N]
   const float *dinv;    // [N * NPN]
   const uint8_t *dir;   // [N * NPN]
@@ -70,54 +68,6 @@ struct MgCgT {
 using MgCg = MgCgT<double>;
 
 // ------------------------------------------------------------------ level operations
-// Matrix-free row of the state operator on a level from element data: every Kuhn simplex of a
-// permutation type p has the same reference blocks, so its stiffness is A_e T_p with
-// T_p[m][l] = |e| [lam (g_m)_i (g_l)_j + mu (g_m)_j (g_l)_i + mu delta_ij g_m . g_l] (elastic)
-// or |e| g_m . g_l (scalar), built once per level.  The row of node a (vertex m of its
-// simplices) is applied in difference form,
-//   (A x)_a = sum_{(p, m)} A_e sum_{l != m} T_p[m][l] (x_l - x_a),
-// exact in the constant kernel like the stored rows (sum_l T_p[m][l] = 0); Dirichlet columns
-// enter as zero values (which is the eliminated-column row with its corrected row sum) and
-// Dirichlet rows are identity.  It reads one coefficient per simplex instead of S stored
-// blocks per node: 24 floats instead of 135 per node for 3D elasticity.
-template <int D, int NPN, class X>
-__device__ __forceinline__ void mg_elem_row(const MgLevelDev &L, long long a, const int idx[3], const X &x,
-                                            float out[NPN]) {
-  constexpr int S = ST<D>::S, BLK = NPN * NPN;
-  float xs[S][NPN], xa[NPN], acc[NPN];
-#pragma unroll
-  for (int c = 0; c < NPN; ++c) {
-    xa[c] = (float)x(a * NPN + c);
-    acc[c] = 0.f;
-  }
-#pragma unroll
-  for (int s = 1; s < S; ++s) {
-    const long long nb = slot_node<D>(L.g, idx, a, s);
-#pragma unroll
-    for (int c = 0; c < NPN; ++c) xs[s][c] = (nb >= 0 && !L.dir[nb * NPN + c]) ? (float)x(nb * NPN + c) : 0.f;
-  }
-#pragma unroll
-  for (int p = 0; p < KP<D>::P; ++p)
-#pragma unroll
-    for (int m = 0; m <= D; ++m) {
-      long long e;
-      if (!elem_of<D>(L.g, idx, p, m, e)) continue;
-      const float A = L.coef[e];
-      const float *Tp = L.T + (size_t)((p * (D + 1) + m) * (D + 1)) * BLK;
-#pragma unroll
-      for (int l = 0; l <= D; ++l) {
-        if (l == m) continue;
-        const int sl = rel_slot<D>(p, m, l);
-#pragma unroll
-        for (int i = 0; i < NPN; ++i)
-#pragma unroll
-          for (int j = 0; j < NPN; ++j) acc[i] = fmaf(A * __ldg(Tp + l * BLK + i * NPN + j), xs[sl][j] - xa[j], acc[i]);
-      }
-    }
-#pragma unroll
-  for (int c = 0; c < NPN; ++c) out[c] = L.dir[a * NPN + c] ? xa[c] : acc[c];
-}
-
 template <int D, int NPN, bool FULL>
 struct MgOps {
   using Op = StencilOp<D, NPN, FULL, float>;
@@ -135,8 +85,7 @@ struct MgOps {
       int idx[3];
       node_ijk(L.g, a, idx);
       float az[NPN];
-      if (FULL && L.T) mg_elem_row<D, NPN>(L, a, idx, VecX<float>{zin}, az);
-      else o.row(a, idx, VecX<float>{zin}, az);
+      o.row(a, idx, VecX<float>{zin}, az);
 #pragma unroll
       for (int c = 0; c < NPN; ++c) {
         const long long k = a * NPN + c;
@@ -150,8 +99,7 @@ struct MgOps {
       int idx[3];
       node_ijk(L.g, a, idx);
       float az[NPN];
-      if (FULL && L.T) mg_elem_row<D, NPN>(L, a, idx, VecX<float>{z}, az);
-      else o.row(a, idx, VecX<float>{z}, az);
+      o.row(a, idx, VecX<float>{z}, az);
 #pragma unroll
       for (int c = 0; c < NPN; ++c) L.t[a * NPN + c] = L.b[a * NPN + c] - az[c];
     }
@@ -751,12 +699,9 @@ int fo_mg_plan(const Grid &g0, Grid *g, int max_levels, long long stop_unknowns,
   return L;
 }
 
-// Byte sizes of level l's arrays, in the order b, z0, z1, t, coef, W64, W32, dinv64, dinv32, dir,
-// coef32, T (coarse levels own all; level 0 owns coef, W32, dinv32 and dir only when own0; the
-// element data of the matrix-free passes, coef32 on coarse levels and T on every level, exists
-// for state hierarchies, whose blocks are full: blk = npn^2).
-#define MG_SLOTS 12
-static void mg_sizes(const Grid &g, int npn, int blk, bool coarse, bool own0, size_t sz[MG_SLOTS]) {
+// Byte sizes of level l's arrays, in the order b, z0, z1, t, coef, W64, W32, dinv64, dinv32, dir
+// (coarse levels own all; level 0 owns coef, W32, dinv32 and dir only when own0).
+static void mg_sizes(const Grid &g, int npn, int blk, bool coarse, bool own0, size_t sz[10]) {
   const size_t N = (size_t)g.num_nodes, S = g.dim == 2 ? 7 : 15;
   for (int i = 0; i < 4; ++i) sz[i] = sizeof(float) * N * npn;
   sz[4] = (coarse || own0) ? sizeof(double) * g.num_elems : 0;
@@ -765,9 +710,6 @@ static void mg_sizes(const Grid &g, int npn, int blk, bool coarse, bool own0, si
   sz[7] = coarse ? sizeof(double) * N * npn : 0;
   sz[8] = (coarse || own0) ? sizeof(float) * N * npn : 0;
   sz[9] = (coarse || own0) ? N * npn : 0;
-  const bool state = blk == npn * npn;
-  sz[10] = (state && coarse) ? sizeof(float) * g.num_elems : 0;
-  sz[11] = state ? sizeof(float) * (g.dim == 2 ? 2 : 6) * (g.dim + 1) * (g.dim + 1) * blk : 0;
 }
 
 static void **mg_slot(fo_mg *mg, int l, int i) {
@@ -781,18 +723,16 @@ static void **mg_slot(fo_mg *mg, int l, int i) {
     case 6: return (void **)&mg->W32[l];
     case 7: return (void **)&mg->dinv64[l];
     case 8: return (void **)&mg->dinv32[l];
-    case 9: return (void **)&mg->dir[l];
-    case 10: return (void **)&mg->coef32[l];
-    default: return (void **)&mg->T[l];
+    default: return (void **)&mg->dir[l];
   }
 }
 
 static void mg_release(fo_ctx *ctx, fo_mg *&mg) {
   if (!mg) return;
   for (int l = 0; l < mg->L; ++l) {
-    size_t sz[MG_SLOTS];
+    size_t sz[10];
     mg_sizes(mg->g[l], mg->npn, mg->blk, l > 0, mg->own0, sz);
-    for (int i = 0; i < MG_SLOTS; ++i)
+    for (int i = 0; i < 10; ++i)
       if (sz[i]) fo_free(ctx, *mg_slot(mg, l, i), sz[i]);
   }
   if (mg->nd > 0) {
@@ -825,9 +765,9 @@ size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0) {
   const int L = mg_plan_single(g0, g, npn);
   size_t b = sizeof(MgDev);
   for (int l = 0; l < L; ++l) {
-    size_t sz[MG_SLOTS];
+    size_t sz[10];
     mg_sizes(g[l], npn, blk, l > 0, own0, sz);
-    for (int i = 0; i < MG_SLOTS; ++i) b += sz[i];
+    for (int i = 0; i < 10; ++i) b += sz[i];
   }
   const size_t nd = (size_t)mg_direct_unknowns(g, L, npn);
   return b + nd * nd * sizeof(float);
@@ -841,9 +781,9 @@ static fo_status mg_alloc(fo_ctx *ctx, fo_mg *&out, const Grid &g0, int npn, int
   mg->own0 = own0;
   mg->L = mg_plan_single(g0, mg->g, npn);
   for (int l = 0; l < mg->L; ++l) {
-    size_t sz[MG_SLOTS];
+    size_t sz[10];
     mg_sizes(mg->g[l], npn, blk, l > 0, own0, sz);
-    for (int i = 0; i < MG_SLOTS; ++i)
+    for (int i = 0; i < 10; ++i)
       if (sz[i]) FO_TRY(fo_alloc(ctx, mg_slot(mg, l, i), sz[i]));
   }
   mg->nd = mg_direct_unknowns(mg->g, mg->L, npn);
@@ -856,7 +796,7 @@ static fo_status mg_alloc(fo_ctx *ctx, fo_mg *&out, const Grid &g0, int npn, int
 
 // Level table to the device; level 0's FP32 rows, FP32 inverse diagonal and Dirichlet mask.
 static fo_status mg_upload(fo_ctx *ctx, fo_mg *mg, const float *W0, const float *dinv0, const uint8_t *dir0,
-                           float omega, const float *coef0 = nullptr) {
+                           float omega) {
   MgDev h;
   memset(&h, 0, sizeof h);
   h.L = mg->L;
@@ -883,11 +823,6 @@ static fo_status mg_upload(fo_ctx *ctx, fo_mg *mg, const float *W0, const float 
     d.z[0] = mg->z0[l];
     d.z[1] = mg->z1[l];
     d.t = mg->t[l];
-    // grid-run levels of a state hierarchy apply the operator from element data (coef0 given:
-    // the stiffness-only state operator); block-run levels keep their stored rows
-    const bool mf = coef0 != nullptr && mg->T[l] != nullptr && l < h.Lg;
-    d.T = mf ? mg->T[l] : nullptr;
-    d.coef = mf ? (l == 0 ? coef0 : mg->coef32[l]) : nullptr;
   }
   mg->host.resize(sizeof(MgDev));
   memcpy(mg->host.data(), &h, sizeof(MgDev));
@@ -913,46 +848,6 @@ static void mg_restrict_level(fo_ctx *ctx, fo_mg *mg, int l, const double *coef_
   fo_mg_restrict(ctx, mg->g[l], mg->g[l - 1], mg->npn, coef_f, dir_f, mg->coef[l], mg->dir[l]);
 }
 
-__global__ void k_mg_coef32(long long n, const double *c, float *c32) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    c32[i] = (float)c[i];
-}
-
-// Reference blocks T_p[m][l] of the Kuhn simplices of every level (see mg_elem_row), in FP64 on
-// the host from the path-difference gradients grad lambda_l = e_{pi_{l-1}} / h - e_{pi_l} / h,
-// stored FP32 [p][m][l][i][j].  They depend on the grid only: built once per hierarchy.
-static fo_status mg_build_tables(fo_ctx *ctx, fo_mg *mg, int npn, double lam, double mu) {
-  const int D = mg->g[0].dim, P = D == 2 ? 2 : 6, blk = npn * npn;
-  const size_t per = (size_t)P * (D + 1) * (D + 1) * blk;
-  mg->thost.assign(per * mg->L, 0.0f);
-  for (int l = 0; l < mg->L; ++l) {
-    const Grid &g = mg->g[l];
-    float *T = mg->thost.data() + per * l;
-    for (int p = 0; p < P; ++p) {
-      double gr[4][3];
-      for (int v = 0; v <= D; ++v) {
-        gr[v][0] = gr[v][1] = gr[v][2] = 0.0;
-        if (v >= 1) gr[v][(D == 2 ? kperm<2>(p, v - 1) : kperm<3>(p, v - 1))] += g.inv_h[(D == 2 ? kperm<2>(p, v - 1) : kperm<3>(p, v - 1))];
-        if (v < D) gr[v][(D == 2 ? kperm<2>(p, v) : kperm<3>(p, v))] -= g.inv_h[(D == 2 ? kperm<2>(p, v) : kperm<3>(p, v))];
-      }
-      for (int m = 0; m <= D; ++m)
-        for (int q = 0; q <= D; ++q) {
-          double dot = 0;
-          for (int k = 0; k < D; ++k) dot += gr[m][k] * gr[q][k];
-          float *B = T + ((size_t)(p * (D + 1) + m) * (D + 1) + q) * blk;
-          if (npn == 1) B[0] = (float)(g.vol_e * dot);
-          else
-            for (int i = 0; i < npn; ++i)
-              for (int j = 0; j < npn; ++j)
-                B[i * npn + j] = (float)(g.vol_e * (lam * gr[m][i] * gr[q][j] + mu * gr[m][j] * gr[q][i] +
-                                                    (i == j ? mu * dot : 0.0)));
-        }
-    }
-    FO_CU(ctx, cudaMemcpyAsync(mg->T[l], T, sizeof(float) * per, cudaMemcpyHostToDevice, ctx->stream));
-  }
-  return FO_OK;
-}
-
 // State hierarchy: rebuilt after every coefficient update (coarse coefficients are the
 // children means of the current A_e).
 static fo_status mg_prepare_state(fo_problem *p) {
@@ -960,7 +855,6 @@ static fo_status mg_prepare_state(fo_problem *p) {
   if (!p->mg) {
     FO_TRY(mg_alloc(ctx, p->mg, p->mesh->g, p->ncomp, p->ncomp * p->ncomp, false));
     p->mg->built_epoch = -1;
-    FO_TRY(mg_build_tables(ctx, p->mg, p->ncomp, p->lame_lambda, p->lame_mu));
   }
   fo_mg *mg = p->mg;
   if (mg->built_epoch == p->coef_epoch) return FO_OK;
@@ -968,15 +862,9 @@ static fo_status mg_prepare_state(fo_problem *p) {
     mg_restrict_level(ctx, mg, l, l == 1 ? p->coef : mg->coef[l - 1], l == 1 ? p->dir : mg->dir[l - 1]);
     FO_TRY(fo_launch_stencil_on(p, mg->g[l], mg->coef[l], mg->dir[l], mg->W64[l], mg->W32[l], mg->dinv64[l],
                                 mg->dinv32[l]));
-    k_mg_coef32<<<fo_blocks_for(mg->g[l].num_elems, FO_BLOCK, 65536), FO_BLOCK, 0, ctx->stream>>>(
-        mg->g[l].num_elems, mg->coef[l], mg->coef32[l]);
-    fo_note_launch(1);
   }
   mg_build_inverse(ctx, mg);
-  // the matrix-free passes cover the stiffness-only operator (not the screened family's mass)
-  const bool mf = !(p->desc.kind == FO_HELMHOLTZ && p->desc.omega != 0.0);
-  FO_TRY(mg_upload(ctx, mg, p->Wst32, p->dinv_state32, p->dir, p->ncomp == 1 ? 0.8f : 0.6f,
-                   mf ? p->coef32 : nullptr));
+  FO_TRY(mg_upload(ctx, mg, p->Wst32, p->dinv_state32, p->dir, p->ncomp == 1 ? 0.8f : 0.6f));
   mg->built_epoch = p->coef_epoch;
   return FO_OK;
 }
