@@ -1195,7 +1195,7 @@ extern "C" fo_status fo_batch_autotune(fo_problem *p, int precision, fo_tune_res
 fo_status fo_batch_state(fo_problem *p, bool adjoint, const fo_solve_opts *o, fo_solve_stats *st) {
   fo_batch *bt = p->batch;
   double *X = adjoint ? bt->P : bt->U;
-  if (o->precond == FO_PC_MG && fo_mg_applicable(p->mesh->g, 1))
+  if (o->precond == FO_PC_MG && fo_mg_applicable(p->mesh->g, 1, false))
     return fo_batch_state_mg(p, bt->B, adjoint ? -1.0 : 1.0, X, o, adjoint ? 0 : o->warm_start, st);
   const int prec = o->precision == FO_MIXED ? FO_MIXED : FO_FP64;
   if (o->grid_blocks <= 0 && bt->tuned_block[prec == FO_MIXED ? 1 : 0] == 0) FO_TRY(fo_batch_autotune(p, prec, nullptr));

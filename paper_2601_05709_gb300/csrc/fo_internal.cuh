@@ -515,8 +515,8 @@ fo_status fo_batch_apply(fo_problem *p, const double *x, double *y, bool fp32);
 fo_status fo_state_pcg_mg(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st);
 void fo_mg_destroy(fo_problem *p);
 size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0);
-bool fo_mg_applicable(const Grid &g0, int npn);
-int fo_mg_plan(const Grid &g0, Grid *g, int max_levels, long long stop_unknowns = 0, int npn = 1);
+bool fo_mg_applicable(const Grid &g0, int npn, bool general = true);
+int fo_mg_plan(const Grid &g0, Grid *g, int max_levels, long long stop_unknowns = 0, int npn = 1, bool general = false);
 void fo_mg_restrict(fo_ctx *ctx, const Grid &gc, const Grid &gf, int npn, const double *coef_f, const uint8_t *dir_f,
                     double *coef_c, uint8_t *dir_c);
 // batched multigrid (fo_batch_mg.cu) and the batch stencil builder it shares (fo_batch.cu)

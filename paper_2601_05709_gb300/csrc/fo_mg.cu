@@ -68,6 +68,57 @@ struct MgCgT {
 using MgCg = MgCgT<double>;
 
 // ------------------------------------------------------------------ level operations
+// Level pairs: a coarse grid either halves every axis of the fine one (nested: the existing
+// Kuhn refinement relation) or, where an axis does not halve, has ceil(n/2) cells per axis over
+// the same box (non-nested).  Then P is P1 interpolation of the coarse field at the fine nodes:
+// a fine node at coarse coordinate s = i n_c / n_f per axis lies in coarse cell floor(s) with
+// local coordinates t = frac(s) (exact in integers: the remainder of i n_c / n_f), in the Kuhn
+// simplex whose axis order sorts t descending (ties by axis index), with barycentric weights
+// 1 - t_(0), t_(0) - t_(1), ..., t_(d-1) on the path vertices; R = P^T.
+__host__ __device__ __forceinline__ bool mg_nested(const Grid &F, const Grid &C) {
+  for (int k = 0; k < F.dim; ++k)
+    if (F.n[k] != 2 * C.n[k]) return false;
+  return true;
+}
+
+template <int D>
+__device__ __forceinline__ void mg_interp(const Grid &F, const Grid &C, const int ifn[3], long long vert[D + 1],
+                                          float w[D + 1]) {
+  int cc[3] = {0, 0, 0}, ax[3] = {0, 1, 2};
+  long long rem[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const long long num = (long long)ifn[k] * C.n[k];
+    cc[k] = (int)(num / F.n[k]);
+    rem[k] = num % F.n[k];
+  }
+  // axes by t_k = rem_k / n_f,k descending (cross-multiplied: exact), ties by axis index
+#pragma unroll
+  for (int i = 1; i < D; ++i)
+    for (int j = i; j > 0; --j) {
+      const int a = ax[j], b = ax[j - 1];
+      if (rem[a] * F.n[b] > rem[b] * F.n[a]) {
+        ax[j] = b;
+        ax[j - 1] = a;
+      } else {
+        break;
+      }
+    }
+  double t[3];
+#pragma unroll
+  for (int m = 0; m < D; ++m) t[m] = (double)rem[ax[m]] / (double)F.n[ax[m]];
+  long long v = cc[0] + C.stride[1] * cc[1] + (D == 3 ? C.stride[2] * cc[2] : 0);
+  vert[0] = v;
+  w[0] = (float)(1.0 - t[0]);
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    const double wm = (m + 1 < D) ? t[m] - t[m + 1] : t[m];
+    v += C.stride[ax[m]];
+    vert[m + 1] = wm > 0.0 ? v : -1;   // a zero weight may point past the grid
+    w[m + 1] = (float)wm;
+  }
+}
+
 template <int D, int NPN, bool FULL>
 struct MgOps {
   using Op = StencilOp<D, NPN, FULL, float>;
@@ -107,6 +158,47 @@ struct MgOps {
   // coarse b = P^T t (fine residual), and the coarse level's first sweep from zero
   static __device__ void restrict_(const MgLevelDev &F, const MgLevelDev &C, float omega, long long first,
                                    long long step) {
+    if (!mg_nested(F.g, C.g)) {   // gather over the fine nodes whose interpolation uses c
+      for (long long c = first; c < C.g.num_nodes; c += step) {
+        int ic[3];
+        node_ijk(C.g, c, ic);
+        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const long long nf = F.g.n[k], ncs = C.g.n[k];
+          // the coarse hat of c lives on coarse coordinates (c - 1, c + 1) along each axis
+          lo[k] = ic[k] == 0 ? 0 : (int)(((long long)(ic[k] - 1) * nf + ncs - 1) / ncs);
+          hi[k] = (int)std::min(nf, ((long long)(ic[k] + 1) * nf) / ncs);
+        }
+        float v[NPN];
+#pragma unroll
+        for (int j = 0; j < NPN; ++j) v[j] = 0.f;
+        for (int i2 = lo[2]; i2 <= (D == 3 ? hi[2] : 0); ++i2)
+          for (int i1 = lo[1]; i1 <= hi[1]; ++i1)
+            for (int i0 = lo[0]; i0 <= hi[0]; ++i0) {
+              const int ifn[3] = {i0, i1, i2};
+              long long vert[D + 1];
+              float w[D + 1];
+              mg_interp<D>(F.g, C.g, ifn, vert, w);
+              float wc = 0.f;
+#pragma unroll
+              for (int m = 0; m <= D; ++m)
+                if (vert[m] == c) wc = w[m];
+              if (wc == 0.f) continue;
+              const long long f = i0 + F.g.stride[1] * i1 + (D == 3 ? F.g.stride[2] * i2 : 0);
+#pragma unroll
+              for (int j = 0; j < NPN; ++j) v[j] = fmaf(wc, F.t[f * NPN + j], v[j]);
+            }
+#pragma unroll
+        for (int j = 0; j < NPN; ++j) {
+          const long long k = c * NPN + j;
+          const float bk = C.dir[k] ? 0.f : v[j];
+          C.b[k] = bk;
+          C.z[0][k] = omega * C.dinv[k] * bk;
+        }
+      }
+      return;
+    }
     for (long long c = first; c < C.g.num_nodes; c += step) {
       int ic[3];
       node_ijk(C.g, c, ic);
@@ -134,6 +226,26 @@ struct MgOps {
   // fine z += P (coarse z)
   static __device__ void prolong(const MgLevelDev &F, float *zf, const MgLevelDev &C, const float *zc,
                                  long long first, long long step) {
+    if (!mg_nested(F.g, C.g)) {
+      for (long long a = first; a < F.g.num_nodes; a += step) {
+        int idx[3];
+        node_ijk(F.g, a, idx);
+        long long vert[D + 1];
+        float w[D + 1];
+        mg_interp<D>(F.g, C.g, idx, vert, w);
+#pragma unroll
+        for (int j = 0; j < NPN; ++j) {
+          const long long k = a * NPN + j;
+          if (F.dir[k]) continue;
+          float v = 0.f;
+#pragma unroll
+          for (int m = 0; m <= D; ++m)
+            if (vert[m] >= 0) v = fmaf(w[m], zc[vert[m] * NPN + j], v);
+          zf[k] += v;
+        }
+      }
+      return;
+    }
     for (long long a = first; a < F.g.num_nodes; a += step) {
       int idx[3];
       node_ijk(F.g, a, idx);
@@ -578,6 +690,105 @@ __global__ void k_mg_restrict_coef(Grid gc, Grid gf, const double *coef_f, doubl
   }
 }
 
+// Non-nested pair: the coarse element's coefficient is the mean over the fine elements whose
+// centroid lies in it (in integer coordinates: exact), or, should none, the coefficient of the
+// fine element holding the coarse element's centroid.  A Kuhn simplex's centroid has local
+// coordinate (D - j) / (D + 1) along axis pi_j.
+template <int D>
+__device__ __forceinline__ int mg_simplex_of(const long long rem[3], const long long den[3]) {
+  int ax[3] = {0, 1, 2};
+  for (int i = 1; i < D; ++i)
+    for (int j = i; j > 0; --j) {
+      const int a = ax[j], b = ax[j - 1];
+      if (rem[a] * den[b] > rem[b] * den[a]) {
+        ax[j] = b;
+        ax[j - 1] = a;
+      } else {
+        break;
+      }
+    }
+  for (int cand = 0; cand < KP<D>::P; ++cand) {
+    bool same = true;
+    for (int l = 0; l < D; ++l) same = same && kperm<D>(cand, l) == ax[l];
+    if (same) return cand;
+  }
+  return 0;
+}
+
+template <int D>
+__global__ void k_mg_restrict_coef_general(Grid gc, Grid gf, const double *coef_f, double *coef_c) {
+  constexpr int P = KP<D>::P;
+  for (long long ec = blockIdx.x * (long long)blockDim.x + threadIdx.x; ec < gc.num_elems;
+       ec += (long long)gridDim.x * blockDim.x) {
+    const long long cellc = ec / P;
+    const int pc = (int)(ec % P);
+    int ci[3];
+    ci[0] = (int)(cellc % gc.n[0]);
+    long long tt = cellc / gc.n[0];
+    ci[1] = (int)(tt % gc.n[1]);
+    ci[2] = (int)(tt / gc.n[1]);
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int k = 0; k < D; ++k) {
+      lo[k] = (int)(((long long)ci[k] * gf.n[k]) / gc.n[k]);
+      hi[k] = (int)std::min<long long>(gf.n[k] - 1, ((long long)(ci[k] + 1) * gf.n[k] + gc.n[k] - 1) / gc.n[k] - 1);
+    }
+    double sum = 0.0;
+    int cnt = 0;
+    for (int i2 = lo[2]; i2 <= (D == 3 ? hi[2] : 0); ++i2)
+      for (int i1 = lo[1]; i1 <= hi[1]; ++i1)
+        for (int i0 = lo[0]; i0 <= hi[0]; ++i0) {
+          const int fi[3] = {i0, i1, i2};
+          const long long fcell = i0 + gf.cstride[1] * i1 + (D == 3 ? gf.cstride[2] * i2 : 0);
+          for (int pf = 0; pf < P; ++pf) {
+            long long rem[3] = {0, 0, 0}, den[3] = {1, 1, 1};
+            bool in = true;
+            for (int j = 0; j < D; ++j) {
+              const int k = kperm<D>(pf, j);
+              const long long num = ((long long)fi[k] * (D + 1) + (D - j)) * gc.n[k];
+              den[k] = (long long)gf.n[k] * (D + 1);
+              in = in && num / den[k] == ci[k];
+              rem[k] = num % den[k];
+            }
+            if (in && mg_simplex_of<D>(rem, den) == pc) {
+              sum += coef_f[(long long)P * fcell + pf];
+              ++cnt;
+            }
+          }
+        }
+    if (cnt == 0) {   // the fine element holding the coarse centroid
+      int fi[3] = {0, 0, 0};
+      long long rem[3] = {0, 0, 0}, den[3] = {1, 1, 1};
+      for (int j = 0; j < D; ++j) {
+        const int k = kperm<D>(pc, j);
+        const long long num = ((long long)ci[k] * (D + 1) + (D - j)) * gf.n[k];
+        den[k] = (long long)gc.n[k] * (D + 1);
+        fi[k] = (int)std::min<long long>(gf.n[k] - 1, num / den[k]);
+        rem[k] = num % den[k];
+      }
+      const long long fcell = fi[0] + gf.cstride[1] * fi[1] + (D == 3 ? gf.cstride[2] * fi[2] : 0);
+      sum = coef_f[(long long)P * fcell + mg_simplex_of<D>(rem, den)];
+      cnt = 1;
+    }
+    coef_c[ec] = sum / (double)cnt;
+  }
+}
+
+// Non-nested pair: a coarse node takes the Dirichlet flags of the fine node nearest to it
+// (boundary nodes map to boundary nodes of the same faces).
+__global__ void k_mg_coarse_dir_general(Grid gc, Grid gf, int npn, const uint8_t *dir_f, uint8_t *dir_c) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < gc.num_nodes;
+       c += (long long)gridDim.x * blockDim.x) {
+    int ic[3];
+    node_ijk(gc, c, ic);
+    long long f = 0;
+    for (int k = 0; k < gc.dim; ++k) {
+      const long long i = (2LL * ic[k] * gf.n[k] + gc.n[k]) / (2LL * gc.n[k]);   // round(ic n_f / n_c)
+      f += i * gf.stride[k];
+    }
+    for (int j = 0; j < npn; ++j) dir_c[c * npn + j] = dir_f[f * npn + j];
+  }
+}
+
 __global__ void k_mg_coarse_dir(Grid gc, Grid gf, int npn, const uint8_t *dir_f, uint8_t *dir_c) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < gc.num_nodes;
        c += (long long)gridDim.x * blockDim.x) {
@@ -666,7 +877,7 @@ static void mg_build_inverse(fo_ctx *ctx, fo_mg *mg) {
 
 // The single-problem hierarchy ends at the first level small enough to be solved directly.
 static int mg_plan_single(const Grid &g0, Grid *g, int npn) {
-  return fo_mg_plan(g0, g, MG_MAX_LEVELS, MG_DIRECT_MAX, npn);
+  return fo_mg_plan(g0, g, MG_MAX_LEVELS, MG_DIRECT_MAX, npn, true);
 }
 
 static int mg_direct_unknowns(const Grid *g, int L, int npn) {
@@ -680,17 +891,19 @@ static int mg_direct_unknowns(const Grid *g, int L, int npn) {
 // Levels: halve every axis while all are even and the coarse grid keeps >= 2 cells per axis;
 // with stop_unknowns > 0, also stop at the first level of at most that many unknowns (npn per
 // node).
-int fo_mg_plan(const Grid &g0, Grid *g, int max_levels, long long stop_unknowns, int npn) {
+int fo_mg_plan(const Grid &g0, Grid *g, int max_levels, long long stop_unknowns, int npn, bool general) {
   g[0] = g0;
   int L = 1;
   while (L < max_levels) {
     const Grid &f = g[L - 1];
     if (stop_unknowns > 0 && f.num_nodes * npn <= stop_unknowns) break;
     int n[3] = {1, 1, 1};
-    bool ok = true;
+    bool ok = true, even = true;
+    for (int a = 0; a < f.dim; ++a) even = even && f.n[a] % 2 == 0 && f.n[a] / 2 >= 2;
     for (int a = 0; a < f.dim; ++a) {
-      if (f.n[a] % 2 != 0 || f.n[a] / 2 < 2) ok = false;
-      n[a] = f.n[a] / 2;
+      // halve while every axis halves; otherwise (general) ceil(n/2) cells per axis
+      n[a] = even ? f.n[a] / 2 : (f.n[a] + 1) / 2;
+      if (!even && (!general || f.n[a] < 3)) ok = false;
     }
     if (!ok) break;
     if (!fo_grid_make(f.dim, n, f.lo, f.hi, g[L])) break;
@@ -748,12 +961,14 @@ void fo_mg_destroy(fo_problem *p) {
   mg_release(p->ctx, p->mgv);
 }
 
-// Multigrid pays when the hierarchy reaches a small coarsest level; grids whose cell counts
-// are not divisible by enough powers of two (odd sizes) keep the Jacobi-preconditioned CG.
+// Multigrid pays when the hierarchy reaches a small coarsest level.  Single problems coarsen
+// any grid (non-nested levels where an axis does not halve); the batched multigrid needs nested
+// levels (general = false), so grids not divisible by enough powers of two keep its Jacobi
+// solver.
 #define MG_COARSEST_MAX_DOFS 8192
-bool fo_mg_applicable(const Grid &g0, int npn) {
+bool fo_mg_applicable(const Grid &g0, int npn, bool general) {
   Grid g[MG_MAX_LEVELS];
-  const int L = mg_plan_single(g0, g, npn);
+  const int L = fo_mg_plan(g0, g, MG_MAX_LEVELS, MG_DIRECT_MAX, npn, general);
   return L >= 2 && g[L - 1].num_nodes * npn <= MG_COARSEST_MAX_DOFS;
 }
 
@@ -837,6 +1052,14 @@ void fo_mg_restrict(fo_ctx *ctx, const Grid &gc, const Grid &gf, int npn, const 
                     double *coef_c, uint8_t *dir_c) {
   cudaStream_t s = ctx->stream;
   const int blocks = fo_blocks_for(gc.num_elems, FO_BLOCK, 65536);
+  if (!mg_nested(gf, gc)) {
+    if (gc.dim == 2) k_mg_restrict_coef_general<2><<<blocks, FO_BLOCK, 0, s>>>(gc, gf, coef_f, coef_c);
+    else k_mg_restrict_coef_general<3><<<blocks, FO_BLOCK, 0, s>>>(gc, gf, coef_f, coef_c);
+    k_mg_coarse_dir_general<<<fo_blocks_for(gc.num_nodes, FO_BLOCK, 65536), FO_BLOCK, 0, s>>>(gc, gf, npn, dir_f,
+                                                                                              dir_c);
+    fo_note_launch(2);
+    return;
+  }
   if (gc.dim == 2) k_mg_restrict_coef<2><<<blocks, FO_BLOCK, 0, s>>>(gc, gf, coef_f, coef_c);
   else k_mg_restrict_coef<3><<<blocks, FO_BLOCK, 0, s>>>(gc, gf, coef_f, coef_c);
   k_mg_coarse_dir<<<fo_blocks_for(gc.num_nodes, FO_BLOCK, 65536), FO_BLOCK, 0, s>>>(gc, gf, npn, dir_f, dir_c);

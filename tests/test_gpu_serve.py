@@ -94,7 +94,7 @@ def test_served_equals_direct_api(ctx):
                                                 (FO_HEAT, 2, 63, api.FO_FP64, api.FO_PC_MG)])
 def test_request_footprint_exact(kind, dim, n, prec, pc):
     """The estimate equals what the request allocates, multigrid hierarchies included (the
-    odd 63x63 grid cannot coarsen, so it falls back to Jacobi and holds no hierarchy)."""
+    odd 63x63 grid coarsens to non-nested levels)."""
     c2 = api.Context(0)
     phi = workloads.phi_cos(np.random.default_rng(0).random((int((n + 1) ** dim), dim)))
     rq = api.ServedRequest(dim, (n,) * dim, _desc(kind, dim), phi=phi,
