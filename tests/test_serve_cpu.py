@@ -97,4 +97,5 @@ def test_footprint_counts_multigrid_only_where_it_applies():
         r.struct.velocity.precond = pc
         return r.device_bytes()
     assert req(64, api.FO_PC_MG) > req(64, api.FO_PC_JACOBI)    # 64 halves down to a small coarsest grid
-    assert req(63, api.FO_PC_MG) == req(63, api.FO_PC_JACOBI)   # odd: no hierarchy, Jacobi fallback
+    assert req(63, api.FO_PC_MG) > req(63, api.FO_PC_JACOBI)    # odd: non-nested ceil(n/2) levels
+    assert req(2, api.FO_PC_MG) == req(2, api.FO_PC_JACOBI)     # too small to coarsen: Jacobi fallback
