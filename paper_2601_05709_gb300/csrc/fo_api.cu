@@ -33,6 +33,10 @@ fo_status fo_fail(fo_ctx *ctx, fo_status st, const char *fmt, ...) {
 
 fo_status fo_cuda_check(fo_ctx *ctx, cudaError_t e, const char *what) {
   if (e == cudaSuccess) return FO_OK;
+  // a failed call leaves its error as the host thread's last error: clear it, so that the
+  // thread's next call (another request, on the server's executors) does not report it again
+  // (a sticky error stays, as it should)
+  (void)cudaGetLastError();
   if (e == cudaErrorMemoryAllocation) return fo_fail(ctx, FO_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
   return fo_fail(ctx, FO_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }

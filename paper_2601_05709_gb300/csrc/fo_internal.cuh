@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -557,3 +558,11 @@ fo_status fo_scratch(fo_problem *p, size_t bytes, void **out);
 int fo_persistent_block(const fo_problem *p, long long n);
 fo_status fo_cooperative_grid(fo_problem *p, const void *kernel, int block, size_t smem, long long work,
                               int requested, int *grid);
+// Kernel attributes are process-wide, while the library may run one context per host thread
+// (the request server's executors).  A launch whose dynamic shared memory depends on the
+// problem (the multigrid solve's staged levels, the coarsest-level inverse) holds this lock
+// from raising the kernel's limit through its occupancy query to the launch, and limits only
+// rise (fo_smem_limit, called with the lock held): another thread can then neither lower the
+// limit below a launch's request nor change it between a grid's sizing and its launch.
+std::mutex &fo_launch_mutex();
+fo_status fo_smem_limit(fo_ctx *ctx, const void *kernel, size_t bytes);

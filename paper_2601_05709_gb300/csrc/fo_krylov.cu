@@ -19,6 +19,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <map>
 #include <mutex>
 
 #include "fo_internal.cuh"
@@ -51,6 +52,21 @@ fo_status fo_cooperative_grid(fo_problem *p, const void *kernel, int block, size
   if (want > 4096) want = 4096;
   if (want < 1) want = 1;
   *grid = (int)want;
+  return FO_OK;
+}
+
+std::mutex &fo_launch_mutex() {
+  static std::mutex m;
+  return m;
+}
+
+fo_status fo_smem_limit(fo_ctx *ctx, const void *kernel, size_t bytes) {
+  static std::map<std::pair<int, const void *>, size_t> limit;
+  size_t &cur = limit[{ctx->device, kernel}];
+  if (bytes > cur) {
+    FO_CU(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+  }
   return FO_OK;
 }
 
@@ -319,8 +335,8 @@ static fo_status run_pcg(fo_problem *p, const Op &op, PcgArgs<NC, T> a, long lon
   long long work;
   size_t smem;
   sweep_shape(p, op, nodes, &block, &work, &smem);
-  if (smem > 48 * 1024)
-    FO_CU(p->ctx, cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  std::unique_lock<std::mutex> lk(fo_launch_mutex());
+  if (smem > 48 * 1024) FO_TRY(fo_smem_limit(p->ctx, (const void *)kern, smem));
   FO_TRY(fo_cooperative_grid(p, (const void *)kern, block, smem, work, requested, &grid));
   a.partials = p->red;
   a.out = out_area(p);
@@ -331,6 +347,7 @@ static fo_status run_pcg(fo_problem *p, const Op &op, PcgArgs<NC, T> a, long lon
   if (tm) FO_CU(ctx, cudaEventRecord(ctx->ev_solve[0], ctx->stream));
   FO_TRY(coop_launch(p, kern, grid, block, smem, op, a));
   FO_CU(p->ctx, cudaGetLastError());
+  lk.unlock();
   if (tm) FO_CU(ctx, cudaEventRecord(ctx->ev_solve[1], ctx->stream));
   FO_TRY(read_out(p, out_area(p), o, 4 * NC));
   if (tm) {   // device time of the persistent PCG launch alone, summed over restarts

@@ -853,26 +853,28 @@ __global__ void k_mg_coarse_inverse(Grid g, const double *W, int n, float *ainv)
   for (int k = threadIdx.x; k < n * n; k += blockDim.x) ainv[k] = (float)A[k];
 }
 
-static void mg_build_inverse(fo_ctx *ctx, fo_mg *mg) {
-  if (mg->nd == 0) return;
+static fo_status mg_build_inverse(fo_ctx *ctx, fo_mg *mg) {
+  if (mg->nd == 0) return FO_OK;
   const Grid &gc = mg->g[mg->L - 1];
   const double *W = mg->W64[mg->L - 1];
   cudaStream_t s = ctx->stream;
   const size_t smem = sizeof(double) * mg->nd * mg->nd;
-  auto run = [&](auto kern) {
-    cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto run = [&](auto kern) -> fo_status {
+    std::lock_guard<std::mutex> lk(fo_launch_mutex());
+    FO_TRY(fo_smem_limit(ctx, (const void *)kern, smem));
     kern<<<1, 256, smem, s>>>(gc, W, mg->nd, mg->ainv);
+    fo_note_launch(1);
+    FO_CU(ctx, cudaGetLastError());
+    return FO_OK;
   };
   if (gc.dim == 2) {
-    if (mg->npn == 1) run(k_mg_coarse_inverse<2, 1, true>);
-    else if (mg->blk == 4) run(k_mg_coarse_inverse<2, 2, true>);
-    else run(k_mg_coarse_inverse<2, 2, false>);
-  } else {
-    if (mg->npn == 1) run(k_mg_coarse_inverse<3, 1, true>);
-    else if (mg->blk == 9) run(k_mg_coarse_inverse<3, 3, true>);
-    else run(k_mg_coarse_inverse<3, 3, false>);
+    if (mg->npn == 1) return run(k_mg_coarse_inverse<2, 1, true>);
+    if (mg->blk == 4) return run(k_mg_coarse_inverse<2, 2, true>);
+    return run(k_mg_coarse_inverse<2, 2, false>);
   }
-  fo_note_launch(1);
+  if (mg->npn == 1) return run(k_mg_coarse_inverse<3, 1, true>);
+  if (mg->blk == 9) return run(k_mg_coarse_inverse<3, 3, true>);
+  return run(k_mg_coarse_inverse<3, 3, false>);
 }
 
 // The single-problem hierarchy ends at the first level small enough to be solved directly.
@@ -1086,7 +1088,7 @@ static fo_status mg_prepare_state(fo_problem *p) {
     FO_TRY(fo_launch_stencil_on(p, mg->g[l], mg->coef[l], mg->dir[l], mg->W64[l], mg->W32[l], mg->dinv64[l],
                                 mg->dinv32[l]));
   }
-  mg_build_inverse(ctx, mg);
+  FO_TRY(mg_build_inverse(ctx, mg));
   FO_TRY(mg_upload(ctx, mg, p->Wst32, p->dinv_state32, p->dir, p->ncomp == 1 ? 0.8f : 0.6f));
   mg->built_epoch = p->coef_epoch;
   return FO_OK;
@@ -1131,7 +1133,7 @@ static fo_status mg_prepare_velocity(fo_problem *p) {
     FO_TRY(fo_launch_velocity_stencil_on(p, mg->g[l], mg->coef[l], mg->dir[l], mg->W64[l], mg->W32[l], mg->dinv64[l],
                                          mg->dinv32[l]));
   }
-  mg_build_inverse(ctx, mg);
+  FO_TRY(mg_build_inverse(ctx, mg));
   FO_TRY(mg_upload(ctx, mg, mg->W32[0], mg->dinv32[0], mg->dir[0], 0.8f));
   return FO_OK;
 }
@@ -1151,6 +1153,7 @@ static fo_status mg_launch(fo_problem *p, fo_mg *mg, MgCgT<V> C, const fo_solve_
   C.warm = warm;
   auto kern = k_pcg_mg<D, NPN, FULL, NC, V>;
   int grid;
+  std::unique_lock<std::mutex> lk(fo_launch_mutex());
   FO_TRY(fo_cooperative_grid(p, (const void *)kern, FO_BLOCK, 0, p->mesh->g.num_nodes, o->grid_blocks, &grid));
   // Block 0 keeps the levels it runs alone in shared memory when they fit and the launch
   // keeps its grid (the extra shared memory per block may lower the co-resident count).
@@ -1159,7 +1162,7 @@ static fo_status mg_launch(fo_problem *p, fo_mg *mg, MgCgT<V> C, const fo_solve_
     const MgDev *h = reinterpret_cast<const MgDev *>(mg->host.data());
     const size_t bytes = h->Lg < h->L ? mg_stage_layout<D, NPN, FULL>(*h, nullptr, nullptr) : 0;
     if (bytes > 0 && bytes <= MG_STAGE_MAX_BYTES) {
-      FO_CU(ctx, cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      FO_TRY(fo_smem_limit(ctx, (const void *)kern, bytes));
       int g1 = 0;
       FO_TRY(fo_cooperative_grid(p, (const void *)kern, FO_BLOCK, bytes, p->mesh->g.num_nodes, o->grid_blocks, &g1));
       if (g1 == grid) smem = bytes;
@@ -1175,6 +1178,7 @@ static fo_status mg_launch(fo_problem *p, fo_mg *mg, MgCgT<V> C, const fo_solve_
   FO_CU(ctx, cudaLaunchCooperativeKernel((const void *)kern, grid, FO_BLOCK, argv, smem, ctx->stream));
   fo_note_launch(1);
   FO_CU(ctx, cudaGetLastError());
+  lk.unlock();
   if (tm) FO_CU(ctx, cudaEventRecord(ctx->ev_solve[1], ctx->stream));
   FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars, C.out, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars + 32, p->dev_status, sizeof(int) * DS_COUNT, cudaMemcpyDeviceToHost,

@@ -134,3 +134,39 @@ def test_served_heat_matches_oracle(ctx):
     theta, Btt = ovel.solve(op.mesh, op.vform, op.rhs(u, A, chi, 0.0))
     assert close_scaled(rq.theta, theta, 1e-10), np.max(np.abs(rq.theta - theta))
     assert abs(r.Btt - Btt) <= 1e-10 * abs(Btt)
+
+
+@pytest.mark.parametrize("prec", [api.FO_FP64, api.FO_MIXED])
+def test_concurrent_multigrid_requests_of_distinct_sizes(ctx, prec):
+    """Eight executors launching multigrid solves whose staged shared memory differs from request
+    to request (the kernel's shared-memory limit is process-wide state): every request runs, and
+    in-mix results equal the same request served alone (same bits)."""
+    rng = np.random.default_rng(5)
+    items = []
+    for i, n in enumerate([40, 72, 96, 130, 64, 100, 150, 84, 112, 56, 140, 90, 120, 48, 160, 76, 33, 45]):
+        kind = FO_HEAT if i % 2 == 0 else FO_ELASTIC
+        items.append((2, n, kind, rng.random((6, 2))))
+
+    def req(dim, n, kind, centers):
+        return api.ServedRequest(dim, (n,) * dim, _desc(kind, dim), centers=centers, width=0.15, offset=0.2,
+                                 state=api.solve_opts(precision=prec, rtol=1e-9, precond=api.FO_PC_MG),
+                                 velocity=api.solve_opts(rtol=1e-9, precond=api.FO_PC_MG), want_theta=True)
+
+    def serve(its, executors):
+        srv = api.Server(ctx, executors=executors)
+        reqs = [req(*it) for it in its]
+        res = [srv.wait(srv.submit(r)[1], 300.0) for r in reqs]
+        st = srv.stats()
+        srv.close()
+        return reqs, res, st
+
+    reqs, res, st = serve(items, 8)
+    assert st.failed == 0 and st.completed == len(items)
+    for it, r in zip(items, res):
+        assert r is not None and r.status == 0, (it[:3], r.message)
+        if it[2] == FO_ELASTIC:   # (the heat requests here have no source: a zero state)
+            assert r.state.iterations > 0
+    for k in (0, 3, 6):
+        (rq_a,), (r_a,), _ = serve([items[k]], 1)
+        assert (res[k].J, res[k].C, res[k].Btt) == (r_a.J, r_a.C, r_a.Btt), items[k][:3]
+        assert np.array_equal(reqs[k].theta, rq_a.theta)
