@@ -35,6 +35,8 @@ Module map (paper section / equation each follows):
                 the initial level set (eq. phi0).
 * ``ppl``       Proximal-Perturbed Lagrangian update (eqs lagrangian,
                 lag_method) and adaptive time stepping (eqs tend, steps).
+* ``logistic``  the population model of Sec. 6.4 (eqs log_cost, log_prob, log_KOmega,
+                log_weak): Newton state solve, linear adjoint, cost and the S1 tensor.
 * ``algorithm`` one iteration of Algorithm 1.
 * ``solvers``   sparse direct solve, Jacobi-PCG, Jacobi-BiCGStab.
 
@@ -46,5 +48,9 @@ an equal history = explicit Euler", and a pointwise brute-force evaluation of
 one Euler and one AB2 step with finite-difference test-function gradients
 (``tests/test_oracle_pins_load_reinit.py``); the traction load
 (``fem.facet_load``) by hand-computed facets, subdivision quadrature and the
-face sums and first moments.
+face sums and first moments.  The logistic model (``logistic``) by the cubic integrals
+against a collapsed Gauss product rule, the residual against per-element quadrature, the
+Jacobian against central differences of the residual, constant equilibria, quadratic Newton
+convergence, the adjoint against a finite-difference source derivative and a Taylor test of
+the shape derivative (``tests/test_oracle_logistic.py``).
 """

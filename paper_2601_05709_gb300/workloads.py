@@ -39,6 +39,12 @@ def phi_cos(coords):
     return np.cos(4 * np.pi * coords[:, 0]) * np.cos(4 * np.pi * coords[:, 1]) + 0.3
 
 
+def u0_logistic(coords):
+    """Initial Newton guess of the population example: 1 + 0.2 sin(6 pi x) sin(6 pi y)
+    (its third coordinate, if any, is ignored)."""
+    return 1.0 + 0.2 * np.sin(6 * np.pi * coords[:, 0]) * np.sin(6 * np.pi * coords[:, 1])
+
+
 def hole_lattice(nx=8, ny=4, spacing=0.25, radius=0.08):
     """Centres ((i + 1/2) s, (j + 1/2) s) and radii of a lattice of round holes."""
     centres = [((i + 0.5) * spacing, (j + 0.5) * spacing) for j in range(ny) for i in range(nx)]
