@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--precond", choices=["jacobi", "mg"], default="mg", help="state-solve preconditioner")
+    ap.add_argument("--mg-bf16", type=int, default=0, help="1: V-cycle grid-level rows in BF16")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--l2-flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
@@ -68,11 +69,11 @@ def parse():
 
 
 # ------------------------------------------------------------------------------ problem
-def run_options(api, precision, precond="mg"):
+def run_options(api, precision, precond="mg", mg_bf16=0):
     prec = api.FO_MIXED if precision == "mixed" else api.FO_FP64
     pc = api.FO_PC_MG if precond == "mg" else api.FO_PC_JACOBI
-    state = api.solve_opts(precision=prec, rtol=1e-12, warm_start=1, precond=pc)
-    vel = api.solve_opts(rtol=1e-12, warm_start=1, precond=pc)
+    state = api.solve_opts(precision=prec, rtol=1e-12, warm_start=1, precond=pc, mg_bf16=mg_bf16)
+    vel = api.solve_opts(rtol=1e-12, warm_start=1, precond=pc, mg_bf16=mg_bf16)
     tr = api.solve_opts(rtol=1e-12)
     # no reinitialisation inside the 50 iterations: on this mesh the reinitialisation scheme
     # (Sec. 5.7) is unstable for the level sets the transport produces (the oracle shows the
@@ -526,8 +527,10 @@ def bench_configs(api, ctx, stream, peaks):
     solves = {}
     # the configured solve: FP32 CG (FP32 rows and vectors, FP64 dots) inside FP64 refinement to
     # 1e-8, preconditioned by the FP32 V-cycle; beside it the FP64 CG with the same V-cycle
-    for name, prec in (("mixed", api.FO_MIXED), ("fp64", api.FO_FP64)):
-        so = api.solve_opts(precision=prec, rtol=1e-8, inner_rtol=1e-4, precond=mg)
+    # and both again with the V-cycle's grid-level rows in BF16 (the BF16 element-data option)
+    for name, prec, bf16 in (("mixed", api.FO_MIXED, 0), ("fp64", api.FO_FP64, 0), ("mixed_bf16", api.FO_MIXED, 1),
+                             ("fp64_bf16", api.FO_FP64, 1)):
+        so = api.solve_opts(precision=prec, rtol=1e-8, inner_rtol=1e-4, precond=mg, mg_bf16=bf16)
         prob.state_solve(so)                              # builds the hierarchy (first call)
         reps, kms = [], []
         for _ in range(3):
@@ -535,13 +538,13 @@ def bench_configs(api, ctx, stream, peaks):
             reps.append(ms1)
             kms.append(ctx.solve_kernel_ms())
         st1 = st1[-1]
-        w = 4 if name == "mixed" else 8
+        w = 4 if prec == api.FO_MIXED else 8
         bpi = survey_pcg_bytes(ndof, mesh.num_elems, mesh.num_nodes, 3, w)
         kms_mean = sum(kms) / len(kms)
         achieved = bpi * st1.iterations / (kms_mean / 1e3) / 1e9
         solves[name] = {"solve_ms": sum(reps) / len(reps), "cg_kernel_ms": kms_mean,
                         "iterations": st1.iterations, "refinements": st1.outer_iterations,
-                        "rel_residual": st1.rel_residual,
+                        "rel_residual": st1.rel_residual, "vcycle_rows": "bf16" if bf16 else "fp32",
                         "gdof_iters_per_s": ndof * st1.iterations / (sum(reps) / len(reps) / 1e3) / 1e9,
                         "roofline": {"bound": "hbm", "kernel": "k_pcg_mg<3, 3, true, 1, %s>" % (
                                          "float" if w == 4 else "double"),
@@ -834,7 +837,7 @@ def main():
     ctx = api.Context(local, stream=stream.cuda_stream)
     ctx.set_timing(True)
     mesh, prob = make_problem(api, ctx)
-    opts = run_options(api, args.precision, args.precond)
+    opts = run_options(api, args.precision, args.precond, args.mg_bf16)
     ppl = api.PPL(1)
     flush = torch.empty(max(args.l2_flush_mb, 1) * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2
 
@@ -929,7 +932,7 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "precision": args.precision,
+                   "precision": args.precision, "vcycle_rows": "bf16" if args.mg_bf16 else "fp32",
                    "l2": f"flushed between timed steps ({args.l2_flush_mb} MiB write, untimed)"},
         "pcg_gdof_iters_per_s": gdof, "state_pcg_iterations": state_iters,
         "phase_ms_per_step": phase, "roofline": roof, "gpu_launches": int(launches), "clocks": clock_info,

@@ -71,6 +71,9 @@ typedef struct fo_problem fo_problem;
 #define FO_HEAT       0   /* -div(A grad u) = f, J = int A |grad u|^2          (Sec. 6.3) */
 #define FO_ELASTIC    1   /* -div(A sigma(u)) = 0 + loads, J = int A sigma:eps   (Sec. 6.2) */
 #define FO_HELMHOLTZ  2   /* -div(A k grad u) + omega^2 u = f, J = int f u (screened family) */
+#define FO_LOGISTIC   3   /* -Delta u = r u (1 - u / K), K = a_in on {phi < 0}, a_out     */
+                          /* elsewhere, natural boundary; J = -int u; Newton state,      */
+                          /* linear adjoint (Sec. 6.4, eqs log_cost, log_prob, log_KOmega) */
 
 /* precisions (fo_solve_opts.precision) */
 #define FO_FP64   0       /* FP64 operator, vectors and reductions                        */
@@ -162,6 +165,20 @@ typedef struct {
    * n_volume = 0: the single constraint |Omega| / volume_target when volume_target > 0. */
   int n_volume;
   double volume_lo[4][3], volume_hi[4][3], volume_V[4];
+  /* Logistic population model (FO_LOGISTIC, Sec. 6.4; box meshes, one load case, the
+   * one-point coefficient rule, at most the single constraint |Omega| / volume_target).
+   * growth_rate: r > 0.  The carrying capacity K_e is the element coefficient (a_in inside,
+   * a_out outside; the paper's example takes 1 and 1e-2).  u_init: host array of N_n initial
+   * Newton values, copied at creation (NULL: u = a_in everywhere); a state solve with
+   * warm_start = 1 starts from the current state instead.  Newton stops at the first iterate
+   * with ||F(u_k)||_2 <= newton_rtol ||F(u_0)||_2 + newton_atol, or when the update has
+   * ||du||_inf <= 1e-14 ||u||_inf, and fails (FO_ENOCONV, result kept) after newton_maxit
+   * steps; zeros select 1e-13, 0 and 50.  Each Newton step solves DF(u) du = -F(u) with the
+   * Jacobi-preconditioned CG of the state options (multigrid is not used for this model). */
+  double growth_rate;
+  const double *u_init;
+  double newton_rtol, newton_atol;
+  int newton_maxit;
 } fo_model_desc;
 
 #define FO_COEF_CENTROID 0
@@ -178,9 +195,11 @@ typedef struct {
   int inner_maxit;          /* FO_MIXED: cap per FP32 solve                             */
   int grid_blocks;          /* 0 = autotuned; else blocks of the persistent kernel      */
   int precond;              /* FO_PC_JACOBI, or FO_PC_MG: an FP32 geometric-multigrid   */
-                            /* V-cycle as preconditioner, on grids that halve at least  */
-                            /* once down to a coarsest level of <= 8192 unknowns (else  */
-                            /* the Jacobi solver runs).  Single problems: FO_FP64 ->    */
+                            /* V-cycle as preconditioner.  Single problems coarsen any  */
+                            /* grid of >= 3 cells per axis (ceil(n/2) per axis where an */
+                            /* axis does not halve) down to a coarsest level of <= 8192 */
+                            /* unknowns (else the Jacobi solver runs); batches need     */
+                            /* grids that halve.  Single problems: FO_FP64 ->           */
                             /* FP64 CG; FO_MIXED (state, adjoint) -> FP64 refinement     */
                             /* around an FP32 CG (FP32 rows and vectors, FP64 dots;      */
                             /* inner_rtol, inner_maxit per step); the velocity solve is */
@@ -189,6 +208,14 @@ typedef struct {
                             /* FP64 refinement around an FP32 CG (inner_rtol,           */
                             /* inner_maxit per refinement step), stopping an instance   */
                             /* also when a step fails to halve its true residual.       */
+  int mg_bf16;              /* FO_PC_MG, single problems: 1 = the V-cycle levels run by  */
+                            /* the whole grid read their rows rounded to BF16 (FP32      */
+                            /* arithmetic); the CG operator, its vectors and dots keep   */
+                            /* their precision, so only the preconditioner changes and   */
+                            /* the stopping test and accuracy are those of `precision`.  */
+                            /* The rows are difference-form weights, so the rounded      */
+                            /* operator keeps its symmetry and constant kernel.  Costs   */
+                            /* half the FP32 rows' bytes more memory.  0 = FP32 rows.    */
 } fo_solve_opts;
 
 #define FO_PC_JACOBI 0
@@ -232,6 +259,8 @@ typedef struct {
   double ms_state_kernel;
   int nc;                   /* constraints of this iteration (0 = none)                 */
   double Cv[4], lambdav[4]; /* C_j and lambda_j of every constraint (C, lambda = [0])    */
+  fo_solve_stats adjoint;   /* explicit adjoint solve of the iteration (FO_LOGISTIC)     */
+  int newton_steps;         /* Newton steps of the state solve (FO_LOGISTIC)             */
 } fo_iter_log;
 
 /* ---------------------------------------------------------------- context ----- */

@@ -13,7 +13,7 @@ FO_ENOCONV, FO_ENAN, FO_ETIMEOUT, FO_EBUSY, FO_ESTATE = -5, -6, -7, -8, -9
 STATUS_NAMES = {0: "FO_OK", -1: "FO_EINVAL", -2: "FO_ENOMEM", -3: "FO_ENOMEM_BUDGET", -4: "FO_ECUDA",
                 -5: "FO_ENOCONV", -6: "FO_ENAN", -7: "FO_ETIMEOUT", -8: "FO_EBUSY", -9: "FO_ESTATE"}
 
-FO_HEAT, FO_ELASTIC, FO_HELMHOLTZ = 0, 1, 2
+FO_HEAT, FO_ELASTIC, FO_HELMHOLTZ, FO_LOGISTIC = 0, 1, 2, 3
 FO_FP64, FO_MIXED = 0, 1
 FO_PC_JACOBI, FO_PC_MG = 0, 1
 FO_COEF_CENTROID, FO_COEF_CUT = 0, 1
@@ -41,7 +41,9 @@ class ModelDesc(C.Structure):
                 ("n_inst", C.c_int), ("inst_k", C.POINTER(C.c_double)), ("inst_omega", C.POINTER(C.c_double)),
                 ("inst_f", C.POINTER(C.c_double)), ("coef_rule", C.c_int), ("n_cases", C.c_int),
                 ("point_case", C.c_int * 4), ("traction_case", C.c_int * 4), ("n_volume", C.c_int),
-                ("volume_lo", D43), ("volume_hi", D43), ("volume_V", C.c_double * 4)]
+                ("volume_lo", D43), ("volume_hi", D43), ("volume_V", C.c_double * 4),
+                ("growth_rate", C.c_double), ("u_init", C.POINTER(C.c_double)), ("newton_rtol", C.c_double),
+                ("newton_atol", C.c_double), ("newton_maxit", C.c_int)]
 
 
 class TuneResult(C.Structure):
@@ -52,7 +54,7 @@ class TuneResult(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int), ("warm_start", C.c_int),
                 ("inner_rtol", C.c_double), ("inner_maxit", C.c_int), ("grid_blocks", C.c_int),
-                ("precond", C.c_int)]
+                ("precond", C.c_int), ("mg_bf16", C.c_int)]
 
 
 class SolveStats(C.Structure):
@@ -104,7 +106,8 @@ class IterLog(C.Structure):
                 ("reinit_stats", SolveStats), ("ms_state", C.c_double), ("ms_functionals", C.c_double),
                 ("ms_shape", C.c_double), ("ms_velocity", C.c_double), ("ms_transport", C.c_double),
                 ("ms_reinit", C.c_double), ("ms_state_kernel", C.c_double), ("nc", C.c_int),
-                ("Cv", C.c_double * 4), ("lambdav", C.c_double * 4)]
+                ("Cv", C.c_double * 4), ("lambdav", C.c_double * 4), ("adjoint", SolveStats),
+                ("newton_steps", C.c_int)]
 
 
 class StopOpts(C.Structure):

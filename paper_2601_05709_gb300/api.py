@@ -11,11 +11,11 @@ import numpy as np
 from . import _lib
 from ._lib import (FO_COEF_CENTROID, FO_COEF_CUT, FO_PC_JACOBI, FO_PC_MG, FO_ELASTIC, FO_FIELD_CHI, FO_FIELD_COEF, FO_FIELD_LOAD, FO_FIELD_OMEGA0, FO_FIELD_P,
                    FO_FIELD_PHI, FO_FIELD_RHS, FO_FIELD_THETA, FO_FIELD_U, FO_FP64, FO_HEAT, FO_HELMHOLTZ,
-                   FO_MIXED, FO_OP_STATE, FO_OP_STATE_FP32, FO_OP_TRANSPORT_L, FO_OP_TRANSPORT_R,
+                   FO_LOGISTIC, FO_MIXED, FO_OP_STATE, FO_OP_STATE_FP32, FO_OP_TRANSPORT_L, FO_OP_TRANSPORT_R,
                    FO_OP_VELOCITY, FO_OK, FormoptError)
 
 __all__ = ["Context", "Mesh", "Problem", "model_desc", "solve_opts", "run_options", "PPL", "adaptime",
-           "FO_HEAT", "FO_ELASTIC", "FO_HELMHOLTZ", "FO_FP64", "FO_MIXED", "FormoptError"]
+           "FO_HEAT", "FO_ELASTIC", "FO_HELMHOLTZ", "FO_LOGISTIC", "FO_FP64", "FO_MIXED", "FormoptError"]
 
 
 def _dp(a):
@@ -31,11 +31,12 @@ def _is_device(x):
 
 
 def solve_opts(precision=FO_FP64, rtol=1e-12, maxit=200000, warm_start=0, inner_rtol=1e-3, inner_maxit=20000,
-               grid_blocks=0, precond=0):
+               grid_blocks=0, precond=0, mg_bf16=0):
     o = _lib.SolveOpts()
     _lib.load().fo_solve_opts_default(C.byref(o))
     o.precision, o.rtol, o.maxit, o.warm_start = precision, rtol, maxit, int(warm_start)
     o.inner_rtol, o.inner_maxit, o.grid_blocks, o.precond = inner_rtol, inner_maxit, grid_blocks, precond
+    o.mg_bf16 = int(bool(mg_bf16))
     return o
 
 
@@ -62,9 +63,12 @@ def run_options(dfactor=1e-2, lv_time=(1e-3, 1e-1), lv_iter=(8, 16), smooth=Fals
 def model_desc(kind, a_in=1.0, a_out=1e-3, E=1.0, nu=0.3, k=1.0, omega=0.0, dirichlet=(), f_nodal=None,
                point_loads=(), tractions=(), volume=0.0, alpha_mass=0.1, normal_penalty=0.0, omega0_weight=0.0,
                omega0_boxes=(), velocity_dirichlet=False, inst_k=None, inst_omega=None, inst_f=None, coef_rule=0,
-               load_cases=None, volume_regions=None):
+               load_cases=None, volume_regions=None, growth_rate=0.0, u_init=None, newton_rtol=0.0,
+               newton_atol=0.0, newton_maxit=0):
     """Build a fo_model_desc.  dirichlet: [(axis, side)]; point_loads: [(node, vec)];
     tractions: [(axis, side, vec)]; omega0_boxes: [(lo, hi)] with strict inequalities.
+    The logistic model (kind FO_LOGISTIC): growth_rate r, u_init [N_n] initial Newton values,
+    carrying capacity a_in / a_out inside / outside.
     A task-parallel batch (kind FO_HELMHOLTZ): inst_k, inst_omega [n_inst] and
     inst_f [n_inst, N_n]."""
     d = _lib.ModelDesc()
@@ -136,6 +140,11 @@ def model_desc(kind, a_in=1.0, a_out=1e-3, E=1.0, nu=0.3, k=1.0, omega=0.0, diri
         d.n_inst = len(ik)
         d.inst_k, d.inst_omega, d.inst_f = _dp(ik), _dp(io), _dp(iF)
         kept += [ik, io, iF]
+    d.growth_rate, d.newton_rtol, d.newton_atol, d.newton_maxit = growth_rate, newton_rtol, newton_atol, newton_maxit
+    if u_init is not None:
+        ui = _f64(u_init)
+        d.u_init = _dp(ui)
+        kept.append(ui)
     d._keep = kept                       # keep the arrays alive until fo_problem_create copied them
     return d
 

@@ -372,14 +372,6 @@ __global__ void k_f2d(const float *x, double *y, long long n) {
 }
 
 // ------------------------------------------------------------------ stored stencils
-// grad lambda_l of the Kuhn simplex p: e_{pi_{l-1}} / h - e_{pi_l} / h (sparse)
-template <int D>
-__device__ __forceinline__ void kuhn_grad(const Grid &g, int p, int l, double gr[3]) {
-  gr[0] = gr[1] = gr[2] = 0.0;
-  if (l >= 1) gr[kperm<D>(p, l - 1)] += g.inv_h[kperm<D>(p, l - 1)];
-  if (l < D) gr[kperm<D>(p, l)] -= g.inv_h[kperm<D>(p, l)];
-}
-
 // Stored rows are kept in difference form: slot 0 holds the row sum R (an NPN x NPN block, or
 // its diagonal), slots s >= 1 the neighbour blocks W_s, and the row is applied as
 //   (A x)_a = R x_a + sum_{s >= 1} W_s (x_{nb(s)} - x_a),
@@ -808,6 +800,11 @@ __global__ void k_functionals(FuncArgs f, const double *coef, const uint8_t *chi
         g2 += d * d;
       }
       v[0] += A * g.vol_e * g2;
+    } else if (f.kind == FO_LOGISTIC) {   // J = -int u
+      double su = 0;
+#pragma unroll
+      for (int l = 0; l <= D; ++l) su += u[vtx[l]];
+      v[0] -= g.vol_e * su / (D + 1);
     }
     v[1] += chif ? chif[e] * g.vol_e : (chi[e] ? g.vol_e : 0.0);
   }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 #include <cstdio>
 #include <mutex>
@@ -97,6 +98,9 @@ struct fo_mg {
   float *b[MG_MAX_LEVELS] = {}, *z0[MG_MAX_LEVELS] = {}, *z1[MG_MAX_LEVELS] = {}, *t[MG_MAX_LEVELS] = {};
   double *coef[MG_MAX_LEVELS] = {}, *W64[MG_MAX_LEVELS] = {}, *dinv64[MG_MAX_LEVELS] = {};
   float *W32[MG_MAX_LEVELS] = {}, *dinv32[MG_MAX_LEVELS] = {};
+  __nv_bfloat16 *Wh[MG_MAX_LEVELS] = {};   // BF16 copies of the grid-run levels' rows (on request)
+  int Lg = 0;                              // levels >= Lg run in one block (set by the upload)
+  int rows_bf16 = 0;                       // the uploaded table points the grid levels at Wh
   uint8_t *dir[MG_MAX_LEVELS] = {};
   int nd = 0;                              // coarsest level's unknowns when solved directly
   float *ainv = nullptr;                   // [nd][nd] its inverse (FP32)
@@ -123,7 +127,8 @@ struct fo_problem {
   uint8_t *omega0 = nullptr;     // N_T
   uint8_t *dir = nullptr;        // N_dof state Dirichlet mask
   uint8_t *vdir = nullptr;       // N_n velocity Dirichlet mask (H^1_0)
-  double *f = nullptr;           // N_n nodal source (heat / Helmholtz) or null
+  double *f = nullptr;           // N_n nodal source (heat / Helmholtz), the initial Newton
+                                 // guess (logistic: a model without a source), or null
   double *load = nullptr;        // N_dof
   double *u = nullptr;           // N_dof
   double *p = nullptr;           // N_dof
@@ -142,6 +147,7 @@ struct fo_problem {
   int *dev_status = nullptr;     // device error word + solver outputs
   Scratch scratch;
   bool coef_valid = false, u_valid = false, rhs_valid = false, theta_valid = false;
+  int newton_steps = 0;          // Newton steps of the last logistic state solve
   bool transport_valid = false;
   double transport_dt = 0, transport_h = 0;
   int transport_smooth = 0;
@@ -512,10 +518,14 @@ fo_status fo_batch_state(fo_problem *p, bool adjoint, const fo_solve_opts *o, fo
 fo_status fo_batch_functionals(fo_problem *p, double *J, double *vol, double *J_inst);
 fo_status fo_batch_shape_rhs(fo_problem *p, double lambda);
 fo_status fo_batch_apply(fo_problem *p, const double *x, double *y, bool fp32);
+// logistic population model (fo_logistic.cu)
+fo_status fo_logistic_state(fo_problem *p, const fo_solve_opts *o, fo_solve_stats *st, int *steps_out);
+fo_status fo_logistic_adjoint(fo_problem *p, const fo_solve_opts *o, fo_solve_stats *st);
+fo_status fo_launch_logistic_shape(fo_problem *p, double lambda, const double *chif, double inv_V, int add);
 // multigrid (fo_mg.cu)
 fo_status fo_state_pcg_mg(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st);
 void fo_mg_destroy(fo_problem *p);
-size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0);
+size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0, bool bf16 = false);
 bool fo_mg_applicable(const Grid &g0, int npn, bool general = true);
 int fo_mg_plan(const Grid &g0, Grid *g, int max_levels, long long stop_unknowns = 0, int npn = 1, bool general = false);
 void fo_mg_restrict(fo_ctx *ctx, const Grid &gc, const Grid &gf, int npn, const double *coef_f, const uint8_t *dir_f,

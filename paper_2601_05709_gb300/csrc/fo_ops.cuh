@@ -114,6 +114,14 @@ __device__ __forceinline__ bool elem_of(const Grid &g, const int idx[3], int p, 
   return true;
 }
 
+// grad lambda_l of the Kuhn simplex p: e_{pi_{l-1}} / h - e_{pi_l} / h (sparse)
+template <int D>
+__device__ __forceinline__ void kuhn_grad(const Grid &g, int p, int l, double gr[3]) {
+  gr[0] = gr[1] = gr[2] = 0.0;
+  if (l >= 1) gr[kperm<D>(p, l - 1)] += g.inv_h[kperm<D>(p, l - 1)];
+  if (l < D) gr[kperm<D>(p, l)] -= g.inv_h[kperm<D>(p, l)];
+}
+
 // Load NPN components of the field at every stencil neighbour (0 outside the grid).
 template <int D, int NPN, typename T, class X>
 __device__ __forceinline__ void load_stencil(const Grid &g, const int idx[3], long long a, const X &x,
@@ -140,13 +148,25 @@ __device__ __forceinline__ void load_stencil(const Grid &g, const int idx[3], lo
 // entry; on GB300, whose FP64 rate is 1/58 of its FP32 rate, that is several times less FP64
 // work than recomputing element matrices, and a single problem's stencils stay resident in the
 // 129 MB L2.  Built once per coefficient update (state) or once per problem (velocity).
-template <int D, int NPN_, bool FULL, typename T>
+//
+// WT is the storage type of the weights (T, or BF16 rows of a multigrid level applied in FP32:
+// the difference form keeps the rounded operator's constant kernel and its symmetry).
+template <typename T, typename WT>
+__device__ __forceinline__ T stencil_weight(const WT *w) {
+  return (T)*w;
+}
+template <>
+__device__ __forceinline__ float stencil_weight<float, __nv_bfloat16>(const __nv_bfloat16 *w) {
+  return __bfloat162float(*w);
+}
+
+template <int D, int NPN_, bool FULL, typename T, typename WT = T>
 struct StencilOp {
   static constexpr int NPN = NPN_;
   static constexpr int BLK = FULL ? NPN * NPN : NPN;
   Grid g;
   FO_NODE_OWNERSHIP(T)
-  const T *W;
+  const WT *W;
 
   template <class X>
   __device__ __forceinline__ void row(long long a, const int idx[3], const X &x, T out[NPN]) const {
@@ -167,10 +187,10 @@ struct StencilOp {
 #pragma unroll
         for (int i = 0; i < NPN; ++i)
 #pragma unroll
-          for (int j = 0; j < NPN; ++j) acc[i] = fma(W[(s * BLK + i * NPN + j) * N + a], xv[j], acc[i]);
+          for (int j = 0; j < NPN; ++j) acc[i] = fma(stencil_weight<T>(W + (s * BLK + i * NPN + j) * N + a), xv[j], acc[i]);
       } else {
 #pragma unroll
-        for (int c = 0; c < NPN; ++c) acc[c] = fma(W[(s * BLK + c) * N + a], xv[c], acc[c]);
+        for (int c = 0; c < NPN; ++c) acc[c] = fma(stencil_weight<T>(W + (s * BLK + c) * N + a), xv[c], acc[c]);
       }
     }
 #pragma unroll

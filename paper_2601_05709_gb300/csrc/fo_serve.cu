@@ -76,8 +76,8 @@ extern "C" size_t fo_request_device_bytes(const fo_request *rq) {
   const bool vmg = rq->velocity.precond == FO_PC_MG && fo_mg_applicable(g0, rq->dim);
   const int svecs = smg ? 6 : (rq->state.precision == FO_MIXED ? 11 : 8);
   size_t b = fo_problem_footprint(rq->dim, rq->n, rq->model.kind, svecs, vmg ? 7 : 8, rq->n_bumps);
-  if (smg) b += fo_mg_bytes(rq->dim, rq->n, nc, nc * nc, false);
-  if (vmg) b += fo_mg_bytes(rq->dim, rq->n, rq->dim, rq->dim, true);
+  if (smg) b += fo_mg_bytes(rq->dim, rq->n, nc, nc * nc, false, rq->state.mg_bf16 != 0);
+  if (vmg) b += fo_mg_bytes(rq->dim, rq->n, rq->dim, rq->dim, true, rq->velocity.mg_bf16 != 0);
   return b;
 }
 

@@ -241,6 +241,60 @@ def test_state_solve_mixed(ctx, api, c, pc):
     assert st.outer_iterations >= 2
 
 
+@pytest.mark.parametrize("c", [case(**HEAT2D), cantilever2d((128, 64)), cantilever3d((16, 8, 8)),
+                               case(dim=2, n=(75, 41), kind=0, f=lambda X: 1 + X[:, 1], dirichlet=[(0, 0)])])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_multigrid_bf16_rows(ctx, api, c, prec):
+    """V-cycle rows rounded to BF16 change only the preconditioner: the FP64 CG still meets the
+    FP64 bars (1e-10 of the oracle, backward error 1e-12) and the refinement the mixed bar
+    (1e-8), with iteration counts within 1.5x of those of the FP32 rows."""
+    op = oracle_problem(c)
+    phi = (workloads.phi_cos(op.mesh.coords) if c["dim"] == 2 else
+           workloads.phi_bumps(op.mesh.coords, workloads.bump_centres(c["lo"], c["hi"], 8, 0), 0.25, 0.2))
+    u_ref, A, _ = op.state(phi)
+    K, F, free = op.stiffness(A), op.load(), op.dirichlet() == 0
+    its = {}
+    for bf16 in (0, 1):
+        mesh, prob = gpu_problem(ctx, c)
+        prob.set_levelset(phi)
+        if prec == "fp64":
+            so = tight(api, precond=1)
+            so.mg_bf16 = bf16
+        else:
+            so = api.solve_opts(precision=api.FO_MIXED, rtol=1e-12, inner_rtol=1e-3, precond=1, mg_bf16=bf16)
+        st = prob.state_solve(so)
+        its[bf16] = st.iterations
+        u = prob.get(api._lib.FO_FIELD_U)
+        assert_solve_parity(K, F, free, u, u_ref, 1e-10 if prec == "fp64" else 1e-8, omega_max=1e-12)
+        # the same problem switched between the row types reuses the hierarchy
+        so.mg_bf16 = 1 - bf16
+        st2 = prob.state_solve(so)
+        assert_solve_parity(K, F, free, prob.get(api._lib.FO_FIELD_U), u_ref, 1e-10 if prec == "fp64" else 1e-8,
+                            omega_max=1e-12)
+    # BF16 weights perturb the smoother: measured up to ~30 % more iterations (3D elasticity
+    # from zero), nothing like the divergence a broken V-cycle would show
+    assert its[1] <= 1.5 * its[0] + 2, its
+
+
+def test_velocity_multigrid_bf16_rows(ctx, api):
+    """The velocity solve with BF16 V-cycle rows gives the FP32-row result to the solve tolerance."""
+    c = cantilever2d((64, 32))
+    mesh, prob = gpu_problem(ctx, c)
+    _, coords = mesh.copy_out()
+    prob.set_levelset(workloads.phi_cos(coords))
+    prob.state_solve(tight(api, precond=1))
+    prob.shape_derivative(0.3)
+    out = {}
+    for bf16 in (0, 1):
+        so = tight(api, precond=1)
+        so.mg_bf16 = bf16
+        Btt, st = prob.descent(so)
+        out[bf16] = (prob.get(api._lib.FO_FIELD_THETA), Btt, st.iterations)
+    assert close_scaled(out[1][0], out[0][0], 1e-10)
+    assert abs(out[1][1] - out[0][1]) <= 1e-10 * abs(out[0][1])
+    assert out[1][2] <= 1.25 * out[0][2] + 2
+
+
 def test_adjoint_closed_forms(ctx, api):
     for c, factor in ((case(**HEAT2D), -1.0), (cantilever2d((32, 16)), -2.0)):
         mesh, prob = gpu_problem(ctx, c)
