@@ -575,7 +575,7 @@ def bench_variants(api, ctx, stream, peaks):
     """The hot path's variants on the cantilever physics: a general mesh given as arrays
     (jittered, renumbered Kuhn arrays of the 256 x 128 box through the assembled-operator path),
     the exact cut-cell coefficient, and runs to convergence under the stopping criterion with
-    one and with two load cases."""
+    one and with two load cases; and the population example (logistic model) to convergence."""
     import numpy as np
     import torch
     from paper_2601_05709_gb300 import workloads
@@ -657,6 +657,44 @@ def bench_variants(api, ctx, stream, peaks):
                      "L": log.L, "opt_iters_per_s": it / sec,
                      "criterion": "start_to_check 30, lgrn_tol 1e-2, ctrn_tol 1e-2, prev 10 (Sec. 5.7 defaults)"}
         prob.close()
+
+    # the population example of Sec. 6.4 (logistic state by Newton, explicit adjoint): unit
+    # square 128 x 128, r = 40, V = 0.5, B = Dtheta:Dxi + 1e4 normal penalty on H^1, Newton from
+    # 1 + 0.2 sin(6 pi x) sin(6 pi y), phi0 = cos 4pi x cos 4pi y + 0.3; run to the stopping
+    # criterion (at most 400 iterations)
+    lm = ctx.mesh_box(2, (128, 128), (0.0, 0.0), (1.0, 1.0))
+    _, lc = lm.copy_out()
+    prob = lm.problem(api.model_desc(api.FO_LOGISTIC, a_in=1.0, a_out=1e-2, dirichlet=[], volume=0.5,
+                                     alpha_mass=0.0, normal_penalty=1e4, growth_rate=40.0,
+                                     u_init=workloads.u0_logistic(lc)))
+    prob.set_levelset(workloads.phi_cos(lc))
+    lso = api.solve_opts(rtol=1e-12, warm_start=1, maxit=400000, precond=api.FO_PC_JACOBI)
+    lro = api.run_options(dfactor=1e-2, smooth=False, state=lso, velocity=api.solve_opts(rtol=1e-12, warm_start=1,
+                                                                                         precond=api.FO_PC_MG),
+                          transport=api.solve_opts(rtol=1e-12))
+    ppl = api.PPL(1)
+    L, logs, it = [], [], 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while it < 400:
+        log = prob.opt_step(it, lro, ppl)
+        logs.append(log)
+        L.append(log.L)
+        it += 1
+        if api.stop_check(L, [log.C]):
+            break
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    out["logistic2d_128x128_to_convergence"] = {
+        "workload": "population model of Sec. 6.4 on a 128x128 Kuhn mesh of the unit square (32,768 triangles), "
+                    "r = 40, K = 1 / 1e-2, V = 0.5, Newton state (Jacobi-PCG steps), explicit adjoint",
+        "iterations": it, "stopped_by_criterion": it < 400, "seconds": sec, "opt_iters_per_s": it / sec,
+        "J": log.J, "C": log.C, "L": log.L,
+        "newton_steps_per_iteration": float(np.mean([l.newton_steps for l in logs])),
+        "state_cg_iterations_per_iteration": float(np.mean([l.state.iterations for l in logs])),
+        "adjoint_cg_iterations_per_iteration": float(np.mean([l.adjoint.iterations for l in logs])),
+        "criterion": "start_to_check 30, lgrn_tol 1e-2, ctrn_tol 1e-2, prev 10 (Sec. 5.7 defaults)"}
+    prob.close()
     return out
 
 

@@ -1,8 +1,9 @@
 """One iteration of Algorithm 1 ("Level set algorithm", Sec. 4) in the oracle.
 
-Order within iteration i (0-based): coefficients from phi^i; state solve;
-adjoint (closed form for the compliance costs: p = -u for heat, Sec. 6.3, and
-p = -2u for elasticity, Sec. 6.2, already folded into the S tensors); cost and
+Order within iteration i (0-based): coefficients from phi^i; state solve (Newton for
+the logistic model, Sec. 6.4); adjoint (closed form for the compliance costs: p = -u
+for heat, Sec. 6.3, and p = -2u for elasticity, Sec. 6.2, already folded into the S
+tensors; a linear solve for the logistic model); cost and
 constraint; one PPL update giving lambda (Sec. 5.4); S-assembly; velocity solve
 and B(theta, theta); adaptive time; transport to phi^{i+1}; reinitialisation
 when reinit_step > 0, i > 0 and i mod reinit_step == 0 (Sec. 5.7).
@@ -11,10 +12,10 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import fem, levelset, ppl as ppl_mod, shape, solvers, velocity
+from . import fem, levelset, logistic, ppl as ppl_mod, shape, solvers, velocity
 from .mesh import BoxMesh
 
-HEAT, ELASTIC, HELMHOLTZ = 0, 1, 2
+HEAT, ELASTIC, HELMHOLTZ, LOGISTIC = 0, 1, 2, 3
 
 
 @dataclass
@@ -41,6 +42,10 @@ class Problem:
     # Several volume constraints C_j = |Omega cap R_j| / V_j (Sec. 5.4 with N_c = len), R_j a
     # box (lo, hi) with strict inequalities on the element centroid; None = |Omega| / V.
     volume_regions: list = None
+    # Logistic population model (Sec. 6.4): growth rate r, initial Newton guess u_init (None:
+    # u = a_in); the carrying capacity is the element coefficient (a_in inside, a_out outside).
+    growth_rate: float = 0.0
+    u_init: np.ndarray = None
 
     @property
     def ncomp(self):
@@ -150,7 +155,17 @@ class Problem:
                 Ke = Ke + self.omega**2 * fem.mass(vol, m.dim)
         return fem.assemble(Ke, fem.element_dofs(m.cells, self.ncomp), m.num_nodes * self.ncomp)
 
+    def logistic_state(self, phi):
+        """Newton solution u, carrying capacity K_e and chi_e (Sec. 6.4)."""
+        m = self.mesh
+        K, chi = shape.coefficient(phi, m.cells, self.a_in, self.a_out)
+        u0 = self.u_init if self.u_init is not None else np.full(m.num_nodes, self.a_in)
+        u, _ = logistic.newton(m.coords, m.cells, K, self.growth_rate, u0)
+        return u, K, chi
+
     def state(self, phi):
+        if self.kind == LOGISTIC:
+            return self.logistic_state(phi)
         if self.coef_rule == "cut":
             A, chi = shape.coefficient_cut(phi, self.mesh.cells, self.a_in, self.a_out)
         else:
@@ -161,6 +176,8 @@ class Problem:
 
     def cost(self, u, A):
         m = self.mesh
+        if self.kind == LOGISTIC:
+            return logistic.cost(m.coords, m.cells, u)
         vol, g = fem.geometry(m.coords, m.cells)
         if self.kind == ELASTIC:
             lam, mu = fem.lame(self.E, self.nu)
@@ -176,6 +193,9 @@ class Problem:
     def rhs(self, u, A, chi, lam):
         m = self.mesh
         V = self.volume_target if self.volume_target > 0 else 1.0
+        if self.kind == LOGISTIC:      # the adjoint is a linear solve of its own (Sec. 6.4)
+            p = logistic.adjoint(m.coords, m.cells, A, self.growth_rate, u)
+            return logistic.rhs(m.coords, m.cells, A, self.growth_rate, u, p, lam, chi, V)
         if self.kind == ELASTIC:
             le, me = fem.lame(self.E, self.nu)
             return shape.elastic_rhs(m.coords, m.cells, A, u, le, me, lam, chi, V)

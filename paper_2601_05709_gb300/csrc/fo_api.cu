@@ -447,7 +447,13 @@ extern "C" fo_status fo_problem_create(fo_mesh *m, const fo_model_desc *desc, fo
   if (!m || !desc || !out) return FO_EINVAL;
   fo_ctx *ctx = m->ctx;
   *out = nullptr;
-  if (desc->kind < FO_HEAT || desc->kind > FO_HELMHOLTZ) return fo_fail(ctx, FO_EINVAL, "bad model kind");
+  if (desc->kind < FO_HEAT || desc->kind > FO_LOGISTIC) return fo_fail(ctx, FO_EINVAL, "bad model kind");
+  if (desc->kind == FO_LOGISTIC &&
+      (m->um || desc->n_inst > 0 || desc->n_cases > 1 || desc->n_volume > 0 || desc->coef_rule != FO_COEF_CENTROID ||
+       !(desc->growth_rate > 0) || !(desc->a_in > 0) || !(desc->a_out > 0)))
+    return fo_fail(ctx, FO_EINVAL,
+                   "the logistic model runs on box meshes with one load case, the one-point coefficient rule, at "
+                   "most one volume constraint, r > 0 and positive carrying capacities");
   if (desc->n_point_loads < 0 || desc->n_point_loads > 4 || desc->n_tractions < 0 || desc->n_tractions > 4 ||
       desc->n_omega0 < 0 || desc->n_omega0 > 4)
     return fo_fail(ctx, FO_EINVAL, "too many loads / subdomain boxes");
@@ -494,7 +500,8 @@ extern "C" fo_status fo_problem_create(fo_mesh *m, const fo_model_desc *desc, fo
     p->lame_mu = desc->E / (2.0 * (1.0 + desc->nu));
   }
   if (desc->kind == FO_HELMHOLTZ && !(desc->k > 0)) p->desc.k = 1.0;
-  if (desc->kind == FO_HEAT) p->desc.k = 1.0;
+  if (desc->kind == FO_HEAT || desc->kind == FO_LOGISTIC) p->desc.k = 1.0;
+  p->desc.u_init = nullptr;
   p->desc.inst_k = p->desc.inst_omega = p->desc.inst_f = nullptr;
   if (desc->n_inst > 0) {   // batch: A_e alone in coef; k_i, omega_i, f_i per instance
     p->desc.k = 1.0;
@@ -508,7 +515,17 @@ extern "C" fo_status fo_problem_create(fo_mesh *m, const fo_model_desc *desc, fo
     if (st != FO_OK) break;
   }
   ctx->problems.push_back(p);
-  if (st == FO_OK && p->f) {
+  if (st == FO_OK && p->f && desc->kind == FO_LOGISTIC) {   // f holds the initial Newton guess
+    std::vector<double> u0;
+    const double *src = desc->u_init;
+    if (!src) {
+      u0.assign((size_t)g.num_nodes, desc->a_in);
+      src = u0.data();
+    }
+    st = fo_cuda_check(ctx, cudaMemcpyAsync(p->f, src, sizeof(double) * g.num_nodes, cudaMemcpyHostToDevice,
+                                            ctx->stream), "copy u_init");
+    if (st == FO_OK) st = fo_cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "copy u_init");
+  } else if (st == FO_OK && p->f) {
     if (desc->f_nodal)
       st = fo_cuda_check(ctx, cudaMemcpyAsync(p->f, desc->f_nodal, sizeof(double) * g.num_nodes,
                                               cudaMemcpyHostToDevice, ctx->stream), "copy f");
@@ -578,7 +595,7 @@ extern "C" fo_status fo_coefficients(fo_problem *p) {
   }
   FO_TRY(fo_launch_coefficients(p));
   if (p->batch) FO_TRY(fo_batch_prepare(p));
-  else FO_TRY(fo_launch_state_diag(p));
+  else if (p->desc.kind != FO_LOGISTIC) FO_TRY(fo_launch_state_diag(p));   // logistic: rows per Newton step
   p->coef_valid = true;
   p->coef_epoch += 1;
   return FO_OK;
@@ -593,6 +610,7 @@ extern "C" fo_status fo_state_solve(fo_problem *p, const fo_solve_opts *o, fo_so
   p->ctx->last_solve_ms = 0.0;
   fo_status s;
   if (p->batch) s = fo_batch_state(p, false, o, st);
+  else if (p->desc.kind == FO_LOGISTIC) s = fo_logistic_state(p, o, st, &p->newton_steps);
   else if (p->ncases == 1) s = fo_state_pcg(p, p->load, p->u, o, st);
   else {   // one solve per load case (eq. compli_plus); statistics summed, worst residual kept
     fo_solve_stats tot;
@@ -626,6 +644,7 @@ extern "C" fo_status fo_adjoint_solve(fo_problem *p, const fo_solve_opts *o, fo_
   if (!o) o = &def;
   if (!p->coef_valid) FO_TRY(fo_coefficients(p));
   if (p->batch) return fo_batch_state(p, true, o, st);
+  if (p->desc.kind == FO_LOGISTIC) return fo_logistic_adjoint(p, o, st);
   double c = p->desc.kind == FO_ELASTIC ? -2.0 : -1.0;
   double *b = p->rhs;   // reuse the RHS buffer as the adjoint load (d*N_n >= N_dof)
   fo_solve_opts oo = *o;
@@ -743,6 +762,8 @@ extern "C" fo_status fo_shape_derivative(fo_problem *p, double lambda, double *r
   }
   if (!p->coef_valid) FO_TRY(fo_coefficients(p));
   if (p->batch) FO_TRY(fo_batch_shape_rhs(p, lambda));
+  else if (p->desc.kind == FO_LOGISTIC)
+    FO_TRY(fo_launch_logistic_shape(p, lambda, nullptr, p->desc.volume_target > 0 ? 1.0 / p->desc.volume_target : 1.0, 0));
   else if (p->mesh->um) FO_TRY(fo_umesh_shape_rhs(p, lambda));
   else FO_TRY(fo_launch_shape_rhs(p, lambda));
   p->rhs_valid = true;
@@ -1116,6 +1137,11 @@ extern "C" fo_status fo_opt_step(fo_problem *p, int iter, const fo_run_options *
   fo_status s = fo_state_solve(p, &o->state, &lg.state);
   if (s != FO_OK) return s;
   lg.ms_state_kernel = ctx->last_solve_ms;
+  if (p->desc.kind == FO_LOGISTIC) {   // the adjoint is a solve of its own (Sec. 6.4)
+    lg.newton_steps = p->newton_steps;
+    s = fo_adjoint_solve(p, &o->state, &lg.adjoint);
+    if (s != FO_OK) return s;
+  }
   FO_TRY(mark(1));
   const int nc = problem_nc(p);
   double J = 0, Cv[4] = {0, 0, 0, 0}, lv[4] = {0, 0, 0, 0};
