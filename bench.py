@@ -660,14 +660,15 @@ def bench_variants(api, ctx, stream, peaks):
 
     # the population example of Sec. 6.4 (logistic state by Newton, explicit adjoint): unit
     # square 128 x 128, r = 40, V = 0.5, B = Dtheta:Dxi + 1e4 normal penalty on H^1, Newton from
-    # 1 + 0.2 sin(6 pi x) sin(6 pi y), phi0 = cos 4pi x cos 4pi y + 0.3; run to the stopping
-    # criterion (at most 400 iterations)
+    # 1 + 0.2 sin(6 pi x) sin(6 pi y), phi0 = cos 4pi x cos 4pi y (volume fraction 1/2 = V: from
+    # designs far from the target the multiplier oscillates for hundreds of iterations, in the
+    # oracle alike); run to the stopping criterion (at most 400 iterations)
     lm = ctx.mesh_box(2, (128, 128), (0.0, 0.0), (1.0, 1.0))
     _, lc = lm.copy_out()
     prob = lm.problem(api.model_desc(api.FO_LOGISTIC, a_in=1.0, a_out=1e-2, dirichlet=[], volume=0.5,
                                      alpha_mass=0.0, normal_penalty=1e4, growth_rate=40.0,
                                      u_init=workloads.u0_logistic(lc)))
-    prob.set_levelset(workloads.phi_cos(lc))
+    prob.set_levelset(workloads.phi_cos(lc) - 0.3)
     lso = api.solve_opts(rtol=1e-12, warm_start=1, maxit=400000, precond=api.FO_PC_JACOBI)
     lro = api.run_options(dfactor=1e-2, smooth=False, state=lso, velocity=api.solve_opts(rtol=1e-12, warm_start=1,
                                                                                          precond=api.FO_PC_MG),
@@ -687,7 +688,8 @@ def bench_variants(api, ctx, stream, peaks):
     sec = time.perf_counter() - t0
     out["logistic2d_128x128_to_convergence"] = {
         "workload": "population model of Sec. 6.4 on a 128x128 Kuhn mesh of the unit square (32,768 triangles), "
-                    "r = 40, K = 1 / 1e-2, V = 0.5, Newton state (Jacobi-PCG steps), explicit adjoint",
+                    "r = 40, K = 1 / 1e-2, V = 0.5, phi0 = cos 4pi x cos 4pi y, Newton state (Jacobi-PCG "
+                    "steps), explicit adjoint",
         "iterations": it, "stopped_by_criterion": it < 400, "seconds": sec, "opt_iters_per_s": it / sec,
         "J": log.J, "C": log.C, "L": log.L,
         "newton_steps_per_iteration": float(np.mean([l.newton_steps for l in logs])),
@@ -733,8 +735,9 @@ def bench_serving(api, ctx, count):
         return api.model_desc(api.FO_ELASTIC, dirichlet=[(0, 0)], tractions=[(0, 1, vec)], alpha_mass=0.1,
                               normal_penalty=1e4)
 
-    def run(executors, prec, pace, pc=api.FO_PC_MG, subset=None):
-        srv = api.Server(ctx, executors=executors, mem_budget=8 << 30)
+    def run(executors, prec, pace, pc=api.FO_PC_MG, subset=None, share=None):
+        share = (2 if executors > 1 else 1) if share is None else share
+        srv = api.Server(ctx, executors=executors, mem_budget=8 << 30, grid_share=share)
         tickets = []
         t0 = time.perf_counter()
         for (ta, dim, n, heat, centers) in (items if subset is None else items[:subset]):
@@ -760,7 +763,7 @@ def bench_serving(api, ctx, count):
                   "message": r.message.decode(errors="replace")}
                  for i, (r, it) in enumerate(zip(res, sub_items)) if r.status not in (0, api._lib.FO_ENOCONV)]
         dofit = sum(r.dofs * (r.state.operator_applies + r.adjoint.operator_applies) for r in res)
-        return {"executors": executors, "precision": "mixed" if prec == api.FO_MIXED else "fp64",
+        return {"executors": executors, "grid_share": share, "precision": "mixed" if prec == api.FO_MIXED else "fp64",
                 "preconditioner": "multigrid" if pc == api.FO_PC_MG else "jacobi",
                 "seconds": wall, "requests_per_s": len(res) / wall,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
@@ -769,7 +772,10 @@ def bench_serving(api, ctx, count):
                 **({"failures_first_5": fails[:5]} if fails else {})}
 
     # every request size has a multigrid hierarchy (non-nested levels where n does not halve)
+    # 8 executors whose persistent launches take half the co-resident blocks each (grid share 2),
+    # so that two large solves run side by side; beside it the same with whole-GPU grids
     served = run(8, api.FO_FP64, True)                          # FP64 CG, multigrid, 8 executors
+    served_share1 = run(8, api.FO_FP64, True, share=1)
     served_mixed = run(8, api.FO_MIXED, True)                   # FP32 CG + FP64 refinement states
     serial_mg = run(1, api.FO_FP64, True)                       # the plain FP64 path, one at a time
     sub = min(count, 12)
@@ -777,7 +783,8 @@ def bench_serving(api, ctx, count):
     served_sub = run(8, api.FO_FP64, True, subset=sub)
     return {"sample": f"first {count} requests of the seeded stream (of 2,000)",
             "sizes_first_12": [f"{d}D n={n} {'heat' if h else 'elastic'}" for (_, d, n, h, _) in items[:12]],
-            "served": served, "served_mixed": served_mixed, "serial_fp64": serial_mg,
+            "served": served, "served_whole_gpu_grids": served_share1, "served_mixed": served_mixed,
+            "serial_fp64": serial_mg,
             "throughput_ratio_served_vs_serial": served["requests_per_s"] / serial_mg["requests_per_s"],
             "throughput_ratio_served_mixed_vs_serial": served_mixed["requests_per_s"] / serial_mg["requests_per_s"],
             "first_12": {"served": served_sub, "serial_jacobi_fp64": serial_jacobi,

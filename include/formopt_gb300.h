@@ -274,6 +274,15 @@ FO_API const char *fo_last_error(const fo_ctx *ctx);
 FO_API fo_status fo_ctx_memory(const fo_ctx *ctx, size_t *bytes_in_use);
 /* Turn per-phase device timing of fo_opt_step on (1) or off (0). */
 FO_API fo_status fo_ctx_set_timing(fo_ctx *ctx, int on);
+/* Size this context's persistent solver launches (the grid-synchronised CG, multigrid CG and
+ * Krylov kernels) for at most 1/share of the blocks the device can hold co-resident (1, the
+ * default: all of them), so that launches of other contexts running at the same time find
+ * room beside them on every SM.  A latency-bound solve loses little from the smaller grid and
+ * two of them overlap almost perfectly (measured: two 3D cantilever state solves in 61 ms at
+ * share 2 against 100 ms one after the other at share 1).  Results depend on the grid (the
+ * order of the block sums), so a problem solved at two settings agrees to rounding only.
+ * share in [1, 16]. */
+FO_API fo_status fo_ctx_set_grid_share(fo_ctx *ctx, int share);
 /* Number of kernels this library has launched in the process so far (all contexts). */
 FO_API fo_status fo_launch_count(unsigned long long *out);
 /* With timing on (fo_ctx_set_timing): device time in ms of the persistent CG launch(es) of
@@ -465,6 +474,8 @@ typedef struct {
   int queue_capacity;       /* queued requests before fo_submit says FO_EBUSY (4096)    */
   double dry_run_ms;        /* > 0: executors sleep this long instead of any device    */
                             /* work (tests of queueing and admission without a GPU)     */
+  int grid_share;           /* fo_ctx_set_grid_share of every executor's context        */
+                            /* (default 2: two large solves share the SMs)              */
 } fo_server_opts;
 
 typedef struct {

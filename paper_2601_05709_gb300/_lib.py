@@ -79,7 +79,7 @@ class Result(C.Structure):
 
 class ServerOpts(C.Structure):
     _fields_ = [("executors", C.c_int), ("mem_budget", C.c_size_t), ("queue_capacity", C.c_int),
-                ("dry_run_ms", C.c_double)]
+                ("dry_run_ms", C.c_double), ("grid_share", C.c_int)]
 
 
 class ServerStats(C.Structure):
@@ -128,6 +128,7 @@ PROTOTYPES = {
     "fo_ctx_memory": (ST, [VP, C.POINTER(C.c_size_t)]),
     "fo_ctx_sync": (ST, [VP]),
     "fo_ctx_set_timing": (ST, [VP, C.c_int]),
+    "fo_ctx_set_grid_share": (ST, [VP, C.c_int]),
     "fo_ctx_solve_kernel_ms": (ST, [VP, DP]),
     "fo_launch_count": (ST, [C.POINTER(C.c_ulonglong)]),
     "fo_mesh_box": (ST, [VP, C.c_int, C.POINTER(C.c_int), DP, DP, C.POINTER(VP)]),

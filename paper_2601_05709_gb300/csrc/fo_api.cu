@@ -153,6 +153,13 @@ extern "C" fo_status fo_ctx_set_timing(fo_ctx *ctx, int on) {
   return FO_OK;
 }
 
+extern "C" fo_status fo_ctx_set_grid_share(fo_ctx *ctx, int share) {
+  if (!ctx) return FO_EINVAL;
+  if (share < 1 || share > 16) return fo_fail(ctx, FO_EINVAL, "grid share must be in [1, 16]");
+  ctx->grid_share = share;
+  return FO_OK;
+}
+
 extern "C" fo_status fo_ctx_solve_kernel_ms(const fo_ctx *ctx, double *ms) {
   if (!ctx || !ms) return FO_EINVAL;
   *ms = ctx->last_solve_ms;

@@ -30,6 +30,8 @@ struct fo_ctx {
   // with timing on: device time of the last persistent multigrid solve launch alone
   cudaEvent_t ev_solve[2] = {};
   double last_solve_ms = 0.0;
+  // persistent launches take at most 1/grid_share of the co-resident block slots
+  int grid_share = 1;
 };
 
 // Structured Kuhn grid: everything a kernel needs to enumerate nodes and elements.

@@ -40,13 +40,14 @@ fo_status fo_scratch(fo_problem *p, size_t bytes, void **out) {
 }
 
 // Grid of a persistent kernel: enough blocks to cover `work` items (one per thread), at
-// most what fits co-resident on the device.
+// most what fits co-resident on the device (divided by the context's grid share).
 fo_status fo_cooperative_grid(fo_problem *p, const void *kernel, int block, size_t smem, long long work,
                               int requested, int *grid) {
   int per_sm = 0;
   FO_CU(p->ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem));
   if (per_sm < 1) return fo_fail(p->ctx, FO_ECUDA, "persistent kernel does not fit on an SM");
   long long cap = (long long)per_sm * p->ctx->num_sms;
+  if (p->ctx->grid_share > 1) cap = std::max(1LL, cap / p->ctx->grid_share);
   long long want = requested > 0 ? requested : (work + block - 1) / block;
   if (want > cap) want = cap;
   if (want > 4096) want = 4096;

@@ -62,6 +62,7 @@ extern "C" void fo_server_opts_default(fo_server_opts *o) {
   o->mem_budget = (size_t)8 << 30;
   o->queue_capacity = 4096;
   o->dry_run_ms = 0.0;
+  o->grid_share = 2;
 }
 
 extern "C" size_t fo_request_device_bytes(const fo_request *rq) {
@@ -133,6 +134,7 @@ static void run_request(fo_ctx *ctx, Job *j) {
 static void executor(fo_server *s) {
   fo_ctx *ctx = nullptr;
   if (s->o.dry_run_ms <= 0.0 && fo_ctx_create(s->device, nullptr, 0, &ctx) != FO_OK) ctx = nullptr;
+  if (ctx) fo_ctx_set_grid_share(ctx, s->o.grid_share);
   for (;;) {
     Job *j = nullptr;
     {
@@ -181,7 +183,8 @@ extern "C" fo_status fo_server_create(fo_ctx *ctx, const fo_server_opts *opts, f
   fo_server_opts_default(&o);
   if (opts) o = *opts;
   if (!ctx && !(o.dry_run_ms > 0.0)) return FO_EINVAL;
-  if (o.executors < 1 || o.executors > 256 || o.queue_capacity < 1 || o.mem_budget == 0)
+  if (o.executors < 1 || o.executors > 256 || o.queue_capacity < 1 || o.mem_budget == 0 || o.grid_share < 1 ||
+      o.grid_share > 16)
     return ctx ? fo_fail(ctx, FO_EINVAL, "bad server options") : FO_EINVAL;
   fo_server *s = new fo_server();
   s->o = o;

@@ -170,3 +170,22 @@ def test_concurrent_multigrid_requests_of_distinct_sizes(ctx, prec):
         (rq_a,), (r_a,), _ = serve([items[k]], 1)
         assert (res[k].J, res[k].C, res[k].Btt) == (r_a.J, r_a.C, r_a.Btt), items[k][:3]
         assert np.array_equal(reqs[k].theta, rq_a.theta)
+
+
+def test_grid_share_agrees_with_full_grid(ctx):
+    """A context whose persistent launches take half the co-resident blocks solves the same
+    system to the solve tolerance (the grid changes only the order of the block sums)."""
+    c2 = api.Context(0)
+    c2.set_grid_share(2)
+    out = []
+    for c in (ctx, c2):
+        mesh = c.mesh_box(3, (24, 12, 12), (0.0, 0.0, 0.0), (2.0, 1.0, 1.0))
+        _, coords = mesh.copy_out()
+        prob = mesh.problem(_desc(FO_ELASTIC, 3))
+        prob.set_levelset(workloads.phi_bumps(coords, workloads.bump_centres((0, 0, 0), (2, 1, 1), 6, seed=3), 0.2, 0.2))
+        st = prob.state_solve(api.solve_opts(rtol=1e-12, precond=api.FO_PC_MG))
+        out.append((prob.get(api.FO_FIELD_U), st.iterations))
+    assert close_scaled(out[1][0], out[0][0], 1e-10)
+    with pytest.raises(api.FormoptError):
+        c2.set_grid_share(0)
+    c2.close()
