@@ -736,7 +736,7 @@ def bench_serving(api, ctx, count):
                               normal_penalty=1e4)
 
     def run(executors, prec, pace, pc=api.FO_PC_MG, subset=None, share=None):
-        share = (2 if executors > 1 else 1) if share is None else share
+        share = (4 if executors > 1 else 1) if share is None else share
         srv = api.Server(ctx, executors=executors, mem_budget=8 << 30, grid_share=share)
         tickets = []
         t0 = time.perf_counter()
@@ -772,8 +772,8 @@ def bench_serving(api, ctx, count):
                 **({"failures_first_5": fails[:5]} if fails else {})}
 
     # every request size has a multigrid hierarchy (non-nested levels where n does not halve)
-    # 8 executors whose persistent launches take half the co-resident blocks each (grid share 2),
-    # so that two large solves run side by side; beside it the same with whole-GPU grids
+    # 8 executors whose persistent launches take a quarter of the co-resident blocks each (grid
+    # share 4), so that large solves run side by side; beside it the same with whole-GPU grids
     served = run(8, api.FO_FP64, True)                          # FP64 CG, multigrid, 8 executors
     served_share1 = run(8, api.FO_FP64, True, share=1)
     served_mixed = run(8, api.FO_MIXED, True)                   # FP32 CG + FP64 refinement states

@@ -475,7 +475,7 @@ typedef struct {
   double dry_run_ms;        /* > 0: executors sleep this long instead of any device    */
                             /* work (tests of queueing and admission without a GPU)     */
   int grid_share;           /* fo_ctx_set_grid_share of every executor's context        */
-                            /* (default 2: two large solves share the SMs)              */
+                            /* (default 4: up to four large solves share the SMs)       */
 } fo_server_opts;
 
 typedef struct {

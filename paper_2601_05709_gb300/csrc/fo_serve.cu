@@ -62,7 +62,7 @@ extern "C" void fo_server_opts_default(fo_server_opts *o) {
   o->mem_budget = (size_t)8 << 30;
   o->queue_capacity = 4096;
   o->dry_run_ms = 0.0;
-  o->grid_share = 2;
+  o->grid_share = 4;
 }
 
 extern "C" size_t fo_request_device_bytes(const fo_request *rq) {
