@@ -343,7 +343,14 @@ def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True):
             "max_rel_residual": float(res.max()),
             "gdof_iters_per_s": nfree * float(its.sum()) / dt / 1e9}
     # batched CG with a per-instance FP32 multigrid V-cycle: FP64 refinement around an FP32 CG
-    # (mixed), and FP64 CG; the first call builds the hierarchy
+    # (mixed), and FP64 CG, each under the schedule its autotuner picks
+    mg_tune = {}
+    for prec, name in ((api.FO_MIXED, "mixed"), (api.FO_FP64, "fp64")):
+        r = prob.batch_mg_autotune(prec, 1e-8)
+        mg_tune[name] = {"blocks_per_sm": r.blocks_per_sm, "finest_level_sweeps": r.nu0,
+                         "per_instance_levels": r.inst_levels, "tile": list(r.tile), "tuning_solve_ms": r.ms,
+                         "iterations": r.iterations, "candidates": r.candidates}
+    out["multigrid_autotune"] = mg_tune
     for prec, name in ((api.FO_MIXED, "mixed"), (api.FO_FP64, "fp64")):
         om_mg = api.solve_opts(precision=prec, rtol=1e-8, inner_rtol=1e-3, maxit=2000, inner_maxit=1000,
                                precond=api.FO_PC_MG)

@@ -431,6 +431,30 @@ typedef struct {
  * by later solves whose opts->grid_blocks is 0; the first such solve tunes by itself. */
 FO_API fo_status fo_batch_autotune(fo_problem *prob, int precision, fo_tune_result *out);
 
+/* Schedule of the batched multigrid (FO_PC_MG). */
+typedef struct {
+  int blocks_per_sm;        /* co-resident blocks per SM; grid = blocks_per_sm * SMs   */
+  int nu0;                  /* smoothing sweeps before and after the coarse correction */
+                            /* on the finest level                                      */
+  int inst_levels;          /* coarse levels run one instance per block in shared memory */
+  double ms;                /* the chosen schedule's solve time (CUDA events)           */
+  int iterations;           /* its Krylov iterations (inner ones for FO_MIXED)          */
+  int candidates;           /* schedules timed                                          */
+  int tile[3];              /* nodes per FP32-pass tile along x, y, z (fixed per        */
+                            /* dimension and batch width; a 16x16 2D tile at one block  */
+                            /* per SM measured 22-28 % slower than 16x8 at two)         */
+} fo_mg_tune_result;
+/* Time the batched multigrid's schedules on this problem for `precision` (FO_FP64 or FO_MIXED):
+ * blocks per SM from one to the kernel's co-residency limit, one or two finest-level sweeps,
+ * and the per-instance levels from the size limit or one level later.  Each candidate solves
+ * the current system from zero to rtol into a scratch solution (the problem's fields are not
+ * touched); the fastest one that converges is kept and used by later multigrid solves whose
+ * opts->grid_blocks is 0 (a schedule changes the iteration count, not the stopping test).
+ * Untuned problems use two blocks per SM, one finest-level sweep and the size limit.  The
+ * schedule changes the order of the block sums, so results of a tuned and an untuned problem
+ * agree to rounding only. */
+FO_API fo_status fo_batch_mg_autotune(fo_problem *prob, int precision, double rtol, fo_mg_tune_result *out);
+
 /* --------------------------------------------------------------- serving ----- */
 /* A request is one Algorithm-1 step without the transport (state solve, explicit adjoint
  * solve, cost and constraint, shape derivative, velocity) on its own box mesh.  A server

@@ -46,6 +46,11 @@ class ModelDesc(C.Structure):
                 ("newton_atol", C.c_double), ("newton_maxit", C.c_int)]
 
 
+class MgTuneResult(C.Structure):
+    _fields_ = [("blocks_per_sm", C.c_int), ("nu0", C.c_int), ("inst_levels", C.c_int), ("ms", C.c_double),
+                ("iterations", C.c_int), ("candidates", C.c_int), ("tile", C.c_int * 3)]
+
+
 class TuneResult(C.Structure):
     _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("us_per_iteration", C.c_double),
                 ("candidates", C.c_int), ("tile", C.c_int * 3)]
@@ -173,6 +178,7 @@ PROTOTYPES = {
     "fo_batch_costs": (ST, [VP, DP]),
     "fo_batch_solve_info": (ST, [VP, C.POINTER(C.c_int), DP]),
     "fo_batch_autotune": (ST, [VP, C.c_int, C.POINTER(TuneResult)]),
+    "fo_batch_mg_autotune": (ST, [VP, C.c_int, C.c_double, C.POINTER(MgTuneResult)]),
     "fo_ppl_init": (None, [C.POINTER(PPLState), C.c_int]),
     "fo_ppl_update": (None, [C.POINTER(PPLState), DP, C.c_double, DP, DP]),
     "fo_adaptime": (None, [C.c_double, C.POINTER(RunOptions), DP, C.POINTER(C.c_int)]),

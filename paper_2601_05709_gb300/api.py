@@ -355,6 +355,12 @@ class Problem:
         self._chk(self.lib.fo_batch_autotune(self.handle, precision, C.byref(r)), "fo_batch_autotune")
         return r
 
+    def batch_mg_autotune(self, precision=_lib.FO_MIXED, rtol=1e-8):
+        r = _lib.MgTuneResult()
+        self._chk(self.lib.fo_batch_mg_autotune(self.handle, precision, float(rtol), C.byref(r)),
+                  "fo_batch_mg_autotune")
+        return r
+
     def _field_len(self, field):
         m = self.mesh
         if field in (FO_FIELD_U, FO_FIELD_P, FO_FIELD_LOAD):

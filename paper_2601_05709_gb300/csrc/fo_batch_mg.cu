@@ -1460,7 +1460,12 @@ __global__ void k_bmg_coarse_inverse(Grid g, const double *WK, const double *WM,
 
 // ===================================================================================== host
 struct fo_bmg {
-  int L = 0, nip = 0, grid_cap = 0;
+  int L = 0, nip = 0, grid_cap = 0, per_sm = 0;
+  int Lg0 = 0;                // first level run one instance per block (from the size limits)
+  // schedule chosen by fo_batch_mg_autotune per precision (index 1: FO_MIXED; tuned = 0: the
+  // defaults: grid_cap blocks, one finest-level sweep, per-instance levels from Lg0)
+  int tuned[2] = {0, 0}, t_bpsm[2] = {0, 0}, t_nu0[2] = {1, 1}, t_lgshift[2] = {0, 0};
+  int up_pi = -1;             // precision index of the uploaded level table (-1: none)
   long long built_epoch = -1;
   Grid g[MG_MAX_LEVELS];
   double *coef[MG_MAX_LEVELS] = {}, *WK[MG_MAX_LEVELS] = {}, *WM[MG_MAX_LEVELS] = {};
@@ -1522,6 +1527,7 @@ static fo_status bmg_alloc(fo_problem *p) {
     per_sm = std::min(per_sm, v);
   }
   if (per_sm < 1) return fo_fail(ctx, FO_ECUDA, "batched multigrid kernel does not fit on an SM");
+  mg->per_sm = per_sm;
   mg->grid_cap = std::min(per_sm * ctx->num_sms, 4096);
   auto add = [&](void **ptr, size_t bytes) { mg->allocs.push_back({ptr, bytes}); };
   for (int l = 0; l < mg->L; ++l) {
@@ -1559,6 +1565,47 @@ static fo_status bmg_alloc(fo_problem *p) {
   return FO_OK;
 }
 
+// The level table with the current schedule: one sweep before and after the coarse correction
+// on the finest level (its passes carry nearly all the traffic; 104 instead of 100 iterations
+// on the 64-instance 512x512 batch, 13 % less time per solve) unless tuned otherwise, two on
+// the coarser ones; per-instance levels from Lg0, or one level later when tuned so.
+static fo_status bmg_upload(fo_problem *p, int pi) {
+  fo_ctx *ctx = p->ctx;
+  fo_batch *bt = p->batch;
+  fo_bmg *mg = bt->mg;
+  BmgDev h;
+  memset(&h, 0, sizeof h);
+  h.L = mg->L;
+  h.Lg = mg->Lg0;
+  if (mg->tuned[pi] && mg->t_lgshift[pi] > 0 && mg->Lg0 + mg->t_lgshift[pi] < mg->L) h.Lg = mg->Lg0 + mg->t_lgshift[pi];
+  h.nu0 = mg->tuned[pi] ? mg->t_nu0[pi] : 1;
+  h.nu = 2;
+  h.nuc = 16;
+  h.omega = 0.8f;
+  if (mg->nd > 0 && h.Lg < h.L) {
+    h.nd = mg->nd;
+    h.ainv = mg->ainv;
+    h.direct = mg->direct;
+  }
+  for (int l = 0; l < mg->L; ++l) {
+    BmgLevel &d = h.lv[l];
+    d.g = mg->g[l];
+    d.SK = mg->SK[l];
+    d.SM = mg->SM[l];
+    d.dir = l == 0 ? p->dir : mg->dir[l];
+    d.b = mg->b[l];
+    d.z[0] = mg->z0[l];
+    d.z[1] = mg->z1[l];
+    d.t = mg->t[l];
+  }
+  mg->host.resize(sizeof(BmgDev));
+  memcpy(mg->host.data(), &h, sizeof(BmgDev));
+  FO_CU(ctx, cudaMemcpyAsync(mg->dev, mg->host.data(), sizeof(BmgDev), cudaMemcpyHostToDevice, ctx->stream));
+  FO_CU(ctx, cudaGetLastError());
+  mg->up_pi = pi;
+  return FO_OK;
+}
+
 // Rows of every level from the current coefficients (the batch's fine FP64 rows are rebuilt
 // by every coefficient update; coarse levels from children-mean coefficients).
 static fo_status bmg_prepare(fo_problem *p) {
@@ -1582,31 +1629,21 @@ static fo_status bmg_prepare(fo_problem *p) {
                                                                                       mg->SK[l], mg->SM[l]);
     fo_note_launch(1);
   }
-  BmgDev h;
-  memset(&h, 0, sizeof h);
-  h.L = mg->L;
   // levels from Lg down run one instance per block in shared memory: small enough, and their
   // vectors (b, z0, z1, t of every such level) fit in the kernel's dynamic shared memory
-  h.Lg = mg->L;
+  mg->Lg0 = mg->L;
   {
     const size_t cap = bmg_kernel(mg->g[0].dim, bt->nip / 32, false).smem;
     for (int l = 0; l < mg->L; ++l) {
       size_t need = 0;
       for (int m = l; m < mg->L; ++m) need += 16 * (size_t)mg->g[m].num_nodes;
       if (mg->g[l].num_nodes <= BMG_INST_NODES && need <= cap) {
-        h.Lg = l;
+        mg->Lg0 = l;
         break;
       }
     }
   }
-  // one sweep before and after the coarse correction on the finest level (its passes carry
-  // nearly all the traffic), two on the coarser ones: 104 instead of 100 iterations on the
-  // 64-instance 512x512 batch, 13 % less time per solve
-  h.nu0 = 1;
-  h.nu = 2;
-  h.nuc = 16;
-  h.omega = 0.8f;
-  if (mg->nd > 0 && h.Lg < h.L) {   // the coarsest level runs in the per-instance cycle
+  if (mg->nd > 0 && mg->Lg0 < mg->L) {   // the coarsest level runs in the per-instance cycle
     const int L1 = mg->L - 1;
     const double *WK = L1 == 0 ? bt->WK : mg->WK[L1], *WM = L1 == 0 ? bt->WM : mg->WM[L1];
     if (mg->g[0].dim == 2)
@@ -1614,25 +1651,8 @@ static fo_status bmg_prepare(fo_problem *p) {
     else
       k_bmg_coarse_inverse<3><<<bt->nip, 256, 0, s>>>(mg->g[L1], WK, WM, bt->kk, bt->w2, mg->nd, mg->ainv, mg->direct);
     fo_note_launch(1);
-    h.nd = mg->nd;
-    h.ainv = mg->ainv;
-    h.direct = mg->direct;
   }
-  for (int l = 0; l < mg->L; ++l) {
-    BmgLevel &d = h.lv[l];
-    d.g = mg->g[l];
-    d.SK = mg->SK[l];
-    d.SM = mg->SM[l];
-    d.dir = l == 0 ? p->dir : mg->dir[l];
-    d.b = mg->b[l];
-    d.z[0] = mg->z0[l];
-    d.z[1] = mg->z1[l];
-    d.t = mg->t[l];
-  }
-  mg->host.resize(sizeof(BmgDev));
-  memcpy(mg->host.data(), &h, sizeof(BmgDev));
-  FO_CU(ctx, cudaMemcpyAsync(mg->dev, mg->host.data(), sizeof(BmgDev), cudaMemcpyHostToDevice, s));
-  FO_CU(ctx, cudaGetLastError());
+  mg->up_pi = -1;   // the level table is uploaded by the solve, for its precision
   mg->built_epoch = p->coef_epoch;
   return FO_OK;
 }
@@ -1645,7 +1665,10 @@ fo_status fo_batch_state_mg(fo_problem *p, const double *B, double bscale, doubl
   fo_bmg *mg = bt->mg;
   const Grid &g = p->mesh->g;
   const int nip = bt->nip;
-  long long grid = o->grid_blocks > 0 ? o->grid_blocks : mg->grid_cap;
+  const int pi = o->precision == FO_MIXED ? 1 : 0;
+  if (mg->up_pi != pi) FO_TRY(bmg_upload(p, pi));
+  long long grid = o->grid_blocks > 0 ? o->grid_blocks
+                                      : (mg->tuned[pi] ? (long long)mg->t_bpsm[pi] * ctx->num_sms : mg->grid_cap);
   grid = std::min(grid, (long long)mg->grid_cap);
   grid = std::min(grid, (g.num_nodes + BMG_WARPS - 1) / BMG_WARPS);
   grid = std::max(grid, 1LL);
@@ -1690,4 +1713,110 @@ fo_status fo_batch_state_mg(fo_problem *p, const double *B, double bscale, doubl
   fo_status r = fo_batch_read(p, &s, o);
   if (st) *st = s;
   return r;
+}
+
+// FP32-pass tile of the batched multigrid kernels for a dimension and batch width.
+template <int D, int NJ>
+static void bmg_tile_of(int tile[3]) {
+  using TL = typename BmgTiles<D, NJ>::T32;
+  tile[0] = TL::TX;
+  tile[1] = TL::TY;
+  tile[2] = TL::TZ;
+}
+
+// Schedule autotuner of the batched multigrid: every candidate (blocks per SM from 1 to the
+// kernel's co-residency limit, one or two smoothing sweeps on the finest level, per-instance
+// levels from the size limit or one level later) solves the batch's current system from zero to
+// rtol into a scratch solution, timed with CUDA events on the context stream; the fastest one
+// that converges is kept (a schedule changes the iteration count, not the accuracy: every
+// candidate stops on the same FP64 residual test).
+extern "C" fo_status fo_batch_mg_autotune(fo_problem *p, int precision, double rtol, fo_mg_tune_result *out) {
+  if (!p || (precision != FO_FP64 && precision != FO_MIXED) || !(rtol > 0)) return FO_EINVAL;
+  if (!p->batch) return fo_fail(p->ctx, FO_EINVAL, "not a batch problem");
+  fo_ctx *ctx = p->ctx;
+  fo_batch *bt = p->batch;
+  const Grid &g = p->mesh->g;
+  if (!fo_mg_applicable(g, 1, false))
+    return fo_fail(ctx, FO_EINVAL, "the batched multigrid needs a grid that halves");
+  if (!p->coef_valid) FO_TRY(fo_coefficients(p));
+  FO_TRY(bmg_prepare(p));
+  fo_bmg *mg = bt->mg;
+  const size_t nx = (size_t)g.num_nodes * bt->nip;
+  double *X;
+  FO_TRY(fo_alloc(ctx, (void **)&X, sizeof(double) * nx));
+  fo_solve_opts o;
+  fo_solve_opts_default(&o);
+  o.precision = precision;
+  o.precond = FO_PC_MG;
+  o.rtol = rtol;
+  o.maxit = 5000;
+  o.inner_rtol = 1e-3;
+  o.inner_maxit = 1000;
+  cudaEvent_t e0, e1;
+  FO_CU(ctx, cudaEventCreate(&e0));
+  FO_CU(ctx, cudaEventCreate(&e1));
+  const int shifts = (mg->Lg0 + 1 < mg->L) ? 2 : 1;
+  int best_b = 0, best_nu = 1, best_sh = 0, best_it = 0, cand = 0;
+  double best = INFINITY;
+  fo_status st = FO_OK;
+  for (int b = 1; b <= mg->per_sm && st == FO_OK; ++b)
+    for (int nu = 1; nu <= 2 && st == FO_OK; ++nu)
+      for (int sh = 0; sh < shifts && st == FO_OK; ++sh) {
+        const int pi = precision == FO_MIXED ? 1 : 0;
+        mg->tuned[pi] = 1;
+        mg->t_bpsm[pi] = b;
+        mg->t_nu0[pi] = nu;
+        mg->t_lgshift[pi] = sh;
+        mg->up_pi = -1;   // the solve uploads the candidate's table
+        float ms = 0.f;
+        fo_solve_stats s;
+        bool conv = true;
+        for (int rep = 0; rep < 2 && st == FO_OK && conv; ++rep) {   // the first run warms the caches
+          FO_CU(ctx, cudaMemsetAsync(X, 0, sizeof(double) * nx, ctx->stream));
+          FO_CU(ctx, cudaEventRecord(e0, ctx->stream));
+          const fo_status r = fo_batch_state_mg(p, bt->B, 1.0, X, &o, 0, &s);
+          FO_CU(ctx, cudaEventRecord(e1, ctx->stream));
+          if (r == FO_ENOCONV) conv = false;               // this schedule does not converge
+          else st = r;
+        }
+        if (st != FO_OK) break;
+        if (!conv) continue;
+        FO_CU(ctx, cudaEventSynchronize(e1));
+        FO_CU(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        ++cand;
+        if (ms < best) {
+          best = ms;
+          best_b = b;
+          best_nu = nu;
+          best_sh = sh;
+          best_it = s.iterations;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  fo_free(ctx, X, sizeof(double) * nx);
+  if (st == FO_OK && cand == 0) st = fo_fail(ctx, FO_ENOCONV, "no schedule of the batched multigrid converged");
+  const int pi = precision == FO_MIXED ? 1 : 0;
+  mg->up_pi = -1;
+  if (st != FO_OK) {
+    mg->tuned[pi] = 0;
+    return st;
+  }
+  mg->tuned[pi] = 1;
+  mg->t_bpsm[pi] = best_b;
+  mg->t_nu0[pi] = best_nu;
+  mg->t_lgshift[pi] = best_sh;
+  if (out) {
+    memset(out, 0, sizeof *out);
+    out->blocks_per_sm = best_b;
+    out->nu0 = best_nu;
+    out->inst_levels = mg->L - std::min(mg->Lg0 + best_sh, mg->L);
+    out->ms = best;
+    out->iterations = best_it;
+    out->candidates = cand;
+    const int nj = bt->nip / 32;
+    if (g.dim == 2) nj == 1 ? bmg_tile_of<2, 1>(out->tile) : (nj == 2 ? bmg_tile_of<2, 2>(out->tile) : bmg_tile_of<2, 4>(out->tile));
+    else nj == 1 ? bmg_tile_of<3, 1>(out->tile) : (nj == 2 ? bmg_tile_of<3, 2>(out->tile) : bmg_tile_of<3, 4>(out->tile));
+  }
+  return FO_OK;
 }

@@ -136,6 +136,31 @@ def test_batch_instance_equals_alone(ctx, precision):
         assert np.array_equal(ui, U[:, i]), (i, np.max(np.abs(ui - U[:, i])))
 
 
+@pytest.mark.parametrize("name", ["2d_mg_40", "3d_mg_5"])
+@pytest.mark.parametrize("precision", [api.FO_FP64, api.FO_MIXED])
+def test_batch_multigrid_autotuned_schedule(ctx, name, precision):
+    """The schedule autotuner times its candidates on scratch data (the problem's fields are not
+    touched) and keeps a converging one; solves under it still meet the oracle."""
+    c, ob, prob, phi = _setup(ctx, name)
+    prob.coefficients()
+    before = prob.get(FO_FIELD_U).copy()
+    r = prob.batch_mg_autotune(precision, 1e-8)
+    assert np.array_equal(prob.get(FO_FIELD_U), before)
+    assert r.candidates >= 2 and 1 <= r.blocks_per_sm <= 4 and r.nu0 in (1, 2) and r.iterations > 0, (
+        r.candidates, r.blocks_per_sm, r.nu0, r.iterations)
+    assert r.tile[0] >= 2 and r.tile[1] >= 2
+    rtol = 1e-12 if precision == api.FO_FP64 else 1e-10
+    prob.state_solve(api.solve_opts(precision=precision, rtol=rtol, precond=api.FO_PC_MG))
+    U = prob.get(FO_FIELD_U)
+    U_ref, A, _ = ob.state(phi)
+    its, res = prob.batch_solve_info()
+    assert np.all(res <= rtol), res
+    F = ob.loads()
+    free = ob.problem(0).dirichlet() == 0
+    for i in range(c["n_inst"]):
+        assert_solve_parity(_K(ob, i, A), F[:, i], free, U[:, i], U_ref[:, i], 1e2 * rtol, omega_max=10 * rtol)
+
+
 @pytest.mark.parametrize("name", list(MG_CASES) + ["2d_5"])
 @pytest.mark.parametrize("precision", [api.FO_FP64, api.FO_MIXED])
 def test_batch_state_multigrid_parity(ctx, name, precision):
