@@ -251,19 +251,25 @@ static int mg_direct_unknowns(const Grid *g, int L, int npn) {
 int fo_mg_plan(const Grid &g0, Grid *g, int max_levels, long long stop_unknowns, int npn, bool general) {
   g[0] = g0;
   int L = 1;
+  bool halved = false;
   while (L < max_levels) {
     const Grid &f = g[L - 1];
     if (stop_unknowns > 0 && f.num_nodes * npn <= stop_unknowns) break;
     int n[3] = {1, 1, 1};
     bool ok = true, even = true;
     for (int a = 0; a < f.dim; ++a) even = even && f.n[a] % 2 == 0 && f.n[a] / 2 >= 2;
+    // halve while every axis halves; otherwise (general) ceil(n/2) cells per axis -- except
+    // below a hierarchy that already reached the block-run size by halving: there the block's
+    // smoothing sweeps on its coarsest level cost less than the non-nested transfers' point
+    // location (3D cantilever 96x48x48: 6x3x3 -> 3x2x2 made each CG iteration 50 % slower)
+    if (!even && general && halved && f.num_nodes * npn <= MG_BLOCK_DOFS) ok = false;
     for (int a = 0; a < f.dim; ++a) {
-      // halve while every axis halves; otherwise (general) ceil(n/2) cells per axis
       n[a] = even ? f.n[a] / 2 : (f.n[a] + 1) / 2;
       if (!even && (!general || f.n[a] < 3)) ok = false;
     }
     if (!ok) break;
     if (!fo_grid_make(f.dim, n, f.lo, f.hi, g[L])) break;
+    halved = halved || even;
     ++L;
   }
   return L;

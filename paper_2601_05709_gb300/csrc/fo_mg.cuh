@@ -178,48 +178,55 @@ struct MgOps {
     if (L.Wh) residual_with(oph(L), L, z, first, step);
     else residual_with(op(L), L, z, first, step);
   }
+  // the gather of restrict_ between non-nested grids, out of line: the nested transfers are the
+  // hot path, and the general ones (integer point location per fine node) would otherwise
+  // be inlined into every caller of the persistent kernel
+  static __device__ __noinline__ void restrict_general(const MgLevelDev &F, const MgLevelDev &C, float omega,
+                                                       long long first, long long step) {
+    for (long long c = first; c < C.g.num_nodes; c += step) {
+      int ic[3];
+      node_ijk(C.g, c, ic);
+      int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const long long nf = F.g.n[k], ncs = C.g.n[k];
+        // the coarse hat of c lives on coarse coordinates (c - 1, c + 1) along each axis
+        lo[k] = ic[k] == 0 ? 0 : (int)(((long long)(ic[k] - 1) * nf + ncs - 1) / ncs);
+        hi[k] = (int)std::min(nf, ((long long)(ic[k] + 1) * nf) / ncs);
+      }
+      float v[NPN];
+#pragma unroll
+      for (int j = 0; j < NPN; ++j) v[j] = 0.f;
+      for (int i2 = lo[2]; i2 <= (D == 3 ? hi[2] : 0); ++i2)
+        for (int i1 = lo[1]; i1 <= hi[1]; ++i1)
+          for (int i0 = lo[0]; i0 <= hi[0]; ++i0) {
+            const int ifn[3] = {i0, i1, i2};
+            long long vert[D + 1];
+            float w[D + 1];
+            mg_interp<D>(F.g, C.g, ifn, vert, w);
+            float wc = 0.f;
+#pragma unroll
+            for (int m = 0; m <= D; ++m)
+              if (vert[m] == c) wc = w[m];
+            if (wc == 0.f) continue;
+            const long long f = i0 + F.g.stride[1] * i1 + (D == 3 ? F.g.stride[2] * i2 : 0);
+#pragma unroll
+            for (int j = 0; j < NPN; ++j) v[j] = fmaf(wc, F.t[f * NPN + j], v[j]);
+          }
+#pragma unroll
+      for (int j = 0; j < NPN; ++j) {
+        const long long k = c * NPN + j;
+        const float bk = C.dir[k] ? 0.f : v[j];
+        C.b[k] = bk;
+        C.z[0][k] = omega * C.dinv[k] * bk;
+      }
+    }
+  }
   // coarse b = P^T t (fine residual), and the coarse level's first sweep from zero
   static __device__ void restrict_(const MgLevelDev &F, const MgLevelDev &C, float omega, long long first,
                                    long long step) {
     if (!mg_nested(F.g, C.g)) {   // gather over the fine nodes whose interpolation uses c
-      for (long long c = first; c < C.g.num_nodes; c += step) {
-        int ic[3];
-        node_ijk(C.g, c, ic);
-        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          const long long nf = F.g.n[k], ncs = C.g.n[k];
-          // the coarse hat of c lives on coarse coordinates (c - 1, c + 1) along each axis
-          lo[k] = ic[k] == 0 ? 0 : (int)(((long long)(ic[k] - 1) * nf + ncs - 1) / ncs);
-          hi[k] = (int)std::min(nf, ((long long)(ic[k] + 1) * nf) / ncs);
-        }
-        float v[NPN];
-#pragma unroll
-        for (int j = 0; j < NPN; ++j) v[j] = 0.f;
-        for (int i2 = lo[2]; i2 <= (D == 3 ? hi[2] : 0); ++i2)
-          for (int i1 = lo[1]; i1 <= hi[1]; ++i1)
-            for (int i0 = lo[0]; i0 <= hi[0]; ++i0) {
-              const int ifn[3] = {i0, i1, i2};
-              long long vert[D + 1];
-              float w[D + 1];
-              mg_interp<D>(F.g, C.g, ifn, vert, w);
-              float wc = 0.f;
-#pragma unroll
-              for (int m = 0; m <= D; ++m)
-                if (vert[m] == c) wc = w[m];
-              if (wc == 0.f) continue;
-              const long long f = i0 + F.g.stride[1] * i1 + (D == 3 ? F.g.stride[2] * i2 : 0);
-#pragma unroll
-              for (int j = 0; j < NPN; ++j) v[j] = fmaf(wc, F.t[f * NPN + j], v[j]);
-            }
-#pragma unroll
-        for (int j = 0; j < NPN; ++j) {
-          const long long k = c * NPN + j;
-          const float bk = C.dir[k] ? 0.f : v[j];
-          C.b[k] = bk;
-          C.z[0][k] = omega * C.dinv[k] * bk;
-        }
-      }
+      restrict_general(F, C, omega, first, step);
       return;
     }
     for (long long c = first; c < C.g.num_nodes; c += step) {
@@ -246,27 +253,33 @@ struct MgOps {
       }
     }
   }
+  // P between non-nested grids (P1 interpolation of the coarse field at each fine node), out of
+  // line like restrict_general
+  static __device__ __noinline__ void prolong_general(const MgLevelDev &F, float *zf, const MgLevelDev &C,
+                                                      const float *zc, long long first, long long step) {
+    for (long long a = first; a < F.g.num_nodes; a += step) {
+      int idx[3];
+      node_ijk(F.g, a, idx);
+      long long vert[D + 1];
+      float w[D + 1];
+      mg_interp<D>(F.g, C.g, idx, vert, w);
+#pragma unroll
+      for (int j = 0; j < NPN; ++j) {
+        const long long k = a * NPN + j;
+        if (F.dir[k]) continue;
+        float v = 0.f;
+#pragma unroll
+        for (int m = 0; m <= D; ++m)
+          if (vert[m] >= 0) v = fmaf(w[m], zc[vert[m] * NPN + j], v);
+        zf[k] += v;
+      }
+    }
+  }
   // fine z += P (coarse z)
   static __device__ void prolong(const MgLevelDev &F, float *zf, const MgLevelDev &C, const float *zc,
                                  long long first, long long step) {
     if (!mg_nested(F.g, C.g)) {
-      for (long long a = first; a < F.g.num_nodes; a += step) {
-        int idx[3];
-        node_ijk(F.g, a, idx);
-        long long vert[D + 1];
-        float w[D + 1];
-        mg_interp<D>(F.g, C.g, idx, vert, w);
-#pragma unroll
-        for (int j = 0; j < NPN; ++j) {
-          const long long k = a * NPN + j;
-          if (F.dir[k]) continue;
-          float v = 0.f;
-#pragma unroll
-          for (int m = 0; m <= D; ++m)
-            if (vert[m] >= 0) v = fmaf(w[m], zc[vert[m] * NPN + j], v);
-          zf[k] += v;
-        }
-      }
+      prolong_general(F, zf, C, zc, first, step);
       return;
     }
     for (long long a = first; a < F.g.num_nodes; a += step) {
