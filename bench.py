@@ -457,8 +457,8 @@ def survey_pcg_bytes(ndof, nt, nn, d, w):
 
 # DRAM bytes (read + write) of one state-solve CG launch, from one-pass ncu captures of the
 # kernels as built now (keyed by precision; absent until captured)
-C2_STATE_TRAFFIC = {"fp64": 13.59e6 + 0.66e6}
-C3_STATE_TRAFFIC = {"fp64": 53.39e9 + 3.27e9, "mixed": 27.92e9 + 1.48e9}
+C2_STATE_TRAFFIC = {"fp64": 14.13e6 + 0.67e6}
+C3_STATE_TRAFFIC = {"fp64": 53.41e9 + 3.29e9, "fp64_bf16": 25.63e9 + 3.12e9}
 
 
 def mg_state_bytes_per_iteration(nx, ny, c):

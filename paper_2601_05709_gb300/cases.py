@@ -12,7 +12,7 @@ CUDA-event time per solve.  The cases are the launches the profiles summarise:
   cantilever3d the 96 x 48 x 48 elasticity cantilever with 20 Gaussian bumps (or a smaller
                box with --n): the multigrid state solve to 1e-8.
 
-Usage: python -m paper_2601_05709_gb300.cases <case> [--n N] [--precision fp64|mixed] [--reps R]
+Usage: python -m paper_2601_05709_gb300.cases <case> [--n N] [--precision fp64|mixed] [--reps R] [--mg-bf16 1]
 """
 import argparse
 import json
@@ -41,6 +41,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=0, help="cells per axis (batch: n x n; cantilever3d: 2n x n x n)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--mg-bf16", type=int, default=0, help="1: V-cycle grid-level rows in BF16 (single problems)")
     args = ap.parse_args(argv)
 
     import numpy as np
@@ -85,7 +86,7 @@ def main(argv=None):
                                                   0.1, 0.2))
             rtol = 1e-8
         prob.coefficients()
-        opts = api.solve_opts(precision=prec, rtol=rtol, inner_rtol=1e-4, precond=mg)
+        opts = api.solve_opts(precision=prec, rtol=rtol, inner_rtol=1e-4, precond=mg, mg_bf16=args.mg_bf16)
 
         def solve():
             return prob.state_solve(opts)
@@ -94,7 +95,7 @@ def main(argv=None):
     for _ in range(max(args.reps, 1)):
         ms, st = _timed(stream, solve)
         times.append(ms)
-    print(json.dumps({"case": args.case, "n": args.n, "precision": args.precision, "ms": times,
+    print(json.dumps({"case": args.case, "n": args.n, "precision": args.precision, "mg_bf16": args.mg_bf16, "ms": times,
                       "iterations": st.iterations, "refinements": st.outer_iterations,
                       "rel_residual": st.rel_residual}), flush=True)
     ctx.close()

@@ -265,7 +265,8 @@ int fo_mg_plan(const Grid &g0, Grid *g, int max_levels, long long stop_unknowns,
     if (!even && general && halved && f.num_nodes * npn <= MG_BLOCK_DOFS) ok = false;
     for (int a = 0; a < f.dim; ++a) {
       n[a] = even ? f.n[a] / 2 : (f.n[a] + 1) / 2;
-      if (!even && (!general || f.n[a] < 3)) ok = false;
+      // (non-nested transfers locate points in 32-bit integers: axes below 2^15 cells)
+      if (!even && (!general || f.n[a] < 3 || f.n[a] >= 32768)) ok = false;
     }
     if (!ok) break;
     if (!fo_grid_make(f.dim, n, f.lo, f.hi, g[L])) break;

@@ -90,13 +90,16 @@ __host__ __device__ __forceinline__ bool mg_nested(const Grid &F, const Grid &C)
 template <int D>
 __device__ __forceinline__ void mg_interp(const Grid &F, const Grid &C, const int ifn[3], long long vert[D + 1],
                                           float w[D + 1]) {
+  // 32-bit integer arithmetic: node indices and cell counts per axis stay below 2^15 on any grid
+  // that fits the device, so i n_c and the cross products below stay below 2^30 (64-bit
+  // divisions are emulated and cost far more)
   int cc[3] = {0, 0, 0}, ax[3] = {0, 1, 2};
-  long long rem[3] = {0, 0, 0};
+  int rem[3] = {0, 0, 0};
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    const long long num = (long long)ifn[k] * C.n[k];
-    cc[k] = (int)(num / F.n[k]);
-    rem[k] = num % F.n[k];
+    const int num = ifn[k] * C.n[k];
+    cc[k] = num / F.n[k];
+    rem[k] = num - cc[k] * F.n[k];
   }
   // axes by t_k = rem_k / n_f,k descending (cross-multiplied: exact), ties by axis index
 #pragma unroll
