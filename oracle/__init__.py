@@ -37,6 +37,8 @@ Module map (paper section / equation each follows):
                 lag_method) and adaptive time stepping (eqs tend, steps).
 * ``logistic``  the population model of Sec. 6.4 (eqs log_cost, log_prob, log_KOmega,
                 log_weak): Newton state solve, linear adjoint, cost and the S1 tensor.
+* ``inverse``   the inverse-elasticity model of Sec. 3 / Sec. 6.1 (eqs cost, w-f, w-g, the two
+                adjoints and eq. SDelast_inv) and the Dirichlet extension (Sec. 5.7, eq. dir).
 * ``algorithm`` one iteration of Algorithm 1.
 * ``solvers``   sparse direct solve, Jacobi-PCG, Jacobi-BiCGStab.
 
@@ -52,5 +54,9 @@ face sums and first moments.  The logistic model (``logistic``) by the cubic int
 against a collapsed Gauss product rule, the residual against per-element quadrature, the
 Jacobian against central differences of the residual, constant equilibria, quadratic Newton
 convergence, the adjoint against a finite-difference source derivative and a Taylor test of
-the shape derivative (``tests/test_oracle_logistic.py``).
+the shape derivative (``tests/test_oracle_logistic.py``).  The inverse-elasticity model
+(``inverse``) by Taylor tests of its shape derivative with a linear measurement field, the zero
+of the cost, states, adjoints and derivative at the true inclusion, finite-difference checks
+of both adjoints through the traction and the measurement, and the Dirichlet extension's patch
+test (``tests/test_oracle_inverse.py``).
 """
