@@ -89,6 +89,9 @@ typedef struct fo_problem fo_problem;
 #define FO_FIELD_CHI    6 /* chi_e per element as double (0 / 1; the fraction for FO_COEF_CUT) */
 #define FO_FIELD_LOAD   7 /* state load F, N_dof (zero on Dirichlet DOFs)                 */
 #define FO_FIELD_OMEGA0 8 /* penalised-subdomain mask per element as double (0 / 1)       */
+#define FO_FIELD_V      9 /* inverse elasticity: second states v_k (y_k = v_k + g_k), n_cases x N_dof */
+#define FO_FIELD_Q     10 /* inverse elasticity: their adjoints q_k, n_cases x N_dof        */
+#define FO_FIELD_MEAS  11 /* inverse elasticity: measurement extensions g_k, n_cases x N_dof */
 
 /* operators (fo_apply) */
 #define FO_OP_STATE      0 /* y = K_A x, Dirichlet rows/columns replaced by identity      */
@@ -179,6 +182,21 @@ typedef struct {
   const double *u_init;
   double newton_rtol, newton_atol;
   int newton_maxit;
+  /* Inverse elasticity by a Kohn-Vogelius cost (Sec. 3, Sec. 6.1; kind FO_ELASTIC, box meshes,
+   * the one-point coefficient rule, no constraint).  inverse = 1 makes every load case k a
+   * force-displacement pair: its tractions (traction_case) are the applied force f_k on
+   * Gamma1 and meas[k * N_dof ..] (host, interleaved, copied at creation) the measured
+   * displacement extended into D (g_k; see fo_dirichlet_extension).  Gamma0 = dirichlet_faces
+   * (clamped), Gamma1 = gamma1_faces (same bitmask form).  States: u_k (Gamma0 clamped, force
+   * f_k) and v_k (zero on the whole boundary, int A sigma(v_k + g_k):eps(w) = 0); cost
+   * J = sum_k alpha/2 int |u_k - v_k - g_k|^2 + beta/2 int_Gamma1 |u_k - g_k|^2 with
+   * alpha = kv_alpha, beta = kv_beta; fo_adjoint_solve solves both adjoints p_k, q_k and the
+   * shape derivative is the paper's S0, S1 summed over the pairs.  A = a_in (kappa) inside,
+   * a_out outside. */
+  int inverse;
+  uint32_t gamma1_faces;
+  const double *meas;
+  double kv_alpha, kv_beta;
 } fo_model_desc;
 
 #define FO_COEF_CENTROID 0

@@ -18,7 +18,7 @@ FO_FP64, FO_MIXED = 0, 1
 FO_PC_JACOBI, FO_PC_MG = 0, 1
 FO_COEF_CENTROID, FO_COEF_CUT = 0, 1
 (FO_FIELD_PHI, FO_FIELD_U, FO_FIELD_P, FO_FIELD_THETA, FO_FIELD_RHS, FO_FIELD_COEF, FO_FIELD_CHI,
- FO_FIELD_LOAD, FO_FIELD_OMEGA0) = range(9)
+ FO_FIELD_LOAD, FO_FIELD_OMEGA0, FO_FIELD_V, FO_FIELD_Q, FO_FIELD_MEAS) = range(12)
 FO_OP_STATE, FO_OP_VELOCITY, FO_OP_TRANSPORT_L, FO_OP_TRANSPORT_R, FO_OP_STATE_FP32 = range(5)
 
 D3 = C.c_double * 3
@@ -43,7 +43,9 @@ class ModelDesc(C.Structure):
                 ("point_case", C.c_int * 4), ("traction_case", C.c_int * 4), ("n_volume", C.c_int),
                 ("volume_lo", D43), ("volume_hi", D43), ("volume_V", C.c_double * 4),
                 ("growth_rate", C.c_double), ("u_init", C.POINTER(C.c_double)), ("newton_rtol", C.c_double),
-                ("newton_atol", C.c_double), ("newton_maxit", C.c_int)]
+                ("newton_atol", C.c_double), ("newton_maxit", C.c_int), ("inverse", C.c_int),
+                ("gamma1_faces", C.c_uint32), ("meas", C.POINTER(C.c_double)), ("kv_alpha", C.c_double),
+                ("kv_beta", C.c_double)]
 
 
 class MgTuneResult(C.Structure):

@@ -64,11 +64,14 @@ def model_desc(kind, a_in=1.0, a_out=1e-3, E=1.0, nu=0.3, k=1.0, omega=0.0, diri
                point_loads=(), tractions=(), volume=0.0, alpha_mass=0.1, normal_penalty=0.0, omega0_weight=0.0,
                omega0_boxes=(), velocity_dirichlet=False, inst_k=None, inst_omega=None, inst_f=None, coef_rule=0,
                load_cases=None, volume_regions=None, growth_rate=0.0, u_init=None, newton_rtol=0.0,
-               newton_atol=0.0, newton_maxit=0):
+               newton_atol=0.0, newton_maxit=0, inverse=False, gamma1=(), meas=None, kv_alpha=1.0, kv_beta=0.0):
     """Build a fo_model_desc.  dirichlet: [(axis, side)]; point_loads: [(node, vec)];
     tractions: [(axis, side, vec)]; omega0_boxes: [(lo, hi)] with strict inequalities.
     The logistic model (kind FO_LOGISTIC): growth_rate r, u_init [N_n] initial Newton values,
     carrying capacity a_in / a_out inside / outside.
+    Inverse elasticity (kind FO_ELASTIC, inverse=True): every load case is a force-displacement
+    pair; gamma1 [(axis, side)] the measured faces, meas [n_cases, d N_n] the measurement
+    extensions g_k, kv_alpha / kv_beta the cost weights.
     A task-parallel batch (kind FO_HELMHOLTZ): inst_k, inst_omega [n_inst] and
     inst_f [n_inst, N_n]."""
     d = _lib.ModelDesc()
@@ -141,6 +144,16 @@ def model_desc(kind, a_in=1.0, a_out=1e-3, E=1.0, nu=0.3, k=1.0, omega=0.0, diri
         d.inst_k, d.inst_omega, d.inst_f = _dp(ik), _dp(io), _dp(iF)
         kept += [ik, io, iF]
     d.growth_rate, d.newton_rtol, d.newton_atol, d.newton_maxit = growth_rate, newton_rtol, newton_atol, newton_maxit
+    if inverse:
+        d.inverse = 1
+        gm = 0
+        for axis, side in gamma1:
+            gm |= 1 << (2 * axis + side)
+        d.gamma1_faces = gm
+        mv = _f64(meas).reshape(-1)
+        d.meas = _dp(mv)
+        d.kv_alpha, d.kv_beta = kv_alpha, kv_beta
+        kept.append(mv)
     if u_init is not None:
         ui = _f64(u_init)
         d.u_init = _dp(ui)
@@ -363,7 +376,7 @@ class Problem:
 
     def _field_len(self, field):
         m = self.mesh
-        if field in (FO_FIELD_U, FO_FIELD_P, FO_FIELD_LOAD):
+        if field in (FO_FIELD_U, FO_FIELD_P, FO_FIELD_LOAD, _lib.FO_FIELD_V, _lib.FO_FIELD_Q, _lib.FO_FIELD_MEAS):
             return self.ncomp * m.num_nodes * max(self.n_inst, 1) * self.n_cases
         if field in (FO_FIELD_THETA, FO_FIELD_RHS):
             return m.dim * m.num_nodes

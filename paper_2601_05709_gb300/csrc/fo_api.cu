@@ -437,6 +437,7 @@ extern "C" fo_status fo_problem_destroy(fo_problem *p) {
   fo_ctx *ctx = p->ctx;
   cudaStreamSynchronize(ctx->stream);
   fo_batch_destroy(p);
+  fo_inverse_destroy(p);
   fo_mg_destroy(p);
   std::vector<std::pair<void **, size_t>> list;
   prob_bytes_fields(p, list);
@@ -493,6 +494,12 @@ extern "C" fo_status fo_problem_create(fo_mesh *m, const fo_model_desc *desc, fo
     return fo_fail(ctx, FO_EINVAL, "task-parallel batches take the one-point coefficient rule");
   if (m->um && desc->n_inst > 0)
     return fo_fail(ctx, FO_EINVAL, "task-parallel batches run on box meshes (fo_mesh_box)");
+  if (desc->inverse &&
+      (desc->kind != FO_ELASTIC || m->um || desc->n_inst > 0 || desc->coef_rule != FO_COEF_CENTROID ||
+       desc->n_volume > 0 || desc->volume_target > 0 || !desc->meas || !(desc->kv_alpha >= 0) || !(desc->kv_beta >= 0)))
+    return fo_fail(ctx, FO_EINVAL,
+                   "inverse elasticity: FO_ELASTIC on a box mesh, one-point rule, no constraint, measurements given, "
+                   "alpha, beta >= 0");
   fo_problem *p = new fo_problem();
   p->ctx = ctx;
   p->mesh = m;
@@ -510,6 +517,7 @@ extern "C" fo_status fo_problem_create(fo_mesh *m, const fo_model_desc *desc, fo
   if (desc->kind == FO_HEAT || desc->kind == FO_LOGISTIC) p->desc.k = 1.0;
   p->desc.u_init = nullptr;
   p->desc.inst_k = p->desc.inst_omega = p->desc.inst_f = nullptr;
+  p->desc.meas = nullptr;   // copied by fo_inverse_create
   if (desc->n_inst > 0) {   // batch: A_e alone in coef; k_i, omega_i, f_i per instance
     p->desc.k = 1.0;
     p->desc.omega = 0.0;
@@ -553,6 +561,7 @@ extern "C" fo_status fo_problem_create(fo_mesh *m, const fo_model_desc *desc, fo
     if (st == FO_OK) st = fo_launch_velocity_diag(p);
   }
   if (st == FO_OK && desc->n_inst > 0) st = fo_batch_create(p, desc);
+  if (st == FO_OK && desc->inverse) st = fo_inverse_create(p, desc);
   if (st == FO_OK) st = fo_cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "problem setup");
   if (st != FO_OK) {
     fo_problem_destroy(p);
@@ -618,6 +627,7 @@ extern "C" fo_status fo_state_solve(fo_problem *p, const fo_solve_opts *o, fo_so
   fo_status s;
   if (p->batch) s = fo_batch_state(p, false, o, st);
   else if (p->desc.kind == FO_LOGISTIC) s = fo_logistic_state(p, o, st, &p->newton_steps);
+  else if (p->inv) s = fo_inverse_states(p, o, st);
   else if (p->ncases == 1) s = fo_state_pcg(p, p->load, p->u, o, st);
   else {   // one solve per load case (eq. compli_plus); statistics summed, worst residual kept
     fo_solve_stats tot;
@@ -652,6 +662,7 @@ extern "C" fo_status fo_adjoint_solve(fo_problem *p, const fo_solve_opts *o, fo_
   if (!p->coef_valid) FO_TRY(fo_coefficients(p));
   if (p->batch) return fo_batch_state(p, true, o, st);
   if (p->desc.kind == FO_LOGISTIC) return fo_logistic_adjoint(p, o, st);
+  if (p->inv) return fo_inverse_adjoints(p, o, st);
   double c = p->desc.kind == FO_ELASTIC ? -2.0 : -1.0;
   double *b = p->rhs;   // reuse the RHS buffer as the adjoint load (d*N_n >= N_dof)
   fo_solve_opts oo = *o;
@@ -683,6 +694,7 @@ static fo_status cost_and_volume(fo_problem *p, double *J, double *vol) {
       else FO_TRY(fo_launch_functionals_on(p, u, F, &jk, &v));
       j += jk;
     }
+  if (p->inv) FO_TRY(fo_inverse_cost(p, &j));   // the Kohn-Vogelius cost (|Omega| as computed)
   if (!std::isfinite(j) || !std::isfinite(v)) return fo_fail(p->ctx, FO_ENAN, "non-finite functional");
   *J = j;
   *vol = v;
@@ -727,7 +739,7 @@ extern "C" fo_status fo_shape_derivative_v(fo_problem *p, const double *lambda, 
   if (!p) return FO_EINVAL;
   if (nc != problem_nc(p) || (nc > 0 && !lambda))
     return fo_fail(p->ctx, FO_EINVAL, "the problem has %d constraints", problem_nc(p));
-  if (p->batch || (p->ncases == 1 && p->nvol == 0)) return fo_shape_derivative(p, nc ? lambda[0] : 0.0, rhs_out);
+  if (p->batch || p->inv || (p->ncases == 1 && p->nvol == 0)) return fo_shape_derivative(p, nc ? lambda[0] : 0.0, rhs_out);
   if (!p->coef_valid) FO_TRY(fo_coefficients(p));
   fo_ctx *ctx = p->ctx;
   const Grid &g = p->mesh->g;
@@ -763,12 +775,13 @@ extern "C" fo_status fo_shape_derivative_v(fo_problem *p, const double *lambda, 
 
 extern "C" fo_status fo_shape_derivative(fo_problem *p, double lambda, double *rhs_out) {
   if (!p) return FO_EINVAL;
-  if (!p->batch && (p->ncases > 1 || p->nvol > 0)) {   // one multiplier: the first constraint's
+  if (!p->batch && !p->inv && (p->ncases > 1 || p->nvol > 0)) {   // one multiplier: the first constraint's
     double lv[4] = {lambda, 0, 0, 0};
     return fo_shape_derivative_v(p, lv, problem_nc(p), rhs_out);
   }
   if (!p->coef_valid) FO_TRY(fo_coefficients(p));
   if (p->batch) FO_TRY(fo_batch_shape_rhs(p, lambda));
+  else if (p->inv) FO_TRY(fo_inverse_shape(p));
   else if (p->desc.kind == FO_LOGISTIC)
     FO_TRY(fo_launch_logistic_shape(p, lambda, nullptr, p->desc.volume_target > 0 ? 1.0 / p->desc.volume_target : 1.0, 0));
   else if (p->mesh->um) FO_TRY(fo_umesh_shape_rhs(p, lambda));
@@ -912,6 +925,9 @@ static double *field_ptr(fo_problem *p, int field, size_t *n, bool *is_u8) {
       return p->desc.coef_rule == FO_COEF_CUT ? p->chif : (double *)p->chi;
     case FO_FIELD_LOAD: *n = p->ndof * p->ncases; return p->load;
     case FO_FIELD_OMEGA0: *n = g.num_elems; *is_u8 = true; return (double *)p->omega0;
+    case FO_FIELD_V: *n = p->ndof * p->ncases; return p->inv ? p->inv->v : nullptr;
+    case FO_FIELD_Q: *n = p->ndof * p->ncases; return p->inv ? p->inv->q : nullptr;
+    case FO_FIELD_MEAS: *n = p->ndof * p->ncases; return p->inv ? p->inv->g : nullptr;
     default: return nullptr;
   }
 }
@@ -1144,10 +1160,10 @@ extern "C" fo_status fo_opt_step(fo_problem *p, int iter, const fo_run_options *
   fo_status s = fo_state_solve(p, &o->state, &lg.state);
   if (s != FO_OK) return s;
   lg.ms_state_kernel = ctx->last_solve_ms;
-  if (p->desc.kind == FO_LOGISTIC) {   // the adjoint is a solve of its own (Sec. 6.4)
-    lg.newton_steps = p->newton_steps;
+  if (p->desc.kind == FO_LOGISTIC || p->inv) {   // the adjoints are solves of their own (Sec. 6.4, Sec. 3)
+    lg.newton_steps = p->desc.kind == FO_LOGISTIC ? p->newton_steps : 0;
     s = fo_adjoint_solve(p, &o->state, &lg.adjoint);
-    if (s != FO_OK) return s;
+    if (s != FO_OK && s != FO_ENOCONV) return s;
   }
   FO_TRY(mark(1));
   const int nc = problem_nc(p);

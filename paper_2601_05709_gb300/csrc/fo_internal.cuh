@@ -110,6 +110,18 @@ struct fo_mg {
   std::vector<unsigned char> host;         // its host image (kept alive for the async copy)
 };
 
+// Inverse-elasticity model (fo_inverse.cu): the second states, their adjoints, the measurement
+// extensions (n_cases x N_dof each) and the operator with the whole boundary clamped.
+struct fo_inv {
+  double *v = nullptr, *q = nullptr, *g = nullptr, *r = nullptr;   // r: one N_dof work vector
+  double *W = nullptr, *dinv = nullptr;      // rows with every boundary DOF clamped (FP64)
+  float *W32 = nullptr, *dinv32 = nullptr;
+  uint8_t *dirb = nullptr, *none = nullptr;  // boundary mask per DOF; an all-zero mask
+  uint8_t *gamma1 = nullptr;                 // per node: bit (2 axis + side) of the Gamma1 faces it is on
+  long long rows_epoch = -1;                 // coefficient epoch of W
+  std::vector<std::pair<void **, size_t>> allocs;
+};
+
 struct fo_problem {
   fo_ctx *ctx;
   fo_mesh *mesh;
@@ -150,6 +162,7 @@ struct fo_problem {
   Scratch scratch;
   bool coef_valid = false, u_valid = false, rhs_valid = false, theta_valid = false;
   int newton_steps = 0;          // Newton steps of the last logistic state solve
+  fo_inv *inv = nullptr;         // inverse-elasticity data (desc.inverse)
   bool transport_valid = false;
   double transport_dt = 0, transport_h = 0;
   int transport_smooth = 0;
@@ -520,6 +533,13 @@ fo_status fo_batch_state(fo_problem *p, bool adjoint, const fo_solve_opts *o, fo
 fo_status fo_batch_functionals(fo_problem *p, double *J, double *vol, double *J_inst);
 fo_status fo_batch_shape_rhs(fo_problem *p, double lambda);
 fo_status fo_batch_apply(fo_problem *p, const double *x, double *y, bool fp32);
+// inverse elasticity (fo_inverse.cu)
+fo_status fo_inverse_create(fo_problem *p, const fo_model_desc *desc);
+void fo_inverse_destroy(fo_problem *p);
+fo_status fo_inverse_states(fo_problem *p, const fo_solve_opts *o, fo_solve_stats *st);
+fo_status fo_inverse_adjoints(fo_problem *p, const fo_solve_opts *o, fo_solve_stats *st);
+fo_status fo_inverse_cost(fo_problem *p, double *J);
+fo_status fo_inverse_shape(fo_problem *p);
 // logistic population model (fo_logistic.cu)
 fo_status fo_logistic_state(fo_problem *p, const fo_solve_opts *o, fo_solve_stats *st, int *steps_out);
 fo_status fo_logistic_adjoint(fo_problem *p, const fo_solve_opts *o, fo_solve_stats *st);
