@@ -582,7 +582,8 @@ def bench_variants(api, ctx, stream, peaks):
     """The hot path's variants on the cantilever physics: a general mesh given as arrays
     (jittered, renumbered Kuhn arrays of the 256 x 128 box through the assembled-operator path),
     the exact cut-cell coefficient, and runs to convergence under the stopping criterion with
-    one and with two load cases; and the population example (logistic model) to convergence."""
+    one and with two load cases; the population example (logistic model) to convergence; and the
+    inverse-elasticity example."""
     import numpy as np
     import torch
     from paper_2601_05709_gb300 import workloads
@@ -703,6 +704,45 @@ def bench_variants(api, ctx, stream, peaks):
         "state_cg_iterations_per_iteration": float(np.mean([l.state.iterations for l in logs])),
         "adjoint_cg_iterations_per_iteration": float(np.mean([l.adjoint.iterations for l in logs])),
         "criterion": "start_to_check 30, lgrn_tol 1e-2, ctrn_tol 1e-2, prev 10 (Sec. 5.7 defaults)"}
+    prob.close()
+
+    # inverse elasticity (Sec. 3, Sec. 6.1): unit square 128 x 128, kappa = 10 inclusions, Gamma0 the
+    # x = 0 face, three force-displacement pairs (tractions on the other faces); the measurements
+    # are the displacements of a true two-inclusion design computed on the 256 x 256 mesh, taken
+    # at the coarse nodes of Gamma1 and extended into D (fo_dirichlet_extension); 30 iterations
+    # from one central inclusion
+    nI = 128
+    faces1 = [(0, 1), (1, 0), (1, 1)]
+    trs = [(0, 1, (1.0, 0.0)), (1, 0, (0.0, -1.0)), (1, 1, (0.3, 1.0))]
+    cases = [([], [tr]) for tr in trs]
+    true_c = np.array([[0.35, 0.6], [0.7, 0.35]])
+    fine = ctx.mesh_box(2, (2 * nI, 2 * nI), (0.0, 0.0), (1.0, 1.0))
+    _, fc = fine.copy_out()
+    fp = fine.problem(api.model_desc(api.FO_ELASTIC, a_in=10.0, a_out=1.0, dirichlet=[(0, 0)], load_cases=cases))
+    fp.set_levelset(workloads.phi_bumps(fc, true_c, 0.1, 0.5))
+    fp.state_solve(api.solve_opts(rtol=1e-12, precond=api.FO_PC_MG))
+    Uf = fp.get(api.FO_FIELD_U).reshape(3, 2 * nI + 1, 2 * nI + 1, 2)
+    fp.close()
+    im = ctx.mesh_box(2, (nI, nI), (0.0, 0.0), (1.0, 1.0))
+    _, ic = im.copy_out()
+    all_faces = [(a, sd) for a in range(2) for sd in (0, 1)]
+    meas = np.stack([im.dirichlet_extension(all_faces, Uf[k, ::2, ::2, :].reshape(-1),
+                                            api.solve_opts(rtol=1e-12, maxit=200000)) for k in range(3)])
+    prob = im.problem(api.model_desc(api.FO_ELASTIC, a_in=10.0, a_out=1.0, dirichlet=[(0, 0)], load_cases=cases,
+                                     inverse=True, gamma1=faces1, meas=meas, kv_alpha=1.0, kv_beta=1.0,
+                                     alpha_mass=0.1, velocity_dirichlet=True))
+    prob.set_levelset(workloads.phi_bumps(ic, np.array([[0.5, 0.5]]), 0.15, 0.5))
+    iso = api.solve_opts(rtol=1e-10, warm_start=1, maxit=400000, precond=api.FO_PC_MG)
+    iro = api.run_options(dfactor=1e-2, smooth=False, state=iso,
+                          velocity=api.solve_opts(rtol=1e-10, warm_start=1, precond=api.FO_PC_MG),
+                          transport=api.solve_opts(rtol=1e-12))
+    ms, logs = timed_iters(prob, iro, 1, 30, api.PPL(0))
+    out["inverse_elasticity_128x128"] = {
+        "workload": "inverse elasticity (Kohn-Vogelius cost, Sec. 3 / 6.1) on a 128x128 Kuhn mesh of the unit square, "
+                    "kappa = 10, three force-displacement pairs measured on a 256x256 mesh of a two-inclusion design",
+        "ms_per_opt_step": ms, "opt_iters_per_s": 1e3 / ms, "J_first": logs[0].J, "J_last": logs[-1].J,
+        "state_cg_iterations_per_iteration": float(np.mean([l.state.iterations for l in logs])),
+        "adjoint_cg_iterations_per_iteration": float(np.mean([l.adjoint.iterations for l in logs]))}
     prob.close()
     return out
 

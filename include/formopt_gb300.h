@@ -473,6 +473,15 @@ typedef struct {
  * agree to rounding only. */
 FO_API fo_status fo_batch_mg_autotune(fo_problem *prob, int precision, double rtol, fo_mg_tune_result *out);
 
+/* Dirichlet extension (Sec. 5.7, eq. dir), the helper that extends boundary measurements into D:
+ * per component, eta = values at the nodes of the listed faces (bitmask (2 axis + side), as
+ * dirichlet_faces) and int D eta : D zeta = 0 for every P1 zeta vanishing there (natural
+ * condition elsewhere).  values and out are host arrays of d * N_n (interleaved; only the
+ * values at the face nodes are read).  Box meshes; solved by Jacobi-preconditioned CG to
+ * opts->rtol (NULL: the defaults), with temporary device memory freed before returning. */
+FO_API fo_status fo_dirichlet_extension(fo_mesh *mesh, uint32_t faces, const double *values, double *out,
+                                        const fo_solve_opts *opts);
+
 /* --------------------------------------------------------------- serving ----- */
 /* A request is one Algorithm-1 step without the transport (state solve, explicit adjoint
  * solve, cost and constraint, shape derivative, velocity) on its own box mesh.  A server

@@ -181,6 +181,8 @@ PROTOTYPES = {
     "fo_batch_solve_info": (ST, [VP, C.POINTER(C.c_int), DP]),
     "fo_batch_autotune": (ST, [VP, C.c_int, C.POINTER(TuneResult)]),
     "fo_batch_mg_autotune": (ST, [VP, C.c_int, C.c_double, C.POINTER(MgTuneResult)]),
+    "fo_dirichlet_extension": (ST, [VP, C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(SolveOpts)]),
     "fo_ppl_init": (None, [C.POINTER(PPLState), C.c_int]),
     "fo_ppl_update": (None, [C.POINTER(PPLState), DP, C.c_double, DP, DP]),
     "fo_adaptime": (None, [C.c_double, C.POINTER(RunOptions), DP, C.POINTER(C.c_int)]),

@@ -264,6 +264,18 @@ class Mesh:
     def problem(self, desc):
         return Problem(self, desc)
 
+    def dirichlet_extension(self, faces, values, opts=None):
+        """fo_dirichlet_extension: values [d N_n] kept on the listed faces [(axis, side)],
+        extended by the vector Laplacian elsewhere."""
+        mask = 0
+        for axis, side in faces:
+            mask |= 1 << (2 * axis + side)
+        v = _f64(values).reshape(-1)
+        out = np.empty_like(v)
+        self.ctx.check(self.ctx.lib.fo_dirichlet_extension(self.handle, mask, _dp(v), _dp(out),
+                                                           C.byref(opts) if opts else None), "fo_dirichlet_extension")
+        return out
+
 
 class Problem:
     def __init__(self, mesh, desc):

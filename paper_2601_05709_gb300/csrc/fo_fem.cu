@@ -621,6 +621,17 @@ fo_status fo_launch_stencil_on(fo_problem *p, const Grid &g, const double *coef,
   return FO_OK;
 }
 
+// Scalar P1 rows (coef-weighted Laplacian, no mass) on grid g with the Dirichlet mask dir.
+fo_status fo_launch_scalar_stencil(fo_ctx *ctx, const Grid &g, const double *coef, const uint8_t *dir, double *W,
+                                   float *W32, double *di, float *di32) {
+  const int blocks = fo_blocks_for(g.num_nodes, FO_BLOCK, 65536);
+  if (g.dim == 2) k_state_stencil<2, 1><<<blocks, FO_BLOCK, 0, ctx->stream>>>(g, coef, dir, 0.0, 0.0, 0.0, W, W32, di, di32);
+  else k_state_stencil<3, 1><<<blocks, FO_BLOCK, 0, ctx->stream>>>(g, coef, dir, 0.0, 0.0, 0.0, W, W32, di, di32);
+  fo_note_launch(1);
+  FO_CU(ctx, cudaGetLastError());
+  return FO_OK;
+}
+
 fo_status fo_launch_state_diag(fo_problem *p) {
   // the state operator's stencil rows (from the current coefficients) and its Jacobi diagonal
   return fo_launch_stencil_on(p, p->mesh->g, p->coef, p->dir, p->Wst, p->Wst32, p->dinv_state, p->dinv_state32);

@@ -119,6 +119,7 @@ struct fo_inv {
   uint8_t *dirb = nullptr, *none = nullptr;  // boundary mask per DOF; an all-zero mask
   uint8_t *gamma1 = nullptr;                 // per node: bit (2 axis + side) of the Gamma1 faces it is on
   long long rows_epoch = -1;                 // coefficient epoch of W
+  fo_mg *mgb = nullptr;                      // multigrid hierarchy of the boundary-clamped operator
   std::vector<std::pair<void **, size_t>> allocs;
 };
 
@@ -540,6 +541,8 @@ fo_status fo_inverse_states(fo_problem *p, const fo_solve_opts *o, fo_solve_stat
 fo_status fo_inverse_adjoints(fo_problem *p, const fo_solve_opts *o, fo_solve_stats *st);
 fo_status fo_inverse_cost(fo_problem *p, double *J);
 fo_status fo_inverse_shape(fo_problem *p);
+fo_status fo_launch_scalar_stencil(fo_ctx *ctx, const Grid &g, const double *coef, const uint8_t *dir, double *W,
+                                   float *W32, double *di, float *di32);
 // logistic population model (fo_logistic.cu)
 fo_status fo_logistic_state(fo_problem *p, const fo_solve_opts *o, fo_solve_stats *st, int *steps_out);
 fo_status fo_logistic_adjoint(fo_problem *p, const fo_solve_opts *o, fo_solve_stats *st);
@@ -547,6 +550,7 @@ fo_status fo_launch_logistic_shape(fo_problem *p, double lambda, const double *c
 // multigrid (fo_mg.cu)
 fo_status fo_state_pcg_mg(fo_problem *p, const double *b, double *x, const fo_solve_opts *o, fo_solve_stats *st);
 void fo_mg_destroy(fo_problem *p);
+void fo_mg_release(fo_ctx *ctx, fo_mg *&mg);
 size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0, bool bf16 = false);
 bool fo_mg_applicable(const Grid &g0, int npn, bool general = true);
 int fo_mg_plan(const Grid &g0, Grid *g, int max_levels, long long stop_unknowns = 0, int npn = 1, bool general = false);

@@ -14,7 +14,7 @@
 // mass on the Gamma1 faces (|f| (1 + delta) / (d (d+1)) per facet); every integral is exact for
 // P1 data.  u_k and p_k use the problem's own operator (Gamma0 = its Dirichlet faces); v_k and
 // q_k an operator with every boundary DOF clamped, built by the same stencil builder from the
-// same coefficients (Jacobi-PCG).  The lifting -K g_k of v_k's right-hand side needs the
+// same coefficients, with a multigrid hierarchy of its own.  The lifting -K g_k of v_k's right-hand side needs the
 // operator without any clamped DOF, built into the same rows just before.
 #include <cmath>
 #include <cstring>
@@ -315,27 +315,29 @@ fo_status fo_inverse_create(fo_problem *p, const fo_model_desc *desc) {
 
 void fo_inverse_destroy(fo_problem *p) {
   if (!p->inv) return;
+  fo_mg_release(p->ctx, p->inv->mgb);
   for (auto &e : p->inv->allocs) fo_free(p->ctx, *e.first, e.second);
   delete p->inv;
   p->inv = nullptr;
 }
 
 // Runs f with the problem's operator replaced by the boundary-clamped one (the solvers read the
-// problem's rows, inverse diagonals and Dirichlet mask).
+// problem's rows, inverse diagonals, Dirichlet mask and multigrid hierarchy; the clamped
+// operator keeps a hierarchy of its own, built from the same coefficients on first use).
 template <class F>
 static fo_status with_boundary_rows(fo_problem *p, F &&f) {
   fo_inv *iv = p->inv;
-  std::swap(p->Wst, iv->W);
-  std::swap(p->Wst32, iv->W32);
-  std::swap(p->dinv_state, iv->dinv);
-  std::swap(p->dinv_state32, iv->dinv32);
-  std::swap(p->dir, iv->dirb);
+  auto swap_all = [&] {
+    std::swap(p->Wst, iv->W);
+    std::swap(p->Wst32, iv->W32);
+    std::swap(p->dinv_state, iv->dinv);
+    std::swap(p->dinv_state32, iv->dinv32);
+    std::swap(p->dir, iv->dirb);
+    std::swap(p->mg, iv->mgb);
+  };
+  swap_all();
   const fo_status s = f();
-  std::swap(p->Wst, iv->W);
-  std::swap(p->Wst32, iv->W32);
-  std::swap(p->dinv_state, iv->dinv);
-  std::swap(p->dinv_state32, iv->dinv32);
-  std::swap(p->dir, iv->dirb);
+  swap_all();
   return s;
 }
 
@@ -390,13 +392,11 @@ fo_status fo_inverse_states(fo_problem *p, const fo_solve_opts *o, fo_solve_stat
     if (r != FO_OK) res = r;
     add_stats(tot, s);
   }
-  fo_solve_opts oj = *o;
-  oj.precond = FO_PC_JACOBI;
   for (int k = 0; k < p->ncases; ++k) {
     fo_solve_stats s;
     memset(&s, 0, sizeof s);
     const fo_status r = with_boundary_rows(
-        p, [&] { return fo_state_pcg(p, iv->q + (size_t)k * nd, iv->v + (size_t)k * nd, &oj, &s); });
+        p, [&] { return fo_state_pcg(p, iv->q + (size_t)k * nd, iv->v + (size_t)k * nd, o, &s); });
     if (r != FO_OK && r != FO_ENOCONV) return r;
     if (r != FO_OK) res = r;
     add_stats(tot, s);
@@ -419,8 +419,6 @@ fo_status fo_inverse_adjoints(fo_problem *p, const fo_solve_opts *o, fo_solve_st
   const double al = p->desc.kv_alpha, be = p->desc.kv_beta;
   fo_solve_opts oa = *o;
   oa.warm_start = 0;
-  fo_solve_opts oj = oa;
-  oj.precond = FO_PC_JACOBI;
   fo_solve_stats tot;
   memset(&tot, 0, sizeof tot);
   fo_status res = FO_OK;
@@ -441,7 +439,7 @@ fo_status fo_inverse_adjoints(fo_problem *p, const fo_solve_opts *o, fo_solve_st
     if (r != FO_OK) res = r;
     add_stats(tot, s);
     memset(&s, 0, sizeof s);
-    r = with_boundary_rows(p, [&] { return fo_state_pcg(p, iv->r, iv->q + (size_t)k * nd, &oj, &s); });
+    r = with_boundary_rows(p, [&] { return fo_state_pcg(p, iv->r, iv->q + (size_t)k * nd, &oa, &s); });
     if (r != FO_OK && r != FO_ENOCONV) return r;
     if (r != FO_OK) res = r;
     add_stats(tot, s);
@@ -497,4 +495,222 @@ fo_status fo_inverse_shape(fo_problem *p) {
     FO_CU(ctx, cudaGetLastError());
   }
   return FO_OK;
+}
+
+// ------------------------------------------------------------- Dirichlet extension (Sec. 5.7)
+// Per component: eta = the given values on the nodes of the listed faces, and the P1 Laplacian of
+// eta vanishes at every other node (int D eta : D zeta = 0 for zeta zero on those faces).  Written
+// eta = fix + x with fix the values on the faces (zero elsewhere) and x zero there:
+// L_b x = -(L fix) at the free nodes, L the Laplacian rows without clamped nodes and L_b with the
+// face nodes clamped; Jacobi-preconditioned CG per component, host-driven.
+template <int D>
+__global__ void k_ext_setup(Grid g, uint32_t faces, const double *vals, uint8_t *mask, double *fix, double *ones_e) {
+  const long long N = g.num_nodes;
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < N; a += (long long)gridDim.x * blockDim.x) {
+    int idx[3];
+    node_ijk(g, a, idx);
+    bool on = false;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      if (idx[c] == 0 && (faces & (1u << (2 * c)))) on = true;
+      if (idx[c] == g.n[c] && (faces & (1u << (2 * c + 1)))) on = true;
+    }
+    mask[a] = on ? 1 : 0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) fix[c * N + a] = on ? vals[a * D + c] : 0.0;   // component-major
+  }
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.num_elems;
+       e += (long long)gridDim.x * blockDim.x)
+    ones_e[e] = 1.0;
+}
+
+// y = scale * L x at the nodes mask leaves free (0 at masked nodes); x read unmasked
+template <int D>
+__global__ void k_ext_apply(StencilOp<D, 1, true, double> op, const double *x, const uint8_t *mask, double scale,
+                            double *y) {
+  op.sweep(VecX<double>{x}, [&](long long a, const double (&ax)[1]) { y[a] = mask[a] ? 0.0 : scale * ax[0]; });
+}
+
+// per-block partials of (a . b) and (c . d)
+__global__ void k_ext_dots(const double *a, const double *b, const double *c, const double *d, long long n,
+                           double *partials) {
+  __shared__ double smem[64];
+  double s[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    s[0] += a[i] * b[i];
+    s[1] += c[i] * d[i];
+  }
+  block_sum<2>(s, smem);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = s[0];
+    partials[2 * blockIdx.x + 1] = s[1];
+  }
+}
+
+// x += alpha p; r -= alpha q; z = dinv r
+__global__ void k_ext_update(double *x, double *r, double *z, const double *p, const double *q, const double *dinv,
+                             double alpha, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    z[i] = dinv[i] * ri;
+  }
+}
+
+// p = z + beta p
+__global__ void k_ext_dir(double *p, const double *z, double beta, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// eta (interleaved) = fix + x (component-major)
+__global__ void k_ext_out(const double *fix, const double *x, long long N, int D, double *eta) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N * D; i += (long long)gridDim.x * blockDim.x) {
+    const long long a = i / D, c = i % D;
+    eta[i] = fix[c * N + a] + x[c * N + a];
+  }
+}
+
+extern "C" fo_status fo_dirichlet_extension(fo_mesh *m, uint32_t faces, const double *values, double *out,
+                                            const fo_solve_opts *opts) {
+  if (!m || !values || !out) return FO_EINVAL;
+  fo_ctx *ctx = m->ctx;
+  if (m->um) return fo_fail(ctx, FO_EINVAL, "the Dirichlet extension runs on box meshes");
+  if (faces == 0) return fo_fail(ctx, FO_EINVAL, "no face to extend from");
+  fo_solve_opts def;
+  fo_solve_opts_default(&def);
+  const fo_solve_opts *o = opts ? opts : &def;
+  const Grid &g = m->g;
+  const int D = g.dim;
+  const long long N = g.num_nodes, S = D == 2 ? 7 : 15;
+  std::vector<std::pair<void **, size_t>> al;
+  double *vals, *fix, *x, *r, *z, *p, *q, *W, *dinv, *ones, *part;
+  float *W32, *dinv32;
+  uint8_t *mask;
+  al.push_back({(void **)&vals, sizeof(double) * N * D});
+  al.push_back({(void **)&fix, sizeof(double) * N * D});
+  al.push_back({(void **)&x, sizeof(double) * N * D});
+  al.push_back({(void **)&r, sizeof(double) * N});
+  al.push_back({(void **)&z, sizeof(double) * N});
+  al.push_back({(void **)&p, sizeof(double) * N});
+  al.push_back({(void **)&q, sizeof(double) * N});
+  al.push_back({(void **)&W, sizeof(double) * S * N});
+  al.push_back({(void **)&W32, sizeof(float) * S * N});
+  al.push_back({(void **)&dinv, sizeof(double) * N});
+  al.push_back({(void **)&dinv32, sizeof(float) * N});
+  al.push_back({(void **)&ones, sizeof(double) * g.num_elems});
+  al.push_back({(void **)&mask, (size_t)N});
+  al.push_back({(void **)&part, sizeof(double) * 2048});
+  fo_status st = FO_OK;
+  size_t done = 0;
+  for (; done < al.size() && st == FO_OK; ++done) st = fo_alloc(ctx, al[done].first, al[done].second);
+  auto release = [&] {
+    cudaStreamSynchronize(ctx->stream);
+    for (size_t i = 0; i < done; ++i) fo_free(ctx, *al[i].first, al[i].second);
+  };
+  if (st != FO_OK) {
+    release();
+    return st;
+  }
+  cudaStream_t s = ctx->stream;
+  const int blocks = fo_blocks_for(N, FO_BLOCK, 1024);
+  std::vector<double> hp(2048);
+  int iters = 0;
+  auto run = [&]() -> fo_status {
+    FO_CU(ctx, cudaMemcpyAsync(vals, values, sizeof(double) * N * D, cudaMemcpyHostToDevice, s));
+    if (D == 2) k_ext_setup<2><<<fo_blocks_for(std::max(N, g.num_elems), FO_BLOCK, 65536), FO_BLOCK, 0, s>>>(
+        g, faces, vals, mask, fix, ones);
+    else k_ext_setup<3><<<fo_blocks_for(std::max(N, g.num_elems), FO_BLOCK, 65536), FO_BLOCK, 0, s>>>(
+        g, faces, vals, mask, fix, ones);
+    fo_note_launch(1);
+    FO_CU(ctx, cudaMemsetAsync(x, 0, sizeof(double) * N * D, s));
+    // right-hand sides -(L fix) with the rows that clamp nothing (mask of zeros: r as scratch)
+    FO_CU(ctx, cudaMemsetAsync(r, 0, (size_t)N, s));   // r's first N bytes, zero, serve as the empty mask
+    FO_TRY(fo_launch_scalar_stencil(ctx, g, ones, (const uint8_t *)r, W, W32, dinv, dinv32));
+    for (int c = 0; c < D; ++c) {
+      if (D == 2) {
+        StencilOp<2, 1, true, double> op;
+        op.g = g;
+        op.W = W;
+        k_ext_apply<2><<<blocks, FO_BLOCK, 0, s>>>(op, fix + c * N, mask, -1.0, x + c * N);   // rhs in x for now
+      } else {
+        StencilOp<3, 1, true, double> op;
+        op.g = g;
+        op.W = W;
+        k_ext_apply<3><<<blocks, FO_BLOCK, 0, s>>>(op, fix + c * N, mask, -1.0, x + c * N);
+      }
+      fo_note_launch(1);
+    }
+    FO_TRY(fo_launch_scalar_stencil(ctx, g, ones, mask, W, W32, dinv, dinv32));
+    for (int c = 0; c < D; ++c) {
+      double *xc = x + c * N;
+      // r = b (x = 0), z = D^{-1} r, p = z; the right-hand side moves from xc into r
+      FO_CU(ctx, cudaMemcpyAsync(r, xc, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      FO_CU(ctx, cudaMemsetAsync(xc, 0, sizeof(double) * N, s));
+      FO_CU(ctx, cudaMemsetAsync(p, 0, sizeof(double) * N, s));   // (read, times zero, by the update)
+      FO_CU(ctx, cudaMemsetAsync(q, 0, sizeof(double) * N, s));
+      k_ext_update<<<blocks, FO_BLOCK, 0, s>>>(xc, r, z, p, q, dinv, 0.0, N);   // z = D^{-1} r
+      FO_CU(ctx, cudaMemcpyAsync(p, z, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      k_ext_dots<<<blocks, FO_BLOCK, 0, s>>>(r, z, r, r, N, part);
+      fo_note_launch(2);
+      auto sums = [&](double *a, double *b2) -> fo_status {
+        FO_CU(ctx, cudaMemcpyAsync(hp.data(), part, sizeof(double) * 2 * blocks, cudaMemcpyDeviceToHost, s));
+        FO_CU(ctx, cudaStreamSynchronize(s));
+        double t0 = 0, t1 = 0;
+        for (int b = 0; b < blocks; ++b) {
+          t0 += hp[2 * b];
+          t1 += hp[2 * b + 1];
+        }
+        *a = t0;
+        *b2 = t1;
+        return FO_OK;
+      };
+      double rz = 0, rr = 0;
+      FO_TRY(sums(&rz, &rr));
+      const double bb = rr;
+      int it = 0;
+      while (rr > o->rtol * o->rtol * bb && it < o->maxit && bb > 0) {
+        if (D == 2) {
+          StencilOp<2, 1, true, double> op;
+          op.g = g;
+          op.W = W;
+          k_ext_apply<2><<<blocks, FO_BLOCK, 0, s>>>(op, p, mask, 1.0, q);
+        } else {
+          StencilOp<3, 1, true, double> op;
+          op.g = g;
+          op.W = W;
+          k_ext_apply<3><<<blocks, FO_BLOCK, 0, s>>>(op, p, mask, 1.0, q);
+        }
+        k_ext_dots<<<blocks, FO_BLOCK, 0, s>>>(p, q, p, q, N, part);
+        fo_note_launch(2);
+        double pq = 0, unused = 0;
+        FO_TRY(sums(&pq, &unused));
+        if (!(pq > 0)) break;
+        const double alpha = rz / pq;
+        k_ext_update<<<blocks, FO_BLOCK, 0, s>>>(xc, r, z, p, q, dinv, alpha, N);
+        k_ext_dots<<<blocks, FO_BLOCK, 0, s>>>(r, z, r, r, N, part);
+        fo_note_launch(2);
+        double rz1 = 0;
+        FO_TRY(sums(&rz1, &rr));
+        k_ext_dir<<<blocks, FO_BLOCK, 0, s>>>(p, z, rz1 / rz, N);
+        fo_note_launch(1);
+        rz = rz1;
+        ++it;
+      }
+      iters += it;
+      if (!std::isfinite(rr)) return fo_fail(ctx, FO_ENAN, "NaN in the Dirichlet extension");
+      if (it >= o->maxit) return fo_fail(ctx, FO_ENOCONV, "Dirichlet extension reached maxit=%d", o->maxit);
+    }
+    // eta = fix + x, interleaved, into vals (device) and out to the host
+    k_ext_out<<<fo_blocks_for(N * D, FO_BLOCK, 65536), FO_BLOCK, 0, s>>>(fix, x, N, D, vals);
+    fo_note_launch(1);
+    FO_CU(ctx, cudaGetLastError());
+    FO_CU(ctx, cudaMemcpyAsync(out, vals, sizeof(double) * N * D, cudaMemcpyDeviceToHost, s));
+    FO_CU(ctx, cudaStreamSynchronize(s));
+    return FO_OK;
+  };
+  st = run();
+  release();
+  return st;
 }

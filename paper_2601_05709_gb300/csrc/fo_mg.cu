@@ -332,6 +332,8 @@ static void mg_release(fo_ctx *ctx, fo_mg *&mg) {
   mg = nullptr;
 }
 
+void fo_mg_release(fo_ctx *ctx, fo_mg *&mg) { mg_release(ctx, mg); }
+
 void fo_mg_destroy(fo_problem *p) {
   mg_release(p->ctx, p->mg);
   mg_release(p->ctx, p->mgv);

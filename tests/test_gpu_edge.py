@@ -1,0 +1,118 @@
+"""Edge cases of the hot path on the GPU: one-cell and strip meshes, level sets with every element
+inside or outside, zero loads, and the largest served 2D size (checked by properties that hold
+at any size: the solve criterion on the library's own operator and the Galerkin identity)."""
+import numpy as np
+import pytest
+
+from oracle import algorithm as oalg, ppl as oppl
+from paper_2601_05709_gb300 import workloads
+from tests.helpers import assert_solve_parity, cantilever2d, case, close_scaled, gpu_problem, oracle_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2601_05709_gb300 import api as a
+    return a
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def _tight(api, pc=0):
+    return api.solve_opts(rtol=1e-13, maxit=400000, precond=pc)
+
+
+@pytest.mark.parametrize("c", [
+    case(dim=2, n=(1, 1), kind=0, f=lambda X: np.ones(X.shape[0]), dirichlet=[(0, 0)], alpha_mass=0.01,
+         velocity_dirichlet=False),
+    case(dim=3, n=(1, 1, 1), kind=1, dirichlet=[(0, 0)], tractions=[(0, 1, (0.0, 0.0, -1.0))], volume=0.5),
+    case(dim=2, n=(64, 1), kind=1, dirichlet=[(0, 0)], tractions=[(0, 1, (0.0, -1.0))], volume=0.5),
+    case(dim=2, n=(1, 48), kind=0, f=lambda X: 1 + X[:, 1], dirichlet=[(1, 0)]),
+    case(dim=3, n=(24, 1, 1), kind=0, f=lambda X: np.ones(X.shape[0]), dirichlet=[(0, 0)]),
+])
+@pytest.mark.parametrize("pc", [0, 1], ids=["jacobi", "multigrid"])
+def test_degenerate_meshes_iteration(ctx, api, c, pc):
+    """One-cell and one-cell-wide meshes: one Algorithm-1 iteration against the oracle (multigrid
+    requests fall back to the Jacobi solver where no hierarchy exists)."""
+    mesh, prob = gpu_problem(ctx, c)
+    op = oracle_problem(c)
+    phi = workloads.phi_bumps(op.mesh.coords, workloads.bump_centres(c["lo"], c["hi"], 2, 0), 0.4, 0.6)
+    prob.set_levelset(phi)
+    so = _tight(api, pc)
+    ro = api.run_options(dfactor=1e-2, state=so, velocity=so, transport=api.solve_opts(rtol=1e-13, maxit=400000))
+    nc = 1 if c["volume"] > 0 else 0
+    log = prob.opt_step(0, ro, api.PPL(nc))
+    ophi, olog = oalg.opt_step(op, phi, 0, oppl.PPL(nc), oalg.RunOptions(dfactor=1e-2))
+    assert abs(log.J - olog["J"]) <= 1e-10 * abs(olog["J"])
+    assert abs(log.Btt - olog["Btt"]) <= 1e-9 * max(abs(olog["Btt"]), 1e-30)
+    assert log.nsteps == olog["nsteps"]
+    assert close_scaled(prob.get(api.FO_FIELD_THETA), olog["theta"], 1e-9)
+    assert close_scaled(prob.get(api.FO_FIELD_PHI), ophi, 1e-9)
+
+
+@pytest.mark.parametrize("inside", [True, False])
+@pytest.mark.parametrize("c", [case(dim=2, n=(32, 24), kind=0, f=lambda X: 1 + X[:, 0], dirichlet=[(0, 0)], volume=0.4),
+                               cantilever2d((32, 16))])
+def test_level_set_all_inside_or_outside(ctx, api, c, inside):
+    """A constant coefficient (every element inside, or every one outside): state, cost,
+    constraint and shape derivative against the oracle."""
+    mesh, prob = gpu_problem(ctx, c)
+    op = oracle_problem(c)
+    phi = np.full(op.mesh.num_nodes, -1.0 if inside else 1.0)
+    prob.set_levelset(phi)
+    prob.state_solve(_tight(api, 1))
+    u_ref, A, chi = op.state(phi)
+    assert np.all(A == (c["a_in"] if inside else c["a_out"]))
+    assert_solve_parity(op.stiffness(A), op.load(), op.dirichlet() == 0, prob.get(api.FO_FIELD_U), u_ref, 1e-10,
+                        omega_max=1e-12)
+    J, C = prob.functionals()
+    assert abs(J - op.cost(u_ref, A)) <= 1e-10 * abs(op.cost(u_ref, A))
+    assert C == pytest.approx(op.constraint(chi), rel=1e-14, abs=0.0)
+    prob.set(api.FO_FIELD_U, u_ref)
+    b = prob.shape_derivative(0.3)
+    b_ref = op.rhs(u_ref, A, chi, 0.3)
+    assert close_scaled(b, b_ref, 1e-12)
+
+
+def test_zero_load_gives_zero_everything(ctx, api):
+    """No load: u = 0 exactly, J = 0, and without a constraint b = 0 and theta = 0."""
+    c = case(dim=2, n=(40, 20), kind=1, dirichlet=[(0, 0)], alpha_mass=0.1)
+    mesh, prob = gpu_problem(ctx, c)
+    _, coords = mesh.copy_out()
+    prob.set_levelset(workloads.phi_cos(coords))
+    for pc in (0, 1):
+        prob.state_solve(_tight(api, pc))
+        assert np.all(prob.get(api.FO_FIELD_U) == 0.0)
+    J, _ = prob.functionals()
+    assert J == 0.0
+    b = prob.shape_derivative(0.0)
+    assert np.all(b == 0.0)
+    Btt, _ = prob.descent(_tight(api, 1))
+    assert Btt == 0.0 and np.all(prob.get(api.FO_FIELD_THETA) == 0.0)
+
+
+def test_largest_served_2d_size(ctx, api):
+    """The largest 2D request of the serving workload (1024 x 1024 heat, 1,050,625 nodes): the
+    multigrid state solve meets its criterion on the library's own operator, and the Galerkin
+    identity J = int A |grad u|^2 = F . u holds."""
+    n = 1024
+    mesh = ctx.mesh_box(2, (n, n), (0.0, 0.0), (1.0, 1.0))
+    _, coords = mesh.copy_out()
+    prob = mesh.problem(api.model_desc(api.FO_HEAT, dirichlet=[(0, 0)], f_nodal=np.ones(mesh.num_nodes)))
+    prob.set_levelset(workloads.phi_bumps(coords, workloads.bump_centres((0, 0), (1, 1), 20, seed=3), 0.1, 0.2))
+    st = prob.state_solve(api.solve_opts(rtol=1e-10, precond=api.FO_PC_MG))
+    assert st.iterations < 300, st.iterations
+    u = prob.get(api.FO_FIELD_U)
+    F = prob.get(api.FO_FIELD_LOAD)
+    r = F - prob.apply(api.FO_OP_STATE, u)
+    assert np.linalg.norm(r) <= 2e-10 * np.linalg.norm(F)
+    J, _ = prob.functionals()
+    assert abs(J - F @ u) <= 1e-9 * abs(J)

@@ -84,14 +84,19 @@ def _meas(m, npairs, seed=6):
     return [0.5 * workloads.smooth_field(m.coords, m.dim, seed + k) for k in range(npairs)]
 
 
-@pytest.mark.parametrize("dim,n,npairs", [(2, (24, 20), 1), (2, (17, 23), 2), (3, (6, 5, 5), 1)])
-def test_states_cost_adjoints(ctx, api, dim, n, npairs):
+@pytest.mark.parametrize("dim,n,npairs,pc", [(2, (24, 20), 1, 0), (2, (17, 23), 2, 0), (3, (6, 5, 5), 1, 0),
+                                           (2, (32, 24), 2, 1), (3, (8, 8, 4), 1, 1)])
+def test_states_cost_adjoints(ctx, api, dim, n, npairs, pc):
+    """Jacobi (pc 0) or multigrid (pc 1; the boundary-clamped systems on a hierarchy of their own)."""
     m = BoxMesh(dim, n, (0.0,) * dim, (1.0,) * dim)
     phi = _phi(m, 1)
     meas = _meas(m, npairs)
     A, chi, ref = _oracle(m, phi, meas, npairs)
     mesh, prob = _gpu(ctx, api, m, phi, meas, npairs)
-    prob.state_solve(_opts(api))
+    so = api.solve_opts(rtol=1e-13, maxit=400000, precond=pc)
+    st = prob.state_solve(so)
+    if pc == 1:
+        assert st.iterations < 600, st.iterations
     U = prob.get(api.FO_FIELD_U).reshape(npairs, -1)
     V = prob.get(api._lib.FO_FIELD_V).reshape(npairs, -1)
     for k in range(npairs):
@@ -100,7 +105,7 @@ def test_states_cost_adjoints(ctx, api, dim, n, npairs):
     J, _ = prob.functionals()
     J_ref = sum(r["J"] for r in ref)
     assert abs(J - J_ref) <= 1e-10 * abs(J_ref), (J, J_ref)
-    prob.adjoint_solve(_opts(api))
+    prob.adjoint_solve(so)
     P = prob.get(api.FO_FIELD_P).reshape(npairs, -1)
     Q = prob.get(api._lib.FO_FIELD_Q).reshape(npairs, -1)
     for k in range(npairs):
@@ -170,3 +175,21 @@ def test_algorithm_iteration(ctx, api):
     assert log.nsteps == ns
     assert close_scaled(prob.get(api.FO_FIELD_THETA), theta, 1e-9)
     assert close_scaled(prob.get(api.FO_FIELD_PHI), phi1, 1e-9)
+
+
+@pytest.mark.parametrize("dim,n", [(2, (23, 17)), (3, (6, 5, 4))])
+def test_dirichlet_extension(ctx, api, dim, n):
+    """fo_dirichlet_extension against the oracle's (Sec. 5.7): values kept on the faces, the
+    harmonic extension elsewhere; linear data extend to the linear field."""
+    m = BoxMesh(dim, n, (0.0,) * dim, (1.0,) * dim)
+    mesh = ctx.mesh_box(dim, n, (0.0,) * dim, (1.0,) * dim)
+    faces = [(0, 1), (1, 0), (1, 1)]
+    vals = workloads.smooth_field(m.coords, dim, 3)
+    eta = mesh.dirichlet_extension(faces, vals, api.solve_opts(rtol=1e-13, maxit=100000))
+    ref = inverse.dirichlet_extension(m, vals, faces)
+    assert close_scaled(eta, ref, 1e-10), np.max(np.abs(eta - ref))
+    G = np.random.default_rng(1).standard_normal((dim, dim))
+    lin = (m.coords @ G.T).reshape(-1)
+    eta = mesh.dirichlet_extension([(a, s) for a in range(dim) for s in (0, 1)], lin,
+                                   api.solve_opts(rtol=1e-13, maxit=100000))
+    assert close_scaled(eta, lin, 1e-10)
