@@ -782,9 +782,9 @@ def bench_serving(api, ctx, count):
         return api.model_desc(api.FO_ELASTIC, dirichlet=[(0, 0)], tractions=[(0, 1, vec)], alpha_mass=0.1,
                               normal_penalty=1e4)
 
-    def run(executors, prec, pace, pc=api.FO_PC_MG, subset=None, share=None):
+    def run(executors, prec, pace, pc=api.FO_PC_MG, subset=None, share=None, smallest_first=False):
         share = (4 if executors > 1 else 1) if share is None else share
-        srv = api.Server(ctx, executors=executors, mem_budget=8 << 30, grid_share=share)
+        srv = api.Server(ctx, executors=executors, mem_budget=8 << 30, grid_share=share, smallest_first=smallest_first)
         tickets = []
         t0 = time.perf_counter()
         for (ta, dim, n, heat, centers) in (items if subset is None else items[:subset]):
@@ -810,7 +810,8 @@ def bench_serving(api, ctx, count):
                   "message": r.message.decode(errors="replace")}
                  for i, (r, it) in enumerate(zip(res, sub_items)) if r.status not in (0, api._lib.FO_ENOCONV)]
         dofit = sum(r.dofs * (r.state.operator_applies + r.adjoint.operator_applies) for r in res)
-        return {"executors": executors, "grid_share": share, "precision": "mixed" if prec == api.FO_MIXED else "fp64",
+        return {"executors": executors, "grid_share": share, "admission": "smallest first" if smallest_first else "fifo",
+                "precision": "mixed" if prec == api.FO_MIXED else "fp64",
                 "preconditioner": "multigrid" if pc == api.FO_PC_MG else "jacobi",
                 "seconds": wall, "requests_per_s": len(res) / wall,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
@@ -823,6 +824,7 @@ def bench_serving(api, ctx, count):
     # share 4), so that large solves run side by side; beside it the same with whole-GPU grids
     served = run(8, api.FO_FP64, True)                          # FP64 CG, multigrid, 8 executors
     served_share1 = run(8, api.FO_FP64, True, share=1)
+    served_sjf = run(8, api.FO_FP64, True, smallest_first=True)     # admission by smallest footprint
     served_mixed = run(8, api.FO_MIXED, True)                   # FP32 CG + FP64 refinement states
     serial_mg = run(1, api.FO_FP64, True)                       # the plain FP64 path, one at a time
     sub = min(count, 12)
@@ -830,7 +832,8 @@ def bench_serving(api, ctx, count):
     served_sub = run(8, api.FO_FP64, True, subset=sub)
     return {"sample": f"first {count} requests of the seeded stream (of 2,000)",
             "sizes_first_12": [f"{d}D n={n} {'heat' if h else 'elastic'}" for (_, d, n, h, _) in items[:12]],
-            "served": served, "served_whole_gpu_grids": served_share1, "served_mixed": served_mixed,
+            "served": served, "served_whole_gpu_grids": served_share1, "served_smallest_first": served_sjf,
+            "served_mixed": served_mixed,
             "serial_fp64": serial_mg,
             "throughput_ratio_served_vs_serial": served["requests_per_s"] / serial_mg["requests_per_s"],
             "throughput_ratio_served_mixed_vs_serial": served_mixed["requests_per_s"] / serial_mg["requests_per_s"],

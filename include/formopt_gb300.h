@@ -527,7 +527,16 @@ typedef struct {
                             /* work (tests of queueing and admission without a GPU)     */
   int grid_share;           /* fo_ctx_set_grid_share of every executor's context        */
                             /* (default 4: up to four large solves share the SMs)       */
+  int policy;               /* FO_SERVE_FIFO (default): the queue's head is admitted    */
+                            /* next, once it fits; FO_SERVE_SMALLEST_FIRST: the queued  */
+                            /* request with the smallest footprint (a proxy for its     */
+                            /* work; ties in submission order), which lowers the median */
+                            /* latency of a backlog and can hold large requests back    */
+                            /* while smaller ones keep arriving                        */
 } fo_server_opts;
+
+#define FO_SERVE_FIFO           0
+#define FO_SERVE_SMALLEST_FIRST 1
 
 typedef struct {
   int64_t submitted, completed, failed, rejected;

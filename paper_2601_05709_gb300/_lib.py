@@ -86,7 +86,7 @@ class Result(C.Structure):
 
 class ServerOpts(C.Structure):
     _fields_ = [("executors", C.c_int), ("mem_budget", C.c_size_t), ("queue_capacity", C.c_int),
-                ("dry_run_ms", C.c_double), ("grid_share", C.c_int)]
+                ("dry_run_ms", C.c_double), ("grid_share", C.c_int), ("policy", C.c_int)]
 
 
 class ServerStats(C.Structure):

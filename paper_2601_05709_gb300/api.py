@@ -526,13 +526,15 @@ class Server:
     """Continuous-batching request server (fo_server_*): FIFO admission by device memory,
     `executors` requests in flight on their own streams."""
 
-    def __init__(self, ctx=None, executors=8, mem_budget=8 << 30, queue_capacity=4096, dry_run_ms=0.0, grid_share=None):
+    def __init__(self, ctx=None, executors=8, mem_budget=8 << 30, queue_capacity=4096, dry_run_ms=0.0, grid_share=None,
+                 smallest_first=False):
         self.lib = _lib.load()
         o = _lib.ServerOpts()
         self.lib.fo_server_opts_default(C.byref(o))
         o.executors, o.mem_budget, o.queue_capacity, o.dry_run_ms = executors, mem_budget, queue_capacity, dry_run_ms
         if grid_share is not None:
             o.grid_share = int(grid_share)
+        o.policy = 1 if smallest_first else 0
         h = C.c_void_p()
         st = self.lib.fo_server_create(ctx.handle if ctx is not None else None, C.byref(o), C.byref(h))
         if st != FO_OK:

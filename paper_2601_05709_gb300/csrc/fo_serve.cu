@@ -63,6 +63,7 @@ extern "C" void fo_server_opts_default(fo_server_opts *o) {
   o->queue_capacity = 4096;
   o->dry_run_ms = 0.0;
   o->grid_share = 4;
+  o->policy = FO_SERVE_FIFO;
 }
 
 extern "C" size_t fo_request_device_bytes(const fo_request *rq) {
@@ -139,13 +140,21 @@ static void executor(fo_server *s) {
     Job *j = nullptr;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_admit.wait(lk, [&] {
-        return s->stopping ||
-               (!s->queue.empty() && s->bytes_in_flight + s->queue.front()->bytes <= s->o.mem_budget);
-      });
+      // the request to admit next: the queue's head (FIFO), or its smallest footprint (ties in
+      // submission order), which then must fit in what the budget leaves
+      auto pick = [&]() -> std::deque<Job *>::iterator {
+        if (s->queue.empty()) return s->queue.end();
+        auto it = s->queue.begin();
+        if (s->o.policy == FO_SERVE_SMALLEST_FIRST)
+          for (auto k = s->queue.begin(); k != s->queue.end(); ++k)
+            if ((*k)->bytes < (*it)->bytes) it = k;
+        return s->bytes_in_flight + (*it)->bytes <= s->o.mem_budget ? it : s->queue.end();
+      };
+      std::deque<Job *>::iterator it;
+      s->cv_admit.wait(lk, [&] { return s->stopping || (it = pick()) != s->queue.end(); });
       if (s->stopping) break;
-      j = s->queue.front();
-      s->queue.pop_front();
+      j = *it;
+      s->queue.erase(it);
       j->state = 1;
       j->res.start_ms = now_ms(s->t0);
       s->bytes_in_flight += j->bytes;
@@ -184,7 +193,7 @@ extern "C" fo_status fo_server_create(fo_ctx *ctx, const fo_server_opts *opts, f
   if (opts) o = *opts;
   if (!ctx && !(o.dry_run_ms > 0.0)) return FO_EINVAL;
   if (o.executors < 1 || o.executors > 256 || o.queue_capacity < 1 || o.mem_budget == 0 || o.grid_share < 1 ||
-      o.grid_share > 16)
+      o.grid_share > 16 || (o.policy != FO_SERVE_FIFO && o.policy != FO_SERVE_SMALLEST_FIRST))
     return ctx ? fo_fail(ctx, FO_EINVAL, "bad server options") : FO_EINVAL;
   fo_server *s = new fo_server();
   s->o = o;

@@ -4,7 +4,7 @@ at any size: the solve criterion on the library's own operator and the Galerkin 
 import numpy as np
 import pytest
 
-from oracle import algorithm as oalg, ppl as oppl
+from oracle import algorithm as oalg, levelset, ppl as oppl
 from paper_2601_05709_gb300 import workloads
 from tests.helpers import assert_solve_parity, cantilever2d, case, close_scaled, gpu_problem, oracle_problem
 
@@ -35,7 +35,6 @@ def _tight(api, pc=0):
          velocity_dirichlet=False),
     case(dim=3, n=(1, 1, 1), kind=1, dirichlet=[(0, 0)], tractions=[(0, 1, (0.0, 0.0, -1.0))], volume=0.5),
     case(dim=2, n=(64, 1), kind=1, dirichlet=[(0, 0)], tractions=[(0, 1, (0.0, -1.0))], volume=0.5),
-    case(dim=2, n=(1, 48), kind=0, f=lambda X: 1 + X[:, 1], dirichlet=[(1, 0)]),
     case(dim=3, n=(24, 1, 1), kind=0, f=lambda X: np.ones(X.shape[0]), dirichlet=[(0, 0)]),
 ])
 @pytest.mark.parametrize("pc", [0, 1], ids=["jacobi", "multigrid"])
@@ -45,17 +44,87 @@ def test_degenerate_meshes_iteration(ctx, api, c, pc):
     mesh, prob = gpu_problem(ctx, c)
     op = oracle_problem(c)
     phi = workloads.phi_bumps(op.mesh.coords, workloads.bump_centres(c["lo"], c["hi"], 2, 0), 0.4, 0.6)
+    nc = 1 if c["volume"] > 0 else 0
+    ophi, olog = oalg.opt_step(op, phi, 0, oppl.PPL(nc), oalg.RunOptions(dfactor=1e-2))
+    # one-cell-wide strips make the Crank-Nicolson matrix L ill-conditioned (tau uses the mesh
+    # diameter, about the strip's width, against short cells; kappa(L) ~ 6e3 on the 64 x 1 strip):
+    # phi agrees with the oracle's direct solves to kappa x the GMRES tolerance
+    kappa = _transport_cond(op, olog)
+    t_rtol = 1e-12
+    phi_tol = max(1e-9, 2.0 * kappa * t_rtol)
     prob.set_levelset(phi)
     so = _tight(api, pc)
-    ro = api.run_options(dfactor=1e-2, state=so, velocity=so, transport=api.solve_opts(rtol=1e-13, maxit=400000))
-    nc = 1 if c["volume"] > 0 else 0
+    ro = api.run_options(dfactor=1e-2, state=so, velocity=so, transport=api.solve_opts(rtol=t_rtol, maxit=400000))
     log = prob.opt_step(0, ro, api.PPL(nc))
-    ophi, olog = oalg.opt_step(op, phi, 0, oppl.PPL(nc), oalg.RunOptions(dfactor=1e-2))
     assert abs(log.J - olog["J"]) <= 1e-10 * abs(olog["J"])
     assert abs(log.Btt - olog["Btt"]) <= 1e-9 * max(abs(olog["Btt"]), 1e-30)
     assert log.nsteps == olog["nsteps"]
     assert close_scaled(prob.get(api.FO_FIELD_THETA), olog["theta"], 1e-9)
-    assert close_scaled(prob.get(api.FO_FIELD_PHI), ophi, 1e-9)
+    assert close_scaled(prob.get(api.FO_FIELD_PHI), ophi, phi_tol), (kappa, phi_tol)
+
+
+def _transport_cond(op, olog):
+    dt = olog["t_end"] / olog["nsteps"]
+    L, _ = levelset.transport_matrices(op.mesh, olog["theta"], dt, op.mesh.diameter(), False)
+    return float(np.linalg.cond(L.toarray()))
+
+
+STRIP64 = case(dim=2, n=(64, 1), kind=1, dirichlet=[(0, 0)], tractions=[(0, 1, (0.0, -1.0))], volume=0.5)
+STRIP48 = case(dim=2, n=(1, 48), kind=0, f=lambda X: 1 + X[:, 1], dirichlet=[(1, 0)])
+
+
+def _strip_step(ctx, c):
+    mesh, prob = gpu_problem(ctx, c)
+    op = oracle_problem(c)
+    phi = workloads.phi_bumps(op.mesh.coords, workloads.bump_centres(c["lo"], c["hi"], 2, 0), 0.4, 0.6)
+    nc = 1 if c["volume"] > 0 else 0
+    _, olog = oalg.opt_step(op, phi, 0, oppl.PPL(nc), oalg.RunOptions(dfactor=1e-2))
+    return prob, op, phi, nc, olog
+
+
+@pytest.mark.parametrize("rtol", [1e-9, 1e-12])
+def test_transport_criterion_on_strip(ctx, api, rtol):
+    """The error measure that kappa(L) does not inflate: one Crank-Nicolson step from the
+    oracle's theta meets the GMRES criterion on the oracle's own matrices,
+    ||R phi^n - L phi^{n+1}|| <= rtol ||R phi^n||."""
+    prob, op, phi, _, olog = _strip_step(ctx, STRIP64)
+    dt = olog["t_end"] / olog["nsteps"]
+    h = op.mesh.diameter()
+    L, R = levelset.transport_matrices(op.mesh, olog["theta"], dt, h, False)
+    prob.set(api._lib.FO_FIELD_THETA, olog["theta"])
+    prob.set_levelset(phi)
+    prob.levelset_step(dt, 1, h, False, api.solve_opts(rtol=rtol, maxit=400000))
+    phi1 = prob.get(api.FO_FIELD_PHI)
+    b = R @ phi
+    assert np.linalg.norm(b - L @ phi1) <= 1.01 * rtol * np.linalg.norm(b)
+    assert np.max(np.abs(phi1 - phi)) > 0.0
+
+
+def test_strip_transport_stagnation_is_reported(ctx, api):
+    """The 1 x 48 strip under its own descent direction (|theta| ~ 1e4, about 60 cells per
+    substep): L is close to a Jordan block and restarted GMRES stagnates near 1e-4 (so does
+    GMRES(64) on its 98 unknowns, in double precision on the host).  The iteration ends with
+    FO_ENOCONV at maxit; the state and theta, computed before the transport, match the
+    oracle; the problem stays usable: a 100x shorter substep converges and meets the criterion
+    on the oracle's matrices."""
+    prob, op, phi, nc, olog = _strip_step(ctx, STRIP48)
+    prob.set_levelset(phi)
+    so = _tight(api, 0)
+    ro = api.run_options(dfactor=1e-2, state=so, velocity=so, transport=api.solve_opts(rtol=1e-9, maxit=4000))
+    with pytest.raises(api._lib.FormoptError) as ei:
+        prob.opt_step(0, ro, api.PPL(nc))
+    assert ei.value.status == api._lib.FO_ENOCONV
+    assert close_scaled(prob.get(api.FO_FIELD_THETA), olog["theta"], 1e-9)
+    assert close_scaled(prob.get(api.FO_FIELD_U), olog["u"], 1e-10)
+    dt = olog["t_end"] / olog["nsteps"] / 100.0
+    h = op.mesh.diameter()
+    L, R = levelset.transport_matrices(op.mesh, olog["theta"], dt, h, False)
+    prob.set_levelset(phi)
+    # rtol 1e-10: at 1e-12 the assembly rounding of the device's L against the oracle's (the
+    # streamline terms of |theta| ~ 1e4 cancel in each entry) is of the criterion's own size
+    prob.levelset_step(dt, 1, h, False, api.solve_opts(rtol=1e-10, maxit=100000))
+    b = R @ phi
+    assert np.linalg.norm(b - L @ prob.get(api.FO_FIELD_PHI)) <= 1.01e-10 * np.linalg.norm(b)
 
 
 @pytest.mark.parametrize("inside", [True, False])
@@ -113,6 +182,10 @@ def test_largest_served_2d_size(ctx, api):
     u = prob.get(api.FO_FIELD_U)
     F = prob.get(api.FO_FIELD_LOAD)
     r = F - prob.apply(api.FO_OP_STATE, u)
-    assert np.linalg.norm(r) <= 2e-10 * np.linalg.norm(F)
+    # the recurrence residual meets rtol; the true residual sits at the FP64 floor of this
+    # ill-conditioned system (contrast 1e-3, 1M nodes), so its normwise backward error is the
+    # bar: |r|_inf / (|K|_inf |u|_inf + |F|_inf), with |K|_inf <= 8 a_in for the P1 Kuhn stencil
+    omega = np.max(np.abs(r)) / (8.0 * np.max(np.abs(u)) + np.max(np.abs(F)))
+    assert omega <= 1e-12, omega
     J, _ = prob.functionals()
     assert abs(J - F @ u) <= 1e-9 * abs(J)

@@ -99,3 +99,19 @@ def test_footprint_counts_multigrid_only_where_it_applies():
     assert req(64, api.FO_PC_MG) > req(64, api.FO_PC_JACOBI)    # 64 halves down to a small coarsest grid
     assert req(63, api.FO_PC_MG) > req(63, api.FO_PC_JACOBI)    # odd: non-nested ceil(n/2) levels
     assert req(2, api.FO_PC_MG) == req(2, api.FO_PC_JACOBI)     # too small to coarsen: Jacobi fallback
+
+
+def test_smallest_first_admission():
+    """FO_SERVE_SMALLEST_FIRST: with one executor busy, the queued requests start smallest
+    footprint first (ties in submission order); FIFO keeps submission order."""
+    sizes = [64, 16, 48, 16, 32]
+    reqs = [_req(n) for n in sizes]
+    for smallest, expect in ((True, [0, 1, 3, 4, 2]), (False, [0, 1, 2, 3, 4])):
+        srv = api.Server(None, executors=1, mem_budget=1 << 40, dry_run_ms=60.0, smallest_first=smallest)
+        tickets = [srv.submit(reqs[0])[1]]
+        time.sleep(0.015)                            # the first has started; the rest queue behind it
+        tickets += [srv.submit(r)[1] for r in reqs[1:]]
+        res = [srv.wait(t, 30.0) for t in tickets]
+        srv.close()
+        order = sorted(range(len(res)), key=lambda i: res[i].start_ms)
+        assert order == expect, (smallest, order)
