@@ -162,8 +162,7 @@ __device__ __forceinline__ double stencil_row(const Grid &g, const double *M, lo
   double acc = 0;
 #pragma unroll
   for (int s = 0; s < ST<D>::S; ++s) {
-    const long long nb = slot_node<D>(g, idx, a, s);
-    if (nb >= 0) acc += M[s * g.num_nodes + a] * x(nb);
+    acc += M[s * g.num_nodes + a] * x(slot_node_or_self<D>(g, idx, a, s));
   }
   return acc;
 }
@@ -293,8 +292,8 @@ __device__ bool arnoldi_step(const Grid &g, const double *M, const double *dinv,
     double wa = 0.0;
 #pragma unroll
     for (int s = 0; s < ST<D>::S; ++s) {
-      const long long nb = slot_node<D>(g, idx, a, s);
-      if (nb >= 0) wa += M[s * N + a] * (dinv[nb] * Vj[nb]);
+      const long long nb = slot_node_or_self<D>(g, idx, a, s);
+      wa += M[s * N + a] * (dinv[nb] * Vj[nb]);
     }
     K.w[a] = wa;
 #pragma unroll
@@ -421,12 +420,10 @@ __device__ int gmres_solve(const Grid &g, const double *M, const double *dinv, c
         double la = 0.0;
 #pragma unroll
         for (int s = 0; s < ST<D>::S; ++s) {
-          const long long nb = slot_node<D>(g, idx, a, s);
-          if (nb >= 0) {
-            const double xv = x[nb];
-            ra += Rm[s * N + a] * xv;
-            la += M[s * N + a] * (order == 0 ? xv : start(nb));
-          }
+          const long long nb = slot_node_or_self<D>(g, idx, a, s);
+          const double xv = x[nb];
+          ra += Rm[s * N + a] * xv;
+          la += M[s * N + a] * (order == 0 ? xv : start(nb));
         }
         K.rhs[a] = ra;
         ra = ra - la;
@@ -435,8 +432,7 @@ __device__ int gmres_solve(const Grid &g, const double *M, const double *dinv, c
         double la = 0.0;
 #pragma unroll
         for (int s = 0; s < ST<D>::S; ++s) {
-          const long long nb = slot_node<D>(g, idx, a, s);
-          if (nb >= 0) la += M[s * N + a] * x[nb];
+          la += M[s * N + a] * x[slot_node_or_self<D>(g, idx, a, s)];
         }
         ra = K.rhs[a] - la;
       }

