@@ -394,7 +394,8 @@ FO_API fo_status fo_apply(fo_problem *prob, int op, const double *x, double *y, 
  * callers that cannot let a library call cudaMalloc / cudaFree while they run -- those calls
  * may synchronise the whole device (a stall a latency-bound loop cannot take), and another
  * framework's caching allocator or a fixed memory budget may already own the device memory.
- * Computes the same FP64 Jacobi-PCG solve K_A x = b as fo_state_solve, but its working
+ * Solves K_A x = b with fo_state_solve's FP64 Jacobi-PCG (FO_PC_JACOBI: the same recurrence,
+ * then at most two restarts from the true residual b - A x while it is above rtol), but its working
  * memory (Krylov vectors, reduction partials, grid-barrier counter, status words) is one
  * fixed array of FO_NOALLOC_SCRATCH_BYTES that the library declares in device memory; every
  * GPU that loads the library holds it until the process exits.

@@ -669,37 +669,52 @@ static fo_status noalloc_pcg(fo_problem *p, const Op &op, const double *b, doubl
   unsigned *bar = (unsigned *)base;
   int *status = (int *)(base + 8);
   double *out = base + 16;
-  // the counter must start at zero and the status words are read back: clear them (the
-  // array keeps whatever the previous call left there)
-  FO_CU(ctx, cudaMemsetAsync(base, 0, 64 * sizeof(double), ctx->stream));
-  PcgArgs<1, double> a{};
-  bind_vectors(a, x, base + FO_NOALLOC_HEADER, n);
-  a.b = b;
-  a.bscale = 1.0;
-  a.dinv = p->dinv_state;
-  a.rtol2 = o->rtol * o->rtol;
-  a.maxit = o->maxit;
-  a.warm = o->warm_start;
-  a.partials = base + 64;
-  a.out = out;
-  a.status = status;
-  a.bar = GridBar{bar, status + DS_ERR, 2000000000ull};
   auto kern = k_pcg<D, Op, double, 1>;
   const int block = fo_persistent_block(p, p->mesh->g.num_nodes);
   int grid;
   FO_TRY(fo_cooperative_grid(p, (const void *)kern, block, 0, p->mesh->g.num_nodes, o->grid_blocks, &grid));
-  void *argv[] = {(void *)&op, (void *)&a};
-  FO_CU(ctx, cudaLaunchCooperativeKernel((const void *)kern, grid, block, argv, 0, ctx->stream));
-  fo_note_launch(1);
-  FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars, out, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars + 32, status, sizeof(int) * DS_COUNT, cudaMemcpyDeviceToHost, ctx->stream));
-  FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
   const int *hs = (const int *)(ctx->h_scalars + 32);
+  // one persistent launch (warm: from x, forming b - A x afresh); its iterations and status
+  auto launch = [&](int warm, int maxit) -> fo_status {
+    // the counter must start at zero and the status words are read back: clear them (the
+    // array keeps whatever the previous launch or call left there)
+    FO_CU(ctx, cudaMemsetAsync(base, 0, 64 * sizeof(double), ctx->stream));
+    PcgArgs<1, double> a{};
+    bind_vectors(a, x, base + FO_NOALLOC_HEADER, n);
+    a.b = b;
+    a.bscale = 1.0;
+    a.dinv = p->dinv_state;
+    a.rtol2 = o->rtol * o->rtol;
+    a.maxit = maxit;
+    a.warm = warm;
+    a.partials = base + 64;
+    a.out = out;
+    a.status = status;
+    a.bar = GridBar{bar, status + DS_ERR, 2000000000ull};
+    void *argv[] = {(void *)&op, (void *)&a};
+    FO_CU(ctx, cudaLaunchCooperativeKernel((const void *)kern, grid, block, argv, 0, ctx->stream));
+    fo_note_launch(1);
+    FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars, out, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars + 32, status, sizeof(int) * DS_COUNT, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+    FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return FO_OK;
+  };
+  FO_TRY(launch(o->warm_start, o->maxit));
+  int iters = hs[DS_ITERS], launches = 1;
+  // The single-reduction recurrence updates its residual recursively and may drift from
+  // b - A x over many iterations.  As in fo_state_solve, restart from x at most twice: a warm
+  // launch starts from the true residual and stops at once when that meets rtol.
+  for (int restart = 0; restart < 2 && hs[DS_ERR] == DEV_OK && hs[DS_ITERS] > 0 && iters < o->maxit; ++restart) {
+    FO_TRY(launch(1, o->maxit - iters));
+    iters += hs[DS_ITERS];
+    ++launches;
+  }
   if (st) {
     memset(st, 0, sizeof *st);
-    st->iterations = hs[DS_ITERS];
-    st->operator_applies = hs[DS_ITERS] + 1 + (o->warm_start ? 1 : 0);
-    st->outer_iterations = 1;
+    st->iterations = iters;
+    st->operator_applies = iters + 1 + (o->warm_start ? 1 : 0) + 2 * (launches - 1);
+    st->outer_iterations = launches;
     st->rel_residual = ctx->h_scalars[1] > 0 ? std::sqrt(ctx->h_scalars[0] / ctx->h_scalars[1]) : 0.0;
   }
   if (hs[DS_ERR] == DEV_TIMEOUT) return fo_fail(ctx, FO_ETIMEOUT, "grid barrier timed out in PCG");

@@ -7,16 +7,18 @@ working memory is a fixed array inside the library.  This file is collected last
 run stopping at the first failure has already run every other test.
 
 The check: through the C ABI, two calls in a row give the result of the ordinary entry
-point fo_state_solve on the same problem (within the FP64 solve tolerance of the parity
-tests), the context's device-memory count does not move, and a problem larger than the
-array is refused with FO_EINVAL.
+point fo_state_solve on the same problem under the solve criterion of the parity tests (the
+two solvers sum in different orders, and the 128 x 64 cantilever's Skeel condition is ~1e9:
+1e-10 where the conditioning allows it, else a componentwise backward error at the rounding
+level and a forward difference within the perturbation bound), the context's device-memory
+count does not move, and a problem larger than the array is refused with FO_EINVAL.
 """
 import ctypes as C
 
 import numpy as np
 import pytest
 
-from tests.helpers import HEAT2D, cantilever2d, case, gpu_problem, rel
+from tests.helpers import HEAT2D, assert_solve_parity, cantilever2d, case, gpu_problem, oracle_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -48,6 +50,9 @@ def test_noalloc_matches_state_solve(api, c):
         opts = api.solve_opts(rtol=1e-12)
         prob.state_solve(opts)                                  # the ordinary entry point
         u_ref = prob.get(api._lib.FO_FIELD_U)
+        op = oracle_problem(c)
+        _, A, _ = op.state(workloads.phi_cos(op.mesh.coords))
+        K, F, free = op.stiffness(A), op.load(), op.dirichlet() == 0
         b = torch.from_numpy(prob.get(api._lib.FO_FIELD_LOAD)).cuda()
         torch.cuda.synchronize()
         before = ctx.memory()
@@ -56,7 +61,7 @@ def test_noalloc_matches_state_solve(api, c):
             s, st = _noalloc(api, prob, b, x, opts)
             assert s == 0, api._lib.STATUS_NAMES.get(s, s)
             u = x.cpu().numpy()
-            assert rel(u, u_ref) <= 1e-10, (call, rel(u, u_ref))
+            assert_solve_parity(K, F, free, u, u_ref, 1e-10, omega_max=1e-12)
             assert st.iterations > 0 and st.rel_residual <= 1e-12
         assert ctx.memory() == before                           # nothing allocated by the calls
     finally:
