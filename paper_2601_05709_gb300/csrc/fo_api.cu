@@ -369,12 +369,14 @@ extern "C" fo_status fo_mesh_copy_out(const fo_mesh *m, int32_t *cells, double *
 // `entries`: stored operator entries per block slot -- S N_n on the structured grid (S stencil
 // slots per node), the node graph's nonzeros on a general mesh; `vel_blk`: entries per velocity
 // block (d: component-diagonal on the box grid; d^2 on a general mesh).
+// entries: stencil entries of the transport rows (all slots, or the general mesh's CSR);
+// rows: those of the stored symmetric state and velocity rows (the stored slots, or the CSR).
 static std::vector<size_t> problem_field_sizes(int d, long long NN, long long NT, long long ND, bool with_f,
-                                               long long entries, int vel_blk, int ncases = 1) {
-  const size_t E = (size_t)entries;
+                                               long long entries, long long rows, int vel_blk, int ncases = 1) {
+  const size_t E = (size_t)entries, ER = (size_t)rows;
   const size_t npn = (size_t)(ND / NN);   // state components per node
   std::vector<size_t> v = {
-      sizeof(double) * E * npn * npn, sizeof(float) * E * npn * npn, sizeof(double) * E * vel_blk,
+      sizeof(double) * ER * npn * npn, sizeof(float) * ER * npn * npn, sizeof(double) * ER * vel_blk,
       sizeof(double) * NN,     sizeof(double) * NT,     sizeof(float) * NT,       (size_t)NT,
       (size_t)NT,              (size_t)ND,              (size_t)NN,               sizeof(double) * ND * ncases,
       sizeof(double) * ND * ncases, sizeof(double) * ND * ncases, sizeof(double) * d * NN, sizeof(double) * d * NN,
@@ -389,8 +391,9 @@ static std::vector<size_t> problem_field_sizes(int d, long long NN, long long NT
 static size_t prob_bytes_fields(const fo_problem *p, std::vector<std::pair<void **, size_t>> &list) {
   const Grid &g = p->mesh->g;
   const long long entries = p->mesh->um ? p->mesh->um->nnz : (long long)(g.dim == 2 ? 7 : 15) * g.num_nodes;
+  const long long rows = p->mesh->um ? p->mesh->um->nnz : (long long)fo_row_slots(g.dim) * g.num_nodes;
   const std::vector<size_t> sz = problem_field_sizes(g.dim, g.num_nodes, g.num_elems, p->ndof,
-                                                     p->f || p->desc.kind != FO_ELASTIC, entries,
+                                                     p->f || p->desc.kind != FO_ELASTIC, entries, rows,
                                                      p->mesh->um ? g.dim * g.dim : g.dim, p->ncases);
   std::vector<void **> ptr = {
       (void **)&p->Wst,        (void **)&p->Wst32,        (void **)&p->Wvel,
@@ -424,7 +427,8 @@ size_t fo_problem_footprint(int dim, const int n[3], int kind, int state_vecs, i
   const long long NT = cells * (dim == 2 ? 2 : 6);
   const long long ND = NN * (kind == FO_ELASTIC ? dim : 1);
   size_t total = sizeof(int32_t) * NT * (dim + 1) + sizeof(double) * NN * dim;   // mesh
-  for (size_t b : problem_field_sizes(dim, NN, NT, ND, kind != FO_ELASTIC, (dim == 2 ? 7 : 15) * NN, dim))
+  for (size_t b : problem_field_sizes(dim, NN, NT, ND, kind != FO_ELASTIC, (dim == 2 ? 7 : 15) * NN,
+                                      (long long)fo_row_slots(dim) * NN, dim))
     total += b;
   const size_t state = sizeof(double) * state_vecs * (size_t)ND;
   const size_t vel = sizeof(double) * vel_vecs * (size_t)dim * NN;

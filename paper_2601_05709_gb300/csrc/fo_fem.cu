@@ -464,7 +464,7 @@ __global__ void k_state_stencil(Grid g, const double *coef, const uint8_t *dir, 
 #pragma unroll
     for (int k = 0; k < BLK; ++k) w[0][k] = R[k];
 #pragma unroll
-    for (int s = 0; s < S; ++s)
+    for (int s = 0; s < ST<D>::SH; ++s)   // the stored slots (symmetric operator)
 #pragma unroll
       for (int k = 0; k < BLK; ++k) {
         W[(s * BLK + k) * N + a] = w[s][k];
@@ -591,7 +591,7 @@ __global__ void k_velocity_stencil(Grid g, const uint8_t *omega0, const double *
 #pragma unroll
     for (int c = 0; c < D; ++c) w[0][c] = R[c];
 #pragma unroll
-    for (int s = 0; s < S; ++s)
+    for (int s = 0; s < ST<D>::SH; ++s)   // the stored slots (symmetric operator)
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         W[(s * D + c) * N + a] = w[s][c];

@@ -269,7 +269,15 @@ __device__ __forceinline__ int stencil_slot(const int delta[3]) {
   if (neg == 0) return pos;
   return (1 << D) - 1 + neg;
 }
-template <int D> struct ST { static constexpr int S = (D == 2) ? 7 : 15; };
+// Stencil slots of a node (itself and its Kuhn neighbours); stored operator rows keep the first
+// SH of them (the node's own slot and its positive-direction neighbours, slot_offset below):
+// the operators stored by rows are symmetric, so a negative-direction block is the transpose of
+// the neighbour's block in the opposite slot.
+template <int D> struct ST {
+  static constexpr int S = (D == 2) ? 7 : 15;
+  static constexpr int SH = 1 << D;
+};
+inline int fo_row_slots(int dim) { return dim == 2 ? 4 : 8; }
 
 template <int D>
 __device__ __forceinline__ void slot_offset(int s, int delta[3]) {

@@ -285,7 +285,7 @@ fo_status fo_inverse_create(fo_problem *p, const fo_model_desc *desc) {
   const Grid &g = p->mesh->g;
   fo_inv *iv = new fo_inv();
   p->inv = iv;
-  const size_t nd = (size_t)p->ndof, nc = (size_t)p->ncases, S = g.dim == 2 ? 7 : 15, blk = (size_t)g.dim * g.dim;
+  const size_t nd = (size_t)p->ndof, nc = (size_t)p->ncases, S = (size_t)fo_row_slots(g.dim), blk = (size_t)g.dim * g.dim;
   auto add = [&](void **ptr, size_t bytes) { iv->allocs.push_back({ptr, bytes}); };
   add((void **)&iv->v, sizeof(double) * nd * nc);
   add((void **)&iv->q, sizeof(double) * nd * nc);
@@ -583,7 +583,7 @@ extern "C" fo_status fo_dirichlet_extension(fo_mesh *m, uint32_t faces, const do
   const fo_solve_opts *o = opts ? opts : &def;
   const Grid &g = m->g;
   const int D = g.dim;
-  const long long N = g.num_nodes, S = D == 2 ? 7 : 15;
+  const long long N = g.num_nodes, S = fo_row_slots(D);
   std::vector<std::pair<void **, size_t>> al;
   double *vals, *fix, *x, *r, *z, *p, *q, *W, *dinv, *ones, *part;
   float *W32, *dinv32;

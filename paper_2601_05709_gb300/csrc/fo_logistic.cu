@@ -129,7 +129,7 @@ __global__ void k_logistic_newton(Grid g, const double *Kc, const uint8_t *dir, 
     }
     w[0] = R;
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
+    for (int s = 0; s < ST<D>::SH; ++s) {   // the stored slots (the Jacobian is symmetric)
       W[s * N + a] = w[s];
       W32[s * N + a] = (float)w[s];
     }

@@ -180,7 +180,7 @@ __global__ void k_mg_coarse_inverse(Grid g, const double *W, int n, float *ainv)
         for (int s = 1; s < S; ++s) {
           const long long nb = slot_node<D>(g, idx, a, s);
           if (nb < 0) continue;
-          const double w = W[((long long)s * BLK + e) * N + a];
+          const double w = *slot_weight<D, NPN, FULL>(W, N, a, nb, s, e);
           diag -= w;
           A[r * n + nb * NPN + k] += w;
         }
@@ -279,7 +279,7 @@ int fo_mg_plan(const Grid &g0, Grid *g, int max_levels, long long stop_unknowns,
 // Byte sizes of level l's arrays, in the order b, z0, z1, t, coef, W64, W32, dinv64, dinv32, dir
 // (coarse levels own all; level 0 owns coef, W32, dinv32 and dir only when own0).
 static void mg_sizes(const Grid &g, int npn, int blk, bool coarse, bool own0, size_t sz[10]) {
-  const size_t N = (size_t)g.num_nodes, S = g.dim == 2 ? 7 : 15;
+  const size_t N = (size_t)g.num_nodes, S = (size_t)fo_row_slots(g.dim);
   for (int i = 0; i < 4; ++i) sz[i] = sizeof(float) * N * npn;
   sz[4] = (coarse || own0) ? sizeof(double) * g.num_elems : 0;
   sz[5] = coarse ? sizeof(double) * S * blk * N : 0;
@@ -306,7 +306,7 @@ static void **mg_slot(fo_mg *mg, int l, int i) {
 
 // Bytes of a level's BF16 rows.
 static size_t mg_bf16_bytes(const Grid &g, int blk) {
-  return sizeof(__nv_bfloat16) * (size_t)(g.dim == 2 ? 7 : 15) * blk * (size_t)g.num_nodes;
+  return sizeof(__nv_bfloat16) * (size_t)fo_row_slots(g.dim) * blk * (size_t)g.num_nodes;
 }
 // Shared memory block 0 needs to stage levels from..L-1 (the layout of mg_stage_layout: rows,
 // inverse diagonal, b, z[2], t and mask per level, each array 16-byte aligned, and the
@@ -316,7 +316,7 @@ static size_t mg_stage_bytes_from(const Grid *g, int L, int npn, int blk, int fr
   size_t b = nd > 0 ? al(sizeof(float) * (size_t)nd * nd) : 0;
   for (int l = from; l < L; ++l) {
     const size_t n = (size_t)g[l].num_nodes;
-    b += al(sizeof(float) * (g[l].dim == 2 ? 7 : 15) * blk * n) + 5 * al(sizeof(float) * npn * n) + al(npn * n);
+    b += al(sizeof(float) * fo_row_slots(g[l].dim) * blk * n) + 5 * al(sizeof(float) * npn * n) + al(npn * n);
   }
   return b;
 }

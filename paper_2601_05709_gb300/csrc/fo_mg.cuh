@@ -362,7 +362,7 @@ __device__ void mg_block_cycle(const MgDev &mg, int from, int *zc) {
 // vectors b, z[2], t.  Bytes needed (each array 16-byte aligned): see mg_stage_bytes.
 template <int D, int NPN, bool FULL>
 __host__ __device__ inline size_t mg_stage_layout(const MgDev &mg, MgDev *out, unsigned char *base) {
-  constexpr int S = ST<D>::S, BLK = FULL ? NPN * NPN : NPN;
+  constexpr int S = ST<D>::SH, BLK = FULL ? NPN * NPN : NPN;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     unsigned char *p = base ? base + off : nullptr;
@@ -399,7 +399,7 @@ __host__ __device__ inline size_t mg_stage_layout(const MgDev &mg, MgDev *out, u
 // Block 0: the staged view mgs of mg (levels >= Lg in shared memory, constants copied).
 template <int D, int NPN, bool FULL>
 __device__ void mg_stage(const MgDev &mg, MgDev &mgs, unsigned char *smem) {
-  constexpr int S = ST<D>::S, BLK = FULL ? NPN * NPN : NPN;
+  constexpr int S = ST<D>::SH, BLK = FULL ? NPN * NPN : NPN;
   {
     const int *src = reinterpret_cast<const int *>(&mg);
     int *dst = reinterpret_cast<int *>(&mgs);

@@ -162,6 +162,20 @@ __device__ __forceinline__ void load_stencil(const Grid &g, const int idx[3], lo
 //
 // WT is the storage type of the weights (T, or BF16 rows of a multigrid level applied in FP32:
 // the difference form keeps the rounded operator's constant kernel and its symmetry).
+// Where the weight of entry e of slot s in node a's row is stored (nb: the slot's neighbour,
+// or a itself outside the grid).  Slots below SH are the node's own; slot s >= SH (offset -m,
+// m = s - SH + 1) is the transpose of the neighbour's slot-m block: entry (i, j) is read as
+// (j, i) of row nb.  Outside the grid nb = a reads an arbitrary stored weight, which the
+// difference form multiplies by x_a - x_a = 0.
+template <int D, int NPN, bool FULL, class WT>
+__device__ __forceinline__ const WT *slot_weight(const WT *W, long long N, long long a, long long nb, int s, int e) {
+  constexpr int BLK = FULL ? NPN * NPN : NPN;
+  if (s < ST<D>::SH) return W + ((long long)s * BLK + e) * N + a;
+  const int m = s - ST<D>::SH + 1;
+  const int et = FULL ? (e % NPN) * NPN + e / NPN : e;
+  return W + ((long long)m * BLK + et) * N + nb;
+}
+
 template <typename T, typename WT>
 __device__ __forceinline__ T stencil_weight(const WT *w) {
   return (T)*w;
@@ -197,10 +211,12 @@ struct StencilOp {
 #pragma unroll
         for (int i = 0; i < NPN; ++i)
 #pragma unroll
-          for (int j = 0; j < NPN; ++j) acc[i] = fma(stencil_weight<T>(W + (s * BLK + i * NPN + j) * N + a), xv[j], acc[i]);
+          for (int j = 0; j < NPN; ++j)
+            acc[i] = fma(stencil_weight<T>(slot_weight<D, NPN, FULL>(W, N, a, nb, s, i * NPN + j)), xv[j], acc[i]);
       } else {
 #pragma unroll
-        for (int c = 0; c < NPN; ++c) acc[c] = fma(stencil_weight<T>(W + (s * BLK + c) * N + a), xv[c], acc[c]);
+        for (int c = 0; c < NPN; ++c)
+          acc[c] = fma(stencil_weight<T>(slot_weight<D, NPN, FULL>(W, N, a, nb, s, c)), xv[c], acc[c]);
       }
     }
 #pragma unroll
