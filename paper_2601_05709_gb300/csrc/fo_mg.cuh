@@ -4,11 +4,11 @@
 // The Kuhn triangulation is nested under uniform refinement (each simplex of the grid with
 // n/2 cells per axis is the union of 2^d simplices of the grid with n cells), so the P1 spaces
 // are nested.  The coarse operators are rediscretisations: the P1 operator of the coarse grid
-// with each coarse element's coefficient the mean of its 2^d fine children's.  That equals the
-// Galerkin product P^T A P for the constant-coefficient mass and penalty terms and for a
-// constant A, but not for the stiffness with a discontinuous A (a preconditioner only needs
-// a spectrally close coarse operator).  Coarse rows are built by the same stencil builder as
-// the fine ones, from the restricted coefficients.  P is P1
+// with each coarse element's coefficient the mean of its 2^d fine children's.  That is the
+// Galerkin product P^T A P of a piecewise-constant A (the coarse hat gradients are constant
+// on a coarse simplex, whose children have equal measure) and of the mass and penalty terms,
+// except next to Dirichlet nodes, where P skips the fine Dirichlet DOFs.  Coarse rows are
+// built by the same stencil builder as the fine ones, from the restricted coefficients.  P is P1
 // interpolation along the Kuhn edges: a fine node with index parities b in {0,1}^d takes the
 // mean of the coarse nodes (i - b)/2 and (i + b)/2; the restriction is P^T.  Smoother: damped
 // Jacobi, nu1 = nu2 sweeps; coarsest level: an exact solve with its precomputed inverse when
