@@ -458,7 +458,7 @@ def survey_pcg_bytes(ndof, nt, nn, d, w):
 # DRAM bytes (read + write) of one state-solve CG launch, from one-pass ncu captures of the
 # kernels as built now (keyed by precision; absent until captured)
 C2_STATE_TRAFFIC = {"fp64": 8.87e6 + 0.74e6}
-C3_STATE_TRAFFIC = {"fp64": 17.33e9 + 2.99e9}
+C3_STATE_TRAFFIC = {}
 
 
 def mg_state_bytes_per_iteration(nx, ny, c):

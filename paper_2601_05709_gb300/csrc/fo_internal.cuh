@@ -106,6 +106,8 @@ struct fo_mg {
   uint8_t *dir[MG_MAX_LEVELS] = {};
   int nd = 0;                              // coarsest level's unknowns when solved directly
   float *ainv = nullptr;                   // [nd][nd] its inverse (FP32)
+  double *adense = nullptr;                // nd > MG_DIRECT_MAX: the FP64 matrix the whole grid
+                                           // inverts ([nd][nd], then 16 doubles: barrier, status)
   void *dev = nullptr;                     // device copy of the level table
   std::vector<unsigned char> host;         // its host image (kept alive for the async copy)
 };

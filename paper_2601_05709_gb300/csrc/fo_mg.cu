@@ -208,8 +208,99 @@ __global__ void k_mg_coarse_inverse(Grid g, const double *W, int n, float *ainv)
   for (int k = threadIdx.x; k < n * n; k += blockDim.x) ainv[k] = (float)A[k];
 }
 
+// The inverse of a coarsest level too large for one block's shared memory (MG_DIRECT_MAX < n
+// <= MG_DIRECT_GRID_MAX): the same FP64 Gauss-Jordan elimination on a dense matrix in global
+// memory, each pivot's update spread over the whole (cooperative) grid with a grid barrier after
+// the update and after the pivot row and column are scaled.  The hierarchy rebuild pays 2n
+// barriers; the V-cycle then solves the coarsest level exactly instead of with nuc sweeps.
+template <int D, int NPN, bool FULL>
+__global__ void k_mg_coarse_inverse_grid(Grid g, const double *W, int n, double *A, float *ainv, GridBar bar) {
+  constexpr int S = ST<D>::S;
+  const long long N = g.num_nodes, nn = (long long)n * n;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long gs = (long long)gridDim.x * blockDim.x;
+  for (long long k = tid; k < nn; k += gs) A[k] = 0.0;
+  if (!grid_sync(bar)) return;
+  for (long long a = tid; a < N; a += gs) {   // rows of node a: each entry written by one thread
+    int idx[3];
+    node_ijk(g, a, idx);
+    for (int c = 0; c < NPN; ++c)
+      for (int k = 0; k < NPN; ++k) {
+        if (!FULL && k != c) continue;
+        const int e = FULL ? c * NPN + k : c;
+        const long long r = a * NPN + c;
+        double diag = W[(long long)e * N + a];
+        for (int s = 1; s < S; ++s) {
+          const long long nb = slot_node<D>(g, idx, a, s);
+          if (nb < 0) continue;
+          const double w = *slot_weight<D, NPN, FULL>(W, N, a, nb, s, e);
+          diag -= w;
+          A[r * n + nb * NPN + k] += w;
+        }
+        A[r * n + a * NPN + k] += diag;
+      }
+  }
+  if (!grid_sync(bar)) return;
+  for (int p = 0; p < n; ++p) {
+    const double q = 1.0 / A[(long long)p * n + p];
+    for (long long k = tid; k < nn; k += gs) {   // outside row and column p
+      const long long i = k / n, j = k - i * n;
+      if (i != p && j != p) A[k] -= A[i * n + p] * A[(long long)p * n + j] * q;
+    }
+    if (!grid_sync(bar)) return;
+    for (long long k = tid; k < n; k += gs)
+      if (k != p) {
+        A[(long long)p * n + k] *= q;
+        A[k * n + p] *= -q;
+      }
+    if (tid == 0) A[(long long)p * n + p] = q;
+    if (!grid_sync(bar)) return;
+  }
+  for (long long k = tid; k < nn; k += gs) ainv[k] = (float)A[k];
+}
+
+static fo_status mg_build_inverse_grid(fo_ctx *ctx, fo_mg *mg) {
+  const Grid &gc = mg->g[mg->L - 1];
+  const double *W = mg->W64[mg->L - 1];
+  const int n = mg->nd;
+  double *tail = mg->adense + (size_t)n * n;   // barrier counter and status word
+  GridBar bar{reinterpret_cast<unsigned *>(tail), reinterpret_cast<int *>(tail + 8), 2000000000ull};
+  auto run = [&](auto kern) -> fo_status {
+    int per_sm = 0;
+    FO_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)kern, FO_BLOCK, 0));
+    if (per_sm < 1) return fo_fail(ctx, FO_ECUDA, "coarse inverse kernel does not fit on an SM");
+    long long cap = (long long)per_sm * ctx->num_sms;
+    if (ctx->grid_share > 1) cap = std::max(1LL, cap / ctx->grid_share);
+    // one block per SM at most: the 2n barriers, not the n^3 flops, set the time
+    const int grid = (int)std::min<long long>(std::min<long long>(cap, ctx->num_sms),
+                                              ((long long)n * n + FO_BLOCK - 1) / FO_BLOCK);
+    FO_CU(ctx, cudaMemsetAsync(tail, 0, 16 * sizeof(double), ctx->stream));
+    void *argv[] = {(void *)&gc, (void *)&W, (void *)&n, (void *)&mg->adense, (void *)&mg->ainv, (void *)&bar};
+    {
+      std::lock_guard<std::mutex> lk(fo_launch_mutex());
+      FO_CU(ctx, cudaLaunchCooperativeKernel((const void *)kern, grid, FO_BLOCK, argv, 0, ctx->stream));
+    }
+    fo_note_launch(1);
+    FO_CU(ctx, cudaGetLastError());
+    FO_CU(ctx, cudaMemcpyAsync(ctx->h_scalars + 48, tail + 8, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    FO_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    if (*reinterpret_cast<const int *>(ctx->h_scalars + 48) == DEV_TIMEOUT)
+      return fo_fail(ctx, FO_ETIMEOUT, "grid barrier timed out in the coarse inverse");
+    return FO_OK;
+  };
+  if (gc.dim == 2) {
+    if (mg->npn == 1) return run(k_mg_coarse_inverse_grid<2, 1, true>);
+    if (mg->blk == 4) return run(k_mg_coarse_inverse_grid<2, 2, true>);
+    return run(k_mg_coarse_inverse_grid<2, 2, false>);
+  }
+  if (mg->npn == 1) return run(k_mg_coarse_inverse_grid<3, 1, true>);
+  if (mg->blk == 9) return run(k_mg_coarse_inverse_grid<3, 3, true>);
+  return run(k_mg_coarse_inverse_grid<3, 3, false>);
+}
+
 static fo_status mg_build_inverse(fo_ctx *ctx, fo_mg *mg) {
   if (mg->nd == 0) return FO_OK;
+  if (mg->nd > MG_DIRECT_MAX) return mg_build_inverse_grid(ctx, mg);
   const Grid &gc = mg->g[mg->L - 1];
   const double *W = mg->W64[mg->L - 1];
   cudaStream_t s = ctx->stream;
@@ -240,7 +331,7 @@ static int mg_plan_single(const Grid &g0, Grid *g, int npn) {
 static int mg_direct_unknowns(const Grid *g, int L, int npn) {
   if (L < 2) return 0;
   const long long n = g[L - 1].num_nodes * npn;
-  return n <= MG_DIRECT_MAX ? (int)n : 0;
+  return n <= MG_DIRECT_GRID_MAX ? (int)n : 0;
 }
 
 
@@ -313,7 +404,7 @@ static size_t mg_bf16_bytes(const Grid &g, int blk) {
 // coarsest inverse).
 static size_t mg_stage_bytes_from(const Grid *g, int L, int npn, int blk, int from, int nd) {
   auto al = [](size_t b) { return (b + 15) / 16 * 16; };
-  size_t b = nd > 0 ? al(sizeof(float) * (size_t)nd * nd) : 0;
+  size_t b = nd > 0 && nd <= MG_DIRECT_MAX ? al(sizeof(float) * (size_t)nd * nd) : 0;
   for (int l = from; l < L; ++l) {
     const size_t n = (size_t)g[l].num_nodes;
     b += al(sizeof(float) * fo_row_slots(g[l].dim) * blk * n) + 5 * al(sizeof(float) * npn * n) + al(npn * n);
@@ -352,6 +443,7 @@ static void mg_release(fo_ctx *ctx, fo_mg *&mg) {
   }
   if (mg->nd > 0) {
     fo_free(ctx, mg->ainv, sizeof(float) * mg->nd * mg->nd);
+    if (mg->adense) fo_free(ctx, mg->adense, sizeof(double) * ((size_t)mg->nd * mg->nd + 16));
   }
   for (int l = 0; l < mg->L; ++l)
     if (mg->Wh[l]) fo_free(ctx, mg->Wh[l], mg_bf16_bytes(mg->g[l], mg->blk));
@@ -393,7 +485,7 @@ size_t fo_mg_bytes(int dim, const int n[3], int npn, int blk, bool own0, bool bf
   if (bf16)
     for (int l = 0; l < mg_block_level(g, L, npn, blk); ++l) b += mg_bf16_bytes(g[l], blk);
   const size_t nd = (size_t)mg_direct_unknowns(g, L, npn);
-  return b + nd * nd * sizeof(float);
+  return b + nd * nd * sizeof(float) + (nd > MG_DIRECT_MAX ? sizeof(double) * (nd * nd + 16) : 0);
 }
 
 static fo_status mg_alloc(fo_ctx *ctx, fo_mg *&out, const Grid &g0, int npn, int blk, bool own0) {
@@ -412,6 +504,8 @@ static fo_status mg_alloc(fo_ctx *ctx, fo_mg *&out, const Grid &g0, int npn, int
   mg->nd = mg_direct_unknowns(mg->g, mg->L, npn);
   if (mg->nd > 0) {
     FO_TRY(fo_alloc(ctx, (void **)&mg->ainv, sizeof(float) * mg->nd * mg->nd));
+    if (mg->nd > MG_DIRECT_MAX)
+      FO_TRY(fo_alloc(ctx, (void **)&mg->adense, sizeof(double) * ((size_t)mg->nd * mg->nd + 16)));
   }
   FO_TRY(fo_alloc(ctx, (void **)&mg->dev, sizeof(MgDev)));
   return FO_OK;

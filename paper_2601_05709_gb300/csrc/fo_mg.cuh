@@ -32,7 +32,10 @@
 #define MG_BLOCK_DOFS 2048
 #define MG_STAGE_MAX_BYTES (180 * 1024)   // shared memory block 0 may take for its levels
 #define MG_DIRECT_MAX 64                  // coarsest levels of at most this many unknowns are
-                                          // solved with a precomputed inverse
+                                          // solved with a precomputed inverse (built by one block)
+#define MG_DIRECT_GRID_MAX 400            // a coarsest level the hierarchy cannot coarsen below
+                                          // MG_DIRECT_MAX gets one too up to this size (built by the
+                                          // whole grid; its inverse stays in global memory)
 
 struct MgLevelDev {
   Grid g;
@@ -321,10 +324,9 @@ __device__ void mg_block_cycle(const MgDev &mg, int from, int *zc) {
     if (l == mg.L - 1 && mg.nd > 0) {   // exact coarse solve, into the sweeps' final buffer
       c = (sweeps - 1) & 1;
       __syncthreads();
-      for (long long i = t; i < mg.nd; i += st) {
-        const float *row = mg.ainv + i * mg.nd;
-        float acc = 0.f;
-        for (int k = 0; k < mg.nd; ++k) acc = fmaf(row[k], L.b[k], acc);
+      for (long long i = t; i < mg.nd; i += st) {   // z_i = sum_k (A^-1)_ki b_k (A^-1 symmetric:
+        float acc = 0.f;                               // a warp's loads of one k are contiguous)
+        for (int k = 0; k < mg.nd; ++k) acc = fmaf(mg.ainv[(long long)k * mg.nd + i], L.b[k], acc);
         L.z[c][i] = acc;
       }
       zc[l] = c;
@@ -369,7 +371,7 @@ __host__ __device__ inline size_t mg_stage_layout(const MgDev &mg, MgDev *out, u
     off += (bytes + 15) / 16 * 16;
     return p;
   };
-  if (mg.nd > 0) {
+  if (mg.nd > 0 && mg.nd <= MG_DIRECT_MAX) {   // a larger inverse stays in global memory (L2)
     float *a = (float *)take(sizeof(float) * (size_t)mg.nd * mg.nd);
     if (out) out->ainv = a;
   }
@@ -408,7 +410,7 @@ __device__ void mg_stage(const MgDev &mg, MgDev &mgs, unsigned char *smem) {
   __syncthreads();
   if (threadIdx.x == 0) mg_stage_layout<D, NPN, FULL>(mg, &mgs, smem);
   __syncthreads();
-  if (mg.nd > 0)
+  if (mg.nd > 0 && mg.nd <= MG_DIRECT_MAX)
     for (int k = threadIdx.x; k < mg.nd * mg.nd; k += blockDim.x) const_cast<float *>(mgs.ainv)[k] = mg.ainv[k];
   for (int l = mg.Lg; l < mg.L; ++l) {
     const long long n = mg.lv[l].g.num_nodes;
