@@ -457,8 +457,8 @@ def survey_pcg_bytes(ndof, nt, nn, d, w):
 
 # DRAM bytes (read + write) of one state-solve CG launch, from one-pass ncu captures of the
 # kernels as built now (keyed by precision; absent until captured)
-C2_STATE_TRAFFIC = {"fp64": 8.87e6 + 0.74e6}
-C3_STATE_TRAFFIC = {}
+C2_STATE_TRAFFIC = {"fp64": 8.87e6 + 0.78e6}
+C3_STATE_TRAFFIC = {"fp64": 16.09e9 + 2.69e9}
 
 
 def mg_state_bytes_per_iteration(nx, ny, c):
