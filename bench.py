@@ -32,6 +32,7 @@ independent replica of the workload (the step does not shard); rank 0 prints.
 import argparse
 import json
 import os
+import tempfile
 import statistics
 import subprocess
 import sys
@@ -447,7 +448,7 @@ def bench_batch(api, ctx, stream, peaks, n=BATCH_N, maxit=400000, plain=True):
     return out
 
 
-def survey_pcg_bytes(ndof, nt, nn, d, w):
+def algorithmic_pcg_bytes(ndof, nt, nn, d, w):
     """Algorithmic bytes of one PCG iteration on explicit connectivity: 9 vector passes of w-byte
     values over the DOFs (read/write x, r, p; write and read q = A p; read the Jacobi diagonal),
     plus per element its d+1 int32 vertex ids and a 1-byte coefficient flag, plus the FP64
@@ -546,7 +547,7 @@ def bench_configs(api, ctx, stream, peaks):
             kms.append(ctx.solve_kernel_ms())
         st1 = st1[-1]
         w = 4 if prec == api.FO_MIXED else 8
-        bpi = survey_pcg_bytes(ndof, mesh.num_elems, mesh.num_nodes, 3, w)
+        bpi = algorithmic_pcg_bytes(ndof, mesh.num_elems, mesh.num_nodes, 3, w)
         kms_mean = sum(kms) / len(kms)
         achieved = bpi * st1.iterations / (kms_mean / 1e3) / 1e9
         solves[name] = {"solve_ms": sum(reps) / len(reps), "cg_kernel_ms": kms_mean,
@@ -615,7 +616,7 @@ def bench_variants(api, ctx, stream, peaks):
     ms, logs = timed_iters(prob, ro, 3, 10, api.PPL(1))
     its = float(np.mean([l.state.iterations for l in logs]))
     kms = float(np.mean([l.ms_state_kernel for l in logs]))
-    bpi = survey_pcg_bytes(2 * mesh.num_nodes, mesh.num_elems, mesh.num_nodes, 2, 8)
+    bpi = algorithmic_pcg_bytes(2 * mesh.num_nodes, mesh.num_elems, mesh.num_nodes, 2, 8)
     ach = bpi * its / (kms / 1e3) / 1e9
     out["cantilever2d_general_mesh"] = {
         "workload": "the cantilever on a general mesh: 256x128 Kuhn arrays, interior nodes jittered by 0.3 cell, "
@@ -625,7 +626,7 @@ def bench_variants(api, ctx, stream, peaks):
                               for k in ("state", "velocity", "transport")},
         "roofline": {"bound": "hbm", "kernel": "k_pcg<2, CsrOp<2, double>, double, 1>", "achieved": ach, "peak": hbm,
                      "unit": "GB/s", "frac": ach / hbm, "algorithmic_bytes_per_iteration": bpi, "traffic": None,
-                     "note": "survey model bytes x iterations / the PCG launch's CUDA-event time"}}
+                     "note": "algorithmic model bytes x iterations / the PCG launch's CUDA-event time"}}
     prob.close()
 
     def box(desc_kw):
@@ -912,8 +913,7 @@ def main():
         raise SystemExit("at least 3 warm-up steps")
     # the CPU baseline runs first, in its own interpreter, before this process touches CUDA
     cpu = cpu_omp = None
-    dump = os.path.join(ROOT, "gpurun_out", "_oracle_iter0.npz") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) \
-        else os.path.join("/tmp", f"_oracle_iter0_{os.getpid()}.npz")
+    dump = os.path.join(tempfile.gettempdir(), f"_oracle_iter0_{os.getpid()}.npz")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(CPU_SAMPLE_ITERS, warm=args.warmup, dump=dump)
         cpu_omp = oracle_omp_pcg()
@@ -990,11 +990,11 @@ def main():
     except OSError:
         pass
     if args.precond == "mg":
-        # algorithmic bytes of one CG iteration in the survey's model (9 vector passes of the
+        # algorithmic bytes of one CG iteration in the connectivity-based model (9 vector passes of the
         # state DOFs plus connectivity, coefficient flags and coordinates), per launch of the
         # state solve; the time is that launch alone (CUDA events around it, no hierarchy rebuild)
         w = 8 if args.precision == "fp64" else 4
-        bpi = survey_pcg_bytes(2 * mesh.num_nodes, 2 * NX * NY, mesh.num_nodes, 2, w)
+        bpi = algorithmic_pcg_bytes(2 * mesh.num_nodes, 2 * NX * NY, mesh.num_nodes, 2, w)
         launch_ms = sum(l.ms_state_kernel for l in logs) / len(logs)
         its_per_launch = state_iters / len(logs)
         achieved = bpi * its_per_launch / (launch_ms / 1e3) / 1e9
