@@ -389,88 +389,108 @@ __global__ void k_f2d(const float *x, double *y, long long n) {
 // A_e|e| [lam (g_m)_i (g_l)_j + mu (g_m)_j (g_l)_i + mu delta_ij g_m . g_l] coupling component i of
 // the node with component j of vertex l (plane strain / 3D Lame constants).
 template <int D, int NPN>
-__global__ void k_state_stencil(Grid g, const double *coef, const uint8_t *dir, double lam, double mu, double w2,
-                                double *W, float *W32, double *dinv, float *dinv32) {
+__device__ __forceinline__ void state_stencil_node(const Grid &g, long long a, const double *coef, const uint8_t *dir,
+                                                   double lam, double mu, double w2, double *W, float *W32,
+                                                   double *dinv, float *dinv32) {
   constexpr int S = ST<D>::S, BLK = NPN * NPN;
   const long long N = g.num_nodes;
   const double mref = g.vol_e / ((D + 1) * (D + 2));
-  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < N; a += (long long)gridDim.x * blockDim.x) {
-    int idx[3];
-    node_ijk(g, a, idx);
-    double w[S][BLK];
-    double R[BLK];
+  int idx[3];
+  node_ijk(g, a, idx);
+  double w[S][BLK];
+  double R[BLK];
 #pragma unroll
-    for (int k = 0; k < BLK; ++k) R[k] = 0.0;
+  for (int k = 0; k < BLK; ++k) R[k] = 0.0;
 #pragma unroll
-    for (int s = 0; s < S; ++s)
+  for (int s = 0; s < S; ++s)
 #pragma unroll
-      for (int k = 0; k < BLK; ++k) w[s][k] = 0.0;
+    for (int k = 0; k < BLK; ++k) w[s][k] = 0.0;
 #pragma unroll
-    for (int p = 0; p < KP<D>::P; ++p)
+  for (int p = 0; p < KP<D>::P; ++p)
 #pragma unroll
-      for (int m = 0; m <= D; ++m) {
-        long long e;
-        if (!elem_of<D>(g, idx, p, m, e)) continue;
-        const double Av = coef[e] * g.vol_e;
-        double gm[3];
-        kuhn_grad<D>(g, p, m, gm);
-        if (NPN == 1 && w2 != 0.0) R[0] += w2 * mref * (D + 2);   // mass row sum
+    for (int m = 0; m <= D; ++m) {
+      long long e;
+      if (!elem_of<D>(g, idx, p, m, e)) continue;
+      const double Av = coef[e] * g.vol_e;
+      double gm[3];
+      kuhn_grad<D>(g, p, m, gm);
+      if (NPN == 1 && w2 != 0.0) R[0] += w2 * mref * (D + 2);   // mass row sum
 #pragma unroll
-        for (int l = 0; l <= D; ++l) {
-          const int sl = rel_slot<D>(p, m, l);
-          double gl[3];
-          kuhn_grad<D>(g, p, l, gl);
-          double dot = 0.0;
+      for (int l = 0; l <= D; ++l) {
+        const int sl = rel_slot<D>(p, m, l);
+        double gl[3];
+        kuhn_grad<D>(g, p, l, gl);
+        double dot = 0.0;
 #pragma unroll
-          for (int k = 0; k < D; ++k) dot += gm[k] * gl[k];
-          if (NPN == 1) {
-            w[sl][0] += Av * dot + (w2 != 0.0 ? w2 * mref * (l == m ? 2.0 : 1.0) : 0.0);
-          } else {
+        for (int k = 0; k < D; ++k) dot += gm[k] * gl[k];
+        if (NPN == 1) {
+          w[sl][0] += Av * dot + (w2 != 0.0 ? w2 * mref * (l == m ? 2.0 : 1.0) : 0.0);
+        } else {
 #pragma unroll
-            for (int i = 0; i < NPN; ++i)
+          for (int i = 0; i < NPN; ++i)
 #pragma unroll
-              for (int j = 0; j < NPN; ++j)
-                w[sl][i * NPN + j] += Av * (lam * gm[i] * gl[j] + mu * gm[j] * gl[i] + (i == j ? mu * dot : 0.0));
-          }
+            for (int j = 0; j < NPN; ++j)
+              w[sl][i * NPN + j] += Av * (lam * gm[i] * gl[j] + mu * gm[j] * gl[i] + (i == j ? mu * dot : 0.0));
         }
       }
-    // eliminated Dirichlet columns leave the row: their weight comes off the row sum
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      const long long nb = slot_node<D>(g, idx, a, s);
-#pragma unroll
-      for (int j = 0; j < NPN; ++j)
-        if (nb >= 0 && dir[nb * NPN + j])
-#pragma unroll
-          for (int i = 0; i < NPN; ++i) {
-            R[i * NPN + j] -= w[s][i * NPN + j];
-            w[s][i * NPN + j] = 0.0;
-          }
     }
+  // eliminated Dirichlet columns leave the row: their weight comes off the row sum
 #pragma unroll
-    for (int i = 0; i < NPN; ++i) {
-      const double diag = dir[a * NPN + i] ? 1.0 : w[0][i * NPN + i];
-      dinv[a * NPN + i] = 1.0 / diag;
-      dinv32[a * NPN + i] = (float)(1.0 / diag);
-      if (dir[a * NPN + i]) {   // identity row
+  for (int s = 0; s < S; ++s) {
+    const long long nb = slot_node<D>(g, idx, a, s);
 #pragma unroll
-        for (int s = 0; s < S; ++s)
+    for (int j = 0; j < NPN; ++j)
+      if (nb >= 0 && dir[nb * NPN + j])
 #pragma unroll
-          for (int j = 0; j < NPN; ++j) w[s][i * NPN + j] = 0.0;
-#pragma unroll
-        for (int j = 0; j < NPN; ++j) R[i * NPN + j] = (i == j) ? 1.0 : 0.0;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < BLK; ++k) w[0][k] = R[k];
-#pragma unroll
-    for (int s = 0; s < ST<D>::SH; ++s)   // the stored slots (symmetric operator)
-#pragma unroll
-      for (int k = 0; k < BLK; ++k) {
-        W[(s * BLK + k) * N + a] = w[s][k];
-        W32[(s * BLK + k) * N + a] = (float)w[s][k];
-      }
+        for (int i = 0; i < NPN; ++i) {
+          R[i * NPN + j] -= w[s][i * NPN + j];
+          w[s][i * NPN + j] = 0.0;
+        }
   }
+#pragma unroll
+  for (int i = 0; i < NPN; ++i) {
+    const double diag = dir[a * NPN + i] ? 1.0 : w[0][i * NPN + i];
+    dinv[a * NPN + i] = 1.0 / diag;
+    dinv32[a * NPN + i] = (float)(1.0 / diag);
+    if (dir[a * NPN + i]) {   // identity row
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+#pragma unroll
+        for (int j = 0; j < NPN; ++j) w[s][i * NPN + j] = 0.0;
+#pragma unroll
+      for (int j = 0; j < NPN; ++j) R[i * NPN + j] = (i == j) ? 1.0 : 0.0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < BLK; ++k) w[0][k] = R[k];
+#pragma unroll
+  for (int s = 0; s < ST<D>::SH; ++s)   // the stored slots (symmetric operator)
+#pragma unroll
+    for (int k = 0; k < BLK; ++k) {
+      W[(s * BLK + k) * N + a] = w[s][k];
+      W32[(s * BLK + k) * N + a] = (float)w[s][k];
+    }
+}
+
+template <int D, int NPN>
+__global__ void k_state_stencil(Grid g, const double *coef, const uint8_t *dir, double lam, double mu, double w2,
+                                double *W, float *W32, double *dinv, float *dinv32) {
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < g.num_nodes;
+       a += (long long)gridDim.x * blockDim.x)
+    state_stencil_node<D, NPN>(g, a, coef, dir, lam, mu, w2, W, W32, dinv, dinv32);
+}
+
+// The rows of several grids in one launch (the coarse levels of a multigrid hierarchy: each
+// launch of a small level is latency bound, ~30 us whatever its size, so one launch for all
+// of them costs about what one did).  Blocks first_block[k] .. first_block[k + 1] - 1 take
+// level k, one node per thread.
+template <int D, int NPN>
+__global__ void k_state_stencil_levels(StencilLevels L, double lam, double mu, double w2) {
+  int k = 0;
+  while (k + 1 < L.n && (int)blockIdx.x >= L.first_block[k + 1]) ++k;
+  const long long a = (long long)((int)blockIdx.x - L.first_block[k]) * blockDim.x + threadIdx.x;
+  if (a < L.g[k].num_nodes)
+    state_stencil_node<D, NPN>(L.g[k], a, L.coef[k], L.dir[k], lam, mu, w2, L.W[k], L.W32[k], L.di[k], L.di32[k]);
 }
 
 // Rows of the velocity form B of node a (component-diagonal), in difference form as above: for
@@ -615,6 +635,24 @@ fo_status fo_launch_stencil_on(fo_problem *p, const Grid &g, const double *coef,
   } else {
     if (g.dim == 2) k_state_stencil<2, 1><<<blocks, FO_BLOCK, 0, s>>>(g, coef, dir, 0.0, 0.0, w2, W, W32, di, di32);
     else k_state_stencil<3, 1><<<blocks, FO_BLOCK, 0, s>>>(g, coef, dir, 0.0, 0.0, w2, W, W32, di, di32);
+  }
+  fo_note_launch(1);
+  FO_CU(p->ctx, cudaGetLastError());
+  return FO_OK;
+}
+
+fo_status fo_launch_stencil_levels(fo_problem *p, const StencilLevels &L) {
+  if (L.n == 0) return FO_OK;
+  const int blocks = L.first_block[L.n];
+  cudaStream_t s = p->ctx->stream;
+  const double w2 = p->desc.kind == FO_HELMHOLTZ ? p->desc.omega * p->desc.omega : 0.0;
+  const int dim = L.g[0].dim;
+  if (p->desc.kind == FO_ELASTIC) {
+    if (dim == 2) k_state_stencil_levels<2, 2><<<blocks, FO_BLOCK, 0, s>>>(L, p->lame_lambda, p->lame_mu, 0.0);
+    else k_state_stencil_levels<3, 3><<<blocks, FO_BLOCK, 0, s>>>(L, p->lame_lambda, p->lame_mu, 0.0);
+  } else {
+    if (dim == 2) k_state_stencil_levels<2, 1><<<blocks, FO_BLOCK, 0, s>>>(L, 0.0, 0.0, w2);
+    else k_state_stencil_levels<3, 1><<<blocks, FO_BLOCK, 0, s>>>(L, 0.0, 0.0, w2);
   }
   fo_note_launch(1);
   FO_CU(p->ctx, cudaGetLastError());

@@ -576,6 +576,19 @@ fo_status fo_batch_read(fo_problem *p, fo_solve_stats *st, const fo_solve_opts *
 fo_status fo_velocity_pcg_mg(fo_problem *p, const fo_solve_opts *o, double *Btt, fo_solve_stats *st);
 fo_status fo_launch_velocity_stencil_on(fo_problem *p, const Grid &g, const double *mcoef, const uint8_t *dofmask,
                                         double *W, float *W32, double *dinv, float *dinv32);
+// State rows of several grids in one launch (the coarse levels of a hierarchy).
+struct StencilLevels {
+  int n = 0;
+  Grid g[MG_MAX_LEVELS];
+  const double *coef[MG_MAX_LEVELS];
+  const uint8_t *dir[MG_MAX_LEVELS];
+  double *W[MG_MAX_LEVELS];
+  float *W32[MG_MAX_LEVELS];
+  double *di[MG_MAX_LEVELS];
+  float *di32[MG_MAX_LEVELS];
+  int first_block[MG_MAX_LEVELS + 1];
+};
+fo_status fo_launch_stencil_levels(fo_problem *p, const StencilLevels &L);
 fo_status fo_launch_stencil_on(fo_problem *p, const Grid &g, const double *coef, const uint8_t *dir, double *W,
                                float *W32, double *dinv, float *dinv32);
 fo_status fo_launch_loads(fo_problem *p);

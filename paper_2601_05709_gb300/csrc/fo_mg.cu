@@ -601,11 +601,23 @@ static fo_status mg_prepare_state(fo_problem *p, bool bf16) {
     if ((mg->rows_bf16 != 0) == bf16) return FO_OK;
     return mg_upload(ctx, mg, p->Wst32, p->dinv_state32, p->dir, p->ncomp == 1 ? 0.8f : 0.6f, bf16);
   }
+  // coefficients and masks level by level, then every coarse level's rows in one launch
+  StencilLevels sl;
+  sl.first_block[0] = 0;
   for (int l = 1; l < mg->L; ++l) {
     mg_restrict_level(ctx, mg, l, l == 1 ? p->coef : mg->coef[l - 1], l == 1 ? p->dir : mg->dir[l - 1]);
-    FO_TRY(fo_launch_stencil_on(p, mg->g[l], mg->coef[l], mg->dir[l], mg->W64[l], mg->W32[l], mg->dinv64[l],
-                                mg->dinv32[l]));
+    const int k = sl.n++;
+    sl.g[k] = mg->g[l];
+    sl.coef[k] = mg->coef[l];
+    sl.dir[k] = mg->dir[l];
+    sl.W[k] = mg->W64[l];
+    sl.W32[k] = mg->W32[l];
+    sl.di[k] = mg->dinv64[l];
+    sl.di32[k] = mg->dinv32[l];
+    sl.first_block[k + 1] = sl.first_block[k] + (int)((mg->g[l].num_nodes + FO_BLOCK - 1) / FO_BLOCK);
   }
+  FO_CU(ctx, cudaGetLastError());
+  FO_TRY(fo_launch_stencil_levels(p, sl));
   FO_TRY(mg_build_inverse(ctx, mg));
   FO_TRY(mg_upload(ctx, mg, p->Wst32, p->dinv_state32, p->dir, p->ncomp == 1 ? 0.8f : 0.6f, bf16));
   mg->built_epoch = p->coef_epoch;
